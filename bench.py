@@ -1,0 +1,422 @@
+#!/usr/bin/env python3
+"""Throughput of multi-resolution inter analysis on GB300.
+
+A step analyses one ladder frame: the reference rung independently (full
+search +-R), then every other rung as a dependent (scaled reference MVs,
++-r refinement, depth n..n+1).  ``value`` is ladder frames per second with
+the planes already resident in HBM; ``e2e`` is the same through the C ABI
+with the planes copied from pinned host memory and every rung's decisions
+read back inside each step.  The same ladder analysed independently (+-R on
+every rung) gives the multi-resolution speedup.
+
+``--impl reference`` times the CPU oracle (the only reference this method
+has) on the host cores for the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2301_12191_gb300 import synth  # noqa: E402
+
+WORKLOADS = {
+    # 1080p source pair -> 1080p / 720p / 540p / 360p rungs; 360p reference
+    "ladder1080": dict(source=(1920, 1080), rungs=[(1920, 1080), (1280, 720), (960, 540), (640, 360)], ref=3,
+                       bit_depth=8, R=32, r=4, qp=27, ctu=64),
+    # 2160p 10-bit source -> six rungs; 360p reference at +-64, dependents +-8
+    "uhd10": dict(source=(3840, 2160), rungs=[(3840, 2160), (2560, 1440), (1920, 1080), (1280, 720), (960, 540),
+                                              (640, 360)], ref=5, bit_depth=10, R=64, r=8, qp=27, ctu=64),
+    # single 416x240 pair, independent only
+    "frame416": dict(source=(416, 240), rungs=[(416, 240)], ref=0, bit_depth=8, R=16, r=4, qp=32, ctu=64),
+}
+METRIC = "ladder frames/sec (multi-resolution inter analysis)"
+UNIT = "ladder_frames/s"
+L2_FLUSH_BYTES = 256 << 20
+
+# DRAM traffic of one full-search launch from an ncu capture, keyed by the
+# hash of the kernel source it was taken on (null once the kernel changes).
+TRAFFIC_NCU = {}
+
+
+def kernel_source_hash(name="me_full.cu"):
+    p = os.path.join(ROOT, "paper_2301_12191_gb300", "csrc", name)
+    return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
+
+
+def make_frames(wl, n_frames, seed0):
+    frames = []
+    for f in range(n_frames):
+        pairs, _ = synth.ladder_pairs(seed0 + f, source=wl["source"], rungs=wl["rungs"][1:],
+                                      bit_depth=wl["bit_depth"], include_source=True)
+        frames.append(pairs)
+    return frames
+
+
+# ---------------------------------------------------------------- clocks --
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ oracle leg --
+def oracle_ladder_frame(wl, pairs, threads):
+    import oracle
+    ref_i = wl["ref"]
+    w, h, c, f = pairs[ref_i]
+    ref_out = oracle.analyze(c, f, qp=wl["qp"], search_range=wl["R"], ctu=wl["ctu"], threads=threads)
+    for i, (w2, h2, c2, f2) in enumerate(pairs):
+        if i == ref_i:
+            continue
+        oracle.analyze(c2, f2, qp=wl["qp"], search_range=wl["r"], ctu=wl["ctu"], threads=threads,
+                       dep={"ref_size": (w, h), "leaf_depth": ref_out["leaf_depth"],
+                            "leaf_mvx": ref_out["leaf_mvx"], "leaf_mvy": ref_out["leaf_mvy"]})
+
+
+def cpu_baseline(wl, frames, budget_s=10.0):
+    """The oracle as it stands, all host cores, whole ladder frames until the
+    budget is used (at least one)."""
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        oracle_ladder_frame(wl, frames[n % len(frames)], threads)
+        n += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} whole ladder frame(s) of the bench workload ({dt:.1f} s)"}
+
+
+# --------------------------------------------------------- device helpers --
+def evals_of(out, grid_size, ctu, rng):
+    """SAD-candidate evaluations (8x8 block x candidate) the analysis made."""
+    total = 0
+    for d, ev in enumerate(out["evaluated"]):
+        S = ctu >> d
+        total += int(np.count_nonzero(ev)) * (S // 8) ** 2 * (2 * rng + 1) ** 2
+    return total
+
+
+def run_ours(args, wl):
+    import torch
+    import torch.distributed as dist
+    from paper_2301_12191_gb300 import ladder as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    n_frames = 4
+    frames = make_frames(wl, n_frames, seed0=1000 * (rank + 1))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, frames)      # before any GPU work in this process
+
+    sizes = [(w, h) for (w, h, _, _) in frames[0]]
+    lad = L.Ladder(sizes, wl["ref"], bit_depth=wl["bit_depth"], ctu_size=wl["ctu"], search_range=wl["R"],
+                   refine_range=wl["r"], max_frames=2)
+    dplanes = [[(L.device_plane(c, dev), L.device_plane(f, dev)) for (_, _, c, f) in fr] for fr in frames]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ref_i, qp = wl["ref"], wl["qp"]
+    n_rungs = len(sizes)
+
+    def step_multi(fi, frame_id=0):
+        pl = dplanes[fi % n_frames]
+        lad.analyze_reference(frame_id, pl[ref_i][0], pl[ref_i][1], qp)
+        for i in range(n_rungs):
+            if i != ref_i:
+                lad.analyze_dependent(i, frame_id, pl[i][0], pl[i][1], qp)
+
+    def step_indep(fi, frame_id=1):
+        pl = dplanes[fi % n_frames]
+        for i in range(n_rungs):
+            lad.analyze_independent(i, frame_id, pl[i][0], pl[i][1], qp)
+
+    def timed(step, K, W):
+        for i in range(W):
+            step(i)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = []
+        for i in range(K):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(i)
+            b.record(stream)
+            flush.fill_(i & 0xff)          # L2 flush between timed steps (not timed)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        lad.sync()
+        return ms
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # evaluation counts (work per step) from one untimed pass
+    step_multi(0)
+    evals_multi = 0
+    for i in range(n_rungs):
+        out = lad.fetch(i, 0)
+        evals_multi += evals_of(out, sizes[i], wl["ctu"], wl["R"] if i == ref_i else wl["r"])
+    evals_indep = 0
+    for (w, h) in sizes:
+        evals_indep += ((w + 7) // 8) * ((h + 7) // 8) * (2 * wl["R"] + 1) ** 2
+
+    K, W = args.steps, args.warmup
+    launches0 = sum(n for n, _ in lad.kernel_stats().values())
+    with ClockSampler(local) as clk:
+        ms_multi = timed(step_multi, K, W)
+    launches1 = sum(n for n, _ in lad.kernel_stats().values())
+    gpu_launches = (launches1 - launches0) * K // (K + W)
+    ms_multi = max_over_ranks(ms_multi)
+    ms_indep = max_over_ranks(timed(step_indep, max(3, K // 2), W))
+    indep_steps = max(3, K // 2)
+
+    # per-kernel device time (events on the launching stream), separate pass
+    lad.kernel_stats(reset=True)
+    lad.profile(True)
+    ms_prof = timed(step_multi, K, 0)
+    stats = lad.kernel_stats(reset=True)
+    lad.profile(False)
+
+    # end to end: pinned host planes in, every rung's decisions out
+    host = [[(torch.from_numpy(np.ascontiguousarray(c).view(np.int16) if c.dtype == np.uint16 else c).pin_memory(),
+              torch.from_numpy(np.ascontiguousarray(f).view(np.int16) if f.dtype == np.uint16 else f).pin_memory())
+             for (_, _, c, f) in fr] for fr in frames]
+    h2d = sum(int(c.numel() * c.element_size() + f.numel() * f.element_size()) for (c, f) in host[0])
+    d2h = 0
+
+    def step_e2e(i):
+        nonlocal d2h
+        pl, hp = dplanes[i % n_frames], host[i % n_frames]
+        for (dc, dr), (hc, hr) in zip(pl, hp):
+            dc.copy_(hc, non_blocking=True)
+            dr.copy_(hr, non_blocking=True)
+        step_multi(i)
+        nbytes = 0
+        for r in range(n_rungs):
+            o = lad.fetch(r, 0)
+            nbytes += sum(a.nbytes for k in ("mvx", "mvy", "sad", "satd", "cost", "best", "split", "evaluated")
+                          for a in o[k]) + o["leaf_depth"].nbytes + o["leaf_mvx"].nbytes + o["leaf_mvy"].nbytes
+        d2h = nbytes
+
+    for i in range(W):
+        step_e2e(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(K):
+        step_e2e(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+
+    props = torch.cuda.get_device_properties(dev)
+    clocks = clk.summary()
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    lanes_per_sm_clk = 4 * 32                     # 4 SM sub-partitions x 32 lanes, one issue per clock
+    absdiff_per_instr = 4 if wl["bit_depth"] == 8 else 2
+    peak = props.multi_processor_count * lanes_per_sm_clk * absdiff_per_instr * sm_max * 1e6 / 1e12
+
+    # dominant kernel of the step
+    dom = max(stats.items(), key=lambda kv: kv[1][1])
+    kname, (klaunch, kms) = dom
+    if kname == "full_search":
+        w, h = sizes[ref_i]
+        algo = ((w + 7) // 8 * 8) * ((h + 7) // 8 * 8) * (2 * wl["R"] + 1) ** 2
+    elif kname == "refine":
+        algo = 64 * (evals_multi - ((sizes[ref_i][0] + 7) // 8) * ((sizes[ref_i][1] + 7) // 8)
+                     * (2 * wl["R"] + 1) ** 2) / max(1, n_rungs - 1)
+    else:
+        algo = None
+    achieved = (algo / (kms / klaunch * 1e-3) / 1e12) if (algo and klaunch) else None
+    traffic = TRAFFIC_NCU.get((kname, args.config, kernel_source_hash()))
+
+    frames_per_s = world * K / (ms_multi * 1e-3)
+    result = {
+        "metric": METRIC,
+        "value": frames_per_s,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": ms_multi / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8" if wl["bit_depth"] == 8 else "u16",
+        "data": "synthetic (seeded sinusoid texture + planted global/patch motion + noise; ladder by Q16 bilinear)",
+        "config": {
+            "workload": args.config,
+            "rungs": [f"{w}x{h}" for (w, h) in sizes],
+            "reference_rung": f"{sizes[ref_i][0]}x{sizes[ref_i][1]}",
+            "search_range": wl["R"], "refine_range": wl["r"], "qp": qp, "ctu": wl["ctu"],
+            "bit_depth": wl["bit_depth"], "distinct_frames": n_frames,
+            "l2": "flushed between timed steps (256 MiB write, outside the step events)",
+            "parallelism": f"replicas x{world} (independent ladders per GPU)",
+        },
+        "sad_candidate_evals_per_s": evals_multi * world * K / (ms_multi * 1e-3),
+        "independent": {
+            "frames_per_s": world * indep_steps / (ms_indep * 1e-3),
+            "ms_per_step": ms_indep / indep_steps,
+            "sad_candidate_evals_per_s": evals_indep * world * indep_steps / (ms_indep * 1e-3),
+        },
+        "multires_speedup_vs_independent": (ms_indep / indep_steps) / (ms_multi / K),
+        "e2e": {"value": world * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(gpu_launches),
+        "kernels": {k: {"launches": n, "ms_total": ms, "share": ms / max(1e-9, sum(v[1] for v in stats.values()))}
+                    for k, (n, ms) in stats.items()},
+        "roofline": {
+            "kernel": kname,
+            "bound": "alu",
+            "achieved": achieved,
+            "peak": peak,
+            "unit": "Tabsdiff/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic,
+            "peak_note": f"{props.multi_processor_count} SMs x 128 lanes x {absdiff_per_instr} absdiff per packed "
+                         f"instruction x {sm_max:.0f} MHz (issue bound of vabsdiff{absdiff_per_instr}.add)",
+            "algorithmic_absdiffs_per_launch": algo,
+            "avg_launch_ms": (kms / klaunch) if klaunch else None,
+        },
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        result["cpu_baseline"] = cpu
+    if world > 1:
+        dist.barrier()
+    if rank == 0:
+        print(json.dumps(result))
+        if args.json_out:
+            with open(args.json_out, "w") as fh:
+                json.dump(result, fh, indent=1)
+    lad.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args, wl):
+    """The oracle on the host cores, same metric and workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    frames = make_frames(wl, 2, seed0=1000)
+    threads = os.cpu_count() or 1
+    for i in range(args.warmup):
+        oracle_ladder_frame(wl, frames[i % 2], threads)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle_ladder_frame(wl, frames[i % 2], threads)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8" if wl["bit_depth"] == 8 else "u16",
+        "data": "synthetic", "config": {"workload": args.config},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} whole ladder frames"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=sorted(WORKLOADS), default="ladder1080")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--json-out", default=None)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    wl = WORKLOADS[args.config]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * ladder.h -- C ABI of libladder.so: GB300 (sm_103a) inter analysis for
+ * multi-resolution (ABR ladder) encoding.
+ *
+ * The library analyses frame pairs (current, reference) of 8- or 10-bit luma:
+ * integer full-search block-matching motion estimation by SAD (Sec. 5.4.1,
+ * SAD equation), then, per CU of the quadtree (Sec. 2.1: a CTU of 64x64,
+ * 32x32 or 16x16 split down to 8x8), an 8x8-Hadamard SATD at the chosen
+ * vector (Sec. 5.4.1, SATD equation) plus lambda(QP) times an MV-bit estimate,
+ * and the bottom-up rate-distortion split decision (Sec. 2.1).  One rung of
+ * the ladder (the reference rung) is analysed independently; the other rungs
+ * are analysed as dependents that reuse the reference rung's co-located CU
+ * depth and its motion vector scaled by the resolution ratio, refined in a
+ * small window (inter-resolution analysis sharing with refinement, Sec. 4.3
+ * and Sec. 6.3; the reuse and refinement controls of App. A.1 / A.2).
+ *
+ * All analysis is integer; results are bit-exact against a plain CPU oracle.
+ *
+ * Threading and streams: a ladder_t is not thread-safe; serialise calls on
+ * one handle.  Every call that takes a stream enqueues work on it and returns
+ * without waiting, except fetch_decisions (waits for its copies) and
+ * ladder_sync.  The analyses of one frame must be enqueued on one stream, or
+ * the caller orders the streams itself (the dependent reads device state that
+ * the reference analysis writes).
+ *
+ * Memory: the caller owns the input planes (device pointers, typically from
+ * PyTorch tensors) and must keep them alive and unmodified until the stream
+ * has passed the call.  The library owns its decision buffers and the
+ * resident reference decisions of each frame slot until ladder_release_frame
+ * or ladder_destroy.  fetch_decisions copies into caller-owned host arrays.
+ */
+#ifndef LADDER_H
+#define LADDER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LADDER_API __attribute__((visibility("default")))
+#else
+#define LADDER_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ladder ladder_t; /* opaque, library-owned */
+
+typedef enum {
+    LADDER_OK = 0,
+    LADDER_E_INVAL = -1,   /* bad argument (geometry, QP, pitch, rung, pointer) */
+    LADDER_E_NOMEM = -2,   /* device or host allocation failed */
+    LADDER_E_NOREF = -3,   /* dependent analysis before its frame's reference */
+    LADDER_E_BUSY = -4,    /* no free frame slot */
+    LADDER_E_CUDA = -5,    /* a CUDA runtime call failed; see ladder_last_error */
+    LADDER_E_TIMEOUT = -6, /* a bounded device wait ran out (device status word) */
+    LADDER_E_STATE = -7    /* call out of order (e.g. fetch before analysis) */
+} ladder_status;
+
+#define LADDER_MAX_DEPTHS 4 /* CU depths 0..3 for a 64x64 CTU: 64, 32, 16, 8 */
+
+typedef struct {
+    int width, height; /* luma size in samples; both must be even */
+} ladder_rung;
+
+typedef struct {
+    int n_rungs;               /* 1..16 */
+    const ladder_rung *rungs;  /* copied at init */
+    int ref_rung;              /* index of the independently analysed rung */
+    int bit_depth;             /* 8 => uint8 samples, 10 => uint16 samples in [0, 1023] */
+    int ctu_size;              /* 16, 32 or 64; smallest CU is 8x8, so depths 0..log2(ctu/8) */
+    int ref_search_range;      /* R: full search +-R around (0,0), 4..64 */
+    int dep_refine_range;      /* r: dependents search +-r around the scaled vector, 0..32 */
+    int dep_depth_lo;          /* allowed dependent leaf depths [Deq+lo, Deq+hi]; */
+    int dep_depth_hi;          /*   defaults 0, +1 (evaluate depth n and n+1) */
+    int dep_use_ref_mv;        /* 1: search centre = scaled reference MV; 0: (0,0) */
+    int satd_mode;             /* 0: 8x8 Hadamard, (sum|T|)>>2; 1: two 4x4 per 8x4 half, >>1 */
+    int max_frames;            /* resident frame slots (1..64) */
+} ladder_geometry;
+
+/* Decisions of one rung for one frame, all in CU raster order of the frame's
+ * depth-d CU grid: cols_d = ceil(W8 / S_d), rows_d = ceil(H8 / S_d) with
+ * W8, H8 the size rounded up to a multiple of 8 and S_d = ctu_size >> d.
+ * Arrays for depths beyond log2(ctu/8) are ignored and may be NULL.
+ * Not-evaluated CUs carry mv = INT16_MIN and sad/satd/cost = INT32_MAX. */
+typedef struct {
+    int16_t *mvx[LADDER_MAX_DEPTHS], *mvy[LADDER_MAX_DEPTHS];
+    int32_t *sad[LADDER_MAX_DEPTHS];   /* SAD at the chosen vector */
+    int32_t *satd[LADDER_MAX_DEPTHS];  /* SATD at the chosen vector */
+    int32_t *cost[LADDER_MAX_DEPTHS];  /* J = SATD + ((lambdaQ16[qp]*bits + 2^15) >> 16) */
+    int32_t *best[LADDER_MAX_DEPTHS];  /* min over the subtree; INT32_MAX if unreachable */
+    uint8_t *split[LADDER_MAX_DEPTHS]; /* 1 = split into four children */
+    uint8_t *evaluated[LADDER_MAX_DEPTHS];
+    uint8_t *leaf_depth;               /* per 8x8, (W8/8) x (H8/8) raster */
+    int16_t *leaf_mvx, *leaf_mvy;      /* per 8x8: vector of its leaf CU */
+} ladder_decisions;
+
+/* Creates a ladder handle: validates the geometry (LADDER_E_INVAL), sizes and
+ * allocates every device buffer up front (LADDER_E_NOMEM), and uploads the
+ * constant tables on `cuda_stream` (a cudaStream_t, NULL for the legacy
+ * default stream).  On success *out owns everything; free with ladder_destroy. */
+LADDER_API ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, ladder_t **out);
+
+/* Independent analysis of the reference rung of frame `frame_id` (any int):
+ * full search +-R for every CU at every depth, SATD, cost and split (the
+ * analysis that the x265 "analysis-save" master encode performs, App. A.1).
+ * `cur` and `ref` are device pointers to W x H planes of the reference rung,
+ * rows `pitch_bytes` apart (a multiple of 16, >= W * sample size).  Claims a
+ * frame slot for `frame_id` (LADDER_E_BUSY if none is free; re-analysing a
+ * frame that holds a slot reuses it).  QP outside 0..51 -> LADDER_E_INVAL. */
+LADDER_API ladder_status analyze_reference(ladder_t *ladder, int frame_id, const void *cur, const void *ref,
+                                long pitch_bytes, int qp, void *cuda_stream);
+
+/* Dependent analysis of rung `rung` (!= ref_rung) of frame `frame_id`: each
+ * CU maps its centre to the reference rung, takes the co-located reference
+ * leaf's depth and MV, searches +-r around the MV scaled by the rung ratio
+ * (round half away from zero) and only at the depths the reference leaf
+ * allows (Sec. 4.3 / 6.3 reuse with refinement).  LADDER_E_NOREF if the
+ * frame's reference rung has not been analysed. */
+LADDER_API ladder_status analyze_dependent(ladder_t *ladder, int rung, int frame_id, const void *cur,
+                                const void *ref, long pitch_bytes, int qp, void *cuda_stream);
+
+/* Independent full search (+-R) of any rung, the per-rung baseline against
+ * which the multi-resolution speedup is measured.  Needs no reference; claims
+ * a frame slot like analyze_reference, and does not change the frame's
+ * reference decisions unless `rung` is the reference rung. */
+LADDER_API ladder_status analyze_independent(ladder_t *ladder, int rung, int frame_id, const void *cur,
+                                  const void *ref, long pitch_bytes, int qp, void *cuda_stream);
+
+/* Copies the decisions of (rung, frame_id) into caller-owned host arrays
+ * (sizes per ladder_grid); NULL members are skipped.  Waits for the copies on
+ * `cuda_stream`, then checks the device status word: LADDER_E_TIMEOUT if a
+ * bounded device wait ran out, LADDER_E_STATE if the rung was not analysed. */
+LADDER_API ladder_status fetch_decisions(ladder_t *ladder, int rung, int frame_id, ladder_decisions *out,
+                              void *cuda_stream);
+
+/* Grid of a rung: dims[2d], dims[2d+1] = cols_d, rows_d for d = 0..dmax, then
+ * dims[2(dmax+1)], dims[2(dmax+1)+1] = 8x8 cols, rows; returns dmax in *n_depths - 1.
+ * `dims` must hold 2 * LADDER_MAX_DEPTHS + 2 ints. */
+LADDER_API ladder_status ladder_grid(const ladder_t *ladder, int rung, int *dims, int *n_depths);
+
+/* Frees the frame slot of `frame_id` (its resident reference decisions).
+ * Enqueued work that still reads the slot must have completed (ladder_sync). */
+LADDER_API ladder_status ladder_release_frame(ladder_t *ladder, int frame_id);
+
+/* Waits for `cuda_stream` and returns the device status word (LADDER_OK or
+ * LADDER_E_TIMEOUT), clearing it. */
+LADDER_API ladder_status ladder_sync(ladder_t *ladder, void *cuda_stream);
+
+/* Frees every buffer; waits for the device first.  NULL is ignored. */
+LADDER_API void ladder_destroy(ladder_t *ladder);
+
+/* Text of the last error on this handle ("" if none).  Valid until the next call. */
+LADDER_API const char *ladder_last_error(const ladder_t *ladder);
+
+/* Kernel timing (tracing).  Launches are always counted per kernel kind;
+ * when timing is enabled every launch is also bracketed by CUDA events on
+ * its own stream (a few microseconds per launch, off by default).  Kinds:
+ * 0 full search, 1 SATD/cost/split, 2 constraint derivation, 3 refinement
+ * search, 4 key initialisation. */
+LADDER_API ladder_status ladder_profile_enable(ladder_t *ladder, int enable);
+
+/* Reads the launch count and the summed event time (ms; 0 when timing was
+ * off) of kernel kind `kind`, waiting for pending events; clears the kind's
+ * counters when `reset` != 0.  LADDER_E_INVAL for an unknown kind. */
+LADDER_API ladder_status ladder_profile_read(ladder_t *ladder, int kind, long *launches, double *total_ms,
+                                             int reset);
+
+/* Library version string. */
+LADDER_API const char *ladder_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LADDER_H */

@@ -49,6 +49,7 @@ class _Job(ctypes.Structure):
         ("ref_leaf_depth", ctypes.c_void_p), ("ref_leaf_mvx", ctypes.c_void_p),
         ("ref_leaf_mvy", ctypes.c_void_p),
         ("depth_lo", ctypes.c_int), ("depth_hi", ctypes.c_int), ("use_ref_mv", ctypes.c_int),
+        ("ctu_mask", ctypes.c_void_p),
     ]
 
 
@@ -132,7 +133,7 @@ def _make_job(cur, ref, qp, ctu, search_range, satd_mode, dep):
 
 
 def analyze(cur, ref, *, qp: int, search_range: int, ctu: int = 64, satd_mode: int = 0,
-            dep: dict | None = None, threads: int | None = None) -> dict:
+            dep: dict | None = None, threads: int | None = None, ctu_mask=None) -> dict:
     """Analyse one frame pair.
 
     ``dep`` (dependent mode) holds ``ref_size=(Wr, Hr)`` and the reference
@@ -145,6 +146,12 @@ def analyze(cur, ref, *, qp: int, search_range: int, ctu: int = 64, satd_mode: i
     lib = _load()
     job, keep = _make_job(cur, ref, qp, ctu, search_range, satd_mode, dep)
     dims, (c8, r8) = grid(job.width, job.height, ctu)
+    if ctu_mask is not None:
+        m = np.ascontiguousarray(np.asarray(ctu_mask, dtype=np.uint8).reshape(-1))
+        if m.size != dims[0][0] * dims[0][1]:
+            raise ValueError("ctu_mask must have one entry per CTU")
+        keep.append(m)
+        job.ctu_mask = m.ctypes.data
     out = {k: [] for k in ("mvx", "mvy", "sad", "satd", "cost", "best", "split", "evaluated")}
     dec = _Decisions()
     for d, (c, r) in enumerate(dims):

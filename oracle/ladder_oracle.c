@@ -61,6 +61,8 @@ typedef struct {
     const int16_t *ref_leaf_mvx, *ref_leaf_mvy;
     int depth_lo, depth_hi;             /* allowed leaf window [Deq+lo, Deq+hi] */
     int use_ref_mv;                     /* 1: centre = scaled reference MV */
+    /* optional CTU sample: analyse only CTUs with ctu_mask[row * cols + col] != 0 */
+    const uint8_t *ctu_mask;
 } oracle_job;
 
 /* ------------------------------------------------------------------ */
@@ -389,6 +391,7 @@ static void *worker(void *arg)
         pthread_mutex_unlock(&c->lock);
         if (row >= c->ctu_rows) break;
         for (int col = 0; col < c->ctu_cols; col++) {
+            if (c->job->ctu_mask && !c->job->ctu_mask[row * c->ctu_cols + col]) continue;
             int x0 = col * c->job->ctu, y0 = row * c->job->ctu;
             analyse_cu(c, 0, x0, y0, 1);
             fill_leaves(c, 0, x0, y0);

@@ -1,0 +1,127 @@
+// ladder_internal.h -- declarations shared by the translation units of
+// libladder.so (kernels + host C ABI).  Not a public header.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ladder_impl {
+
+constexpr int kMaxDepths = 4;
+constexpr int kThreads = 256;  // every analysis kernel runs 256-thread CTAs
+
+// Device status word values (mirror ladder_status).
+constexpr int kStatusOk = 0;
+constexpr int kStatusTimeout = -6;
+
+// Per-CTU layout of the candidate keys written by the motion search and read
+// by the decision kernel: depth d occupies (4^d - 1) / 3 ... (4^(d+1) - 1) / 3,
+// CUs of a depth in raster order inside the CTU.  A key is
+// (SAD << 32) | tb, tb = L1 * K^2 + (dy + r) * K + (dx + r) with K = 2r + 1 and
+// (dx, dy) the offset from the CU's search centre: the unsigned order of keys
+// is the (SAD, |dx|+|dy|, dy, dx) order of the tie-break.
+__host__ __device__ constexpr int key_offset(int d) { return ((1 << (2 * d)) - 1) / 3; }
+__host__ __device__ constexpr int keys_per_ctu(int dmax) { return key_offset(dmax + 1); }
+
+// Dependent-mode rule of one CU, written by the constraint-derivation kernel.
+enum : uint8_t {
+    kRuleEvaluated = 1,  // reachable, inside the 8-aligned frame, allowed as a leaf
+    kRuleCanSplit = 2,   // reachable and (forced or allowed to split)
+    kRuleReachable = 4,  // every ancestor may split
+};
+
+// Geometry of one rung (host and device).
+struct RungGeom {
+    int W, H, W8, H8;
+    int ctu, dmax;
+    int ctu_cols, ctu_rows;
+    int cols[kMaxDepths], rows[kMaxDepths];
+    int cols8, rows8;
+};
+
+// Device decision arrays of one (rung, frame slot).
+struct DevDecisions {
+    int16_t *mvx[kMaxDepths], *mvy[kMaxDepths];
+    int32_t *sad[kMaxDepths], *satd[kMaxDepths], *cost[kMaxDepths], *best[kMaxDepths];
+    uint8_t *split[kMaxDepths], *evaluated[kMaxDepths];
+    uint8_t *leaf_depth;
+    int16_t *leaf_mvx, *leaf_mvy;
+};
+
+// Dependent-mode rule arrays of one (rung, frame slot), per depth, CU raster.
+struct DevRules {
+    int16_t *cx[kMaxDepths], *cy[kMaxDepths];
+    uint8_t *flags[kMaxDepths];
+};
+
+// ---- full search (independent analysis) --------------------------------
+struct FullSearchArgs {
+    const void *cur;      // W x H plane, pitch bytes below
+    long pitch_bytes;
+    int W, H;
+    int R;                // search range
+    int Rp;               // left/right window margin: R rounded up to 16 samples
+    int ntiles;           // candidate tiles of the search square
+    int tiles_per_slice;  // tiles handled by one CTA
+    const int *tiles;     // packed (dx_base & 0xffff) | (dy_base << 16)
+    unsigned long long *keys;  // per CTU keys_per_ctu(dmax), initialised to ~0
+    int *status;
+};
+
+struct FullSearchPlan {
+    int tile_dy, tile_nx;  // candidates per tile: tile_dy rows x tile_nx same-class columns
+    int smem_bytes;
+    int box_w, box_h;      // TMA box (samples x rows)
+    int pitch_words;       // row pitch of each shifted window copy in 32-bit words
+};
+
+// Returns the shared-memory plan for bit depth / CTU / R (box, pitch, bytes).
+FullSearchPlan full_search_plan(int bit_depth, int ctu, int R);
+// Builds the candidate tile list for range R (host); returns the count.
+int full_search_tiles(int bit_depth, int R, int *out, int cap);
+cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchArgs &a, const CUtensorMap &ref_map,
+                               int nslices, int nctus, cudaStream_t s);
+
+// ---- constraint derivation (dependent analysis) --------------------------
+struct RuleArgs {
+    RungGeom g;              // dependent rung
+    int Wr, Hr, cols8_r;     // reference rung size and 8x8 grid width
+    const uint8_t *ref_leaf_depth;
+    const int16_t *ref_leaf_mvx, *ref_leaf_mvy;
+    int depth_lo, depth_hi, use_ref_mv;
+    DevRules rules;
+};
+cudaError_t launch_rules(const RuleArgs &a, cudaStream_t s);
+
+// ---- constrained refinement search (dependent analysis) ------------------
+struct RefineArgs {
+    const void *cur, *ref;
+    long pitch_bytes;
+    RungGeom g;
+    int r;                  // refinement range
+    DevRules rules;
+    unsigned long long *keys;
+    int *status;
+};
+cudaError_t launch_refine(int bit_depth, const RefineArgs &a, cudaStream_t s);
+
+// ---- SATD, cost, split and leaf maps -------------------------------------
+struct DecideArgs {
+    const void *cur, *ref;
+    long pitch_bytes;
+    RungGeom g;
+    int range;              // R (independent) or r (dependent): decodes the keys
+    int dependent;          // 1: rules below give centres and flags
+    DevRules rules;
+    const unsigned long long *keys;
+    int qp;
+    int satd_mode;
+    DevDecisions out;
+};
+cudaError_t launch_decide(int bit_depth, const DecideArgs &a, cudaStream_t s);
+
+// Fills n 64-bit words with ~0 (key initialisation).
+cudaError_t launch_fill_keys(unsigned long long *keys, long n, cudaStream_t s);
+
+}  // namespace ladder_impl

@@ -1,0 +1,285 @@
+"""ctypes binding of libladder.so (C ABI in include/ladder.h).
+
+Argument marshalling only: every step of the analysis runs in the CUDA
+library.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if the library cannot be loaded this module raises.
+
+Functions with the C names (``ladder_init``, ``analyze_reference``,
+``analyze_dependent``, ``analyze_independent``, ``fetch_decisions``,
+``ladder_grid``, ``ladder_sync``, ``ladder_release_frame``,
+``ladder_destroy``) take raw pointers; :class:`Ladder` wraps them for torch
+tensors and numpy outputs.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAX_DEPTHS = 4
+STATUS = {0: "LADDER_OK", -1: "LADDER_E_INVAL", -2: "LADDER_E_NOMEM", -3: "LADDER_E_NOREF",
+          -4: "LADDER_E_BUSY", -5: "LADDER_E_CUDA", -6: "LADDER_E_TIMEOUT", -7: "LADDER_E_STATE"}
+
+
+class LadderError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Rung(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int)]
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n_rungs", ctypes.c_int), ("rungs", ctypes.POINTER(Rung)), ("ref_rung", ctypes.c_int),
+                ("bit_depth", ctypes.c_int), ("ctu_size", ctypes.c_int), ("ref_search_range", ctypes.c_int),
+                ("dep_refine_range", ctypes.c_int), ("dep_depth_lo", ctypes.c_int),
+                ("dep_depth_hi", ctypes.c_int), ("dep_use_ref_mv", ctypes.c_int), ("satd_mode", ctypes.c_int),
+                ("max_frames", ctypes.c_int)]
+
+
+class Decisions(ctypes.Structure):
+    _fields_ = [("mvx", ctypes.c_void_p * MAX_DEPTHS), ("mvy", ctypes.c_void_p * MAX_DEPTHS),
+                ("sad", ctypes.c_void_p * MAX_DEPTHS), ("satd", ctypes.c_void_p * MAX_DEPTHS),
+                ("cost", ctypes.c_void_p * MAX_DEPTHS), ("best", ctypes.c_void_p * MAX_DEPTHS),
+                ("split", ctypes.c_void_p * MAX_DEPTHS), ("evaluated", ctypes.c_void_p * MAX_DEPTHS),
+                ("leaf_depth", ctypes.c_void_p), ("leaf_mvx", ctypes.c_void_p), ("leaf_mvy", ctypes.c_void_p)]
+
+
+# (name, restype, argtypes) of every symbol declared in include/ladder.h
+SIGNATURES = [
+    ("ladder_init", ctypes.c_int, [ctypes.POINTER(Geometry), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    ("analyze_reference", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_long, ctypes.c_int, ctypes.c_void_p]),
+    ("analyze_dependent", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_long, ctypes.c_int, ctypes.c_void_p]),
+    ("analyze_independent", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_long, ctypes.c_int, ctypes.c_void_p]),
+    ("fetch_decisions", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Decisions),
+                                       ctypes.c_void_p]),
+    ("ladder_grid", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int)]),
+    ("ladder_release_frame", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("ladder_sync", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ladder_destroy", None, [ctypes.c_void_p]),
+    ("ladder_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("ladder_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("ladder_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_long),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    ("ladder_version", ctypes.c_char_p, []),
+]
+
+KERNEL_KINDS = ("full_search", "decide", "rules", "refine", "fill_keys")
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libladder.so (building it first when it is missing or stale and
+    nvcc is available); raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and _build.stale():
+        _build.build()
+    if not os.path.exists(path):
+        raise OSError(f"libladder.so not found at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _call(handle, name, *args):
+    lib = load()
+    st = getattr(lib, name)(*args)
+    if st != 0:
+        msg = lib.ladder_last_error(handle).decode() if handle else ""
+        raise LadderError(st, f"{name}: {msg}")
+    return st
+
+
+# ---- C names, raw pointers ------------------------------------------------
+def ladder_init(geometry: Geometry, stream: int = 0) -> int:
+    h = ctypes.c_void_p()
+    st = load().ladder_init(ctypes.byref(geometry), ctypes.c_void_p(stream), ctypes.byref(h))
+    if st != 0:
+        raise LadderError(st, "ladder_init")
+    return h.value
+
+
+def analyze_reference(h, frame_id, cur_ptr, ref_ptr, pitch_bytes, qp, stream=0):
+    return _call(h, "analyze_reference", h, frame_id, cur_ptr, ref_ptr, pitch_bytes, qp, stream)
+
+
+def analyze_dependent(h, rung, frame_id, cur_ptr, ref_ptr, pitch_bytes, qp, stream=0):
+    return _call(h, "analyze_dependent", h, rung, frame_id, cur_ptr, ref_ptr, pitch_bytes, qp, stream)
+
+
+def analyze_independent(h, rung, frame_id, cur_ptr, ref_ptr, pitch_bytes, qp, stream=0):
+    return _call(h, "analyze_independent", h, rung, frame_id, cur_ptr, ref_ptr, pitch_bytes, qp, stream)
+
+
+def fetch_decisions(h, rung, frame_id, decisions: Decisions, stream=0):
+    return _call(h, "fetch_decisions", h, rung, frame_id, ctypes.byref(decisions), stream)
+
+
+def ladder_grid(h, rung):
+    dims = (ctypes.c_int * (2 * MAX_DEPTHS + 2))()
+    nd = ctypes.c_int()
+    _call(h, "ladder_grid", h, rung, dims, ctypes.byref(nd))
+    n = nd.value
+    return [(dims[2 * d], dims[2 * d + 1]) for d in range(n)], (dims[2 * n], dims[2 * n + 1])
+
+
+def ladder_sync(h, stream=0):
+    return _call(h, "ladder_sync", h, stream)
+
+
+def ladder_release_frame(h, frame_id):
+    return _call(h, "ladder_release_frame", h, frame_id)
+
+
+def ladder_destroy(h):
+    load().ladder_destroy(h)
+
+
+def ladder_profile_enable(h, enable: bool):
+    return _call(h, "ladder_profile_enable", h, 1 if enable else 0)
+
+
+def ladder_profile_read(h, kind: int, reset: bool = False):
+    n = ctypes.c_long()
+    ms = ctypes.c_double()
+    _call(h, "ladder_profile_read", h, kind, ctypes.byref(n), ctypes.byref(ms), 1 if reset else 0)
+    return n.value, ms.value
+
+
+# ---- torch convenience ----------------------------------------------------
+def device_plane(array, device="cuda"):
+    """Copies an (H, W) uint8 / uint16 numpy plane into a CUDA tensor whose
+    row pitch is a multiple of 128 bytes; returns the (H, W) view."""
+    import torch
+    a = np.ascontiguousarray(array)
+    H, W = a.shape
+    if a.dtype == np.uint8:
+        tdt, es = torch.uint8, 1
+        src = torch.from_numpy(a)
+    elif a.dtype == np.uint16:
+        tdt, es = torch.int16, 2          # same bits for samples in [0, 1023]
+        src = torch.from_numpy(a.view(np.int16))
+    else:
+        raise ValueError("planes must be uint8 or uint16")
+    pitch = (W * es + 127) // 128 * 128
+    buf = torch.zeros((H, pitch // es), dtype=tdt, device=device)
+    view = buf[:, :W]
+    view.copy_(src.to(device))
+    return view
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _pitch_bytes(t) -> int:
+    return int(t.stride(0) * t.element_size())
+
+
+class Ladder:
+    """One ladder geometry (rungs, reference rung, search ranges) and its
+    resident per-frame decision state on the device."""
+
+    def __init__(self, rungs, ref_rung, *, bit_depth=8, ctu_size=64, search_range=32, refine_range=4,
+                 depth_lo=0, depth_hi=1, use_ref_mv=1, satd_mode=0, max_frames=4, stream=None):
+        self.rungs = [tuple(r) for r in rungs]
+        self._rung_arr = (Rung * len(self.rungs))(*[Rung(w, h) for w, h in self.rungs])
+        g = Geometry(len(self.rungs), self._rung_arr, ref_rung, bit_depth, ctu_size, search_range,
+                     refine_range, depth_lo, depth_hi, use_ref_mv, satd_mode, max_frames)
+        self.geometry = g
+        self.ref_rung = ref_rung
+        self.bit_depth = bit_depth
+        self.ctu_size = ctu_size
+        self.handle = ladder_init(g, _stream_handle(stream))
+
+    def close(self):
+        if self.handle:
+            ladder_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def analyze_reference(self, frame_id, cur, ref, qp, stream=None):
+        analyze_reference(self.handle, frame_id, cur.data_ptr(), ref.data_ptr(), _pitch_bytes(cur), qp,
+                          _stream_handle(stream))
+
+    def analyze_dependent(self, rung, frame_id, cur, ref, qp, stream=None):
+        analyze_dependent(self.handle, rung, frame_id, cur.data_ptr(), ref.data_ptr(), _pitch_bytes(cur), qp,
+                          _stream_handle(stream))
+
+    def analyze_independent(self, rung, frame_id, cur, ref, qp, stream=None):
+        analyze_independent(self.handle, rung, frame_id, cur.data_ptr(), ref.data_ptr(), _pitch_bytes(cur), qp,
+                            _stream_handle(stream))
+
+    def grid(self, rung):
+        return ladder_grid(self.handle, rung)
+
+    def sync(self, stream=None):
+        ladder_sync(self.handle, _stream_handle(stream))
+
+    def release_frame(self, frame_id):
+        ladder_release_frame(self.handle, frame_id)
+
+    def profile(self, enable: bool = True):
+        ladder_profile_enable(self.handle, enable)
+
+    def kernel_stats(self, reset: bool = False) -> dict:
+        """{kind: (launches, summed event ms)} since the last reset."""
+        return {name: ladder_profile_read(self.handle, k, reset) for k, name in enumerate(KERNEL_KINDS)}
+
+    def fetch(self, rung, frame_id, stream=None) -> dict:
+        """Decisions of (rung, frame) as numpy arrays, laid out like the
+        oracle's output (per-depth lists in CU raster order + per-8x8 maps)."""
+        dims, (c8, r8) = self.grid(rung)
+        out = {k: [] for k in ("mvx", "mvy", "sad", "satd", "cost", "best", "split", "evaluated")}
+        dec = Decisions()
+        for d, (c, r) in enumerate(dims):
+            n = c * r
+            for k, dt in (("mvx", np.int16), ("mvy", np.int16), ("sad", np.int32), ("satd", np.int32),
+                          ("cost", np.int32), ("best", np.int32), ("split", np.uint8), ("evaluated", np.uint8)):
+                a = np.zeros(n, dtype=dt)
+                out[k].append(a)
+                getattr(dec, k)[d] = a.ctypes.data
+        for k, dt in (("leaf_depth", np.uint8), ("leaf_mvx", np.int16), ("leaf_mvy", np.int16)):
+            a = np.zeros(c8 * r8, dtype=dt)
+            out[k] = a
+            setattr(dec, k, a.ctypes.data)
+        fetch_decisions(self.handle, rung, frame_id, dec, _stream_handle(stream))
+        out["grid"] = dims
+        out["grid8"] = (c8, r8)
+        out["size"] = self.rungs[rung]
+        return out

@@ -1,0 +1,71 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every
+function that include/ladder.h declares; geometry validation happens before
+any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2301_12191_gb300 import build as lbuild
+from paper_2301_12191_gb300 import ladder as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "ladder.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:LADDER_API\s+)?(?:ladder_status|void|const char\s*\*)\s*\*?\s*(\w+)\s*\(", src, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    lbuild.build()
+    return ctypes.CDLL(lbuild.LIB)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for n in ("ladder_init", "analyze_reference", "analyze_dependent", "fetch_decisions",
+              "analyze_independent", "ladder_release_frame", "ladder_destroy", "ladder_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    bound = {n for n, _, _ in L.SIGNATURES}
+    assert set(_declared_functions()) <= bound
+
+
+def test_version_string(lib):
+    lib.ladder_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.ladder_version()
+
+
+@pytest.mark.parametrize("field,value", [
+    ("bit_depth", 12), ("ctu_size", 48), ("ref_search_range", 3), ("ref_search_range", 65),
+    ("dep_refine_range", 33), ("satd_mode", 2), ("max_frames", 0), ("ref_rung", 2),
+    ("dep_depth_lo", 2), ("dep_use_ref_mv", 3), ("n_rungs", 0),
+])
+def test_invalid_geometry_is_rejected_before_cuda(lib, field, value):
+    rungs = (L.Rung * 2)(L.Rung(640, 360), L.Rung(320, 180))
+    g = L.Geometry(2, rungs, 1, 8, 64, 16, 4, 0, 1, 1, 0, 2)
+    setattr(g, field, value)
+    h = ctypes.c_void_p()
+    lib.ladder_init.restype = ctypes.c_int
+    lib.ladder_init.argtypes = [ctypes.POINTER(L.Geometry), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    assert lib.ladder_init(ctypes.byref(g), None, ctypes.byref(h)) == -1
+    assert not h.value
+
+
+def test_odd_rung_size_rejected(lib):
+    rungs = (L.Rung * 1)(L.Rung(641, 360))
+    g = L.Geometry(1, rungs, 0, 8, 64, 16, 4, 0, 1, 1, 0, 2)
+    h = ctypes.c_void_p()
+    lib.ladder_init.restype = ctypes.c_int
+    assert lib.ladder_init(ctypes.byref(g), None, ctypes.byref(h)) == -1
