@@ -240,14 +240,24 @@ def run_ours(args, wl):
         evals_indep += ((w + 7) // 8) * ((h + 7) // 8) * (2 * wl["R"] + 1) ** 2
 
     K, W = args.steps, args.warmup
-    launches0 = sum(n for n, _ in lad.kernel_stats().values())
+    indep_steps = max(3, K // 2)
     with ClockSampler(local) as clk:
+        # untimed soak so that the clock samples (every 200 ms) see the load
+        t_end = time.perf_counter() + args.soak
+        i = 0
+        while time.perf_counter() < t_end:
+            step_multi(i)
+            i += 1
+            if i % 64 == 0:
+                torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        launches0 = sum(n for n, _ in lad.kernel_stats().values())
         ms_multi = timed(step_multi, K, W)
-    launches1 = sum(n for n, _ in lad.kernel_stats().values())
+        launches1 = sum(n for n, _ in lad.kernel_stats().values())
+        ms_indep = timed(step_indep, indep_steps, W)
     gpu_launches = (launches1 - launches0) * K // (K + W)
     ms_multi = max_over_ranks(ms_multi)
-    ms_indep = max_over_ranks(timed(step_indep, max(3, K // 2), W))
-    indep_steps = max(3, K // 2)
+    ms_indep = max_over_ranks(ms_indep)
 
     # per-kernel device time (events on the launching stream), separate pass
     lad.kernel_stats(reset=True)
@@ -303,7 +313,7 @@ def run_ours(args, wl):
     if kname == "full_search":
         w, h = sizes[ref_i]
         algo = ((w + 7) // 8 * 8) * ((h + 7) // 8 * 8) * (2 * wl["R"] + 1) ** 2
-    elif kname == "refine":
+    elif kname == "dependent":
         algo = 64 * (evals_multi - ((sizes[ref_i][0] + 7) // 8) * ((sizes[ref_i][1] + 7) // 8)
                      * (2 * wl["R"] + 1) ** 2) / max(1, n_rungs - 1)
     else:
@@ -358,7 +368,7 @@ def run_ours(args, wl):
             "algorithmic_absdiffs_per_launch": algo,
             "avg_launch_ms": (kms / klaunch) if klaunch else None,
         },
-        "clocks": clocks,
+        "clocks": dict(clocks, window="untimed soak + timed multi-res and independent loops"),
     }
     if cpu is not None:
         result["cpu_baseline"] = cpu
@@ -408,6 +418,7 @@ def main():
     ap.add_argument("--config", choices=sorted(WORKLOADS), default="ladder1080")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--json-out", default=None)
+    ap.add_argument("--soak", type=float, default=1.5, help="untimed seconds of load before timing (clock sampling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

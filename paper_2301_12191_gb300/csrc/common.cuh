@@ -1,0 +1,338 @@
+// common.cuh -- device helpers shared by the kernels of libladder.so:
+// packed absdiff-accumulate, TMA / mbarrier wrappers with bounded waits,
+// the integer rate term, and the CTU decision step (SATD at the chosen
+// vectors, cost, bottom-up split, leaf maps).
+#pragma once
+
+#include "ladder_internal.h"
+
+namespace ladder_impl {
+namespace dev {
+
+template <typename T> struct Traits;
+template <> struct Traits<uint8_t> { static constexpr int SPW = 4; };   // samples per 32-bit word
+template <> struct Traits<uint16_t> { static constexpr int SPW = 2; };
+
+template <int CTU> struct Ctu {
+    static constexpr int DMAX = CTU == 64 ? 3 : (CTU == 32 ? 2 : 1);
+    static constexpr int NKEY = keys_per_ctu(DMAX);
+    static constexpr int N8 = CTU / 8;
+    static constexpr int NB8 = N8 * N8;
+};
+
+// d = c + sum of |a_i - b_i| over the packed samples of a and b.
+template <int SPW> __device__ __forceinline__ uint32_t sad_acc(uint32_t a, uint32_t b, uint32_t c);
+template <> __device__ __forceinline__ uint32_t sad_acc<4>(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+template <> __device__ __forceinline__ uint32_t sad_acc<2>(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("vabsdiff2.u32.u32.u32.add %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~2^22 polls (over a second with the
+// back-off), so a lost completion cannot hang the GPU.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < (1u << 22); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (it > 32) __nanosleep(256);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Length of the signed Exp-Golomb code se(v).
+__device__ __forceinline__ int se_bits(int v)
+{
+    const unsigned k = v > 0 ? 2u * static_cast<unsigned>(v) - 1u : static_cast<unsigned>(-2 * v);
+    return 2 * (31 - __clz(static_cast<int>(k + 1))) + 1;
+}
+
+// In-place unnormalised Walsh-Hadamard transform of N values (natural order).
+template <int N>
+__device__ __forceinline__ void fwht(int (&v)[N])
+{
+#pragma unroll
+    for (int s = N / 2; s >= 1; s >>= 1)
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if ((i & s) == 0) {
+                const int a = v[i], b = v[i + s];
+                v[i] = a + b;
+                v[i + s] = a - b;
+            }
+}
+
+template <typename T>
+__device__ __forceinline__ int ld_sample(const char *base, long pitch, int x, int y)
+{
+    return static_cast<int>(__ldg(reinterpret_cast<const T *>(base + static_cast<long>(y) * pitch) + x));
+}
+
+// SATD of the 8x8 block at (px, py) against the reference displaced by
+// (mvx, mvy), computed by the 8 lanes of an aligned lane group (lane & 7 =
+// row); every lane of the group returns the block's SATD.  Samples are read
+// with clamping (current: replicate to the 8-aligned size; reference: frame
+// edge).  `gmask` is the group's lane mask.
+//   mode 0: 8x8 Hadamard T = H8 D H8^T, (sum |T|) >> 2
+//   mode 1: two 4x4 Hadamards per 8x4 half, (sum of both) >> 1, halves added
+template <typename T>
+__device__ int satd8_group(const void *cur, const void *ref, long pitch, int W, int H, int px, int py, int mvx,
+                           int mvy, int mode, unsigned gmask)
+{
+    const char *cb = static_cast<const char *>(cur);
+    const char *rb = static_cast<const char *>(ref);
+    const int y = threadIdx.x & 7;
+    const int cy = min(py + y, H - 1);
+    const int ry = min(max(py + y + mvy, 0), H - 1);
+    int v[8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+        const int cx = min(px + x, W - 1);
+        const int rx = min(max(px + x + mvx, 0), W - 1);
+        v[x] = ld_sample<T>(cb, pitch, cx, cy) - ld_sample<T>(rb, pitch, rx, ry);
+    }
+    if (mode == 0) {
+        fwht<8>(v);  // along the row
+#pragma unroll
+        for (int s = 4; s >= 1; s >>= 1) {  // along the column: butterflies across lanes
+            const bool upper = y & s;
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                const int o = __shfl_xor_sync(gmask, v[x], s);
+                v[x] = upper ? o - v[x] : v[x] + o;
+            }
+        }
+        int sum = 0;
+#pragma unroll
+        for (int x = 0; x < 8; ++x) sum += abs(v[x]);
+#pragma unroll
+        for (int s = 4; s >= 1; s >>= 1) sum += __shfl_xor_sync(gmask, sum, s);
+        return sum >> 2;
+    }
+    int lo[4] = {v[0], v[1], v[2], v[3]}, hi[4] = {v[4], v[5], v[6], v[7]};
+    fwht<4>(lo);
+    fwht<4>(hi);
+#pragma unroll
+    for (int s = 2; s >= 1; s >>= 1) {  // columns of each 4-row half
+        const bool upper = y & s;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int ol = __shfl_xor_sync(gmask, lo[x], s);
+            const int oh = __shfl_xor_sync(gmask, hi[x], s);
+            lo[x] = upper ? ol - lo[x] : lo[x] + ol;
+            hi[x] = upper ? oh - hi[x] : hi[x] + oh;
+        }
+    }
+    int sum = 0;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) sum += abs(lo[x]) + abs(hi[x]);
+#pragma unroll
+    for (int s = 2; s >= 1; s >>= 1) sum += __shfl_xor_sync(gmask, sum, s);  // one 8x4 half
+    sum >>= 1;
+    sum += __shfl_xor_sync(gmask, sum, 4);                                  // both halves
+    return sum;
+}
+
+constexpr uint8_t kPresent = 8;  // CU lies (at least partly) inside the 8-aligned frame
+
+// Per-CTU state of the decision step, in shared memory.
+template <int CTU>
+struct CtuState {
+    int32_t satd[Ctu<CTU>::NKEY], sad[Ctu<CTU>::NKEY], best[Ctu<CTU>::NKEY];
+    int16_t mvx[Ctu<CTU>::NKEY], mvy[Ctu<CTU>::NKEY];
+    uint8_t flags[Ctu<CTU>::NKEY], split[Ctu<CTU>::NKEY];
+};
+
+struct DecideIO {
+    const void *cur, *ref;
+    long pitch_bytes;
+    const RungGeom *g;
+    int qp, satd_mode;
+    const int *lambda_q16;  // 52 entries
+    DevDecisions out;
+};
+
+// Index of CU (d, local raster li) in the per-CTU key layout.
+__device__ __forceinline__ int key_index(int d, int li) { return key_offset(d) + li; }
+
+// The decision step for one CTU, given flags / vectors / SADs in `st`
+// (satd[] must be zero).  All threads of the CTA take part.
+//   SATD   -- Sec. 5.4.1 SATD equation; Sec. 5.4.2 satd8 / satd_8x4 listings
+//   cost   -- J = SATD + ((lambdaQ16[qp] * bits + 2^15) >> 16), bits = se()
+//             lengths of the quarter-pel components (predictor (0,0))
+//   split  -- Sec. 2.1: split iff it may and (it is not a leaf candidate or
+//             the children's best sum is strictly lower), or it must
+template <typename T, int CTU>
+__device__ void ctu_decide(CtuState<CTU> &st, const DecideIO &io, int x0, int y0)
+{
+    using C = Ctu<CTU>;
+    const RungGeom &g = *io.g;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+
+    // SATD: one 8-lane group per (depth, 8x8 block) pair of an evaluated CU
+    const unsigned gmask = 0xffu << (tid & 24);
+    for (int t = tid >> 3; t < (C::DMAX + 1) * C::NB8; t += nthr >> 3) {
+        const int d = t / C::NB8, b = t % C::NB8;
+        const int bx = b % C::N8, by = b / C::N8;
+        const int S = CTU >> d;
+        const int i = key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S);
+        if (!(st.flags[i] & kRuleEvaluated)) continue;
+        const int v = satd8_group<T>(io.cur, io.ref, io.pitch_bytes, g.W, g.H, x0 + 8 * bx, y0 + 8 * by,
+                                     st.mvx[i], st.mvy[i], io.satd_mode, gmask);
+        if ((tid & 7) == 0) atomicAdd(&st.satd[i], v);
+    }
+    __syncthreads();
+
+    const int lam = io.lambda_q16[io.qp];
+    for (int d = C::DMAX; d >= 0; --d) {
+        const int n = 1 << d, S = CTU >> d;
+        for (int li = tid; li < n * n; li += nthr) {
+            const int i = key_index(d, li);
+            const uint8_t f = st.flags[i];
+            if (!(f & kPresent)) continue;
+            const bool ev = f & kRuleEvaluated;
+            int32_t J = INT32_MAX;
+            if (ev) {
+                const long long bits = se_bits(4 * st.mvx[i]) + se_bits(4 * st.mvy[i]);
+                J = st.satd[i] + static_cast<int32_t>((static_cast<long long>(lam) * bits + 32768) >> 16);
+            }
+            int32_t best = J;
+            uint8_t split = 0;
+            if (d < C::DMAX) {
+                const bool can_split = f & kRuleCanSplit;
+                int32_t children = 0;
+                if (can_split) {
+                    const int cxl = li % n, cyl = li / n;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int ci = key_index(d + 1, (2 * cyl + (q >> 1)) * (2 * n) + 2 * cxl + (q & 1));
+                        if (st.flags[ci] & kPresent) children += st.best[ci];
+                    }
+                }
+                split = can_split && (!ev || children < J);
+                best = !(f & kRuleReachable) ? INT32_MAX : (split ? children : J);
+            }
+            st.best[i] = best;
+            st.split[i] = split;
+            const long gi = static_cast<long>(y0 / S + li / n) * g.cols[d] + x0 / S + li % n;
+            io.out.mvx[d][gi] = st.mvx[i];
+            io.out.mvy[d][gi] = st.mvy[i];
+            io.out.sad[d][gi] = st.sad[i];
+            io.out.satd[d][gi] = ev ? st.satd[i] : INT32_MAX;
+            io.out.cost[d][gi] = J;
+            io.out.best[d][gi] = best;
+            io.out.split[d][gi] = split;
+            io.out.evaluated[d][gi] = ev ? 1 : 0;
+        }
+        __syncthreads();
+    }
+
+    for (int b = tid; b < C::NB8; b += nthr) {
+        const int bx = b % C::N8, by = b / C::N8;
+        const int px = x0 + 8 * bx, py = y0 + 8 * by;
+        if (px >= g.W8 || py >= g.H8) continue;
+        int d = 0, i = 0;
+        for (;;) {
+            const int S = CTU >> d;
+            i = key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S);
+            if (d == C::DMAX || !st.split[i]) break;
+            ++d;
+        }
+        const long li = static_cast<long>(py / 8) * g.cols8 + px / 8;
+        io.out.leaf_depth[li] = static_cast<uint8_t>(d);
+        io.out.leaf_mvx[li] = st.mvx[i];
+        io.out.leaf_mvy[li] = st.mvy[i];
+    }
+}
+
+// ---- dependent-mode constraint derivation --------------------------------
+// Sec. 4.3 / 6.3 and App. A.1-A.2: a dependent CU maps its centre to the
+// reference rung, takes the co-located reference leaf's depth and vector,
+// scales the vector by the resolution ratio (round half away from zero,
+// clamped to +-256) as its search centre, and bounds its own depth around
+// Deq, the deepest depth whose CU still covers the projected reference leaf.
+struct Rule {
+    int cx, cy;
+    bool allowed_leaf, allowed_split;
+};
+
+__device__ __forceinline__ int scale_component(int v, int to, int from)
+{
+    const long long av = v < 0 ? -static_cast<long long>(v) : v;
+    const long long s = (2 * av * to + from) / (2LL * from);
+    const int r = static_cast<int>(v < 0 ? -s : s);
+    return min(max(r, -256), 256);
+}
+
+__device__ __forceinline__ Rule derive_rule(const RungGeom &g, const DepRefs &rf, int d, int x0, int y0)
+{
+    const int S = g.ctu >> d;
+    long long xm = (static_cast<long long>(2 * x0 + S) * rf.Wr) / (2LL * g.W);
+    long long ym = (static_cast<long long>(2 * y0 + S) * rf.Hr) / (2LL * g.H);
+    xm = xm > rf.Wr - 1 ? rf.Wr - 1 : xm;
+    ym = ym > rf.Hr - 1 ? rf.Hr - 1 : ym;
+    const long li = (ym >> 3) * rf.cols8_r + (xm >> 3);
+    const int depth_r = rf.leaf_depth[li];
+    Rule r;
+    if (rf.use_ref_mv) {
+        r.cx = scale_component(rf.leaf_mvx[li], g.W, rf.Wr);
+        r.cy = scale_component(rf.leaf_mvy[li], g.H, rf.Hr);
+    } else {
+        r.cx = r.cy = 0;
+    }
+    const long long proj = static_cast<long long>(g.ctu >> depth_r) * g.W;
+    int deq = 0;
+    for (int dd = 0; dd <= g.dmax; ++dd)
+        if (static_cast<long long>(g.ctu >> dd) * rf.Wr >= proj) deq = dd;
+    r.allowed_split = d < g.dmax && d < deq + rf.depth_hi;
+    r.allowed_leaf = (deq + rf.depth_lo <= d && d <= deq + rf.depth_hi) || d == g.dmax || !r.allowed_split;
+    return r;
+}
+
+}  // namespace dev
+}  // namespace ladder_impl

@@ -20,7 +20,6 @@ namespace {
 
 struct RungBuffers {
     DevDecisions dec;
-    DevRules rules;
     unsigned long long *keys;
     int analysed;  // 0: nothing, 1: independent, 2: dependent
 };
@@ -39,7 +38,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace
 
-constexpr int kKinds = 5;  // full search, decide, rules, refine, fill keys
+constexpr int kKinds = 4;  // full search, decide, dependent, fill keys
 
 struct ProfEvent {
     int kind;
@@ -166,9 +165,6 @@ size_t carve(const RungGeom &g, char *base, RungBuffers *rb)
         p = take(n * 4); if (rb) rb->dec.best[d] = reinterpret_cast<int32_t *>(p);
         p = take(n); if (rb) rb->dec.split[d] = reinterpret_cast<uint8_t *>(p);
         p = take(n); if (rb) rb->dec.evaluated[d] = reinterpret_cast<uint8_t *>(p);
-        p = take(n * 2); if (rb) rb->rules.cx[d] = reinterpret_cast<int16_t *>(p);
-        p = take(n * 2); if (rb) rb->rules.cy[d] = reinterpret_cast<int16_t *>(p);
-        p = take(n); if (rb) rb->rules.flags[d] = reinterpret_cast<uint8_t *>(p);
     }
     const size_t n8 = static_cast<size_t>(g.cols8) * g.rows8;
     char *p;
@@ -287,7 +283,7 @@ ladder_status run_independent(ladder_t *l, Slot *slot, int rung, const void *cur
     const FullSearchPlan plan = full_search_plan(l->geo.bit_depth, g.ctu, R);
     CUtensorMap map;
     if (!encode_ref_map(l, &map, ref, g, pitch, plan)) return LADDER_E_CUDA;
-    cudaError_t e = traced(l, 4, s, [&] {
+    cudaError_t e = traced(l, 3, s, [&] {
         return launch_fill_keys(rb.keys, static_cast<long>(nctus) * keys_per_ctu(g.dmax), s);
     });
     if (e != cudaSuccess) return cuda_fail(l, e, "fill keys");
@@ -312,7 +308,6 @@ ladder_status run_independent(ladder_t *l, Slot *slot, int rung, const void *cur
     da.pitch_bytes = pitch;
     da.g = g;
     da.range = R;
-    da.dependent = 0;
     da.keys = rb.keys;
     da.qp = qp;
     da.satd_mode = l->geo.satd_mode;
@@ -424,47 +419,27 @@ ladder_status analyze_dependent(ladder_t *l, int rung, int frame_id, const void 
     RungBuffers &rb = slot->rungs[rung];
     const RungBuffers &ref_rb = slot->rungs[l->geo.ref_rung];
 
-    RuleArgs ra{};
-    ra.g = g;
-    ra.Wr = gr.W;
-    ra.Hr = gr.H;
-    ra.cols8_r = gr.cols8;
-    ra.ref_leaf_depth = ref_rb.dec.leaf_depth;
-    ra.ref_leaf_mvx = ref_rb.dec.leaf_mvx;
-    ra.ref_leaf_mvy = ref_rb.dec.leaf_mvy;
-    ra.depth_lo = l->geo.dep_depth_lo;
-    ra.depth_hi = l->geo.dep_depth_hi;
-    ra.use_ref_mv = l->geo.dep_use_ref_mv;
-    ra.rules = rb.rules;
-    cudaError_t e = traced(l, 2, s, [&] { return launch_rules(ra, s); });
-    if (e != cudaSuccess) return cuda_fail(l, e, "rules launch");
-
-    RefineArgs fa{};
-    fa.cur = cur;
-    fa.ref = ref;
-    fa.pitch_bytes = pitch_bytes;
-    fa.g = g;
-    fa.r = l->geo.dep_refine_range;
-    fa.rules = rb.rules;
-    fa.keys = rb.keys;
-    fa.status = l->d_status;
-    e = traced(l, 3, s, [&] { return launch_refine(l->geo.bit_depth, fa, s); });
-    if (e != cudaSuccess) return cuda_fail(l, e, "refine launch");
-
-    DecideArgs da{};
+    DependentArgs da{};
     da.cur = cur;
     da.ref = ref;
     da.pitch_bytes = pitch_bytes;
     da.g = g;
-    da.range = l->geo.dep_refine_range;
-    da.dependent = 1;
-    da.rules = rb.rules;
-    da.keys = rb.keys;
+    da.r = l->geo.dep_refine_range;
+    da.refs.Wr = gr.W;
+    da.refs.Hr = gr.H;
+    da.refs.cols8_r = gr.cols8;
+    da.refs.leaf_depth = ref_rb.dec.leaf_depth;
+    da.refs.leaf_mvx = ref_rb.dec.leaf_mvx;
+    da.refs.leaf_mvy = ref_rb.dec.leaf_mvy;
+    da.refs.depth_lo = l->geo.dep_depth_lo;
+    da.refs.depth_hi = l->geo.dep_depth_hi;
+    da.refs.use_ref_mv = l->geo.dep_use_ref_mv;
     da.qp = qp;
     da.satd_mode = l->geo.satd_mode;
     da.out = rb.dec;
-    e = traced(l, 1, s, [&] { return launch_decide(l->geo.bit_depth, da, s); });
-    if (e != cudaSuccess) return cuda_fail(l, e, "decide launch");
+    da.status = l->d_status;
+    cudaError_t e = traced(l, 2, s, [&] { return launch_dependent(l->geo.bit_depth, da, s); });
+    if (e != cudaSuccess) return cuda_fail(l, e, "dependent launch");
     rb.analysed = 2;
     return LADDER_OK;
 }

@@ -49,12 +49,6 @@ struct DevDecisions {
     int16_t *leaf_mvx, *leaf_mvy;
 };
 
-// Dependent-mode rule arrays of one (rung, frame slot), per depth, CU raster.
-struct DevRules {
-    int16_t *cx[kMaxDepths], *cy[kMaxDepths];
-    uint8_t *flags[kMaxDepths];
-};
-
 // ---- full search (independent analysis) --------------------------------
 struct FullSearchArgs {
     const void *cur;      // W x H plane, pitch bytes below
@@ -83,37 +77,34 @@ int full_search_tiles(int bit_depth, int R, int *out, int cap);
 cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchArgs &a, const CUtensorMap &ref_map,
                                int nslices, int nctus, cudaStream_t s);
 
-// ---- constraint derivation (dependent analysis) --------------------------
-struct RuleArgs {
-    RungGeom g;              // dependent rung
+// ---- dependent analysis (one fused kernel per rung) ------------------------
+// Reference-rung state a dependent rung reads.
+struct DepRefs {
     int Wr, Hr, cols8_r;     // reference rung size and 8x8 grid width
-    const uint8_t *ref_leaf_depth;
-    const int16_t *ref_leaf_mvx, *ref_leaf_mvy;
+    const uint8_t *leaf_depth;
+    const int16_t *leaf_mvx, *leaf_mvy;
     int depth_lo, depth_hi, use_ref_mv;
-    DevRules rules;
 };
-cudaError_t launch_rules(const RuleArgs &a, cudaStream_t s);
 
-// ---- constrained refinement search (dependent analysis) ------------------
-struct RefineArgs {
+struct DependentArgs {
     const void *cur, *ref;
     long pitch_bytes;
     RungGeom g;
     int r;                  // refinement range
-    DevRules rules;
-    unsigned long long *keys;
+    DepRefs refs;
+    int qp, satd_mode;
+    DevDecisions out;
     int *status;
 };
-cudaError_t launch_refine(int bit_depth, const RefineArgs &a, cudaStream_t s);
+// Constraint derivation, refinement search, SATD, cost and split: one CTA per CTU.
+cudaError_t launch_dependent(int bit_depth, const DependentArgs &a, cudaStream_t s);
 
 // ---- SATD, cost, split and leaf maps -------------------------------------
 struct DecideArgs {
     const void *cur, *ref;
     long pitch_bytes;
     RungGeom g;
-    int range;              // R (independent) or r (dependent): decodes the keys
-    int dependent;          // 1: rules below give centres and flags
-    DevRules rules;
+    int range;              // R: decodes the keys
     const unsigned long long *keys;
     int qp;
     int satd_mode;

@@ -1,0 +1,324 @@
+// me_dependent.cu -- dependent analysis of one rung in one kernel (one CTA
+// per CTU): constraint derivation from the resident reference-rung leaves,
+// refinement search around the scaled reference vectors, SATD, cost, split
+// and leaf maps (inter-resolution analysis sharing with refinement,
+// Sec. 4.3 / 6.3; reuse and refinement controls, App. A.1 / A.2).
+//
+// Search layout.  The CTA lists the evaluated CUs of every depth, then
+// spreads (CU, 8x8 block, candidate-row tile, candidate-column chunk) items
+// over its threads.  An item holds the block's 8 current rows in registers,
+// walks the 8 + TY - 1 reference rows it needs once each (aligned 32-bit
+// loads through L1, one funnel shift to the row start, SPW-1 more for the
+// sub-word candidate offsets), and accumulates a TY x KC tile of packed
+// absdiff sums: every reference row feeds up to 8 x KC x (8/SPW) packed
+// instructions.  Block sums are added into a per-CU candidate table in
+// shared memory (integer reductions, so the order is free); one warp per CU
+// then takes the argmin of (SAD, |dx|+|dy|, dy, dx).
+#include "common.cuh"
+
+#include <algorithm>
+
+namespace ladder_impl {
+namespace {
+
+using dev::Traits;
+
+__constant__ int c_lambda_q16[52] = {
+#include "lambda_table.inc"
+};
+
+// SADs of the 8x8 block at (bx, by) for the TY x KC candidates whose
+// reference block starts at (xs + j, ys + i).
+template <typename T, int KC, int TY>
+__device__ __forceinline__ void block_tile_sads(const char *cb, const char *rb, long pitch, int W, int H, int bx,
+                                                int by, int xs, int ys, uint32_t (&acc)[TY][KC])
+{
+    constexpr int SPW = Traits<T>::SPW, BITS = 32 / SPW, WPR = 8 / SPW;
+    constexpr int NWN = (8 + KC - 1 + SPW - 1) / SPW;  // words of a reference row segment
+    uint32_t cw[8][WPR];
+    if (bx + 8 <= W) {
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+            const char *row = cb + static_cast<long>(min(by + y, H - 1)) * pitch + static_cast<long>(bx) * sizeof(T);
+            if constexpr (WPR == 2) {
+                const uint2 v = __ldg(reinterpret_cast<const uint2 *>(row));
+                cw[y][0] = v.x;
+                cw[y][1] = v.y;
+            } else {
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(row));
+                cw[y][0] = v.x;
+                cw[y][1] = v.y;
+                cw[y][2] = v.z;
+                cw[y][3] = v.w;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+            const int cy = min(by + y, H - 1);
+#pragma unroll
+            for (int m = 0; m < WPR; ++m) {
+                uint32_t w = 0;
+#pragma unroll
+                for (int e = 0; e < SPW; ++e)
+                    w |= static_cast<uint32_t>(dev::ld_sample<T>(cb, pitch, min(bx + m * SPW + e, W - 1), cy))
+                         << (e * BITS);
+                cw[y][m] = w;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < TY; ++i)
+#pragma unroll
+        for (int j = 0; j < KC; ++j) acc[i][j] = 0;
+
+    const bool xfast = xs >= 0 && (xs / SPW + NWN + 1) * SPW <= W;
+    const int sh = (xs & (SPW - 1)) * BITS;
+#pragma unroll
+    for (int rr = 0; rr < 8 + TY - 1; ++rr) {
+        const int ry = min(max(ys + rr, 0), H - 1);
+        const char *rowb = rb + static_cast<long>(ry) * pitch;
+        uint32_t nw[NWN];
+        if (xfast) {
+            const uint32_t *rp = reinterpret_cast<const uint32_t *>(rowb) + xs / SPW;
+            uint32_t raw[NWN + 1];
+#pragma unroll
+            for (int m = 0; m <= NWN; ++m) raw[m] = __ldg(rp + m);
+#pragma unroll
+            for (int m = 0; m < NWN; ++m) nw[m] = __funnelshift_r(raw[m], raw[m + 1], sh);
+        } else {
+#pragma unroll
+            for (int m = 0; m < NWN; ++m) {
+                uint32_t w = 0;
+#pragma unroll
+                for (int e = 0; e < SPW; ++e)
+                    w |= static_cast<uint32_t>(dev::ld_sample<T>(rb, pitch, min(max(xs + m * SPW + e, 0), W - 1), ry))
+                         << (e * BITS);
+                nw[m] = w;
+            }
+        }
+        // shw[k][m]: samples starting at sub-word offset k of word m
+        uint32_t shw[SPW][NWN];
+#pragma unroll
+        for (int m = 0; m < NWN; ++m) shw[0][m] = nw[m];
+#pragma unroll
+        for (int k = 1; k < SPW; ++k)
+#pragma unroll
+            for (int m = 0; m + 1 < NWN; ++m) shw[k][m] = __funnelshift_r(nw[m], nw[m + 1], k * BITS);
+#pragma unroll
+        for (int i = 0; i < TY; ++i) {
+            const int j = rr - i;  // current row j meets reference row rr at candidate row i
+            if (j < 0 || j >= 8) continue;
+#pragma unroll
+            for (int jx = 0; jx < KC; ++jx) {
+                const int q = jx / SPW, k = jx % SPW;
+#pragma unroll
+                for (int m = 0; m < WPR; ++m) acc[i][jx] = dev::sad_acc<SPW>(cw[j][m], shw[k][q + m], acc[i][jx]);
+            }
+        }
+    }
+}
+
+template <typename T, int CTU, int KC, int TY>
+__global__ void __launch_bounds__(kThreads) k_dependent(const DependentArgs a, const int batch)
+{
+    using C = dev::Ctu<CTU>;
+    __shared__ dev::CtuState<CTU> st;
+    __shared__ int16_t s_cx[C::NKEY], s_cy[C::NKEY];
+    __shared__ uint8_t s_leaf[C::NKEY], s_splitok[C::NKEY];
+    __shared__ int s_list[C::NKEY];       // evaluated CUs (key index), grouped by depth
+    __shared__ int s_pre[C::NKEY + 1];    // item prefix of the current batch
+    __shared__ int s_cnt[C::DMAX + 1];
+    __shared__ int s_base[C::DMAX + 2];
+    extern __shared__ uint32_t s_sum[];   // per listed CU: (2r+1)^2 candidate sums
+
+    const RungGeom &g = a.g;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ctu_idx = blockIdx.x;
+    const int x0 = (ctu_idx % g.ctu_cols) * CTU, y0 = (ctu_idx / g.ctu_cols) * CTU;
+    const int r = a.r, K = 2 * r + 1, KK = K * K;
+    const char *cb = static_cast<const char *>(a.cur);
+    const char *rb = static_cast<const char *>(a.ref);
+
+    // 1. local rule of every present CU
+    for (int i = tid; i < C::NKEY; i += kThreads) {
+        int d = 0;
+        while (d < C::DMAX && i >= key_offset(d + 1)) ++d;
+        const int li = i - key_offset(d), n = 1 << d, S = CTU >> d;
+        const int cu_x = x0 + (li % n) * S, cu_y = y0 + (li / n) * S;
+        const bool present = cu_x < g.W8 && cu_y < g.H8;
+        uint8_t leaf = 0, splitok = 0;
+        int16_t cx = 0, cy = 0;
+        if (present) {
+            const bool inside = cu_x + S <= g.W8 && cu_y + S <= g.H8;
+            const dev::Rule ru = dev::derive_rule(g, a.refs, d, cu_x, cu_y);
+            cx = static_cast<int16_t>(ru.cx);
+            cy = static_cast<int16_t>(ru.cy);
+            leaf = inside && ru.allowed_leaf;
+            splitok = d < C::DMAX && (!inside || ru.allowed_split);
+        }
+        s_cx[i] = cx;
+        s_cy[i] = cy;
+        s_leaf[i] = leaf;
+        s_splitok[i] = splitok;
+        st.flags[i] = present ? dev::kPresent : 0;
+    }
+    if (tid <= C::DMAX) s_cnt[tid] = 0;
+    __syncthreads();
+
+    // 2. reachability (every ancestor may split) and the decision flags
+    for (int i = tid; i < C::NKEY; i += kThreads) {
+        st.satd[i] = 0;
+        st.mvx[i] = INT16_MIN;
+        st.mvy[i] = INT16_MIN;
+        st.sad[i] = INT32_MAX;
+        if (!(st.flags[i] & dev::kPresent)) continue;
+        int d = 0;
+        while (d < C::DMAX && i >= key_offset(d + 1)) ++d;
+        const int li = i - key_offset(d), n = 1 << d;
+        const int cxl = li % n, cyl = li / n;
+        bool reach = true;
+        for (int e = 0; e < d; ++e)
+            reach = reach && s_splitok[dev::key_index(e, (cyl >> (d - e)) * (1 << e) + (cxl >> (d - e)))];
+        uint8_t f = dev::kPresent;
+        if (reach) f |= kRuleReachable;
+        if (reach && s_leaf[i]) f |= kRuleEvaluated;
+        if (reach && s_splitok[i]) f |= kRuleCanSplit;
+        st.flags[i] = f;
+        if (f & kRuleEvaluated) atomicAdd(&s_cnt[d], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        s_base[0] = 0;
+        for (int d = 0; d <= C::DMAX; ++d) {
+            s_base[d + 1] = s_base[d] + s_cnt[d];
+            s_cnt[d] = 0;
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < C::NKEY; i += kThreads) {
+        if (!(st.flags[i] & kRuleEvaluated)) continue;
+        int d = 0;
+        while (d < C::DMAX && i >= key_offset(d + 1)) ++d;
+        s_list[s_base[d] + atomicAdd(&s_cnt[d], 1)] = i;
+    }
+    __syncthreads();
+    const int n_list = s_base[C::DMAX + 1];
+
+    // 3. refinement search, in batches of CUs that fit the sum table
+    const int n_ty = (K + TY - 1) / TY, n_dc = (K + KC - 1) / KC;
+    for (int b0 = 0; b0 < n_list; b0 += batch) {
+        const int nbat = min(batch, n_list - b0);
+        if (tid == 0) {
+            s_pre[0] = 0;
+            for (int e = 0; e < nbat; ++e) {
+                const int i = s_list[b0 + e];
+                int d = 0;
+                while (d < C::DMAX && i >= key_offset(d + 1)) ++d;
+                const int nb = (CTU >> d) / 8;
+                s_pre[e + 1] = s_pre[e] + nb * nb * n_ty * n_dc;
+            }
+        }
+        for (int x = tid; x < nbat * KK; x += kThreads) s_sum[x] = 0;
+        __syncthreads();
+        const int items = s_pre[nbat];
+        for (int it = tid; it < items; it += kThreads) {
+            int lo = 0, hi = nbat - 1;  // entry e with s_pre[e] <= it < s_pre[e+1]
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_pre[mid] <= it) lo = mid; else hi = mid - 1;
+            }
+            const int e = lo, i = s_list[b0 + e];
+            int d = 0;
+            while (d < C::DMAX && i >= key_offset(d + 1)) ++d;
+            const int li = i - key_offset(d), n = 1 << d, S = CTU >> d, nb = S / 8;
+            int rem = it - s_pre[e];
+            const int dc = rem % n_dc;
+            rem /= n_dc;
+            const int ty = rem % n_ty;
+            const int blk = rem / n_ty;
+            const int bx = x0 + (li % n) * S + (blk % nb) * 8;
+            const int by = y0 + (li / n) * S + (blk / nb) * 8;
+            const int dy0 = ty * TY, dx0 = dc * KC;
+            uint32_t acc[TY][KC];
+            block_tile_sads<T, KC, TY>(cb, rb, a.pitch_bytes, g.W, g.H, bx, by, bx + s_cx[i] - r + dx0,
+                                       by + s_cy[i] - r + dy0, acc);
+            uint32_t *dst = s_sum + e * KK + dy0 * K + dx0;
+            const int rows = min(TY, K - dy0), cols = min(KC, K - dx0);
+#pragma unroll
+            for (int ii = 0; ii < TY; ++ii)
+#pragma unroll
+                for (int jj = 0; jj < KC; ++jj)
+                    if (ii < rows && jj < cols) atomicAdd(dst + ii * K + jj, acc[ii][jj]);
+        }
+        __syncthreads();
+        for (int e = warp; e < nbat; e += kThreads / 32) {
+            unsigned long long best = ~0ull;
+            for (int c = lane; c < KK; c += 32) {
+                const int dxi = c % K, dyi = c / K;
+                const uint32_t tb = static_cast<uint32_t>((abs(dxi - r) + abs(dyi - r)) * KK + c);
+                const unsigned long long key = (static_cast<unsigned long long>(s_sum[e * KK + c]) << 32) | tb;
+                best = key < best ? key : best;
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+                best = other < best ? other : best;
+            }
+            if (lane == 0) {
+                const int i = s_list[b0 + e];
+                const int c = static_cast<int>(static_cast<uint32_t>(best & 0xffffffffu) % static_cast<uint32_t>(KK));
+                st.mvx[i] = static_cast<int16_t>(s_cx[i] + c % K - r);
+                st.mvy[i] = static_cast<int16_t>(s_cy[i] + c / K - r);
+                st.sad[i] = static_cast<int32_t>(best >> 32);
+            }
+        }
+        __syncthreads();
+    }
+
+    // 4. SATD, cost, split, leaf maps
+    dev::DecideIO io{a.cur, a.ref, a.pitch_bytes, &a.g, a.qp, a.satd_mode, c_lambda_q16, a.out};
+    dev::ctu_decide<T, CTU>(st, io, x0, y0);
+}
+
+constexpr int kSumBudgetBytes = 64 * 1024;
+
+template <typename T, int CTU, int KC, int TY>
+cudaError_t dependent_t(const DependentArgs &a, cudaStream_t s)
+{
+    const int K = 2 * a.r + 1, KK = K * K;
+    const int batch = std::max(1, std::min(dev::Ctu<CTU>::NKEY, kSumBudgetBytes / (4 * KK)));
+    const int smem = batch * KK * 4;
+    auto kern = k_dependent<T, CTU, KC, TY>;
+    static int configured = 0;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSumBudgetBytes);
+        if (e != cudaSuccess) return e;
+        configured = 1;
+    }
+    kern<<<a.g.ctu_cols * a.g.ctu_rows, kThreads, smem, s>>>(a, batch);
+    return cudaGetLastError();
+}
+
+template <typename T, int CTU>
+cudaError_t dependent_ctu(const DependentArgs &a, cudaStream_t s)
+{
+    if (2 * a.r + 1 <= 9) return dependent_t<T, CTU, 9, 3>(a, s);
+    return dependent_t<T, CTU, 17, 3>(a, s);
+}
+
+}  // namespace
+
+cudaError_t launch_dependent(int bit_depth, const DependentArgs &a, cudaStream_t s)
+{
+    if (bit_depth == 8) {
+        if (a.g.ctu == 64) return dependent_ctu<uint8_t, 64>(a, s);
+        if (a.g.ctu == 32) return dependent_ctu<uint8_t, 32>(a, s);
+        return dependent_ctu<uint8_t, 16>(a, s);
+    }
+    if (a.g.ctu == 64) return dependent_ctu<uint16_t, 64>(a, s);
+    if (a.g.ctu == 32) return dependent_ctu<uint16_t, 32>(a, s);
+    return dependent_ctu<uint16_t, 16>(a, s);
+}
+
+}  // namespace ladder_impl

@@ -28,80 +28,19 @@
 //     64-bit keys, then into the global per-CTU keys with global atomicMin
 //     (slices of the same CTU run in different CTAs).  Integer min is
 //     order-independent, so the result is deterministic.
-#include "ladder_internal.h"
+#include "common.cuh"
 
 #include <algorithm>
 
 namespace ladder_impl {
 namespace {
 
-template <typename T> struct Traits;
-template <> struct Traits<uint8_t> { static constexpr int SPW = 4; };
-template <> struct Traits<uint16_t> { static constexpr int SPW = 2; };
-
-template <int SPW> __device__ __forceinline__ uint32_t sad_acc(uint32_t a, uint32_t b, uint32_t c);
-template <> __device__ __forceinline__ uint32_t sad_acc<4>(uint32_t a, uint32_t b, uint32_t c)
-{
-    uint32_t d;
-    asm("vabsdiff4.u32.u32.u32.add %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-    return d;
-}
-template <> __device__ __forceinline__ uint32_t sad_acc<2>(uint32_t a, uint32_t b, uint32_t c)
-{
-    uint32_t d;
-    asm("vabsdiff2.u32.u32.u32.add %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-    return d;
-}
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: gives up after ~2^22 polls (well over a second with the
-// back-off), so a lost completion cannot hang the GPU.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
-{
-    for (uint32_t it = 0; it < (1u << 22); ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (it > 32) __nanosleep(256);
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
-        : "memory");
-}
+using dev::mbar_arrive_expect_tx;
+using dev::mbar_init;
+using dev::mbar_wait_bounded;
+using dev::sad_acc;
+using dev::tma_load_2d;
+using dev::Traits;
 
 // Origin (in samples, inside the CTU) of unit u.  Units are Z-ordered so
 // that lanes sharing a 16x16 / 32x32 / 64x64 CU differ only in low lane bits.
@@ -197,6 +136,18 @@ __device__ __forceinline__ void level_argmin(unsigned long long &best, const uin
         }
         fold_key32<SPW, NX, KS, LNC>(best, kmin, dxb, dyb, R, K);
     }
+}
+
+// Min of a 64-bit key over the lanes that differ only in the bits of `mask`.
+__device__ __forceinline__ unsigned long long warp_min_over(unsigned long long v, unsigned mask)
+{
+#pragma unroll
+    for (int b = 0; b < 5; ++b)
+        if (mask & (1u << b)) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, 1 << b);
+            v = o < v ? o : v;
+        }
+    return v;
 }
 
 template <typename T, int CTU, int TY, int NX>
@@ -426,18 +377,32 @@ __global__ void __launch_bounds__(kThreads)
         }
     }
 
-    // Merge: per-thread bests -> CTA keys (shared atomics) -> global keys.
+    // Merge: per-thread bests -> min over the lanes of a warp that share the
+    // CU -> CTA keys (shared atomics) -> global keys (atomics across slices).
+    // Lane bits: unit bits below log2(NU) (Z-order: 8-bit 2 per level from
+    // 32x32 up; 10-bit one for the 16x16 half, then 2 per level), group bits above.
+    constexpr int LNU = NU == 32 ? 5 : (NU == 16 ? 4 : (NU == 8 ? 3 : (NU == 4 ? 2 : (NU == 2 ? 1 : 0))));
+    constexpr unsigned GROUP_BITS = 0x1fu & ~((1u << LNU) - 1u);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        const int bx = ux + 8 * (b % NBH), by = uy + 8 * (b / NBH);
-        const int li = (by / 8) * (CTU / 8) + bx / 8;
-        atomicMin(&cta_keys[key_offset(DMAX) + li], best_blk[b]);
+        const unsigned long long v = warp_min_over(best_blk[b], GROUP_BITS);
+        if ((lane & GROUP_BITS) == 0) {
+            const int bx = ux + 8 * (b % NBH), by = uy + 8 * (b / NBH);
+            const int li = (by / 8) * (CTU / 8) + bx / 8;
+            atomicMin(&cta_keys[key_offset(DMAX) + li], v);
+        }
     }
 #pragma unroll
     for (int d = 0; d < DMAX; ++d) {
-        const int S = CTU >> d;
-        const int li = (uy / S) * (CTU / S) + ux / S;
-        atomicMin(&cta_keys[key_offset(d) + li], best_lv[d]);
+        // unit bits inside a depth-d CU: 8-bit 2*(DMAX-1-d), 10-bit 2*(DMAX-1-d)+1
+        const int inner = 2 * (DMAX - 1 - d) + B0;
+        const unsigned m = GROUP_BITS | ((1u << inner) - 1u);
+        const unsigned long long v = warp_min_over(best_lv[d], m);
+        if ((lane & m) == 0) {
+            const int S = CTU >> d;
+            const int li = (uy / S) * (CTU / S) + ux / S;
+            atomicMin(&cta_keys[key_offset(d) + li], v);
+        }
     }
     __syncthreads();
     for (int i = tid; i < NKEY; i += kThreads) {

@@ -73,7 +73,7 @@ SIGNATURES = [
     ("ladder_version", ctypes.c_char_p, []),
 ]
 
-KERNEL_KINDS = ("full_search", "decide", "rules", "refine", "fill_keys")
+KERNEL_KINDS = ("full_search", "decide", "dependent", "fill_keys")
 
 _lib = None
 
