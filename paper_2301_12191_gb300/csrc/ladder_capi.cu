@@ -57,6 +57,7 @@ struct ladder {
     int ntiles = 0;
     std::string err;
     int sm_count = 0;
+    int fs_ctas_per_sm = 1;  // resident full-search CTAs per SM
     // tracing
     int prof_on = 0;
     long launches[kKinds] = {};
@@ -264,13 +265,15 @@ bool encode_ref_map(ladder_t *l, CUtensorMap *map, const void *ref, const RungGe
     return true;
 }
 
-// Candidate slices per CTU so that the grid covers the GPU a few times over.
-int choose_slices(const ladder_t *l, int nctus, int ntiles)
+// Candidate slices per CTU: whole group-iterations per slice (no duplicate
+// tiles), about two waves of CTAs at one resident CTA per SM.
+int choose_tiles_per_slice(const ladder_t *l, int nctus, int ntiles, int groups)
 {
-    const int target = std::max(1, l->sm_count) * 4;
-    int slices = (target + nctus - 1) / nctus;
-    const int max_slices = std::max(1, ntiles / 16);  // keep >= 16 tiles (one per group) per slice
-    return std::max(1, std::min(slices, max_slices));
+    const int target = 2 * std::max(1, l->sm_count) * std::max(1, l->fs_ctas_per_sm);
+    const int slices = std::max(1, (target + nctus - 1) / nctus);
+    int tps = (ntiles + slices - 1) / slices;
+    tps = (tps + groups - 1) / groups * groups;
+    return std::max(groups, tps);
 }
 
 ladder_status run_independent(ladder_t *l, Slot *slot, int rung, const void *cur, const void *ref, long pitch,
@@ -287,7 +290,8 @@ ladder_status run_independent(ladder_t *l, Slot *slot, int rung, const void *cur
         return launch_fill_keys(rb.keys, static_cast<long>(nctus) * keys_per_ctu(g.dmax), s);
     });
     if (e != cudaSuccess) return cuda_fail(l, e, "fill keys");
-    const int slices = choose_slices(l, nctus, l->ntiles);
+    const int tps = choose_tiles_per_slice(l, nctus, l->ntiles, plan.groups);
+    const int slices = (l->ntiles + tps - 1) / tps;
     FullSearchArgs fa{};
     fa.cur = cur;
     fa.pitch_bytes = pitch;
@@ -296,7 +300,7 @@ ladder_status run_independent(ladder_t *l, Slot *slot, int rung, const void *cur
     fa.R = R;
     fa.Rp = (R + 15) / 16 * 16;
     fa.ntiles = l->ntiles;
-    fa.tiles_per_slice = (l->ntiles + slices - 1) / slices;
+    fa.tiles_per_slice = tps;
     fa.tiles = l->d_tiles;
     fa.keys = rb.keys;
     fa.status = l->d_status;
@@ -339,6 +343,7 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&l->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    l->fs_ctas_per_sm = full_search_ctas_per_sm(geometry->bit_depth, geometry->ctu_size, geometry->ref_search_range);
 
     size_t per_slot = 0;
     for (const auto &g : l->rg) per_slot += carve(g, nullptr, nullptr);

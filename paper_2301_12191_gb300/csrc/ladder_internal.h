@@ -67,11 +67,15 @@ struct FullSearchPlan {
     int tile_dy, tile_nx;  // candidates per tile: tile_dy rows x tile_nx same-class columns
     int smem_bytes;
     int box_w, box_h;      // TMA box (samples x rows)
-    int pitch_words;       // row pitch of each shifted window copy in 32-bit words
+    int pitch_words;       // words per window row (staging and copies)
+    int copy_stride;       // words between shifted copies
+    int groups;            // candidate groups per CTA (tiles per CTA iteration)
 };
 
 // Returns the shared-memory plan for bit depth / CTU / R (box, pitch, bytes).
 FullSearchPlan full_search_plan(int bit_depth, int ctu, int R);
+// Resident full-search CTAs per SM for this plan (occupancy calculator).
+int full_search_ctas_per_sm(int bit_depth, int ctu, int R);
 // Builds the candidate tile list for range R (host); returns the count.
 int full_search_tiles(int bit_depth, int R, int *out, int cap);
 cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchArgs &a, const CUtensorMap &ref_map,

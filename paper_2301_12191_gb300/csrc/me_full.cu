@@ -150,14 +150,20 @@ __device__ __forceinline__ unsigned long long warp_min_over(unsigned long long v
     return v;
 }
 
+// Word offset of window row `row`, word `w` in a shifted copy: rows are
+// `pw` words apart plus one pad word every 16 rows, so that the lanes of a
+// warp (units 16 rows apart, 4 words apart) hit distinct banks.
+__device__ __forceinline__ int copy_off(int row, int w, int pw) { return row * pw + (row >> 4) + w; }
+
 template <typename T, int CTU, int TY, int NX>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 1 ? 2 : 1)
     k_full_search(const __grid_constant__ CUtensorMap ref_map, const FullSearchArgs a, const int box_h,
-                  const int pw)
+                  const int pw, const int cstride)
 {
     constexpr int SPW = Traits<T>::SPW;
     constexpr int UW = 4 * SPW;                 // unit width in samples
     constexpr int NU = (CTU / UW) * (CTU / 16); // units per CTU
+    constexpr int G = 32 / NU;                  // candidate groups per warp
     constexpr int NG = kThreads / NU;           // candidate groups per CTA
     constexpr int WPB = 8 / SPW;                // words per 8-sample block row
     constexpr int NBH = 4 / WPB;                // 8x8 blocks across a unit
@@ -169,27 +175,28 @@ __global__ void __launch_bounds__(kThreads)
     constexpr int NKEY = keys_per_ctu(DMAX);
     constexpr int B0 = SPW == 4 ? 0 : 1;        // lane bits already spent inside a 16x16
     static_assert((1 << LNC) == NC, "tile size must be a power of two");
-    static_assert(NU <= 32, "a CTU's units must fit in one warp");
+    static_assert(NU <= 32 && 32 % NU == 0, "a CTU's units must tile a warp");
     // Key widths: SAD < 2^(32-KS) wherever a level holds >= 2 candidates
     // (8-bit 32x32 <= 261120, 10-bit 32x32 <= 1047552, 10-bit 16x16 <= 261888);
     // single-candidate levels fold the sum directly into 64 bits.
 
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    // TMA destination: explicitly 128-byte aligned (the plan reserves the slack)
-    uint32_t *const win = reinterpret_cast<uint32_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    // staging: the TMA box, dense (box_h rows x pw words); then SPW shifted copies
+    uint32_t *const stage =
+        reinterpret_cast<uint32_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint32_t *const copies = stage + box_h * pw;
     __shared__ __align__(8) uint64_t bar;
     __shared__ unsigned long long cta_keys[NKEY];
 
     const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const int u = tid % NU;
-    const int grp = tid / NU;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int u = lane % NU;
+    const int g = lane / NU;
     const int ctu_idx = blockIdx.y;
     const int W8 = (a.W + 7) & ~7;
     const int ctu_cols = (W8 + CTU - 1) / CTU;
     const int x0 = (ctu_idx % ctu_cols) * CTU;
     const int y0 = (ctu_idx / ctu_cols) * CTU;
-    const int copy_words = box_h * pw;
     const int R = a.R, K = 2 * R + 1;
 
     if (tid == 0) {
@@ -199,8 +206,8 @@ __global__ void __launch_bounds__(kThreads)
     for (int i = tid; i < NKEY; i += kThreads) cta_keys[i] = ~0ull;
     __syncthreads();
     if (tid == 0) {
-        mbar_arrive_expect_tx(&bar, static_cast<uint32_t>(copy_words) * 4u);
-        tma_load_2d(win, &ref_map, &bar, x0 - a.Rp, y0 - R);
+        mbar_arrive_expect_tx(&bar, static_cast<uint32_t>(box_h * pw) * 4u);
+        tma_load_2d(stage, &ref_map, &bar, x0 - a.Rp, y0 - R);
     }
 
     // Current unit -> registers while the window is in flight.
@@ -237,6 +244,14 @@ __global__ void __launch_bounds__(kThreads)
         }
     }
 
+    // Tiles of this slice; tiles are ordered by candidate row, so the slice
+    // needs window rows [r_lo, r_hi) only.
+    const int tile_begin = blockIdx.x * a.tiles_per_slice;
+    const int tile_end = min(tile_begin + a.tiles_per_slice, a.ntiles);
+    const int n_iter = (tile_end - tile_begin + NG - 1) / NG;  // uniform across the CTA
+    const int r_lo = (__ldg(a.tiles + tile_begin) >> 16) + R;
+    const int r_hi = min(box_h, (__ldg(a.tiles + tile_end - 1) >> 16) + R + TY - 1 + CTU);
+
     const bool ok = mbar_wait_bounded(&bar, 0);
     if (__syncthreads_or(!ok)) {
         if (tid == 0) atomicExch(a.status, kStatusTimeout);
@@ -249,8 +264,8 @@ __global__ void __launch_bounds__(kThreads)
         const int gx0 = x0 - a.Rp, gy0 = y0 - R;
         const int ww = pw * SPW;
         if (gx0 < 0 || gy0 < 0 || gx0 + ww > a.W || gy0 + box_h > a.H) {
-            T *w0 = reinterpret_cast<T *>(win);
-            for (int i = tid; i < box_h * ww; i += kThreads) {
+            T *w0 = reinterpret_cast<T *>(stage);
+            for (int i = r_lo * ww + tid; i < r_hi * ww; i += kThreads) {
                 const int row = i / ww, col = i - row * ww;
                 const int gx = gx0 + col, gy = gy0 + row;
                 const int cx = min(max(gx, 0), a.W - 1), cy = min(max(gy, 0), a.H - 1);
@@ -259,14 +274,15 @@ __global__ void __launch_bounds__(kThreads)
             __syncthreads();
         }
     }
-    // Byte-shifted copies: copy k word w = samples [SPW*w + k, SPW*w + k + SPW).
-#pragma unroll
-    for (int k = 1; k < SPW; ++k) {
-        for (int i = tid; i < copy_words; i += kThreads) {
-            const int w = i % pw;
-            const uint32_t lo = win[i];
-            const uint32_t hi = (w + 1 < pw) ? win[i + 1] : 0u;
-            win[k * copy_words + i] = __funnelshift_r(lo, hi, k * (32 / SPW));
+    // Shifted copies: copy k word w of a row = samples [SPW*w + k, SPW*w + k + SPW).
+    {
+        const int nw = (r_hi - r_lo) * pw;
+        for (int i = tid; i < SPW * nw; i += kThreads) {
+            const int k = i / nw, rem = i - k * nw;
+            const int row = r_lo + rem / pw, w = rem % pw;
+            const uint32_t lo = stage[row * pw + w];
+            const uint32_t hi = (w + 1 < pw) ? stage[row * pw + w + 1] : 0u;
+            copies[k * cstride + copy_off(row, w, pw)] = __funnelshift_r(lo, hi, k * (32 / SPW));
         }
     }
     __syncthreads();
@@ -279,18 +295,16 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int d = 0; d < DMAX; ++d) best_lv[d] = ~0ull;
 
-    const int tile_begin = blockIdx.x * a.tiles_per_slice;
-    const int tile_end = min(tile_begin + a.tiles_per_slice, a.ntiles);
-    const int n_iter = (tile_end - tile_begin + NG - 1) / NG;  // uniform across the CTA
-
     for (int it = 0; it < n_iter; ++it) {
-        int t = tile_begin + grp + it * NG;
+        // the G groups of a warp take G consecutive tiles (paired word classes)
+        int t = tile_begin + G * (warp + (kThreads / 32) * it) + g;
         if (t >= tile_end) t = tile_begin;  // a duplicate tile cannot change a min
         const int packed = __ldg(a.tiles + t);
         const int dxb = static_cast<int>(static_cast<short>(packed & 0xffff));
         const int dyb = packed >> 16;
         const int k = dxb & (SPW - 1);
-        const uint32_t *cp = win + k * copy_words + (uy + dyb + R) * pw + (ux + dxb + a.Rp - k) / SPW;
+        const uint32_t *cp = copies + k * cstride + (ux + dxb + a.Rp - k) / SPW;
+        const int row0 = uy + dyb + R;
 
         uint32_t acc[NB][NC];
 #pragma unroll
@@ -301,7 +315,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int rr = 0; rr < 16 + TY - 1; ++rr) {
             uint32_t w[NX + 3];
-            const uint32_t *rowp = cp + rr * pw;
+            const uint32_t *rowp = cp + copy_off(row0 + rr, 0, pw);
 #pragma unroll
             for (int c = 0; c < NX + 3; ++c) w[c] = rowp[c];
 #pragma unroll
@@ -415,55 +429,90 @@ constexpr int kTileDY = 4;
 constexpr int kTileNX = 2;
 
 template <typename T, int CTU>
-cudaError_t launch_t(const FullSearchArgs &a, const CUtensorMap &map, int box_h, int pw, int smem, int nslices,
+cudaError_t launch_t(const FullSearchArgs &a, const CUtensorMap &map, const FullSearchPlan &p, int nslices,
                      int nctus, cudaStream_t s)
 {
     auto kern = k_full_search<T, CTU, kTileDY, kTileNX>;
     static int configured = -1;
-    if (configured != smem) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (configured < p.smem_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes);
         if (e != cudaSuccess) return e;
-        configured = smem;
+        configured = p.smem_bytes;
     }
     dim3 grid(nslices, nctus);
-    kern<<<grid, kThreads, smem, s>>>(map, a, box_h, pw);
+    kern<<<grid, kThreads, p.smem_bytes, s>>>(map, a, p.box_h, p.pitch_words, p.copy_stride);
     return cudaGetLastError();
 }
 
+template <typename T, int CTU>
+int occupancy_t(int smem)
+{
+    auto kern = k_full_search<T, CTU, kTileDY, kTileNX>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
+    int n = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kThreads, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
 }  // namespace
+
+int full_search_ctas_per_sm(int bit_depth, int ctu, int R)
+{
+    const FullSearchPlan p = full_search_plan(bit_depth, ctu, R);
+    if (bit_depth == 8)
+        return ctu == 64 ? occupancy_t<uint8_t, 64>(p.smem_bytes)
+                         : (ctu == 32 ? occupancy_t<uint8_t, 32>(p.smem_bytes) : occupancy_t<uint8_t, 16>(p.smem_bytes));
+    return ctu == 64 ? occupancy_t<uint16_t, 64>(p.smem_bytes)
+                     : (ctu == 32 ? occupancy_t<uint16_t, 32>(p.smem_bytes) : occupancy_t<uint16_t, 16>(p.smem_bytes));
+}
 
 FullSearchPlan full_search_plan(int bit_depth, int ctu, int R)
 {
     FullSearchPlan p{};
     const int spw = bit_depth == 8 ? 4 : 2;
     const int Rp = (R + 15) / 16 * 16;
-    const int nw = (ctu + 2 * Rp) / spw;  // words per window row
     p.tile_dy = kTileDY;
     p.tile_nx = kTileNX;
-    p.pitch_words = nw + 4;
+    p.pitch_words = (ctu + 2 * Rp) / spw;   // words per window row (a multiple of 4)
     p.box_w = p.pitch_words * spw;
     p.box_h = ctu + 2 * R;
-    p.smem_bytes = spw * p.box_h * p.pitch_words * 4 + 128;  // + alignment slack
+    const int raw = p.box_h * p.pitch_words + (p.box_h >> 4) + 1;
+    p.copy_stride = (raw + 31) / 32 * 32 + 16;  // copies of paired word classes 16 banks apart
+    p.smem_bytes = (p.box_h * p.pitch_words + spw * p.copy_stride) * 4 + 128;  // + alignment slack
+    const int unit_w = 4 * spw;
+    const int nu = (ctu / unit_w) * (ctu / 16);
+    p.groups = kThreads / nu;
     return p;
 }
 
+// Candidate tiles, ordered by candidate row (dy), then by pairs of word
+// classes (0,1), (2,3): the two lane groups of a warp take the two tiles of a
+// pair, which read the same rows and columns of copies k and k+1.
 int full_search_tiles(int bit_depth, int R, int *out, int cap)
 {
     const int spw = bit_depth == 8 ? 4 : 2;
     const int n_ty = (2 * R + 1 + kTileDY - 1) / kTileDY;
+    int first[4], last[4], ntx[4];
+    for (int k = 0; k < spw; ++k) {
+        first[k] = -R + (((k + R) % spw) + spw) % spw;
+        last[k] = R - (((R - k) % spw) + spw) % spw;
+        const int cnt = (last[k] - first[k]) / spw + 1;
+        ntx[k] = (cnt + kTileNX - 1) / kTileNX;
+    }
     int n = 0;
+    auto emit = [&](int dxb, int dyb) {
+        if (n < cap && out) out[n] = (dxb & 0xffff) | (dyb << 16);
+        ++n;
+    };
     for (int ty = 0; ty < n_ty; ++ty) {
         const int dyb = std::min(-R + kTileDY * ty, R - kTileDY + 1);
-        for (int k = 0; k < spw; ++k) {
-            const int first = -R + (((k + R) % spw) + spw) % spw;
-            const int last = R - (((R - k) % spw) + spw) % spw;
-            const int cnt = (last - first) / spw + 1;
-            const int n_tx = (cnt + kTileNX - 1) / kTileNX;
-            for (int tx = 0; tx < n_tx; ++tx) {
-                const int dxb = std::min(first + spw * kTileNX * tx, last - spw * (kTileNX - 1));
-                if (n < cap && out) out[n] = (dxb & 0xffff) | (dyb << 16);
-                ++n;
-            }
+        for (int k0 = 0; k0 < spw; k0 += 2) {
+            const int m = std::max(ntx[k0], ntx[k0 + 1]);
+            for (int tx = 0; tx < m; ++tx)
+                for (int k = k0; k < k0 + 2; ++k) {
+                    const int t = std::min(tx, ntx[k] - 1);
+                    emit(std::min(first[k] + spw * kTileNX * t, last[k] - spw * (kTileNX - 1)), dyb);
+                }
         }
     }
     return n;
@@ -474,13 +523,13 @@ cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchArgs &a, 
 {
     const FullSearchPlan p = full_search_plan(bit_depth, ctu, a.R);
     if (bit_depth == 8) {
-        if (ctu == 64) return launch_t<uint8_t, 64>(a, ref_map, p.box_h, p.pitch_words, p.smem_bytes, nslices, nctus, s);
-        if (ctu == 32) return launch_t<uint8_t, 32>(a, ref_map, p.box_h, p.pitch_words, p.smem_bytes, nslices, nctus, s);
-        return launch_t<uint8_t, 16>(a, ref_map, p.box_h, p.pitch_words, p.smem_bytes, nslices, nctus, s);
+        if (ctu == 64) return launch_t<uint8_t, 64>(a, ref_map, p, nslices, nctus, s);
+        if (ctu == 32) return launch_t<uint8_t, 32>(a, ref_map, p, nslices, nctus, s);
+        return launch_t<uint8_t, 16>(a, ref_map, p, nslices, nctus, s);
     }
-    if (ctu == 64) return launch_t<uint16_t, 64>(a, ref_map, p.box_h, p.pitch_words, p.smem_bytes, nslices, nctus, s);
-    if (ctu == 32) return launch_t<uint16_t, 32>(a, ref_map, p.box_h, p.pitch_words, p.smem_bytes, nslices, nctus, s);
-    return launch_t<uint16_t, 16>(a, ref_map, p.box_h, p.pitch_words, p.smem_bytes, nslices, nctus, s);
+    if (ctu == 64) return launch_t<uint16_t, 64>(a, ref_map, p, nslices, nctus, s);
+    if (ctu == 32) return launch_t<uint16_t, 32>(a, ref_map, p, nslices, nctus, s);
+    return launch_t<uint16_t, 16>(a, ref_map, p, nslices, nctus, s);
 }
 
 }  // namespace ladder_impl
