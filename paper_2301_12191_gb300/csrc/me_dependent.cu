@@ -31,7 +31,7 @@ __constant__ int c_lambda_q16[52] = {
 // reference block starts at (xs + j, ys + i).
 template <typename T, int KC, int TY>
 __device__ __forceinline__ void block_tile_sads(const char *cb, const char *rb, long pitch, int W, int H, int bx,
-                                                int by, int xs, int ys, uint32_t (&acc)[TY][KC])
+                                                int by, int xs, int ys, uint32_t (&acc)[TY * KC])
 {
     constexpr int SPW = Traits<T>::SPW, BITS = 32 / SPW, WPR = 8 / SPW;
     constexpr int NWN = (8 + KC - 1 + SPW - 1) / SPW;  // words of a reference row segment
@@ -68,9 +68,7 @@ __device__ __forceinline__ void block_tile_sads(const char *cb, const char *rb, 
         }
     }
 #pragma unroll
-    for (int i = 0; i < TY; ++i)
-#pragma unroll
-        for (int j = 0; j < KC; ++j) acc[i][j] = 0;
+    for (int c = 0; c < TY * KC; ++c) acc[c] = 0;
 
     const bool xfast = xs >= 0 && (xs / SPW + NWN + 1) * SPW <= W;
     const int sh = (xs & (SPW - 1)) * BITS;
@@ -113,24 +111,77 @@ __device__ __forceinline__ void block_tile_sads(const char *cb, const char *rb, 
             for (int jx = 0; jx < KC; ++jx) {
                 const int q = jx / SPW, k = jx % SPW;
 #pragma unroll
-                for (int m = 0; m < WPR; ++m) acc[i][jx] = dev::sad_acc<SPW>(cw[j][m], shw[k][q + m], acc[i][jx]);
+                for (int m = 0; m < WPR; ++m)
+                    acc[i * KC + jx] = dev::sad_acc<SPW>(cw[j][m], shw[k][q + m], acc[i * KC + jx]);
             }
         }
     }
 }
 
+constexpr int kDepThreads = 128;  // 4 warps per CTU
+
+// Reduce-scatter of the candidate tables of the lanes that differ in the
+// low LG lane bits (the 8x8 blocks of one CU).  The table has N entries,
+// padded with zeros to NCP (a multiple of 32); afterwards each lane holds
+// NCP >> LG summed entries in s[0..], candidates off .. off + (NCP >> LG) - 1.
+template <int N, int NCP, int LG>
+__device__ __forceinline__ int scatter_tables(uint32_t (&s)[N], int lane)
+{
+    int off = 0;
+#pragma unroll
+    for (int b = 0; b < LG; ++b) {
+        const int half = NCP >> (b + 1);
+        const bool up = (lane >> b) & 1;
+#pragma unroll
+        for (int m = 0; m < half; ++m) {
+            if (m >= N) break;
+            const uint32_t lo = s[m];
+            const uint32_t hi = (m + half < N && (b > 0 || m + half < N)) ? s[m + half] : 0u;
+            const uint32_t send = up ? lo : hi;
+            const uint32_t keep = up ? hi : lo;
+            s[m] = keep + __shfl_xor_sync(0xffffffffu, send, 1 << b);
+        }
+        off += up ? half : 0;
+    }
+    return off;
+}
+
+// Best 64-bit key (SAD << 32 | tie-break) among the held candidates.
+// Candidate c of a (ty, dc) job is (dyi, dxi) = (ty*TY + c / KC, dc*KC + c % KC).
+template <int TY, int KC, int N, int CNT>
+__device__ __forceinline__ unsigned long long held_best(const uint32_t (&s)[N], int off, int ty, int dc, int K,
+                                                        int r)
+{
+    unsigned long long best = ~0ull;
+#pragma unroll
+    for (int m = 0; m < CNT; ++m) {
+        const int c = off + m;
+        const int dyi = ty * TY + c / KC, dxi = dc * KC + c % KC;
+        if (c < TY * KC && dyi < K && dxi < K) {
+            const uint32_t tb = static_cast<uint32_t>((abs(dxi - r) + abs(dyi - r)) * K * K + dyi * K + dxi);
+            const unsigned long long key = (static_cast<unsigned long long>(s[m]) << 32) | tb;
+            best = key < best ? key : best;
+        }
+    }
+    return best;
+}
+
 template <typename T, int CTU, int KC, int TY>
-__global__ void __launch_bounds__(kThreads) k_dependent(const DependentArgs a, const int batch)
+__global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const DependentArgs a)
 {
     using C = dev::Ctu<CTU>;
+    constexpr int NT = kDepThreads, NWARP = NT / 32;
+    constexpr int NCAND = TY * KC;
+    constexpr int NCP = (NCAND + 31) / 32 * 32;  // padded so that 5 halvings stay whole
     __shared__ dev::CtuState<CTU> st;
     __shared__ int16_t s_cx[C::NKEY], s_cy[C::NKEY];
     __shared__ uint8_t s_leaf[C::NKEY], s_splitok[C::NKEY];
+    __shared__ unsigned long long s_key[C::NKEY];
     __shared__ int s_list[C::NKEY];       // evaluated CUs (key index), grouped by depth
-    __shared__ int s_pre[C::NKEY + 1];    // item prefix of the current batch
     __shared__ int s_cnt[C::DMAX + 1];
     __shared__ int s_base[C::DMAX + 2];
-    extern __shared__ uint32_t s_sum[];   // per listed CU: (2r+1)^2 candidate sums
+    __shared__ int s_wpre[C::DMAX + 2];   // warp-job prefix per depth
+    extern __shared__ uint32_t s_sum[];   // 64x64 CU only: its (2r+1)^2 candidate sums
 
     const RungGeom &g = a.g;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -141,7 +192,7 @@ __global__ void __launch_bounds__(kThreads) k_dependent(const DependentArgs a, c
     const char *rb = static_cast<const char *>(a.ref);
 
     // 1. local rule of every present CU
-    for (int i = tid; i < C::NKEY; i += kThreads) {
+    for (int i = tid; i < C::NKEY; i += NT) {
         int d = 0;
         while (d < C::DMAX && i >= key_offset(d + 1)) ++d;
         const int li = i - key_offset(d), n = 1 << d, S = CTU >> d;
@@ -161,13 +212,15 @@ __global__ void __launch_bounds__(kThreads) k_dependent(const DependentArgs a, c
         s_cy[i] = cy;
         s_leaf[i] = leaf;
         s_splitok[i] = splitok;
+        s_key[i] = ~0ull;
         st.flags[i] = present ? dev::kPresent : 0;
     }
     if (tid <= C::DMAX) s_cnt[tid] = 0;
+    for (int x = tid; x < KK; x += NT) s_sum[x] = 0;
     __syncthreads();
 
     // 2. reachability (every ancestor may split) and the decision flags
-    for (int i = tid; i < C::NKEY; i += kThreads) {
+    for (int i = tid; i < C::NKEY; i += NT) {
         st.satd[i] = 0;
         st.mvx[i] = INT16_MIN;
         st.mvy[i] = INT16_MIN;
@@ -188,123 +241,140 @@ __global__ void __launch_bounds__(kThreads) k_dependent(const DependentArgs a, c
         if (f & kRuleEvaluated) atomicAdd(&s_cnt[d], 1);
     }
     __syncthreads();
+    const int n_ty = (K + TY - 1) / TY, n_dc = (K + KC - 1) / KC;
     if (tid == 0) {
         s_base[0] = 0;
+        s_wpre[0] = 0;
         for (int d = 0; d <= C::DMAX; ++d) {
             s_base[d + 1] = s_base[d] + s_cnt[d];
+            const int nblk = ((CTU >> d) / 8) * ((CTU >> d) / 8);
+            const int groups = nblk >= 32 ? s_cnt[d] * (nblk / 32) : (s_cnt[d] * nblk + 31) / 32;
+            s_wpre[d + 1] = s_wpre[d] + groups * n_ty * n_dc;
             s_cnt[d] = 0;
         }
     }
     __syncthreads();
-    for (int i = tid; i < C::NKEY; i += kThreads) {
+    for (int i = tid; i < C::NKEY; i += NT) {
         if (!(st.flags[i] & kRuleEvaluated)) continue;
         int d = 0;
         while (d < C::DMAX && i >= key_offset(d + 1)) ++d;
         s_list[s_base[d] + atomicAdd(&s_cnt[d], 1)] = i;
     }
     __syncthreads();
-    const int n_list = s_base[C::DMAX + 1];
 
-    // 3. refinement search, in batches of CUs that fit the sum table
-    const int n_ty = (K + TY - 1) / TY, n_dc = (K + KC - 1) / KC;
-    for (int b0 = 0; b0 < n_list; b0 += batch) {
-        const int nbat = min(batch, n_list - b0);
-        if (tid == 0) {
-            s_pre[0] = 0;
-            for (int e = 0; e < nbat; ++e) {
-                const int i = s_list[b0 + e];
-                int d = 0;
-                while (d < C::DMAX && i >= key_offset(d + 1)) ++d;
-                const int nb = (CTU >> d) / 8;
-                s_pre[e + 1] = s_pre[e] + nb * nb * n_ty * n_dc;
+    // 3. refinement search: warp jobs of 32 lanes = 8x8 blocks of CUs of one
+    //    depth (the blocks of a CU on consecutive lanes), one (ty, dc) tile.
+    const int n_wjobs = s_wpre[C::DMAX + 1];
+    for (int wj = warp; wj < n_wjobs; wj += NWARP) {
+        int d = 0;
+        while (d < C::DMAX && wj >= s_wpre[d + 1]) ++d;
+        const int S = CTU >> d, nb = S / 8, nblk = nb * nb;
+        int loc = wj - s_wpre[d];
+        const int dc = loc % n_dc;
+        loc /= n_dc;
+        const int ty = loc % n_ty;
+        const int grp = loc / n_ty;
+        int e, blk;
+        if (nblk >= 32) {
+            e = grp / (nblk / 32);
+            blk = (grp % (nblk / 32)) * 32 + lane;
+        } else {
+            e = (grp * 32 + lane) / nblk;
+            blk = lane % nblk;
+        }
+        const bool valid = e < s_cnt[d];
+        const int i = s_list[s_base[d] + (valid ? e : 0)];
+        const int li = i - key_offset(d), n = 1 << d;
+        const int bx = x0 + (li % n) * S + (blk % nb) * 8;
+        const int by = y0 + (li / n) * S + (blk / nb) * 8;
+        uint32_t t[NCAND];
+        block_tile_sads<T, KC, TY>(cb, rb, a.pitch_bytes, g.W, g.H, bx, by, bx + s_cx[i] - r + dc * KC,
+                                   by + s_cy[i] - r + ty * TY, t);
+        if (nblk == 1) {
+            const unsigned long long best = held_best<TY, KC, NCAND, NCAND>(t, 0, ty, dc, K, r);
+            if (valid) atomicMin(&s_key[i], best);
+        } else if (nblk == 4) {
+            const int off = scatter_tables<NCAND, NCP, 2>(t, lane);
+            unsigned long long best = held_best<TY, KC, NCAND, NCP / 4>(t, off, ty, dc, K, r);
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, 1 << b);
+                best = o < best ? o : best;
+            }
+            if (valid && (lane & 3) == 0) atomicMin(&s_key[i], best);
+        } else if (nblk == 16) {
+            const int off = scatter_tables<NCAND, NCP, 4>(t, lane);
+            unsigned long long best = held_best<TY, KC, NCAND, NCP / 16>(t, off, ty, dc, K, r);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, 1 << b);
+                best = o < best ? o : best;
+            }
+            if (valid && (lane & 15) == 0) atomicMin(&s_key[i], best);
+        } else {
+            // 64x64: the 64 blocks span two warp jobs; add both halves' sums
+            const int off = scatter_tables<NCAND, NCP, 5>(t, lane);
+#pragma unroll
+            for (int m = 0; m < NCP / 32; ++m) {
+                const int c = off + m;
+                const int dyi = ty * TY + c / KC, dxi = dc * KC + c % KC;
+                if (valid && c < NCAND && dyi < K && dxi < K) atomicAdd(&s_sum[dyi * K + dxi], t[m]);
             }
         }
-        for (int x = tid; x < nbat * KK; x += kThreads) s_sum[x] = 0;
-        __syncthreads();
-        const int items = s_pre[nbat];
-        for (int it = tid; it < items; it += kThreads) {
-            int lo = 0, hi = nbat - 1;  // entry e with s_pre[e] <= it < s_pre[e+1]
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_pre[mid] <= it) lo = mid; else hi = mid - 1;
-            }
-            const int e = lo, i = s_list[b0 + e];
-            int d = 0;
-            while (d < C::DMAX && i >= key_offset(d + 1)) ++d;
-            const int li = i - key_offset(d), n = 1 << d, S = CTU >> d, nb = S / 8;
-            int rem = it - s_pre[e];
-            const int dc = rem % n_dc;
-            rem /= n_dc;
-            const int ty = rem % n_ty;
-            const int blk = rem / n_ty;
-            const int bx = x0 + (li % n) * S + (blk % nb) * 8;
-            const int by = y0 + (li / n) * S + (blk / nb) * 8;
-            const int dy0 = ty * TY, dx0 = dc * KC;
-            uint32_t acc[TY][KC];
-            block_tile_sads<T, KC, TY>(cb, rb, a.pitch_bytes, g.W, g.H, bx, by, bx + s_cx[i] - r + dx0,
-                                       by + s_cy[i] - r + dy0, acc);
-            uint32_t *dst = s_sum + e * KK + dy0 * K + dx0;
-            const int rows = min(TY, K - dy0), cols = min(KC, K - dx0);
-#pragma unroll
-            for (int ii = 0; ii < TY; ++ii)
-#pragma unroll
-                for (int jj = 0; jj < KC; ++jj)
-                    if (ii < rows && jj < cols) atomicAdd(dst + ii * K + jj, acc[ii][jj]);
-        }
-        __syncthreads();
-        for (int e = warp; e < nbat; e += kThreads / 32) {
-            unsigned long long best = ~0ull;
-            for (int c = lane; c < KK; c += 32) {
-                const int dxi = c % K, dyi = c / K;
-                const uint32_t tb = static_cast<uint32_t>((abs(dxi - r) + abs(dyi - r)) * KK + c);
-                const unsigned long long key = (static_cast<unsigned long long>(s_sum[e * KK + c]) << 32) | tb;
-                best = key < best ? key : best;
-            }
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) {
-                const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
-                best = other < best ? other : best;
-            }
-            if (lane == 0) {
-                const int i = s_list[b0 + e];
-                const int c = static_cast<int>(static_cast<uint32_t>(best & 0xffffffffu) % static_cast<uint32_t>(KK));
-                st.mvx[i] = static_cast<int16_t>(s_cx[i] + c % K - r);
-                st.mvy[i] = static_cast<int16_t>(s_cy[i] + c / K - r);
-                st.sad[i] = static_cast<int32_t>(best >> 32);
-            }
-        }
-        __syncthreads();
     }
+    __syncthreads();
+    if (CTU == 64 && warp == 0 && (st.flags[0] & kRuleEvaluated)) {
+        unsigned long long best = ~0ull;
+        for (int c = lane; c < KK; c += 32) {
+            const int dxi = c % K, dyi = c / K;
+            const uint32_t tb = static_cast<uint32_t>((abs(dxi - r) + abs(dyi - r)) * KK + c);
+            const unsigned long long key = (static_cast<unsigned long long>(s_sum[c]) << 32) | tb;
+            best = key < best ? key : best;
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+            best = v < best ? v : best;
+        }
+        if (lane == 0) s_key[0] = best;
+    }
+    __syncthreads();
+    for (int i = tid; i < C::NKEY; i += NT) {
+        if (!(st.flags[i] & kRuleEvaluated)) continue;
+        const unsigned long long best = s_key[i];
+        const int c = static_cast<int>(static_cast<uint32_t>(best & 0xffffffffu) % static_cast<uint32_t>(KK));
+        st.mvx[i] = static_cast<int16_t>(s_cx[i] + c % K - r);
+        st.mvy[i] = static_cast<int16_t>(s_cy[i] + c / K - r);
+        st.sad[i] = static_cast<int32_t>(best >> 32);
+    }
+    __syncthreads();
 
     // 4. SATD, cost, split, leaf maps
     dev::DecideIO io{a.cur, a.ref, a.pitch_bytes, &a.g, a.qp, a.satd_mode, c_lambda_q16, a.out};
     dev::ctu_decide<T, CTU>(st, io, x0, y0);
 }
 
-constexpr int kSumBudgetBytes = 64 * 1024;
-
 template <typename T, int CTU, int KC, int TY>
 cudaError_t dependent_t(const DependentArgs &a, cudaStream_t s)
 {
-    const int K = 2 * a.r + 1, KK = K * K;
-    const int batch = std::max(1, std::min(dev::Ctu<CTU>::NKEY, kSumBudgetBytes / (4 * KK)));
-    const int smem = batch * KK * 4;
+    const int K = 2 * a.r + 1;
+    const int smem = K * K * 4;
     auto kern = k_dependent<T, CTU, KC, TY>;
     static int configured = 0;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSumBudgetBytes);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 65 * 65 * 4);
         if (e != cudaSuccess) return e;
         configured = 1;
     }
-    kern<<<a.g.ctu_cols * a.g.ctu_rows, kThreads, smem, s>>>(a, batch);
+    kern<<<a.g.ctu_cols * a.g.ctu_rows, kDepThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T, int CTU>
 cudaError_t dependent_ctu(const DependentArgs &a, cudaStream_t s)
 {
-    if (2 * a.r + 1 <= 9) return dependent_t<T, CTU, 9, 3>(a, s);
-    return dependent_t<T, CTU, 17, 3>(a, s);
+    if (2 * a.r + 1 <= 9) return dependent_t<T, CTU, 9, sizeof(T) == 1 ? 5 : 3>(a, s);
+    return dependent_t<T, CTU, 17, sizeof(T) == 1 ? 2 : 1>(a, s);
 }
 
 }  // namespace
