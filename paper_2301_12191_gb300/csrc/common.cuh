@@ -126,15 +126,60 @@ __device__ int satd8_group(const void *cur, const void *ref, long pitch, int W, 
 {
     const char *cb = static_cast<const char *>(cur);
     const char *rb = static_cast<const char *>(ref);
+    constexpr int SPW = Traits<T>::SPW, BITS = 32 / SPW, WPR = 8 / SPW;
     const int y = threadIdx.x & 7;
     const int cy = min(py + y, H - 1);
     const int ry = min(max(py + y + mvy, 0), H - 1);
+    const int rx0 = px + mvx;
     int v[8];
+    uint32_t cw[WPR], rw[WPR];
+    if (px + 8 <= W) {  // current row: one aligned vector load
+        const char *row = cb + static_cast<long>(cy) * pitch + static_cast<long>(px) * sizeof(T);
+        if constexpr (WPR == 2) {
+            const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row));
+            cw[0] = q.x;
+            cw[1] = q.y;
+        } else {
+            const uint4 q = __ldg(reinterpret_cast<const uint4 *>(row));
+            cw[0] = q.x;
+            cw[1] = q.y;
+            cw[2] = q.z;
+            cw[3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < WPR; ++m) {
+            uint32_t w = 0;
+#pragma unroll
+            for (int e = 0; e < SPW; ++e)
+                w |= static_cast<uint32_t>(ld_sample<T>(cb, pitch, min(px + m * SPW + e, W - 1), cy)) << (e * BITS);
+            cw[m] = w;
+        }
+    }
+    if (rx0 >= 0 && (rx0 / SPW + WPR + 1) * SPW <= W) {  // reference row: aligned words + one funnel shift
+        const uint32_t *rp = reinterpret_cast<const uint32_t *>(rb + static_cast<long>(ry) * pitch) + rx0 / SPW;
+        const int sh = (rx0 & (SPW - 1)) * BITS;
+        uint32_t raw[WPR + 1];
+#pragma unroll
+        for (int m = 0; m <= WPR; ++m) raw[m] = __ldg(rp + m);
+#pragma unroll
+        for (int m = 0; m < WPR; ++m) rw[m] = __funnelshift_r(raw[m], raw[m + 1], sh);
+    } else {
+#pragma unroll
+        for (int m = 0; m < WPR; ++m) {
+            uint32_t w = 0;
+#pragma unroll
+            for (int e = 0; e < SPW; ++e)
+                w |= static_cast<uint32_t>(ld_sample<T>(rb, pitch, min(max(rx0 + m * SPW + e, 0), W - 1), ry))
+                     << (e * BITS);
+            rw[m] = w;
+        }
+    }
 #pragma unroll
     for (int x = 0; x < 8; ++x) {
-        const int cx = min(px + x, W - 1);
-        const int rx = min(max(px + x + mvx, 0), W - 1);
-        v[x] = ld_sample<T>(cb, pitch, cx, cy) - ld_sample<T>(rb, pitch, rx, ry);
+        const int m = x / SPW, sh = (x % SPW) * BITS;
+        const int mask = (1 << BITS) - 1;
+        v[x] = static_cast<int>((cw[m] >> sh) & mask) - static_cast<int>((rw[m] >> sh) & mask);
     }
     if (mode == 0) {
         fwht<8>(v);  // along the row
@@ -303,20 +348,23 @@ struct Rule {
 
 __device__ __forceinline__ int scale_component(int v, int to, int from)
 {
-    const long long av = v < 0 ? -static_cast<long long>(v) : v;
-    const long long s = (2 * av * to + from) / (2LL * from);
-    const int r = static_cast<int>(v < 0 ? -s : s);
+    // |v| <= 32768 and sizes <= 8192: 2|v|*to + from < 2^31
+    const unsigned av = static_cast<unsigned>(v < 0 ? -v : v);
+    const int s = static_cast<int>((2u * av * static_cast<unsigned>(to) + static_cast<unsigned>(from)) /
+                                   (2u * static_cast<unsigned>(from)));
+    const int r = v < 0 ? -s : s;
     return min(max(r, -256), 256);
 }
 
 __device__ __forceinline__ Rule derive_rule(const RungGeom &g, const DepRefs &rf, int d, int x0, int y0)
 {
+    // sizes are <= 8192, so the products below stay inside 32 bits
     const int S = g.ctu >> d;
-    long long xm = (static_cast<long long>(2 * x0 + S) * rf.Wr) / (2LL * g.W);
-    long long ym = (static_cast<long long>(2 * y0 + S) * rf.Hr) / (2LL * g.H);
-    xm = xm > rf.Wr - 1 ? rf.Wr - 1 : xm;
-    ym = ym > rf.Hr - 1 ? rf.Hr - 1 : ym;
-    const long li = (ym >> 3) * rf.cols8_r + (xm >> 3);
+    const int xm = min(static_cast<int>(static_cast<unsigned>((2 * x0 + S) * rf.Wr) / static_cast<unsigned>(2 * g.W)),
+                       rf.Wr - 1);
+    const int ym = min(static_cast<int>(static_cast<unsigned>((2 * y0 + S) * rf.Hr) / static_cast<unsigned>(2 * g.H)),
+                       rf.Hr - 1);
+    const int li = (ym >> 3) * rf.cols8_r + (xm >> 3);
     const int depth_r = rf.leaf_depth[li];
     Rule r;
     if (rf.use_ref_mv) {
@@ -325,10 +373,10 @@ __device__ __forceinline__ Rule derive_rule(const RungGeom &g, const DepRefs &rf
     } else {
         r.cx = r.cy = 0;
     }
-    const long long proj = static_cast<long long>(g.ctu >> depth_r) * g.W;
+    const int proj = (g.ctu >> depth_r) * g.W;
     int deq = 0;
     for (int dd = 0; dd <= g.dmax; ++dd)
-        if (static_cast<long long>(g.ctu >> dd) * rf.Wr >= proj) deq = dd;
+        if ((g.ctu >> dd) * rf.Wr >= proj) deq = dd;
     r.allowed_split = d < g.dmax && d < deq + rf.depth_hi;
     r.allowed_leaf = (deq + rf.depth_lo <= d && d <= deq + rf.depth_hi) || d == g.dmax || !r.allowed_split;
     return r;

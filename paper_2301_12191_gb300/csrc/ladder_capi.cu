@@ -20,6 +20,8 @@ namespace {
 
 struct RungBuffers {
     DevDecisions dec;
+    char *dec_base;     // the decision arrays form one contiguous block
+    size_t dec_bytes;
     unsigned long long *keys;
     int analysed;  // 0: nothing, 1: independent, 2: dependent
 };
@@ -55,9 +57,13 @@ struct ladder {
     int *d_status = nullptr;
     int *d_tiles = nullptr;
     int ntiles = 0;
+    uint16_t *d_rank = nullptr, *d_unrank = nullptr;  // refinement candidate order
+    int rank_bits = 0;
     std::string err;
     int sm_count = 0;
     int fs_ctas_per_sm = 1;  // resident full-search CTAs per SM
+    char *host_stage = nullptr;  // pinned staging for fetch_decisions
+    size_t host_stage_bytes = 0;
     // tracing
     int prof_on = 0;
     long launches[kKinds] = {};
@@ -172,6 +178,10 @@ size_t carve(const RungGeom &g, char *base, RungBuffers *rb)
     p = take(n8); if (rb) rb->dec.leaf_depth = reinterpret_cast<uint8_t *>(p);
     p = take(n8 * 2); if (rb) rb->dec.leaf_mvx = reinterpret_cast<int16_t *>(p);
     p = take(n8 * 2); if (rb) rb->dec.leaf_mvy = reinterpret_cast<int16_t *>(p);
+    if (rb) {
+        rb->dec_base = base;
+        rb->dec_bytes = off;
+    }
     const size_t nk = static_cast<size_t>(g.ctu_cols) * g.ctu_rows * keys_per_ctu(g.dmax);
     p = take(nk * 8); if (rb) rb->keys = reinterpret_cast<unsigned long long *>(p);
     return off;
@@ -349,7 +359,9 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
     for (const auto &g : l->rg) per_slot += carve(g, nullptr, nullptr);
     const int ntiles = full_search_tiles(geometry->bit_depth, geometry->ref_search_range, nullptr, 0);
     l->ntiles = ntiles;
-    const size_t fixed = align_up(256, 256) + align_up(static_cast<size_t>(ntiles) * 4, 256);
+    const int Kr = 2 * geometry->dep_refine_range + 1;
+    const size_t rank_bytes = align_up(static_cast<size_t>(Kr) * Kr * 2, 256);
+    const size_t fixed = align_up(256, 256) + align_up(static_cast<size_t>(ntiles) * 4, 256) + 2 * rank_bytes;
     l->arena_bytes = fixed + per_slot * geometry->max_frames;
     cudaError_t e = cudaMalloc(&l->arena, l->arena_bytes);
     if (e != cudaSuccess) {
@@ -360,6 +372,9 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
     char *base = static_cast<char *>(l->arena);
     l->d_status = reinterpret_cast<int *>(base);
     l->d_tiles = reinterpret_cast<int *>(base + 256);
+    l->d_rank = reinterpret_cast<uint16_t *>(base + 256 + align_up(static_cast<size_t>(ntiles) * 4, 256));
+    l->d_unrank = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(l->d_rank) + rank_bytes);
+    while ((1 << l->rank_bits) < Kr * Kr) ++l->rank_bits;
     char *p = base + fixed;
     l->slots.resize(geometry->max_frames);
     for (auto &s : l->slots) {
@@ -372,14 +387,27 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
             s.rungs[r].analysed = 0;
         }
     }
+    for (const auto &r : l->slots[0].rungs) l->host_stage_bytes = std::max(l->host_stage_bytes, r.dec_bytes);
+    if (cudaMallocHost(&l->host_stage, l->host_stage_bytes) != cudaSuccess) {
+        cudaFree(l->arena);
+        delete l;
+        cudaGetLastError();
+        return LADDER_E_NOMEM;
+    }
     std::vector<int> tiles(ntiles);
     full_search_tiles(geometry->bit_depth, geometry->ref_search_range, tiles.data(), ntiles);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     e = cudaMemsetAsync(l->d_status, 0, sizeof(int), s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(l->d_tiles, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice, s);
+    std::vector<uint16_t> rank(static_cast<size_t>(Kr) * Kr), unrank(rank.size());
+    refine_rank_tables(geometry->dep_refine_range, rank.data(), unrank.data());
+    if (e == cudaSuccess) e = cudaMemcpyAsync(l->d_rank, rank.data(), rank.size() * 2, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(l->d_unrank, unrank.data(), unrank.size() * 2, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
+        cudaFreeHost(l->host_stage);
         cudaFree(l->arena);
         delete l;
         return LADDER_E_CUDA;
@@ -430,6 +458,9 @@ ladder_status analyze_dependent(ladder_t *l, int rung, int frame_id, const void 
     da.pitch_bytes = pitch_bytes;
     da.g = g;
     da.r = l->geo.dep_refine_range;
+    da.rank = l->d_rank;
+    da.unrank = l->d_unrank;
+    da.rank_bits = l->rank_bits;
     da.refs.Wr = gr.W;
     da.refs.Hr = gr.H;
     da.refs.cols8_r = gr.cols8;
@@ -487,11 +518,16 @@ ladder_status fetch_decisions(ladder_t *l, int rung, int frame_id, ladder_decisi
     if (!slot || !slot->rungs[rung].analysed)
         return fail(l, LADDER_E_STATE, "rung %d of frame %d has not been analysed", rung, frame_id);
     const RungGeom &g = l->rg[rung];
-    const DevDecisions &dec = slot->rungs[rung].dec;
+    const RungBuffers &rb = slot->rungs[rung];
+    const DevDecisions &dec = rb.dec;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    cudaError_t e = cudaSuccess;
+    // one copy of the rung's whole decision block into pinned memory, then
+    // host copies into the caller's arrays
+    cudaError_t e = cudaMemcpyAsync(l->host_stage, rb.dec_base, rb.dec_bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(l, e, "fetch copy");
     auto copy = [&](void *dst, const void *src, size_t bytes) {
-        if (dst && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+        if (dst) memcpy(dst, l->host_stage + (static_cast<const char *>(src) - rb.dec_base), bytes);
     };
     for (int d = 0; d <= g.dmax; ++d) {
         const size_t n = static_cast<size_t>(g.cols[d]) * g.rows[d];
@@ -508,7 +544,6 @@ ladder_status fetch_decisions(ladder_t *l, int rung, int frame_id, ladder_decisi
     copy(out->leaf_depth, dec.leaf_depth, n8);
     copy(out->leaf_mvx, dec.leaf_mvx, n8 * 2);
     copy(out->leaf_mvy, dec.leaf_mvy, n8 * 2);
-    if (e != cudaSuccess) return cuda_fail(l, e, "fetch copy");
     return ladder_sync(l, cuda_stream);
 }
 
@@ -549,6 +584,7 @@ void ladder_destroy(ladder_t *l)
     cudaDeviceSynchronize();
     drain_events(l);
     for (cudaEvent_t e : l->spare) cudaEventDestroy(e);
+    cudaFreeHost(l->host_stage);
     cudaFree(l->arena);
     delete l;
 }

@@ -95,6 +95,9 @@ struct DependentArgs {
     long pitch_bytes;
     RungGeom g;
     int r;                  // refinement range
+    const uint16_t *rank;   // (2r+1)^2: rank of candidate (dyi*K + dxi) in (|dx|+|dy|, dy, dx) order
+    const uint16_t *unrank; // inverse of rank
+    int rank_bits;          // ceil(log2((2r+1)^2))
     DepRefs refs;
     int qp, satd_mode;
     DevDecisions out;
@@ -102,6 +105,8 @@ struct DependentArgs {
 };
 // Constraint derivation, refinement search, SATD, cost and split: one CTA per CTU.
 cudaError_t launch_dependent(int bit_depth, const DependentArgs &a, cudaStream_t s);
+// Rank / inverse tables of the refinement candidates for range r (host).
+void refine_rank_tables(int r, uint16_t *rank, uint16_t *unrank);
 
 // ---- SATD, cost, split and leaf maps -------------------------------------
 struct DecideArgs {

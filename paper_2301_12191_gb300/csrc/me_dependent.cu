@@ -17,6 +17,8 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <cstdlib>
+#include <vector>
 
 namespace ladder_impl {
 namespace {
@@ -146,24 +148,49 @@ __device__ __forceinline__ int scatter_tables(uint32_t (&s)[N], int lane)
     return off;
 }
 
-// Best 64-bit key (SAD << 32 | tie-break) among the held candidates.
-// Candidate c of a (ty, dc) job is (dyi, dxi) = (ty*TY + c / KC, dc*KC + c % KC).
-template <int TY, int KC, int N, int CNT>
+// Best key among the held candidates, as SAD << 32 | rank (rank = position
+// of the candidate in the (|dx|+|dy|, dy, dx) order).  Candidate c of a
+// (ty, dc) job is (dyi, dxi) = (ty*TY + c / KC, dc*KC + c % KC).  The min is
+// taken on 32-bit keys SAD << RB | rank when SB + RB <= 32 (SB = bits of the
+// CU's largest SAD), else on 64-bit keys.
+template <int TY, int KC, int N, int CNT, int SB>
 __device__ __forceinline__ unsigned long long held_best(const uint32_t (&s)[N], int off, int ty, int dc, int K,
-                                                        int r)
+                                                        const uint16_t *rank, int rb)
 {
+    const int base = ty * TY * K + dc * KC;
+    if (SB + rb <= 32) {
+        uint32_t best = 0xffffffffu;
+        const uint32_t mul = 1u << rb;
+#pragma unroll
+        for (int m = 0; m < CNT; ++m) {
+            const int c = off + m;
+            const int dyi = ty * TY + c / KC, dxi = dc * KC + c % KC;
+            if (c < TY * KC && dyi < K && dxi < K) {
+                const uint32_t key = s[m] * mul + rank[base + (c / KC) * K + c % KC];
+                best = key < best ? key : best;
+            }
+        }
+        if (best == 0xffffffffu) return ~0ull;
+        return (static_cast<unsigned long long>(best >> rb) << 32) | (best & (mul - 1u));
+    }
     unsigned long long best = ~0ull;
 #pragma unroll
     for (int m = 0; m < CNT; ++m) {
         const int c = off + m;
         const int dyi = ty * TY + c / KC, dxi = dc * KC + c % KC;
         if (c < TY * KC && dyi < K && dxi < K) {
-            const uint32_t tb = static_cast<uint32_t>((abs(dxi - r) + abs(dyi - r)) * K * K + dyi * K + dxi);
-            const unsigned long long key = (static_cast<unsigned long long>(s[m]) << 32) | tb;
+            const unsigned long long key =
+                (static_cast<unsigned long long>(s[m]) << 32) | rank[base + (c / KC) * K + c % KC];
             best = key < best ? key : best;
         }
     }
     return best;
+}
+
+// Bits of the largest SAD of an S x S CU of B-bit samples.
+template <typename T> __host__ __device__ constexpr int sad_bits(int S)
+{
+    return (S == 8 ? 6 : S == 16 ? 8 : S == 32 ? 10 : 12) + (sizeof(T) == 1 ? 8 : 10);
 }
 
 template <typename T, int CTU, int KC, int TY>
@@ -181,7 +208,10 @@ __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const DependentArg
     __shared__ int s_cnt[C::DMAX + 1];
     __shared__ int s_base[C::DMAX + 2];
     __shared__ int s_wpre[C::DMAX + 2];   // warp-job prefix per depth
-    extern __shared__ uint32_t s_sum[];   // 64x64 CU only: its (2r+1)^2 candidate sums
+    extern __shared__ uint32_t s_dyn[];   // 64x64 CU sums, then rank / unrank tables
+    uint32_t *const s_sum = s_dyn;
+    uint16_t *const s_rank = reinterpret_cast<uint16_t *>(s_dyn + (2 * a.r + 1) * (2 * a.r + 1));
+    uint16_t *const s_unrank = s_rank + (2 * a.r + 1) * (2 * a.r + 1);
 
     const RungGeom &g = a.g;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -216,7 +246,11 @@ __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const DependentArg
         st.flags[i] = present ? dev::kPresent : 0;
     }
     if (tid <= C::DMAX) s_cnt[tid] = 0;
-    for (int x = tid; x < KK; x += NT) s_sum[x] = 0;
+    for (int x = tid; x < KK; x += NT) {
+        s_sum[x] = 0;
+        s_rank[x] = a.rank[x];
+        s_unrank[x] = a.unrank[x];
+    }
     __syncthreads();
 
     // 2. reachability (every ancestor may split) and the decision flags
@@ -291,11 +325,13 @@ __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const DependentArg
         block_tile_sads<T, KC, TY>(cb, rb, a.pitch_bytes, g.W, g.H, bx, by, bx + s_cx[i] - r + dc * KC,
                                    by + s_cy[i] - r + ty * TY, t);
         if (nblk == 1) {
-            const unsigned long long best = held_best<TY, KC, NCAND, NCAND>(t, 0, ty, dc, K, r);
+            const unsigned long long best =
+                held_best<TY, KC, NCAND, NCAND, sad_bits<T>(8)>(t, 0, ty, dc, K, s_rank, a.rank_bits);
             if (valid) atomicMin(&s_key[i], best);
         } else if (nblk == 4) {
             const int off = scatter_tables<NCAND, NCP, 2>(t, lane);
-            unsigned long long best = held_best<TY, KC, NCAND, NCP / 4>(t, off, ty, dc, K, r);
+            unsigned long long best =
+                held_best<TY, KC, NCAND, NCP / 4, sad_bits<T>(16)>(t, off, ty, dc, K, s_rank, a.rank_bits);
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
                 const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, 1 << b);
@@ -304,7 +340,8 @@ __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const DependentArg
             if (valid && (lane & 3) == 0) atomicMin(&s_key[i], best);
         } else if (nblk == 16) {
             const int off = scatter_tables<NCAND, NCP, 4>(t, lane);
-            unsigned long long best = held_best<TY, KC, NCAND, NCP / 16>(t, off, ty, dc, K, r);
+            unsigned long long best =
+                held_best<TY, KC, NCAND, NCP / 16, sad_bits<T>(32)>(t, off, ty, dc, K, s_rank, a.rank_bits);
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, 1 << b);
@@ -326,9 +363,7 @@ __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const DependentArg
     if (CTU == 64 && warp == 0 && (st.flags[0] & kRuleEvaluated)) {
         unsigned long long best = ~0ull;
         for (int c = lane; c < KK; c += 32) {
-            const int dxi = c % K, dyi = c / K;
-            const uint32_t tb = static_cast<uint32_t>((abs(dxi - r) + abs(dyi - r)) * KK + c);
-            const unsigned long long key = (static_cast<unsigned long long>(s_sum[c]) << 32) | tb;
+            const unsigned long long key = (static_cast<unsigned long long>(s_sum[c]) << 32) | s_rank[c];
             best = key < best ? key : best;
         }
 #pragma unroll
@@ -342,7 +377,7 @@ __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const DependentArg
     for (int i = tid; i < C::NKEY; i += NT) {
         if (!(st.flags[i] & kRuleEvaluated)) continue;
         const unsigned long long best = s_key[i];
-        const int c = static_cast<int>(static_cast<uint32_t>(best & 0xffffffffu) % static_cast<uint32_t>(KK));
+        const int c = s_unrank[static_cast<uint32_t>(best & 0xffffffffu)];
         st.mvx[i] = static_cast<int16_t>(s_cx[i] + c % K - r);
         st.mvy[i] = static_cast<int16_t>(s_cy[i] + c / K - r);
         st.sad[i] = static_cast<int32_t>(best >> 32);
@@ -358,11 +393,11 @@ template <typename T, int CTU, int KC, int TY>
 cudaError_t dependent_t(const DependentArgs &a, cudaStream_t s)
 {
     const int K = 2 * a.r + 1;
-    const int smem = K * K * 4;
+    const int smem = K * K * 8;
     auto kern = k_dependent<T, CTU, KC, TY>;
     static int configured = 0;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 65 * 65 * 4);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 65 * 65 * 8);
         if (e != cudaSuccess) return e;
         configured = 1;
     }
@@ -378,6 +413,25 @@ cudaError_t dependent_ctu(const DependentArgs &a, cudaStream_t s)
 }
 
 }  // namespace
+
+void refine_rank_tables(int r, uint16_t *rank, uint16_t *unrank)
+{
+    const int K = 2 * r + 1, KK = K * K;
+    std::vector<int> order(KK);
+    for (int c = 0; c < KK; ++c) order[c] = c;
+    // (|dx|+|dy|, dy, dx) with dx = c % K - r, dy = c / K - r
+    std::sort(order.begin(), order.end(), [&](int p, int q) {
+        const int px = p % K - r, py = p / K - r, qx = q % K - r, qy = q / K - r;
+        const int lp = std::abs(px) + std::abs(py), lq = std::abs(qx) + std::abs(qy);
+        if (lp != lq) return lp < lq;
+        if (py != qy) return py < qy;
+        return px < qx;
+    });
+    for (int k = 0; k < KK; ++k) {
+        rank[order[k]] = static_cast<uint16_t>(k);
+        unrank[k] = static_cast<uint16_t>(order[k]);
+    }
+}
 
 cudaError_t launch_dependent(int bit_depth, const DependentArgs &a, cudaStream_t s)
 {
