@@ -121,6 +121,14 @@ LADDER_API ladder_status analyze_reference(ladder_t *ladder, int frame_id, const
 LADDER_API ladder_status analyze_dependent(ladder_t *ladder, int rung, int frame_id, const void *cur,
                                 const void *ref, long pitch_bytes, int qp, void *cuda_stream);
 
+/* Several dependent rungs of frame `frame_id` in one launch (all CTUs of
+ * all listed rungs run concurrently; results are identical to one
+ * analyze_dependent call per rung).  n in 1..16, rungs distinct and not the
+ * reference rung; cur[k], ref[k], pitch_bytes[k] describe rung rungs[k]. */
+LADDER_API ladder_status analyze_dependents(ladder_t *ladder, int frame_id, int n, const int *rungs,
+                                            const void *const *cur, const void *const *ref,
+                                            const long *pitch_bytes, int qp, void *cuda_stream);
+
 /* Independent full search (+-R) of any rung, the per-rung baseline against
  * which the multi-resolution speedup is measured.  Needs no reference; claims
  * a frame slot like analyze_reference, and does not change the frame's

@@ -231,6 +231,8 @@ struct CtuState {
     int32_t satd[Ctu<CTU>::NKEY], sad[Ctu<CTU>::NKEY], best[Ctu<CTU>::NKEY];
     int16_t mvx[Ctu<CTU>::NKEY], mvy[Ctu<CTU>::NKEY];
     uint8_t flags[Ctu<CTU>::NKEY], split[Ctu<CTU>::NKEY];
+    uint16_t pairs[(Ctu<CTU>::DMAX + 1) * Ctu<CTU>::NB8];  // (depth, 8x8) pairs needing a SATD
+    int npairs;
 };
 
 struct DecideIO {
@@ -259,17 +261,42 @@ __device__ void ctu_decide(CtuState<CTU> &st, const DecideIO &io, int x0, int y0
     const RungGeom &g = *io.g;
     const int tid = threadIdx.x, nthr = blockDim.x;
 
-    // SATD: one 8-lane group per (depth, 8x8 block) pair of an evaluated CU
-    const unsigned gmask = 0xffu << (tid & 24);
-    for (int t = tid >> 3; t < (C::DMAX + 1) * C::NB8; t += nthr >> 3) {
+    // SATD: list the (depth, 8x8 block) pairs of evaluated CUs, then one
+    // 8-lane group per pair, two pairs at a time so their loads overlap
+    if (tid == 0) st.npairs = 0;
+    __syncthreads();
+    for (int t = tid; t < (C::DMAX + 1) * C::NB8; t += nthr) {
         const int d = t / C::NB8, b = t % C::NB8;
-        const int bx = b % C::N8, by = b / C::N8;
         const int S = CTU >> d;
-        const int i = key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S);
-        if (!(st.flags[i] & kRuleEvaluated)) continue;
-        const int v = satd8_group<T>(io.cur, io.ref, io.pitch_bytes, g.W, g.H, x0 + 8 * bx, y0 + 8 * by,
-                                     st.mvx[i], st.mvy[i], io.satd_mode, gmask);
-        if ((tid & 7) == 0) atomicAdd(&st.satd[i], v);
+        const int i = key_index(d, (((b / C::N8) * 8) / S) * (1 << d) + ((b % C::N8) * 8) / S);
+        if (st.flags[i] & kRuleEvaluated) st.pairs[atomicAdd(&st.npairs, 1)] = static_cast<uint16_t>(t);
+    }
+    __syncthreads();
+    const unsigned gmask = 0xffu << (tid & 24);
+    const int ng = nthr >> 3, np = st.npairs;
+    for (int p = tid >> 3; p < np; p += 2 * ng) {
+        const bool two = p + ng < np;
+        int px[2], py[2], mx[2], my[2], ci[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int t = st.pairs[(k == 1 && two) ? p + ng : p];
+            const int d = t / C::NB8, b = t % C::NB8;
+            const int bx = b % C::N8, by = b / C::N8;
+            const int S = CTU >> d;
+            ci[k] = key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S);
+            px[k] = x0 + 8 * bx;
+            py[k] = y0 + 8 * by;
+            mx[k] = st.mvx[ci[k]];
+            my[k] = st.mvy[ci[k]];
+        }
+        const int v0 = satd8_group<T>(io.cur, io.ref, io.pitch_bytes, g.W, g.H, px[0], py[0], mx[0], my[0],
+                                      io.satd_mode, gmask);
+        const int v1 = satd8_group<T>(io.cur, io.ref, io.pitch_bytes, g.W, g.H, px[1], py[1], mx[1], my[1],
+                                      io.satd_mode, gmask);
+        if ((tid & 7) == 0) {
+            atomicAdd(&st.satd[ci[0]], v0);
+            if (two) atomicAdd(&st.satd[ci[1]], v1);
+        }
     }
     __syncthreads();
 

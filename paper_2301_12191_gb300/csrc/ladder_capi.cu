@@ -436,48 +436,66 @@ ladder_status analyze_reference(ladder_t *l, int frame_id, const void *cur, cons
     return analyze_independent(l, l->geo.ref_rung, frame_id, cur, ref, pitch_bytes, qp, cuda_stream);
 }
 
-ladder_status analyze_dependent(ladder_t *l, int rung, int frame_id, const void *cur, const void *ref,
-                                long pitch_bytes, int qp, void *cuda_stream)
+ladder_status analyze_dependents(ladder_t *l, int frame_id, int n, const int *rungs, const void *const *cur,
+                                 const void *const *ref, const long *pitch_bytes, int qp, void *cuda_stream)
 {
     if (!l) return LADDER_E_INVAL;
-    ladder_status st = check_planes(l, rung, cur, ref, pitch_bytes, qp);
-    if (st != LADDER_OK) return st;
-    if (rung == l->geo.ref_rung) return fail(l, LADDER_E_INVAL, "rung %d is the reference rung", rung);
+    if (n < 1 || n > kMaxBatch || !rungs || !cur || !ref || !pitch_bytes)
+        return fail(l, LADDER_E_INVAL, "dependent batch of %d rungs (1..%d)", n, kMaxBatch);
+    for (int k = 0; k < n; ++k) {
+        ladder_status st = check_planes(l, rungs[k], cur[k], ref[k], pitch_bytes[k], qp);
+        if (st != LADDER_OK) return st;
+        if (rungs[k] == l->geo.ref_rung) return fail(l, LADDER_E_INVAL, "rung %d is the reference rung", rungs[k]);
+        for (int j = 0; j < k; ++j)
+            if (rungs[j] == rungs[k]) return fail(l, LADDER_E_INVAL, "rung %d appears twice", rungs[k]);
+    }
     Slot *slot = find_slot(l, frame_id);
     if (!slot || !slot->ref_done)
         return fail(l, LADDER_E_NOREF, "frame %d has no reference analysis", frame_id);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    const RungGeom &g = l->rg[rung];
     const RungGeom &gr = l->rg[l->geo.ref_rung];
-    RungBuffers &rb = slot->rungs[rung];
     const RungBuffers &ref_rb = slot->rungs[l->geo.ref_rung];
-
-    DependentArgs da{};
-    da.cur = cur;
-    da.ref = ref;
-    da.pitch_bytes = pitch_bytes;
-    da.g = g;
-    da.r = l->geo.dep_refine_range;
-    da.rank = l->d_rank;
-    da.unrank = l->d_unrank;
-    da.rank_bits = l->rank_bits;
-    da.refs.Wr = gr.W;
-    da.refs.Hr = gr.H;
-    da.refs.cols8_r = gr.cols8;
-    da.refs.leaf_depth = ref_rb.dec.leaf_depth;
-    da.refs.leaf_mvx = ref_rb.dec.leaf_mvx;
-    da.refs.leaf_mvy = ref_rb.dec.leaf_mvy;
-    da.refs.depth_lo = l->geo.dep_depth_lo;
-    da.refs.depth_hi = l->geo.dep_depth_hi;
-    da.refs.use_ref_mv = l->geo.dep_use_ref_mv;
-    da.qp = qp;
-    da.satd_mode = l->geo.satd_mode;
-    da.out = rb.dec;
-    da.status = l->d_status;
-    cudaError_t e = traced(l, 2, s, [&] { return launch_dependent(l->geo.bit_depth, da, s); });
+    DependentBatch batch{};
+    batch.n = n;
+    batch.cta_begin[0] = 0;
+    for (int k = 0; k < n; ++k) {
+        const RungGeom &g = l->rg[rungs[k]];
+        DependentArgs &da = batch.rung[k];
+        da.cur = cur[k];
+        da.ref = ref[k];
+        da.pitch_bytes = pitch_bytes[k];
+        da.g = g;
+        da.r = l->geo.dep_refine_range;
+        da.rank = l->d_rank;
+        da.unrank = l->d_unrank;
+        da.rank_bits = l->rank_bits;
+        da.refs.Wr = gr.W;
+        da.refs.Hr = gr.H;
+        da.refs.cols8_r = gr.cols8;
+        da.refs.leaf_depth = ref_rb.dec.leaf_depth;
+        da.refs.leaf_mvx = ref_rb.dec.leaf_mvx;
+        da.refs.leaf_mvy = ref_rb.dec.leaf_mvy;
+        da.refs.depth_lo = l->geo.dep_depth_lo;
+        da.refs.depth_hi = l->geo.dep_depth_hi;
+        da.refs.use_ref_mv = l->geo.dep_use_ref_mv;
+        da.qp = qp;
+        da.satd_mode = l->geo.satd_mode;
+        da.out = slot->rungs[rungs[k]].dec;
+        da.status = l->d_status;
+        batch.cta_begin[k + 1] = batch.cta_begin[k] + g.ctu_cols * g.ctu_rows;
+    }
+    cudaError_t e = traced(l, 2, s, [&] {
+        return launch_dependent(l->geo.bit_depth, l->geo.ctu_size, l->geo.dep_refine_range, batch, s);
+    });
     if (e != cudaSuccess) return cuda_fail(l, e, "dependent launch");
-    rb.analysed = 2;
+    for (int k = 0; k < n; ++k) slot->rungs[rungs[k]].analysed = 2;
     return LADDER_OK;
+}
+
+ladder_status analyze_dependent(ladder_t *l, int rung, int frame_id, const void *cur, const void *ref,
+                                long pitch_bytes, int qp, void *cuda_stream)
+{
+    return analyze_dependents(l, frame_id, 1, &rung, &cur, &ref, &pitch_bytes, qp, cuda_stream);
 }
 
 ladder_status ladder_grid(const ladder_t *l, int rung, int *dims, int *n_depths)

@@ -103,8 +103,17 @@ struct DependentArgs {
     DevDecisions out;
     int *status;
 };
+// Several dependent rungs analysed by one launch (kernel parameter: CUDA
+// 12.1+ allows up to 32 KB).  CTA b belongs to rung i with
+// cta_begin[i] <= b < cta_begin[i+1]; all rungs share bit depth, CTU size and r.
+constexpr int kMaxBatch = 16;
+struct DependentBatch {
+    int n;
+    int cta_begin[kMaxBatch + 1];
+    DependentArgs rung[kMaxBatch];
+};
 // Constraint derivation, refinement search, SATD, cost and split: one CTA per CTU.
-cudaError_t launch_dependent(int bit_depth, const DependentArgs &a, cudaStream_t s);
+cudaError_t launch_dependent(int bit_depth, int ctu, int r, const DependentBatch &b, cudaStream_t s);
 // Rank / inverse tables of the refinement candidates for range r (host).
 void refine_rank_tables(int r, uint16_t *rank, uint16_t *unrank);
 

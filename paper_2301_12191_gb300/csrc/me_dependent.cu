@@ -194,8 +194,11 @@ template <typename T> __host__ __device__ constexpr int sad_bits(int S)
 }
 
 template <typename T, int CTU, int KC, int TY>
-__global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const DependentArgs a)
+__global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const __grid_constant__ DependentBatch b)
 {
+    int ri = 0;
+    while (ri + 1 < b.n && static_cast<int>(blockIdx.x) >= b.cta_begin[ri + 1]) ++ri;
+    const DependentArgs &a = b.rung[ri];
     using C = dev::Ctu<CTU>;
     constexpr int NT = kDepThreads, NWARP = NT / 32;
     constexpr int NCAND = TY * KC;
@@ -215,7 +218,7 @@ __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const DependentArg
 
     const RungGeom &g = a.g;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ctu_idx = blockIdx.x;
+    const int ctu_idx = blockIdx.x - b.cta_begin[ri];
     const int x0 = (ctu_idx % g.ctu_cols) * CTU, y0 = (ctu_idx / g.ctu_cols) * CTU;
     const int r = a.r, K = 2 * r + 1, KK = K * K;
     const char *cb = static_cast<const char *>(a.cur);
@@ -390,9 +393,9 @@ __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const DependentArg
 }
 
 template <typename T, int CTU, int KC, int TY>
-cudaError_t dependent_t(const DependentArgs &a, cudaStream_t s)
+cudaError_t dependent_t(int r, const DependentBatch &b, cudaStream_t s)
 {
-    const int K = 2 * a.r + 1;
+    const int K = 2 * r + 1;
     const int smem = K * K * 8;
     auto kern = k_dependent<T, CTU, KC, TY>;
     static int configured = 0;
@@ -401,15 +404,15 @@ cudaError_t dependent_t(const DependentArgs &a, cudaStream_t s)
         if (e != cudaSuccess) return e;
         configured = 1;
     }
-    kern<<<a.g.ctu_cols * a.g.ctu_rows, kDepThreads, smem, s>>>(a);
+    kern<<<b.cta_begin[b.n], kDepThreads, smem, s>>>(b);
     return cudaGetLastError();
 }
 
 template <typename T, int CTU>
-cudaError_t dependent_ctu(const DependentArgs &a, cudaStream_t s)
+cudaError_t dependent_ctu(int r, const DependentBatch &b, cudaStream_t s)
 {
-    if (2 * a.r + 1 <= 9) return dependent_t<T, CTU, 9, sizeof(T) == 1 ? 5 : 3>(a, s);
-    return dependent_t<T, CTU, 17, sizeof(T) == 1 ? 2 : 1>(a, s);
+    if (2 * r + 1 <= 9) return dependent_t<T, CTU, 9, sizeof(T) == 1 ? 5 : 3>(r, b, s);
+    return dependent_t<T, CTU, 17, sizeof(T) == 1 ? 2 : 1>(r, b, s);
 }
 
 }  // namespace
@@ -433,16 +436,17 @@ void refine_rank_tables(int r, uint16_t *rank, uint16_t *unrank)
     }
 }
 
-cudaError_t launch_dependent(int bit_depth, const DependentArgs &a, cudaStream_t s)
+cudaError_t launch_dependent(int bit_depth, int ctu, int r, const DependentBatch &b, cudaStream_t s)
 {
+    if (b.n < 1 || b.n > kMaxBatch || b.cta_begin[b.n] <= 0) return cudaErrorInvalidValue;
     if (bit_depth == 8) {
-        if (a.g.ctu == 64) return dependent_ctu<uint8_t, 64>(a, s);
-        if (a.g.ctu == 32) return dependent_ctu<uint8_t, 32>(a, s);
-        return dependent_ctu<uint8_t, 16>(a, s);
+        if (ctu == 64) return dependent_ctu<uint8_t, 64>(r, b, s);
+        if (ctu == 32) return dependent_ctu<uint8_t, 32>(r, b, s);
+        return dependent_ctu<uint8_t, 16>(r, b, s);
     }
-    if (a.g.ctu == 64) return dependent_ctu<uint16_t, 64>(a, s);
-    if (a.g.ctu == 32) return dependent_ctu<uint16_t, 32>(a, s);
-    return dependent_ctu<uint16_t, 16>(a, s);
+    if (ctu == 64) return dependent_ctu<uint16_t, 64>(r, b, s);
+    if (ctu == 32) return dependent_ctu<uint16_t, 32>(r, b, s);
+    return dependent_ctu<uint16_t, 16>(r, b, s);
 }
 
 }  // namespace ladder_impl

@@ -57,6 +57,9 @@ SIGNATURES = [
                                          ctypes.c_long, ctypes.c_int, ctypes.c_void_p]),
     ("analyze_dependent", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_long, ctypes.c_int, ctypes.c_void_p]),
+    ("analyze_dependents", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                          ctypes.POINTER(ctypes.c_long), ctypes.c_int, ctypes.c_void_p]),
     ("analyze_independent", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_long, ctypes.c_int, ctypes.c_void_p]),
     ("fetch_decisions", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Decisions),
@@ -126,6 +129,13 @@ def analyze_reference(h, frame_id, cur_ptr, ref_ptr, pitch_bytes, qp, stream=0):
 
 def analyze_dependent(h, rung, frame_id, cur_ptr, ref_ptr, pitch_bytes, qp, stream=0):
     return _call(h, "analyze_dependent", h, rung, frame_id, cur_ptr, ref_ptr, pitch_bytes, qp, stream)
+
+
+def analyze_dependents(h, frame_id, rungs, cur_ptrs, ref_ptrs, pitches, qp, stream=0):
+    n = len(rungs)
+    return _call(h, "analyze_dependents", h, frame_id, n, (ctypes.c_int * n)(*rungs),
+                 (ctypes.c_void_p * n)(*cur_ptrs), (ctypes.c_void_p * n)(*ref_ptrs), (ctypes.c_long * n)(*pitches),
+                 qp, stream)
 
 
 def analyze_independent(h, rung, frame_id, cur_ptr, ref_ptr, pitch_bytes, qp, stream=0):
@@ -240,6 +250,12 @@ class Ladder:
     def analyze_dependent(self, rung, frame_id, cur, ref, qp, stream=None):
         analyze_dependent(self.handle, rung, frame_id, cur.data_ptr(), ref.data_ptr(), _pitch_bytes(cur), qp,
                           _stream_handle(stream))
+
+    def analyze_dependents(self, frame_id, items, qp, stream=None):
+        """items: [(rung, cur, ref), ...] analysed by one launch."""
+        analyze_dependents(self.handle, frame_id, [r for r, _, _ in items], [c.data_ptr() for _, c, _ in items],
+                           [f.data_ptr() for _, _, f in items], [_pitch_bytes(c) for _, c, _ in items], qp,
+                           _stream_handle(stream))
 
     def analyze_independent(self, rung, frame_id, cur, ref, qp, stream=None):
         analyze_independent(self.handle, rung, frame_id, cur.data_ptr(), ref.data_ptr(), _pitch_bytes(cur), qp,

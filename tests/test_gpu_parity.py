@@ -123,6 +123,26 @@ def test_dependent_small_ladder(bd, R, r, lo, hi, use_mv, satd):
         assert_decisions_equal(gpu[i], oras[i], 64, where=f"rung {i}")
 
 
+def test_batched_dependents_equal_single_calls():
+    pairs, _ = synth.ladder_pairs(25, source=(960, 540), rungs=[(640, 360), (480, 270), (320, 180)])
+    sizes = [(w, h) for (w, h, _, _) in pairs]
+    with L.Ladder(sizes, 3, search_range=8, refine_range=3, max_frames=2) as lad:
+        planes = [(L.device_plane(c), L.device_plane(f)) for (_, _, c, f) in pairs]
+        for fid in (0, 1):
+            lad.analyze_reference(fid, *planes[3], 32)
+        for i in range(3):
+            lad.analyze_dependent(i, 0, *planes[i], 32)
+        lad.analyze_dependents(1, [(i, planes[i][0], planes[i][1]) for i in (2, 0, 1)], 32)
+        single = [lad.fetch(i, 0) for i in range(3)]
+        batched = [lad.fetch(i, 1) for i in range(3)]
+    ref = oracle.analyze(pairs[3][2], pairs[3][3], qp=32, search_range=8)
+    for i in range(3):
+        assert_decisions_equal(batched[i], single[i], 64, where=f"batched rung {i}")
+        ora = oracle.analyze(pairs[i][2], pairs[i][3], qp=32, search_range=3,
+                             dep=dep_from(ref, sizes[3]))
+        assert_decisions_equal(batched[i], ora, 64, where=f"batched vs oracle rung {i}")
+
+
 def test_dependent_ctu32():
     pairs, gpu, oras, _ = _ladder_case(22, (384, 216), [(288, 162), (192, 108)], 1, 8, 6, 3, 32, ctu=32)
     for i in range(len(pairs)):
