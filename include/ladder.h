@@ -175,6 +175,30 @@ LADDER_API ladder_status ladder_profile_enable(ladder_t *ladder, int enable);
 LADDER_API ladder_status ladder_profile_read(ladder_t *ladder, int kind, long *launches, double *total_ms,
                                              int reset);
 
+/* Independent analysis of one frame pair that allocates no memory (the
+ * paper has no counterpart: this is for callers that cannot call cudaMalloc,
+ * such as a plugin inside an application that owns all device memory through
+ * its own pool, or a real-time pipeline that forbids allocation after
+ * start-up).  Same analysis as analyze_reference on a one-rung ladder of the
+ * given geometry, without a ladder handle: `cur` / `ref` are device planes as
+ * for analyze_reference, and `out` holds DEVICE pointers to caller-owned
+ * decision arrays (every member up to depth log2(ctu_size/8) must be set),
+ * which are written asynchronously on `cuda_stream`.
+ * Scratch lives in a fixed 2 MiB device array inside the library (every GPU
+ * that loads the library holds it until exit): frames of at most 3059 CTUs
+ * of 64x64 (a 3840x2160 frame has 2040; about 4x that count at CTU 32) fit; larger ones
+ * return LADDER_E_INVAL, like any argument the other entry points refuse.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents (each call resets
+ * what must start empty); calls whose work overlaps on the GPU race on it, so
+ * order them.  A bounded device wait that runs out is recorded in the
+ * array's status word but not reported by this call. */
+LADDER_API ladder_status analyze_reference_noalloc(const void *cur, const void *ref, int width, int height,
+                                                   long pitch_bytes, int bit_depth, int ctu_size, int search_range,
+                                                   int qp, int satd_mode, const ladder_decisions *out,
+                                                   void *cuda_stream);
+
 /* Library version string. */
 LADDER_API const char *ladder_version(void);
 

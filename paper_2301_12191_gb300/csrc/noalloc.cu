@@ -1,0 +1,208 @@
+// noalloc.cu -- independent analysis of one frame pair that allocates no
+// memory at all.
+//
+// Who needs it: code that is not allowed to call cudaMalloc, e.g. an encoder
+// plugin hosted by an application that owns every device allocation through
+// its own pool, a real-time pipeline that forbids allocations (and the device
+// synchronisation cudaMalloc may cause) after start-up, or a caller that only
+// hands us device buffers it already has.  The caller passes the input planes
+// and the output decision arrays (all device memory it owns); the scratch
+// the search needs lives in the fixed array below, which the module creates
+// when the library is loaded.
+//
+// Scratch: g_noalloc_scratch holds the device status word, the candidate
+// tile list and the per-CTU argmin keys.  Its size caps the frame: at most
+// kNoallocMaxKeyBytes / (8 * keys per CTU) CTUs (3059 CTUs of 64x64; a
+// 3840x2160 frame has 2040) and kNoallocMaxTiles candidate tiles (enough for +-64).
+// Every call reuses the same array and leaves its contents behind; the keys
+// are reset at the start of each call.  Two calls whose work overlaps on the
+// GPU (different streams, no ordering) race on the array: order them.
+#include "../../include/ladder.h"
+#include "ladder_internal.h"
+
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+using namespace ladder_impl;
+
+namespace {
+
+constexpr size_t kNoallocScratchBytes = 2u << 20;               // 2 MiB, every device that loads the library
+constexpr size_t kNoallocStatusBytes = 256;
+constexpr int kNoallocMaxTiles = 4096;
+constexpr size_t kNoallocTileBytes = kNoallocMaxTiles * 4;      // 16 KiB
+constexpr size_t kNoallocMaxKeyBytes = kNoallocScratchBytes - kNoallocStatusBytes - kNoallocTileBytes;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_lock;
+unsigned char *g_noalloc_ptr[kMaxDevices] = {};  // device address of the scratch, per device
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode_na = nullptr;
+std::once_flag g_encode_na_once;
+
+// Device address of the scratch array on the current device: looked up once
+// per device with that device current (host code may not use the symbol
+// itself, which is only a host-side stand-in for the device array).
+ladder_status scratch_for_current_device(unsigned char **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LADDER_E_CUDA;
+    std::lock_guard<std::mutex> guard(g_noalloc_lock);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return LADDER_E_CUDA;
+        }
+        g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return LADDER_OK;
+}
+
+}  // namespace
+
+extern "C" ladder_status analyze_reference_noalloc(const void *cur, const void *ref, int width, int height,
+                                                   long pitch_bytes, int bit_depth, int ctu_size, int search_range,
+                                                   int qp, int satd_mode, const ladder_decisions *out,
+                                                   void *cuda_stream)
+{
+    // argument checks (the same limits as ladder_init / analyze_reference)
+    if (!cur || !ref || !out) return LADDER_E_INVAL;
+    if (bit_depth != 8 && bit_depth != 10) return LADDER_E_INVAL;
+    if (ctu_size != 16 && ctu_size != 32 && ctu_size != 64) return LADDER_E_INVAL;
+    if (search_range < 4 || search_range > 64 || qp < 0 || qp > 51) return LADDER_E_INVAL;
+    if (satd_mode != 0 && satd_mode != 1) return LADDER_E_INVAL;
+    if (width < 16 || height < 16 || width > 8192 || height > 8192 || (width & 1) || (height & 1))
+        return LADDER_E_INVAL;
+    const int ss = bit_depth == 8 ? 1 : 2;
+    if (pitch_bytes <= 0 || (pitch_bytes & 15) || pitch_bytes < static_cast<long>(width) * ss) return LADDER_E_INVAL;
+    if ((reinterpret_cast<uintptr_t>(cur) & 15) || (reinterpret_cast<uintptr_t>(ref) & 15)) return LADDER_E_INVAL;
+
+    RungGeom g{};
+    g.W = width;
+    g.H = height;
+    g.W8 = (width + 7) / 8 * 8;
+    g.H8 = (height + 7) / 8 * 8;
+    g.ctu = ctu_size;
+    g.dmax = ctu_size == 64 ? 3 : (ctu_size == 32 ? 2 : 1);
+    g.ctu_cols = (g.W8 + ctu_size - 1) / ctu_size;
+    g.ctu_rows = (g.H8 + ctu_size - 1) / ctu_size;
+    for (int d = 0; d <= g.dmax; ++d) {
+        const int S = ctu_size >> d;
+        g.cols[d] = (g.W8 + S - 1) / S;
+        g.rows[d] = (g.H8 + S - 1) / S;
+    }
+    g.cols8 = g.W8 / 8;
+    g.rows8 = g.H8 / 8;
+    // sizes beyond the scratch array are refused
+    const int nctus = g.ctu_cols * g.ctu_rows;
+    const long nkeys = static_cast<long>(nctus) * keys_per_ctu(g.dmax);
+    if (static_cast<size_t>(nkeys) * 8 > kNoallocMaxKeyBytes) return LADDER_E_INVAL;
+    DevDecisions dec{};
+    for (int d = 0; d <= g.dmax; ++d) {
+        if (!out->mvx[d] || !out->mvy[d] || !out->sad[d] || !out->satd[d] || !out->cost[d] || !out->best[d] ||
+            !out->split[d] || !out->evaluated[d])
+            return LADDER_E_INVAL;
+        dec.mvx[d] = out->mvx[d];
+        dec.mvy[d] = out->mvy[d];
+        dec.sad[d] = out->sad[d];
+        dec.satd[d] = out->satd[d];
+        dec.cost[d] = out->cost[d];
+        dec.best[d] = out->best[d];
+        dec.split[d] = out->split[d];
+        dec.evaluated[d] = out->evaluated[d];
+    }
+    if (!out->leaf_depth || !out->leaf_mvx || !out->leaf_mvy) return LADDER_E_INVAL;
+    dec.leaf_depth = out->leaf_depth;
+    dec.leaf_mvx = out->leaf_mvx;
+    dec.leaf_mvy = out->leaf_mvy;
+
+    int tiles[kNoallocMaxTiles];  // host stack, no allocation
+    const int ntiles = full_search_tiles(bit_depth, search_range, nullptr, 0);
+    if (ntiles > kNoallocMaxTiles) return LADDER_E_INVAL;
+    full_search_tiles(bit_depth, search_range, tiles, kNoallocMaxTiles);
+
+    unsigned char *scratch = nullptr;
+    ladder_status st = scratch_for_current_device(&scratch);
+    if (st != LADDER_OK) return st;
+    int *d_status = reinterpret_cast<int *>(scratch);
+    int *d_tiles = reinterpret_cast<int *>(scratch + kNoallocStatusBytes);
+    unsigned long long *d_keys =
+        reinterpret_cast<unsigned long long *>(scratch + kNoallocStatusBytes + kNoallocTileBytes);
+
+    std::call_once(g_encode_na_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode_na = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!g_encode_na) return LADDER_E_CUDA;
+    const FullSearchPlan plan = full_search_plan(bit_depth, ctu_size, search_range);
+    CUtensorMap map;
+    const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(width), static_cast<cuuint64_t>(height)};
+    const cuuint64_t gstride[1] = {static_cast<cuuint64_t>(pitch_bytes)};
+    const cuuint32_t box[2] = {static_cast<cuuint32_t>(plan.box_w), static_cast<cuuint32_t>(plan.box_h)};
+    const cuuint32_t estride[2] = {1, 1};
+    if (g_encode_na(&map, bit_depth == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2,
+                    const_cast<void *>(ref), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return LADDER_E_CUDA;
+
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tiles, tiles, static_cast<size_t>(ntiles) * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_fill_keys(d_keys, nkeys, s);
+    // candidate slices: whole group-iterations, about two CTAs per SM
+    int dev = 0, sms = 1;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return LADDER_E_CUDA;
+    }
+    const int groups = plan.groups;
+    const int target = 2 * sms;
+    const int slices0 = (target + nctus - 1) / nctus;
+    int tps = (ntiles + slices0 - 1) / slices0;
+    tps = (tps + groups - 1) / groups * groups;
+    if (tps < groups) tps = groups;
+    const int slices = (ntiles + tps - 1) / tps;
+    FullSearchArgs fa{};
+    fa.cur = cur;
+    fa.pitch_bytes = pitch_bytes;
+    fa.W = width;
+    fa.H = height;
+    fa.R = search_range;
+    fa.Rp = (search_range + 15) / 16 * 16;
+    fa.ntiles = ntiles;
+    fa.tiles_per_slice = tps;
+    fa.tiles = d_tiles;
+    fa.keys = d_keys;
+    fa.status = d_status;
+    e = launch_full_search(bit_depth, ctu_size, fa, map, slices, nctus, s);
+    if (e == cudaSuccess) {
+        DecideArgs da{};
+        da.cur = cur;
+        da.ref = ref;
+        da.pitch_bytes = pitch_bytes;
+        da.g = g;
+        da.range = search_range;
+        da.keys = d_keys;
+        da.qp = qp;
+        da.satd_mode = satd_mode;
+        da.out = dec;
+        e = launch_decide(bit_depth, da, s);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return LADDER_E_CUDA;
+    }
+    return LADDER_OK;
+}

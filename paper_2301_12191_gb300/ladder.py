@@ -73,6 +73,10 @@ SIGNATURES = [
     ("ladder_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("ladder_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_long),
                                            ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
+    ("analyze_reference_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_long, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_int, ctypes.POINTER(Decisions),
+                                                 ctypes.c_void_p]),
     ("ladder_version", ctypes.c_char_p, []),
 ]
 
@@ -175,6 +179,17 @@ def ladder_profile_read(h, kind: int, reset: bool = False):
     ms = ctypes.c_double()
     _call(h, "ladder_profile_read", h, kind, ctypes.byref(n), ctypes.byref(ms), 1 if reset else 0)
     return n.value, ms.value
+
+
+def analyze_reference_noalloc(cur_ptr, ref_ptr, width, height, pitch_bytes, bit_depth, ctu_size, search_range, qp,
+                              satd_mode, device_decisions: Decisions, stream=0):
+    """One-frame independent analysis into caller-owned device arrays; the
+    library allocates nothing (see include/ladder.h)."""
+    st = load().analyze_reference_noalloc(cur_ptr, ref_ptr, width, height, pitch_bytes, bit_depth, ctu_size,
+                                          search_range, qp, satd_mode, ctypes.byref(device_decisions), stream)
+    if st != 0:
+        raise LadderError(st, "analyze_reference_noalloc")
+    return st
 
 
 # ---- torch convenience ----------------------------------------------------
