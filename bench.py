@@ -45,14 +45,22 @@ METRIC = "ladder frames/sec (multi-resolution inter analysis)"
 UNIT = "ladder_frames/s"
 L2_FLUSH_BYTES = 256 << 20
 
-# DRAM traffic of one full-search launch from an ncu capture, keyed by the
-# hash of the kernel source it was taken on (null once the kernel changes).
-TRAFFIC_NCU = {}
+# DRAM bytes (read + write) of one launch from an ncu capture of the bench
+# command (profiles/ladder1080_launch_list.md), keyed by kernel, workload and
+# the hash of the kernel sources it was taken on: null once a kernel changes.
+KERNEL_SOURCES = {"full_search": ["me_full.cu", "common.cuh"], "dependent": ["me_dependent.cu", "common.cuh"]}
+TRAFFIC_NCU = {
+    ("full_search", "ladder1080", "1763a35d0493"): 599296,
+    ("dependent", "ladder1080", "b8679e064de9"): 7197696,
+}
 
 
-def kernel_source_hash(name="me_full.cu"):
-    p = os.path.join(ROOT, "paper_2301_12191_gb300", "csrc", name)
-    return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
+def kernel_source_hash(kernel):
+    m = hashlib.sha1()
+    for name in KERNEL_SOURCES.get(kernel, []):
+        with open(os.path.join(ROOT, "paper_2301_12191_gb300", "csrc", name), "rb") as f:
+            m.update(f.read())
+    return m.hexdigest()[:12]
 
 
 def make_frames(wl, n_frames, seed0):
@@ -245,6 +253,13 @@ def run_ours(args, wl):
 
     K, W = args.steps, args.warmup
     indep_steps = max(3, K // 2)
+    if args.only_multires:
+        ms = timed(step_multi, K, W)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": world * K / (ms * 1e-3), "unit": UNIT, "steps": K,
+                              "warmup": W, "ms_per_step": ms / K, "only": "multires"}))
+        lad.close()
+        return
     with ClockSampler(local) as clk:
         # untimed soak so that the clock samples (every 200 ms) see the load
         t_end = time.perf_counter() + args.soak
@@ -324,7 +339,7 @@ def run_ours(args, wl):
     else:
         algo = None
     achieved = (algo / (kms / klaunch * 1e-3) / 1e12) if (algo and klaunch) else None
-    traffic = TRAFFIC_NCU.get((kname, args.config, kernel_source_hash()))
+    traffic = TRAFFIC_NCU.get((kname, args.config, kernel_source_hash(kname)))
 
     frames_per_s = world * K / (ms_multi * 1e-3)
     result = {
@@ -424,6 +439,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--json-out", default=None)
     ap.add_argument("--soak", type=float, default=1.5, help="untimed seconds of load before timing (clock sampling)")
+    ap.add_argument("--only-multires", action="store_true",
+                    help="run only warm-up + the timed multi-resolution steps (for profiler launch lists)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
