@@ -35,9 +35,15 @@ WORKLOADS = {
     # 1080p source pair -> 1080p / 720p / 540p / 360p rungs; 360p reference
     "ladder1080": dict(source=(1920, 1080), rungs=[(1920, 1080), (1280, 720), (960, 540), (640, 360)], ref=3,
                        bit_depth=8, R=32, r=4, qp=27, ctu=64),
-    # 2160p 10-bit source -> six rungs; 360p reference at +-64, dependents +-8
-    "uhd10": dict(source=(3840, 2160), rungs=[(3840, 2160), (2560, 1440), (1920, 1080), (1280, 720), (960, 540),
-                                              (640, 360)], ref=5, bit_depth=10, R=64, r=8, qp=27, ctu=64),
+    # 8 ladders x 5 consecutive frames (4 pairs each) of 1080p, one batched graph per step
+    "batch8x5": dict(mode="batch", ladders=8, frames=5, source=(1920, 1080),
+                     rungs=[(1920, 1080), (1280, 720), (960, 540), (640, 360)], ref=3, bit_depth=8, R=32, r=4,
+                     qps=[22, 27, 32, 37], sigmas=[1, 4, 8], global_range=16, patch_range=24, ctu=64),
+    # 8 frame pairs of 2160p 10-bit -> six rungs; 360p reference at +-64, dependents +-8
+    "uhd8": dict(mode="batch", ladders=8, frames=2, source=(3840, 2160),
+                 rungs=[(3840, 2160), (2560, 1440), (1920, 1080), (1280, 720), (960, 540), (640, 360)], ref=5,
+                 bit_depth=10, R=64, r=8, qps=[22, 27, 32, 37], sigmas=[8], global_range=8 * 3840 // 416,
+                 patch_range=12 * 3840 // 416, ctu=64),
     # single 416x240 pair, independent only
     "frame416": dict(source=(416, 240), rungs=[(416, 240)], ref=0, bit_depth=8, R=16, r=4, qp=32, ctu=64),
 }
@@ -404,6 +410,136 @@ def run_ours(args, wl):
         dist.destroy_process_group()
 
 
+def batch_requests(wl, seed0):
+    """Per ladder a seeded sequence; consecutive frames form the pairs.
+    Returns (frames[l][t][rung] planes, [(ladder, t, qp)] per request)."""
+    frames, reqs = [], []
+    W = wl["source"][0]
+    for l in range(wl["ladders"]):
+        seq = synth.ladder_sequence(seed0 + l, wl["frames"], source=wl["source"], rungs=wl["rungs"],
+                                    bit_depth=wl["bit_depth"], global_range=wl["global_range"],
+                                    patch_range=wl["patch_range"], patch_size=int(round(64 * W / 416 / 8)) * 8,
+                                    noise_sigma=wl["sigmas"][l % len(wl["sigmas"])])
+        frames.append(seq)
+        for t in range(wl["frames"] - 1):
+            reqs.append((l, t, wl["qps"][l % len(wl["qps"])]))
+    return frames, reqs
+
+
+def run_batch(args, wl):
+    """Many ladder frames per step: one captured graph replays
+    ladder_analyze_batch over every (ladder, consecutive pair)."""
+    import torch
+    from paper_2301_12191_gb300 import ladder as L
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    frames, reqs = batch_requests(wl, seed0=3000)
+    n = len(reqs)
+    sizes = list(wl["rungs"])
+    ref_i = wl["ref"]
+    cpu = None
+    if not args.no_cpu_baseline:
+        # oracle: one ladder frame of the batch, all host cores
+        l, t, qp = reqs[0]
+        pairs = [(w, h, frames[l][t + 1][r], frames[l][t][r]) for r, (w, h) in enumerate(sizes)]
+        threads = os.cpu_count() or 1
+        sub = dict(wl, qp=qp)
+        t0 = time.perf_counter()
+        oracle_ladder_frame(sub, pairs, threads)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"1 ladder frame of the batch ({dt:.1f} s)"}
+    dplanes = [[[L.device_plane(p, dev) for p in fr] for fr in seq] for seq in frames]
+    items = [(k, qp, [(dplanes[l][t + 1][r], dplanes[l][t][r]) for r in range(len(sizes))])
+             for k, (l, t, qp) in enumerate(reqs)]
+    lad = L.Ladder(sizes, ref_i, bit_depth=wl["bit_depth"], ctu_size=wl["ctu"], search_range=wl["R"],
+                   refine_range=wl["r"], max_frames=2 * n)
+    items_ind = [(n + k, qp, pl) for (k, qp, pl) in items]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        lad.analyze_batch(items, stream)                 # eager once (sets up slots)
+        lad.analyze_batch_independent(items_ind, stream)
+    stream.synchronize()
+    g_multi = lad.capture_batch(items, stream)
+    # independent baseline, batched the same way (eager: full searches in chunks of 64)
+    evals_ref = sum(((w + 7) // 8) * ((h + 7) // 8) for (w, h) in [sizes[ref_i]]) * (2 * wl["R"] + 1) ** 2
+    evals_dep = 0
+    for r in range(len(sizes)):
+        if r != ref_i:
+            evals_dep += evals_of(lad.fetch(r, 0), sizes[r], wl["ctu"], wl["r"])   # request 0 as the sample
+    evals_multi = n * (evals_ref + evals_dep)
+    evals_indep = n * sum(((w + 7) // 8) * ((h + 7) // 8) for (w, h) in sizes) * (2 * wl["R"] + 1) ** 2
+
+    def timed(fn, K, W):
+        for _ in range(W):
+            fn()
+        stream.synchronize()
+        evs = []
+        for _ in range(K):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            evs.append((a, b))
+        stream.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    K, W = args.steps, args.warmup
+    with ClockSampler(0) as clk:
+        t_end = time.perf_counter() + args.soak
+        while time.perf_counter() < t_end:
+            g_multi.launch(stream)
+            stream.synchronize()
+        ms_multi = timed(lambda: g_multi.launch(stream), K, W)
+        ms_indep = timed(lambda: lad.analyze_batch_independent(items_ind, stream), max(3, K // 2), W)
+    indep_steps = max(3, K // 2)
+    lad.kernel_stats(reset=True)
+    lad.profile(True)
+    for _ in range(3):
+        lad.analyze_batch(items, stream)
+    stats = lad.kernel_stats(reset=True)
+    lad.profile(False)
+    dom = max(stats.items(), key=lambda kv: kv[1][1])
+    kname, (klaunch, kms) = dom
+    props = torch.cuda.get_device_properties(dev)
+    clocks = clk.summary()
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    absdiff_per_instr = 4 if wl["bit_depth"] == 8 else 2
+    peak = props.multi_processor_count * 64 * absdiff_per_instr * sm_max * 1e6 / 1e12
+    algo = {"full_search": 64 * evals_ref * n, "dependent": 64 * evals_dep * n}.get(kname)
+    achieved = (algo / (kms / klaunch * 1e-3) / 1e12) if (algo and klaunch) else None
+    result = {
+        "metric": METRIC, "value": n * K / (ms_multi * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W,
+        "ms_per_step": ms_multi / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u8" if wl["bit_depth"] == 8 else "u16", "data": "synthetic (seeded sequences, see DESIGN.md)",
+        "config": {"workload": args.config, "ladder_frames_per_step": n, "rungs": [f"{w}x{h}" for (w, h) in sizes],
+                   "reference_rung": f"{sizes[ref_i][0]}x{sizes[ref_i][1]}", "search_range": wl["R"],
+                   "refine_range": wl["r"], "bit_depth": wl["bit_depth"],
+                   "l2": "inputs larger than L2 (no flush)", "launch": "one CUDA graph per step (4 kernels)"},
+        "sad_candidate_evals_per_s": evals_multi * K / (ms_multi * 1e-3),
+        "independent": {"frames_per_s": n * indep_steps / (ms_indep * 1e-3), "ms_per_step": ms_indep / indep_steps,
+                        "sad_candidate_evals_per_s": evals_indep * indep_steps / (ms_indep * 1e-3)},
+        "multires_speedup_vs_independent": (ms_indep / indep_steps) / (ms_multi / K),
+        "kernels": {k: {"launches": nl, "ms_total": ms, "share": ms / max(1e-9, sum(v[1] for v in stats.values()))}
+                    for k, (nl, ms) in stats.items()},
+        "gpu_launches": 4 * K,
+        "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tabsdiff/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "algorithmic_absdiffs_per_launch": algo, "avg_launch_ms": (kms / klaunch) if klaunch else None},
+        "clocks": dict(clocks, window="untimed soak + timed loops"),
+    }
+    if cpu:
+        result["cpu_baseline"] = cpu
+    print(json.dumps(result))
+    if args.json_out:
+        with open(args.json_out, "w") as fh:
+            json.dump(result, fh, indent=1)
+    g_multi.close()
+    lad.close()
+
+
 def run_reference(args, wl):
     """The oracle on the host cores, same metric and workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -447,6 +583,8 @@ def main():
     wl = WORKLOADS[args.config]
     if args.impl == "reference":
         run_reference(args, wl)
+    elif wl.get("mode") == "batch":
+        run_batch(args, wl)
     else:
         run_ours(args, wl)
 

@@ -76,7 +76,7 @@ typedef struct {
     int dep_depth_hi;          /*   defaults 0, +1 (evaluate depth n and n+1) */
     int dep_use_ref_mv;        /* 1: search centre = scaled reference MV; 0: (0,0) */
     int satd_mode;             /* 0: 8x8 Hadamard, (sum|T|)>>2; 1: two 4x4 per 8x4 half, >>1 */
-    int max_frames;            /* resident frame slots (1..64) */
+    int max_frames;            /* resident frame slots (1..256) */
 } ladder_geometry;
 
 /* Decisions of one rung for one frame, all in CU raster order of the frame's
@@ -128,6 +128,50 @@ LADDER_API ladder_status analyze_dependent(ladder_t *ladder, int rung, int frame
 LADDER_API ladder_status analyze_dependents(ladder_t *ladder, int frame_id, int n, const int *rungs,
                                             const void *const *cur, const void *const *ref,
                                             const long *pitch_bytes, int qp, void *cuda_stream);
+
+/* One frame of one ladder in a batch: its planes for every rung, in rung
+ * order (device pointers), and its QP.  `frame_id` names its frame slot. */
+typedef struct {
+    int frame_id;
+    int qp;
+    const void *const *cur;     /* n_rungs current planes */
+    const void *const *ref;     /* n_rungs reference planes */
+    const long *pitch_bytes;    /* n_rungs row pitches */
+} ladder_request;
+
+/* Analyses many ladder frames together: the reference rung of every request
+ * independently, then every other rung as a dependent of its own frame's
+ * reference (results identical to analyze_reference + analyze_dependents per
+ * request).  Four launches for the whole batch: key reset, full search,
+ * decisions, dependents.  n in 1..64 and n x (n_rungs - 1) <= 192; frame ids
+ * distinct.  LADDER_E_BUSY when the batch needs more free frame slots than
+ * there are (nothing is launched then). */
+LADDER_API ladder_status ladder_analyze_batch(ladder_t *ladder, const ladder_request *requests, int n,
+                                              void *cuda_stream);
+
+/* Every rung of every request analysed independently (full search +-R on
+ * each rung), batched like ladder_analyze_batch: the per-rung baseline of the
+ * multi-resolution speedup.  n in 1..64. */
+LADDER_API ladder_status ladder_analyze_batch_independent(ladder_t *ladder, const ladder_request *requests, int n,
+                                                          void *cuda_stream);
+
+/* A batch captured once into a CUDA graph, replayed by ladder_graph_launch
+ * (the planes named in the requests are read at every replay, so the caller
+ * refills those buffers between replays).  Capture runs on `cuda_stream`,
+ * which must not be the legacy default stream; kernel timing is off inside
+ * the graph. */
+typedef struct ladder_graph ladder_graph_t;
+LADDER_API ladder_status ladder_capture_batch(ladder_t *ladder, const ladder_request *requests, int n,
+                                              void *cuda_stream, ladder_graph_t **out);
+LADDER_API ladder_status ladder_graph_launch(ladder_graph_t *graph, void *cuda_stream);
+LADDER_API void ladder_graph_destroy(ladder_graph_t *graph);
+
+/* Candidate tiles per full-search CTA (0 restores the built-in choice of
+ * about two waves): the knob the autotuner sets. */
+LADDER_API ladder_status ladder_set_tiles_per_slice(ladder_t *ladder, int tiles_per_slice);
+
+/* Device bytes the handle holds (decision buffers of every frame slot). */
+LADDER_API long ladder_device_bytes(const ladder_t *ladder);
 
 /* Independent full search (+-R) of any rung, the per-rung baseline against
  * which the multi-resolution speedup is measured.  Needs no reference; claims

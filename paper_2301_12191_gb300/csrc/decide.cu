@@ -1,7 +1,7 @@
 // decide.cu -- independent analysis, step 2: decode the per-CTU argmin keys
 // of the full search, then SATD at the chosen vectors, rate-distortion cost,
-// bottom-up quadtree split and leaf maps (one CTA per CTU); and the key
-// initialisation kernel.
+// bottom-up quadtree split and leaf maps (one CTA per CTU, for every frame
+// of a batch); and the key initialisation kernel.
 #include "common.cuh"
 
 #include <algorithm>
@@ -14,15 +14,20 @@ __constant__ int c_lambda_q16[52] = {
 };
 
 template <typename T, int CTU>
-__global__ void __launch_bounds__(kThreads) k_decide(const DecideArgs a)
+__global__ void __launch_bounds__(kThreads) k_decide(const __grid_constant__ DecideBatch b)
 {
     using C = dev::Ctu<CTU>;
     __shared__ dev::CtuState<CTU> st;
-    const RungGeom &g = a.g;
+    int ii = 0;  // the batch item of this CTA
+    while (ii + 1 < b.n && static_cast<int>(blockIdx.x) >= b.item[ii + 1].cta_begin) ++ii;
+    const DecideItem &item = b.item[ii];
+    const RungInfo &ri = b.rung[item.rung];
+    const RungGeom &g = ri.g;
+    const unsigned long long *keys = reinterpret_cast<const unsigned long long *>(item.block + ri.off.keys);
     const int tid = threadIdx.x;
-    const int ctu_idx = blockIdx.x;
+    const int ctu_idx = blockIdx.x - item.cta_begin;
     const int x0 = (ctu_idx % g.ctu_cols) * CTU, y0 = (ctu_idx / g.ctu_cols) * CTU;
-    const int K = 2 * a.range + 1;
+    const int K = 2 * b.range + 1;
 
     for (int i = tid; i < C::NKEY; i += kThreads) {
         int d = 0;
@@ -38,10 +43,10 @@ __global__ void __launch_bounds__(kThreads) k_decide(const DecideArgs a)
         st.flags[i] = flags;
         st.satd[i] = 0;
         if (flags & kRuleEvaluated) {
-            const unsigned long long key = a.keys[static_cast<long>(ctu_idx) * C::NKEY + i];
+            const unsigned long long key = keys[static_cast<long>(ctu_idx) * C::NKEY + i];
             const int rem = static_cast<int>(static_cast<uint32_t>(key & 0xffffffffu) % static_cast<uint32_t>(K * K));
-            st.mvx[i] = static_cast<int16_t>(rem % K - a.range);
-            st.mvy[i] = static_cast<int16_t>(rem / K - a.range);
+            st.mvx[i] = static_cast<int16_t>(rem % K - b.range);
+            st.mvy[i] = static_cast<int16_t>(rem / K - b.range);
             st.sad[i] = static_cast<int32_t>(key >> 32);
         } else {
             st.mvx[i] = INT16_MIN;
@@ -50,42 +55,48 @@ __global__ void __launch_bounds__(kThreads) k_decide(const DecideArgs a)
         }
     }
     __syncthreads();
-    dev::DecideIO io{a.cur, a.ref, a.pitch_bytes, &a.g, a.qp, a.satd_mode, c_lambda_q16, a.out};
+    dev::DecideIO io{item.cur, item.ref, item.pitch_bytes, &g, item.qp, b.satd_mode, c_lambda_q16,
+                     decisions_at(item.block, ri.off)};
     dev::ctu_decide<T, CTU>(st, io, x0, y0);
 }
 
-__global__ void k_fill_keys(unsigned long long *keys, long n)
+__global__ void k_fill_keys(const __grid_constant__ FillBatch b)
 {
-    for (long i = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += static_cast<long>(gridDim.x) * blockDim.x)
-        keys[i] = ~0ull;
+    for (int k = 0; k < b.n; ++k)
+        for (long i = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x; i < b.item[k].n;
+             i += static_cast<long>(gridDim.x) * blockDim.x)
+            b.item[k].keys[i] = ~0ull;
 }
 
 template <typename T, int CTU>
-cudaError_t decide_t(const DecideArgs &a, cudaStream_t s)
+cudaError_t decide_t(const DecideBatch &b, cudaStream_t s)
 {
-    k_decide<T, CTU><<<a.g.ctu_cols * a.g.ctu_rows, kThreads, 0, s>>>(a);
+    k_decide<T, CTU><<<b.total_ctas, kThreads, 0, s>>>(b);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_decide(int bit_depth, const DecideArgs &a, cudaStream_t s)
+cudaError_t launch_decide(int bit_depth, int ctu, const DecideBatch &b, cudaStream_t s)
 {
+    if (b.n < 1 || b.n > kMaxItems || b.total_ctas <= 0) return cudaErrorInvalidValue;
     if (bit_depth == 8) {
-        if (a.g.ctu == 64) return decide_t<uint8_t, 64>(a, s);
-        if (a.g.ctu == 32) return decide_t<uint8_t, 32>(a, s);
-        return decide_t<uint8_t, 16>(a, s);
+        if (ctu == 64) return decide_t<uint8_t, 64>(b, s);
+        if (ctu == 32) return decide_t<uint8_t, 32>(b, s);
+        return decide_t<uint8_t, 16>(b, s);
     }
-    if (a.g.ctu == 64) return decide_t<uint16_t, 64>(a, s);
-    if (a.g.ctu == 32) return decide_t<uint16_t, 32>(a, s);
-    return decide_t<uint16_t, 16>(a, s);
+    if (ctu == 64) return decide_t<uint16_t, 64>(b, s);
+    if (ctu == 32) return decide_t<uint16_t, 32>(b, s);
+    return decide_t<uint16_t, 16>(b, s);
 }
 
-cudaError_t launch_fill_keys(unsigned long long *keys, long n, cudaStream_t s)
+cudaError_t launch_fill_keys(const FillBatch &b, cudaStream_t s)
 {
-    const int blocks = static_cast<int>(std::min<long>((n + kThreads - 1) / kThreads, 1024));
-    k_fill_keys<<<blocks > 0 ? blocks : 1, kThreads, 0, s>>>(keys, n);
+    if (b.n < 1 || b.n > kMaxItems) return cudaErrorInvalidValue;
+    long most = 0;
+    for (int k = 0; k < b.n; ++k) most = std::max(most, b.item[k].n);
+    const int blocks = static_cast<int>(std::max<long>(1, std::min<long>((most + kThreads - 1) / kThreads, 1024)));
+    k_fill_keys<<<blocks, kThreads, 0, s>>>(b);
     return cudaGetLastError();
 }
 

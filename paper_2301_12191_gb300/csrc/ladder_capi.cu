@@ -1,6 +1,7 @@
 // ladder_capi.cu -- host side of the C ABI declared in include/ladder.h:
 // geometry validation, frame slots, one device arena per handle, TMA
-// descriptor encoding and the launch sequence of each analysis.
+// descriptor encoding, batched launch descriptors, CUDA-graph capture of a
+// batch, and per-kernel tracing.
 #include "../../include/ladder.h"
 #include "ladder_internal.h"
 
@@ -19,10 +20,7 @@ using namespace ladder_impl;
 namespace {
 
 struct RungBuffers {
-    DevDecisions dec;
-    char *dec_base;     // the decision arrays form one contiguous block
-    size_t dec_bytes;
-    unsigned long long *keys;
+    char *block;   // decision arrays [0, dec_bytes) then the argmin keys
     int analysed;  // 0: nothing, 1: independent, 2: dependent
 };
 
@@ -38,8 +36,6 @@ std::once_flag g_encode_once;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-}  // namespace
-
 constexpr int kKinds = 4;  // full search, decide, dependent, fill keys
 
 struct ProfEvent {
@@ -47,10 +43,12 @@ struct ProfEvent {
     cudaEvent_t start, stop;
 };
 
+}  // namespace
+
 struct ladder {
     ladder_geometry geo;
     std::vector<ladder_rung> rungs;
-    std::vector<RungGeom> rg;
+    std::vector<RungInfo> info;  // geometry + block layout per rung
     std::vector<Slot> slots;
     void *arena = nullptr;
     size_t arena_bytes = 0;
@@ -61,7 +59,8 @@ struct ladder {
     int rank_bits = 0;
     std::string err;
     int sm_count = 0;
-    int fs_ctas_per_sm = 1;  // resident full-search CTAs per SM
+    int fs_ctas_per_sm = 1;      // resident full-search CTAs per SM
+    int fs_tps_override = 0;     // tiles per slice set by a tuner (0: heuristic)
     char *host_stage = nullptr;  // pinned staging for fetch_decisions
     size_t host_stage_bytes = 0;
     // tracing
@@ -70,6 +69,11 @@ struct ladder {
     double total_ms[kKinds] = {};
     std::vector<ProfEvent> pending;
     std::vector<cudaEvent_t> spare;
+};
+
+struct ladder_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -123,7 +127,8 @@ void drain_events(ladder_t *l)
 {
     for (auto &pe : l->pending) {
         float ms = 0.f;
-        if (cudaEventSynchronize(pe.stop) == cudaSuccess && cudaEventElapsedTime(&ms, pe.start, pe.stop) == cudaSuccess)
+        if (cudaEventSynchronize(pe.stop) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, pe.start, pe.stop) == cudaSuccess)
             l->total_ms[pe.kind] += ms;
         l->spare.push_back(pe.start);
         l->spare.push_back(pe.stop);
@@ -152,45 +157,41 @@ RungGeom make_geom(int W, int H, int ctu)
     return g;
 }
 
-// Bytes of one (slot, rung) buffer set; carves it when base != nullptr.
-size_t carve(const RungGeom &g, char *base, RungBuffers *rb)
+// Layout of one (slot, rung) block: the decision arrays, each 256-byte
+// aligned, then the argmin keys.  Returns the block's bytes.
+size_t layout(const RungGeom &g, DecOffsets &o)
 {
     size_t off = 0;
     auto take = [&](size_t bytes) {
-        char *p = base ? base + off : nullptr;
+        const long at = static_cast<long>(off);
         off += align_up(bytes, 256);
-        return p;
+        return at;
     };
+    o = DecOffsets{};
     for (int d = 0; d <= g.dmax; ++d) {
         const size_t n = static_cast<size_t>(g.cols[d]) * g.rows[d];
-        char *p;
-        p = take(n * 2); if (rb) rb->dec.mvx[d] = reinterpret_cast<int16_t *>(p);
-        p = take(n * 2); if (rb) rb->dec.mvy[d] = reinterpret_cast<int16_t *>(p);
-        p = take(n * 4); if (rb) rb->dec.sad[d] = reinterpret_cast<int32_t *>(p);
-        p = take(n * 4); if (rb) rb->dec.satd[d] = reinterpret_cast<int32_t *>(p);
-        p = take(n * 4); if (rb) rb->dec.cost[d] = reinterpret_cast<int32_t *>(p);
-        p = take(n * 4); if (rb) rb->dec.best[d] = reinterpret_cast<int32_t *>(p);
-        p = take(n); if (rb) rb->dec.split[d] = reinterpret_cast<uint8_t *>(p);
-        p = take(n); if (rb) rb->dec.evaluated[d] = reinterpret_cast<uint8_t *>(p);
+        o.mvx[d] = take(n * 2);
+        o.mvy[d] = take(n * 2);
+        o.sad[d] = take(n * 4);
+        o.satd[d] = take(n * 4);
+        o.cost[d] = take(n * 4);
+        o.best[d] = take(n * 4);
+        o.split[d] = take(n);
+        o.evaluated[d] = take(n);
     }
     const size_t n8 = static_cast<size_t>(g.cols8) * g.rows8;
-    char *p;
-    p = take(n8); if (rb) rb->dec.leaf_depth = reinterpret_cast<uint8_t *>(p);
-    p = take(n8 * 2); if (rb) rb->dec.leaf_mvx = reinterpret_cast<int16_t *>(p);
-    p = take(n8 * 2); if (rb) rb->dec.leaf_mvy = reinterpret_cast<int16_t *>(p);
-    if (rb) {
-        rb->dec_base = base;
-        rb->dec_bytes = off;
-    }
-    const size_t nk = static_cast<size_t>(g.ctu_cols) * g.ctu_rows * keys_per_ctu(g.dmax);
-    p = take(nk * 8); if (rb) rb->keys = reinterpret_cast<unsigned long long *>(p);
+    o.leaf_depth = take(n8);
+    o.leaf_mvx = take(n8 * 2);
+    o.leaf_mvy = take(n8 * 2);
+    o.dec_bytes = static_cast<long>(off);
+    o.keys = take(static_cast<size_t>(g.ctu_cols) * g.ctu_rows * keys_per_ctu(g.dmax) * 8);
     return off;
 }
 
 ladder_status validate_geometry(const ladder_geometry *g)
 {
     if (!g || !g->rungs) return LADDER_E_INVAL;
-    if (g->n_rungs < 1 || g->n_rungs > 16) return LADDER_E_INVAL;
+    if (g->n_rungs < 1 || g->n_rungs > kMaxRungs) return LADDER_E_INVAL;
     if (g->ref_rung < 0 || g->ref_rung >= g->n_rungs) return LADDER_E_INVAL;
     if (g->bit_depth != 8 && g->bit_depth != 10) return LADDER_E_INVAL;
     if (g->ctu_size != 16 && g->ctu_size != 32 && g->ctu_size != 64) return LADDER_E_INVAL;
@@ -201,7 +202,7 @@ ladder_status validate_geometry(const ladder_geometry *g)
         return LADDER_E_INVAL;
     if (g->dep_use_ref_mv != 0 && g->dep_use_ref_mv != 1) return LADDER_E_INVAL;
     if (g->satd_mode != 0 && g->satd_mode != 1) return LADDER_E_INVAL;
-    if (g->max_frames < 1 || g->max_frames > 64) return LADDER_E_INVAL;
+    if (g->max_frames < 1 || g->max_frames > 256) return LADDER_E_INVAL;
     for (int i = 0; i < g->n_rungs; ++i) {
         const ladder_rung &r = g->rungs[i];
         if (r.width < 16 || r.height < 16 || r.width > 8192 || r.height > 8192) return LADDER_E_INVAL;
@@ -275,60 +276,111 @@ bool encode_ref_map(ladder_t *l, CUtensorMap *map, const void *ref, const RungGe
     return true;
 }
 
-// Candidate slices per CTU: whole group-iterations per slice (no duplicate
-// tiles), about two waves of CTAs at one resident CTA per SM.
-int choose_tiles_per_slice(const ladder_t *l, int nctus, int ntiles, int groups)
+// Candidate tiles per slice: whole group-iterations (no duplicate tiles),
+// about two waves of CTAs over the whole batch.
+int choose_tiles_per_slice(const ladder_t *l, int total_ctus, int ntiles, int groups)
 {
+    if (l->fs_tps_override > 0) return std::max(groups, l->fs_tps_override / groups * groups);
     const int target = 2 * std::max(1, l->sm_count) * std::max(1, l->fs_ctas_per_sm);
-    const int slices = std::max(1, (target + nctus - 1) / nctus);
+    const int slices = std::max(1, (target + total_ctus - 1) / total_ctus);
     int tps = (ntiles + slices - 1) / slices;
     tps = (tps + groups - 1) / groups * groups;
     return std::max(groups, tps);
 }
 
-ladder_status run_independent(ladder_t *l, Slot *slot, int rung, const void *cur, const void *ref, long pitch,
-                              int qp, cudaStream_t s)
+// One rung of one frame and its planes.
+struct Job {
+    Slot *slot;
+    int rung;
+    const void *cur, *ref;
+    long pitch;
+    int qp;
+};
+
+// Full search + decisions of independently analysed jobs, in batched
+// launches of at most kMaxItems jobs.
+ladder_status launch_independent(ladder_t *l, const Job *jobs, int n, cudaStream_t s)
 {
-    const RungGeom &g = l->rg[rung];
-    RungBuffers &rb = slot->rungs[rung];
-    const int nctus = g.ctu_cols * g.ctu_rows;
     const int R = l->geo.ref_search_range;
-    const FullSearchPlan plan = full_search_plan(l->geo.bit_depth, g.ctu, R);
-    CUtensorMap map;
-    if (!encode_ref_map(l, &map, ref, g, pitch, plan)) return LADDER_E_CUDA;
-    cudaError_t e = traced(l, 3, s, [&] {
-        return launch_fill_keys(rb.keys, static_cast<long>(nctus) * keys_per_ctu(g.dmax), s);
-    });
-    if (e != cudaSuccess) return cuda_fail(l, e, "fill keys");
-    const int tps = choose_tiles_per_slice(l, nctus, l->ntiles, plan.groups);
-    const int slices = (l->ntiles + tps - 1) / tps;
-    FullSearchArgs fa{};
-    fa.cur = cur;
-    fa.pitch_bytes = pitch;
-    fa.W = g.W;
-    fa.H = g.H;
-    fa.R = R;
-    fa.Rp = (R + 15) / 16 * 16;
-    fa.ntiles = l->ntiles;
-    fa.tiles_per_slice = tps;
-    fa.tiles = l->d_tiles;
-    fa.keys = rb.keys;
-    fa.status = l->d_status;
-    e = traced(l, 0, s, [&] { return launch_full_search(l->geo.bit_depth, g.ctu, fa, map, slices, nctus, s); });
-    if (e != cudaSuccess) return cuda_fail(l, e, "full search launch");
-    DecideArgs da{};
-    da.cur = cur;
-    da.ref = ref;
-    da.pitch_bytes = pitch;
-    da.g = g;
-    da.range = R;
-    da.keys = rb.keys;
-    da.qp = qp;
-    da.satd_mode = l->geo.satd_mode;
-    da.out = rb.dec;
-    e = traced(l, 1, s, [&] { return launch_decide(l->geo.bit_depth, da, s); });
-    if (e != cudaSuccess) return cuda_fail(l, e, "decide launch");
-    rb.analysed = 1;
+    const FullSearchPlan plan = full_search_plan(l->geo.bit_depth, l->geo.ctu_size, R);
+    for (int j0 = 0; j0 < n; j0 += kMaxItems) {
+        const int m = std::min(kMaxItems, n - j0);
+        FillBatch fill{};
+        FullSearchBatch fb{};
+        DecideBatch db{};
+        fill.n = m;
+        fb.n = m;
+        fb.R = R;
+        fb.Rp = (R + 15) / 16 * 16;
+        fb.ntiles = l->ntiles;
+        fb.tiles = l->d_tiles;
+        fb.status = l->d_status;
+        db.n = m;
+        db.range = R;
+        db.satd_mode = l->geo.satd_mode;
+        for (int r = 0; r < l->geo.n_rungs; ++r) db.rung[r] = l->info[r];
+        int total = 0;
+        for (int k = 0; k < m; ++k) {
+            const Job &jb = jobs[j0 + k];
+            const RungInfo &ri = l->info[jb.rung];
+            char *block = jb.slot->rungs[jb.rung].block;
+            auto *keys = reinterpret_cast<unsigned long long *>(block + ri.off.keys);
+            const int nctus = ri.g.ctu_cols * ri.g.ctu_rows;
+            fill.item[k] = FillItem{keys, static_cast<long>(nctus) * keys_per_ctu(ri.g.dmax)};
+            if (!encode_ref_map(l, &fb.map[k], jb.ref, ri.g, jb.pitch, plan)) return LADDER_E_CUDA;
+            fb.item[k] = FullSearchItem{jb.cur, jb.pitch, ri.g.W, ri.g.H, keys, total};
+            db.item[k] = DecideItem{jb.cur, jb.ref, jb.pitch, block, jb.rung, jb.qp, total};
+            total += nctus;
+        }
+        db.total_ctas = total;
+        fb.tiles_per_slice = choose_tiles_per_slice(l, total, l->ntiles, plan.groups);
+        const int slices = (l->ntiles + fb.tiles_per_slice - 1) / fb.tiles_per_slice;
+        cudaError_t e = traced(l, 3, s, [&] { return launch_fill_keys(fill, s); });
+        if (e != cudaSuccess) return cuda_fail(l, e, "fill keys");
+        e = traced(l, 0, s, [&] {
+            return launch_full_search(l->geo.bit_depth, l->geo.ctu_size, fb, slices, total, s);
+        });
+        if (e != cudaSuccess) return cuda_fail(l, e, "full search launch");
+        e = traced(l, 1, s, [&] { return launch_decide(l->geo.bit_depth, l->geo.ctu_size, db, s); });
+        if (e != cudaSuccess) return cuda_fail(l, e, "decide launch");
+    }
+    for (int k = 0; k < n; ++k) jobs[k].slot->rungs[jobs[k].rung].analysed = 1;
+    return LADDER_OK;
+}
+
+// Dependent analyses in batched launches of at most kMaxDepItems jobs.
+ladder_status launch_dependents(ladder_t *l, const Job *jobs, int n, cudaStream_t s)
+{
+    for (int j0 = 0; j0 < n; j0 += kMaxDepItems) {
+        const int m = std::min(kMaxDepItems, n - j0);
+        DependentBatch b{};
+        b.n = m;
+        b.r = l->geo.dep_refine_range;
+        b.rank = l->d_rank;
+        b.unrank = l->d_unrank;
+        b.rank_bits = l->rank_bits;
+        b.satd_mode = l->geo.satd_mode;
+        b.ref_rung = l->geo.ref_rung;
+        b.depth_lo = l->geo.dep_depth_lo;
+        b.depth_hi = l->geo.dep_depth_hi;
+        b.use_ref_mv = l->geo.dep_use_ref_mv;
+        b.status = l->d_status;
+        for (int r = 0; r < l->geo.n_rungs; ++r) b.rung[r] = l->info[r];
+        int total = 0;
+        for (int k = 0; k < m; ++k) {
+            const Job &jb = jobs[j0 + k];
+            const RungGeom &g = l->info[jb.rung].g;
+            b.item[k] = DependentItem{jb.cur, jb.ref, jb.pitch, jb.slot->rungs[jb.rung].block,
+                                      jb.slot->rungs[l->geo.ref_rung].block, jb.rung, jb.qp, total};
+            total += g.ctu_cols * g.ctu_rows;
+        }
+        b.total_ctas = total;
+        cudaError_t e = traced(l, 2, s, [&] {
+            return launch_dependent(l->geo.bit_depth, l->geo.ctu_size, l->geo.dep_refine_range, b, s);
+        });
+        if (e != cudaSuccess) return cuda_fail(l, e, "dependent launch");
+    }
+    for (int k = 0; k < n; ++k) jobs[k].slot->rungs[jobs[k].rung].analysed = 2;
     return LADDER_OK;
 }
 
@@ -336,7 +388,7 @@ ladder_status run_independent(ladder_t *l, Slot *slot, int rung, const void *cur
 
 extern "C" {
 
-const char *ladder_version(void) { return "ladder 0.1 (sm_103a)"; }
+const char *ladder_version(void) { return "ladder 0.2 (sm_103a)"; }
 
 ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, ladder_t **out)
 {
@@ -349,19 +401,29 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
     l->geo = *geometry;
     l->rungs.assign(geometry->rungs, geometry->rungs + geometry->n_rungs);
     l->geo.rungs = l->rungs.data();
-    for (const auto &r : l->rungs) l->rg.push_back(make_geom(r.width, r.height, geometry->ctu_size));
+    size_t per_slot = 0;
+    for (const auto &r : l->rungs) {
+        RungInfo ri{};
+        ri.g = make_geom(r.width, r.height, geometry->ctu_size);
+        per_slot += layout(ri.g, ri.off);
+        l->info.push_back(ri);
+    }
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&l->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (prepare_kernels(geometry->bit_depth, geometry->ctu_size, geometry->ref_search_range,
+                        geometry->dep_refine_range) != cudaSuccess) {
+        cudaGetLastError();
+        delete l;
+        return LADDER_E_CUDA;
+    }
     l->fs_ctas_per_sm = full_search_ctas_per_sm(geometry->bit_depth, geometry->ctu_size, geometry->ref_search_range);
 
-    size_t per_slot = 0;
-    for (const auto &g : l->rg) per_slot += carve(g, nullptr, nullptr);
     const int ntiles = full_search_tiles(geometry->bit_depth, geometry->ref_search_range, nullptr, 0);
     l->ntiles = ntiles;
     const int Kr = 2 * geometry->dep_refine_range + 1;
     const size_t rank_bytes = align_up(static_cast<size_t>(Kr) * Kr * 2, 256);
-    const size_t fixed = align_up(256, 256) + align_up(static_cast<size_t>(ntiles) * 4, 256) + 2 * rank_bytes;
+    const size_t fixed = 256 + align_up(static_cast<size_t>(ntiles) * 4, 256) + 2 * rank_bytes;
     l->arena_bytes = fixed + per_slot * geometry->max_frames;
     cudaError_t e = cudaMalloc(&l->arena, l->arena_bytes);
     if (e != cudaSuccess) {
@@ -377,17 +439,20 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
     while ((1 << l->rank_bits) < Kr * Kr) ++l->rank_bits;
     char *p = base + fixed;
     l->slots.resize(geometry->max_frames);
-    for (auto &s : l->slots) {
-        s.used = 0;
-        s.frame_id = 0;
-        s.ref_done = 0;
-        s.rungs.resize(l->rg.size());
-        for (size_t r = 0; r < l->rg.size(); ++r) {
-            p += carve(l->rg[r], p, &s.rungs[r]);
-            s.rungs[r].analysed = 0;
+    for (auto &sl : l->slots) {
+        sl.used = 0;
+        sl.frame_id = 0;
+        sl.ref_done = 0;
+        sl.rungs.resize(l->info.size());
+        for (size_t r = 0; r < l->info.size(); ++r) {
+            DecOffsets o;
+            sl.rungs[r].block = p;
+            sl.rungs[r].analysed = 0;
+            p += layout(l->info[r].g, o);
         }
     }
-    for (const auto &r : l->slots[0].rungs) l->host_stage_bytes = std::max(l->host_stage_bytes, r.dec_bytes);
+    for (const auto &ri : l->info)
+        l->host_stage_bytes = std::max(l->host_stage_bytes, static_cast<size_t>(ri.off.dec_bytes));
     if (cudaMallocHost(&l->host_stage, l->host_stage_bytes) != cudaSuccess) {
         cudaFree(l->arena);
         delete l;
@@ -396,12 +461,12 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
     }
     std::vector<int> tiles(ntiles);
     full_search_tiles(geometry->bit_depth, geometry->ref_search_range, tiles.data(), ntiles);
+    std::vector<uint16_t> rank(static_cast<size_t>(Kr) * Kr), unrank(rank.size());
+    refine_rank_tables(geometry->dep_refine_range, rank.data(), unrank.data());
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     e = cudaMemsetAsync(l->d_status, 0, sizeof(int), s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(l->d_tiles, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice, s);
-    std::vector<uint16_t> rank(static_cast<size_t>(Kr) * Kr), unrank(rank.size());
-    refine_rank_tables(geometry->dep_refine_range, rank.data(), unrank.data());
     if (e == cudaSuccess) e = cudaMemcpyAsync(l->d_rank, rank.data(), rank.size() * 2, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(l->d_unrank, unrank.data(), unrank.size() * 2, cudaMemcpyHostToDevice, s);
@@ -424,7 +489,8 @@ ladder_status analyze_independent(ladder_t *l, int rung, int frame_id, const voi
     if (st != LADDER_OK) return st;
     Slot *slot = claim_slot(l, frame_id);
     if (!slot) return fail(l, LADDER_E_BUSY, "no free frame slot for frame %d", frame_id);
-    st = run_independent(l, slot, rung, cur, ref, pitch_bytes, qp, static_cast<cudaStream_t>(cuda_stream));
+    Job job{slot, rung, cur, ref, pitch_bytes, qp};
+    st = launch_independent(l, &job, 1, static_cast<cudaStream_t>(cuda_stream));
     if (st == LADDER_OK && rung == l->geo.ref_rung) slot->ref_done = 1;
     return st;
 }
@@ -440,8 +506,8 @@ ladder_status analyze_dependents(ladder_t *l, int frame_id, int n, const int *ru
                                  const void *const *ref, const long *pitch_bytes, int qp, void *cuda_stream)
 {
     if (!l) return LADDER_E_INVAL;
-    if (n < 1 || n > kMaxBatch || !rungs || !cur || !ref || !pitch_bytes)
-        return fail(l, LADDER_E_INVAL, "dependent batch of %d rungs (1..%d)", n, kMaxBatch);
+    if (n < 1 || n > kMaxRungs || !rungs || !cur || !ref || !pitch_bytes)
+        return fail(l, LADDER_E_INVAL, "dependent batch of %d rungs (1..%d)", n, kMaxRungs);
     for (int k = 0; k < n; ++k) {
         ladder_status st = check_planes(l, rungs[k], cur[k], ref[k], pitch_bytes[k], qp);
         if (st != LADDER_OK) return st;
@@ -452,44 +518,9 @@ ladder_status analyze_dependents(ladder_t *l, int frame_id, int n, const int *ru
     Slot *slot = find_slot(l, frame_id);
     if (!slot || !slot->ref_done)
         return fail(l, LADDER_E_NOREF, "frame %d has no reference analysis", frame_id);
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    const RungGeom &gr = l->rg[l->geo.ref_rung];
-    const RungBuffers &ref_rb = slot->rungs[l->geo.ref_rung];
-    DependentBatch batch{};
-    batch.n = n;
-    batch.cta_begin[0] = 0;
-    for (int k = 0; k < n; ++k) {
-        const RungGeom &g = l->rg[rungs[k]];
-        DependentArgs &da = batch.rung[k];
-        da.cur = cur[k];
-        da.ref = ref[k];
-        da.pitch_bytes = pitch_bytes[k];
-        da.g = g;
-        da.r = l->geo.dep_refine_range;
-        da.rank = l->d_rank;
-        da.unrank = l->d_unrank;
-        da.rank_bits = l->rank_bits;
-        da.refs.Wr = gr.W;
-        da.refs.Hr = gr.H;
-        da.refs.cols8_r = gr.cols8;
-        da.refs.leaf_depth = ref_rb.dec.leaf_depth;
-        da.refs.leaf_mvx = ref_rb.dec.leaf_mvx;
-        da.refs.leaf_mvy = ref_rb.dec.leaf_mvy;
-        da.refs.depth_lo = l->geo.dep_depth_lo;
-        da.refs.depth_hi = l->geo.dep_depth_hi;
-        da.refs.use_ref_mv = l->geo.dep_use_ref_mv;
-        da.qp = qp;
-        da.satd_mode = l->geo.satd_mode;
-        da.out = slot->rungs[rungs[k]].dec;
-        da.status = l->d_status;
-        batch.cta_begin[k + 1] = batch.cta_begin[k] + g.ctu_cols * g.ctu_rows;
-    }
-    cudaError_t e = traced(l, 2, s, [&] {
-        return launch_dependent(l->geo.bit_depth, l->geo.ctu_size, l->geo.dep_refine_range, batch, s);
-    });
-    if (e != cudaSuccess) return cuda_fail(l, e, "dependent launch");
-    for (int k = 0; k < n; ++k) slot->rungs[rungs[k]].analysed = 2;
-    return LADDER_OK;
+    std::vector<Job> jobs;
+    for (int k = 0; k < n; ++k) jobs.push_back(Job{slot, rungs[k], cur[k], ref[k], pitch_bytes[k], qp});
+    return launch_dependents(l, jobs.data(), n, static_cast<cudaStream_t>(cuda_stream));
 }
 
 ladder_status analyze_dependent(ladder_t *l, int rung, int frame_id, const void *cur, const void *ref,
@@ -498,10 +529,148 @@ ladder_status analyze_dependent(ladder_t *l, int rung, int frame_id, const void 
     return analyze_dependents(l, frame_id, 1, &rung, &cur, &ref, &pitch_bytes, qp, cuda_stream);
 }
 
+ladder_status ladder_analyze_batch(ladder_t *l, const ladder_request *reqs, int n, void *cuda_stream)
+{
+    if (!l) return LADDER_E_INVAL;
+    const int nd = l->geo.n_rungs - 1;
+    if (!reqs || n < 1 || n > kMaxItems || n * nd > kMaxDepItems)
+        return fail(l, LADDER_E_INVAL, "batch of %d frames (1..%d, and frames x dependent rungs <= %d)", n,
+                    kMaxItems, kMaxDepItems);
+    for (int k = 0; k < n; ++k) {
+        if (!reqs[k].cur || !reqs[k].ref || !reqs[k].pitch_bytes)
+            return fail(l, LADDER_E_INVAL, "request %d has null plane arrays", k);
+        for (int r = 0; r < l->geo.n_rungs; ++r) {
+            ladder_status st =
+                check_planes(l, r, reqs[k].cur[r], reqs[k].ref[r], reqs[k].pitch_bytes[r], reqs[k].qp);
+            if (st != LADDER_OK) return st;
+        }
+        for (int j = 0; j < k; ++j)
+            if (reqs[j].frame_id == reqs[k].frame_id)
+                return fail(l, LADDER_E_INVAL, "frame %d appears twice in the batch", reqs[k].frame_id);
+    }
+    int free_slots = 0, needed = 0;
+    for (auto &sl : l->slots) free_slots += !sl.used;
+    for (int k = 0; k < n; ++k) needed += find_slot(l, reqs[k].frame_id) == nullptr;
+    if (needed > free_slots)
+        return fail(l, LADDER_E_BUSY, "batch needs %d free frame slots, %d free", needed, free_slots);
+    std::vector<Slot *> slots(n);
+    for (int k = 0; k < n; ++k) slots[k] = claim_slot(l, reqs[k].frame_id);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int rr = l->geo.ref_rung;
+    std::vector<Job> ij, dj;
+    for (int k = 0; k < n; ++k) {
+        ij.push_back(Job{slots[k], rr, reqs[k].cur[rr], reqs[k].ref[rr], reqs[k].pitch_bytes[rr], reqs[k].qp});
+        for (int r = 0; r < l->geo.n_rungs; ++r)
+            if (r != rr)
+                dj.push_back(Job{slots[k], r, reqs[k].cur[r], reqs[k].ref[r], reqs[k].pitch_bytes[r], reqs[k].qp});
+    }
+    ladder_status st = launch_independent(l, ij.data(), n, s);
+    if (st != LADDER_OK) return st;
+    for (int k = 0; k < n; ++k) slots[k]->ref_done = 1;
+    if (!dj.empty()) st = launch_dependents(l, dj.data(), static_cast<int>(dj.size()), s);
+    return st;
+}
+
+ladder_status ladder_analyze_batch_independent(ladder_t *l, const ladder_request *reqs, int n, void *cuda_stream)
+{
+    if (!l) return LADDER_E_INVAL;
+    if (!reqs || n < 1 || n > kMaxItems) return fail(l, LADDER_E_INVAL, "batch of %d frames (1..%d)", n, kMaxItems);
+    for (int k = 0; k < n; ++k) {
+        if (!reqs[k].cur || !reqs[k].ref || !reqs[k].pitch_bytes)
+            return fail(l, LADDER_E_INVAL, "request %d has null plane arrays", k);
+        for (int r = 0; r < l->geo.n_rungs; ++r) {
+            ladder_status st =
+                check_planes(l, r, reqs[k].cur[r], reqs[k].ref[r], reqs[k].pitch_bytes[r], reqs[k].qp);
+            if (st != LADDER_OK) return st;
+        }
+        for (int j = 0; j < k; ++j)
+            if (reqs[j].frame_id == reqs[k].frame_id)
+                return fail(l, LADDER_E_INVAL, "frame %d appears twice in the batch", reqs[k].frame_id);
+    }
+    int free_slots = 0, needed = 0;
+    for (auto &sl : l->slots) free_slots += !sl.used;
+    for (int k = 0; k < n; ++k) needed += find_slot(l, reqs[k].frame_id) == nullptr;
+    if (needed > free_slots)
+        return fail(l, LADDER_E_BUSY, "batch needs %d free frame slots, %d free", needed, free_slots);
+    std::vector<Job> jobs;
+    std::vector<Slot *> slots(n);
+    for (int k = 0; k < n; ++k) {
+        slots[k] = claim_slot(l, reqs[k].frame_id);
+        for (int r = 0; r < l->geo.n_rungs; ++r)
+            jobs.push_back(Job{slots[k], r, reqs[k].cur[r], reqs[k].ref[r], reqs[k].pitch_bytes[r], reqs[k].qp});
+    }
+    ladder_status st = launch_independent(l, jobs.data(), static_cast<int>(jobs.size()),
+                                          static_cast<cudaStream_t>(cuda_stream));
+    if (st == LADDER_OK)
+        for (int k = 0; k < n; ++k) slots[k]->ref_done = 1;
+    return st;
+}
+
+ladder_status ladder_capture_batch(ladder_t *l, const ladder_request *reqs, int n, void *cuda_stream,
+                                   ladder_graph_t **out)
+{
+    if (!l || !out) return LADDER_E_INVAL;
+    *out = nullptr;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (!s) return fail(l, LADDER_E_INVAL, "capture needs a non-default stream");
+    const int prof = l->prof_on;
+    l->prof_on = 0;  // no event records inside the graph
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        l->prof_on = prof;
+        return cuda_fail(l, e, "begin capture");
+    }
+    ladder_status st = ladder_analyze_batch(l, reqs, n, cuda_stream);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(s, &graph);
+    l->prof_on = prof;
+    if (st != LADDER_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(l, e, "end capture");
+    ladder_graph_t *g = new (std::nothrow) ladder_graph();
+    if (!g) {
+        cudaGraphDestroy(graph);
+        return LADDER_E_NOMEM;
+    }
+    g->graph = graph;
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        delete g;
+        return cuda_fail(l, e, "graph instantiate");
+    }
+    *out = g;
+    return LADDER_OK;
+}
+
+ladder_status ladder_graph_launch(ladder_graph_t *g, void *cuda_stream)
+{
+    if (!g || !g->exec) return LADDER_E_INVAL;
+    return cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess ? LADDER_OK
+                                                                                          : LADDER_E_CUDA;
+}
+
+void ladder_graph_destroy(ladder_graph_t *g)
+{
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}
+
+ladder_status ladder_set_tiles_per_slice(ladder_t *l, int tiles_per_slice)
+{
+    if (!l || tiles_per_slice < 0) return LADDER_E_INVAL;
+    l->fs_tps_override = tiles_per_slice;
+    return LADDER_OK;
+}
+
 ladder_status ladder_grid(const ladder_t *l, int rung, int *dims, int *n_depths)
 {
     if (!l || !dims || rung < 0 || rung >= l->geo.n_rungs) return LADDER_E_INVAL;
-    const RungGeom &g = l->rg[rung];
+    const RungGeom &g = l->info[rung].g;
     for (int d = 0; d <= g.dmax; ++d) {
         dims[2 * d] = g.cols[d];
         dims[2 * d + 1] = g.rows[d];
@@ -535,33 +704,34 @@ ladder_status fetch_decisions(ladder_t *l, int rung, int frame_id, ladder_decisi
     Slot *slot = find_slot(l, frame_id);
     if (!slot || !slot->rungs[rung].analysed)
         return fail(l, LADDER_E_STATE, "rung %d of frame %d has not been analysed", rung, frame_id);
-    const RungGeom &g = l->rg[rung];
-    const RungBuffers &rb = slot->rungs[rung];
-    const DevDecisions &dec = rb.dec;
+    const RungGeom &g = l->info[rung].g;
+    const DecOffsets &o = l->info[rung].off;
+    const char *block = slot->rungs[rung].block;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     // one copy of the rung's whole decision block into pinned memory, then
     // host copies into the caller's arrays
-    cudaError_t e = cudaMemcpyAsync(l->host_stage, rb.dec_base, rb.dec_bytes, cudaMemcpyDeviceToHost, s);
+    cudaError_t e =
+        cudaMemcpyAsync(l->host_stage, block, static_cast<size_t>(o.dec_bytes), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(l, e, "fetch copy");
-    auto copy = [&](void *dst, const void *src, size_t bytes) {
-        if (dst) memcpy(dst, l->host_stage + (static_cast<const char *>(src) - rb.dec_base), bytes);
+    auto copy = [&](void *dst, long off, size_t bytes) {
+        if (dst) memcpy(dst, l->host_stage + off, bytes);
     };
     for (int d = 0; d <= g.dmax; ++d) {
         const size_t n = static_cast<size_t>(g.cols[d]) * g.rows[d];
-        copy(out->mvx[d], dec.mvx[d], n * 2);
-        copy(out->mvy[d], dec.mvy[d], n * 2);
-        copy(out->sad[d], dec.sad[d], n * 4);
-        copy(out->satd[d], dec.satd[d], n * 4);
-        copy(out->cost[d], dec.cost[d], n * 4);
-        copy(out->best[d], dec.best[d], n * 4);
-        copy(out->split[d], dec.split[d], n);
-        copy(out->evaluated[d], dec.evaluated[d], n);
+        copy(out->mvx[d], o.mvx[d], n * 2);
+        copy(out->mvy[d], o.mvy[d], n * 2);
+        copy(out->sad[d], o.sad[d], n * 4);
+        copy(out->satd[d], o.satd[d], n * 4);
+        copy(out->cost[d], o.cost[d], n * 4);
+        copy(out->best[d], o.best[d], n * 4);
+        copy(out->split[d], o.split[d], n);
+        copy(out->evaluated[d], o.evaluated[d], n);
     }
     const size_t n8 = static_cast<size_t>(g.cols8) * g.rows8;
-    copy(out->leaf_depth, dec.leaf_depth, n8);
-    copy(out->leaf_mvx, dec.leaf_mvx, n8 * 2);
-    copy(out->leaf_mvy, dec.leaf_mvy, n8 * 2);
+    copy(out->leaf_depth, o.leaf_depth, n8);
+    copy(out->leaf_mvx, o.leaf_mvx, n8 * 2);
+    copy(out->leaf_mvy, o.leaf_mvy, n8 * 2);
     return ladder_sync(l, cuda_stream);
 }
 
@@ -595,6 +765,8 @@ ladder_status ladder_profile_read(ladder_t *l, int kind, long *launches, double 
     }
     return LADDER_OK;
 }
+
+long ladder_device_bytes(const ladder_t *l) { return l ? static_cast<long>(l->arena_bytes) : 0; }
 
 void ladder_destroy(ladder_t *l)
 {

@@ -49,18 +49,66 @@ struct DevDecisions {
     int16_t *leaf_mvx, *leaf_mvy;
 };
 
+// Byte offsets of the decision arrays (and the per-CTU argmin keys) inside
+// one (frame slot, rung) block; the same for every slot of a rung.
+struct DecOffsets {
+    long mvx[kMaxDepths], mvy[kMaxDepths], sad[kMaxDepths], satd[kMaxDepths], cost[kMaxDepths], best[kMaxDepths];
+    long split[kMaxDepths], evaluated[kMaxDepths];
+    long leaf_depth, leaf_mvx, leaf_mvy;
+    long keys;
+    long dec_bytes;  // the decision arrays span [0, dec_bytes)
+};
+
+struct RungInfo {
+    RungGeom g;
+    DecOffsets off;
+};
+
+__host__ __device__ inline DevDecisions decisions_at(char *base, const DecOffsets &o)
+{
+    DevDecisions d{};
+    for (int k = 0; k < kMaxDepths; ++k) {
+        d.mvx[k] = reinterpret_cast<int16_t *>(base + o.mvx[k]);
+        d.mvy[k] = reinterpret_cast<int16_t *>(base + o.mvy[k]);
+        d.sad[k] = reinterpret_cast<int32_t *>(base + o.sad[k]);
+        d.satd[k] = reinterpret_cast<int32_t *>(base + o.satd[k]);
+        d.cost[k] = reinterpret_cast<int32_t *>(base + o.cost[k]);
+        d.best[k] = reinterpret_cast<int32_t *>(base + o.best[k]);
+        d.split[k] = reinterpret_cast<uint8_t *>(base + o.split[k]);
+        d.evaluated[k] = reinterpret_cast<uint8_t *>(base + o.evaluated[k]);
+    }
+    d.leaf_depth = reinterpret_cast<uint8_t *>(base + o.leaf_depth);
+    d.leaf_mvx = reinterpret_cast<int16_t *>(base + o.leaf_mvx);
+    d.leaf_mvy = reinterpret_cast<int16_t *>(base + o.leaf_mvy);
+    return d;
+}
+
+constexpr int kMaxRungs = 16;
+constexpr int kMaxItems = 64;                    // frames per batched launch
+constexpr int kMaxDepItems = kMaxItems * 3;      // dependent (frame, rung) pairs per batched launch
+
 // ---- full search (independent analysis) --------------------------------
-struct FullSearchArgs {
+// One item = one frame's independently analysed rung.  The grid is
+// (candidate slices) x (sum of the items' CTUs); kernel parameters are
+// grid-constant (CUDA 12.1+ allows 32 KB), the tensor maps included.
+struct FullSearchItem {
     const void *cur;      // W x H plane, pitch bytes below
     long pitch_bytes;
     int W, H;
+    unsigned long long *keys;  // per CTU keys_per_ctu(dmax), initialised to ~0
+    int cta_begin;        // first grid.y row of this item
+};
+
+struct FullSearchBatch {
+    int n;
     int R;                // search range
     int Rp;               // left/right window margin: R rounded up to 16 samples
     int ntiles;           // candidate tiles of the search square
     int tiles_per_slice;  // tiles handled by one CTA
     const int *tiles;     // packed (dx_base & 0xffff) | (dy_base << 16)
-    unsigned long long *keys;  // per CTU keys_per_ctu(dmax), initialised to ~0
     int *status;
+    FullSearchItem item[kMaxItems];
+    CUtensorMap map[kMaxItems];  // reference plane of each item
 };
 
 struct FullSearchPlan {
@@ -78,10 +126,31 @@ FullSearchPlan full_search_plan(int bit_depth, int ctu, int R);
 int full_search_ctas_per_sm(int bit_depth, int ctu, int R);
 // Builds the candidate tile list for range R (host); returns the count.
 int full_search_tiles(int bit_depth, int R, int *out, int cap);
-cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchArgs &a, const CUtensorMap &ref_map,
-                               int nslices, int nctus, cudaStream_t s);
+// grid = (nslices, total CTUs of the batch)
+cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchBatch &b, int nslices, int total_ctus,
+                               cudaStream_t s);
 
-// ---- dependent analysis (one fused kernel per rung) ------------------------
+// ---- decision step of independently analysed rungs -------------------------
+struct DecideItem {
+    const void *cur, *ref;
+    long pitch_bytes;
+    char *block;          // the (slot, rung) block: decisions + keys
+    int rung;
+    int qp;
+    int cta_begin;        // first CTA of this item (one CTA per CTU)
+};
+
+struct DecideBatch {
+    int n;
+    int range;            // R: decodes the keys
+    int satd_mode;
+    int total_ctas;
+    RungInfo rung[kMaxRungs];
+    DecideItem item[kMaxItems];
+};
+cudaError_t launch_decide(int bit_depth, int ctu, const DecideBatch &b, cudaStream_t s);
+
+// ---- dependent analysis (one fused kernel for many rungs / frames) ---------
 // Reference-rung state a dependent rung reads.
 struct DepRefs {
     int Wr, Hr, cols8_r;     // reference rung size and 8x8 grid width
@@ -90,47 +159,49 @@ struct DepRefs {
     int depth_lo, depth_hi, use_ref_mv;
 };
 
-struct DependentArgs {
+struct DependentItem {
     const void *cur, *ref;
     long pitch_bytes;
-    RungGeom g;
+    char *block;             // this (slot, rung) block
+    const char *ref_block;   // the frame's reference-rung block
+    int rung;
+    int qp;
+    int cta_begin;           // first CTA of this item (one CTA per CTU)
+};
+
+struct DependentBatch {
+    int n;
     int r;                  // refinement range
     const uint16_t *rank;   // (2r+1)^2: rank of candidate (dyi*K + dxi) in (|dx|+|dy|, dy, dx) order
     const uint16_t *unrank; // inverse of rank
     int rank_bits;          // ceil(log2((2r+1)^2))
-    DepRefs refs;
-    int qp, satd_mode;
-    DevDecisions out;
+    int satd_mode;
+    int ref_rung;
+    int depth_lo, depth_hi, use_ref_mv;
+    int total_ctas;
     int *status;
-};
-// Several dependent rungs analysed by one launch (kernel parameter: CUDA
-// 12.1+ allows up to 32 KB).  CTA b belongs to rung i with
-// cta_begin[i] <= b < cta_begin[i+1]; all rungs share bit depth, CTU size and r.
-constexpr int kMaxBatch = 16;
-struct DependentBatch {
-    int n;
-    int cta_begin[kMaxBatch + 1];
-    DependentArgs rung[kMaxBatch];
+    RungInfo rung[kMaxRungs];
+    DependentItem item[kMaxDepItems];
 };
 // Constraint derivation, refinement search, SATD, cost and split: one CTA per CTU.
 cudaError_t launch_dependent(int bit_depth, int ctu, int r, const DependentBatch &b, cudaStream_t s);
 // Rank / inverse tables of the refinement candidates for range r (host).
 void refine_rank_tables(int r, uint16_t *rank, uint16_t *unrank);
 
-// ---- SATD, cost, split and leaf maps -------------------------------------
-struct DecideArgs {
-    const void *cur, *ref;
-    long pitch_bytes;
-    RungGeom g;
-    int range;              // R: decodes the keys
-    const unsigned long long *keys;
-    int qp;
-    int satd_mode;
-    DevDecisions out;
+// Fills the keys of every block of a batch with ~0 (key initialisation).
+struct FillItem {
+    unsigned long long *keys;
+    long n;
 };
-cudaError_t launch_decide(int bit_depth, const DecideArgs &a, cudaStream_t s);
+struct FillBatch {
+    int n;
+    FillItem item[kMaxItems];
+};
+cudaError_t launch_fill_keys(const FillBatch &b, cudaStream_t s);
 
-// Fills n 64-bit words with ~0 (key initialisation).
-cudaError_t launch_fill_keys(unsigned long long *keys, long n, cudaStream_t s);
+// Sets the kernels' shared-memory attributes for a geometry (before any
+// stream capture).
+cudaError_t prepare_full_search(int bit_depth, int ctu, int R);
+cudaError_t prepare_kernels(int bit_depth, int ctu, int R, int r);
 
 }  // namespace ladder_impl

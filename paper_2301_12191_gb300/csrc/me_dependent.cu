@@ -196,9 +196,21 @@ template <typename T> __host__ __device__ constexpr int sad_bits(int S)
 template <typename T, int CTU, int KC, int TY>
 __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const __grid_constant__ DependentBatch b)
 {
-    int ri = 0;
-    while (ri + 1 < b.n && static_cast<int>(blockIdx.x) >= b.cta_begin[ri + 1]) ++ri;
-    const DependentArgs &a = b.rung[ri];
+    int ri = 0;  // the batch item of this CTA
+    while (ri + 1 < b.n && static_cast<int>(blockIdx.x) >= b.item[ri + 1].cta_begin) ++ri;
+    const DependentItem &a = b.item[ri];
+    const RungInfo &rinf = b.rung[a.rung];
+    const RungInfo &rref = b.rung[b.ref_rung];
+    DepRefs refs;
+    refs.Wr = rref.g.W;
+    refs.Hr = rref.g.H;
+    refs.cols8_r = rref.g.cols8;
+    refs.leaf_depth = reinterpret_cast<const uint8_t *>(a.ref_block + rref.off.leaf_depth);
+    refs.leaf_mvx = reinterpret_cast<const int16_t *>(a.ref_block + rref.off.leaf_mvx);
+    refs.leaf_mvy = reinterpret_cast<const int16_t *>(a.ref_block + rref.off.leaf_mvy);
+    refs.depth_lo = b.depth_lo;
+    refs.depth_hi = b.depth_hi;
+    refs.use_ref_mv = b.use_ref_mv;
     using C = dev::Ctu<CTU>;
     constexpr int NT = kDepThreads, NWARP = NT / 32;
     constexpr int NCAND = TY * KC;
@@ -213,14 +225,14 @@ __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const __grid_const
     __shared__ int s_wpre[C::DMAX + 2];   // warp-job prefix per depth
     extern __shared__ uint32_t s_dyn[];   // 64x64 CU sums, then rank / unrank tables
     uint32_t *const s_sum = s_dyn;
-    uint16_t *const s_rank = reinterpret_cast<uint16_t *>(s_dyn + (2 * a.r + 1) * (2 * a.r + 1));
-    uint16_t *const s_unrank = s_rank + (2 * a.r + 1) * (2 * a.r + 1);
+    uint16_t *const s_rank = reinterpret_cast<uint16_t *>(s_dyn + (2 * b.r + 1) * (2 * b.r + 1));
+    uint16_t *const s_unrank = s_rank + (2 * b.r + 1) * (2 * b.r + 1);
 
-    const RungGeom &g = a.g;
+    const RungGeom &g = rinf.g;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ctu_idx = blockIdx.x - b.cta_begin[ri];
+    const int ctu_idx = blockIdx.x - a.cta_begin;
     const int x0 = (ctu_idx % g.ctu_cols) * CTU, y0 = (ctu_idx / g.ctu_cols) * CTU;
-    const int r = a.r, K = 2 * r + 1, KK = K * K;
+    const int r = b.r, K = 2 * r + 1, KK = K * K;
     const char *cb = static_cast<const char *>(a.cur);
     const char *rb = static_cast<const char *>(a.ref);
 
@@ -235,7 +247,7 @@ __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const __grid_const
         int16_t cx = 0, cy = 0;
         if (present) {
             const bool inside = cu_x + S <= g.W8 && cu_y + S <= g.H8;
-            const dev::Rule ru = dev::derive_rule(g, a.refs, d, cu_x, cu_y);
+            const dev::Rule ru = dev::derive_rule(g, refs, d, cu_x, cu_y);
             cx = static_cast<int16_t>(ru.cx);
             cy = static_cast<int16_t>(ru.cy);
             leaf = inside && ru.allowed_leaf;
@@ -251,8 +263,8 @@ __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const __grid_const
     if (tid <= C::DMAX) s_cnt[tid] = 0;
     for (int x = tid; x < KK; x += NT) {
         s_sum[x] = 0;
-        s_rank[x] = a.rank[x];
-        s_unrank[x] = a.unrank[x];
+        s_rank[x] = b.rank[x];
+        s_unrank[x] = b.unrank[x];
     }
     __syncthreads();
 
@@ -329,12 +341,12 @@ __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const __grid_const
                                    by + s_cy[i] - r + ty * TY, t);
         if (nblk == 1) {
             const unsigned long long best =
-                held_best<TY, KC, NCAND, NCAND, sad_bits<T>(8)>(t, 0, ty, dc, K, s_rank, a.rank_bits);
+                held_best<TY, KC, NCAND, NCAND, sad_bits<T>(8)>(t, 0, ty, dc, K, s_rank, b.rank_bits);
             if (valid) atomicMin(&s_key[i], best);
         } else if (nblk == 4) {
             const int off = scatter_tables<NCAND, NCP, 2>(t, lane);
             unsigned long long best =
-                held_best<TY, KC, NCAND, NCP / 4, sad_bits<T>(16)>(t, off, ty, dc, K, s_rank, a.rank_bits);
+                held_best<TY, KC, NCAND, NCP / 4, sad_bits<T>(16)>(t, off, ty, dc, K, s_rank, b.rank_bits);
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
                 const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, 1 << b);
@@ -344,7 +356,7 @@ __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const __grid_const
         } else if (nblk == 16) {
             const int off = scatter_tables<NCAND, NCP, 4>(t, lane);
             unsigned long long best =
-                held_best<TY, KC, NCAND, NCP / 16, sad_bits<T>(32)>(t, off, ty, dc, K, s_rank, a.rank_bits);
+                held_best<TY, KC, NCAND, NCP / 16, sad_bits<T>(32)>(t, off, ty, dc, K, s_rank, b.rank_bits);
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, 1 << b);
@@ -388,8 +400,25 @@ __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const __grid_const
     __syncthreads();
 
     // 4. SATD, cost, split, leaf maps
-    dev::DecideIO io{a.cur, a.ref, a.pitch_bytes, &a.g, a.qp, a.satd_mode, c_lambda_q16, a.out};
+    dev::DecideIO io{a.cur, a.ref, a.pitch_bytes, &rinf.g, a.qp, b.satd_mode, c_lambda_q16,
+                     decisions_at(a.block, rinf.off)};
     dev::ctu_decide<T, CTU>(st, io, x0, y0);
+}
+
+template <typename T, int CTU, int KC, int TY> cudaError_t ensure_attr()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_dependent<T, CTU, KC, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         65 * 65 * 8);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+template <typename T, int CTU> cudaError_t prepare_dependent_t(int r)
+{
+    if (2 * r + 1 <= 9) return ensure_attr<T, CTU, 9, sizeof(T) == 1 ? 5 : 3>();
+    return ensure_attr<T, CTU, 17, sizeof(T) == 1 ? 2 : 1>();
 }
 
 template <typename T, int CTU, int KC, int TY>
@@ -398,13 +427,9 @@ cudaError_t dependent_t(int r, const DependentBatch &b, cudaStream_t s)
     const int K = 2 * r + 1;
     const int smem = K * K * 8;
     auto kern = k_dependent<T, CTU, KC, TY>;
-    static int configured = 0;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 65 * 65 * 8);
-        if (e != cudaSuccess) return e;
-        configured = 1;
-    }
-    kern<<<b.cta_begin[b.n], kDepThreads, smem, s>>>(b);
+    cudaError_t e = ensure_attr<T, CTU, KC, TY>();
+    if (e != cudaSuccess) return e;
+    kern<<<b.total_ctas, kDepThreads, smem, s>>>(b);
     return cudaGetLastError();
 }
 
@@ -436,9 +461,20 @@ void refine_rank_tables(int r, uint16_t *rank, uint16_t *unrank)
     }
 }
 
+cudaError_t prepare_kernels(int bit_depth, int ctu, int R, int r)
+{
+    cudaError_t e = prepare_full_search(bit_depth, ctu, R);
+    if (e != cudaSuccess) return e;
+    if (bit_depth == 8)
+        return ctu == 64 ? prepare_dependent_t<uint8_t, 64>(r)
+                         : (ctu == 32 ? prepare_dependent_t<uint8_t, 32>(r) : prepare_dependent_t<uint8_t, 16>(r));
+    return ctu == 64 ? prepare_dependent_t<uint16_t, 64>(r)
+                     : (ctu == 32 ? prepare_dependent_t<uint16_t, 32>(r) : prepare_dependent_t<uint16_t, 16>(r));
+}
+
 cudaError_t launch_dependent(int bit_depth, int ctu, int r, const DependentBatch &b, cudaStream_t s)
 {
-    if (b.n < 1 || b.n > kMaxBatch || b.cta_begin[b.n] <= 0) return cudaErrorInvalidValue;
+    if (b.n < 1 || b.n > kMaxDepItems || b.total_ctas <= 0) return cudaErrorInvalidValue;
     if (bit_depth == 8) {
         if (ctu == 64) return dependent_ctu<uint8_t, 64>(r, b, s);
         if (ctu == 32) return dependent_ctu<uint8_t, 32>(r, b, s);

@@ -157,8 +157,7 @@ __device__ __forceinline__ int copy_off(int row, int w, int pw) { return row * p
 
 template <typename T, int CTU, int TY, int NX>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 1 ? 2 : 1)
-    k_full_search(const __grid_constant__ CUtensorMap ref_map, const FullSearchArgs a, const int box_h,
-                  const int pw, const int cstride)
+    k_full_search(const __grid_constant__ FullSearchBatch b, const int box_h, const int pw, const int cstride)
 {
     constexpr int SPW = Traits<T>::SPW;
     constexpr int UW = 4 * SPW;                 // unit width in samples
@@ -187,27 +186,37 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 1 ? 2 : 1)
     uint32_t *const copies = stage + box_h * pw;
     __shared__ __align__(8) uint64_t bar;
     __shared__ unsigned long long cta_keys[NKEY];
+    __shared__ unsigned long long *s_out_keys;  // this CTU's global keys (read after the main loop)
+    // 8-bit: running best keys live in shared memory ([slot][thread], conflict-free)
+    // to keep the main loop within 128 registers
+    constexpr bool kSmemBest = SPW == 4;
+    __shared__ unsigned long long s_best[kSmemBest ? NB + DMAX : 1][kSmemBest ? kThreads : 1];
 
+    int ii = 0;  // the batch item of this CTA row
+    while (ii + 1 < b.n && static_cast<int>(blockIdx.y) >= b.item[ii + 1].cta_begin) ++ii;
+    const FullSearchItem &a = b.item[ii];
+    const CUtensorMap *ref_map = &b.map[ii];
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int u = lane % NU;
     const int g = lane / NU;
-    const int ctu_idx = blockIdx.y;
+    const int ctu_idx = blockIdx.y - a.cta_begin;
     const int W8 = (a.W + 7) & ~7;
     const int ctu_cols = (W8 + CTU - 1) / CTU;
     const int x0 = (ctu_idx % ctu_cols) * CTU;
     const int y0 = (ctu_idx / ctu_cols) * CTU;
-    const int R = a.R, K = 2 * R + 1;
+    const int R = b.R, K = 2 * R + 1;
 
     if (tid == 0) {
         mbar_init(&bar, 1);
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ref_map)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(ref_map)) : "memory");
     }
     for (int i = tid; i < NKEY; i += kThreads) cta_keys[i] = ~0ull;
+    if (tid == 0) s_out_keys = a.keys + static_cast<long>(ctu_idx) * NKEY;
     __syncthreads();
     if (tid == 0) {
         mbar_arrive_expect_tx(&bar, static_cast<uint32_t>(box_h * pw) * 4u);
-        tma_load_2d(stage, &ref_map, &bar, x0 - a.Rp, y0 - R);
+        tma_load_2d(stage, ref_map, &bar, x0 - b.Rp, y0 - R);
     }
 
     // Current unit -> registers while the window is in flight.
@@ -246,22 +255,22 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 1 ? 2 : 1)
 
     // Tiles of this slice; tiles are ordered by candidate row, so the slice
     // needs window rows [r_lo, r_hi) only.
-    const int tile_begin = blockIdx.x * a.tiles_per_slice;
-    const int tile_end = min(tile_begin + a.tiles_per_slice, a.ntiles);
+    const int tile_begin = blockIdx.x * b.tiles_per_slice;
+    const int tile_end = min(tile_begin + b.tiles_per_slice, b.ntiles);
     const int n_iter = (tile_end - tile_begin + NG - 1) / NG;  // uniform across the CTA
-    const int r_lo = (__ldg(a.tiles + tile_begin) >> 16) + R;
-    const int r_hi = min(box_h, (__ldg(a.tiles + tile_end - 1) >> 16) + R + TY - 1 + CTU);
+    const int r_lo = (__ldg(b.tiles + tile_begin) >> 16) + R;
+    const int r_hi = min(box_h, (__ldg(b.tiles + tile_end - 1) >> 16) + R + TY - 1 + CTU);
 
     const bool ok = mbar_wait_bounded(&bar, 0);
     if (__syncthreads_or(!ok)) {
-        if (tid == 0) atomicExch(a.status, kStatusTimeout);
+        if (tid == 0) atomicExch(b.status, kStatusTimeout);
         if (!ok) mbar_wait_bounded(&bar, 0);
         return;
     }
 
     // Out-of-frame samples of the window take the clamped sample.
     {
-        const int gx0 = x0 - a.Rp, gy0 = y0 - R;
+        const int gx0 = x0 - b.Rp, gy0 = y0 - R;
         const int ww = pw * SPW;
         if (gx0 < 0 || gy0 < 0 || gx0 + ww > a.W || gy0 + box_h > a.H) {
             T *w0 = reinterpret_cast<T *>(stage);
@@ -288,22 +297,26 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 1 ? 2 : 1)
     __syncthreads();
 
     // Running bests: 8x8 blocks of the unit, then one per coarser depth.
-    unsigned long long best_blk[NB];
-    unsigned long long best_lv[DMAX];
+    unsigned long long rbest[kSmemBest ? 1 : NB + DMAX];
 #pragma unroll
-    for (int b = 0; b < NB; ++b) best_blk[b] = ~0ull;
-#pragma unroll
-    for (int d = 0; d < DMAX; ++d) best_lv[d] = ~0ull;
+    for (int q = 0; q < NB + DMAX; ++q) {
+        if constexpr (kSmemBest) s_best[q][tid] = ~0ull;
+        else rbest[q] = ~0ull;
+    }
+    auto best_ref = [&](int q) -> unsigned long long & {
+        if constexpr (kSmemBest) return s_best[q][tid];
+        else return rbest[q];
+    };
 
     for (int it = 0; it < n_iter; ++it) {
         // the G groups of a warp take G consecutive tiles (paired word classes)
         int t = tile_begin + G * (warp + (kThreads / 32) * it) + g;
         if (t >= tile_end) t = tile_begin;  // a duplicate tile cannot change a min
-        const int packed = __ldg(a.tiles + t);
+        const int packed = __ldg(b.tiles + t);
         const int dxb = static_cast<int>(static_cast<short>(packed & 0xffff));
         const int dyb = packed >> 16;
         const int k = dxb & (SPW - 1);
-        const uint32_t *cp = copies + k * cstride + (ux + dxb + a.Rp - k) / SPW;
+        const uint32_t *cp = copies + k * cstride + (ux + dxb + b.Rp - k) / SPW;
         const int row0 = uy + dyb + R;
 
         uint32_t acc[NB][NC];
@@ -352,7 +365,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 1 ? 2 : 1)
                 const uint32_t kk = (acc[b][c] << KS) | code[c];
                 kmin = kk < kmin ? kk : kmin;
             }
-            fold_key32<SPW, NX, KS, LNC>(best_blk[b], kmin, dxb, dyb, R, K);
+            fold_key32<SPW, NX, KS, LNC>(best_ref(b), kmin, dxb, dyb, R, K);
         }
 
         // unit sums
@@ -367,10 +380,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 1 ? 2 : 1)
         int off = 0;
         // depth DMAX-1 (16x16)
         if constexpr (B0 == 0) {
-            level_argmin<SPW, NX, NC, NC, KS, LNC>(best_lv[DMAX - 1], s, code, off, dxb, dyb, R, K);
+            level_argmin<SPW, NX, NC, NC, KS, LNC>(best_ref(NB + DMAX - 1), s, code, off, dxb, dyb, R, K);
         } else {
             scatter_step<NC, NC>(s, off, lane, 0);
-            level_argmin<SPW, NX, NC, after_step<NC>(), KS, LNC>(best_lv[DMAX - 1], s, code, off, dxb, dyb, R, K);
+            level_argmin<SPW, NX, NC, after_step<NC>(), KS, LNC>(best_ref(NB + DMAX - 1), s, code, off, dxb, dyb, R,
+                                                                 K);
         }
         // depth DMAX-2 (32x32)
         if constexpr (DMAX >= 2) {
@@ -379,14 +393,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 1 ? 2 : 1)
             constexpr int C2 = after_step<C1>();
             scatter_step<NC, C0>(s, off, lane, B0);
             scatter_step<NC, C1>(s, off, lane, B0 + 1);
-            level_argmin<SPW, NX, NC, C2, KS, LNC>(best_lv[DMAX - 2], s, code, off, dxb, dyb, R, K);
+            level_argmin<SPW, NX, NC, C2, KS, LNC>(best_ref(NB + DMAX - 2), s, code, off, dxb, dyb, R, K);
             // depth DMAX-3 (64x64)
             if constexpr (DMAX >= 3) {
                 constexpr int C3 = after_step<C2>();
                 constexpr int C4 = after_step<C3>();
                 scatter_step<NC, C2>(s, off, lane, B0 + 2);
                 scatter_step<NC, C3>(s, off, lane, B0 + 3);
-                level_argmin<SPW, NX, NC, C4, KS, LNC>(best_lv[DMAX - 3], s, code, off, dxb, dyb, R, K);
+                level_argmin<SPW, NX, NC, C4, KS, LNC>(best_ref(NB + DMAX - 3), s, code, off, dxb, dyb, R, K);
             }
         }
     }
@@ -399,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 1 ? 2 : 1)
     constexpr unsigned GROUP_BITS = 0x1fu & ~((1u << LNU) - 1u);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        const unsigned long long v = warp_min_over(best_blk[b], GROUP_BITS);
+        const unsigned long long v = warp_min_over(best_ref(b), GROUP_BITS);
         if ((lane & GROUP_BITS) == 0) {
             const int bx = ux + 8 * (b % NBH), by = uy + 8 * (b / NBH);
             const int li = (by / 8) * (CTU / 8) + bx / 8;
@@ -411,7 +425,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 1 ? 2 : 1)
         // unit bits inside a depth-d CU: 8-bit 2*(DMAX-1-d), 10-bit 2*(DMAX-1-d)+1
         const int inner = 2 * (DMAX - 1 - d) + B0;
         const unsigned m = GROUP_BITS | ((1u << inner) - 1u);
-        const unsigned long long v = warp_min_over(best_lv[d], m);
+        const unsigned long long v = warp_min_over(best_ref(NB + d), m);
         if ((lane & m) == 0) {
             const int S = CTU >> d;
             const int li = (uy / S) * (CTU / S) + ux / S;
@@ -421,26 +435,37 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 1 ? 2 : 1)
     __syncthreads();
     for (int i = tid; i < NKEY; i += kThreads) {
         const unsigned long long v = cta_keys[i];
-        if (v != ~0ull) atomicMin(a.keys + static_cast<long>(ctu_idx) * NKEY + i, v);
+        if (v != ~0ull) atomicMin(s_out_keys + i, v);
     }
 }
 
 constexpr int kTileDY = 4;
 constexpr int kTileNX = 2;
 
+// Largest dynamic shared memory already granted to k_full_search<T, CTU>.
+template <typename T, int CTU> int &granted_smem()
+{
+    static int bytes = -1;
+    return bytes;
+}
+
+template <typename T, int CTU> cudaError_t ensure_smem(int smem)
+{
+    if (granted_smem<T, CTU>() >= smem) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_full_search<T, CTU, kTileDY, kTileNX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) granted_smem<T, CTU>() = smem;
+    return e;
+}
+
 template <typename T, int CTU>
-cudaError_t launch_t(const FullSearchArgs &a, const CUtensorMap &map, const FullSearchPlan &p, int nslices,
-                     int nctus, cudaStream_t s)
+cudaError_t launch_t(const FullSearchBatch &b, const FullSearchPlan &p, int nslices, int total_ctus, cudaStream_t s)
 {
     auto kern = k_full_search<T, CTU, kTileDY, kTileNX>;
-    static int configured = -1;
-    if (configured < p.smem_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem_bytes);
-        if (e != cudaSuccess) return e;
-        configured = p.smem_bytes;
-    }
-    dim3 grid(nslices, nctus);
-    kern<<<grid, kThreads, p.smem_bytes, s>>>(map, a, p.box_h, p.pitch_words, p.copy_stride);
+    cudaError_t e = ensure_smem<T, CTU>(p.smem_bytes);
+    if (e != cudaSuccess) return e;
+    dim3 grid(nslices, total_ctus);
+    kern<<<grid, kThreads, p.smem_bytes, s>>>(b, p.box_h, p.pitch_words, p.copy_stride);
     return cudaGetLastError();
 }
 
@@ -448,13 +473,28 @@ template <typename T, int CTU>
 int occupancy_t(int smem)
 {
     auto kern = k_full_search<T, CTU, kTileDY, kTileNX>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
+    if (ensure_smem<T, CTU>(smem) != cudaSuccess) return 1;
     int n = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kThreads, smem) != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }
 
 }  // namespace
+
+cudaError_t prepare_full_search(int bit_depth, int ctu, int R)
+{
+    const FullSearchPlan p = full_search_plan(bit_depth, ctu, R);
+    // launch_t raises the attribute on first use; doing it here keeps the
+    // attribute call out of any later stream capture
+    int n = bit_depth == 8 ? (ctu == 64 ? occupancy_t<uint8_t, 64>(p.smem_bytes)
+                                        : (ctu == 32 ? occupancy_t<uint8_t, 32>(p.smem_bytes)
+                                                     : occupancy_t<uint8_t, 16>(p.smem_bytes)))
+                           : (ctu == 64 ? occupancy_t<uint16_t, 64>(p.smem_bytes)
+                                        : (ctu == 32 ? occupancy_t<uint16_t, 32>(p.smem_bytes)
+                                                     : occupancy_t<uint16_t, 16>(p.smem_bytes)));
+    (void)n;
+    return cudaGetLastError();
+}
 
 int full_search_ctas_per_sm(int bit_depth, int ctu, int R)
 {
@@ -518,18 +558,19 @@ int full_search_tiles(int bit_depth, int R, int *out, int cap)
     return n;
 }
 
-cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchArgs &a, const CUtensorMap &ref_map,
-                               int nslices, int nctus, cudaStream_t s)
+cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchBatch &b, int nslices, int total_ctus,
+                               cudaStream_t s)
 {
-    const FullSearchPlan p = full_search_plan(bit_depth, ctu, a.R);
+    if (b.n < 1 || b.n > kMaxItems || total_ctus <= 0 || nslices <= 0) return cudaErrorInvalidValue;
+    const FullSearchPlan p = full_search_plan(bit_depth, ctu, b.R);
     if (bit_depth == 8) {
-        if (ctu == 64) return launch_t<uint8_t, 64>(a, ref_map, p, nslices, nctus, s);
-        if (ctu == 32) return launch_t<uint8_t, 32>(a, ref_map, p, nslices, nctus, s);
-        return launch_t<uint8_t, 16>(a, ref_map, p, nslices, nctus, s);
+        if (ctu == 64) return launch_t<uint8_t, 64>(b, p, nslices, total_ctus, s);
+        if (ctu == 32) return launch_t<uint8_t, 32>(b, p, nslices, total_ctus, s);
+        return launch_t<uint8_t, 16>(b, p, nslices, total_ctus, s);
     }
-    if (ctu == 64) return launch_t<uint16_t, 64>(a, ref_map, p, nslices, nctus, s);
-    if (ctu == 32) return launch_t<uint16_t, 32>(a, ref_map, p, nslices, nctus, s);
-    return launch_t<uint16_t, 16>(a, ref_map, p, nslices, nctus, s);
+    if (ctu == 64) return launch_t<uint16_t, 64>(b, p, nslices, total_ctus, s);
+    if (ctu == 32) return launch_t<uint16_t, 32>(b, p, nslices, total_ctus, s);
+    return launch_t<uint16_t, 16>(b, p, nslices, total_ctus, s);
 }
 
 }  // namespace ladder_impl

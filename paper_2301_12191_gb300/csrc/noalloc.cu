@@ -158,7 +158,10 @@ extern "C" ladder_status analyze_reference_noalloc(const void *cur, const void *
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_tiles, tiles, static_cast<size_t>(ntiles) * 4, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_fill_keys(d_keys, nkeys, s);
+    FillBatch fill{};
+    fill.n = 1;
+    fill.item[0] = FillItem{d_keys, nkeys};
+    if (e == cudaSuccess) e = launch_fill_keys(fill, s);
     // candidate slices: whole group-iterations, about two CTAs per SM
     int dev = 0, sms = 1;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
@@ -174,31 +177,44 @@ extern "C" ladder_status analyze_reference_noalloc(const void *cur, const void *
     tps = (tps + groups - 1) / groups * groups;
     if (tps < groups) tps = groups;
     const int slices = (ntiles + tps - 1) / tps;
-    FullSearchArgs fa{};
-    fa.cur = cur;
-    fa.pitch_bytes = pitch_bytes;
-    fa.W = width;
-    fa.H = height;
-    fa.R = search_range;
-    fa.Rp = (search_range + 15) / 16 * 16;
-    fa.ntiles = ntiles;
-    fa.tiles_per_slice = tps;
-    fa.tiles = d_tiles;
-    fa.keys = d_keys;
-    fa.status = d_status;
-    e = launch_full_search(bit_depth, ctu_size, fa, map, slices, nctus, s);
+    FullSearchBatch fb{};
+    fb.n = 1;
+    fb.R = search_range;
+    fb.Rp = (search_range + 15) / 16 * 16;
+    fb.ntiles = ntiles;
+    fb.tiles_per_slice = tps;
+    fb.tiles = d_tiles;
+    fb.status = d_status;
+    fb.item[0] = FullSearchItem{cur, pitch_bytes, width, height, d_keys, 0};
+    fb.map[0] = map;
+    e = launch_full_search(bit_depth, ctu_size, fb, slices, nctus, s);
     if (e == cudaSuccess) {
-        DecideArgs da{};
-        da.cur = cur;
-        da.ref = ref;
-        da.pitch_bytes = pitch_bytes;
-        da.g = g;
-        da.range = search_range;
-        da.keys = d_keys;
-        da.qp = qp;
-        da.satd_mode = satd_mode;
-        da.out = dec;
-        e = launch_decide(bit_depth, da, s);
+        // the decision kernel reads its outputs as offsets from a block base;
+        // here every array is the caller's, so the base is 0 and the offsets
+        // are the caller's addresses
+        DecideBatch db{};
+        db.n = 1;
+        db.range = search_range;
+        db.satd_mode = satd_mode;
+        db.total_ctas = nctus;
+        RungInfo &ri = db.rung[0];
+        ri.g = g;
+        for (int d = 0; d <= g.dmax; ++d) {
+            ri.off.mvx[d] = reinterpret_cast<long>(dec.mvx[d]);
+            ri.off.mvy[d] = reinterpret_cast<long>(dec.mvy[d]);
+            ri.off.sad[d] = reinterpret_cast<long>(dec.sad[d]);
+            ri.off.satd[d] = reinterpret_cast<long>(dec.satd[d]);
+            ri.off.cost[d] = reinterpret_cast<long>(dec.cost[d]);
+            ri.off.best[d] = reinterpret_cast<long>(dec.best[d]);
+            ri.off.split[d] = reinterpret_cast<long>(dec.split[d]);
+            ri.off.evaluated[d] = reinterpret_cast<long>(dec.evaluated[d]);
+        }
+        ri.off.leaf_depth = reinterpret_cast<long>(dec.leaf_depth);
+        ri.off.leaf_mvx = reinterpret_cast<long>(dec.leaf_mvx);
+        ri.off.leaf_mvy = reinterpret_cast<long>(dec.leaf_mvy);
+        ri.off.keys = reinterpret_cast<long>(d_keys);
+        db.item[0] = DecideItem{cur, ref, pitch_bytes, nullptr, 0, qp, 0};
+        e = launch_decide(bit_depth, ctu_size, db, s);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -50,6 +50,11 @@ class Decisions(ctypes.Structure):
                 ("leaf_depth", ctypes.c_void_p), ("leaf_mvx", ctypes.c_void_p), ("leaf_mvy", ctypes.c_void_p)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("frame_id", ctypes.c_int), ("qp", ctypes.c_int), ("cur", ctypes.POINTER(ctypes.c_void_p)),
+                ("ref", ctypes.POINTER(ctypes.c_void_p)), ("pitch_bytes", ctypes.POINTER(ctypes.c_long))]
+
+
 # (name, restype, argtypes) of every symbol declared in include/ladder.h
 SIGNATURES = [
     ("ladder_init", ctypes.c_int, [ctypes.POINTER(Geometry), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
@@ -60,6 +65,15 @@ SIGNATURES = [
     ("analyze_dependents", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                           ctypes.POINTER(ctypes.c_long), ctypes.c_int, ctypes.c_void_p]),
+    ("ladder_analyze_batch", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.c_int, ctypes.c_void_p]),
+    ("ladder_analyze_batch_independent", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.c_int,
+                                                        ctypes.c_void_p]),
+    ("ladder_capture_batch", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_void_p)]),
+    ("ladder_graph_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("ladder_graph_destroy", None, [ctypes.c_void_p]),
+    ("ladder_set_tiles_per_slice", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("ladder_device_bytes", ctypes.c_long, [ctypes.c_void_p]),
     ("analyze_independent", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_long, ctypes.c_int, ctypes.c_void_p]),
     ("fetch_decisions", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Decisions),
@@ -225,6 +239,30 @@ def _pitch_bytes(t) -> int:
     return int(t.stride(0) * t.element_size())
 
 
+class Graph:
+    """A captured batch (ladder_capture_batch); launch() replays it."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def launch(self, stream=None):
+        st = load().ladder_graph_launch(self.handle, _stream_handle(stream))
+        if st != 0:
+            raise LadderError(st, "ladder_graph_launch")
+
+    def close(self):
+        if self.handle:
+            load().ladder_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Ladder:
     """One ladder geometry (rungs, reference rung, search ranges) and its
     resident per-frame decision state on the device."""
@@ -275,6 +313,45 @@ class Ladder:
     def analyze_independent(self, rung, frame_id, cur, ref, qp, stream=None):
         analyze_independent(self.handle, rung, frame_id, cur.data_ptr(), ref.data_ptr(), _pitch_bytes(cur), qp,
                             _stream_handle(stream))
+
+    def _requests(self, items):
+        """items: [(frame_id, qp, [(cur, ref), ...] per rung)] -> ctypes array (kept alive on self)."""
+        reqs = (Request * len(items))()
+        keep = []
+        for k, (fid, qp, planes) in enumerate(items):
+            n = len(planes)
+            cur = (ctypes.c_void_p * n)(*[c.data_ptr() for c, _ in planes])
+            ref = (ctypes.c_void_p * n)(*[f.data_ptr() for _, f in planes])
+            pit = (ctypes.c_long * n)(*[_pitch_bytes(c) for c, _ in planes])
+            keep += [cur, ref, pit]
+            reqs[k] = Request(fid, qp, cur, ref, pit)
+        self._keep_requests = (reqs, keep)
+        return reqs
+
+    def analyze_batch(self, items, stream=None):
+        """Many ladder frames in one batch: items = [(frame_id, qp, planes)],
+        planes = [(cur, ref)] for every rung in rung order."""
+        reqs = self._requests(items)
+        _call(self.handle, "ladder_analyze_batch", self.handle, reqs, len(items), _stream_handle(stream))
+
+    def analyze_batch_independent(self, items, stream=None):
+        """Every rung of every item analysed independently (full search)."""
+        reqs = self._requests(items)
+        _call(self.handle, "ladder_analyze_batch_independent", self.handle, reqs, len(items), _stream_handle(stream))
+
+    def capture_batch(self, items, stream):
+        """Captures analyze_batch(items) into a CUDA graph on `stream`."""
+        reqs = self._requests(items)
+        g = ctypes.c_void_p()
+        _call(self.handle, "ladder_capture_batch", self.handle, reqs, len(items), _stream_handle(stream),
+              ctypes.byref(g))
+        return Graph(g.value, (reqs, self._keep_requests))
+
+    def set_tiles_per_slice(self, tps: int):
+        _call(self.handle, "ladder_set_tiles_per_slice", self.handle, int(tps))
+
+    def device_bytes(self) -> int:
+        return int(load().ladder_device_bytes(self.handle))
 
     def grid(self, rung):
         return ladder_grid(self.handle, rung)

@@ -23,7 +23,7 @@ import dataclasses
 
 import numpy as np
 
-__all__ = ["FramePair", "frame_pair", "downscale", "ladder_pairs", "RUNGS"]
+__all__ = ["FramePair", "frame_pair", "sequence", "downscale", "ladder_pairs", "ladder_sequence", "RUNGS"]
 
 RUNGS = {
     "2160p": (3840, 2160),
@@ -127,6 +127,52 @@ def frame_pair(seed: int, width: int, height: int, bit_depth: int = 8, *,
     dt = _dtype(bit_depth)
     return FramePair(cur=cur.astype(dt), ref=ref.astype(dt), bit_depth=bit_depth,
                      global_mv=gmv, patches=patches)
+
+
+def sequence(seed: int, width: int, height: int, n_frames: int, bit_depth: int = 8, *, global_range: int = 16,
+             patch_range: int = 24, n_patches: int = 4, patch_size: int = 64, period_scale: float = 1.0,
+             noise_sigma: float = 4.0):
+    """Consecutive frames: frame t+1 is frame t moved by a fresh global integer
+    motion (uniform in +-global_range) with ``n_patches`` patches moved by
+    their own motion (+-patch_range), plus Gaussian noise of ``noise_sigma``.
+    Returns the list of frames and the per-step motions."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    hi = (1 << bit_depth) - 1
+    frame = _texture(rng, width, height, bit_depth, period_scale, noise_sigma)
+    frames, motions = [frame], []
+    for _ in range(n_frames - 1):
+        g = (int(rng.integers(-global_range, global_range + 1)), int(rng.integers(-global_range, global_range + 1)))
+        nxt = np.empty_like(frame)
+        _displace(frame, nxt, 0, 0, width, height, g[0], g[1])
+        patches = []
+        for _ in range(n_patches):
+            pw, ph = min(patch_size, width), min(patch_size, height)
+            px = int(rng.integers(0, width - pw + 1))
+            py = int(rng.integers(0, height - ph + 1))
+            mv = (int(rng.integers(-patch_range, patch_range + 1)), int(rng.integers(-patch_range, patch_range + 1)))
+            _displace(frame, nxt, px, py, pw, ph, mv[0], mv[1])
+            patches.append((px, py, pw, mv))
+        if noise_sigma > 0:
+            nxt = nxt + rng.normal(0.0, noise_sigma, size=nxt.shape)
+        frame = np.clip(np.rint(nxt), 0, hi)
+        frames.append(frame)
+        motions.append((g, patches))
+    dt = _dtype(bit_depth)
+    return [f.astype(dt) for f in frames], motions
+
+
+def ladder_sequence(seed: int, n_frames: int, source=(1920, 1080), rungs=((1920, 1080), (1280, 720), (960, 540),
+                                                                         (640, 360)), bit_depth: int = 8, **kw):
+    """A sequence at the source size and every rung made from each frame
+    directly: returns ``[[plane of rung r for frame t] for r] ...`` as
+    ``out[t][r]``."""
+    W, H = source
+    kw.setdefault("period_scale", W / 416.0)
+    frames, _ = sequence(seed, W, H, n_frames, bit_depth, **kw)
+    out = []
+    for f in frames:
+        out.append([f if (w, h) == (W, H) else downscale(f, w, h) for (w, h) in rungs])
+    return out
 
 
 def _taps(n_in: int, n_out: int):

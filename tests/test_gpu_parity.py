@@ -143,6 +143,83 @@ def test_batched_dependents_equal_single_calls():
         assert_decisions_equal(batched[i], ora, 64, where=f"batched vs oracle rung {i}")
 
 
+def _batch_frames(n, seed0, sizes_src=(640, 360), rungs=((480, 270), (320, 180))):
+    out = []
+    for k in range(n):
+        pairs, _ = synth.ladder_pairs(seed0 + k, source=sizes_src, rungs=list(rungs), include_source=True)
+        out.append(pairs)
+    return out
+
+
+def test_analyze_batch_equals_per_call_and_oracle():
+    frames = _batch_frames(5, 300)
+    sizes = [(w, h) for (w, h, _, _) in frames[0]]
+    ref_i, qps = 2, [22, 27, 32, 37, 30]
+    with L.Ladder(sizes, ref_i, search_range=12, refine_range=3, max_frames=10) as lad:
+        planes = [[(L.device_plane(c), L.device_plane(f)) for (_, _, c, f) in fr] for fr in frames]
+        lad.analyze_batch([(100 + k, qps[k], planes[k]) for k in range(5)])
+        got = [[lad.fetch(r, 100 + k) for r in range(3)] for k in range(5)]
+        for k in range(5):   # the same frames one call at a time
+            lad.analyze_reference(200 + k, *planes[k][ref_i], qps[k])
+            lad.analyze_dependents(200 + k, [(r, *planes[k][r]) for r in range(3) if r != ref_i], qps[k])
+        single = [[lad.fetch(r, 200 + k) for r in range(3)] for k in range(5)]
+    for k in range(5):
+        for r in range(3):
+            assert_decisions_equal(got[k][r], single[k][r], 64, where=f"batch frame {k} rung {r}")
+    for k in (0, 3):
+        fr = frames[k]
+        ora_ref = oracle.analyze(fr[ref_i][2], fr[ref_i][3], qp=qps[k], search_range=12)
+        assert_decisions_equal(got[k][ref_i], ora_ref, 64, where=f"batch vs oracle ref {k}")
+        for r in (0, 1):
+            ora = oracle.analyze(fr[r][2], fr[r][3], qp=qps[k], search_range=3, dep=dep_from(ora_ref, sizes[ref_i]))
+            assert_decisions_equal(got[k][r], ora, 64, where=f"batch vs oracle frame {k} rung {r}")
+
+
+def test_captured_batch_graph_replays():
+    frames = _batch_frames(3, 400)
+    sizes = [(w, h) for (w, h, _, _) in frames[0]]
+    with L.Ladder(sizes, 2, search_range=8, refine_range=2, max_frames=6) as lad:
+        planes = [[(L.device_plane(c), L.device_plane(f)) for (_, _, c, f) in fr] for fr in frames]
+        items = [(k, 32, planes[k]) for k in range(3)]
+        lad.analyze_batch(items)
+        eager = [[lad.fetch(r, k) for r in range(3)] for k in range(3)]
+        stream = torch.cuda.Stream()
+        graph = lad.capture_batch(items, stream)
+        for _ in range(2):
+            graph.launch(stream)
+        stream.synchronize()
+        replayed = [[lad.fetch(r, k) for r in range(3)] for k in range(3)]
+        # new content in the same buffers: the replay reads it
+        other = _batch_frames(1, 500)[0]
+        for r, (_, _, c, f) in enumerate(other):
+            planes[1][r][0].copy_(L.device_plane(c))
+            planes[1][r][1].copy_(L.device_plane(f))
+        graph.launch(stream)
+        stream.synchronize()
+        fresh = [lad.fetch(r, 1) for r in range(3)]
+        graph.close()
+    for k in range(3):
+        for r in range(3):
+            assert_decisions_equal(replayed[k][r], eager[k][r], 64, where=f"graph frame {k} rung {r}")
+    ora_ref = oracle.analyze(other[2][2], other[2][3], qp=32, search_range=8)
+    assert_decisions_equal(fresh[2], ora_ref, 64, where="graph new content")
+
+
+def test_batch_status_codes():
+    frames = _batch_frames(2, 600)
+    sizes = [(w, h) for (w, h, _, _) in frames[0]]
+    with L.Ladder(sizes, 2, search_range=8, refine_range=2, max_frames=1) as lad:
+        planes = [[(L.device_plane(c), L.device_plane(f)) for (_, _, c, f) in fr] for fr in frames]
+        with pytest.raises(L.LadderError) as e:
+            lad.analyze_batch([(0, 30, planes[0]), (1, 30, planes[1])])
+        assert e.value.status == -4          # two frames, one slot
+        with pytest.raises(L.LadderError) as e:
+            lad.analyze_batch([(0, 30, planes[0]), (0, 30, planes[1])])
+        assert e.value.status == -1          # same frame twice
+        lad.analyze_batch([(7, 30, planes[0])])
+        lad.sync()
+
+
 def test_dependent_ctu32():
     pairs, gpu, oras, _ = _ladder_case(22, (384, 216), [(288, 162), (192, 108)], 1, 8, 6, 3, 32, ctu=32)
     for i in range(len(pairs)):
