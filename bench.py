@@ -44,6 +44,12 @@ WORKLOADS = {
                  rungs=[(3840, 2160), (2560, 1440), (1920, 1080), (1280, 720), (960, 540), (640, 360)], ref=5,
                  bit_depth=10, R=64, r=8, qps=[22, 27, 32, 37], sigmas=[8], global_range=8 * 3840 // 416,
                  patch_range=12 * 3840 // 416, ctu=64),
+    # serving: Poisson requests (200/s) for single rungs of 2160p->360p ladders,
+    # 8- and 10-bit mixed, continuous batching on several streams
+    "serve": dict(mode="serve", rate=200.0, seconds=10.0, source=(3840, 2160),
+                  rungs=[(3840, 2160), (2560, 1440), (1920, 1080), (1280, 720), (960, 540), (640, 360)], ref=5,
+                  bit_depths=[8, 10], R=64, r=8, qps=[22, 27, 32, 37], ctu=64, max_frames=24,
+                  hbm_budget=16 << 30, n_open=6, streams=3, max_batch=32),
     # single 416x240 pair, independent only
     "frame416": dict(source=(416, 240), rungs=[(416, 240)], ref=0, bit_depth=8, R=16, r=4, qp=32, ctu=64),
 }
@@ -540,6 +546,75 @@ def run_batch(args, wl):
     lad.close()
 
 
+def serve_setup(wl, seed0=500):
+    """Ladder classes (one per bit depth) and their pre-made content: two
+    ladder frames each, as lists over rungs of (cur, ref) planes."""
+    from paper_2301_12191_gb300 import serve
+    classes, content = {}, {}
+    for bd in wl["bit_depths"]:
+        k = f"ladder{bd}"
+        classes[k] = serve.LadderClass(rungs=wl["rungs"], ref_rung=wl["ref"], bit_depth=bd,
+                                       search_range=wl["R"], refine_range=wl["r"], ctu=wl["ctu"],
+                                       max_frames=wl["max_frames"])
+        frames = []
+        for f in range(2):
+            pairs, _ = synth.ladder_pairs(seed0 + 10 * bd + f, source=wl["source"], rungs=wl["rungs"][1:],
+                                          bit_depth=bd, include_source=True)
+            frames.append([(c, r) for (_, _, c, r) in pairs])
+        content[k] = frames
+    return classes, content
+
+
+def run_serve(args, wl):
+    """Continuous-batching serving loop on one GPU: latency percentiles,
+    throughput and device memory held by resident reference state."""
+    import torch
+    from paper_2301_12191_gb300 import serve
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    classes, content = serve_setup(wl)
+    pinned = {k: [[(serve.pin_plane(c), serve.pin_plane(r)) for c, r in fr] for fr in v]
+              for k, v in content.items()}
+    ex = serve.GpuExecutor(classes, n_streams=wl["streams"])
+    kw = dict(hbm_budget=wl["hbm_budget"], max_batch=wl["max_batch"], max_inflight=wl["streams"])
+    # warm-up: a short burst through every class (module load, first launches)
+    warm = serve.request_stream(99, 12 * max(1, args.warmup), 2000.0, classes, pinned, qps=wl["qps"],
+                                n_open=wl["n_open"], first_frame=1 << 20)
+    serve.Server(classes, ex, **kw).run(warm)
+    torch.cuda.synchronize()
+    n_req = int(wl["rate"] * wl["seconds"])
+    reqs = serve.request_stream(7 + rank, n_req, wl["rate"], classes, pinned, qps=wl["qps"], n_open=wl["n_open"])
+    launches0 = sum(n for lad in ex.ladders.values() for n, _ in lad.kernel_stats().values())
+    srv = serve.Server(classes, ex, **kw)
+    with ClockSampler(local) as clk:
+        rep = srv.run(reqs)
+        torch.cuda.synchronize()
+    launches = sum(n for lad in ex.ladders.values() for n, _ in lad.kernel_stats().values()) - launches0
+    h2d = sum(2 * classes[r.klass].plane_bytes(r.rung) for r in reqs) // max(1, len(reqs))
+    rung_mix = {f"{w}x{h}": sum(1 for r in reqs if classes[r.klass].rungs[r.rung] == (w, h)) for (w, h) in wl["rungs"]}
+    ex.close()
+    if rank != 0:
+        return
+    result = {
+        "metric": "served frame-pair analysis requests/sec (continuous batching)", "value": rep["throughput_req_s"],
+        "unit": "requests/s", "n_gpus": 1, "higher_is_better": True, "dtype": "u8+u16", "data": "synthetic",
+        "offered_rate": wl["rate"], "latency_p50_ms": rep["latency_p50_ms"], "latency_p99_ms": rep["latency_p99_ms"],
+        "completed": rep["completed"], "failed": rep["failed"], "elapsed_s": rep["elapsed_s"],
+        "resident_bytes_max": rep["resident_bytes_max"], "resident_bytes_mean": rep["resident_bytes_mean"],
+        "held_bytes_max": rep["held_bytes_max"], "batches": rep["batches"], "mean_batch": rep["mean_batch"],
+        "gpu_launches": launches, "h2d_bytes_per_request": h2d, "clocks": clk.summary(),
+        "config": {"workload": "serve", "rungs": [f"{w}x{h}" for (w, h) in wl["rungs"]], "bit_depths": wl["bit_depths"],
+                   "R": wl["R"], "r": wl["r"], "rung_mix": rung_mix, "streams": wl["streams"],
+                   "hbm_budget": wl["hbm_budget"], "max_frames": wl["max_frames"]},
+    }
+    print(json.dumps(result))
+    if args.json_out:
+        with open(args.json_out, "w") as fh:
+            json.dump(result, fh, indent=1)
+
+
 def run_reference(args, wl):
     """The oracle on the host cores, same metric and workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -581,8 +656,13 @@ def main():
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     wl = WORKLOADS[args.config]
-    if args.impl == "reference":
+    if args.impl == "reference" and wl.get("mode") == "serve":
+        print(json.dumps({"impl": "reference", "unavailable": "the serving loop has no CPU counterpart; "
+                          "the oracle is timed on the ladder workloads"}))
+    elif args.impl == "reference":
         run_reference(args, wl)
+    elif wl.get("mode") == "serve":
+        run_serve(args, wl)
     elif wl.get("mode") == "batch":
         run_batch(args, wl)
     else:

@@ -149,6 +149,27 @@ typedef struct {
 LADDER_API ladder_status ladder_analyze_batch(ladder_t *ladder, const ladder_request *requests, int n,
                                               void *cuda_stream);
 
+/* One rung of one frame: kind 0 = independent full search (the reference
+ * rung's makes the frame's reference resident), kind 1 = dependent of the
+ * frame's reference. */
+typedef struct {
+    int frame_id;
+    int rung;
+    int kind;
+    int qp;
+    const void *cur, *ref;
+    long pitch_bytes;
+} ladder_job;
+
+/* Any mix of jobs of any frames in one call: all independent jobs in
+ * batched launches first, then all dependent jobs in batched launches, on
+ * `cuda_stream` (a dependent may use a reference job of the same call).
+ * (frame, rung) pairs distinct.  Results are identical to one call per job.
+ * LADDER_E_NOREF if a dependent's frame has no reference (resident or in
+ * the call); LADDER_E_BUSY if the new frames need more free slots than
+ * there are; nothing is launched on an error. */
+LADDER_API ladder_status ladder_analyze_jobs(ladder_t *ladder, const ladder_job *jobs, int n, void *cuda_stream);
+
 /* Every rung of every request analysed independently (full search +-R on
  * each rung), batched like ladder_analyze_batch: the per-rung baseline of the
  * multi-resolution speedup.  n in 1..64. */

@@ -606,6 +606,59 @@ ladder_status ladder_analyze_batch_independent(ladder_t *l, const ladder_request
     return st;
 }
 
+ladder_status ladder_analyze_jobs(ladder_t *l, const ladder_job *jobs, int n, void *cuda_stream)
+{
+    if (!l) return LADDER_E_INVAL;
+    if (!jobs || n < 0) return fail(l, LADDER_E_INVAL, "bad job list");
+    if (n == 0) return LADDER_OK;
+    std::vector<Job> ij, dj;
+    // validate everything before touching any slot
+    for (int k = 0; k < n; ++k) {
+        const ladder_job &jb = jobs[k];
+        ladder_status st = check_planes(l, jb.rung, jb.cur, jb.ref, jb.pitch_bytes, jb.qp);
+        if (st != LADDER_OK) return st;
+        if (jb.kind != 0 && jb.kind != 1) return fail(l, LADDER_E_INVAL, "job %d: kind %d", k, jb.kind);
+        if (jb.kind == 1 && jb.rung == l->geo.ref_rung)
+            return fail(l, LADDER_E_INVAL, "job %d: the reference rung cannot be dependent", k);
+        for (int j = 0; j < k; ++j)
+            if (jobs[j].frame_id == jb.frame_id && jobs[j].rung == jb.rung)
+                return fail(l, LADDER_E_INVAL, "job %d repeats (frame %d, rung %d)", k, jb.frame_id, jb.rung);
+    }
+    int free_slots = 0;
+    for (auto &sl : l->slots) free_slots += !sl.used;
+    std::vector<int> new_frames;
+    for (int k = 0; k < n; ++k)
+        if (!find_slot(l, jobs[k].frame_id) &&
+            std::find(new_frames.begin(), new_frames.end(), jobs[k].frame_id) == new_frames.end())
+            new_frames.push_back(jobs[k].frame_id);
+    if (static_cast<int>(new_frames.size()) > free_slots)
+        return fail(l, LADDER_E_BUSY, "jobs need %zu free frame slots, %d free", new_frames.size(), free_slots);
+    // a dependent needs its frame's reference: already resident, or a
+    // reference-rung job in this same call
+    for (int k = 0; k < n; ++k) {
+        if (jobs[k].kind != 1) continue;
+        Slot *sl = find_slot(l, jobs[k].frame_id);
+        bool ok = sl && sl->ref_done;
+        for (int j = 0; j < n && !ok; ++j)
+            ok = jobs[j].kind == 0 && jobs[j].rung == l->geo.ref_rung && jobs[j].frame_id == jobs[k].frame_id;
+        if (!ok) return fail(l, LADDER_E_NOREF, "job %d: frame %d has no reference analysis", k, jobs[k].frame_id);
+    }
+    for (int k = 0; k < n; ++k) {
+        const ladder_job &jb = jobs[k];
+        Slot *sl = claim_slot(l, jb.frame_id);
+        (jb.kind == 0 ? ij : dj).push_back(Job{sl, jb.rung, jb.cur, jb.ref, jb.pitch_bytes, jb.qp});
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (!ij.empty()) {
+        ladder_status st = launch_independent(l, ij.data(), static_cast<int>(ij.size()), s);
+        if (st != LADDER_OK) return st;
+        for (const Job &jb : ij)
+            if (jb.rung == l->geo.ref_rung) jb.slot->ref_done = 1;
+    }
+    if (!dj.empty()) return launch_dependents(l, dj.data(), static_cast<int>(dj.size()), s);
+    return LADDER_OK;
+}
+
 ladder_status ladder_capture_batch(ladder_t *l, const ladder_request *reqs, int n, void *cuda_stream,
                                    ladder_graph_t **out)
 {

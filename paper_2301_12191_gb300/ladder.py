@@ -50,6 +50,11 @@ class Decisions(ctypes.Structure):
                 ("leaf_depth", ctypes.c_void_p), ("leaf_mvx", ctypes.c_void_p), ("leaf_mvy", ctypes.c_void_p)]
 
 
+class Job(ctypes.Structure):
+    _fields_ = [("frame_id", ctypes.c_int), ("rung", ctypes.c_int), ("kind", ctypes.c_int), ("qp", ctypes.c_int),
+                ("cur", ctypes.c_void_p), ("ref", ctypes.c_void_p), ("pitch_bytes", ctypes.c_long)]
+
+
 class Request(ctypes.Structure):
     _fields_ = [("frame_id", ctypes.c_int), ("qp", ctypes.c_int), ("cur", ctypes.POINTER(ctypes.c_void_p)),
                 ("ref", ctypes.POINTER(ctypes.c_void_p)), ("pitch_bytes", ctypes.POINTER(ctypes.c_long))]
@@ -66,6 +71,7 @@ SIGNATURES = [
                                           ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                           ctypes.POINTER(ctypes.c_long), ctypes.c_int, ctypes.c_void_p]),
     ("ladder_analyze_batch", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.c_int, ctypes.c_void_p]),
+    ("ladder_analyze_jobs", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Job), ctypes.c_int, ctypes.c_void_p]),
     ("ladder_analyze_batch_independent", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.c_int,
                                                         ctypes.c_void_p]),
     ("ladder_capture_batch", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.c_int, ctypes.c_void_p,
@@ -333,6 +339,13 @@ class Ladder:
         planes = [(cur, ref)] for every rung in rung order."""
         reqs = self._requests(items)
         _call(self.handle, "ladder_analyze_batch", self.handle, reqs, len(items), _stream_handle(stream))
+
+    def analyze_jobs(self, jobs, stream=None):
+        """jobs: [(frame_id, rung, kind, qp, cur, ref)], kind 0 = independent,
+        1 = dependent; one call, batched launches."""
+        arr = (Job * len(jobs))(*[Job(f, r, k, q, c.data_ptr(), x.data_ptr(), _pitch_bytes(c))
+                                  for (f, r, k, q, c, x) in jobs])
+        _call(self.handle, "ladder_analyze_jobs", self.handle, arr, len(jobs), _stream_handle(stream))
 
     def analyze_batch_independent(self, items, stream=None):
         """Every rung of every item analysed independently (full search)."""
