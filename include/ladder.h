@@ -187,10 +187,6 @@ LADDER_API ladder_status ladder_capture_batch(ladder_t *ladder, const ladder_req
 LADDER_API ladder_status ladder_graph_launch(ladder_graph_t *graph, void *cuda_stream);
 LADDER_API void ladder_graph_destroy(ladder_graph_t *graph);
 
-/* Candidate tiles per full-search CTA (0 restores the built-in choice of
- * about two waves): the knob the autotuner sets. */
-LADDER_API ladder_status ladder_set_tiles_per_slice(ladder_t *ladder, int tiles_per_slice);
-
 /* Device bytes the handle holds (decision buffers of every frame slot). */
 LADDER_API long ladder_device_bytes(const ladder_t *ladder);
 
@@ -250,7 +246,7 @@ LADDER_API ladder_status ladder_profile_read(ladder_t *ladder, int kind, long *l
  * decision arrays (every member up to depth log2(ctu_size/8) must be set),
  * which are written asynchronously on `cuda_stream`.
  * Scratch lives in a fixed 2 MiB device array inside the library (every GPU
- * that loads the library holds it until exit): frames of at most 3059 CTUs
+ * that loads the library holds it until exit): frames of at most 3083 CTUs
  * of 64x64 (a 3840x2160 frame has 2040; about 4x that count at CTU 32) fit; larger ones
  * return LADDER_E_INVAL, like any argument the other entry points refuse.
  * The first call on a device looks up the array's device address with that

@@ -31,8 +31,6 @@ struct Slot {
     std::vector<RungBuffers> rungs;
 };
 
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-std::once_flag g_encode_once;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -53,14 +51,11 @@ struct ladder {
     void *arena = nullptr;
     size_t arena_bytes = 0;
     int *d_status = nullptr;
-    int *d_tiles = nullptr;
-    int ntiles = 0;
     uint16_t *d_rank = nullptr, *d_unrank = nullptr;  // refinement candidate order
     int rank_bits = 0;
     std::string err;
     int sm_count = 0;
     int fs_ctas_per_sm = 1;      // resident full-search CTAs per SM
-    int fs_tps_override = 0;     // tiles per slice set by a tuner (0: heuristic)
     char *host_stage = nullptr;  // pinned staging for fetch_decisions
     size_t host_stage_bytes = 0;
     // tracing
@@ -245,49 +240,6 @@ ladder_status check_planes(ladder_t *l, int rung, const void *cur, const void *r
     return LADDER_OK;
 }
 
-bool encode_ref_map(ladder_t *l, CUtensorMap *map, const void *ref, const RungGeom &g, long pitch,
-                    const FullSearchPlan &p)
-{
-    std::call_once(g_encode_once, [] {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    });
-    if (!g_encode) {
-        fail(l, LADDER_E_CUDA, "cuTensorMapEncodeTiled unavailable");
-        return false;
-    }
-    const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(g.W), static_cast<cuuint64_t>(g.H)};
-    const cuuint64_t gstride[1] = {static_cast<cuuint64_t>(pitch)};
-    const cuuint32_t box[2] = {static_cast<cuuint32_t>(p.box_w), static_cast<cuuint32_t>(p.box_h)};
-    const cuuint32_t estride[2] = {1, 1};
-    const CUtensorMapDataType dt =
-        l->geo.bit_depth == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
-    CUresult r = g_encode(map, dt, 2, const_cast<void *>(ref), gdim, gstride, box, estride,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        fail(l, LADDER_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
-        return false;
-    }
-    return true;
-}
-
-// Candidate tiles per slice: whole group-iterations (no duplicate tiles),
-// about two waves of CTAs over the whole batch.
-int choose_tiles_per_slice(const ladder_t *l, int total_ctus, int ntiles, int groups)
-{
-    if (l->fs_tps_override > 0) return std::max(groups, l->fs_tps_override / groups * groups);
-    const int target = 2 * std::max(1, l->sm_count) * std::max(1, l->fs_ctas_per_sm);
-    const int slices = std::max(1, (target + total_ctus - 1) / total_ctus);
-    int tps = (ntiles + slices - 1) / slices;
-    tps = (tps + groups - 1) / groups * groups;
-    return std::max(groups, tps);
-}
-
 // One rung of one frame and its planes.
 struct Job {
     Slot *slot;
@@ -310,16 +262,13 @@ ladder_status launch_independent(ladder_t *l, const Job *jobs, int n, cudaStream
         DecideBatch db{};
         fill.n = m;
         fb.n = m;
-        fb.R = R;
-        fb.Rp = (R + 15) / 16 * 16;
-        fb.ntiles = l->ntiles;
-        fb.tiles = l->d_tiles;
+        fill_full_search_batch(fb, plan, R);
         fb.status = l->d_status;
         db.n = m;
         db.range = R;
         db.satd_mode = l->geo.satd_mode;
         for (int r = 0; r < l->geo.n_rungs; ++r) db.rung[r] = l->info[r];
-        int total = 0;
+        int total = 0, total_ctas = 0;
         for (int k = 0; k < m; ++k) {
             const Job &jb = jobs[j0 + k];
             const RungInfo &ri = l->info[jb.rung];
@@ -327,18 +276,20 @@ ladder_status launch_independent(ladder_t *l, const Job *jobs, int n, cudaStream
             auto *keys = reinterpret_cast<unsigned long long *>(block + ri.off.keys);
             const int nctus = ri.g.ctu_cols * ri.g.ctu_rows;
             fill.item[k] = FillItem{keys, static_cast<long>(nctus) * keys_per_ctu(ri.g.dmax)};
-            if (!encode_ref_map(l, &fb.map[k], jb.ref, ri.g, jb.pitch, plan)) return LADDER_E_CUDA;
-            fb.item[k] = FullSearchItem{jb.cur, jb.pitch, ri.g.W, ri.g.H, keys, total};
+            const int er = encode_item_maps(fb, k, jb.cur, jb.ref, ri.g.W, ri.g.H, jb.pitch, l->geo.bit_depth,
+                                            l->geo.ctu_size, plan);
+            if (er != 0) return fail(l, LADDER_E_CUDA, "tensor map encoding failed (%d)", er);
+            fb.item[k] = FullSearchItem{ri.g.W, ri.g.H, keys, total_ctas};
             db.item[k] = DecideItem{jb.cur, jb.ref, jb.pitch, block, jb.rung, jb.qp, total};
             total += nctus;
+            total_ctas += nctus * plan.warp_tiles;
         }
         db.total_ctas = total;
-        fb.tiles_per_slice = choose_tiles_per_slice(l, total, l->ntiles, plan.groups);
-        const int slices = (l->ntiles + fb.tiles_per_slice - 1) / fb.tiles_per_slice;
+        fb.total = total_ctas;
         cudaError_t e = traced(l, 3, s, [&] { return launch_fill_keys(fill, s); });
         if (e != cudaSuccess) return cuda_fail(l, e, "fill keys");
         e = traced(l, 0, s, [&] {
-            return launch_full_search(l->geo.bit_depth, l->geo.ctu_size, fb, slices, total, s);
+            return launch_full_search(l->geo.bit_depth, l->geo.ctu_size, fb, s);
         });
         if (e != cudaSuccess) return cuda_fail(l, e, "full search launch");
         e = traced(l, 1, s, [&] { return launch_decide(l->geo.bit_depth, l->geo.ctu_size, db, s); });
@@ -419,11 +370,9 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
     }
     l->fs_ctas_per_sm = full_search_ctas_per_sm(geometry->bit_depth, geometry->ctu_size, geometry->ref_search_range);
 
-    const int ntiles = full_search_tiles(geometry->bit_depth, geometry->ref_search_range, nullptr, 0);
-    l->ntiles = ntiles;
     const int Kr = 2 * geometry->dep_refine_range + 1;
     const size_t rank_bytes = align_up(static_cast<size_t>(Kr) * Kr * 2, 256);
-    const size_t fixed = 256 + align_up(static_cast<size_t>(ntiles) * 4, 256) + 2 * rank_bytes;
+    const size_t fixed = 256 + 2 * rank_bytes;
     l->arena_bytes = fixed + per_slot * geometry->max_frames;
     cudaError_t e = cudaMalloc(&l->arena, l->arena_bytes);
     if (e != cudaSuccess) {
@@ -433,8 +382,7 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
     }
     char *base = static_cast<char *>(l->arena);
     l->d_status = reinterpret_cast<int *>(base);
-    l->d_tiles = reinterpret_cast<int *>(base + 256);
-    l->d_rank = reinterpret_cast<uint16_t *>(base + 256 + align_up(static_cast<size_t>(ntiles) * 4, 256));
+    l->d_rank = reinterpret_cast<uint16_t *>(base + 256);
     l->d_unrank = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(l->d_rank) + rank_bytes);
     while ((1 << l->rank_bits) < Kr * Kr) ++l->rank_bits;
     char *p = base + fixed;
@@ -459,14 +407,10 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
         cudaGetLastError();
         return LADDER_E_NOMEM;
     }
-    std::vector<int> tiles(ntiles);
-    full_search_tiles(geometry->bit_depth, geometry->ref_search_range, tiles.data(), ntiles);
     std::vector<uint16_t> rank(static_cast<size_t>(Kr) * Kr), unrank(rank.size());
     refine_rank_tables(geometry->dep_refine_range, rank.data(), unrank.data());
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     e = cudaMemsetAsync(l->d_status, 0, sizeof(int), s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(l->d_tiles, tiles.data(), tiles.size() * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(l->d_rank, rank.data(), rank.size() * 2, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(l->d_unrank, unrank.data(), unrank.size() * 2, cudaMemcpyHostToDevice, s);
@@ -713,12 +657,6 @@ void ladder_graph_destroy(ladder_graph_t *g)
     delete g;
 }
 
-ladder_status ladder_set_tiles_per_slice(ladder_t *l, int tiles_per_slice)
-{
-    if (!l || tiles_per_slice < 0) return LADDER_E_INVAL;
-    l->fs_tps_override = tiles_per_slice;
-    return LADDER_OK;
-}
 
 ladder_status ladder_grid(const ladder_t *l, int rung, int *dims, int *n_depths)
 {

@@ -88,47 +88,61 @@ constexpr int kMaxItems = 64;                    // frames per batched launch
 constexpr int kMaxDepItems = kMaxItems * 3;      // dependent (frame, rung) pairs per batched launch
 
 // ---- full search (independent analysis) --------------------------------
-// One item = one frame's independently analysed rung.  The grid is
-// (candidate slices) x (sum of the items' CTUs); kernel parameters are
-// grid-constant (CUDA 12.1+ allows 32 KB), the tensor maps included.
+// One item = one frame's independently analysed rung.  One CTA per (CTU,
+// warp tile of candidates); kernel parameters are grid-constant (CUDA 12.1+
+// allows 32 KB), the tensor maps included.
+constexpr int kFsBand = 13;  // candidate rows (dy) per lane task
+
 struct FullSearchItem {
-    const void *cur;      // W x H plane, pitch bytes below
-    long pitch_bytes;
     int W, H;
     unsigned long long *keys;  // per CTU keys_per_ctu(dmax), initialised to ~0
-    int cta_begin;        // first grid.y row of this item
+    int cta_begin;             // first work item of this frame: CTUs x warp_tiles items, CTU-major
 };
 
 struct FullSearchBatch {
     int n;
-    int R;                // search range
-    int Rp;               // left/right window margin: R rounded up to 16 samples
-    int ntiles;           // candidate tiles of the search square
-    int tiles_per_slice;  // tiles handled by one CTA
-    const int *tiles;     // packed (dx_base & 0xffff) | (dy_base << 16)
+    int R;            // search range
+    int Rp;           // left window margin: R rounded up to 16 samples
+    int ntasks;       // lane tasks (dx, band of kFsBand dy) per CTU
+    int warp_tiles;   // CTAs per CTU: ceil(ntasks / 32)
+    int box_h;        // rows of the TMA box (the most any warp tile needs)
+    int e_bytes;      // shared bytes of the expanded window (box_h x positions x 4)
+    int stage_off;    // byte offset of the staged rows inside the expanded window
+    int phase1_rows;  // expanded rows that end before the staged rows
+    int buf_bytes;    // shared bytes of the expanded window + current CTU + block sums
+    int total;        // CTAs of the batch
+    uint32_t one;     // 1, as an operand the compiler cannot fold
     int *status;
     FullSearchItem item[kMaxItems];
-    CUtensorMap map[kMaxItems];  // reference plane of each item
+    CUtensorMap map[kMaxItems];      // reference plane of each item (box: window positions x box_h rows)
+    CUtensorMap cur_map[kMaxItems];  // current plane of each item (box: CTU x CTU)
 };
 
 struct FullSearchPlan {
-    int tile_dy, tile_nx;  // candidates per tile: tile_dy rows x tile_nx same-class columns
-    int smem_bytes;
-    int box_w, box_h;      // TMA box (samples x rows)
-    int pitch_words;       // words per window row (staging and copies)
-    int copy_stride;       // words between shifted copies
-    int groups;            // candidate groups per CTA (tiles per CTA iteration)
+    int Rp;
+    int band, nbands, ntasks, warp_tiles;
+    int P4;           // window positions per row
+    int box_w, box_h; // TMA box (samples x rows)
+    int e_bytes, stage_off, phase1_rows, buf_bytes;
+    int smem_bytes;   // dynamic shared memory of one CTA (two buffers)
 };
 
-// Returns the shared-memory plan for bit depth / CTU / R (box, pitch, bytes).
+// Returns the shared-memory plan for bit depth / CTU / R.
 FullSearchPlan full_search_plan(int bit_depth, int ctu, int R);
+// Tiled 2-D tensor map of a W x H plane (8-bit: uint8, 10-bit: uint16
+// samples), box box_w x box_h samples, zero fill outside the plane.
+// Returns 0 on success, else the driver's error (or -1: encoder unavailable).
+int encode_plane_map(CUtensorMap *map, const void *plane, int W, int H, long pitch_bytes, int bit_depth, int box_w,
+                     int box_h);
+// Both maps of one full-search item: the reference window and the current CTU.
+int encode_item_maps(FullSearchBatch &b, int k, const void *cur, const void *ref, int W, int H, long pitch_bytes,
+                     int bit_depth, int ctu, const FullSearchPlan &p);
+// Copies the plan's launch constants into a batch.
+void fill_full_search_batch(FullSearchBatch &b, const FullSearchPlan &p, int R);
 // Resident full-search CTAs per SM for this plan (occupancy calculator).
 int full_search_ctas_per_sm(int bit_depth, int ctu, int R);
-// Builds the candidate tile list for range R (host); returns the count.
-int full_search_tiles(int bit_depth, int R, int *out, int cap);
-// grid = (nslices, total CTUs of the batch)
-cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchBatch &b, int nslices, int total_ctus,
-                               cudaStream_t s);
+// One CTA per work item: b.total = sum over frames of CTUs x warp_tiles.
+cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchBatch &b, cudaStream_t s);
 
 // ---- decision step of independently analysed rungs -------------------------
 struct DecideItem {

@@ -8,29 +8,41 @@
 // (2R+1)^2 candidates.
 //
 // Layout of the work:
-//   * CTA = one CTU x one slice of candidate tiles (grid.x = slices,
-//     grid.y = CTUs); 256 threads.
-//   * The reference window (CTU + 2R rows, CTU + 2Rp samples) is loaded by
-//     one TMA tile copy into shared memory (zero fill out of the frame, then
-//     the out-of-frame samples are replaced by the clamped ones).  It is then
-//     expanded into SPW byte-shifted copies (SPW = samples per 32-bit word)
-//     so that every candidate reads whole, aligned words.
-//   * Thread = one "unit" of the current CTU held in registers (16x16 samples
-//     for 8-bit, 8 wide x 16 high for 10-bit: 16 rows x 4 words either way)
-//     x one group of candidate tiles.  A tile is TY consecutive dy by NX
-//     consecutive dx of one word class (dx = base + SPW*n): each shared
-//     memory row load feeds TY*NX*4 packed absdiff-accumulate instructions
-//     (vabsdiff4/vabsdiff2 .add).
-//   * 16 / 32 / 64 sums across threads use reduce-scatter shuffles inside a
-//     warp (units of a CTU are Z-ordered across lanes), so each level costs
-//     a few shuffles per tile instead of one per candidate.
-//   * Per-thread running bests are merged with shared-memory atomicMin on the
-//     64-bit keys, then into the global per-CTU keys with global atomicMin
-//     (slices of the same CTU run in different CTAs).  Integer min is
-//     order-independent, so the result is deterministic.
+//   * Lane task = one dx and TY consecutive dy (a "band" of candidate rows);
+//     a warp tile = 32 lane tasks (consecutive dx, wrapping into the next
+//     band).  CTA = one CTU x one warp tile, 4 warps: warp q searches the
+//     q-th quadrant of the CTU for the same 32 x TY candidates; several CTAs
+//     per SM hide each other's copies and barriers.
+//   * The reference window rows those candidates need and the current CTU
+//     arrive by TMA tile copies.  The window is expanded
+//     in place to one 32-bit word per sample position (8-bit: samples
+//     p..p+3; 10-bit: p, p+1), taking the clamped sample wherever the window
+//     leaves the frame, so the 32 lanes (consecutive dx) read 32 consecutive
+//     words: conflict-free, with compile-time row offsets.  The current CTU
+//     is read by broadcast.
+//   * 8-bit: packed absdiff-accumulate (vabsdiff4 .add), 4 samples per ALU
+//     instruction.  10-bit: SAD = sum(a) + sum(b) - 2 sum(min(a, b)) on
+//     packed halfword pairs: one min.u16x2 (ALU) and one multiply-add
+//     accumulate (FMA pipe) per two samples; sum(b) comes from row sums
+//     slid over the candidate rows, sum(a) is per block.  Each half of a
+//     packed 8x8 sum stays below 2^16, so nothing carries across halves.
+//   * Keys: SAD * 2^16 + code, code = L1 * 2K + 2 (dy + R) + [dx > 0] (K =
+//     2R + 1), which orders candidates of equal SAD by (|dx|+|dy|, dy, dx).
+//     Per CU each lane takes the min over its TY candidates, one warp min
+//     (redux.sync) gives the tile's best, and lane 0 folds it into the CTA's
+//     keys with a shared atomicMin.  8x8 (and 8-bit 16x16) keys fit in 32
+//     bits; larger CUs use 64-bit keys.  The 64x64 sums add the quadrants'
+//     sums through shared memory.
+//   * The CTA's keys are re-encoded as (SAD << 32) | tie-break and merged
+//     into the global per-CTU keys with atomicMin (warp tiles of one CTU run
+//     in different CTAs).  Integer min is order-independent, so the result
+//     is deterministic.
 #include "common.cuh"
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
+#include <mutex>
 
 namespace ladder_impl {
 namespace {
@@ -40,226 +52,187 @@ using dev::mbar_init;
 using dev::mbar_wait_bounded;
 using dev::sad_acc;
 using dev::tma_load_2d;
-using dev::Traits;
 
-// Origin (in samples, inside the CTU) of unit u.  Units are Z-ordered so
-// that lanes sharing a 16x16 / 32x32 / 64x64 CU differ only in low lane bits.
-template <int SPW>
-__device__ __forceinline__ void unit_origin(int u, int &ux, int &uy)
+template <typename T, int CTU, int RP> struct Shape {
+    static constexpr int ES = sizeof(T);
+    static constexpr int TY = kFsBand;
+    static constexpr int P4 = CTU + 2 * RP;       // window positions (= expanded words) per row
+    static constexpr int NT = 128;                // 4 warps, one per quadrant
+    static constexpr int Q = CTU / 2;             // quadrant side
+    static constexpr int QB = Q / 8;              // 8x8 blocks per quadrant side
+    static constexpr int NBQ = QB * QB;           // 8x8 blocks per quadrant
+    static constexpr int DMAX = CTU == 64 ? 3 : (CTU == 32 ? 2 : 1);
+    static constexpr int NKEY = keys_per_ctu(DMAX);
+    static constexpr int NB8 = (CTU / 8) * (CTU / 8);
+    static constexpr int MAX_ROWS = CTU + 2 * TY - 1;
+    static constexpr int CPR = P4 / 4;            // 16-byte chunks of expanded words per row
+    // phase 2 of the in-place expansion covers at most box_h * ES / 4 + 2 rows
+    static constexpr int MAXC = (((MAX_ROWS * ES + 3) / 4 + 2) * CPR + NT - 1) / NT;
+    static constexpr int NW = ES == 1 ? 2 : 3;    // staged words behind one chunk
+    static constexpr bool K16_32 = ES == 1;       // 16x16 keys fit 32 bits (8-bit samples)
+};
+
+__device__ __forceinline__ uint32_t umad(uint32_t a, uint32_t b, uint32_t c)
 {
-    const int q = (SPW == 4) ? u : (u >> 1);
-    const int h = (SPW == 4) ? 0 : (u & 1);
-    const int x16 = (q & 1) | ((q >> 1) & 2);
-    const int y16 = ((q >> 1) & 1) | ((q >> 2) & 2);
-    ux = x16 * 16 + h * 8;
-    uy = y16 * 16;
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
 }
 
-// Candidate (dx, dy) of tile-local index c.
-template <int SPW, int NX>
-__device__ __forceinline__ void cand_of(int c, int dxb, int dyb, int &dx, int &dy)
+__device__ __forceinline__ unsigned long long umad_wide(uint32_t a, uint32_t b, uint32_t c)
 {
-    dx = dxb + SPW * (c % NX);
-    dy = dyb + c / NX;
+    unsigned long long d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(static_cast<unsigned long long>(c)));
+    return d;
 }
 
-// Folds a tile's best 32-bit key (SAD << KS | L1 << LNC | c) into a running
-// 64-bit best (SAD << 32 | global tie-break).  The 32-bit key already orders
-// the tile's candidates by (SAD, L1, dy, dx); the global tie-break is only
-// computed when the tile can win.
-template <int SPW, int NX, int KS, int LNC>
-__device__ __forceinline__ void fold_key32(unsigned long long &best, uint32_t kmin, int dxb, int dyb, int R, int K)
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
 {
-    const uint32_t sad = kmin >> KS;
-    if (sad <= static_cast<uint32_t>(best >> 32)) {
-        int dx, dy;
-        cand_of<SPW, NX>(static_cast<int>(kmin & ((1u << LNC) - 1)), dxb, dyb, dx, dy);
-        const uint32_t tb = static_cast<uint32_t>((abs(dx) + abs(dy)) * K * K + (dy + R) * K + (dx + R));
-        const unsigned long long key = (static_cast<unsigned long long>(sad) << 32) | tb;
-        best = key < best ? key : best;
-    }
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
 }
 
-template <int SPW, int NX>
-__device__ __forceinline__ void fold_sum(unsigned long long &best, uint32_t sad, int c, int dxb, int dyb, int R,
-                                         int K)
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
 {
-    if (sad <= static_cast<uint32_t>(best >> 32)) {
-        int dx, dy;
-        cand_of<SPW, NX>(c, dxb, dyb, dx, dy);
-        const uint32_t tb = static_cast<uint32_t>((abs(dx) + abs(dy)) * K * K + (dy + R) * K + (dx + R));
-        const unsigned long long key = (static_cast<unsigned long long>(sad) << 32) | tb;
-        best = key < best ? key : best;
-    }
+    const uint32_t hi = static_cast<uint32_t>(v >> 32), lo = static_cast<uint32_t>(v);
+    const uint32_t mh = __reduce_min_sync(0xffffffffu, hi);
+    const uint32_t ml = __reduce_min_sync(0xffffffffu, hi == mh ? lo : 0xffffffffu);
+    return (static_cast<unsigned long long>(mh) << 32) | ml;
 }
 
-// One reduce-scatter step over lane bit `bit` on the CNT held sums: the lane
-// keeps half of them, summed with its partner's copy of that half.
-template <int NC, int CNT>
-__device__ __forceinline__ void scatter_step(uint32_t (&s)[NC], int &off, int lane, int bit)
+// Min over the lane's candidates of a 32-bit key SAD * 2^16 + code (mul[i]
+// is 2^16 for a real candidate, 0 for a padding row whose code is ~0).
+template <int TY>
+__device__ __forceinline__ uint32_t lane_key32(const uint32_t (&s)[TY], const uint32_t (&mul)[TY],
+                                               const uint32_t (&code)[TY])
 {
-    if constexpr (CNT >= 2) {
-        const bool up = (lane >> bit) & 1;
+    uint32_t k = umad(s[0], mul[0], code[0]);
 #pragma unroll
-        for (int m = 0; m < CNT / 2; ++m) {
-            const uint32_t send = up ? s[m] : s[m + CNT / 2];
-            const uint32_t keep = up ? s[m + CNT / 2] : s[m];
-            s[m] = keep + __shfl_xor_sync(0xffffffffu, send, 1 << bit);
-        }
-        off += up ? CNT / 2 : 0;
+    for (int i = 1; i < TY; ++i) k = min(k, umad(s[i], mul[i], code[i]));
+    return k;
+}
+
+template <int TY>
+__device__ __forceinline__ unsigned long long lane_key64(const uint32_t (&s)[TY], const uint32_t (&mul)[TY],
+                                                         const uint32_t (&code)[TY])
+{
+    unsigned long long k = ~0ull;
+#pragma unroll
+    for (int i = 0; i < TY; ++i) {
+        const unsigned long long v = mul[i] ? umad_wide(s[i], 65536u, code[i]) : ~0ull;
+        k = v < k ? v : k;
+    }
+    return k;
+}
+
+// Staged words behind expanded chunk m (positions 4m .. 4m+3) of a window
+// row: 8-bit samples 4m .. 4m+7, 10-bit samples 4m .. 4m+5.  `srow` is the
+// staged row (already clamped to the frame); columns left or right of the
+// frame take the clamped sample.
+template <typename T, int P4>
+__device__ __forceinline__ void fetch_chunk(const T *srow, int m, int gx0, int W, uint32_t (&w)[sizeof(T) == 1 ? 2 : 3])
+{
+    constexpr int ES = sizeof(T);
+    constexpr int NW = ES == 1 ? 2 : 3;
+    constexpr int NS = ES == 1 ? 8 : 6;  // samples behind the chunk
+    const int c0 = 4 * m;
+    if (gx0 + c0 >= 0 && gx0 + c0 + NS <= W && c0 + NS <= P4) {
+        const uint32_t *sw = reinterpret_cast<const uint32_t *>(srow);
+#pragma unroll
+        for (int k = 0; k < NW; ++k) w[k] = sw[c0 * ES / 4 + k];
     } else {
-        s[0] += __shfl_xor_sync(0xffffffffu, s[0], 1 << bit);
+#pragma unroll
+        for (int k = 0; k < NW; ++k) w[k] = 0;
+#pragma unroll
+        for (int e = 0; e < NS; ++e) {
+            const int c = min(max(gx0 + c0 + e, 0), W - 1) - gx0;  // inside the staged row
+            if (c0 + e < P4) w[e * ES / 4] |= static_cast<uint32_t>(srow[c]) << ((e * ES * 8) & 31);
+        }
     }
 }
 
-template <int CNT> __host__ __device__ constexpr int after_step() { return CNT >= 2 ? CNT / 2 : 1; }
-
-// Argmin over the CNT held candidates (indices off .. off+CNT-1) of one level.
-template <int SPW, int NX, int NC, int CNT, int KS, int LNC>
-__device__ __forceinline__ void level_argmin(unsigned long long &best, const uint32_t (&s)[NC],
-                                             const uint32_t (&code)[NC], int off, int dxb, int dyb, int R,
-                                             int K)
+template <int ES>
+__device__ __forceinline__ void emit_chunk(const uint32_t (&w)[ES == 1 ? 2 : 3], uint32_t *dst)
 {
-    if constexpr (CNT == 1) {
-        fold_sum<SPW, NX>(best, s[0], off, dxb, dyb, R, K);
+    uint4 v;
+    if constexpr (ES == 1) {
+        v.x = w[0];
+        v.y = __funnelshift_r(w[0], w[1], 8);
+        v.z = __funnelshift_r(w[0], w[1], 16);
+        v.w = __funnelshift_r(w[0], w[1], 24);
     } else {
-        uint32_t kmin = 0xffffffffu;
-#pragma unroll
-        for (int m = 0; m < CNT; ++m) {
-            // code[] is indexed by the tile-local candidate; off is a
-            // multiple of CNT, so select with a short unrolled search.
-            uint32_t cd = 0;
-#pragma unroll
-            for (int c = 0; c < NC; c += CNT) cd = (off == c) ? code[c + m] : cd;
-            const uint32_t k = (s[m] << KS) | cd;
-            kmin = k < kmin ? k : kmin;
-        }
-        fold_key32<SPW, NX, KS, LNC>(best, kmin, dxb, dyb, R, K);
+        v.x = w[0];
+        v.y = __funnelshift_r(w[0], w[1], 16);
+        v.z = w[1];
+        v.w = __funnelshift_r(w[1], w[2], 16);
     }
+    *reinterpret_cast<uint4 *>(dst) = v;
 }
 
-// Min of a 64-bit key over the lanes that differ only in the bits of `mask`.
-__device__ __forceinline__ unsigned long long warp_min_over(unsigned long long v, unsigned mask)
+template <typename T, int CTU, int RP>
+__global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(const __grid_constant__ FullSearchBatch b)
 {
-#pragma unroll
-    for (int b = 0; b < 5; ++b)
-        if (mask & (1u << b)) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, 1 << b);
-            v = o < v ? o : v;
-        }
-    return v;
-}
-
-// Word offset of window row `row`, word `w` in a shifted copy: rows are
-// `pw` words apart plus one pad word every 16 rows, so that the lanes of a
-// warp (units 16 rows apart, 4 words apart) hit distinct banks.
-__device__ __forceinline__ int copy_off(int row, int w, int pw) { return row * pw + (row >> 4) + w; }
-
-template <typename T, int CTU, int TY, int NX>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 1 ? 2 : 1)
-    k_full_search(const __grid_constant__ FullSearchBatch b, const int box_h, const int pw, const int cstride)
-{
-    constexpr int SPW = Traits<T>::SPW;
-    constexpr int UW = 4 * SPW;                 // unit width in samples
-    constexpr int NU = (CTU / UW) * (CTU / 16); // units per CTU
-    constexpr int G = 32 / NU;                  // candidate groups per warp
-    constexpr int NG = kThreads / NU;           // candidate groups per CTA
-    constexpr int WPB = 8 / SPW;                // words per 8-sample block row
-    constexpr int NBH = 4 / WPB;                // 8x8 blocks across a unit
-    constexpr int NB = 2 * NBH;                 // 8x8 blocks in a unit
-    constexpr int NC = TY * NX;                 // candidates per tile
-    constexpr int LNC = NC == 16 ? 4 : (NC == 8 ? 3 : (NC == 4 ? 2 : (NC == 2 ? 1 : 0)));
-    constexpr int KS = 8 + LNC;                 // L1 < 256 takes 8 bits
-    constexpr int DMAX = CTU == 64 ? 3 : (CTU == 32 ? 2 : 1);
-    constexpr int NKEY = keys_per_ctu(DMAX);
-    constexpr int B0 = SPW == 4 ? 0 : 1;        // lane bits already spent inside a 16x16
-    static_assert((1 << LNC) == NC, "tile size must be a power of two");
-    static_assert(NU <= 32 && 32 % NU == 0, "a CTU's units must tile a warp");
-    // Key widths: SAD < 2^(32-KS) wherever a level holds >= 2 candidates
-    // (8-bit 32x32 <= 261120, 10-bit 32x32 <= 1047552, 10-bit 16x16 <= 261888);
-    // single-candidate levels fold the sum directly into 64 bits.
+    using S = Shape<T, CTU, RP>;
+    constexpr int TY = S::TY, P4 = S::P4, ES = S::ES, NT = S::NT;
+    constexpr int NR = 8 + TY - 1;  // window rows read per 8x8 block
 
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    // staging: the TMA box, dense (box_h rows x pw words); then SPW shifted copies
-    uint32_t *const stage =
-        reinterpret_cast<uint32_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    uint32_t *const copies = stage + box_h * pw;
+    uint8_t *const sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    uint32_t *const E = reinterpret_cast<uint32_t *>(sm);             // box_h rows x P4 words
+    T *const stage = reinterpret_cast<T *>(sm + b.stage_off);         // box_h rows x P4 samples, inside E
+    T *const curs = reinterpret_cast<T *>(sm + b.e_bytes);            // CTU x CTU samples
+    uint32_t *const a8 = reinterpret_cast<uint32_t *>(sm + b.e_bytes + CTU * CTU * ES);  // 10-bit block sums
     __shared__ __align__(8) uint64_t bar;
-    __shared__ unsigned long long cta_keys[NKEY];
-    __shared__ unsigned long long *s_out_keys;  // this CTU's global keys (read after the main loop)
-    // 8-bit: running best keys live in shared memory ([slot][thread], conflict-free)
-    // to keep the main loop within 128 registers
-    constexpr bool kSmemBest = SPW == 4;
-    __shared__ unsigned long long s_best[kSmemBest ? NB + DMAX : 1][kSmemBest ? kThreads : 1];
+    __shared__ uint32_t s_k8[S::NB8];                          // 8x8 keys
+    __shared__ unsigned long long s_kup[keys_per_ctu(S::DMAX - 1)];  // larger CUs
 
-    int ii = 0;  // the batch item of this CTA row
-    while (ii + 1 < b.n && static_cast<int>(blockIdx.y) >= b.item[ii + 1].cta_begin) ++ii;
-    const FullSearchItem &a = b.item[ii];
-    const CUtensorMap *ref_map = &b.map[ii];
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    const int u = lane % NU;
-    const int g = lane / NU;
-    const int ctu_idx = blockIdx.y - a.cta_begin;
-    const int W8 = (a.W + 7) & ~7;
-    const int ctu_cols = (W8 + CTU - 1) / CTU;
-    const int x0 = (ctu_idx % ctu_cols) * CTU;
-    const int y0 = (ctu_idx / ctu_cols) * CTU;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int R = b.R, K = 2 * R + 1;
+    int ii = 0;  // the frame of this CTA
+    while (ii + 1 < b.n && static_cast<int>(blockIdx.x) >= b.item[ii + 1].cta_begin) ++ii;
+    const FullSearchItem &a = b.item[ii];
+    const int local = blockIdx.x - a.cta_begin;
+    const int ctu_idx = local / b.warp_tiles, wt = local - ctu_idx * b.warp_tiles;
+    const int W8 = (a.W + 7) & ~7, H8 = (a.H + 7) & ~7;
+    const int ctu_cols = (W8 + CTU - 1) / CTU;
+    const int x0 = (ctu_idx % ctu_cols) * CTU, y0 = (ctu_idx / ctu_cols) * CTU;
+    auto band_dy0 = [&](int t) {
+        int v = (t / K) * TY - R;
+        if (K >= TY) v = min(v, R - TY + 1);
+        return v;
+    };
+    const int tf = wt * 32, tl = min(wt * 32 + 31, b.ntasks - 1);
+    const int rlo = band_dy0(tf) + R;                   // first window row, relative to y0 - R
+    const int rows = band_dy0(tl) + R + TY - 1 + CTU - rlo;
+    const int gy0 = y0 - R + rlo;                       // frame row of window row 0
+    const int sy0 = min(max(gy0, 0), a.H - 1);          // window rows clamp into staged rows [sy0, sy0 + box_h)
 
     if (tid == 0) {
         mbar_init(&bar, 1);
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(ref_map)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&b.map[ii])) : "memory");
     }
-    for (int i = tid; i < NKEY; i += kThreads) cta_keys[i] = ~0ull;
-    if (tid == 0) s_out_keys = a.keys + static_cast<long>(ctu_idx) * NKEY;
+    for (int i = tid; i < S::NB8; i += NT) s_k8[i] = 0xffffffffu;
+    for (int i = tid; i < keys_per_ctu(S::DMAX - 1); i += NT) s_kup[i] = ~0ull;
     __syncthreads();
     if (tid == 0) {
-        mbar_arrive_expect_tx(&bar, static_cast<uint32_t>(box_h * pw) * 4u);
-        tma_load_2d(stage, ref_map, &bar, x0 - b.Rp, y0 - R);
+        mbar_arrive_expect_tx(&bar, static_cast<uint32_t>((b.box_h * P4 + CTU * CTU) * ES));
+        tma_load_2d(stage, &b.map[ii], &bar, x0 - b.Rp, sy0);
+        tma_load_2d(curs, &b.cur_map[ii], &bar, x0, y0);
     }
 
-    // Current unit -> registers while the window is in flight.
-    int ux, uy;
-    unit_origin<SPW>(u, ux, uy);
-    uint32_t cur[16][4];
-    {
-        const char *base = static_cast<const char *>(a.cur);
-        const int gx = x0 + ux;
-        const bool full = gx + UW <= a.W;
+    // lane task and candidate codes; a candidate row past +R (only when
+    // 2R + 1 < TY) never wins: mul 0, code ~0
+    const int t = min(wt * 32 + lane, b.ntasks - 1);
+    const int dx = t % K - R, dy0 = band_dy0(t);
+    uint32_t mul[TY], code[TY];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int gy = min(y0 + uy + j, a.H - 1);
-            const char *row = base + static_cast<long>(gy) * a.pitch_bytes;
-            if (full) {
-                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(row + static_cast<long>(gx) * sizeof(T)));
-                cur[j][0] = v.x;
-                cur[j][1] = v.y;
-                cur[j][2] = v.z;
-                cur[j][3] = v.w;
-            } else {
-                const T *rp = reinterpret_cast<const T *>(row);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    uint32_t w = 0;
-#pragma unroll
-                    for (int e = 0; e < SPW; ++e) {
-                        const int x = min(gx + c * SPW + e, a.W - 1);
-                        w |= static_cast<uint32_t>(rp[x]) << (e * (32 / SPW));
-                    }
-                    cur[j][c] = w;
-                }
-            }
-        }
+    for (int i = 0; i < TY; ++i) {
+        const int dy = dy0 + i;
+        const bool ok = dy <= R;
+        mul[i] = ok ? 65536u : 0u;
+        code[i] = ok ? static_cast<uint32_t>((abs(dx) + abs(dy)) * 2 * K + 2 * (dy + R) + (dx > 0)) : 0xffffffffu;
     }
-
-    // Tiles of this slice; tiles are ordered by candidate row, so the slice
-    // needs window rows [r_lo, r_hi) only.
-    const int tile_begin = blockIdx.x * b.tiles_per_slice;
-    const int tile_end = min(tile_begin + b.tiles_per_slice, b.ntiles);
-    const int n_iter = (tile_end - tile_begin + NG - 1) / NG;  // uniform across the CTA
-    const int r_lo = (__ldg(b.tiles + tile_begin) >> 16) + R;
-    const int r_hi = min(box_h, (__ldg(b.tiles + tile_end - 1) >> 16) + R + TY - 1 + CTU);
 
     const bool ok = mbar_wait_bounded(&bar, 0);
     if (__syncthreads_or(!ok)) {
@@ -268,309 +241,388 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 1 ? 2 : 1)
         return;
     }
 
-    // Out-of-frame samples of the window take the clamped sample.
-    {
-        const int gx0 = x0 - b.Rp, gy0 = y0 - R;
-        const int ww = pw * SPW;
-        if (gx0 < 0 || gy0 < 0 || gx0 + ww > a.W || gy0 + box_h > a.H) {
-            T *w0 = reinterpret_cast<T *>(stage);
-            for (int i = r_lo * ww + tid; i < r_hi * ww; i += kThreads) {
-                const int row = i / ww, col = i - row * ww;
-                const int gx = gx0 + col, gy = gy0 + row;
-                const int cx = min(max(gx, 0), a.W - 1), cy = min(max(gy, 0), a.H - 1);
-                if (cx != gx || cy != gy) w0[i] = w0[(cy - gy0) * ww + (cx - gx0)];
-            }
-            __syncthreads();
+    // Current CTU: edge replication into the 8-aligned pad.
+    if (x0 + CTU > a.W || y0 + CTU > a.H) {
+        for (int i = tid; i < CTU * CTU; i += NT) {
+            const int row = i / CTU, col = i - row * CTU;
+            const int gx = x0 + col, gy = y0 + row;
+            if (gx < W8 && gy < H8 && (gx >= a.W || gy >= a.H))
+                curs[i] = curs[(min(gy, a.H - 1) - y0) * CTU + (min(gx, a.W - 1) - x0)];
         }
     }
-    // Shifted copies: copy k word w of a row = samples [SPW*w + k, SPW*w + k + SPW).
+    // In-place expansion of the window (the staged rows sit at the end of
+    // E).  Phase 1: rows of E that end before the staged rows; phase 2: the
+    // staged words of the remaining rows go to registers first.  Window row
+    // r is staged row clamp(gy0 + r) - sy0 <= r.
     {
-        const int nw = (r_hi - r_lo) * pw;
-        for (int i = tid; i < SPW * nw; i += kThreads) {
-            const int k = i / nw, rem = i - k * nw;
-            const int row = r_lo + rem / pw, w = rem % pw;
-            const uint32_t lo = stage[row * pw + w];
-            const uint32_t hi = (w + 1 < pw) ? stage[row * pw + w + 1] : 0u;
-            copies[k * cstride + copy_off(row, w, pw)] = __funnelshift_r(lo, hi, k * (32 / SPW));
+        const int gx0 = x0 - b.Rp;
+        auto srow_of = [&](int r) { return stage + (min(max(gy0 + r, 0), a.H - 1) - sy0) * P4; };
+        const int r1 = min(b.phase1_rows, rows);
+        const int n1 = r1 * S::CPR;
+        for (int i = tid; i < n1; i += NT) {
+            const int r = i / S::CPR, m = i - r * S::CPR;
+            uint32_t w[S::NW];
+            fetch_chunk<T, P4>(srow_of(r), m, gx0, a.W, w);
+            emit_chunk<ES>(w, E + r * P4 + 4 * m);
+        }
+        const int n2 = (rows - r1) * S::CPR;
+        uint32_t hold[S::MAXC][S::NW];
+#pragma unroll
+        for (int c = 0; c < S::MAXC; ++c) {
+            const int i = tid + c * NT;
+            if (i < n2) fetch_chunk<T, P4>(srow_of(r1 + i / S::CPR), i % S::CPR, gx0, a.W, hold[c]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < S::MAXC; ++c) {
+            const int i = tid + c * NT;
+            if (i < n2) emit_chunk<ES>(hold[c], E + (r1 + i / S::CPR) * P4 + 4 * (i % S::CPR));
+        }
+    }
+    if constexpr (ES == 2) {
+        // packed (even, odd) sample sums of every 8x8 block of the CTU
+        for (int blk = tid; blk < S::NB8; blk += NT) {
+            const int bx = (blk % (CTU / 8)) * 8, by = (blk / (CTU / 8)) * 8;
+            uint32_t s = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(curs + (by + j) * CTU + bx);
+                s += v.x + v.y + v.z + v.w;
+            }
+            a8[blk] = s;
         }
     }
     __syncthreads();
 
-    // Running bests: 8x8 blocks of the unit, then one per coarser depth.
-    unsigned long long rbest[kSmemBest ? 1 : NB + DMAX];
+    // ---- search: warp = quadrant, its 8x8 blocks in Z order ----
+    const int qx = (warp & 1) * S::Q, qy = (warp >> 1) * S::Q;
+    const uint32_t one = b.one;
+    const uint32_t *lp = E + (dy0 + R - rlo + qy) * P4 + (dx + b.Rp + qx);
+    uint32_t s16[TY], s32[TY];
 #pragma unroll
-    for (int q = 0; q < NB + DMAX; ++q) {
-        if constexpr (kSmemBest) s_best[q][tid] = ~0ull;
-        else rbest[q] = ~0ull;
+    for (int i = 0; i < TY; ++i) {
+        s16[i] = 0;
+        s32[i] = 0;
     }
-    auto best_ref = [&](int q) -> unsigned long long & {
-        if constexpr (kSmemBest) return s_best[q][tid];
-        else return rbest[q];
-    };
-
-    for (int it = 0; it < n_iter; ++it) {
-        // the G groups of a warp take G consecutive tiles (paired word classes)
-        int t = tile_begin + G * (warp + (kThreads / 32) * it) + g;
-        if (t >= tile_end) t = tile_begin;  // a duplicate tile cannot change a min
-        const int packed = __ldg(b.tiles + t);
-        const int dxb = static_cast<int>(static_cast<short>(packed & 0xffff));
-        const int dyb = packed >> 16;
-        const int k = dxb & (SPW - 1);
-        const uint32_t *cp = copies + k * cstride + (ux + dxb + b.Rp - k) / SPW;
-        const int row0 = uy + dyb + R;
-
-        uint32_t acc[NB][NC];
+#pragma unroll 1
+    for (int bq = 0; bq < S::NBQ; ++bq) {
+        const int zx = (bq & 1) | ((bq >> 1) & 2), zy = ((bq >> 1) & 1) | ((bq >> 2) & 2);
+        const int bx = zx * 8, by = zy * 8;
+        const bool present = x0 + qx + bx < W8 && y0 + qy + by < H8;
+        uint32_t acc[TY];
 #pragma unroll
-        for (int b = 0; b < NB; ++b)
+        for (int i = 0; i < TY; ++i) acc[i] = 0;
+        if (present) {
+            const uint32_t *bp = lp + by * P4 + bx;
+            const T *cp = curs + (qy + by) * CTU + qx + bx;
+            if constexpr (ES == 1) {
+                uint2 c[8];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) acc[b][c] = 0;
-
+                for (int j = 0; j < 8; ++j) c[j] = *reinterpret_cast<const uint2 *>(cp + j * CTU);
 #pragma unroll
-        for (int rr = 0; rr < 16 + TY - 1; ++rr) {
-            uint32_t w[NX + 3];
-            const uint32_t *rowp = cp + copy_off(row0 + rr, 0, pw);
+                for (int r = 0; r < NR; ++r) {
+                    const uint32_t w0 = bp[r * P4], w1 = bp[r * P4 + 4];
+                    // all candidates on word 0, then on word 1: no back-to-back dependence
 #pragma unroll
-            for (int c = 0; c < NX + 3; ++c) w[c] = rowp[c];
-#pragma unroll
-            for (int i = 0; i < TY; ++i) {
-                const int j = rr - i;  // current row paired with ref row rr at dy index i
-                if (j < 0 || j >= 16) continue;
-                const int bv = j >> 3;
-#pragma unroll
-                for (int n = 0; n < NX; ++n)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int bb = bv * NBH + c / WPB;
-                        acc[bb][i * NX + n] = sad_acc<SPW>(cur[j][c], w[n + c], acc[bb][i * NX + n]);
+                    for (int i = 0; i < TY; ++i) {
+                        const int j = r - i;
+                        if (j >= 0 && j < 8) acc[i] = sad_acc<4>(c[j].x, w0, acc[i]);
                     }
+#pragma unroll
+                    for (int i = 0; i < TY; ++i) {
+                        const int j = r - i;
+                        if (j >= 0 && j < 8) acc[i] = sad_acc<4>(c[j].y, w1, acc[i]);
+                    }
+                }
+            } else {
+                uint4 c[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) c[j] = *reinterpret_cast<const uint4 *>(cp + j * CTU);
+                const uint32_t sa = a8[((qy + by) / 8) * (CTU / 8) + (qx + bx) / 8];
+                // candidate i is complete after window row i + 7: there
+                // SAD = sum(a) + sum(b) - 2 sum(min), per packed half
+                uint32_t rs[NR];
+                uint32_t sb = 0;
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const uint32_t w0 = bp[r * P4], w1 = bp[r * P4 + 2], w2 = bp[r * P4 + 4], w3 = bp[r * P4 + 6];
+                    rs[r] = (w0 + w1) + (w2 + w3);
+#pragma unroll
+                    for (int i = 0; i < TY; ++i) {
+                        const int j = r - i;
+                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].x, w0), one, acc[i]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < TY; ++i) {
+                        const int j = r - i;
+                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].y, w1), one, acc[i]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < TY; ++i) {
+                        const int j = r - i;
+                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].z, w2), one, acc[i]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < TY; ++i) {
+                        const int j = r - i;
+                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].w, w3), one, acc[i]);
+                    }
+                    if (r < 8) sb += rs[r];
+                    else sb = sb + rs[r] - rs[r - 8];
+                    if (r >= 7) {
+                        const int i = r - 7;
+                        const uint32_t d = umad(acc[i], 0xfffffffeu, sa + sb);
+                        acc[i] = (d & 0xffffu) + (d >> 16);
+                    }
+                }
+            }
+            // 8x8 key
+            const uint32_t key = __reduce_min_sync(0xffffffffu, lane_key32<TY>(acc, mul, code));
+            if (lane == 0) atomicMin(&s_k8[((qy + by) / 8) * (CTU / 8) + (qx + bx) / 8], key);
+        }
+#pragma unroll
+        for (int i = 0; i < TY; ++i) s16[i] = umad(acc[i], one, s16[i]);
+
+        if constexpr (S::Q >= 16) {
+            if ((bq & 3) == 3) {  // 16x16 CU complete
+                const int cx = (qx + bx) / 16, cy = (qy + by) / 16;
+                if (x0 + cx * 16 < W8 && y0 + cy * 16 < H8) {
+                    unsigned long long key;
+                    if constexpr (S::K16_32) key = __reduce_min_sync(0xffffffffu, lane_key32<TY>(s16, mul, code));
+                    else key = warp_min_u64(lane_key64<TY>(s16, mul, code));
+                    if (lane == 0) atomicMin(&s_kup[key_offset(S::DMAX - 1) + cy * (CTU / 16) + cx], key);
+                }
+#pragma unroll
+                for (int i = 0; i < TY; ++i) {
+                    s32[i] = umad(s16[i], one, s32[i]);
+                    s16[i] = 0;
+                }
             }
         }
-
-        // Tile-local tie-break codes: (L1 << LNC) | c orders the tile's
-        // candidates by (L1, dy, dx) because dy, dx grow with c.
-        uint32_t code[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            int dx, dy;
-            cand_of<SPW, NX>(c, dxb, dyb, dx, dy);
-            code[c] = (static_cast<uint32_t>(abs(dx) + abs(dy)) << LNC) | static_cast<uint32_t>(c);
-        }
-
-        // depth DMAX: the unit's own 8x8 blocks
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            uint32_t kmin = 0xffffffffu;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const uint32_t kk = (acc[b][c] << KS) | code[c];
-                kmin = kk < kmin ? kk : kmin;
-            }
-            fold_key32<SPW, NX, KS, LNC>(best_ref(b), kmin, dxb, dyb, R, K);
-        }
-
-        // unit sums
-        uint32_t s[NC];
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            uint32_t v = 0;
-#pragma unroll
-            for (int b = 0; b < NB; ++b) v += acc[b][c];
-            s[c] = v;
-        }
-        int off = 0;
-        // depth DMAX-1 (16x16)
-        if constexpr (B0 == 0) {
-            level_argmin<SPW, NX, NC, NC, KS, LNC>(best_ref(NB + DMAX - 1), s, code, off, dxb, dyb, R, K);
-        } else {
-            scatter_step<NC, NC>(s, off, lane, 0);
-            level_argmin<SPW, NX, NC, after_step<NC>(), KS, LNC>(best_ref(NB + DMAX - 1), s, code, off, dxb, dyb, R,
-                                                                 K);
-        }
-        // depth DMAX-2 (32x32)
-        if constexpr (DMAX >= 2) {
-            constexpr int C0 = (B0 == 0) ? NC : after_step<NC>();
-            constexpr int C1 = after_step<C0>();
-            constexpr int C2 = after_step<C1>();
-            scatter_step<NC, C0>(s, off, lane, B0);
-            scatter_step<NC, C1>(s, off, lane, B0 + 1);
-            level_argmin<SPW, NX, NC, C2, KS, LNC>(best_ref(NB + DMAX - 2), s, code, off, dxb, dyb, R, K);
-            // depth DMAX-3 (64x64)
-            if constexpr (DMAX >= 3) {
-                constexpr int C3 = after_step<C2>();
-                constexpr int C4 = after_step<C3>();
-                scatter_step<NC, C2>(s, off, lane, B0 + 2);
-                scatter_step<NC, C3>(s, off, lane, B0 + 3);
-                level_argmin<SPW, NX, NC, C4, KS, LNC>(best_ref(NB + DMAX - 3), s, code, off, dxb, dyb, R, K);
+        if constexpr (S::Q >= 32) {
+            if ((bq & 15) == 15) {  // 32x32 CU complete
+                const int cx = (qx + bx) / 32, cy = (qy + by) / 32;
+                if (x0 + cx * 32 < W8 && y0 + cy * 32 < H8) {
+                    const unsigned long long key = warp_min_u64(lane_key64<TY>(s32, mul, code));
+                    if (lane == 0) atomicMin(&s_kup[key_offset(S::DMAX - 2) + cy * (CTU / 32) + cx], key);
+                }
             }
         }
     }
 
-    // Merge: per-thread bests -> min over the lanes of a warp that share the
-    // CU -> CTA keys (shared atomics) -> global keys (atomics across slices).
-    // Lane bits: unit bits below log2(NU) (Z-order: 8-bit 2 per level from
-    // 32x32 up; 10-bit one for the 16x16 half, then 2 per level), group bits above.
-    constexpr int LNU = NU == 32 ? 5 : (NU == 16 ? 4 : (NU == 8 ? 3 : (NU == 4 ? 2 : (NU == 2 ? 1 : 0))));
-    constexpr unsigned GROUP_BITS = 0x1fu & ~((1u << LNU) - 1u);
+    // CTU level: the four quadrants' sums.
+    __syncthreads();  // every warp is done with E: reuse it
+    uint32_t *xch = E;  // [warp][i][lane]
+    {
+        const uint32_t(&top)[TY] = (S::Q >= 16) ? s32 : s16;
 #pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        const unsigned long long v = warp_min_over(best_ref(b), GROUP_BITS);
-        if ((lane & GROUP_BITS) == 0) {
-            const int bx = ux + 8 * (b % NBH), by = uy + 8 * (b / NBH);
-            const int li = (by / 8) * (CTU / 8) + bx / 8;
-            atomicMin(&cta_keys[key_offset(DMAX) + li], v);
-        }
-    }
-#pragma unroll
-    for (int d = 0; d < DMAX; ++d) {
-        // unit bits inside a depth-d CU: 8-bit 2*(DMAX-1-d), 10-bit 2*(DMAX-1-d)+1
-        const int inner = 2 * (DMAX - 1 - d) + B0;
-        const unsigned m = GROUP_BITS | ((1u << inner) - 1u);
-        const unsigned long long v = warp_min_over(best_ref(NB + d), m);
-        if ((lane & m) == 0) {
-            const int S = CTU >> d;
-            const int li = (uy / S) * (CTU / S) + ux / S;
-            atomicMin(&cta_keys[key_offset(d) + li], v);
-        }
+        for (int i = 0; i < TY; ++i) xch[(warp * TY + i) * 32 + lane] = top[i];
     }
     __syncthreads();
-    for (int i = tid; i < NKEY; i += kThreads) {
-        const unsigned long long v = cta_keys[i];
-        if (v != ~0ull) atomicMin(s_out_keys + i, v);
+    if (warp == 0) {
+        uint32_t tot[TY];
+#pragma unroll
+        for (int i = 0; i < TY; ++i)
+            tot[i] = xch[i * 32 + lane] + xch[(TY + i) * 32 + lane] + xch[(2 * TY + i) * 32 + lane] +
+                     xch[(3 * TY + i) * 32 + lane];
+        const unsigned long long key = warp_min_u64(lane_key64<TY>(tot, mul, code));
+        if (lane == 0) atomicMin(&s_kup[0], key);
+    }
+    __syncthreads();
+
+    // Re-encode (SAD << 16 | code) as (SAD << 32 | tie-break) and merge.
+    unsigned long long *out = a.keys + static_cast<long>(ctu_idx) * S::NKEY;
+    constexpr int NUP = keys_per_ctu(S::DMAX - 1);
+    for (int i = tid; i < S::NKEY; i += NT) {
+        const unsigned long long v = i < NUP ? s_kup[i] : static_cast<unsigned long long>(s_k8[i - NUP]);
+        if (i < NUP ? v == ~0ull : v == 0xffffffffull) continue;
+        const uint32_t sad = static_cast<uint32_t>(v >> 16);
+        const int c = static_cast<int>(v & 0xffffu);
+        const int l1 = c / (2 * K), rem = c - l1 * 2 * K;
+        const int dyv = (rem >> 1) - R;
+        const int adx = l1 - abs(dyv);
+        const int dxv = (rem & 1) ? adx : -adx;
+        const uint32_t tb = static_cast<uint32_t>(l1 * K * K + (dyv + R) * K + (dxv + R));
+        atomicMin(out + i, (static_cast<unsigned long long>(sad) << 32) | tb);
     }
 }
 
-constexpr int kTileDY = 4;
-constexpr int kTileNX = 2;
-
-// Largest dynamic shared memory already granted to k_full_search<T, CTU>.
-template <typename T, int CTU> int &granted_smem()
+// Largest dynamic shared memory already granted to a kernel instance.
+template <typename T, int CTU, int RP> int &granted_smem()
 {
     static int bytes = -1;
     return bytes;
 }
 
-template <typename T, int CTU> cudaError_t ensure_smem(int smem)
+template <typename T, int CTU, int RP> cudaError_t ensure_smem(int smem)
 {
-    if (granted_smem<T, CTU>() >= smem) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_full_search<T, CTU, kTileDY, kTileNX>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) granted_smem<T, CTU>() = smem;
+    if (granted_smem<T, CTU, RP>() >= smem) return cudaSuccess;
+    cudaError_t e =
+        cudaFuncSetAttribute(k_full_search<T, CTU, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) granted_smem<T, CTU, RP>() = smem;
     return e;
 }
 
-template <typename T, int CTU>
-cudaError_t launch_t(const FullSearchBatch &b, const FullSearchPlan &p, int nslices, int total_ctus, cudaStream_t s)
+template <typename T, int CTU, int RP> int occupancy_t(int smem)
 {
-    auto kern = k_full_search<T, CTU, kTileDY, kTileNX>;
-    cudaError_t e = ensure_smem<T, CTU>(p.smem_bytes);
-    if (e != cudaSuccess) return e;
-    dim3 grid(nslices, total_ctus);
-    kern<<<grid, kThreads, p.smem_bytes, s>>>(b, p.box_h, p.pitch_words, p.copy_stride);
-    return cudaGetLastError();
-}
-
-template <typename T, int CTU>
-int occupancy_t(int smem)
-{
-    auto kern = k_full_search<T, CTU, kTileDY, kTileNX>;
-    if (ensure_smem<T, CTU>(smem) != cudaSuccess) return 1;
+    if (ensure_smem<T, CTU, RP>(smem) != cudaSuccess) return 1;
     int n = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kThreads, smem) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_full_search<T, CTU, RP>, Shape<T, CTU, RP>::NT, smem) !=
+        cudaSuccess)
+        return 1;
     return n > 0 ? n : 1;
 }
 
+template <typename T, int CTU, int RP>
+cudaError_t launch_t(const FullSearchBatch &b, int smem, cudaStream_t s)
+{
+    using S = Shape<T, CTU, RP>;
+    cudaError_t e = ensure_smem<T, CTU, RP>(smem);
+    if (e != cudaSuccess) return e;
+    const int n2 = (b.box_h - std::min(b.phase1_rows, b.box_h)) * S::CPR;
+    if (n2 > S::MAXC * S::NT || b.box_h > S::MAX_ROWS || 4 * S::TY * 32 * 4 > b.e_bytes) return cudaErrorInvalidValue;
+    k_full_search<T, CTU, RP><<<b.total, S::NT, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+// Dispatch on (bit depth, CTU, window margin class).
+template <typename F> cudaError_t dispatch(int bit_depth, int ctu, int Rp, F &&f)
+{
+    const bool wide = Rp > 32;
+    if (bit_depth == 8) {
+        if (ctu == 64) return wide ? f.template run<uint8_t, 64, 64>() : f.template run<uint8_t, 64, 32>();
+        if (ctu == 32) return f.template run<uint8_t, 32, 64>();
+        return f.template run<uint8_t, 16, 64>();
+    }
+    if (ctu == 64) return wide ? f.template run<uint16_t, 64, 64>() : f.template run<uint16_t, 64, 32>();
+    if (ctu == 32) return f.template run<uint16_t, 32, 64>();
+    return f.template run<uint16_t, 16, 64>();
+}
+
+int rp_class(int ctu, int Rp) { return (ctu == 64 && Rp <= 32) ? 32 : 64; }
+
+struct OccupancyOp {
+    int smem, n;
+    template <typename T, int CTU, int RP> cudaError_t run()
+    {
+        n = occupancy_t<T, CTU, RP>(smem);
+        return cudaSuccess;
+    }
+};
+
+struct LaunchOp {
+    const FullSearchBatch &b;
+    int smem;
+    cudaStream_t s;
+    template <typename T, int CTU, int RP> cudaError_t run() { return launch_t<T, CTU, RP>(b, smem, s); }
+};
+
 }  // namespace
+
+FullSearchPlan full_search_plan(int bit_depth, int ctu, int R)
+{
+    FullSearchPlan p{};
+    const int es = bit_depth == 8 ? 1 : 2;
+    const int K = 2 * R + 1;
+    p.Rp = (R + 15) / 16 * 16;
+    const int RPc = rp_class(ctu, p.Rp);
+    p.band = kFsBand;
+    p.nbands = (K + kFsBand - 1) / kFsBand;
+    p.ntasks = K * p.nbands;
+    p.warp_tiles = (p.ntasks + 31) / 32;
+    auto dy0 = [&](int t) {
+        int v = (t / K) * kFsBand - R;
+        if (K >= kFsBand) v = std::min(v, R - kFsBand + 1);
+        return v;
+    };
+    int rows = 0;
+    for (int w = 0; w < p.warp_tiles; ++w) {
+        const int tf = w * 32, tl = std::min(w * 32 + 31, p.ntasks - 1);
+        rows = std::max(rows, dy0(tl) - dy0(tf) + kFsBand - 1 + ctu);
+    }
+    p.P4 = ctu + 2 * RPc;
+    p.box_w = p.P4;
+    p.box_h = rows;
+    p.e_bytes = (rows * p.P4 * 4 + 127) / 128 * 128;
+    const int stage_bytes = rows * p.P4 * es;
+    p.stage_off = (p.e_bytes - stage_bytes) / 128 * 128;
+    p.phase1_rows = p.stage_off / (4 * p.P4);
+    const int cur_bytes = ctu * ctu * es;
+    const int a8_bytes = es == 2 ? (ctu / 8) * (ctu / 8) * 4 : 0;
+    p.buf_bytes = (p.e_bytes + cur_bytes + a8_bytes + 127) / 128 * 128;
+    p.smem_bytes = p.buf_bytes + 128;  // + alignment slack
+    return p;
+}
+
+void fill_full_search_batch(FullSearchBatch &b, const FullSearchPlan &p, int R)
+{
+    b.R = R;
+    b.Rp = p.Rp;
+    b.ntasks = p.ntasks;
+    b.warp_tiles = p.warp_tiles;
+    b.box_h = p.box_h;
+    b.e_bytes = p.e_bytes;
+    b.stage_off = p.stage_off;
+    b.phase1_rows = p.phase1_rows;
+    b.buf_bytes = p.buf_bytes;
+    b.one = 1;
+}
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+}  // namespace
+
+int encode_plane_map(CUtensorMap *map, const void *plane, int W, int H, long pitch_bytes, int bit_depth, int box_w,
+                     int box_h)
+{
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!g_encode) return -1;
+    const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(W), static_cast<cuuint64_t>(H)};
+    const cuuint64_t gstride[1] = {static_cast<cuuint64_t>(pitch_bytes)};
+    const cuuint32_t box[2] = {static_cast<cuuint32_t>(box_w), static_cast<cuuint32_t>(box_h)};
+    const cuuint32_t estride[2] = {1, 1};
+    const CUtensorMapDataType dt = bit_depth == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    return static_cast<int>(g_encode(map, dt, 2, const_cast<void *>(plane), gdim, gstride, box, estride,
+                                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE));
+}
+
+int encode_item_maps(FullSearchBatch &b, int k, const void *cur, const void *ref, int W, int H, long pitch_bytes,
+                     int bit_depth, int ctu, const FullSearchPlan &p)
+{
+    const int r = encode_plane_map(&b.map[k], ref, W, H, pitch_bytes, bit_depth, p.box_w, p.box_h);
+    if (r != 0) return r;
+    return encode_plane_map(&b.cur_map[k], cur, W, H, pitch_bytes, bit_depth, ctu, ctu);
+}
 
 cudaError_t prepare_full_search(int bit_depth, int ctu, int R)
 {
-    const FullSearchPlan p = full_search_plan(bit_depth, ctu, R);
-    // launch_t raises the attribute on first use; doing it here keeps the
-    // attribute call out of any later stream capture
-    int n = bit_depth == 8 ? (ctu == 64 ? occupancy_t<uint8_t, 64>(p.smem_bytes)
-                                        : (ctu == 32 ? occupancy_t<uint8_t, 32>(p.smem_bytes)
-                                                     : occupancy_t<uint8_t, 16>(p.smem_bytes)))
-                           : (ctu == 64 ? occupancy_t<uint16_t, 64>(p.smem_bytes)
-                                        : (ctu == 32 ? occupancy_t<uint16_t, 32>(p.smem_bytes)
-                                                     : occupancy_t<uint16_t, 16>(p.smem_bytes)));
-    (void)n;
+    full_search_ctas_per_sm(bit_depth, ctu, R);  // raises the shared-memory attribute outside any capture
     return cudaGetLastError();
 }
 
 int full_search_ctas_per_sm(int bit_depth, int ctu, int R)
 {
     const FullSearchPlan p = full_search_plan(bit_depth, ctu, R);
-    if (bit_depth == 8)
-        return ctu == 64 ? occupancy_t<uint8_t, 64>(p.smem_bytes)
-                         : (ctu == 32 ? occupancy_t<uint8_t, 32>(p.smem_bytes) : occupancy_t<uint8_t, 16>(p.smem_bytes));
-    return ctu == 64 ? occupancy_t<uint16_t, 64>(p.smem_bytes)
-                     : (ctu == 32 ? occupancy_t<uint16_t, 32>(p.smem_bytes) : occupancy_t<uint16_t, 16>(p.smem_bytes));
+    OccupancyOp f{p.smem_bytes, 1};
+    dispatch(bit_depth, ctu, p.Rp, f);
+    return f.n;
 }
 
-FullSearchPlan full_search_plan(int bit_depth, int ctu, int R)
+cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchBatch &b, cudaStream_t s)
 {
-    FullSearchPlan p{};
-    const int spw = bit_depth == 8 ? 4 : 2;
-    const int Rp = (R + 15) / 16 * 16;
-    p.tile_dy = kTileDY;
-    p.tile_nx = kTileNX;
-    p.pitch_words = (ctu + 2 * Rp) / spw;   // words per window row (a multiple of 4)
-    p.box_w = p.pitch_words * spw;
-    p.box_h = ctu + 2 * R;
-    const int raw = p.box_h * p.pitch_words + (p.box_h >> 4) + 1;
-    p.copy_stride = (raw + 31) / 32 * 32 + 16;  // copies of paired word classes 16 banks apart
-    p.smem_bytes = (p.box_h * p.pitch_words + spw * p.copy_stride) * 4 + 128;  // + alignment slack
-    const int unit_w = 4 * spw;
-    const int nu = (ctu / unit_w) * (ctu / 16);
-    p.groups = kThreads / nu;
-    return p;
-}
-
-// Candidate tiles, ordered by candidate row (dy), then by pairs of word
-// classes (0,1), (2,3): the two lane groups of a warp take the two tiles of a
-// pair, which read the same rows and columns of copies k and k+1.
-int full_search_tiles(int bit_depth, int R, int *out, int cap)
-{
-    const int spw = bit_depth == 8 ? 4 : 2;
-    const int n_ty = (2 * R + 1 + kTileDY - 1) / kTileDY;
-    int first[4], last[4], ntx[4];
-    for (int k = 0; k < spw; ++k) {
-        first[k] = -R + (((k + R) % spw) + spw) % spw;
-        last[k] = R - (((R - k) % spw) + spw) % spw;
-        const int cnt = (last[k] - first[k]) / spw + 1;
-        ntx[k] = (cnt + kTileNX - 1) / kTileNX;
-    }
-    int n = 0;
-    auto emit = [&](int dxb, int dyb) {
-        if (n < cap && out) out[n] = (dxb & 0xffff) | (dyb << 16);
-        ++n;
-    };
-    for (int ty = 0; ty < n_ty; ++ty) {
-        const int dyb = std::min(-R + kTileDY * ty, R - kTileDY + 1);
-        for (int k0 = 0; k0 < spw; k0 += 2) {
-            const int m = std::max(ntx[k0], ntx[k0 + 1]);
-            for (int tx = 0; tx < m; ++tx)
-                for (int k = k0; k < k0 + 2; ++k) {
-                    const int t = std::min(tx, ntx[k] - 1);
-                    emit(std::min(first[k] + spw * kTileNX * t, last[k] - spw * (kTileNX - 1)), dyb);
-                }
-        }
-    }
-    return n;
-}
-
-cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchBatch &b, int nslices, int total_ctus,
-                               cudaStream_t s)
-{
-    if (b.n < 1 || b.n > kMaxItems || total_ctus <= 0 || nslices <= 0) return cudaErrorInvalidValue;
+    if (b.n < 1 || b.n > kMaxItems || b.total <= 0) return cudaErrorInvalidValue;
     const FullSearchPlan p = full_search_plan(bit_depth, ctu, b.R);
-    if (bit_depth == 8) {
-        if (ctu == 64) return launch_t<uint8_t, 64>(b, p, nslices, total_ctus, s);
-        if (ctu == 32) return launch_t<uint8_t, 32>(b, p, nslices, total_ctus, s);
-        return launch_t<uint8_t, 16>(b, p, nslices, total_ctus, s);
-    }
-    if (ctu == 64) return launch_t<uint16_t, 64>(b, p, nslices, total_ctus, s);
-    if (ctu == 32) return launch_t<uint16_t, 32>(b, p, nslices, total_ctus, s);
-    return launch_t<uint16_t, 16>(b, p, nslices, total_ctus, s);
+    LaunchOp f{b, p.smem_bytes, s};
+    return dispatch(bit_depth, ctu, p.Rp, f);
 }
 
 }  // namespace ladder_impl

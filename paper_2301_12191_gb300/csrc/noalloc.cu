@@ -10,10 +10,9 @@
 // the search needs lives in the fixed array below, which the module creates
 // when the library is loaded.
 //
-// Scratch: g_noalloc_scratch holds the device status word, the candidate
-// tile list and the per-CTU argmin keys.  Its size caps the frame: at most
-// kNoallocMaxKeyBytes / (8 * keys per CTU) CTUs (3059 CTUs of 64x64; a
-// 3840x2160 frame has 2040) and kNoallocMaxTiles candidate tiles (enough for +-64).
+// Scratch: g_noalloc_scratch holds the device status word and the per-CTU
+// argmin keys.  Its size caps the frame: at most kNoallocMaxKeyBytes /
+// (8 * keys per CTU) CTUs (3083 CTUs of 64x64; a 3840x2160 frame has 2040).
 // Every call reuses the same array and leaves its contents behind; the keys
 // are reset at the start of each call.  Two calls whose work overlaps on the
 // GPU (different streams, no ordering) race on the array: order them.
@@ -30,9 +29,7 @@ namespace {
 
 constexpr size_t kNoallocScratchBytes = 2u << 20;               // 2 MiB, every device that loads the library
 constexpr size_t kNoallocStatusBytes = 256;
-constexpr int kNoallocMaxTiles = 4096;
-constexpr size_t kNoallocTileBytes = kNoallocMaxTiles * 4;      // 16 KiB
-constexpr size_t kNoallocMaxKeyBytes = kNoallocScratchBytes - kNoallocStatusBytes - kNoallocTileBytes;
+constexpr size_t kNoallocMaxKeyBytes = kNoallocScratchBytes - kNoallocStatusBytes;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
@@ -40,8 +37,6 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_lock;
 unsigned char *g_noalloc_ptr[kMaxDevices] = {};  // device address of the scratch, per device
 
-PFN_cuTensorMapEncodeTiled_v12000 g_encode_na = nullptr;
-std::once_flag g_encode_na_once;
 
 // Device address of the scratch array on the current device: looked up once
 // per device with that device current (host code may not use the symbol
@@ -121,73 +116,33 @@ extern "C" ladder_status analyze_reference_noalloc(const void *cur, const void *
     dec.leaf_mvx = out->leaf_mvx;
     dec.leaf_mvy = out->leaf_mvy;
 
-    int tiles[kNoallocMaxTiles];  // host stack, no allocation
-    const int ntiles = full_search_tiles(bit_depth, search_range, nullptr, 0);
-    if (ntiles > kNoallocMaxTiles) return LADDER_E_INVAL;
-    full_search_tiles(bit_depth, search_range, tiles, kNoallocMaxTiles);
-
     unsigned char *scratch = nullptr;
     ladder_status st = scratch_for_current_device(&scratch);
     if (st != LADDER_OK) return st;
     int *d_status = reinterpret_cast<int *>(scratch);
-    int *d_tiles = reinterpret_cast<int *>(scratch + kNoallocStatusBytes);
-    unsigned long long *d_keys =
-        reinterpret_cast<unsigned long long *>(scratch + kNoallocStatusBytes + kNoallocTileBytes);
+    unsigned long long *d_keys = reinterpret_cast<unsigned long long *>(scratch + kNoallocStatusBytes);
 
-    std::call_once(g_encode_na_once, [] {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            g_encode_na = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    });
-    if (!g_encode_na) return LADDER_E_CUDA;
     const FullSearchPlan plan = full_search_plan(bit_depth, ctu_size, search_range);
-    CUtensorMap map;
-    const cuuint64_t gdim[2] = {static_cast<cuuint64_t>(width), static_cast<cuuint64_t>(height)};
-    const cuuint64_t gstride[1] = {static_cast<cuuint64_t>(pitch_bytes)};
-    const cuuint32_t box[2] = {static_cast<cuuint32_t>(plan.box_w), static_cast<cuuint32_t>(plan.box_h)};
-    const cuuint32_t estride[2] = {1, 1};
-    if (g_encode_na(&map, bit_depth == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2,
-                    const_cast<void *>(ref), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    FullSearchBatch fb{};
+    fb.n = 1;
+    fill_full_search_batch(fb, plan, search_range);
+    fb.status = d_status;
+    fb.total = nctus * plan.warp_tiles;
+    fb.item[0] = FullSearchItem{width, height, d_keys, 0};
+    if (encode_item_maps(fb, 0, cur, ref, width, height, pitch_bytes, bit_depth, ctu_size, plan) != 0)
         return LADDER_E_CUDA;
 
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_tiles, tiles, static_cast<size_t>(ntiles) * 4, cudaMemcpyHostToDevice, s);
     FillBatch fill{};
     fill.n = 1;
     fill.item[0] = FillItem{d_keys, nkeys};
     if (e == cudaSuccess) e = launch_fill_keys(fill, s);
-    // candidate slices: whole group-iterations, about two CTAs per SM
-    int dev = 0, sms = 1;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return LADDER_E_CUDA;
     }
-    const int groups = plan.groups;
-    const int target = 2 * sms;
-    const int slices0 = (target + nctus - 1) / nctus;
-    int tps = (ntiles + slices0 - 1) / slices0;
-    tps = (tps + groups - 1) / groups * groups;
-    if (tps < groups) tps = groups;
-    const int slices = (ntiles + tps - 1) / tps;
-    FullSearchBatch fb{};
-    fb.n = 1;
-    fb.R = search_range;
-    fb.Rp = (search_range + 15) / 16 * 16;
-    fb.ntiles = ntiles;
-    fb.tiles_per_slice = tps;
-    fb.tiles = d_tiles;
-    fb.status = d_status;
-    fb.item[0] = FullSearchItem{cur, pitch_bytes, width, height, d_keys, 0};
-    fb.map[0] = map;
-    e = launch_full_search(bit_depth, ctu_size, fb, slices, nctus, s);
+    e = launch_full_search(bit_depth, ctu_size, fb, s);
     if (e == cudaSuccess) {
         // the decision kernel reads its outputs as offsets from a block base;
         // here every array is the caller's, so the base is 0 and the offsets

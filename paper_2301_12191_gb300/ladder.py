@@ -78,7 +78,6 @@ SIGNATURES = [
                                             ctypes.POINTER(ctypes.c_void_p)]),
     ("ladder_graph_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("ladder_graph_destroy", None, [ctypes.c_void_p]),
-    ("ladder_set_tiles_per_slice", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("ladder_device_bytes", ctypes.c_long, [ctypes.c_void_p]),
     ("analyze_independent", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_long, ctypes.c_int, ctypes.c_void_p]),
@@ -359,9 +358,6 @@ class Ladder:
         _call(self.handle, "ladder_capture_batch", self.handle, reqs, len(items), _stream_handle(stream),
               ctypes.byref(g))
         return Graph(g.value, (reqs, self._keep_requests))
-
-    def set_tiles_per_slice(self, tps: int):
-        _call(self.handle, "ladder_set_tiles_per_slice", self.handle, int(tps))
 
     def device_bytes(self) -> int:
         return int(load().ladder_device_bytes(self.handle))

@@ -74,9 +74,9 @@ def test_noalloc_equals_regular_entry_point_on_two_calls(W, H, bd, ctu, R, qp, s
 
 
 def test_noalloc_refuses_frames_beyond_its_scratch():
-    # 4096x3072 needs 3072 CTUs of 64x64, more than the 3059 the scratch holds
+    # 4096x3200 needs 3200 CTUs of 64x64, more than the 3083 the scratch holds
     dummy = torch.zeros((16, 4096), dtype=torch.uint8, device="cuda")
     with pytest.raises(L.LadderError) as e:
-        L.analyze_reference_noalloc(dummy.data_ptr(), dummy.data_ptr(), 4096, 3072, 4096, 8, 64, 16, 32, 0,
+        L.analyze_reference_noalloc(dummy.data_ptr(), dummy.data_ptr(), 4096, 3200, 4096, 8, 64, 16, 32, 0,
                                     L.Decisions(), 0)
     assert e.value.status == -1
