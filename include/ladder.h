@@ -226,8 +226,10 @@ LADDER_API const char *ladder_last_error(const ladder_t *ladder);
 /* Kernel timing (tracing).  Launches are always counted per kernel kind;
  * when timing is enabled every launch is also bracketed by CUDA events on
  * its own stream (a few microseconds per launch, off by default).  Kinds:
- * 0 full search, 1 SATD/cost/split of an independent rung, 2 dependent rung
- * (constraints, refinement search, SATD/cost/split), 3 key initialisation. */
+ * 0 full search, 1 SATD/cost/split of an independent rung, 2 refinement
+ * search of dependent rungs, 3 key initialisation, 4 dependent constraint
+ * derivation (rules, centres, task lists), 5 SATD/cost/split of dependent
+ * rungs. */
 LADDER_API ladder_status ladder_profile_enable(ladder_t *ladder, int enable);
 
 /* Reads the launch count and the summed event time (ms; 0 when timing was

@@ -34,7 +34,7 @@ struct Slot {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-constexpr int kKinds = 4;  // full search, decide, dependent, fill keys
+constexpr int kKinds = 6;  // full search, decide, dependent search, fill keys, dependent rules, dependent decide
 
 struct ProfEvent {
     int kind;
@@ -51,8 +51,10 @@ struct ladder {
     void *arena = nullptr;
     size_t arena_bytes = 0;
     int *d_status = nullptr;
-    uint16_t *d_rank = nullptr, *d_unrank = nullptr;  // refinement candidate order
-    int rank_bits = 0;
+    unsigned int *d_counts = nullptr;  // dependent task counters (one per CU size class)
+    unsigned long long *d_tasks[kSizeClasses] = {};
+    unsigned int *d_sums[kSizeClasses] = {};
+    unsigned int task_cap[kSizeClasses] = {};
     std::string err;
     int sm_count = 0;
     int fs_ctas_per_sm = 1;      // resident full-search CTAs per SM
@@ -84,6 +86,13 @@ ladder_status fail(ladder_t *l, ladder_status st, const char *fmt, ...)
         l->err = buf;
     }
     return st;
+}
+
+// Error of a non-zero device status word.
+ladder_status device_status_error(ladder_t *l, int status)
+{
+    if (status == kStatusTaskOverflow) return fail(l, LADDER_E_STATE, "a dependent task list overflowed");
+    return fail(l, LADDER_E_TIMEOUT, "a bounded device wait ran out");
 }
 
 ladder_status cuda_fail(ladder_t *l, cudaError_t e, const char *what)
@@ -179,7 +188,12 @@ size_t layout(const RungGeom &g, DecOffsets &o)
     o.leaf_mvx = take(n8 * 2);
     o.leaf_mvy = take(n8 * 2);
     o.dec_bytes = static_cast<long>(off);
-    o.keys = take(static_cast<size_t>(g.ctu_cols) * g.ctu_rows * keys_per_ctu(g.dmax) * 8);
+    const size_t nk = static_cast<size_t>(g.ctu_cols) * g.ctu_rows * keys_per_ctu(g.dmax);
+    o.keys = take(nk * 8);
+    o.dep_cx = take(nk * 2);
+    o.dep_cy = take(nk * 2);
+    o.dep_flags = take(nk);
+    o.dep_slot = take(nk * 4);
     return off;
 }
 
@@ -299,7 +313,8 @@ ladder_status launch_independent(ladder_t *l, const Job *jobs, int n, cudaStream
     return LADDER_OK;
 }
 
-// Dependent analyses in batched launches of at most kMaxDepItems jobs.
+// Dependent analyses in batched launches of at most kMaxDepItems jobs:
+// counters reset, rules + task lists, search, decisions.
 ladder_status launch_dependents(ladder_t *l, const Job *jobs, int n, cudaStream_t s)
 {
     for (int j0 = 0; j0 < n; j0 += kMaxDepItems) {
@@ -307,15 +322,19 @@ ladder_status launch_dependents(ladder_t *l, const Job *jobs, int n, cudaStream_
         DependentBatch b{};
         b.n = m;
         b.r = l->geo.dep_refine_range;
-        b.rank = l->d_rank;
-        b.unrank = l->d_unrank;
-        b.rank_bits = l->rank_bits;
         b.satd_mode = l->geo.satd_mode;
         b.ref_rung = l->geo.ref_rung;
         b.depth_lo = l->geo.dep_depth_lo;
         b.depth_hi = l->geo.dep_depth_hi;
         b.use_ref_mv = l->geo.dep_use_ref_mv;
         b.status = l->d_status;
+        b.counts = l->d_counts;
+        b.one = 1;
+        for (int c = 0; c < kSizeClasses; ++c) {
+            b.tasks[c] = l->d_tasks[c];
+            b.sums[c] = l->d_sums[c];
+            b.cap[c] = l->task_cap[c];
+        }
         for (int r = 0; r < l->geo.n_rungs; ++r) b.rung[r] = l->info[r];
         int total = 0;
         for (int k = 0; k < m; ++k) {
@@ -326,10 +345,14 @@ ladder_status launch_dependents(ladder_t *l, const Job *jobs, int n, cudaStream_
             total += g.ctu_cols * g.ctu_rows;
         }
         b.total_ctas = total;
-        cudaError_t e = traced(l, 2, s, [&] {
-            return launch_dependent(l->geo.bit_depth, l->geo.ctu_size, l->geo.dep_refine_range, b, s);
-        });
-        if (e != cudaSuccess) return cuda_fail(l, e, "dependent launch");
+        cudaError_t e = cudaMemsetAsync(l->d_counts, 0, kSizeClasses * sizeof(unsigned int), s);
+        if (e != cudaSuccess) return cuda_fail(l, e, "task counters");
+        e = traced(l, 4, s, [&] { return launch_dependent_rules(l->geo.ctu_size, b, s); });
+        if (e != cudaSuccess) return cuda_fail(l, e, "dependent rules launch");
+        e = traced(l, 2, s, [&] { return launch_dependent_search(l->geo.bit_depth, b, s); });
+        if (e != cudaSuccess) return cuda_fail(l, e, "dependent search launch");
+        e = traced(l, 5, s, [&] { return launch_dependent_decide(l->geo.bit_depth, l->geo.ctu_size, b, s); });
+        if (e != cudaSuccess) return cuda_fail(l, e, "dependent decide launch");
     }
     for (int k = 0; k < n; ++k) jobs[k].slot->rungs[jobs[k].rung].analysed = 2;
     return LADDER_OK;
@@ -370,9 +393,25 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
     }
     l->fs_ctas_per_sm = full_search_ctas_per_sm(geometry->bit_depth, geometry->ctu_size, geometry->ref_search_range);
 
-    const int Kr = 2 * geometry->dep_refine_range + 1;
-    const size_t rank_bytes = align_up(static_cast<size_t>(Kr) * Kr * 2, 256);
-    const size_t fixed = 256 + 2 * rank_bytes;
+    // dependent task lists: room for every CU of every size class of every
+    // dependent rung of every frame slot (a launch never holds more)
+    size_t dep_ctus = 0;
+    for (int r = 0; r < geometry->n_rungs; ++r)
+        if (r != geometry->ref_rung)
+            dep_ctus += static_cast<size_t>(l->info[r].g.ctu_cols) * l->info[r].g.ctu_rows;
+    const size_t kr2 = static_cast<size_t>(2 * geometry->dep_refine_range + 1) * (2 * geometry->dep_refine_range + 1);
+    size_t task_bytes = 0;
+    for (int c = 0; c < kSizeClasses; ++c) {
+        const int S = 8 << c;
+        const size_t per_ctu = S <= geometry->ctu_size ? static_cast<size_t>(geometry->ctu_size / S) *
+                                                             (geometry->ctu_size / S)
+                                                       : 0;
+        const size_t cap = dep_ctus * per_ctu * geometry->max_frames;
+        l->task_cap[c] = static_cast<unsigned int>(std::min<size_t>(cap, 0xffffffffu));
+        task_bytes += align_up(cap * 8, 256);
+        if (c >= kFirstSummedClass) task_bytes += align_up(cap * kr2 * 4, 256);
+    }
+    const size_t fixed = 256 + task_bytes;
     l->arena_bytes = fixed + per_slot * geometry->max_frames;
     cudaError_t e = cudaMalloc(&l->arena, l->arena_bytes);
     if (e != cudaSuccess) {
@@ -382,9 +421,18 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
     }
     char *base = static_cast<char *>(l->arena);
     l->d_status = reinterpret_cast<int *>(base);
-    l->d_rank = reinterpret_cast<uint16_t *>(base + 256);
-    l->d_unrank = reinterpret_cast<uint16_t *>(reinterpret_cast<char *>(l->d_rank) + rank_bytes);
-    while ((1 << l->rank_bits) < Kr * Kr) ++l->rank_bits;
+    l->d_counts = reinterpret_cast<unsigned int *>(base + 64);
+    {
+        char *tp = base + 256;
+        for (int c = 0; c < kSizeClasses; ++c) {
+            l->d_tasks[c] = reinterpret_cast<unsigned long long *>(tp);
+            tp += align_up(static_cast<size_t>(l->task_cap[c]) * 8, 256);
+            if (c >= kFirstSummedClass) {
+                l->d_sums[c] = reinterpret_cast<unsigned int *>(tp);
+                tp += align_up(static_cast<size_t>(l->task_cap[c]) * kr2 * 4, 256);
+            }
+        }
+    }
     char *p = base + fixed;
     l->slots.resize(geometry->max_frames);
     for (auto &sl : l->slots) {
@@ -407,13 +455,8 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
         cudaGetLastError();
         return LADDER_E_NOMEM;
     }
-    std::vector<uint16_t> rank(static_cast<size_t>(Kr) * Kr), unrank(rank.size());
-    refine_rank_tables(geometry->dep_refine_range, rank.data(), unrank.data());
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    e = cudaMemsetAsync(l->d_status, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(l->d_rank, rank.data(), rank.size() * 2, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(l->d_unrank, unrank.data(), unrank.size() * 2, cudaMemcpyHostToDevice, s);
+    e = cudaMemsetAsync(l->arena, 0, 256, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         cudaFreeHost(l->host_stage);
@@ -683,7 +726,7 @@ ladder_status ladder_sync(ladder_t *l, void *cuda_stream)
     if (status != 0) {
         cudaMemsetAsync(l->d_status, 0, sizeof(int), s);
         cudaStreamSynchronize(s);
-        return fail(l, LADDER_E_TIMEOUT, "a bounded device wait ran out");
+        return device_status_error(l, status);
     }
     return LADDER_OK;
 }

@@ -14,6 +14,7 @@ constexpr int kThreads = 256;  // every analysis kernel runs 256-thread CTAs
 // Device status word values (mirror ladder_status).
 constexpr int kStatusOk = 0;
 constexpr int kStatusTimeout = -6;
+constexpr int kStatusTaskOverflow = -7;  // a dependent task list ran out of room (sized so it cannot)
 
 // Per-CTU layout of the candidate keys written by the motion search and read
 // by the decision kernel: depth d occupies (4^d - 1) / 3 ... (4^(d+1) - 1) / 3,
@@ -56,6 +57,9 @@ struct DecOffsets {
     long split[kMaxDepths], evaluated[kMaxDepths];
     long leaf_depth, leaf_mvx, leaf_mvy;
     long keys;
+    // dependent rungs: per CTU and key slot, the search centre, rule flags
+    // and (CUs of 32x32 and up) the CU's place in its task list
+    long dep_cx, dep_cy, dep_flags, dep_slot;
     long dec_bytes;  // the decision arrays span [0, dec_bytes)
 };
 
@@ -164,7 +168,7 @@ struct DecideBatch {
 };
 cudaError_t launch_decide(int bit_depth, int ctu, const DecideBatch &b, cudaStream_t s);
 
-// ---- dependent analysis (one fused kernel for many rungs / frames) ---------
+// ---- dependent analysis: rules, refinement search, decisions --------------
 // Reference-rung state a dependent rung reads.
 struct DepRefs {
     int Wr, Hr, cols8_r;     // reference rung size and 8x8 grid width
@@ -180,27 +184,40 @@ struct DependentItem {
     const char *ref_block;   // the frame's reference-rung block
     int rung;
     int qp;
-    int cta_begin;           // first CTA of this item (one CTA per CTU)
+    int cta_begin;           // first CTA of this item in the per-CTU kernels (one CTA per CTU)
 };
+
+// Evaluated CUs of a launch, one list per CU size class c (size 8 << c).
+// A task is (item | (CTU * keys per CTU + key slot) << 8) in the low word and
+// the centre (cx & 0xffff | cy << 16) in the high word.  CUs of 32x32 and
+// up are searched in 16x16 ranges whose candidate SADs add up in a per-CU
+// table of (2r+1)^2 sums (classes 2 and 3).
+constexpr int kSizeClasses = 4;
+constexpr int kFirstSummedClass = 2;
+constexpr int kDepBand = 17;  // candidate rows per lane task (9 for r <= 4)
 
 struct DependentBatch {
     int n;
     int r;                  // refinement range
-    const uint16_t *rank;   // (2r+1)^2: rank of candidate (dyi*K + dxi) in (|dx|+|dy|, dy, dx) order
-    const uint16_t *unrank; // inverse of rank
-    int rank_bits;          // ceil(log2((2r+1)^2))
     int satd_mode;
     int ref_rung;
     int depth_lo, depth_hi, use_ref_mv;
-    int total_ctas;
+    int total_ctas;         // CTUs of the batch
     int *status;
+    unsigned long long *tasks[kSizeClasses];  // per size class, capacity cap[c]
+    unsigned int *sums[kSizeClasses];         // classes >= kFirstSummedClass: cap[c] x (2r+1)^2
+    unsigned int cap[kSizeClasses];
+    unsigned int *counts;   // kSizeClasses counters, zero before the rules kernel
+    uint32_t one;           // 1, as an operand the compiler cannot fold
     RungInfo rung[kMaxRungs];
     DependentItem item[kMaxDepItems];
 };
-// Constraint derivation, refinement search, SATD, cost and split: one CTA per CTU.
-cudaError_t launch_dependent(int bit_depth, int ctu, int r, const DependentBatch &b, cudaStream_t s);
-// Rank / inverse tables of the refinement candidates for range r (host).
-void refine_rank_tables(int r, uint16_t *rank, uint16_t *unrank);
+// Rules, reachability, centres and task lists (one CTA per CTU); the search
+// over the task lists (persistent grid); SATD, cost, split and leaf maps (one
+// CTA per CTU).  Launched in this order on one stream.
+cudaError_t launch_dependent_rules(int ctu, const DependentBatch &b, cudaStream_t s);
+cudaError_t launch_dependent_search(int bit_depth, const DependentBatch &b, cudaStream_t s);
+cudaError_t launch_dependent_decide(int bit_depth, int ctu, const DependentBatch &b, cudaStream_t s);
 
 // Fills the keys of every block of a batch with ~0 (key initialisation).
 struct FillItem {

@@ -1,206 +1,67 @@
-// me_dependent.cu -- dependent analysis of one rung in one kernel (one CTA
-// per CTU): constraint derivation from the resident reference-rung leaves,
-// refinement search around the scaled reference vectors, SATD, cost, split
-// and leaf maps (inter-resolution analysis sharing with refinement,
-// Sec. 4.3 / 6.3; reuse and refinement controls, App. A.1 / A.2).
+// me_dependent.cu -- dependent analysis of ladder rungs (inter-resolution
+// analysis sharing with refinement, Sec. 4.3 / 6.3; reuse and refinement
+// controls, App. A.1 / A.2), in three kernels over a whole batch:
 //
-// Search layout.  The CTA lists the evaluated CUs of every depth, then
-// spreads (CU, 8x8 block, candidate-row tile, candidate-column chunk) items
-// over its threads.  An item holds the block's 8 current rows in registers,
-// walks the 8 + TY - 1 reference rows it needs once each (aligned 32-bit
-// loads through L1, one funnel shift to the row start, SPW-1 more for the
-// sub-word candidate offsets), and accumulates a TY x KC tile of packed
-// absdiff sums: every reference row feeds up to 8 x KC x (8/SPW) packed
-// instructions.  Block sums are added into a per-CU candidate table in
-// shared memory (integer reductions, so the order is free); one warp per CU
-// then takes the argmin of (SAD, |dx|+|dy|, dy, dx).
+//   1. rules (one CTA per CTU): every CU maps its centre to the reference
+//      rung, takes the co-located leaf's depth and scaled vector (search
+//      centre) and its depth window; reachability through the ancestors'
+//      split permissions; the evaluated CUs are appended to one task list
+//      per CU size, the CTU's argmin keys are reset.
+//   2. search (persistent grid over the task lists): lane task = one CU x
+//      one horizontal offset dx x a band of TY vertical offsets; the lane
+//      walks every 8x8 block of its CU and accumulates the CU's SAD for its
+//      TY candidates.  Reference rows are read straight from L1: three (8-bit)
+//      or five (10-bit) aligned words, shifted to the lane's start with two
+//      multiply-adds per word (FMA pipe; the ALU pipe does the SADs).  8-bit
+//      SADs use vabsdiff4 .add; 10-bit SADs use sum(a) + sum(b) -
+//      2 sum(min(a, b)) on packed halfword pairs (see me_full.cu).  The
+//      lanes of a CU are contiguous in a warp: a segmented min over the
+//      keys SAD * 2^RB + code (code orders (|dx|+|dy|, dy, dx)) leaves one
+//      atomicMin per CU and warp on the CU's global key.  CUs of 32x32 and
+//      up are split into 16x16 ranges (one task each, so no warp walks more
+//      than four blocks); their candidate SADs add up in a per-CU table.
+//   3. decide (one CTA per CTU): vectors from the keys (or the argmin over
+//      a CU's table), then SATD, cost, split and leaf maps.
 #include "common.cuh"
 
 #include <algorithm>
-#include <cstdlib>
-#include <vector>
 
 namespace ladder_impl {
 namespace {
-
-using dev::Traits;
 
 __constant__ int c_lambda_q16[52] = {
 #include "lambda_table.inc"
 };
 
-// SADs of the 8x8 block at (bx, by) for the TY x KC candidates whose
-// reference block starts at (xs + j, ys + i).
-template <typename T, int KC, int TY>
-__device__ __forceinline__ void block_tile_sads(const char *cb, const char *rb, long pitch, int W, int H, int bx,
-                                                int by, int xs, int ys, uint32_t (&acc)[TY * KC])
+constexpr int kRulesThreads = 128;
+constexpr int kSearchThreads = 256;
+constexpr int kDecideThreads = 128;
+
+__device__ __forceinline__ int item_of(const DependentBatch &b)
 {
-    constexpr int SPW = Traits<T>::SPW, BITS = 32 / SPW, WPR = 8 / SPW;
-    constexpr int NWN = (8 + KC - 1 + SPW - 1) / SPW;  // words of a reference row segment
-    uint32_t cw[8][WPR];
-    if (bx + 8 <= W) {
-#pragma unroll
-        for (int y = 0; y < 8; ++y) {
-            const char *row = cb + static_cast<long>(min(by + y, H - 1)) * pitch + static_cast<long>(bx) * sizeof(T);
-            if constexpr (WPR == 2) {
-                const uint2 v = __ldg(reinterpret_cast<const uint2 *>(row));
-                cw[y][0] = v.x;
-                cw[y][1] = v.y;
-            } else {
-                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(row));
-                cw[y][0] = v.x;
-                cw[y][1] = v.y;
-                cw[y][2] = v.z;
-                cw[y][3] = v.w;
-            }
-        }
-    } else {
-#pragma unroll
-        for (int y = 0; y < 8; ++y) {
-            const int cy = min(by + y, H - 1);
-#pragma unroll
-            for (int m = 0; m < WPR; ++m) {
-                uint32_t w = 0;
-#pragma unroll
-                for (int e = 0; e < SPW; ++e)
-                    w |= static_cast<uint32_t>(dev::ld_sample<T>(cb, pitch, min(bx + m * SPW + e, W - 1), cy))
-                         << (e * BITS);
-                cw[y][m] = w;
-            }
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < TY * KC; ++c) acc[c] = 0;
-
-    const bool xfast = xs >= 0 && (xs / SPW + NWN + 1) * SPW <= W;
-    const int sh = (xs & (SPW - 1)) * BITS;
-#pragma unroll
-    for (int rr = 0; rr < 8 + TY - 1; ++rr) {
-        const int ry = min(max(ys + rr, 0), H - 1);
-        const char *rowb = rb + static_cast<long>(ry) * pitch;
-        uint32_t nw[NWN];
-        if (xfast) {
-            const uint32_t *rp = reinterpret_cast<const uint32_t *>(rowb) + xs / SPW;
-            uint32_t raw[NWN + 1];
-#pragma unroll
-            for (int m = 0; m <= NWN; ++m) raw[m] = __ldg(rp + m);
-#pragma unroll
-            for (int m = 0; m < NWN; ++m) nw[m] = __funnelshift_r(raw[m], raw[m + 1], sh);
-        } else {
-#pragma unroll
-            for (int m = 0; m < NWN; ++m) {
-                uint32_t w = 0;
-#pragma unroll
-                for (int e = 0; e < SPW; ++e)
-                    w |= static_cast<uint32_t>(dev::ld_sample<T>(rb, pitch, min(max(xs + m * SPW + e, 0), W - 1), ry))
-                         << (e * BITS);
-                nw[m] = w;
-            }
-        }
-        // shw[k][m]: samples starting at sub-word offset k of word m
-        uint32_t shw[SPW][NWN];
-#pragma unroll
-        for (int m = 0; m < NWN; ++m) shw[0][m] = nw[m];
-#pragma unroll
-        for (int k = 1; k < SPW; ++k)
-#pragma unroll
-            for (int m = 0; m + 1 < NWN; ++m) shw[k][m] = __funnelshift_r(nw[m], nw[m + 1], k * BITS);
-#pragma unroll
-        for (int i = 0; i < TY; ++i) {
-            const int j = rr - i;  // current row j meets reference row rr at candidate row i
-            if (j < 0 || j >= 8) continue;
-#pragma unroll
-            for (int jx = 0; jx < KC; ++jx) {
-                const int q = jx / SPW, k = jx % SPW;
-#pragma unroll
-                for (int m = 0; m < WPR; ++m)
-                    acc[i * KC + jx] = dev::sad_acc<SPW>(cw[j][m], shw[k][q + m], acc[i * KC + jx]);
-            }
-        }
-    }
-}
-
-constexpr int kDepThreads = 128;  // 4 warps per CTU
-
-// Reduce-scatter of the candidate tables of the lanes that differ in the
-// low LG lane bits (the 8x8 blocks of one CU).  The table has N entries,
-// padded with zeros to NCP (a multiple of 32); afterwards each lane holds
-// NCP >> LG summed entries in s[0..], candidates off .. off + (NCP >> LG) - 1.
-template <int N, int NCP, int LG>
-__device__ __forceinline__ int scatter_tables(uint32_t (&s)[N], int lane)
-{
-    int off = 0;
-#pragma unroll
-    for (int b = 0; b < LG; ++b) {
-        const int half = NCP >> (b + 1);
-        const bool up = (lane >> b) & 1;
-#pragma unroll
-        for (int m = 0; m < half; ++m) {
-            if (m >= N) break;
-            const uint32_t lo = s[m];
-            const uint32_t hi = (m + half < N && (b > 0 || m + half < N)) ? s[m + half] : 0u;
-            const uint32_t send = up ? lo : hi;
-            const uint32_t keep = up ? hi : lo;
-            s[m] = keep + __shfl_xor_sync(0xffffffffu, send, 1 << b);
-        }
-        off += up ? half : 0;
-    }
-    return off;
-}
-
-// Best key among the held candidates, as SAD << 32 | rank (rank = position
-// of the candidate in the (|dx|+|dy|, dy, dx) order).  Candidate c of a
-// (ty, dc) job is (dyi, dxi) = (ty*TY + c / KC, dc*KC + c % KC).  The min is
-// taken on 32-bit keys SAD << RB | rank when SB + RB <= 32 (SB = bits of the
-// CU's largest SAD), else on 64-bit keys.
-template <int TY, int KC, int N, int CNT, int SB>
-__device__ __forceinline__ unsigned long long held_best(const uint32_t (&s)[N], int off, int ty, int dc, int K,
-                                                        const uint16_t *rank, int rb)
-{
-    const int base = ty * TY * K + dc * KC;
-    if (SB + rb <= 32) {
-        uint32_t best = 0xffffffffu;
-        const uint32_t mul = 1u << rb;
-#pragma unroll
-        for (int m = 0; m < CNT; ++m) {
-            const int c = off + m;
-            const int dyi = ty * TY + c / KC, dxi = dc * KC + c % KC;
-            if (c < TY * KC && dyi < K && dxi < K) {
-                const uint32_t key = s[m] * mul + rank[base + (c / KC) * K + c % KC];
-                best = key < best ? key : best;
-            }
-        }
-        if (best == 0xffffffffu) return ~0ull;
-        return (static_cast<unsigned long long>(best >> rb) << 32) | (best & (mul - 1u));
-    }
-    unsigned long long best = ~0ull;
-#pragma unroll
-    for (int m = 0; m < CNT; ++m) {
-        const int c = off + m;
-        const int dyi = ty * TY + c / KC, dxi = dc * KC + c % KC;
-        if (c < TY * KC && dyi < K && dxi < K) {
-            const unsigned long long key =
-                (static_cast<unsigned long long>(s[m]) << 32) | rank[base + (c / KC) * K + c % KC];
-            best = key < best ? key : best;
-        }
-    }
-    return best;
-}
-
-// Bits of the largest SAD of an S x S CU of B-bit samples.
-template <typename T> __host__ __device__ constexpr int sad_bits(int S)
-{
-    return (S == 8 ? 6 : S == 16 ? 8 : S == 32 ? 10 : 12) + (sizeof(T) == 1 ? 8 : 10);
-}
-
-template <typename T, int CTU, int KC, int TY>
-__global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const __grid_constant__ DependentBatch b)
-{
-    int ri = 0;  // the batch item of this CTA
+    int ri = 0;
     while (ri + 1 < b.n && static_cast<int>(blockIdx.x) >= b.item[ri + 1].cta_begin) ++ri;
+    return ri;
+}
+
+__device__ __forceinline__ int depth_of(int i, int dmax)
+{
+    int d = 0;
+    while (d < dmax && i >= key_offset(d + 1)) ++d;
+    return d;
+}
+
+// ---- 1. rules ---------------------------------------------------------------
+template <int CTU>
+__global__ void __launch_bounds__(kRulesThreads) k_dep_rules(const __grid_constant__ DependentBatch b)
+{
+    using C = dev::Ctu<CTU>;
+    constexpr int NT = kRulesThreads;
+    const int ri = item_of(b);
     const DependentItem &a = b.item[ri];
     const RungInfo &rinf = b.rung[a.rung];
     const RungInfo &rref = b.rung[b.ref_rung];
+    const RungGeom &g = rinf.g;
     DepRefs refs;
     refs.Wr = rref.g.W;
     refs.Hr = rref.g.H;
@@ -211,35 +72,18 @@ __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const __grid_const
     refs.depth_lo = b.depth_lo;
     refs.depth_hi = b.depth_hi;
     refs.use_ref_mv = b.use_ref_mv;
-    using C = dev::Ctu<CTU>;
-    constexpr int NT = kDepThreads, NWARP = NT / 32;
-    constexpr int NCAND = TY * KC;
-    constexpr int NCP = (NCAND + 31) / 32 * 32;  // padded so that 5 halvings stay whole
-    __shared__ dev::CtuState<CTU> st;
-    __shared__ int16_t s_cx[C::NKEY], s_cy[C::NKEY];
-    __shared__ uint8_t s_leaf[C::NKEY], s_splitok[C::NKEY];
-    __shared__ unsigned long long s_key[C::NKEY];
-    __shared__ int s_list[C::NKEY];       // evaluated CUs (key index), grouped by depth
-    __shared__ int s_cnt[C::DMAX + 1];
-    __shared__ int s_base[C::DMAX + 2];
-    __shared__ int s_wpre[C::DMAX + 2];   // warp-job prefix per depth
-    extern __shared__ uint32_t s_dyn[];   // 64x64 CU sums, then rank / unrank tables
-    uint32_t *const s_sum = s_dyn;
-    uint16_t *const s_rank = reinterpret_cast<uint16_t *>(s_dyn + (2 * b.r + 1) * (2 * b.r + 1));
-    uint16_t *const s_unrank = s_rank + (2 * b.r + 1) * (2 * b.r + 1);
 
-    const RungGeom &g = rinf.g;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ int16_t s_cx[C::NKEY], s_cy[C::NKEY];
+    __shared__ uint8_t s_leaf[C::NKEY], s_splitok[C::NKEY], s_flags[C::NKEY];
+    __shared__ unsigned int s_cnt[kSizeClasses], s_base[kSizeClasses];
+
+    const int tid = threadIdx.x;
     const int ctu_idx = blockIdx.x - a.cta_begin;
     const int x0 = (ctu_idx % g.ctu_cols) * CTU, y0 = (ctu_idx / g.ctu_cols) * CTU;
-    const int r = b.r, K = 2 * r + 1, KK = K * K;
-    const char *cb = static_cast<const char *>(a.cur);
-    const char *rb = static_cast<const char *>(a.ref);
+    const long kbase = static_cast<long>(ctu_idx) * C::NKEY;
 
-    // 1. local rule of every present CU
     for (int i = tid; i < C::NKEY; i += NT) {
-        int d = 0;
-        while (d < C::DMAX && i >= key_offset(d + 1)) ++d;
+        const int d = depth_of(i, C::DMAX);
         const int li = i - key_offset(d), n = 1 << d, S = CTU >> d;
         const int cu_x = x0 + (li % n) * S, cu_y = y0 + (li / n) * S;
         const bool present = cu_x < g.W8 && cu_y < g.H8;
@@ -257,128 +101,444 @@ __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const __grid_const
         s_cy[i] = cy;
         s_leaf[i] = leaf;
         s_splitok[i] = splitok;
-        s_key[i] = ~0ull;
-        st.flags[i] = present ? dev::kPresent : 0;
+        s_flags[i] = present ? dev::kPresent : 0;
     }
-    if (tid <= C::DMAX) s_cnt[tid] = 0;
-    for (int x = tid; x < KK; x += NT) {
-        s_sum[x] = 0;
-        s_rank[x] = b.rank[x];
-        s_unrank[x] = b.unrank[x];
-    }
+    if (tid < kSizeClasses) s_cnt[tid] = 0;
     __syncthreads();
 
-    // 2. reachability (every ancestor may split) and the decision flags
+    // reachability (every ancestor may split) and the rule flags
+    int16_t *const out_cx = reinterpret_cast<int16_t *>(a.block + rinf.off.dep_cx) + kbase;
+    int16_t *const out_cy = reinterpret_cast<int16_t *>(a.block + rinf.off.dep_cy) + kbase;
+    uint8_t *const out_fl = reinterpret_cast<uint8_t *>(a.block + rinf.off.dep_flags) + kbase;
+    unsigned long long *const keys = reinterpret_cast<unsigned long long *>(a.block + rinf.off.keys) + kbase;
     for (int i = tid; i < C::NKEY; i += NT) {
-        st.satd[i] = 0;
-        st.mvx[i] = INT16_MIN;
-        st.mvy[i] = INT16_MIN;
-        st.sad[i] = INT32_MAX;
-        if (!(st.flags[i] & dev::kPresent)) continue;
-        int d = 0;
-        while (d < C::DMAX && i >= key_offset(d + 1)) ++d;
-        const int li = i - key_offset(d), n = 1 << d;
-        const int cxl = li % n, cyl = li / n;
-        bool reach = true;
-        for (int e = 0; e < d; ++e)
-            reach = reach && s_splitok[dev::key_index(e, (cyl >> (d - e)) * (1 << e) + (cxl >> (d - e)))];
-        uint8_t f = dev::kPresent;
-        if (reach) f |= kRuleReachable;
-        if (reach && s_leaf[i]) f |= kRuleEvaluated;
-        if (reach && s_splitok[i]) f |= kRuleCanSplit;
-        st.flags[i] = f;
-        if (f & kRuleEvaluated) atomicAdd(&s_cnt[d], 1);
-    }
-    __syncthreads();
-    const int n_ty = (K + TY - 1) / TY, n_dc = (K + KC - 1) / KC;
-    if (tid == 0) {
-        s_base[0] = 0;
-        s_wpre[0] = 0;
-        for (int d = 0; d <= C::DMAX; ++d) {
-            s_base[d + 1] = s_base[d] + s_cnt[d];
-            const int nblk = ((CTU >> d) / 8) * ((CTU >> d) / 8);
-            const int groups = nblk >= 32 ? s_cnt[d] * (nblk / 32) : (s_cnt[d] * nblk + 31) / 32;
-            s_wpre[d + 1] = s_wpre[d] + groups * n_ty * n_dc;
-            s_cnt[d] = 0;
+        uint8_t f = s_flags[i];
+        if (f & dev::kPresent) {
+            const int d = depth_of(i, C::DMAX);
+            const int li = i - key_offset(d), n = 1 << d;
+            const int cxl = li % n, cyl = li / n;
+            bool reach = true;
+            for (int e = 0; e < d; ++e)
+                reach = reach && s_splitok[dev::key_index(e, (cyl >> (d - e)) * (1 << e) + (cxl >> (d - e)))];
+            if (reach) f |= kRuleReachable;
+            if (reach && s_leaf[i]) f |= kRuleEvaluated;
+            if (reach && s_splitok[i]) f |= kRuleCanSplit;
+            if (f & kRuleEvaluated) atomicAdd(&s_cnt[C::DMAX - d], 1u);  // size class of an S = CTU >> d CU
         }
+        s_flags[i] = f;
+        out_cx[i] = s_cx[i];
+        out_cy[i] = s_cy[i];
+        out_fl[i] = f;
+        keys[i] = ~0ull;
     }
     __syncthreads();
+    if (tid < kSizeClasses) {
+        const unsigned int n = s_cnt[tid];
+        unsigned int base = 0;
+        if (n) base = atomicAdd(&b.counts[tid], n);
+        if (n && base + n > b.cap[tid]) atomicExch(b.status, kStatusTaskOverflow);
+        s_base[tid] = base;
+        s_cnt[tid] = 0;
+    }
+    __syncthreads();
+    __shared__ int s_pos[C::NKEY];
     for (int i = tid; i < C::NKEY; i += NT) {
-        if (!(st.flags[i] & kRuleEvaluated)) continue;
-        int d = 0;
-        while (d < C::DMAX && i >= key_offset(d + 1)) ++d;
-        s_list[s_base[d] + atomicAdd(&s_cnt[d], 1)] = i;
+        s_pos[i] = -1;
+        if (!(s_flags[i] & kRuleEvaluated)) continue;
+        const int c = C::DMAX - depth_of(i, C::DMAX);  // size class: CU size 8 << c
+        const unsigned int pos = s_base[c] + atomicAdd(&s_cnt[c], 1u);
+        if (pos >= b.cap[c]) continue;
+        const uint32_t lo = static_cast<uint32_t>(ri) | (static_cast<uint32_t>(kbase + i) << 8);
+        const uint32_t hi = static_cast<uint32_t>(static_cast<uint16_t>(s_cx[i])) |
+                            (static_cast<uint32_t>(static_cast<uint16_t>(s_cy[i])) << 16);
+        b.tasks[c][pos] = (static_cast<unsigned long long>(hi) << 32) | lo;
+        s_pos[i] = static_cast<int>(pos);
     }
     __syncthreads();
+    // CUs searched in ranges: their list place, and a zeroed sum table
+    int *const out_slot = reinterpret_cast<int *>(a.block + rinf.off.dep_slot) + kbase;
+    const int KK = (2 * b.r + 1) * (2 * b.r + 1);
+    for (int i = tid; i < C::NKEY; i += NT) out_slot[i] = s_pos[i];
+    constexpr int NBIG = key_offset(C::DMAX - kFirstSummedClass + 1);  // CUs of 32x32 and up
+    for (int i = 0; i < NBIG; ++i) {
+        if (s_pos[i] < 0) continue;
+        unsigned int *sum = b.sums[C::DMAX - depth_of(i, C::DMAX)] + static_cast<long>(s_pos[i]) * KK;
+        for (int k = tid; k < KK; k += NT) sum[k] = 0;
+    }
+}
 
-    // 3. refinement search: warp jobs of 32 lanes = 8x8 blocks of CUs of one
-    //    depth (the blocks of a CU on consecutive lanes), one (ty, dc) tile.
-    const int n_wjobs = s_wpre[C::DMAX + 1];
-    for (int wj = warp; wj < n_wjobs; wj += NWARP) {
-        int d = 0;
-        while (d < C::DMAX && wj >= s_wpre[d + 1]) ++d;
-        const int S = CTU >> d, nb = S / 8, nblk = nb * nb;
-        int loc = wj - s_wpre[d];
-        const int dc = loc % n_dc;
-        loc /= n_dc;
-        const int ty = loc % n_ty;
-        const int grp = loc / n_ty;
-        int e, blk;
-        if (nblk >= 32) {
-            e = grp / (nblk / 32);
-            blk = (grp % (nblk / 32)) * 32 + lane;
-        } else {
-            e = (grp * 32 + lane) / nblk;
-            blk = lane % nblk;
+// ---- 2. search --------------------------------------------------------------
+__device__ __forceinline__ uint32_t umad(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t umulhi(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// (hi:lo) >> (32 - log2(m)) for m = 2^(32 - s), s in {8, 16, 24, 32}: the
+// word that starts s bits into lo, on the multiply-add pipe.
+__device__ __forceinline__ uint32_t shift_in(uint32_t lo, uint32_t hi, uint32_t m)
+{
+    return umad(hi, m, umulhi(lo, m));
+}
+
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+template <typename T>
+__device__ __forceinline__ uint32_t sample_word(const char *plane, long pitch, int W, int H, int x, int y)
+{
+    // SPW samples starting at (x, y), coordinates clamped into the frame
+    constexpr int SPW = 4 / sizeof(T);
+    const T *row = reinterpret_cast<const T *>(plane + static_cast<long>(min(max(y, 0), H - 1)) * pitch);
+    uint32_t w = 0;
+#pragma unroll
+    for (int e = 0; e < SPW; ++e) w |= static_cast<uint32_t>(row[min(max(x + e, 0), W - 1)]) << (e * 8 * sizeof(T));
+    return w;
+}
+
+// Frame-edge case of the block SADs (coordinates clamped sample by sample):
+// rolled loops, kept out of line so that the unrolled fast paths stay small.
+// Writes the block's SAD of candidate (x, y + i) to out[i].
+template <typename T, int TY>
+__device__ __noinline__ void block_sads_edge(const char *cur, const char *ref, long pitch, int W, int H, int bx,
+                                             int by, int x, int y, uint32_t one, uint32_t *out)
+{
+    constexpr int NW = sizeof(T) == 1 ? 2 : 4;  // words per block row
+    constexpr int SPW = 4 / sizeof(T);
+    uint32_t sa = 0;
+    if constexpr (sizeof(T) == 2)
+        for (int j = 0; j < 8; ++j)
+            for (int q = 0; q < NW; ++q) sa += sample_word<T>(cur, pitch, W, H, bx + q * SPW, by + j);
+    for (int i = 0; i < TY; ++i) {
+        uint32_t s = 0, sb = 0;
+        for (int j = 0; j < 8; ++j) {
+            for (int q = 0; q < NW; ++q) {
+                const uint32_t cw = sample_word<T>(cur, pitch, W, H, bx + q * SPW, by + j);
+                const uint32_t w = sample_word<T>(ref, pitch, W, H, x + q * SPW, y + i + j);
+                if constexpr (sizeof(T) == 1) {
+                    s = dev::sad_acc<4>(cw, w, s);
+                } else {
+                    s = umad(min_u16x2(cw, w), one, s);  // packed sum(min)
+                    sb += w;                             // packed sum(b)
+                }
+            }
         }
-        const bool valid = e < s_cnt[d];
-        const int i = s_list[s_base[d] + (valid ? e : 0)];
-        const int li = i - key_offset(d), n = 1 << d;
-        const int bx = x0 + (li % n) * S + (blk % nb) * 8;
-        const int by = y0 + (li / n) * S + (blk / nb) * 8;
-        uint32_t t[NCAND];
-        block_tile_sads<T, KC, TY>(cb, rb, a.pitch_bytes, g.W, g.H, bx, by, bx + s_cx[i] - r + dc * KC,
-                                   by + s_cy[i] - r + ty * TY, t);
-        if (nblk == 1) {
-            const unsigned long long best =
-                held_best<TY, KC, NCAND, NCAND, sad_bits<T>(8)>(t, 0, ty, dc, K, s_rank, b.rank_bits);
-            if (valid) atomicMin(&s_key[i], best);
-        } else if (nblk == 4) {
-            const int off = scatter_tables<NCAND, NCP, 2>(t, lane);
-            unsigned long long best =
-                held_best<TY, KC, NCAND, NCP / 4, sad_bits<T>(16)>(t, off, ty, dc, K, s_rank, b.rank_bits);
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, 1 << b);
-                best = o < best ? o : best;
-            }
-            if (valid && (lane & 3) == 0) atomicMin(&s_key[i], best);
-        } else if (nblk == 16) {
-            const int off = scatter_tables<NCAND, NCP, 4>(t, lane);
-            unsigned long long best =
-                held_best<TY, KC, NCAND, NCP / 16, sad_bits<T>(32)>(t, off, ty, dc, K, s_rank, b.rank_bits);
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, 1 << b);
-                best = o < best ? o : best;
-            }
-            if (valid && (lane & 15) == 0) atomicMin(&s_key[i], best);
+        if constexpr (sizeof(T) == 1) {
+            out[i] = s;
         } else {
-            // 64x64: the 64 blocks span two warp jobs; add both halves' sums
-            const int off = scatter_tables<NCAND, NCP, 5>(t, lane);
-#pragma unroll
-            for (int m = 0; m < NCP / 32; ++m) {
-                const int c = off + m;
-                const int dyi = ty * TY + c / KC, dxi = dc * KC + c % KC;
-                if (valid && c < NCAND && dyi < K && dxi < K) atomicAdd(&s_sum[dyi * K + dxi], t[m]);
-            }
+            const uint32_t d = umad(s, 0xfffffffeu, sa + sb);
+            out[i] = (d & 0xffffu) + (d >> 16);
         }
     }
-    __syncthreads();
-    if (CTU == 64 && warp == 0 && (st.flags[0] & kRuleEvaluated)) {
+}
+
+// Adds the 8x8 block SADs at (bx, by) of the TY candidates (x, y + i),
+// i < TY, to acc (8-bit samples).
+template <int TY>
+__device__ __forceinline__ void block_sads_u8(const char *cur, const char *ref, long pitch, int W, int H, int bx,
+                                              int by, int x, int y, uint32_t (&acc)[TY])
+{
+    constexpr int NR = 8 + TY - 1;
+    const int q = (x - 1) >> 2;  // words q .. q+2 hold samples x .. x+7
+    const bool fast = bx + 8 <= W && x >= 1 && 4 * q + 12 <= W && y >= 0 && y + NR <= H;
+    if (!fast) {
+        uint32_t e[TY];
+        block_sads_edge<uint8_t, TY>(cur, ref, pitch, W, H, bx, by, x, y, 1u, e);
+#pragma unroll
+        for (int i = 0; i < TY; ++i) acc[i] += e[i];
+        return;
+    }
+    uint2 c[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        c[j] = __ldg(reinterpret_cast<const uint2 *>(cur + static_cast<long>(min(by + j, H - 1)) * pitch + bx));
+    const uint32_t m = 1u << (32 - 8 * (x - 4 * q));  // x - 4q in 1..4
+    const uint32_t *rp = reinterpret_cast<const uint32_t *>(ref + static_cast<long>(y) * pitch) + q;
+    const long wp = pitch / 4;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const uint32_t a0 = __ldg(rp + r * wp), a1 = __ldg(rp + r * wp + 1), a2 = __ldg(rp + r * wp + 2);
+        const uint32_t w0 = shift_in(a0, a1, m), w1 = shift_in(a1, a2, m);
+#pragma unroll
+        for (int i = 0; i < TY; ++i) {
+            const int j = r - i;
+            if (j >= 0 && j < 8) acc[i] = dev::sad_acc<4>(c[j].x, w0, acc[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < TY; ++i) {
+            const int j = r - i;
+            if (j >= 0 && j < 8) acc[i] = dev::sad_acc<4>(c[j].y, w1, acc[i]);
+        }
+    }
+}
+
+// 10-bit samples: SAD = sum(a) + sum(b) - 2 sum(min(a, b)) per packed half.
+template <int TY>
+__device__ __forceinline__ void block_sads_u16(const char *cur, const char *ref, long pitch, int W, int H, int bx,
+                                               int by, int x, int y, uint32_t one, uint32_t (&acc)[TY])
+{
+    constexpr int NR = 8 + TY - 1;
+    const int q = (x - 1) >> 1;  // words q .. q+4 hold samples x .. x+7
+    const bool fast = bx + 8 <= W && x >= 1 && 2 * q + 10 <= W && y >= 0 && y + NR <= H;
+    if (!fast) {
+        uint32_t e[TY];
+        block_sads_edge<uint16_t, TY>(cur, ref, pitch, W, H, bx, by, x, y, one, e);
+#pragma unroll
+        for (int i = 0; i < TY; ++i) acc[i] += e[i];
+        return;
+    }
+    uint4 c[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        c[j] = __ldg(reinterpret_cast<const uint4 *>(cur + static_cast<long>(min(by + j, H - 1)) * pitch + 2 * bx));
+    uint32_t sa = 0;  // packed sums of the current block's even / odd columns
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sa += (c[j].x + c[j].y) + (c[j].z + c[j].w);
+    uint32_t mn[TY];
+#pragma unroll
+    for (int i = 0; i < TY; ++i) mn[i] = 0;
+    uint32_t rs[NR];
+    uint32_t sb = 0;
+    const uint32_t m = (x - 2 * q == 1) ? (1u << 16) : 1u;
+    const uint32_t *rp = reinterpret_cast<const uint32_t *>(ref + static_cast<long>(y) * pitch) + q;
+    const long wp = pitch / 4;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const uint32_t a0 = __ldg(rp + r * wp), a1 = __ldg(rp + r * wp + 1), a2 = __ldg(rp + r * wp + 2),
+                       a3 = __ldg(rp + r * wp + 3), a4 = __ldg(rp + r * wp + 4);
+        const uint32_t w0 = shift_in(a0, a1, m), w1 = shift_in(a1, a2, m), w2 = shift_in(a2, a3, m),
+                       w3 = shift_in(a3, a4, m);
+        rs[r] = umad(w0, one, w1) + umad(w2, one, w3);
+#pragma unroll
+        for (int i = 0; i < TY; ++i) {
+            const int j = r - i;
+            if (j >= 0 && j < 8) mn[i] = umad(min_u16x2(c[j].x, w0), one, mn[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < TY; ++i) {
+            const int j = r - i;
+            if (j >= 0 && j < 8) mn[i] = umad(min_u16x2(c[j].y, w1), one, mn[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < TY; ++i) {
+            const int j = r - i;
+            if (j >= 0 && j < 8) mn[i] = umad(min_u16x2(c[j].z, w2), one, mn[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < TY; ++i) {
+            const int j = r - i;
+            if (j >= 0 && j < 8) mn[i] = umad(min_u16x2(c[j].w, w3), one, mn[i]);
+        }
+        if (r < 8) sb += rs[r];
+        else sb = sb + rs[r] - rs[r - 8];
+        if (r >= 7) {
+            const int i = r - 7;  // candidate i is complete
+            const uint32_t d = umad(mn[i], 0xfffffffeu, sa + sb);
+            acc[i] += (d & 0xffffu) + (d >> 16);
+        }
+    }
+}
+
+// Bits of the largest SAD of an S x S CU.
+__device__ __forceinline__ int sad_bits(int S, int bit_depth)
+{
+    return (S == 8 ? 6 : S == 16 ? 8 : S == 32 ? 10 : 12) + bit_depth;
+}
+
+template <typename T, int TY>
+__device__ __forceinline__ void search_tile(const DependentBatch &b, int c, int lt, unsigned int ncu, int per_cu,
+                                            int rb, int lane)
+{
+    const int r = b.r, K = 2 * r + 1;
+    // ranges: CUs of 32x32 and up are searched as 16x16 pieces
+    const int S = 8 << c, RS = S < 16 ? S : 16;
+    const int nrs = S / RS, nr = nrs * nrs;
+    const int per_task = nr * per_cu;  // lanes of one CU
+    const long ntask = static_cast<long>(ncu) * per_task;
+    auto task_of = [&](int l) { return min(static_cast<long>(lt) * 32 + l, ntask - 1); };
+    const long traw = static_cast<long>(lt) * 32 + lane;
+    const long t = task_of(lane);
+    const unsigned int u = static_cast<unsigned int>(t / per_task);
+    int rem = static_cast<int>(t - static_cast<long>(u) * per_task);
+    const int rg = rem / per_cu;
+    rem -= rg * per_cu;
+    const int band = rem / K, dxi = rem - band * K;
+    const unsigned long long task = b.tasks[c][u];
+    const uint32_t lo = static_cast<uint32_t>(task), hi = static_cast<uint32_t>(task >> 32);
+    const DependentItem &a = b.item[lo & 0xffu];
+    const RungInfo &rinf = b.rung[a.rung];
+    const RungGeom &g = rinf.g;
+    const int nkey = keys_per_ctu(g.dmax);
+    const int gslot = static_cast<int>(lo >> 8);
+    const int ctu_idx = gslot / nkey, ks = gslot - ctu_idx * nkey;
+    const int d = depth_of(ks, g.dmax);
+    const int li = ks - key_offset(d), n = 1 << d;
+    const int cu_x = (ctu_idx % g.ctu_cols) * g.ctu + (li % n) * S + (rg % nrs) * RS;  // this range's origin
+    const int cu_y = (ctu_idx / g.ctu_cols) * g.ctu + (li / n) * S + (rg / nrs) * RS;
+    const int cx = static_cast<int16_t>(hi & 0xffffu), cy = static_cast<int16_t>(hi >> 16);
+    const int dxo = dxi - r;  // offsets from the centre
+    const int b0 = band * TY - r;
+    const int dy0 = K >= TY ? min(b0, r - TY + 1) : b0;
+
+    uint32_t acc[TY];
+#pragma unroll
+    for (int i = 0; i < TY; ++i) acc[i] = 0;
+    const char *cur = static_cast<const char *>(a.cur), *ref = static_cast<const char *>(a.ref);
+    const int nb = RS / 8;
+#pragma unroll 1
+    for (int blk = 0; blk < nb * nb; ++blk) {
+        const int bx = cu_x + 8 * (blk % nb), by = cu_y + 8 * (blk / nb);
+        if constexpr (sizeof(T) == 1)
+            block_sads_u8<TY>(cur, ref, a.pitch_bytes, g.W, g.H, bx, by, bx + cx + dxo, by + cy + dy0, acc);
+        else
+            block_sads_u16<TY>(cur, ref, a.pitch_bytes, g.W, g.H, bx, by, bx + cx + dxo, by + cy + dy0, b.one, acc);
+    }
+
+    if (nr > 1) {
+        // add this range's SADs to the CU's table; every candidate exactly
+        // once: no padding lanes, no rows a clamped band shares with the
+        // band before it, no rows past +r
+        if (traw < ntask) {
+            unsigned int *sum = b.sums[c] + static_cast<long>(u) * (K * K);
+#pragma unroll
+            for (int i = 0; i < TY; ++i) {
+                const int dyo = dy0 + i;
+                if (dyo >= b0 && dyo <= r) atomicAdd(sum + (dyo + r) * K + dxi, acc[i]);
+            }
+        }
+        return;
+    }
+
+    // keys; candidate rows past +r (only when 2r + 1 < TY) never win
+    const int bits = sad_bits(S, sizeof(T) == 1 ? 8 : 10);
+    unsigned long long best = ~0ull;
+    if (bits + rb <= 32) {
+        uint32_t k = 0xffffffffu;
+#pragma unroll
+        for (int i = 0; i < TY; ++i) {
+            const int dyo = dy0 + i;
+            const bool ok = dyo <= r;
+            const uint32_t code = static_cast<uint32_t>((abs(dxo) + abs(dyo)) * 2 * K + 2 * (dyo + r) + (dxo > 0));
+            const uint32_t key = umad(acc[i], ok ? (1u << rb) : 0u, ok ? code : 0xffffffffu);
+            k = min(k, key);
+        }
+        best = k == 0xffffffffu ? ~0ull : k;
+    } else {
+#pragma unroll
+        for (int i = 0; i < TY; ++i) {
+            const int dyo = dy0 + i;
+            if (dyo > r) continue;
+            const uint32_t code = static_cast<uint32_t>((abs(dxo) + abs(dyo)) * 2 * K + 2 * (dyo + r) + (dxo > 0));
+            const unsigned long long key = (static_cast<unsigned long long>(acc[i]) << rb) | code;
+            best = key < best ? key : best;
+        }
+    }
+    // segmented min over the contiguous lanes of each CU
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long v = __shfl_down_sync(0xffffffffu, best, o);
+        if (lane + o < 32 && task_of(lane + o) / per_task == u) best = v < best ? v : best;
+    }
+    const bool head = lane == 0 || task_of(lane - 1) / per_task != u;
+    if (head && best != ~0ull) {
+        const uint32_t sad = static_cast<uint32_t>(best >> rb);
+        const int code = static_cast<int>(best & ((1ull << rb) - 1));
+        const int l1 = code / (2 * K), rr = code - l1 * 2 * K;
+        const int dyv = (rr >> 1) - r;
+        const int adx = l1 - abs(dyv);
+        const int dxv = (rr & 1) ? adx : -adx;
+        const uint32_t tb = static_cast<uint32_t>(l1 * K * K + (dyv + r) * K + (dxv + r));
+        unsigned long long *keys = reinterpret_cast<unsigned long long *>(a.block + rinf.off.keys);
+        atomicMin(keys + gslot, (static_cast<unsigned long long>(sad) << 32) | tb);
+    }
+}
+
+template <typename T, int TY>
+__global__ void __launch_bounds__(kSearchThreads, 2) k_dep_search(const __grid_constant__ DependentBatch b)
+{
+    const int lane = threadIdx.x & 31;
+    const int r = b.r, K = 2 * r + 1;
+    const int per_cu = K * ((K + TY - 1) / TY);
+    const int code_max = 4 * r * K + 4 * r + 1;
+    const int rb = 32 - __clz(code_max);
+    // per size class: CUs and warp tiles (scalars: no local-memory arrays)
+    const unsigned int n0 = min(__ldg(b.counts + 0), b.cap[0]), n1 = min(__ldg(b.counts + 1), b.cap[1]),
+                       n2 = min(__ldg(b.counts + 2), b.cap[2]), n3 = min(__ldg(b.counts + 3), b.cap[3]);
+    // lanes per CU: per_cu per 16x16 range (one range up to 16x16, 4 for 32x32, 16 for 64x64)
+    const long t0 = (static_cast<long>(n0) * per_cu + 31) / 32, t1 = (static_cast<long>(n1) * per_cu + 31) / 32,
+               t2 = (static_cast<long>(n2) * 4 * per_cu + 31) / 32, t3 = (static_cast<long>(n3) * 16 * per_cu + 31) / 32;
+    const long total = t0 + t1 + t2 + t3;
+    const long nwarps = static_cast<long>(gridDim.x) * (kSearchThreads / 32);
+#pragma unroll 1
+    // consecutive tiles go to different CTAs (SMs): the long tiles of large
+    // CUs come first and spread over the whole GPU
+    for (long w = static_cast<long>(threadIdx.x >> 5) * gridDim.x + blockIdx.x; w < total; w += nwarps) {
+        long lt = w;
+        int c;
+        unsigned int ncu;
+        if (lt < t3) {
+            c = 3;
+            ncu = n3;
+        } else if ((lt -= t3) < t2) {
+            c = 2;
+            ncu = n2;
+        } else if ((lt -= t2) < t1) {
+            c = 1;
+            ncu = n1;
+        } else {
+            lt -= t1;
+            c = 0;
+            ncu = n0;
+        }
+        search_tile<T, TY>(b, c, static_cast<int>(lt), ncu, per_cu, rb, lane);
+    }
+}
+
+// ---- 3. decide --------------------------------------------------------------
+template <typename T, int CTU>
+__global__ void __launch_bounds__(kDecideThreads) k_dep_decide(const __grid_constant__ DependentBatch b)
+{
+    using C = dev::Ctu<CTU>;
+    const DependentItem &a = b.item[item_of(b)];
+    const RungInfo &rinf = b.rung[a.rung];
+    const RungGeom &g = rinf.g;
+    __shared__ dev::CtuState<CTU> st;
+    const int tid = threadIdx.x;
+    const int ctu_idx = blockIdx.x - a.cta_begin;
+    const int x0 = (ctu_idx % g.ctu_cols) * CTU, y0 = (ctu_idx / g.ctu_cols) * CTU;
+    const long kbase = static_cast<long>(ctu_idx) * C::NKEY;
+    const int r = b.r, K = 2 * r + 1;
+    const int16_t *in_cx = reinterpret_cast<const int16_t *>(a.block + rinf.off.dep_cx) + kbase;
+    const int16_t *in_cy = reinterpret_cast<const int16_t *>(a.block + rinf.off.dep_cy) + kbase;
+    const uint8_t *in_fl = reinterpret_cast<const uint8_t *>(a.block + rinf.off.dep_flags) + kbase;
+    const unsigned long long *keys = reinterpret_cast<const unsigned long long *>(a.block + rinf.off.keys) + kbase;
+    const int *in_slot = reinterpret_cast<const int *>(a.block + rinf.off.dep_slot) + kbase;
+    // CUs searched in ranges: argmin of (SAD, |dx|+|dy|, dy, dx) over the
+    // CU's table, one warp per CU
+    __shared__ unsigned long long s_best[C::NKEY];
+    constexpr int NBIG = key_offset(C::DMAX - kFirstSummedClass + 1);
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int i = warp; i < NBIG; i += kDecideThreads / 32) {
+        const int pos = in_slot[i];
+        if (pos < 0 || !(in_fl[i] & kRuleEvaluated)) continue;
+        const unsigned int *sum = b.sums[C::DMAX - depth_of(i, C::DMAX)] + static_cast<long>(pos) * (K * K);
         unsigned long long best = ~0ull;
-        for (int c = lane; c < KK; c += 32) {
-            const unsigned long long key = (static_cast<unsigned long long>(s_sum[c]) << 32) | s_rank[c];
+        for (int k = lane; k < K * K; k += 32) {
+            const int dxo = k % K - r, dyo = k / K - r;
+            const uint32_t tb = static_cast<uint32_t>((abs(dxo) + abs(dyo)) * K * K + k);
+            const unsigned long long key = (static_cast<unsigned long long>(sum[k]) << 32) | tb;
             best = key < best ? key : best;
         }
 #pragma unroll
@@ -386,103 +546,122 @@ __global__ void __launch_bounds__(kDepThreads, 4) k_dependent(const __grid_const
             const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
             best = v < best ? v : best;
         }
-        if (lane == 0) s_key[0] = best;
+        if (lane == 0) s_best[i] = best;
     }
     __syncthreads();
-    for (int i = tid; i < C::NKEY; i += NT) {
-        if (!(st.flags[i] & kRuleEvaluated)) continue;
-        const unsigned long long best = s_key[i];
-        const int c = s_unrank[static_cast<uint32_t>(best & 0xffffffffu)];
-        st.mvx[i] = static_cast<int16_t>(s_cx[i] + c % K - r);
-        st.mvy[i] = static_cast<int16_t>(s_cy[i] + c / K - r);
-        st.sad[i] = static_cast<int32_t>(best >> 32);
+    for (int i = tid; i < C::NKEY; i += kDecideThreads) {
+        const uint8_t f = in_fl[i];
+        st.flags[i] = f;
+        st.satd[i] = 0;
+        if (f & kRuleEvaluated) {
+            const unsigned long long key = (i < NBIG && in_slot[i] >= 0) ? s_best[i] : keys[i];
+            const int rem = static_cast<int>(static_cast<uint32_t>(key & 0xffffffffu) % static_cast<uint32_t>(K * K));
+            st.mvx[i] = static_cast<int16_t>(in_cx[i] + rem % K - r);
+            st.mvy[i] = static_cast<int16_t>(in_cy[i] + rem / K - r);
+            st.sad[i] = static_cast<int32_t>(key >> 32);
+        } else {
+            st.mvx[i] = INT16_MIN;
+            st.mvy[i] = INT16_MIN;
+            st.sad[i] = INT32_MAX;
+        }
     }
     __syncthreads();
-
-    // 4. SATD, cost, split, leaf maps
     dev::DecideIO io{a.cur, a.ref, a.pitch_bytes, &rinf.g, a.qp, b.satd_mode, c_lambda_q16,
                      decisions_at(a.block, rinf.off)};
     dev::ctu_decide<T, CTU>(st, io, x0, y0);
 }
 
-template <typename T, int CTU, int KC, int TY> cudaError_t ensure_attr()
+// ---- launches ---------------------------------------------------------------
+template <typename T, int TY> int search_ctas_per_sm()
 {
-    static bool done = false;
-    if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_dependent<T, CTU, KC, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         65 * 65 * 8);
-    if (e == cudaSuccess) done = true;
-    return e;
+    static int n = 0;
+    if (n == 0) {
+        int v = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_dep_search<T, TY>, kSearchThreads, 0) != cudaSuccess ||
+            v < 1)
+            v = 1;
+        n = v;
+    }
+    return n;
 }
 
-template <typename T, int CTU> cudaError_t prepare_dependent_t(int r)
+int sm_count()
 {
-    if (2 * r + 1 <= 9) return ensure_attr<T, CTU, 9, sizeof(T) == 1 ? 5 : 3>();
-    return ensure_attr<T, CTU, 17, sizeof(T) == 1 ? 2 : 1>();
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 1;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess)
+            v = 1;
+        n = v;
+    }
+    return n;
 }
 
-template <typename T, int CTU, int KC, int TY>
-cudaError_t dependent_t(int r, const DependentBatch &b, cudaStream_t s)
+template <typename T, int TY> cudaError_t search_t(const DependentBatch &b, cudaStream_t s)
 {
-    const int K = 2 * r + 1;
-    const int smem = K * K * 8;
-    auto kern = k_dependent<T, CTU, KC, TY>;
-    cudaError_t e = ensure_attr<T, CTU, KC, TY>();
-    if (e != cudaSuccess) return e;
-    kern<<<b.total_ctas, kDepThreads, smem, s>>>(b);
+    const int grid = sm_count() * search_ctas_per_sm<T, TY>();
+    k_dep_search<T, TY><<<grid, kSearchThreads, 0, s>>>(b);
     return cudaGetLastError();
 }
 
-template <typename T, int CTU>
-cudaError_t dependent_ctu(int r, const DependentBatch &b, cudaStream_t s)
+template <typename T> cudaError_t search_bd(const DependentBatch &b, cudaStream_t s)
 {
-    if (2 * r + 1 <= 9) return dependent_t<T, CTU, 9, sizeof(T) == 1 ? 5 : 3>(r, b, s);
-    return dependent_t<T, CTU, 17, sizeof(T) == 1 ? 2 : 1>(r, b, s);
+    // 10-bit bodies are twice as long per candidate row: bands of 9 rows
+    // keep the unrolled loop inside the instruction cache
+    if constexpr (sizeof(T) == 2) {
+        return search_t<T, 9>(b, s);
+    } else {
+        if (2 * b.r + 1 <= 9) return search_t<T, 9>(b, s);
+        return search_t<T, kDepBand>(b, s);
+    }
 }
 
 }  // namespace
 
-void refine_rank_tables(int r, uint16_t *rank, uint16_t *unrank)
+cudaError_t launch_dependent_rules(int ctu, const DependentBatch &b, cudaStream_t s)
 {
-    const int K = 2 * r + 1, KK = K * K;
-    std::vector<int> order(KK);
-    for (int c = 0; c < KK; ++c) order[c] = c;
-    // (|dx|+|dy|, dy, dx) with dx = c % K - r, dy = c / K - r
-    std::sort(order.begin(), order.end(), [&](int p, int q) {
-        const int px = p % K - r, py = p / K - r, qx = q % K - r, qy = q / K - r;
-        const int lp = std::abs(px) + std::abs(py), lq = std::abs(qx) + std::abs(qy);
-        if (lp != lq) return lp < lq;
-        if (py != qy) return py < qy;
-        return px < qx;
-    });
-    for (int k = 0; k < KK; ++k) {
-        rank[order[k]] = static_cast<uint16_t>(k);
-        unrank[k] = static_cast<uint16_t>(order[k]);
+    if (b.n < 1 || b.n > kMaxDepItems || b.total_ctas <= 0) return cudaErrorInvalidValue;
+    if (ctu == 64) k_dep_rules<64><<<b.total_ctas, kRulesThreads, 0, s>>>(b);
+    else if (ctu == 32) k_dep_rules<32><<<b.total_ctas, kRulesThreads, 0, s>>>(b);
+    else k_dep_rules<16><<<b.total_ctas, kRulesThreads, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dependent_search(int bit_depth, const DependentBatch &b, cudaStream_t s)
+{
+    if (b.n < 1 || b.n > kMaxDepItems) return cudaErrorInvalidValue;
+    return bit_depth == 8 ? search_bd<uint8_t>(b, s) : search_bd<uint16_t>(b, s);
+}
+
+cudaError_t launch_dependent_decide(int bit_depth, int ctu, const DependentBatch &b, cudaStream_t s)
+{
+    if (b.n < 1 || b.n > kMaxDepItems || b.total_ctas <= 0) return cudaErrorInvalidValue;
+    if (bit_depth == 8) {
+        if (ctu == 64) k_dep_decide<uint8_t, 64><<<b.total_ctas, kDecideThreads, 0, s>>>(b);
+        else if (ctu == 32) k_dep_decide<uint8_t, 32><<<b.total_ctas, kDecideThreads, 0, s>>>(b);
+        else k_dep_decide<uint8_t, 16><<<b.total_ctas, kDecideThreads, 0, s>>>(b);
+    } else {
+        if (ctu == 64) k_dep_decide<uint16_t, 64><<<b.total_ctas, kDecideThreads, 0, s>>>(b);
+        else if (ctu == 32) k_dep_decide<uint16_t, 32><<<b.total_ctas, kDecideThreads, 0, s>>>(b);
+        else k_dep_decide<uint16_t, 16><<<b.total_ctas, kDecideThreads, 0, s>>>(b);
     }
+    return cudaGetLastError();
 }
 
 cudaError_t prepare_kernels(int bit_depth, int ctu, int R, int r)
 {
     cudaError_t e = prepare_full_search(bit_depth, ctu, R);
     if (e != cudaSuccess) return e;
-    if (bit_depth == 8)
-        return ctu == 64 ? prepare_dependent_t<uint8_t, 64>(r)
-                         : (ctu == 32 ? prepare_dependent_t<uint8_t, 32>(r) : prepare_dependent_t<uint8_t, 16>(r));
-    return ctu == 64 ? prepare_dependent_t<uint16_t, 64>(r)
-                     : (ctu == 32 ? prepare_dependent_t<uint16_t, 32>(r) : prepare_dependent_t<uint16_t, 16>(r));
-}
-
-cudaError_t launch_dependent(int bit_depth, int ctu, int r, const DependentBatch &b, cudaStream_t s)
-{
-    if (b.n < 1 || b.n > kMaxDepItems || b.total_ctas <= 0) return cudaErrorInvalidValue;
+    sm_count();
     if (bit_depth == 8) {
-        if (ctu == 64) return dependent_ctu<uint8_t, 64>(r, b, s);
-        if (ctu == 32) return dependent_ctu<uint8_t, 32>(r, b, s);
-        return dependent_ctu<uint8_t, 16>(r, b, s);
+        search_ctas_per_sm<uint8_t, 9>();
+        search_ctas_per_sm<uint8_t, kDepBand>();
+    } else {
+        search_ctas_per_sm<uint16_t, 9>();
     }
-    if (ctu == 64) return dependent_ctu<uint16_t, 64>(r, b, s);
-    if (ctu == 32) return dependent_ctu<uint16_t, 32>(r, b, s);
-    return dependent_ctu<uint16_t, 16>(r, b, s);
+    (void)r;
+    return cudaGetLastError();
 }
 
 }  // namespace ladder_impl

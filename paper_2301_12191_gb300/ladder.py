@@ -99,7 +99,7 @@ SIGNATURES = [
     ("ladder_version", ctypes.c_char_p, []),
 ]
 
-KERNEL_KINDS = ("full_search", "decide", "dependent", "fill_keys")
+KERNEL_KINDS = ("full_search", "decide", "dependent", "fill_keys", "dep_rules", "dep_decide")
 
 _lib = None
 
