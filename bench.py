@@ -255,6 +255,7 @@ def run_ours(args, wl):
         return ((w + 7) // 8) * ((h + 7) // 8) * (2 * wl["R"] + 1) ** 2
 
     step_multi(0)
+    tuning = autotune(args, lad, lambda: step_multi(0), "frames1", stream)
     evals_ref = full_evals(*sizes[ref_i])
     evals_dep = 0
     for i in range(n_rungs):
@@ -375,6 +376,7 @@ def run_ours(args, wl):
             "bit_depth": wl["bit_depth"], "distinct_frames": n_frames,
             "l2": "flushed between timed steps (256 MiB write, outside the step events)",
             "parallelism": f"replicas x{world} (independent ladders per GPU)",
+            "tuning": tuning,
         },
         "sad_candidate_evals_per_s": evals_multi * world * K / (ms_multi * 1e-3),
         "independent": {
@@ -414,6 +416,19 @@ def run_ours(args, wl):
     lad.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def autotune(args, lad, step, tag, stream):
+    """Kernel shapes for this workload from the project's autotuner (untimed;
+    every shape gives identical decisions)."""
+    if args.no_tune:
+        return {"knobs": lad.tuning(), "tuned": False}
+    from paper_2301_12191_gb300 import tune
+    import tempfile
+    cache = os.path.join(tempfile.gettempdir(), "ladder_tuning_bench.json")
+    res = tune.tune(lad, step, tag=tag, stream=stream, reps=3, warmup=1, cache_path=cache, use_cache=False)
+    return {"knobs": res["knobs"], "tuned": True, "trials": len(res["trials"]), "seconds": round(res["seconds"], 2),
+            "best_ms": res["ms"]}
 
 
 def batch_requests(wl, seed0):
@@ -467,6 +482,7 @@ def run_batch(args, wl):
         lad.analyze_batch(items, stream)                 # eager once (sets up slots)
         lad.analyze_batch_independent(items_ind, stream)
     stream.synchronize()
+    tuning = autotune(args, lad, lambda: lad.analyze_batch(items, stream), f"frames{n}", stream)
     g_multi = lad.capture_batch(items, stream)
     # independent baseline, batched the same way (eager: full searches in chunks of 64)
     evals_ref = sum(((w + 7) // 8) * ((h + 7) // 8) for (w, h) in [sizes[ref_i]]) * (2 * wl["R"] + 1) ** 2
@@ -507,6 +523,7 @@ def run_batch(args, wl):
         lad.analyze_batch(items, stream)
     stats = lad.kernel_stats(reset=True)
     lad.profile(False)
+    launches_per_step = sum(nl for nl, _ in stats.values()) // 3
     dom = max(stats.items(), key=lambda kv: kv[1][1])
     kname, (klaunch, kms) = dom
     props = torch.cuda.get_device_properties(dev)
@@ -523,14 +540,15 @@ def run_batch(args, wl):
         "config": {"workload": args.config, "ladder_frames_per_step": n, "rungs": [f"{w}x{h}" for (w, h) in sizes],
                    "reference_rung": f"{sizes[ref_i][0]}x{sizes[ref_i][1]}", "search_range": wl["R"],
                    "refine_range": wl["r"], "bit_depth": wl["bit_depth"],
-                   "l2": "inputs larger than L2 (no flush)", "launch": "one CUDA graph per step (4 kernels)"},
+                   "l2": "inputs larger than L2 (no flush)",
+                   "launch": f"one CUDA graph per step ({launches_per_step} kernels)", "tuning": tuning},
         "sad_candidate_evals_per_s": evals_multi * K / (ms_multi * 1e-3),
         "independent": {"frames_per_s": n * indep_steps / (ms_indep * 1e-3), "ms_per_step": ms_indep / indep_steps,
                         "sad_candidate_evals_per_s": evals_indep * indep_steps / (ms_indep * 1e-3)},
         "multires_speedup_vs_independent": (ms_indep / indep_steps) / (ms_multi / K),
         "kernels": {k: {"launches": nl, "ms_total": ms, "share": ms / max(1e-9, sum(v[1] for v in stats.values()))}
                     for k, (nl, ms) in stats.items()},
-        "gpu_launches": 4 * K,
+        "gpu_launches": launches_per_step * K,
         "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tabsdiff/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
                      "algorithmic_absdiffs_per_launch": algo, "avg_launch_ms": (kms / klaunch) if klaunch else None},
@@ -648,6 +666,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=sorted(WORKLOADS), default="ladder1080")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default kernel shapes (skip the autotuner)")
     ap.add_argument("--json-out", default=None)
     ap.add_argument("--soak", type=float, default=1.5, help="untimed seconds of load before timing (clock sampling)")
     ap.add_argument("--only-multires", action="store_true",

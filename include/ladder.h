@@ -187,6 +187,29 @@ LADDER_API ladder_status ladder_capture_batch(ladder_t *ladder, const ladder_req
 LADDER_API ladder_status ladder_graph_launch(ladder_graph_t *graph, void *cuda_stream);
 LADDER_API void ladder_graph_destroy(ladder_graph_t *graph);
 
+/* Kernel-shape knobs (no counterpart in the paper: they choose how the
+ * search is laid out on the GPU, never what it computes; every setting
+ * gives bit-identical decisions).  A change applies to later launches;
+ * captured graphs keep the shapes they were captured with.  Values:
+ *   LADDER_TUNE_FS_BAND          full search: candidate rows per lane task,
+ *                                13 (default) or 9 (64x64 CTUs only)
+ *   LADDER_TUNE_DEP_BAND         dependent search: candidate rows per lane
+ *                                task, 0 (automatic), 9 or 17
+ *   LADDER_TUNE_DEP_RANGE        dependent search: CUs larger than this
+ *                                side (16, default, or 32) are searched in
+ *                                pieces of this side
+ *   LADDER_TUNE_DEP_CTAS_PER_SM  dependent search grid: CTAs per SM, 0 (as
+ *                                many as fit, default) to 8
+ * LADDER_E_INVAL for an unknown knob or value. */
+typedef enum {
+    LADDER_TUNE_FS_BAND = 0,
+    LADDER_TUNE_DEP_BAND = 1,
+    LADDER_TUNE_DEP_RANGE = 2,
+    LADDER_TUNE_DEP_CTAS_PER_SM = 3
+} ladder_tune_knob;
+LADDER_API ladder_status ladder_set_tuning(ladder_t *ladder, int knob, int value);
+LADDER_API ladder_status ladder_get_tuning(const ladder_t *ladder, int knob, int *value);
+
 /* Device bytes the handle holds (decision buffers of every frame slot). */
 LADDER_API long ladder_device_bytes(const ladder_t *ladder);
 

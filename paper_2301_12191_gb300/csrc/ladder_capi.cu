@@ -58,6 +58,8 @@ struct ladder {
     std::string err;
     int sm_count = 0;
     int fs_ctas_per_sm = 1;      // resident full-search CTAs per SM
+    // kernel shapes (ladder_set_tuning): results never depend on them
+    int tune_fs_band = kFsBand, tune_dep_band = 0, tune_dep_range = 16, tune_dep_ctas = 0;
     char *host_stage = nullptr;  // pinned staging for fetch_decisions
     size_t host_stage_bytes = 0;
     // tracing
@@ -268,7 +270,7 @@ struct Job {
 ladder_status launch_independent(ladder_t *l, const Job *jobs, int n, cudaStream_t s)
 {
     const int R = l->geo.ref_search_range;
-    const FullSearchPlan plan = full_search_plan(l->geo.bit_depth, l->geo.ctu_size, R);
+    const FullSearchPlan plan = full_search_plan(l->geo.bit_depth, l->geo.ctu_size, R, l->tune_fs_band);
     for (int j0 = 0; j0 < n; j0 += kMaxItems) {
         const int m = std::min(kMaxItems, n - j0);
         FillBatch fill{};
@@ -322,6 +324,9 @@ ladder_status launch_dependents(ladder_t *l, const Job *jobs, int n, cudaStream_
         DependentBatch b{};
         b.n = m;
         b.r = l->geo.dep_refine_range;
+        b.range = l->tune_dep_range;
+        b.band = l->tune_dep_band;
+        b.ctas_per_sm = l->tune_dep_ctas;
         b.satd_mode = l->geo.satd_mode;
         b.ref_rung = l->geo.ref_rung;
         b.depth_lo = l->geo.dep_depth_lo;
@@ -798,6 +803,44 @@ ladder_status ladder_profile_read(ladder_t *l, int kind, long *launches, double 
         l->total_ms[kind] = 0.0;
     }
     return LADDER_OK;
+}
+
+ladder_status ladder_set_tuning(ladder_t *l, int knob, int value)
+{
+    if (!l) return LADDER_E_INVAL;
+    switch (knob) {
+    case LADDER_TUNE_FS_BAND:
+        if (value != 9 && value != 13) return fail(l, LADDER_E_INVAL, "full-search band %d (9 or 13)", value);
+        if (value == 9 && l->geo.ctu_size != 64) return fail(l, LADDER_E_INVAL, "band 9 needs 64x64 CTUs");
+        l->tune_fs_band = value;
+        return LADDER_OK;
+    case LADDER_TUNE_DEP_BAND:
+        if (value != 0 && value != 9 && value != 17) return fail(l, LADDER_E_INVAL, "dependent band %d", value);
+        l->tune_dep_band = value;
+        return LADDER_OK;
+    case LADDER_TUNE_DEP_RANGE:
+        if (value != 16 && value != 32) return fail(l, LADDER_E_INVAL, "dependent range %d (16 or 32)", value);
+        l->tune_dep_range = value;
+        return LADDER_OK;
+    case LADDER_TUNE_DEP_CTAS_PER_SM:
+        if (value < 0 || value > 8) return fail(l, LADDER_E_INVAL, "CTAs per SM %d (0..8)", value);
+        l->tune_dep_ctas = value;
+        return LADDER_OK;
+    default:
+        return fail(l, LADDER_E_INVAL, "unknown tuning knob %d", knob);
+    }
+}
+
+ladder_status ladder_get_tuning(const ladder_t *l, int knob, int *value)
+{
+    if (!l || !value) return LADDER_E_INVAL;
+    switch (knob) {
+    case LADDER_TUNE_FS_BAND: *value = l->tune_fs_band; return LADDER_OK;
+    case LADDER_TUNE_DEP_BAND: *value = l->tune_dep_band; return LADDER_OK;
+    case LADDER_TUNE_DEP_RANGE: *value = l->tune_dep_range; return LADDER_OK;
+    case LADDER_TUNE_DEP_CTAS_PER_SM: *value = l->tune_dep_ctas; return LADDER_OK;
+    default: return LADDER_E_INVAL;
+    }
 }
 
 long ladder_device_bytes(const ladder_t *l) { return l ? static_cast<long>(l->arena_bytes) : 0; }

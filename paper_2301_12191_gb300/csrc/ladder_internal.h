@@ -106,6 +106,7 @@ struct FullSearchItem {
 struct FullSearchBatch {
     int n;
     int R;            // search range
+    int band;         // candidate rows per lane task (13, or 9 for 64x64 CTUs)
     int Rp;           // left window margin: R rounded up to 16 samples
     int ntasks;       // lane tasks (dx, band of kFsBand dy) per CTU
     int warp_tiles;   // CTAs per CTU: ceil(ntasks / 32)
@@ -131,8 +132,9 @@ struct FullSearchPlan {
     int smem_bytes;   // dynamic shared memory of one CTA (two buffers)
 };
 
-// Returns the shared-memory plan for bit depth / CTU / R.
-FullSearchPlan full_search_plan(int bit_depth, int ctu, int R);
+// Returns the plan for bit depth / CTU / R / band (13 or 9 candidate rows
+// per lane task; 9 only with 64x64 CTUs).
+FullSearchPlan full_search_plan(int bit_depth, int ctu, int R, int band = kFsBand);
 // Tiled 2-D tensor map of a W x H plane (8-bit: uint8, 10-bit: uint16
 // samples), box box_w x box_h samples, zero fill outside the plane.
 // Returns 0 on success, else the driver's error (or -1: encoder unavailable).
@@ -144,7 +146,7 @@ int encode_item_maps(FullSearchBatch &b, int k, const void *cur, const void *ref
 // Copies the plan's launch constants into a batch.
 void fill_full_search_batch(FullSearchBatch &b, const FullSearchPlan &p, int R);
 // Resident full-search CTAs per SM for this plan (occupancy calculator).
-int full_search_ctas_per_sm(int bit_depth, int ctu, int R);
+int full_search_ctas_per_sm(int bit_depth, int ctu, int R, int band = kFsBand);
 // One CTA per work item: b.total = sum over frames of CTUs x warp_tiles.
 cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchBatch &b, cudaStream_t s);
 
@@ -189,9 +191,10 @@ struct DependentItem {
 
 // Evaluated CUs of a launch, one list per CU size class c (size 8 << c).
 // A task is (item | (CTU * keys per CTU + key slot) << 8) in the low word and
-// the centre (cx & 0xffff | cy << 16) in the high word.  CUs of 32x32 and
-// up are searched in 16x16 ranges whose candidate SADs add up in a per-CU
-// table of (2r+1)^2 sums (classes 2 and 3).
+// the centre (cx & 0xffff | cy << 16) in the high word.  CUs larger than the
+// batch's range (16 or 32) are searched in range x range pieces whose
+// candidate SADs add up in a per-CU table of (2r+1)^2 sums (classes 2 and 3
+// have table room).
 constexpr int kSizeClasses = 4;
 constexpr int kFirstSummedClass = 2;
 constexpr int kDepBand = 17;  // candidate rows per lane task (9 for r <= 4)
@@ -199,6 +202,9 @@ constexpr int kDepBand = 17;  // candidate rows per lane task (9 for r <= 4)
 struct DependentBatch {
     int n;
     int r;                  // refinement range
+    int range;              // CUs larger than this (16 or 32) are searched in pieces of this side
+    int band;               // candidate rows per lane task: 9 or 17
+    int ctas_per_sm;        // search grid: CTAs per SM (0: as many as fit)
     int satd_mode;
     int ref_rung;
     int depth_lo, depth_hi, use_ref_mv;

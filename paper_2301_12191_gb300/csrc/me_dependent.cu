@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kRulesThreads) k_dep_rules(const __grid_consta
     for (int i = tid; i < C::NKEY; i += NT) out_slot[i] = s_pos[i];
     constexpr int NBIG = key_offset(C::DMAX - kFirstSummedClass + 1);  // CUs of 32x32 and up
     for (int i = 0; i < NBIG; ++i) {
-        if (s_pos[i] < 0) continue;
+        if (s_pos[i] < 0 || (CTU >> depth_of(i, C::DMAX)) <= b.range) continue;
         unsigned int *sum = b.sums[C::DMAX - depth_of(i, C::DMAX)] + static_cast<long>(s_pos[i]) * KK;
         for (int k = tid; k < KK; k += NT) sum[k] = 0;
     }
@@ -362,8 +362,8 @@ __device__ __forceinline__ void search_tile(const DependentBatch &b, int c, int 
                                             int rb, int lane)
 {
     const int r = b.r, K = 2 * r + 1;
-    // ranges: CUs of 32x32 and up are searched as 16x16 pieces
-    const int S = 8 << c, RS = S < 16 ? S : 16;
+    // CUs larger than the range are searched as range x range pieces
+    const int S = 8 << c, RS = S < b.range ? S : b.range;
     const int nrs = S / RS, nr = nrs * nrs;
     const int per_task = nr * per_cu;  // lanes of one CU
     const long ntask = static_cast<long>(ncu) * per_task;
@@ -476,9 +476,10 @@ __global__ void __launch_bounds__(kSearchThreads, 2) k_dep_search(const __grid_c
     // per size class: CUs and warp tiles (scalars: no local-memory arrays)
     const unsigned int n0 = min(__ldg(b.counts + 0), b.cap[0]), n1 = min(__ldg(b.counts + 1), b.cap[1]),
                        n2 = min(__ldg(b.counts + 2), b.cap[2]), n3 = min(__ldg(b.counts + 3), b.cap[3]);
-    // lanes per CU: per_cu per 16x16 range (one range up to 16x16, 4 for 32x32, 16 for 64x64)
+    // lanes per CU: per_cu per piece (pieces of 32x32 / 64x64 CUs: (S / range)^2)
+    const long p2 = b.range >= 32 ? 1 : 4, p3 = b.range >= 32 ? 4 : 16;
     const long t0 = (static_cast<long>(n0) * per_cu + 31) / 32, t1 = (static_cast<long>(n1) * per_cu + 31) / 32,
-               t2 = (static_cast<long>(n2) * 4 * per_cu + 31) / 32, t3 = (static_cast<long>(n3) * 16 * per_cu + 31) / 32;
+               t2 = (static_cast<long>(n2) * p2 * per_cu + 31) / 32, t3 = (static_cast<long>(n3) * p3 * per_cu + 31) / 32;
     const long total = t0 + t1 + t2 + t3;
     const long nwarps = static_cast<long>(gridDim.x) * (kSearchThreads / 32);
 #pragma unroll 1
@@ -530,9 +531,10 @@ __global__ void __launch_bounds__(kDecideThreads) k_dep_decide(const __grid_cons
     __shared__ unsigned long long s_best[C::NKEY];
     constexpr int NBIG = key_offset(C::DMAX - kFirstSummedClass + 1);
     const int lane = tid & 31, warp = tid >> 5;
+    auto summed = [&](int i) { return i < NBIG && in_slot[i] >= 0 && (CTU >> depth_of(i, C::DMAX)) > b.range; };
     for (int i = warp; i < NBIG; i += kDecideThreads / 32) {
         const int pos = in_slot[i];
-        if (pos < 0 || !(in_fl[i] & kRuleEvaluated)) continue;
+        if (!summed(i) || !(in_fl[i] & kRuleEvaluated)) continue;
         const unsigned int *sum = b.sums[C::DMAX - depth_of(i, C::DMAX)] + static_cast<long>(pos) * (K * K);
         unsigned long long best = ~0ull;
         for (int k = lane; k < K * K; k += 32) {
@@ -554,7 +556,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_dep_decide(const __grid_cons
         st.flags[i] = f;
         st.satd[i] = 0;
         if (f & kRuleEvaluated) {
-            const unsigned long long key = (i < NBIG && in_slot[i] >= 0) ? s_best[i] : keys[i];
+            const unsigned long long key = summed(i) ? s_best[i] : keys[i];
             const int rem = static_cast<int>(static_cast<uint32_t>(key & 0xffffffffu) % static_cast<uint32_t>(K * K));
             st.mvx[i] = static_cast<int16_t>(in_cx[i] + rem % K - r);
             st.mvy[i] = static_cast<int16_t>(in_cy[i] + rem / K - r);
@@ -600,7 +602,8 @@ int sm_count()
 
 template <typename T, int TY> cudaError_t search_t(const DependentBatch &b, cudaStream_t s)
 {
-    const int grid = sm_count() * search_ctas_per_sm<T, TY>();
+    const int fit = search_ctas_per_sm<T, TY>();
+    const int grid = sm_count() * (b.ctas_per_sm > 0 ? std::min(b.ctas_per_sm, fit) : fit);
     k_dep_search<T, TY><<<grid, kSearchThreads, 0, s>>>(b);
     return cudaGetLastError();
 }
@@ -609,12 +612,11 @@ template <typename T> cudaError_t search_bd(const DependentBatch &b, cudaStream_
 {
     // 10-bit bodies are twice as long per candidate row: bands of 9 rows
     // keep the unrolled loop inside the instruction cache
-    if constexpr (sizeof(T) == 2) {
-        return search_t<T, 9>(b, s);
-    } else {
-        if (2 * b.r + 1 <= 9) return search_t<T, 9>(b, s);
-        return search_t<T, kDepBand>(b, s);
-    }
+    // bands of 9 rows when 2r + 1 <= 9 or when asked for; 10-bit bodies are
+    // twice as long per row, so 10-bit takes 9 unless asked for 17
+    const bool nine = 2 * b.r + 1 <= 9 || b.band == 9 || (sizeof(T) == 2 && b.band != kDepBand);
+    if (nine) return search_t<T, 9>(b, s);
+    return search_t<T, kDepBand>(b, s);
 }
 
 }  // namespace
@@ -659,6 +661,7 @@ cudaError_t prepare_kernels(int bit_depth, int ctu, int R, int r)
         search_ctas_per_sm<uint8_t, kDepBand>();
     } else {
         search_ctas_per_sm<uint16_t, 9>();
+        search_ctas_per_sm<uint16_t, kDepBand>();
     }
     (void)r;
     return cudaGetLastError();

@@ -53,9 +53,9 @@ using dev::mbar_wait_bounded;
 using dev::sad_acc;
 using dev::tma_load_2d;
 
-template <typename T, int CTU, int RP> struct Shape {
+template <typename T, int CTU, int RP, int BAND> struct Shape {
     static constexpr int ES = sizeof(T);
-    static constexpr int TY = kFsBand;
+    static constexpr int TY = BAND;
     static constexpr int P4 = CTU + 2 * RP;       // window positions (= expanded words) per row
     static constexpr int NT = 128;                // 4 warps, one per quadrant
     static constexpr int Q = CTU / 2;             // quadrant side
@@ -170,10 +170,10 @@ __device__ __forceinline__ void emit_chunk(const uint32_t (&w)[ES == 1 ? 2 : 3],
     *reinterpret_cast<uint4 *>(dst) = v;
 }
 
-template <typename T, int CTU, int RP>
+template <typename T, int CTU, int RP, int BAND>
 __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(const __grid_constant__ FullSearchBatch b)
 {
-    using S = Shape<T, CTU, RP>;
+    using S = Shape<T, CTU, RP, BAND>;
     constexpr int TY = S::TY, P4 = S::P4, ES = S::ES, NT = S::NT;
     constexpr int NR = 8 + TY - 1;  // window rows read per 8x8 block
 
@@ -448,64 +448,72 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
 }
 
 // Largest dynamic shared memory already granted to a kernel instance.
-template <typename T, int CTU, int RP> int &granted_smem()
+template <typename T, int CTU, int RP, int BAND> int &granted_smem()
 {
     static int bytes = -1;
     return bytes;
 }
 
-template <typename T, int CTU, int RP> cudaError_t ensure_smem(int smem)
+template <typename T, int CTU, int RP, int BAND> cudaError_t ensure_smem(int smem)
 {
-    if (granted_smem<T, CTU, RP>() >= smem) return cudaSuccess;
+    if (granted_smem<T, CTU, RP, BAND>() >= smem) return cudaSuccess;
     cudaError_t e =
-        cudaFuncSetAttribute(k_full_search<T, CTU, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) granted_smem<T, CTU, RP>() = smem;
+        cudaFuncSetAttribute(k_full_search<T, CTU, RP, BAND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) granted_smem<T, CTU, RP, BAND>() = smem;
     return e;
 }
 
-template <typename T, int CTU, int RP> int occupancy_t(int smem)
+template <typename T, int CTU, int RP, int BAND> int occupancy_t(int smem)
 {
-    if (ensure_smem<T, CTU, RP>(smem) != cudaSuccess) return 1;
+    if (ensure_smem<T, CTU, RP, BAND>(smem) != cudaSuccess) return 1;
     int n = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_full_search<T, CTU, RP>, Shape<T, CTU, RP>::NT, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_full_search<T, CTU, RP, BAND>, Shape<T, CTU, RP, BAND>::NT,
+                                                      smem) !=
         cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
 
-template <typename T, int CTU, int RP>
+template <typename T, int CTU, int RP, int BAND>
 cudaError_t launch_t(const FullSearchBatch &b, int smem, cudaStream_t s)
 {
-    using S = Shape<T, CTU, RP>;
-    cudaError_t e = ensure_smem<T, CTU, RP>(smem);
+    using S = Shape<T, CTU, RP, BAND>;
+    cudaError_t e = ensure_smem<T, CTU, RP, BAND>(smem);
     if (e != cudaSuccess) return e;
     const int n2 = (b.box_h - std::min(b.phase1_rows, b.box_h)) * S::CPR;
     if (n2 > S::MAXC * S::NT || b.box_h > S::MAX_ROWS || 4 * S::TY * 32 * 4 > b.e_bytes) return cudaErrorInvalidValue;
-    k_full_search<T, CTU, RP><<<b.total, S::NT, smem, s>>>(b);
+    k_full_search<T, CTU, RP, BAND><<<b.total, S::NT, smem, s>>>(b);
     return cudaGetLastError();
 }
 
-// Dispatch on (bit depth, CTU, window margin class).
-template <typename F> cudaError_t dispatch(int bit_depth, int ctu, int Rp, F &&f)
+// Dispatch on (bit depth, CTU, window margin class, band): 64x64 CTUs have
+// bands of 13 (default) and 9 candidate rows, smaller CTUs only 13.
+template <typename F> cudaError_t dispatch(int bit_depth, int ctu, int Rp, int band, F &&f)
 {
-    const bool wide = Rp > 32;
+    const bool wide = Rp > 32, b9 = band == 9;
     if (bit_depth == 8) {
-        if (ctu == 64) return wide ? f.template run<uint8_t, 64, 64>() : f.template run<uint8_t, 64, 32>();
-        if (ctu == 32) return f.template run<uint8_t, 32, 64>();
-        return f.template run<uint8_t, 16, 64>();
+        if (ctu == 64) {
+            if (wide) return b9 ? f.template run<uint8_t, 64, 64, 9>() : f.template run<uint8_t, 64, 64, 13>();
+            return b9 ? f.template run<uint8_t, 64, 32, 9>() : f.template run<uint8_t, 64, 32, 13>();
+        }
+        if (ctu == 32) return f.template run<uint8_t, 32, 64, 13>();
+        return f.template run<uint8_t, 16, 64, 13>();
     }
-    if (ctu == 64) return wide ? f.template run<uint16_t, 64, 64>() : f.template run<uint16_t, 64, 32>();
-    if (ctu == 32) return f.template run<uint16_t, 32, 64>();
-    return f.template run<uint16_t, 16, 64>();
+    if (ctu == 64) {
+        if (wide) return b9 ? f.template run<uint16_t, 64, 64, 9>() : f.template run<uint16_t, 64, 64, 13>();
+        return b9 ? f.template run<uint16_t, 64, 32, 9>() : f.template run<uint16_t, 64, 32, 13>();
+    }
+    if (ctu == 32) return f.template run<uint16_t, 32, 64, 13>();
+    return f.template run<uint16_t, 16, 64, 13>();
 }
 
 int rp_class(int ctu, int Rp) { return (ctu == 64 && Rp <= 32) ? 32 : 64; }
 
 struct OccupancyOp {
     int smem, n;
-    template <typename T, int CTU, int RP> cudaError_t run()
+    template <typename T, int CTU, int RP, int BAND> cudaError_t run()
     {
-        n = occupancy_t<T, CTU, RP>(smem);
+        n = occupancy_t<T, CTU, RP, BAND>(smem);
         return cudaSuccess;
     }
 };
@@ -514,31 +522,32 @@ struct LaunchOp {
     const FullSearchBatch &b;
     int smem;
     cudaStream_t s;
-    template <typename T, int CTU, int RP> cudaError_t run() { return launch_t<T, CTU, RP>(b, smem, s); }
+    template <typename T, int CTU, int RP, int BAND> cudaError_t run() { return launch_t<T, CTU, RP, BAND>(b, smem, s); }
 };
 
 }  // namespace
 
-FullSearchPlan full_search_plan(int bit_depth, int ctu, int R)
+FullSearchPlan full_search_plan(int bit_depth, int ctu, int R, int band)
 {
+    if (ctu != 64 || band != 9) band = kFsBand;  // the compiled bands
     FullSearchPlan p{};
     const int es = bit_depth == 8 ? 1 : 2;
     const int K = 2 * R + 1;
     p.Rp = (R + 15) / 16 * 16;
     const int RPc = rp_class(ctu, p.Rp);
-    p.band = kFsBand;
-    p.nbands = (K + kFsBand - 1) / kFsBand;
+    p.band = band;
+    p.nbands = (K + band - 1) / band;
     p.ntasks = K * p.nbands;
     p.warp_tiles = (p.ntasks + 31) / 32;
     auto dy0 = [&](int t) {
-        int v = (t / K) * kFsBand - R;
-        if (K >= kFsBand) v = std::min(v, R - kFsBand + 1);
+        int v = (t / K) * band - R;
+        if (K >= band) v = std::min(v, R - band + 1);
         return v;
     };
     int rows = 0;
     for (int w = 0; w < p.warp_tiles; ++w) {
         const int tf = w * 32, tl = std::min(w * 32 + 31, p.ntasks - 1);
-        rows = std::max(rows, dy0(tl) - dy0(tf) + kFsBand - 1 + ctu);
+        rows = std::max(rows, dy0(tl) - dy0(tf) + band - 1 + ctu);
     }
     p.P4 = ctu + 2 * RPc;
     p.box_w = p.P4;
@@ -557,6 +566,7 @@ FullSearchPlan full_search_plan(int bit_depth, int ctu, int R)
 void fill_full_search_batch(FullSearchBatch &b, const FullSearchPlan &p, int R)
 {
     b.R = R;
+    b.band = p.band;
     b.Rp = p.Rp;
     b.ntasks = p.ntasks;
     b.warp_tiles = p.warp_tiles;
@@ -605,24 +615,26 @@ int encode_item_maps(FullSearchBatch &b, int k, const void *cur, const void *ref
 
 cudaError_t prepare_full_search(int bit_depth, int ctu, int R)
 {
-    full_search_ctas_per_sm(bit_depth, ctu, R);  // raises the shared-memory attribute outside any capture
+    // raises the shared-memory attributes outside any capture
+    full_search_ctas_per_sm(bit_depth, ctu, R, kFsBand);
+    if (ctu == 64) full_search_ctas_per_sm(bit_depth, ctu, R, 9);
     return cudaGetLastError();
 }
 
-int full_search_ctas_per_sm(int bit_depth, int ctu, int R)
+int full_search_ctas_per_sm(int bit_depth, int ctu, int R, int band)
 {
-    const FullSearchPlan p = full_search_plan(bit_depth, ctu, R);
+    const FullSearchPlan p = full_search_plan(bit_depth, ctu, R, band);
     OccupancyOp f{p.smem_bytes, 1};
-    dispatch(bit_depth, ctu, p.Rp, f);
+    dispatch(bit_depth, ctu, p.Rp, p.band, f);
     return f.n;
 }
 
 cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchBatch &b, cudaStream_t s)
 {
     if (b.n < 1 || b.n > kMaxItems || b.total <= 0) return cudaErrorInvalidValue;
-    const FullSearchPlan p = full_search_plan(bit_depth, ctu, b.R);
+    const FullSearchPlan p = full_search_plan(bit_depth, ctu, b.R, b.band);
     LaunchOp f{b, p.smem_bytes, s};
-    return dispatch(bit_depth, ctu, p.Rp, f);
+    return dispatch(bit_depth, ctu, p.Rp, p.band, f);
 }
 
 }  // namespace ladder_impl

@@ -97,9 +97,12 @@ SIGNATURES = [
                                                  ctypes.c_int, ctypes.c_int, ctypes.POINTER(Decisions),
                                                  ctypes.c_void_p]),
     ("ladder_version", ctypes.c_char_p, []),
+    ("ladder_set_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    ("ladder_get_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
 ]
 
 KERNEL_KINDS = ("full_search", "decide", "dependent", "fill_keys", "dep_rules", "dep_decide")
+TUNE_KNOBS = {"fs_band": 0, "dep_band": 1, "dep_range": 2, "dep_ctas_per_sm": 3}
 
 _lib = None
 
@@ -358,6 +361,20 @@ class Ladder:
         _call(self.handle, "ladder_capture_batch", self.handle, reqs, len(items), _stream_handle(stream),
               ctypes.byref(g))
         return Graph(g.value, (reqs, self._keep_requests))
+
+    def set_tuning(self, **knobs):
+        """Kernel shapes, e.g. set_tuning(fs_band=9, dep_range=32); results
+        are identical for every setting."""
+        for name, value in knobs.items():
+            _call(self.handle, "ladder_set_tuning", self.handle, TUNE_KNOBS[name], int(value))
+
+    def tuning(self) -> dict:
+        out = {}
+        for name, k in TUNE_KNOBS.items():
+            v = ctypes.c_int()
+            _call(self.handle, "ladder_get_tuning", self.handle, k, ctypes.byref(v))
+            out[name] = v.value
+        return out
 
     def device_bytes(self) -> int:
         return int(load().ladder_device_bytes(self.handle))
