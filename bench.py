@@ -181,20 +181,17 @@ def evals_of(out, grid_size, ctu, rng):
 
 def run_ours(args, wl):
     import torch
-    import torch.distributed as dist
     from paper_2301_12191_gb300 import ladder as L
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl", init_method="env://")
+    from paper_2301_12191_gb300 import replicas
+    rank, world, local = replicas.env()
     torch.cuda.set_device(local)
+    replicas.init("nccl")
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
     n_frames = 4
-    frames = make_frames(wl, n_frames, seed0=1000 * (rank + 1))
+    frames = make_frames(wl, n_frames, seed0=replicas.seed_base(rank))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, frames)      # before any GPU work in this process
@@ -221,8 +218,7 @@ def run_ours(args, wl):
         for i in range(W):
             step(i)
         torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+        replicas.barrier()
         torch.cuda.synchronize()
         evs = []
         for i in range(K):
@@ -234,18 +230,13 @@ def run_ours(args, wl):
             flush.fill_(i & 0xff)          # L2 flush between timed steps (not timed)
             evs.append((a, b))
         torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+        replicas.barrier()
         ms = sum(a.elapsed_time(b) for a, b in evs)
         lad.sync()
         return ms
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(v, dev)
 
     # Work per step from one untimed pass.  One SAD-candidate evaluation = one
     # 8x8 block x one candidate (64 absdiffs).  A full search counts its 8x8
@@ -322,14 +313,12 @@ def run_ours(args, wl):
     for i in range(W):
         step_e2e(i)
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     t0 = time.perf_counter()
     for i in range(K):
         step_e2e(i)
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
 
     props = torch.cuda.get_device_properties(dev)
@@ -406,16 +395,14 @@ def run_ours(args, wl):
     }
     if cpu is not None:
         result["cpu_baseline"] = cpu
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     if rank == 0:
         print(json.dumps(result))
         if args.json_out:
             with open(args.json_out, "w") as fh:
                 json.dump(result, fh, indent=1)
     lad.close()
-    if world > 1:
-        dist.destroy_process_group()
+    replicas.finish()
 
 
 def autotune(args, lad, step, tag, stream):
