@@ -200,12 +200,20 @@ LADDER_API void ladder_graph_destroy(ladder_graph_t *graph);
  *                                pieces of this side
  *   LADDER_TUNE_DEP_CTAS_PER_SM  dependent search grid: CTAs per SM, 0 (as
  *                                many as fit, default) to 8
+ *   LADDER_TUNE_FS_GROUP         full search: consecutive warp tiles of one
+ *                                CTU per CTA, sharing one staged window:
+ *                                0 (automatic, default) to 4
+ *   LADDER_TUNE_FS_FUSE          1 (default): the last full-search CTA of
+ *                                each CTU also takes the CTU's decisions;
+ *                                0: separate key-fill and decision kernels
  * LADDER_E_INVAL for an unknown knob or value. */
 typedef enum {
     LADDER_TUNE_FS_BAND = 0,
     LADDER_TUNE_DEP_BAND = 1,
     LADDER_TUNE_DEP_RANGE = 2,
-    LADDER_TUNE_DEP_CTAS_PER_SM = 3
+    LADDER_TUNE_DEP_CTAS_PER_SM = 3,
+    LADDER_TUNE_FS_GROUP = 4,
+    LADDER_TUNE_FS_FUSE = 5
 } ladder_tune_knob;
 LADDER_API ladder_status ladder_set_tuning(ladder_t *ladder, int knob, int value);
 LADDER_API ladder_status ladder_get_tuning(const ladder_t *ladder, int knob, int *value);

@@ -42,8 +42,11 @@ __global__ void __launch_bounds__(kThreads) k_decide(const __grid_constant__ Dec
         }
         st.flags[i] = flags;
         st.satd[i] = 0;
+        // read the key and reset it to ~0 for the next search
+        unsigned long long *kp = const_cast<unsigned long long *>(keys) + static_cast<long>(ctu_idx) * C::NKEY + i;
+        const unsigned long long key = *kp;
+        *kp = ~0ull;
         if (flags & kRuleEvaluated) {
-            const unsigned long long key = keys[static_cast<long>(ctu_idx) * C::NKEY + i];
             const int rem = static_cast<int>(static_cast<uint32_t>(key & 0xffffffffu) % static_cast<uint32_t>(K * K));
             st.mvx[i] = static_cast<int16_t>(rem % K - b.range);
             st.mvy[i] = static_cast<int16_t>(rem / K - b.range);

@@ -52,14 +52,23 @@ struct ladder {
     size_t arena_bytes = 0;
     int *d_status = nullptr;
     unsigned int *d_counts = nullptr;  // dependent task counters (one per CU size class)
+    // dependent launches share the task lists: each waits for the one
+    // before it (on whatever stream that ran)
+    cudaEvent_t dep_done = nullptr;
+    bool dep_recorded = false;
+    // every argmin key is ~0 at rest (searches reset them after use); after a
+    // failed launch that may not hold, and the next launch fills them first
+    bool keys_dirty = true;
     unsigned long long *d_tasks[kSizeClasses] = {};
+    unsigned int *d_pos[kSizeClasses] = {};
     unsigned int *d_sums[kSizeClasses] = {};
     unsigned int task_cap[kSizeClasses] = {};
     std::string err;
     int sm_count = 0;
     int fs_ctas_per_sm = 1;      // resident full-search CTAs per SM
     // kernel shapes (ladder_set_tuning): results never depend on them
-    int tune_fs_band = kFsBand, tune_dep_band = 0, tune_dep_range = 16, tune_dep_ctas = 0;
+    int tune_fs_band = kFsBand, tune_fs_group = 0, tune_fs_fuse = 1, tune_dep_band = 0, tune_dep_range = 16,
+        tune_dep_ctas = 0;
     char *host_stage = nullptr;  // pinned staging for fetch_decisions
     size_t host_stage_bytes = 0;
     // tracing
@@ -196,6 +205,7 @@ size_t layout(const RungGeom &g, DecOffsets &o)
     o.dep_cy = take(nk * 2);
     o.dep_flags = take(nk);
     o.dep_slot = take(nk * 4);
+    o.done = take(static_cast<size_t>(g.ctu_cols) * g.ctu_rows * 4);
     return off;
 }
 
@@ -270,7 +280,19 @@ struct Job {
 ladder_status launch_independent(ladder_t *l, const Job *jobs, int n, cudaStream_t s)
 {
     const int R = l->geo.ref_search_range;
-    const FullSearchPlan plan = full_search_plan(l->geo.bit_depth, l->geo.ctu_size, R, l->tune_fs_band);
+    // warp tiles per CTA: the knob, or automatically 1 (many small CTAs for
+    // the tail of a small launch) unless the launch has several waves of
+    // tiles, where sharing one staged window between 2 tiles saves work
+    int group = l->tune_fs_group;
+    if (group <= 0) {
+        const FullSearchPlan p1 = full_search_plan(l->geo.bit_depth, l->geo.ctu_size, R, l->tune_fs_band, 1);
+        long tiles = 0;
+        for (int k = 0; k < n; ++k)
+            tiles += static_cast<long>(l->info[jobs[k].rung].g.ctu_cols) * l->info[jobs[k].rung].g.ctu_rows *
+                     p1.warp_tiles;
+        group = tiles >= 6L * l->sm_count * std::max(1, l->fs_ctas_per_sm) ? 2 : 1;
+    }
+    const FullSearchPlan plan = full_search_plan(l->geo.bit_depth, l->geo.ctu_size, R, l->tune_fs_band, group);
     for (int j0 = 0; j0 < n; j0 += kMaxItems) {
         const int m = std::min(kMaxItems, n - j0);
         FillBatch fill{};
@@ -280,6 +302,7 @@ ladder_status launch_independent(ladder_t *l, const Job *jobs, int n, cudaStream
         fb.n = m;
         fill_full_search_batch(fb, plan, R);
         fb.status = l->d_status;
+        for (int r = 0; r < l->geo.n_rungs; ++r) fb.rung[r] = l->info[r];
         db.n = m;
         db.range = R;
         db.satd_mode = l->geo.satd_mode;
@@ -295,22 +318,47 @@ ladder_status launch_independent(ladder_t *l, const Job *jobs, int n, cudaStream
             const int er = encode_item_maps(fb, k, jb.cur, jb.ref, ri.g.W, ri.g.H, jb.pitch, l->geo.bit_depth,
                                             l->geo.ctu_size, plan);
             if (er != 0) return fail(l, LADDER_E_CUDA, "tensor map encoding failed (%d)", er);
-            fb.item[k] = FullSearchItem{ri.g.W, ri.g.H, keys, total_ctas};
+            fb.item[k] = FullSearchItem{ri.g.W,   ri.g.H, keys,   total_ctas, jb.cur,
+                                        jb.ref,   jb.pitch, block, jb.rung,   jb.qp,
+                                        reinterpret_cast<unsigned int *>(block + ri.off.done)};
             db.item[k] = DecideItem{jb.cur, jb.ref, jb.pitch, block, jb.rung, jb.qp, total};
             total += nctus;
-            total_ctas += nctus * plan.warp_tiles;
+            total_ctas += nctus * plan.ctas_per_ctu;
         }
         db.total_ctas = total;
         fb.total = total_ctas;
-        cudaError_t e = traced(l, 3, s, [&] { return launch_fill_keys(fill, s); });
-        if (e != cudaSuccess) return cuda_fail(l, e, "fill keys");
-        e = traced(l, 0, s, [&] {
-            return launch_full_search(l->geo.bit_depth, l->geo.ctu_size, fb, s);
-        });
-        if (e != cudaSuccess) return cuda_fail(l, e, "full search launch");
-        e = traced(l, 1, s, [&] { return launch_decide(l->geo.bit_depth, l->geo.ctu_size, db, s); });
-        if (e != cudaSuccess) return cuda_fail(l, e, "decide launch");
+        // fused: keys are ~0 at rest and the last CTA of each CTU takes its
+        // decisions (and resets its keys); otherwise fill + search + decide
+        const bool fuse = !l->keys_dirty && l->tune_fs_fuse;
+        fb.fuse_decide = fuse ? 1 : 0;
+        fb.satd_mode = l->geo.satd_mode;
+        cudaError_t e = cudaSuccess;
+        if (!fuse) {
+            // after a failed launch: counters back to zero, keys to ~0
+            for (int k = 0; k < m && e == cudaSuccess; ++k) {
+                const RungInfo &ri = l->info[jobs[j0 + k].rung];
+                e = cudaMemsetAsync(fb.item[k].done, 0, static_cast<size_t>(ri.g.ctu_cols) * ri.g.ctu_rows * 4, s);
+            }
+            if (e == cudaSuccess) e = traced(l, 3, s, [&] { return launch_fill_keys(fill, s); });
+            if (e != cudaSuccess) {
+                l->keys_dirty = true;
+                return cuda_fail(l, e, "fill keys");
+            }
+        }
+        e = traced(l, 0, s, [&] { return launch_full_search(l->geo.bit_depth, l->geo.ctu_size, fb, s); });
+        if (e != cudaSuccess) {
+            l->keys_dirty = true;
+            return cuda_fail(l, e, "full search launch");
+        }
+        if (!fuse) {
+            e = traced(l, 1, s, [&] { return launch_decide(l->geo.bit_depth, l->geo.ctu_size, db, s); });
+            if (e != cudaSuccess) {
+                l->keys_dirty = true;
+                return cuda_fail(l, e, "decide launch");
+            }
+        }
     }
+    l->keys_dirty = false;  // every search above left its keys at ~0
     for (int k = 0; k < n; ++k) jobs[k].slot->rungs[jobs[k].rung].analysed = 1;
     return LADDER_OK;
 }
@@ -319,6 +367,15 @@ ladder_status launch_independent(ladder_t *l, const Job *jobs, int n, cudaStream
 // counters reset, rules + task lists, search, decisions.
 ladder_status launch_dependents(ladder_t *l, const Job *jobs, int n, cudaStream_t s)
 {
+    // the task lists are per handle: wait for the previous dependent launch
+    // (not inside a graph capture: a captured batch is one ordered stream)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap);
+    const bool chain = cap == cudaStreamCaptureStatusNone;
+    if (chain && l->dep_recorded) {
+        const cudaError_t e = cudaStreamWaitEvent(s, l->dep_done, 0);
+        if (e != cudaSuccess) return cuda_fail(l, e, "dependent ordering");
+    }
     for (int j0 = 0; j0 < n; j0 += kMaxDepItems) {
         const int m = std::min(kMaxDepItems, n - j0);
         DependentBatch b{};
@@ -337,6 +394,7 @@ ladder_status launch_dependents(ladder_t *l, const Job *jobs, int n, cudaStream_
         b.one = 1;
         for (int c = 0; c < kSizeClasses; ++c) {
             b.tasks[c] = l->d_tasks[c];
+            b.pos[c] = l->d_pos[c];
             b.sums[c] = l->d_sums[c];
             b.cap[c] = l->task_cap[c];
         }
@@ -353,11 +411,18 @@ ladder_status launch_dependents(ladder_t *l, const Job *jobs, int n, cudaStream_
         cudaError_t e = cudaMemsetAsync(l->d_counts, 0, kSizeClasses * sizeof(unsigned int), s);
         if (e != cudaSuccess) return cuda_fail(l, e, "task counters");
         e = traced(l, 4, s, [&] { return launch_dependent_rules(l->geo.ctu_size, b, s); });
-        if (e != cudaSuccess) return cuda_fail(l, e, "dependent rules launch");
-        e = traced(l, 2, s, [&] { return launch_dependent_search(l->geo.bit_depth, b, s); });
-        if (e != cudaSuccess) return cuda_fail(l, e, "dependent search launch");
-        e = traced(l, 5, s, [&] { return launch_dependent_decide(l->geo.bit_depth, l->geo.ctu_size, b, s); });
-        if (e != cudaSuccess) return cuda_fail(l, e, "dependent decide launch");
+        if (e == cudaSuccess) e = traced(l, 2, s, [&] { return launch_dependent_search(l->geo.bit_depth, b, s); });
+        if (e == cudaSuccess)
+            e = traced(l, 5, s, [&] { return launch_dependent_decide(l->geo.bit_depth, l->geo.ctu_size, b, s); });
+        if (e != cudaSuccess) {
+            l->keys_dirty = true;
+            return cuda_fail(l, e, "dependent launch");
+        }
+    }
+    if (chain) {
+        const cudaError_t e = cudaEventRecord(l->dep_done, s);
+        if (e != cudaSuccess) return cuda_fail(l, e, "dependent ordering");
+        l->dep_recorded = true;
     }
     for (int k = 0; k < n; ++k) jobs[k].slot->rungs[jobs[k].rung].analysed = 2;
     return LADDER_OK;
@@ -413,7 +478,7 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
                                                        : 0;
         const size_t cap = dep_ctus * per_ctu * geometry->max_frames;
         l->task_cap[c] = static_cast<unsigned int>(std::min<size_t>(cap, 0xffffffffu));
-        task_bytes += align_up(cap * 8, 256);
+        task_bytes += align_up(cap * 8, 256) + align_up(cap * 4, 256);
         if (c >= kFirstSummedClass) task_bytes += align_up(cap * kr2 * 4, 256);
     }
     const size_t fixed = 256 + task_bytes;
@@ -432,6 +497,8 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
         for (int c = 0; c < kSizeClasses; ++c) {
             l->d_tasks[c] = reinterpret_cast<unsigned long long *>(tp);
             tp += align_up(static_cast<size_t>(l->task_cap[c]) * 8, 256);
+            l->d_pos[c] = reinterpret_cast<unsigned int *>(tp);
+            tp += align_up(static_cast<size_t>(l->task_cap[c]) * 4, 256);
             if (c >= kFirstSummedClass) {
                 l->d_sums[c] = reinterpret_cast<unsigned int *>(tp);
                 tp += align_up(static_cast<size_t>(l->task_cap[c]) * kr2 * 4, 256);
@@ -461,9 +528,29 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
         return LADDER_E_NOMEM;
     }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    e = cudaMemsetAsync(l->arena, 0, 256, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    e = cudaMemsetAsync(l->arena, 0, l->arena_bytes, s);  // counters and per-CTU done counts at zero
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l->dep_done, cudaEventDisableTiming);
+    // every key of every slot to ~0 (searches keep that at rest)
+    if (e == cudaSuccess) {
+        FillBatch fill{};
+        for (auto &sl : l->slots)
+            for (size_t r = 0; r < l->info.size() && e == cudaSuccess; ++r) {
+                const RungInfo &ri = l->info[r];
+                fill.item[fill.n++] = FillItem{reinterpret_cast<unsigned long long *>(sl.rungs[r].block + ri.off.keys),
+                                               static_cast<long>(ri.g.ctu_cols) * ri.g.ctu_rows * keys_per_ctu(ri.g.dmax)};
+                if (fill.n == kMaxItems) {
+                    e = launch_fill_keys(fill, s);
+                    fill.n = 0;
+                }
+            }
+        if (e == cudaSuccess && fill.n > 0) e = launch_fill_keys(fill, s);
+    }
+    if (e == cudaSuccess) {
+        e = cudaStreamSynchronize(s);
+        l->keys_dirty = e != cudaSuccess;
+    }
     if (e != cudaSuccess) {
+        if (l->dep_done) cudaEventDestroy(l->dep_done);
         cudaFreeHost(l->host_stage);
         cudaFree(l->arena);
         delete l;
@@ -826,6 +913,14 @@ ladder_status ladder_set_tuning(ladder_t *l, int knob, int value)
         if (value < 0 || value > 8) return fail(l, LADDER_E_INVAL, "CTAs per SM %d (0..8)", value);
         l->tune_dep_ctas = value;
         return LADDER_OK;
+    case LADDER_TUNE_FS_GROUP:
+        if (value < 0 || value > kFsMaxGroup) return fail(l, LADDER_E_INVAL, "tiles per CTA %d (0..%d)", value, kFsMaxGroup);
+        l->tune_fs_group = value;
+        return LADDER_OK;
+    case LADDER_TUNE_FS_FUSE:
+        if (value != 0 && value != 1) return fail(l, LADDER_E_INVAL, "fuse %d (0 or 1)", value);
+        l->tune_fs_fuse = value;
+        return LADDER_OK;
     default:
         return fail(l, LADDER_E_INVAL, "unknown tuning knob %d", knob);
     }
@@ -839,6 +934,8 @@ ladder_status ladder_get_tuning(const ladder_t *l, int knob, int *value)
     case LADDER_TUNE_DEP_BAND: *value = l->tune_dep_band; return LADDER_OK;
     case LADDER_TUNE_DEP_RANGE: *value = l->tune_dep_range; return LADDER_OK;
     case LADDER_TUNE_DEP_CTAS_PER_SM: *value = l->tune_dep_ctas; return LADDER_OK;
+    case LADDER_TUNE_FS_GROUP: *value = l->tune_fs_group; return LADDER_OK;
+    case LADDER_TUNE_FS_FUSE: *value = l->tune_fs_fuse; return LADDER_OK;
     default: return LADDER_E_INVAL;
     }
 }
@@ -851,6 +948,7 @@ void ladder_destroy(ladder_t *l)
     cudaDeviceSynchronize();
     drain_events(l);
     for (cudaEvent_t e : l->spare) cudaEventDestroy(e);
+    if (l->dep_done) cudaEventDestroy(l->dep_done);
     cudaFreeHost(l->host_stage);
     cudaFree(l->arena);
     delete l;

@@ -57,6 +57,7 @@ struct DecOffsets {
     long split[kMaxDepths], evaluated[kMaxDepths];
     long leaf_depth, leaf_mvx, leaf_mvy;
     long keys;
+    long done;  // per CTU: full-search CTAs finished (zero at rest)
     // dependent rungs: per CTU and key slot, the search centre, rule flags
     // and (CUs of 32x32 and up) the CU's place in its task list
     long dep_cx, dep_cy, dep_flags, dep_slot;
@@ -95,21 +96,29 @@ constexpr int kMaxDepItems = kMaxItems * 3;      // dependent (frame, rung) pair
 // One item = one frame's independently analysed rung.  One CTA per (CTU,
 // warp tile of candidates); kernel parameters are grid-constant (CUDA 12.1+
 // allows 32 KB), the tensor maps included.
-constexpr int kFsBand = 13;  // candidate rows (dy) per lane task
+constexpr int kFsBand = 13;    // candidate rows (dy) per lane task
+constexpr int kFsMaxGroup = 4;  // warp tiles one full-search CTA may take
 
 struct FullSearchItem {
     int W, H;
-    unsigned long long *keys;  // per CTU keys_per_ctu(dmax), initialised to ~0
-    int cta_begin;             // first work item of this frame: CTUs x warp_tiles items, CTU-major
+    unsigned long long *keys;  // per CTU keys_per_ctu(dmax), ~0 before the search
+    int cta_begin;             // first CTA of this frame: CTUs x ctas_per_ctu CTAs, CTU-major
+    // the decisions, when the search takes them too (fuse_decide)
+    const void *cur, *ref;
+    long pitch_bytes;
+    char *block;               // the (slot, rung) block
+    int rung, qp;
+    unsigned int *done;        // per CTU: CTAs finished (fuse_decide; zero before and after)
 };
 
 struct FullSearchBatch {
     int n;
     int R;            // search range
     int band;         // candidate rows per lane task (13, or 9 for 64x64 CTUs)
+    int group;        // consecutive warp tiles of one CTU per CTA (one staged window)
     int Rp;           // left window margin: R rounded up to 16 samples
     int ntasks;       // lane tasks (dx, band of kFsBand dy) per CTU
-    int warp_tiles;   // CTAs per CTU: ceil(ntasks / 32)
+    int warp_tiles;   // warp tiles per CTU: ceil(ntasks / 32)
     int box_h;        // rows of the TMA box (the most any warp tile needs)
     int e_bytes;      // shared bytes of the expanded window (box_h x positions x 4)
     int stage_off;    // byte offset of the staged rows inside the expanded window
@@ -118,6 +127,11 @@ struct FullSearchBatch {
     int total;        // CTAs of the batch
     uint32_t one;     // 1, as an operand the compiler cannot fold
     int *status;
+    // fuse_decide: the last CTA to finish a CTU also takes the CTU's
+    // decisions (SATD, cost, split, leaf maps) and resets its keys to ~0
+    int fuse_decide;
+    int satd_mode;
+    RungInfo rung[kMaxRungs];
     FullSearchItem item[kMaxItems];
     CUtensorMap map[kMaxItems];      // reference plane of each item (box: window positions x box_h rows)
     CUtensorMap cur_map[kMaxItems];  // current plane of each item (box: CTU x CTU)
@@ -126,6 +140,7 @@ struct FullSearchBatch {
 struct FullSearchPlan {
     int Rp;
     int band, nbands, ntasks, warp_tiles;
+    int group, ctas_per_ctu;  // warp tiles per CTA, CTAs per CTU
     int P4;           // window positions per row
     int box_w, box_h; // TMA box (samples x rows)
     int e_bytes, stage_off, phase1_rows, buf_bytes;
@@ -134,7 +149,9 @@ struct FullSearchPlan {
 
 // Returns the plan for bit depth / CTU / R / band (13 or 9 candidate rows
 // per lane task; 9 only with 64x64 CTUs).
-FullSearchPlan full_search_plan(int bit_depth, int ctu, int R, int band = kFsBand);
+// `group` warp tiles share one CTA and its window (reduced while the window
+// would exceed the kernels' bound).
+FullSearchPlan full_search_plan(int bit_depth, int ctu, int R, int band = kFsBand, int group = 1);
 // Tiled 2-D tensor map of a W x H plane (8-bit: uint8, 10-bit: uint16
 // samples), box box_w x box_h samples, zero fill outside the plane.
 // Returns 0 on success, else the driver's error (or -1: encoder unavailable).
@@ -146,8 +163,8 @@ int encode_item_maps(FullSearchBatch &b, int k, const void *cur, const void *ref
 // Copies the plan's launch constants into a batch.
 void fill_full_search_batch(FullSearchBatch &b, const FullSearchPlan &p, int R);
 // Resident full-search CTAs per SM for this plan (occupancy calculator).
-int full_search_ctas_per_sm(int bit_depth, int ctu, int R, int band = kFsBand);
-// One CTA per work item: b.total = sum over frames of CTUs x warp_tiles.
+int full_search_ctas_per_sm(int bit_depth, int ctu, int R, int band = kFsBand, int group = 1);
+// One CTA per work item: b.total = sum over frames of CTUs x ceil(warp_tiles / group).
 cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchBatch &b, cudaStream_t s);
 
 // ---- decision step of independently analysed rungs -------------------------
@@ -211,6 +228,7 @@ struct DependentBatch {
     int total_ctas;         // CTUs of the batch
     int *status;
     unsigned long long *tasks[kSizeClasses];  // per size class, capacity cap[c]
+    unsigned int *pos[kSizeClasses];          // per task: the CU's origin, x | y << 16
     unsigned int *sums[kSizeClasses];         // classes >= kFirstSummedClass: cap[c] x (2r+1)^2
     unsigned int cap[kSizeClasses];
     unsigned int *counts;   // kSizeClasses counters, zero before the rules kernel

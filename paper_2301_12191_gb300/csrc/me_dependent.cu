@@ -33,7 +33,6 @@ __constant__ int c_lambda_q16[52] = {
 #include "lambda_table.inc"
 };
 
-constexpr int kRulesThreads = 128;
 constexpr int kSearchThreads = 256;
 constexpr int kDecideThreads = 128;
 
@@ -52,118 +51,135 @@ __device__ __forceinline__ int depth_of(int i, int dmax)
 }
 
 // ---- 1. rules ---------------------------------------------------------------
+// One warp per CTU, kRulesCtus CTUs per CTA: the work per CTU is small, so
+// a CTA covers several and takes one task-list reservation per size class
+// for all of them (few global atomics on the shared counters).
+constexpr int kRulesCtus = 8;
+
 template <int CTU>
-__global__ void __launch_bounds__(kRulesThreads) k_dep_rules(const __grid_constant__ DependentBatch b)
+__global__ void __launch_bounds__(32 * kRulesCtus) k_dep_rules(const __grid_constant__ DependentBatch b)
 {
     using C = dev::Ctu<CTU>;
-    constexpr int NT = kRulesThreads;
-    const int ri = item_of(b);
+    constexpr int NK = C::NKEY;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gctu = blockIdx.x * kRulesCtus + w;  // CTU of this warp across the batch
+    const bool active = gctu < b.total_ctas;
+
+    __shared__ int16_t s_cx[kRulesCtus][NK], s_cy[kRulesCtus][NK];
+    __shared__ uint8_t s_leaf[kRulesCtus][NK], s_splitok[kRulesCtus][NK], s_flags[kRulesCtus][NK];
+    __shared__ int s_pos[kRulesCtus][NK];
+    __shared__ unsigned int s_cnt[kSizeClasses], s_base[kSizeClasses];
+    if (threadIdx.x < kSizeClasses) s_cnt[threadIdx.x] = 0;
+
+    int ri = 0;
+    while (active && ri + 1 < b.n && gctu >= b.item[ri + 1].cta_begin) ++ri;
     const DependentItem &a = b.item[ri];
     const RungInfo &rinf = b.rung[a.rung];
     const RungInfo &rref = b.rung[b.ref_rung];
     const RungGeom &g = rinf.g;
-    DepRefs refs;
-    refs.Wr = rref.g.W;
-    refs.Hr = rref.g.H;
-    refs.cols8_r = rref.g.cols8;
-    refs.leaf_depth = reinterpret_cast<const uint8_t *>(a.ref_block + rref.off.leaf_depth);
-    refs.leaf_mvx = reinterpret_cast<const int16_t *>(a.ref_block + rref.off.leaf_mvx);
-    refs.leaf_mvy = reinterpret_cast<const int16_t *>(a.ref_block + rref.off.leaf_mvy);
-    refs.depth_lo = b.depth_lo;
-    refs.depth_hi = b.depth_hi;
-    refs.use_ref_mv = b.use_ref_mv;
-
-    __shared__ int16_t s_cx[C::NKEY], s_cy[C::NKEY];
-    __shared__ uint8_t s_leaf[C::NKEY], s_splitok[C::NKEY], s_flags[C::NKEY];
-    __shared__ unsigned int s_cnt[kSizeClasses], s_base[kSizeClasses];
-
-    const int tid = threadIdx.x;
-    const int ctu_idx = blockIdx.x - a.cta_begin;
+    const int ctu_idx = gctu - a.cta_begin;
     const int x0 = (ctu_idx % g.ctu_cols) * CTU, y0 = (ctu_idx / g.ctu_cols) * CTU;
-    const long kbase = static_cast<long>(ctu_idx) * C::NKEY;
-
-    for (int i = tid; i < C::NKEY; i += NT) {
-        const int d = depth_of(i, C::DMAX);
-        const int li = i - key_offset(d), n = 1 << d, S = CTU >> d;
-        const int cu_x = x0 + (li % n) * S, cu_y = y0 + (li / n) * S;
-        const bool present = cu_x < g.W8 && cu_y < g.H8;
-        uint8_t leaf = 0, splitok = 0;
-        int16_t cx = 0, cy = 0;
-        if (present) {
-            const bool inside = cu_x + S <= g.W8 && cu_y + S <= g.H8;
-            const dev::Rule ru = dev::derive_rule(g, refs, d, cu_x, cu_y);
-            cx = static_cast<int16_t>(ru.cx);
-            cy = static_cast<int16_t>(ru.cy);
-            leaf = inside && ru.allowed_leaf;
-            splitok = d < C::DMAX && (!inside || ru.allowed_split);
-        }
-        s_cx[i] = cx;
-        s_cy[i] = cy;
-        s_leaf[i] = leaf;
-        s_splitok[i] = splitok;
-        s_flags[i] = present ? dev::kPresent : 0;
-    }
-    if (tid < kSizeClasses) s_cnt[tid] = 0;
+    const long kbase = static_cast<long>(ctu_idx) * NK;
     __syncthreads();
 
-    // reachability (every ancestor may split) and the rule flags
-    int16_t *const out_cx = reinterpret_cast<int16_t *>(a.block + rinf.off.dep_cx) + kbase;
-    int16_t *const out_cy = reinterpret_cast<int16_t *>(a.block + rinf.off.dep_cy) + kbase;
-    uint8_t *const out_fl = reinterpret_cast<uint8_t *>(a.block + rinf.off.dep_flags) + kbase;
-    unsigned long long *const keys = reinterpret_cast<unsigned long long *>(a.block + rinf.off.keys) + kbase;
-    for (int i = tid; i < C::NKEY; i += NT) {
-        uint8_t f = s_flags[i];
-        if (f & dev::kPresent) {
+    if (active) {
+        DepRefs refs;
+        refs.Wr = rref.g.W;
+        refs.Hr = rref.g.H;
+        refs.cols8_r = rref.g.cols8;
+        refs.leaf_depth = reinterpret_cast<const uint8_t *>(a.ref_block + rref.off.leaf_depth);
+        refs.leaf_mvx = reinterpret_cast<const int16_t *>(a.ref_block + rref.off.leaf_mvx);
+        refs.leaf_mvy = reinterpret_cast<const int16_t *>(a.ref_block + rref.off.leaf_mvy);
+        refs.depth_lo = b.depth_lo;
+        refs.depth_hi = b.depth_hi;
+        refs.use_ref_mv = b.use_ref_mv;
+        for (int i = lane; i < NK; i += 32) {
             const int d = depth_of(i, C::DMAX);
-            const int li = i - key_offset(d), n = 1 << d;
-            const int cxl = li % n, cyl = li / n;
-            bool reach = true;
-            for (int e = 0; e < d; ++e)
-                reach = reach && s_splitok[dev::key_index(e, (cyl >> (d - e)) * (1 << e) + (cxl >> (d - e)))];
-            if (reach) f |= kRuleReachable;
-            if (reach && s_leaf[i]) f |= kRuleEvaluated;
-            if (reach && s_splitok[i]) f |= kRuleCanSplit;
-            if (f & kRuleEvaluated) atomicAdd(&s_cnt[C::DMAX - d], 1u);  // size class of an S = CTU >> d CU
+            const int li = i - key_offset(d), n = 1 << d, S = CTU >> d;
+            const int cu_x = x0 + (li % n) * S, cu_y = y0 + (li / n) * S;
+            const bool present = cu_x < g.W8 && cu_y < g.H8;
+            uint8_t leaf = 0, splitok = 0;
+            int16_t cx = 0, cy = 0;
+            if (present) {
+                const bool inside = cu_x + S <= g.W8 && cu_y + S <= g.H8;
+                const dev::Rule ru = dev::derive_rule(g, refs, d, cu_x, cu_y);
+                cx = static_cast<int16_t>(ru.cx);
+                cy = static_cast<int16_t>(ru.cy);
+                leaf = inside && ru.allowed_leaf;
+                splitok = d < C::DMAX && (!inside || ru.allowed_split);
+            }
+            s_cx[w][i] = cx;
+            s_cy[w][i] = cy;
+            s_leaf[w][i] = leaf;
+            s_splitok[w][i] = splitok;
+            s_flags[w][i] = present ? dev::kPresent : 0;
         }
-        s_flags[i] = f;
-        out_cx[i] = s_cx[i];
-        out_cy[i] = s_cy[i];
-        out_fl[i] = f;
-        keys[i] = ~0ull;
+        __syncwarp();
+        // reachability (every ancestor may split) and the rule flags
+        int16_t *const out_cx = reinterpret_cast<int16_t *>(a.block + rinf.off.dep_cx) + kbase;
+        int16_t *const out_cy = reinterpret_cast<int16_t *>(a.block + rinf.off.dep_cy) + kbase;
+        uint8_t *const out_fl = reinterpret_cast<uint8_t *>(a.block + rinf.off.dep_flags) + kbase;
+        unsigned long long *const keys = reinterpret_cast<unsigned long long *>(a.block + rinf.off.keys) + kbase;
+        for (int i = lane; i < NK; i += 32) {
+            uint8_t f = s_flags[w][i];
+            if (f & dev::kPresent) {
+                const int d = depth_of(i, C::DMAX);
+                const int li = i - key_offset(d), n = 1 << d;
+                const int cxl = li % n, cyl = li / n;
+                bool reach = true;
+                for (int e = 0; e < d; ++e)
+                    reach = reach && s_splitok[w][dev::key_index(e, (cyl >> (d - e)) * (1 << e) + (cxl >> (d - e)))];
+                if (reach) f |= kRuleReachable;
+                if (reach && s_leaf[w][i]) f |= kRuleEvaluated;
+                if (reach && s_splitok[w][i]) f |= kRuleCanSplit;
+                if (f & kRuleEvaluated) atomicAdd(&s_cnt[C::DMAX - d], 1u);  // size class of an S = CTU >> d CU
+            }
+            s_flags[w][i] = f;
+            out_cx[i] = s_cx[w][i];
+            out_cy[i] = s_cy[w][i];
+            out_fl[i] = f;
+            keys[i] = ~0ull;
+        }
     }
     __syncthreads();
-    if (tid < kSizeClasses) {
-        const unsigned int n = s_cnt[tid];
+    if (threadIdx.x < kSizeClasses) {
+        const unsigned int n = s_cnt[threadIdx.x];
         unsigned int base = 0;
-        if (n) base = atomicAdd(&b.counts[tid], n);
-        if (n && base + n > b.cap[tid]) atomicExch(b.status, kStatusTaskOverflow);
-        s_base[tid] = base;
-        s_cnt[tid] = 0;
+        if (n) base = atomicAdd(&b.counts[threadIdx.x], n);
+        if (n && base + n > b.cap[threadIdx.x]) atomicExch(b.status, kStatusTaskOverflow);
+        s_base[threadIdx.x] = base;
+        s_cnt[threadIdx.x] = 0;
     }
     __syncthreads();
-    __shared__ int s_pos[C::NKEY];
-    for (int i = tid; i < C::NKEY; i += NT) {
-        s_pos[i] = -1;
-        if (!(s_flags[i] & kRuleEvaluated)) continue;
+    if (!active) return;
+    for (int i = lane; i < NK; i += 32) {
+        s_pos[w][i] = -1;
+        if (!(s_flags[w][i] & kRuleEvaluated)) continue;
         const int c = C::DMAX - depth_of(i, C::DMAX);  // size class: CU size 8 << c
         const unsigned int pos = s_base[c] + atomicAdd(&s_cnt[c], 1u);
         if (pos >= b.cap[c]) continue;
         const uint32_t lo = static_cast<uint32_t>(ri) | (static_cast<uint32_t>(kbase + i) << 8);
-        const uint32_t hi = static_cast<uint32_t>(static_cast<uint16_t>(s_cx[i])) |
-                            (static_cast<uint32_t>(static_cast<uint16_t>(s_cy[i])) << 16);
+        const uint32_t hi = static_cast<uint32_t>(static_cast<uint16_t>(s_cx[w][i])) |
+                            (static_cast<uint32_t>(static_cast<uint16_t>(s_cy[w][i])) << 16);
         b.tasks[c][pos] = (static_cast<unsigned long long>(hi) << 32) | lo;
-        s_pos[i] = static_cast<int>(pos);
+        {
+            const int d = depth_of(i, C::DMAX);
+            const int li = i - key_offset(d), n = 1 << d, S = CTU >> d;
+            b.pos[c][pos] = static_cast<unsigned int>(x0 + (li % n) * S) |
+                            (static_cast<unsigned int>(y0 + (li / n) * S) << 16);
+        }
+        s_pos[w][i] = static_cast<int>(pos);
     }
-    __syncthreads();
-    // CUs searched in ranges: their list place, and a zeroed sum table
+    __syncwarp();
+    // CUs searched in pieces: their list place, and a zeroed sum table
     int *const out_slot = reinterpret_cast<int *>(a.block + rinf.off.dep_slot) + kbase;
     const int KK = (2 * b.r + 1) * (2 * b.r + 1);
-    for (int i = tid; i < C::NKEY; i += NT) out_slot[i] = s_pos[i];
+    for (int i = lane; i < NK; i += 32) out_slot[i] = s_pos[w][i];
     constexpr int NBIG = key_offset(C::DMAX - kFirstSummedClass + 1);  // CUs of 32x32 and up
     for (int i = 0; i < NBIG; ++i) {
-        if (s_pos[i] < 0 || (CTU >> depth_of(i, C::DMAX)) <= b.range) continue;
-        unsigned int *sum = b.sums[C::DMAX - depth_of(i, C::DMAX)] + static_cast<long>(s_pos[i]) * KK;
-        for (int k = tid; k < KK; k += NT) sum[k] = 0;
+        if (s_pos[w][i] < 0 || (CTU >> depth_of(i, C::DMAX)) <= b.range) continue;
+        unsigned int *sum = b.sums[C::DMAX - depth_of(i, C::DMAX)] + static_cast<long>(s_pos[w][i]) * KK;
+        for (int k = lane; k < KK; k += 32) sum[k] = 0;
     }
 }
 
@@ -246,23 +262,28 @@ __device__ __noinline__ void block_sads_edge(const char *cur, const char *ref, l
 
 // Adds the 8x8 block SADs at (bx, by) of the TY candidates (x, y + i),
 // i < TY, to acc (8-bit samples).
-template <int TY>
+// Adds the SADs of the 8-wide, 8*NBV-high column of current blocks at
+// (bx, by) for the TY candidates (x, y + i), i < TY, to acc (8-bit samples).
+template <int TY, int NBV>
 __device__ __forceinline__ void block_sads_u8(const char *cur, const char *ref, long pitch, int W, int H, int bx,
                                               int by, int x, int y, uint32_t (&acc)[TY])
 {
-    constexpr int NR = 8 + TY - 1;
+    constexpr int CR = 8 * NBV, NR = CR + TY - 1;
     const int q = (x - 1) >> 2;  // words q .. q+2 hold samples x .. x+7
     const bool fast = bx + 8 <= W && x >= 1 && 4 * q + 12 <= W && y >= 0 && y + NR <= H;
     if (!fast) {
-        uint32_t e[TY];
-        block_sads_edge<uint8_t, TY>(cur, ref, pitch, W, H, bx, by, x, y, 1u, e);
+#pragma unroll 1
+        for (int v = 0; v < NBV; ++v) {
+            uint32_t e[TY];
+            block_sads_edge<uint8_t, TY>(cur, ref, pitch, W, H, bx, by + 8 * v, x, y + 8 * v, 1u, e);
 #pragma unroll
-        for (int i = 0; i < TY; ++i) acc[i] += e[i];
+            for (int i = 0; i < TY; ++i) acc[i] += e[i];
+        }
         return;
     }
-    uint2 c[8];
+    uint2 c[CR];
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
+    for (int j = 0; j < CR; ++j)
         c[j] = __ldg(reinterpret_cast<const uint2 *>(cur + static_cast<long>(min(by + j, H - 1)) * pitch + bx));
     const uint32_t m = 1u << (32 - 8 * (x - 4 * q));  // x - 4q in 1..4
     const uint32_t *rp = reinterpret_cast<const uint32_t *>(ref + static_cast<long>(y) * pitch) + q;
@@ -274,12 +295,12 @@ __device__ __forceinline__ void block_sads_u8(const char *cur, const char *ref, 
 #pragma unroll
         for (int i = 0; i < TY; ++i) {
             const int j = r - i;
-            if (j >= 0 && j < 8) acc[i] = dev::sad_acc<4>(c[j].x, w0, acc[i]);
+            if (j >= 0 && j < CR) acc[i] = dev::sad_acc<4>(c[j].x, w0, acc[i]);
         }
 #pragma unroll
         for (int i = 0; i < TY; ++i) {
             const int j = r - i;
-            if (j >= 0 && j < 8) acc[i] = dev::sad_acc<4>(c[j].y, w1, acc[i]);
+            if (j >= 0 && j < CR) acc[i] = dev::sad_acc<4>(c[j].y, w1, acc[i]);
         }
     }
 }
@@ -380,13 +401,9 @@ __device__ __forceinline__ void search_tile(const DependentBatch &b, int c, int 
     const DependentItem &a = b.item[lo & 0xffu];
     const RungInfo &rinf = b.rung[a.rung];
     const RungGeom &g = rinf.g;
-    const int nkey = keys_per_ctu(g.dmax);
-    const int gslot = static_cast<int>(lo >> 8);
-    const int ctu_idx = gslot / nkey, ks = gslot - ctu_idx * nkey;
-    const int d = depth_of(ks, g.dmax);
-    const int li = ks - key_offset(d), n = 1 << d;
-    const int cu_x = (ctu_idx % g.ctu_cols) * g.ctu + (li % n) * S + (rg % nrs) * RS;  // this range's origin
-    const int cu_y = (ctu_idx / g.ctu_cols) * g.ctu + (li / n) * S + (rg / nrs) * RS;
+    const unsigned int p = b.pos[c][u];
+    const int cu_x = static_cast<int>(p & 0xffffu) + (rg % nrs) * RS;  // this piece's origin
+    const int cu_y = static_cast<int>(p >> 16) + (rg / nrs) * RS;
     const int cx = static_cast<int16_t>(hi & 0xffffu), cy = static_cast<int16_t>(hi >> 16);
     const int dxo = dxi - r;  // offsets from the centre
     const int b0 = band * TY - r;
@@ -397,13 +414,23 @@ __device__ __forceinline__ void search_tile(const DependentBatch &b, int c, int 
     for (int i = 0; i < TY; ++i) acc[i] = 0;
     const char *cur = static_cast<const char *>(a.cur), *ref = static_cast<const char *>(a.ref);
     const int nb = RS / 8;
+    if constexpr (sizeof(T) == 1) {
+        if (nb >= 2) {
+            // columns of two stacked blocks: the candidate rows they share are read once
 #pragma unroll 1
-    for (int blk = 0; blk < nb * nb; ++blk) {
-        const int bx = cu_x + 8 * (blk % nb), by = cu_y + 8 * (blk / nb);
-        if constexpr (sizeof(T) == 1)
-            block_sads_u8<TY>(cur, ref, a.pitch_bytes, g.W, g.H, bx, by, bx + cx + dxo, by + cy + dy0, acc);
-        else
+            for (int col = 0; col < nb * nb / 2; ++col) {
+                const int bx = cu_x + 8 * (col % nb), by = cu_y + 16 * (col / nb);
+                block_sads_u8<TY, 2>(cur, ref, a.pitch_bytes, g.W, g.H, bx, by, bx + cx + dxo, by + cy + dy0, acc);
+            }
+        } else {
+            block_sads_u8<TY, 1>(cur, ref, a.pitch_bytes, g.W, g.H, cu_x, cu_y, cu_x + cx + dxo, cu_y + cy + dy0, acc);
+        }
+    } else {
+#pragma unroll 1
+        for (int blk = 0; blk < nb * nb; ++blk) {
+            const int bx = cu_x + 8 * (blk % nb), by = cu_y + 8 * (blk / nb);
             block_sads_u16<TY>(cur, ref, a.pitch_bytes, g.W, g.H, bx, by, bx + cx + dxo, by + cy + dy0, b.one, acc);
+        }
     }
 
     if (nr > 1) {
@@ -421,8 +448,10 @@ __device__ __forceinline__ void search_tile(const DependentBatch &b, int c, int 
         return;
     }
 
-    // keys; candidate rows past +r (only when 2r + 1 < TY) never win
+    // keys; candidate rows past +r (only when 2r + 1 < TY) never win.
+    // code = (|dx|+|dy|) 2K + 2 (dy + r) + [dx > 0]
     const int bits = sad_bits(S, sizeof(T) == 1 ? 8 : 10);
+    const uint32_t cbase = static_cast<uint32_t>(abs(dxo) * 2 * K + 2 * (dy0 + r) + (dxo > 0));
     unsigned long long best = ~0ull;
     if (bits + rb <= 32) {
         uint32_t k = 0xffffffffu;
@@ -430,9 +459,8 @@ __device__ __forceinline__ void search_tile(const DependentBatch &b, int c, int 
         for (int i = 0; i < TY; ++i) {
             const int dyo = dy0 + i;
             const bool ok = dyo <= r;
-            const uint32_t code = static_cast<uint32_t>((abs(dxo) + abs(dyo)) * 2 * K + 2 * (dyo + r) + (dxo > 0));
-            const uint32_t key = umad(acc[i], ok ? (1u << rb) : 0u, ok ? code : 0xffffffffu);
-            k = min(k, key);
+            const uint32_t code = umad(static_cast<uint32_t>(abs(dyo)), 2u * K, cbase + 2u * i);
+            k = min(k, umad(acc[i], ok ? (1u << rb) : 0u, ok ? code : 0xffffffffu));
         }
         best = k == 0xffffffffu ? ~0ull : k;
     } else {
@@ -440,19 +468,21 @@ __device__ __forceinline__ void search_tile(const DependentBatch &b, int c, int 
         for (int i = 0; i < TY; ++i) {
             const int dyo = dy0 + i;
             if (dyo > r) continue;
-            const uint32_t code = static_cast<uint32_t>((abs(dxo) + abs(dyo)) * 2 * K + 2 * (dyo + r) + (dxo > 0));
+            const uint32_t code = umad(static_cast<uint32_t>(abs(dyo)), 2u * K, cbase + 2u * i);
             const unsigned long long key = (static_cast<unsigned long long>(acc[i]) << rb) | code;
             best = key < best ? key : best;
         }
     }
-    // segmented min over the contiguous lanes of each CU
+    // segmented min over the lanes of this CU (contiguous: first .. last)
+    const long cu_first = static_cast<long>(u) * per_task - static_cast<long>(lt) * 32;
+    const int first = static_cast<int>(max(cu_first, 0L));
+    const int last = static_cast<int>(min(cu_first + per_task - 1, ntask - 1 - static_cast<long>(lt) * 32));
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned long long v = __shfl_down_sync(0xffffffffu, best, o);
-        if (lane + o < 32 && task_of(lane + o) / per_task == u) best = v < best ? v : best;
+        if (lane + o <= last) best = v < best ? v : best;
     }
-    const bool head = lane == 0 || task_of(lane - 1) / per_task != u;
-    if (head && best != ~0ull) {
+    if (lane == first && best != ~0ull) {
         const uint32_t sad = static_cast<uint32_t>(best >> rb);
         const int code = static_cast<int>(best & ((1ull << rb) - 1));
         const int l1 = code / (2 * K), rr = code - l1 * 2 * K;
@@ -461,7 +491,7 @@ __device__ __forceinline__ void search_tile(const DependentBatch &b, int c, int 
         const int dxv = (rr & 1) ? adx : -adx;
         const uint32_t tb = static_cast<uint32_t>(l1 * K * K + (dyv + r) * K + (dxv + r));
         unsigned long long *keys = reinterpret_cast<unsigned long long *>(a.block + rinf.off.keys);
-        atomicMin(keys + gslot, (static_cast<unsigned long long>(sad) << 32) | tb);
+        atomicMin(keys + (lo >> 8), (static_cast<unsigned long long>(sad) << 32) | tb);
     }
 }
 
@@ -568,6 +598,9 @@ __global__ void __launch_bounds__(kDecideThreads) k_dep_decide(const __grid_cons
         }
     }
     __syncthreads();
+    // keys back to ~0 for the next search of this rung
+    for (int i = tid; i < C::NKEY; i += kDecideThreads)
+        const_cast<unsigned long long *>(keys)[i] = ~0ull;
     dev::DecideIO io{a.cur, a.ref, a.pitch_bytes, &rinf.g, a.qp, b.satd_mode, c_lambda_q16,
                      decisions_at(a.block, rinf.off)};
     dev::ctu_decide<T, CTU>(st, io, x0, y0);
@@ -624,9 +657,10 @@ template <typename T> cudaError_t search_bd(const DependentBatch &b, cudaStream_
 cudaError_t launch_dependent_rules(int ctu, const DependentBatch &b, cudaStream_t s)
 {
     if (b.n < 1 || b.n > kMaxDepItems || b.total_ctas <= 0) return cudaErrorInvalidValue;
-    if (ctu == 64) k_dep_rules<64><<<b.total_ctas, kRulesThreads, 0, s>>>(b);
-    else if (ctu == 32) k_dep_rules<32><<<b.total_ctas, kRulesThreads, 0, s>>>(b);
-    else k_dep_rules<16><<<b.total_ctas, kRulesThreads, 0, s>>>(b);
+    const int grid = (b.total_ctas + kRulesCtus - 1) / kRulesCtus;
+    if (ctu == 64) k_dep_rules<64><<<grid, 32 * kRulesCtus, 0, s>>>(b);
+    else if (ctu == 32) k_dep_rules<32><<<grid, 32 * kRulesCtus, 0, s>>>(b);
+    else k_dep_rules<16><<<grid, 32 * kRulesCtus, 0, s>>>(b);
     return cudaGetLastError();
 }
 

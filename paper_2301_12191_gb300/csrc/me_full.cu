@@ -64,7 +64,7 @@ template <typename T, int CTU, int RP, int BAND> struct Shape {
     static constexpr int DMAX = CTU == 64 ? 3 : (CTU == 32 ? 2 : 1);
     static constexpr int NKEY = keys_per_ctu(DMAX);
     static constexpr int NB8 = (CTU / 8) * (CTU / 8);
-    static constexpr int MAX_ROWS = CTU + 2 * TY - 1;
+    static constexpr int MAX_ROWS = CTU + 4 * TY - 1;  // a CTA's warp tiles span at most 4 bands
     static constexpr int CPR = P4 / 4;            // 16-byte chunks of expanded words per row
     // phase 2 of the in-place expansion covers at most box_h * ES / 4 + 2 rows
     static constexpr int MAXC = (((MAX_ROWS * ES + 3) / 4 + 2) * CPR + NT - 1) / NT;
@@ -101,29 +101,41 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
     return (static_cast<unsigned long long>(mh) << 32) | ml;
 }
 
-// Min over the lane's candidates of a 32-bit key SAD * 2^16 + code (mul[i]
-// is 2^16 for a real candidate, 0 for a padding row whose code is ~0).
+// Min over the lane's candidates of the 32-bit key SAD * 2^16 + code (m16 =
+// 2^16 as an operand the compiler cannot fold, so the products stay on the
+// multiply-add pipe).  Candidate rows past +R (only when 2R + 1 < TY, i.e.
+// !all_valid) never win.  Tree order: the mins do not form one long chain.
 template <int TY>
-__device__ __forceinline__ uint32_t lane_key32(const uint32_t (&s)[TY], const uint32_t (&mul)[TY],
-                                               const uint32_t (&code)[TY])
+__device__ __forceinline__ uint32_t lane_key32(const uint32_t (&s)[TY], const uint32_t (&code)[TY], uint32_t m16,
+                                               bool all_valid, int dy0, int R)
 {
-    uint32_t k = umad(s[0], mul[0], code[0]);
+    uint32_t k[TY];
 #pragma unroll
-    for (int i = 1; i < TY; ++i) k = min(k, umad(s[i], mul[i], code[i]));
-    return k;
+    for (int i = 0; i < TY; ++i) k[i] = umad(s[i], m16, code[i]);
+    if (!all_valid) {
+#pragma unroll
+        for (int i = 0; i < TY; ++i)
+            if (dy0 + i > R) k[i] = 0xffffffffu;
+    }
+#pragma unroll
+    for (int w = 1; w < TY; w *= 2)
+#pragma unroll
+        for (int i = 0; i + w < TY; i += 2 * w) k[i] = min(k[i], k[i + w]);
+    return k[0];
 }
 
 template <int TY>
-__device__ __forceinline__ unsigned long long lane_key64(const uint32_t (&s)[TY], const uint32_t (&mul)[TY],
-                                                         const uint32_t (&code)[TY])
+__device__ __forceinline__ unsigned long long lane_key64(const uint32_t (&s)[TY], const uint32_t (&code)[TY],
+                                                         uint32_t m16, bool all_valid, int dy0, int R)
 {
-    unsigned long long k = ~0ull;
+    unsigned long long k[TY];
 #pragma unroll
-    for (int i = 0; i < TY; ++i) {
-        const unsigned long long v = mul[i] ? umad_wide(s[i], 65536u, code[i]) : ~0ull;
-        k = v < k ? v : k;
-    }
-    return k;
+    for (int i = 0; i < TY; ++i) k[i] = (all_valid || dy0 + i <= R) ? umad_wide(s[i], m16, code[i]) : ~0ull;
+#pragma unroll
+    for (int w = 1; w < TY; w *= 2)
+#pragma unroll
+        for (int i = 0; i + w < TY; i += 2 * w) k[i] = k[i + w] < k[i] ? k[i + w] : k[i];
+    return k[0];
 }
 
 // Staged words behind expanded chunk m (positions 4m .. 4m+3) of a window
@@ -170,6 +182,54 @@ __device__ __forceinline__ void emit_chunk(const uint32_t (&w)[ES == 1 ? 2 : 3],
     *reinterpret_cast<uint4 *>(dst) = v;
 }
 
+__constant__ int c_lambda_q16[52] = {
+#include "lambda_table.inc"
+};
+
+static_assert(sizeof(FullSearchBatch) <= 32764, "full-search batch exceeds the kernel parameter space");
+
+// The decisions of one CTU after its search (fuse_decide): decode the keys
+// (and reset them to ~0 for the next search), then SATD, cost, split and
+// leaf maps.  `st` lies in the CTA's shared memory.
+template <typename T, int CTU>
+__device__ __forceinline__ void decide_ctu(const FullSearchBatch &b, const FullSearchItem &a, int ctu_idx, int x0,
+                                           int y0, dev::CtuState<CTU> &st)
+{
+    using C = dev::Ctu<CTU>;
+    const RungInfo &ri = b.rung[a.rung];
+    const RungGeom &g = ri.g;
+    const int K = 2 * b.R + 1;
+    unsigned long long *keys = a.keys + static_cast<long>(ctu_idx) * C::NKEY;
+    for (int i = threadIdx.x; i < C::NKEY; i += blockDim.x) {
+        int d = 0;
+        while (d < C::DMAX && i >= key_offset(d + 1)) ++d;
+        const int li = i - key_offset(d), n = 1 << d, S = CTU >> d;
+        const int fx = x0 / S + li % n, fy = y0 / S + li / n;
+        uint8_t flags = 0;
+        if (fx * S < g.W8 && fy * S < g.H8) {
+            const bool inside = fx * S + S <= g.W8 && fy * S + S <= g.H8;
+            flags = dev::kPresent | kRuleReachable | (inside ? kRuleEvaluated : 0) | (d < C::DMAX ? kRuleCanSplit : 0);
+        }
+        st.flags[i] = flags;
+        st.satd[i] = 0;
+        const unsigned long long key = __ldcg(keys + i);
+        __stcg(keys + i, ~0ull);
+        if (flags & kRuleEvaluated) {
+            const int rem = static_cast<int>(static_cast<uint32_t>(key & 0xffffffffu) % static_cast<uint32_t>(K * K));
+            st.mvx[i] = static_cast<int16_t>(rem % K - b.R);
+            st.mvy[i] = static_cast<int16_t>(rem / K - b.R);
+            st.sad[i] = static_cast<int32_t>(key >> 32);
+        } else {
+            st.mvx[i] = INT16_MIN;
+            st.mvy[i] = INT16_MIN;
+            st.sad[i] = INT32_MAX;
+        }
+    }
+    __syncthreads();
+    dev::DecideIO io{a.cur, a.ref, a.pitch_bytes, &g, a.qp, b.satd_mode, c_lambda_q16, decisions_at(a.block, ri.off)};
+    dev::ctu_decide<T, CTU>(st, io, x0, y0);
+}
+
 template <typename T, int CTU, int RP, int BAND>
 __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(const __grid_constant__ FullSearchBatch b)
 {
@@ -186,6 +246,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t s_k8[S::NB8];                          // 8x8 keys
     __shared__ unsigned long long s_kup[keys_per_ctu(S::DMAX - 1)];  // larger CUs
+    // quadrant sums per candidate and lane for the CTU level: in E when the
+    // CTA has one warp tile (E is then free), else after the current CTU
+    uint32_t *const s_xch = b.group > 1 ? a8 + (ES == 2 ? S::NB8 : 0) : E;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int R = b.R, K = 2 * R + 1;
@@ -193,7 +256,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
     while (ii + 1 < b.n && static_cast<int>(blockIdx.x) >= b.item[ii + 1].cta_begin) ++ii;
     const FullSearchItem &a = b.item[ii];
     const int local = blockIdx.x - a.cta_begin;
-    const int ctu_idx = local / b.warp_tiles, wt = local - ctu_idx * b.warp_tiles;
+    // this CTA: warp tiles wt0 .. wt1-1 of one CTU, over one staged window
+    const int ngroups = (b.warp_tiles + b.group - 1) / b.group;
+    const int ctu_idx = local / ngroups, grp = local - ctu_idx * ngroups;
+    const int wt0 = grp * b.group, wt1 = min(wt0 + b.group, b.warp_tiles);
     const int W8 = (a.W + 7) & ~7, H8 = (a.H + 7) & ~7;
     const int ctu_cols = (W8 + CTU - 1) / CTU;
     const int x0 = (ctu_idx % ctu_cols) * CTU, y0 = (ctu_idx / ctu_cols) * CTU;
@@ -202,7 +268,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
         if (K >= TY) v = min(v, R - TY + 1);
         return v;
     };
-    const int tf = wt * 32, tl = min(wt * 32 + 31, b.ntasks - 1);
+    const int tf = wt0 * 32, tl = min(wt1 * 32 - 1, b.ntasks - 1);
     const int rlo = band_dy0(tf) + R;                   // first window row, relative to y0 - R
     const int rows = band_dy0(tl) + R + TY - 1 + CTU - rlo;
     const int gy0 = y0 - R + rlo;                       // frame row of window row 0
@@ -219,19 +285,6 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
         mbar_arrive_expect_tx(&bar, static_cast<uint32_t>((b.box_h * P4 + CTU * CTU) * ES));
         tma_load_2d(stage, &b.map[ii], &bar, x0 - b.Rp, sy0);
         tma_load_2d(curs, &b.cur_map[ii], &bar, x0, y0);
-    }
-
-    // lane task and candidate codes; a candidate row past +R (only when
-    // 2R + 1 < TY) never wins: mul 0, code ~0
-    const int t = min(wt * 32 + lane, b.ntasks - 1);
-    const int dx = t % K - R, dy0 = band_dy0(t);
-    uint32_t mul[TY], code[TY];
-#pragma unroll
-    for (int i = 0; i < TY; ++i) {
-        const int dy = dy0 + i;
-        const bool ok = dy <= R;
-        mul[i] = ok ? 65536u : 0u;
-        code[i] = ok ? static_cast<uint32_t>((abs(dx) + abs(dy)) * 2 * K + 2 * (dy + R) + (dx > 0)) : 0xffffffffu;
     }
 
     const bool ok = mbar_wait_bounded(&bar, 0);
@@ -258,12 +311,21 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
         const int gx0 = x0 - b.Rp;
         auto srow_of = [&](int r) { return stage + (min(max(gy0 + r, 0), a.H - 1) - sy0) * P4; };
         const int r1 = min(b.phase1_rows, rows);
-        const int n1 = r1 * S::CPR;
-        for (int i = tid; i < n1; i += NT) {
-            const int r = i / S::CPR, m = i - r * S::CPR;
-            uint32_t w[S::NW];
-            fetch_chunk<T, P4>(srow_of(r), m, gx0, a.W, w);
-            emit_chunk<ES>(w, E + r * P4 + 4 * m);
+        // phase 1: one warp per row (row clamp once), one chunk per lane
+        constexpr int LPR = (S::CPR + 31) / 32;
+#pragma unroll 1
+        for (int r = warp; r < r1; r += NT / 32) {
+            const T *srow = srow_of(r);
+            uint32_t *erow = E + r * P4;
+#pragma unroll
+            for (int k = 0; k < LPR; ++k) {
+                const int m = lane + 32 * k;
+                if (S::CPR % 32 == 0 || m < S::CPR) {
+                    uint32_t w[S::NW];
+                    fetch_chunk<T, P4>(srow, m, gx0, a.W, w);
+                    emit_chunk<ES>(w, erow + 4 * m);
+                }
+            }
         }
         const int n2 = (rows - r1) * S::CPR;
         uint32_t hold[S::MAXC][S::NW];
@@ -294,140 +356,152 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
     }
     __syncthreads();
 
-    // ---- search: warp = quadrant, its 8x8 blocks in Z order ----
+    // ---- search: per warp tile, warp = quadrant, its 8x8 blocks in Z order ----
     const int qx = (warp & 1) * S::Q, qy = (warp >> 1) * S::Q;
-    const uint32_t one = b.one;
-    const uint32_t *lp = E + (dy0 + R - rlo + qy) * P4 + (dx + b.Rp + qx);
-    uint32_t s16[TY], s32[TY];
-#pragma unroll
-    for (int i = 0; i < TY; ++i) {
-        s16[i] = 0;
-        s32[i] = 0;
-    }
+    const uint32_t one = b.one, m16 = b.one << 16;
+    const bool all_valid = K >= TY;  // else rows past +R exist and never win
 #pragma unroll 1
-    for (int bq = 0; bq < S::NBQ; ++bq) {
-        const int zx = (bq & 1) | ((bq >> 1) & 2), zy = ((bq >> 1) & 1) | ((bq >> 2) & 2);
-        const int bx = zx * 8, by = zy * 8;
-        const bool present = x0 + qx + bx < W8 && y0 + qy + by < H8;
-        uint32_t acc[TY];
-#pragma unroll
-        for (int i = 0; i < TY; ++i) acc[i] = 0;
-        if (present) {
-            const uint32_t *bp = lp + by * P4 + bx;
-            const T *cp = curs + (qy + by) * CTU + qx + bx;
-            if constexpr (ES == 1) {
-                uint2 c[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) c[j] = *reinterpret_cast<const uint2 *>(cp + j * CTU);
-#pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    const uint32_t w0 = bp[r * P4], w1 = bp[r * P4 + 4];
-                    // all candidates on word 0, then on word 1: no back-to-back dependence
-#pragma unroll
-                    for (int i = 0; i < TY; ++i) {
-                        const int j = r - i;
-                        if (j >= 0 && j < 8) acc[i] = sad_acc<4>(c[j].x, w0, acc[i]);
-                    }
-#pragma unroll
-                    for (int i = 0; i < TY; ++i) {
-                        const int j = r - i;
-                        if (j >= 0 && j < 8) acc[i] = sad_acc<4>(c[j].y, w1, acc[i]);
-                    }
-                }
-            } else {
-                uint4 c[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) c[j] = *reinterpret_cast<const uint4 *>(cp + j * CTU);
-                const uint32_t sa = a8[((qy + by) / 8) * (CTU / 8) + (qx + bx) / 8];
-                // candidate i is complete after window row i + 7: there
-                // SAD = sum(a) + sum(b) - 2 sum(min), per packed half
-                uint32_t rs[NR];
-                uint32_t sb = 0;
-#pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    const uint32_t w0 = bp[r * P4], w1 = bp[r * P4 + 2], w2 = bp[r * P4 + 4], w3 = bp[r * P4 + 6];
-                    rs[r] = (w0 + w1) + (w2 + w3);
-#pragma unroll
-                    for (int i = 0; i < TY; ++i) {
-                        const int j = r - i;
-                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].x, w0), one, acc[i]);
-                    }
-#pragma unroll
-                    for (int i = 0; i < TY; ++i) {
-                        const int j = r - i;
-                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].y, w1), one, acc[i]);
-                    }
-#pragma unroll
-                    for (int i = 0; i < TY; ++i) {
-                        const int j = r - i;
-                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].z, w2), one, acc[i]);
-                    }
-#pragma unroll
-                    for (int i = 0; i < TY; ++i) {
-                        const int j = r - i;
-                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].w, w3), one, acc[i]);
-                    }
-                    if (r < 8) sb += rs[r];
-                    else sb = sb + rs[r] - rs[r - 8];
-                    if (r >= 7) {
-                        const int i = r - 7;
-                        const uint32_t d = umad(acc[i], 0xfffffffeu, sa + sb);
-                        acc[i] = (d & 0xffffu) + (d >> 16);
-                    }
-                }
-            }
-            // 8x8 key
-            const uint32_t key = __reduce_min_sync(0xffffffffu, lane_key32<TY>(acc, mul, code));
-            if (lane == 0) atomicMin(&s_k8[((qy + by) / 8) * (CTU / 8) + (qx + bx) / 8], key);
+    for (int wt = wt0; wt < wt1; ++wt) {
+        const int t = min(wt * 32 + lane, b.ntasks - 1);
+        const int dx = t % K - R, dy0 = band_dy0(t);
+        uint32_t code[TY];  // (|dx|+|dy|) 2K + 2 (dy + R) + [dx > 0]
+    #pragma unroll
+        for (int i = 0; i < TY; ++i) {
+            const int dy = dy0 + i;
+            code[i] = static_cast<uint32_t>((abs(dx) + abs(dy)) * 2 * K + 2 * (dy + R) + (dx > 0));
         }
-#pragma unroll
-        for (int i = 0; i < TY; ++i) s16[i] = umad(acc[i], one, s16[i]);
+        const uint32_t *lp = E + (dy0 + R - rlo + qy) * P4 + (dx + b.Rp + qx);
+        uint32_t s16[TY], s32[TY];
+    #pragma unroll
+        for (int i = 0; i < TY; ++i) {
+            s16[i] = 0;
+            s32[i] = 0;
+        }
+    #pragma unroll 1
+        for (int bq = 0; bq < S::NBQ; ++bq) {
+            const int zx = (bq & 1) | ((bq >> 1) & 2), zy = ((bq >> 1) & 1) | ((bq >> 2) & 2);
+            const int bx = zx * 8, by = zy * 8;
+            const bool present = x0 + qx + bx < W8 && y0 + qy + by < H8;
+            uint32_t acc[TY];
+    #pragma unroll
+            for (int i = 0; i < TY; ++i) acc[i] = 0;
+            if (present) {
+                const uint32_t *bp = lp + by * P4 + bx;
+                const T *cp = curs + (qy + by) * CTU + qx + bx;
+                if constexpr (ES == 1) {
+                    uint2 c[8];
+    #pragma unroll
+                    for (int j = 0; j < 8; ++j) c[j] = *reinterpret_cast<const uint2 *>(cp + j * CTU);
+    #pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const uint32_t w0 = bp[r * P4], w1 = bp[r * P4 + 4];
+                        // all candidates on word 0, then on word 1: no back-to-back dependence
+    #pragma unroll
+                        for (int i = 0; i < TY; ++i) {
+                            const int j = r - i;
+                            if (j >= 0 && j < 8) acc[i] = sad_acc<4>(c[j].x, w0, acc[i]);
+                        }
+    #pragma unroll
+                        for (int i = 0; i < TY; ++i) {
+                            const int j = r - i;
+                            if (j >= 0 && j < 8) acc[i] = sad_acc<4>(c[j].y, w1, acc[i]);
+                        }
+                    }
+                } else {
+                    uint4 c[8];
+    #pragma unroll
+                    for (int j = 0; j < 8; ++j) c[j] = *reinterpret_cast<const uint4 *>(cp + j * CTU);
+                    const uint32_t sa = a8[((qy + by) / 8) * (CTU / 8) + (qx + bx) / 8];
+                    // candidate i is complete after window row i + 7: there
+                    // SAD = sum(a) + sum(b) - 2 sum(min), per packed half
+                    uint32_t rs[NR];
+                    uint32_t sb = 0;
+    #pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const uint32_t w0 = bp[r * P4], w1 = bp[r * P4 + 2], w2 = bp[r * P4 + 4], w3 = bp[r * P4 + 6];
+                        rs[r] = (w0 + w1) + (w2 + w3);
+    #pragma unroll
+                        for (int i = 0; i < TY; ++i) {
+                            const int j = r - i;
+                            if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].x, w0), one, acc[i]);
+                        }
+    #pragma unroll
+                        for (int i = 0; i < TY; ++i) {
+                            const int j = r - i;
+                            if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].y, w1), one, acc[i]);
+                        }
+    #pragma unroll
+                        for (int i = 0; i < TY; ++i) {
+                            const int j = r - i;
+                            if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].z, w2), one, acc[i]);
+                        }
+    #pragma unroll
+                        for (int i = 0; i < TY; ++i) {
+                            const int j = r - i;
+                            if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].w, w3), one, acc[i]);
+                        }
+                        if (r < 8) sb += rs[r];
+                        else sb = sb + rs[r] - rs[r - 8];
+                        if (r >= 7) {
+                            const int i = r - 7;
+                            const uint32_t d = umad(acc[i], 0xfffffffeu, sa + sb);
+                            acc[i] = (d & 0xffffu) + (d >> 16);
+                        }
+                    }
+                }
+                // 8x8 key
+                const uint32_t key = __reduce_min_sync(0xffffffffu, lane_key32<TY>(acc, code, m16, all_valid, dy0, R));
+                if (lane == 0) atomicMin(&s_k8[((qy + by) / 8) * (CTU / 8) + (qx + bx) / 8], key);
+            }
+    #pragma unroll
+            for (int i = 0; i < TY; ++i) s16[i] = umad(acc[i], one, s16[i]);
 
-        if constexpr (S::Q >= 16) {
-            if ((bq & 3) == 3) {  // 16x16 CU complete
-                const int cx = (qx + bx) / 16, cy = (qy + by) / 16;
-                if (x0 + cx * 16 < W8 && y0 + cy * 16 < H8) {
-                    unsigned long long key;
-                    if constexpr (S::K16_32) key = __reduce_min_sync(0xffffffffu, lane_key32<TY>(s16, mul, code));
-                    else key = warp_min_u64(lane_key64<TY>(s16, mul, code));
-                    if (lane == 0) atomicMin(&s_kup[key_offset(S::DMAX - 1) + cy * (CTU / 16) + cx], key);
+            if constexpr (S::Q >= 16) {
+                if ((bq & 3) == 3) {  // 16x16 CU complete
+                    const int cx = (qx + bx) / 16, cy = (qy + by) / 16;
+                    if (x0 + cx * 16 < W8 && y0 + cy * 16 < H8) {
+                        unsigned long long key;
+                        if constexpr (S::K16_32) key = __reduce_min_sync(0xffffffffu, lane_key32<TY>(s16, code, m16, all_valid, dy0, R));
+                        else key = warp_min_u64(lane_key64<TY>(s16, code, m16, all_valid, dy0, R));
+                        if (lane == 0) atomicMin(&s_kup[key_offset(S::DMAX - 1) + cy * (CTU / 16) + cx], key);
+                    }
+    #pragma unroll
+                    for (int i = 0; i < TY; ++i) {
+                        s32[i] = umad(s16[i], one, s32[i]);
+                        s16[i] = 0;
+                    }
                 }
-#pragma unroll
-                for (int i = 0; i < TY; ++i) {
-                    s32[i] = umad(s16[i], one, s32[i]);
-                    s16[i] = 0;
+            }
+            if constexpr (S::Q >= 32) {
+                if ((bq & 15) == 15) {  // 32x32 CU complete
+                    const int cx = (qx + bx) / 32, cy = (qy + by) / 32;
+                    if (x0 + cx * 32 < W8 && y0 + cy * 32 < H8) {
+                        const unsigned long long key = warp_min_u64(lane_key64<TY>(s32, code, m16, all_valid, dy0, R));
+                        if (lane == 0) atomicMin(&s_kup[key_offset(S::DMAX - 2) + cy * (CTU / 32) + cx], key);
+                    }
                 }
             }
         }
-        if constexpr (S::Q >= 32) {
-            if ((bq & 15) == 15) {  // 32x32 CU complete
-                const int cx = (qx + bx) / 32, cy = (qy + by) / 32;
-                if (x0 + cx * 32 < W8 && y0 + cy * 32 < H8) {
-                    const unsigned long long key = warp_min_u64(lane_key64<TY>(s32, mul, code));
-                    if (lane == 0) atomicMin(&s_kup[key_offset(S::DMAX - 2) + cy * (CTU / 32) + cx], key);
-                }
-            }
-        }
-    }
 
-    // CTU level: the four quadrants' sums.
-    __syncthreads();  // every warp is done with E: reuse it
-    uint32_t *xch = E;  // [warp][i][lane]
-    {
-        const uint32_t(&top)[TY] = (S::Q >= 16) ? s32 : s16;
-#pragma unroll
-        for (int i = 0; i < TY; ++i) xch[(warp * TY + i) * 32 + lane] = top[i];
-    }
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t tot[TY];
-#pragma unroll
-        for (int i = 0; i < TY; ++i)
-            tot[i] = xch[i * 32 + lane] + xch[(TY + i) * 32 + lane] + xch[(2 * TY + i) * 32 + lane] +
-                     xch[(3 * TY + i) * 32 + lane];
-        const unsigned long long key = warp_min_u64(lane_key64<TY>(tot, mul, code));
-        if (lane == 0) atomicMin(&s_kup[0], key);
-    }
+        // CTU level: the four quadrants' sums (warp 0 has read the previous
+        // tile's exchange once every warp passes the first barrier)
+        __syncthreads();
+        {
+            const uint32_t(&top)[TY] = (S::Q >= 16) ? s32 : s16;
+    #pragma unroll
+            for (int i = 0; i < TY; ++i) s_xch[(warp * TY + i) * 32 + lane] = top[i];
+        }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t tot[TY];
+    #pragma unroll
+            for (int i = 0; i < TY; ++i)
+                tot[i] = s_xch[i * 32 + lane] + s_xch[(TY + i) * 32 + lane] + s_xch[(2 * TY + i) * 32 + lane] +
+                         s_xch[(3 * TY + i) * 32 + lane];
+            const unsigned long long key = warp_min_u64(lane_key64<TY>(tot, code, m16, all_valid, dy0, R));
+            if (lane == 0) atomicMin(&s_kup[0], key);
+        }
+    }  // warp tiles
     __syncthreads();
 
     // Re-encode (SAD << 16 | code) as (SAD << 32 | tie-break) and merge.
@@ -444,6 +518,19 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
         const int dxv = (rem & 1) ? adx : -adx;
         const uint32_t tb = static_cast<uint32_t>(l1 * K * K + (dyv + R) * K + (dxv + R));
         atomicMin(out + i, (static_cast<unsigned long long>(sad) << 32) | tb);
+    }
+    if (b.fuse_decide) {
+        // the last CTA of this CTU to finish takes its decisions
+        __shared__ int s_last;
+        __threadfence();  // this CTA's key updates before its count
+        __syncthreads();
+        unsigned int *done = a.done + ctu_idx;
+        if (tid == 0) s_last = atomicAdd(done, 1u) == static_cast<unsigned int>(ngroups - 1);
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();  // every other CTA's key updates before the reads
+        if (tid == 0) *done = 0;  // zero for the next search of this block
+        decide_ctu<T, CTU>(b, a, ctu_idx, x0, y0, *reinterpret_cast<dev::CtuState<CTU> *>(sm));
     }
 }
 
@@ -527,7 +614,7 @@ struct LaunchOp {
 
 }  // namespace
 
-FullSearchPlan full_search_plan(int bit_depth, int ctu, int R, int band)
+FullSearchPlan full_search_plan(int bit_depth, int ctu, int R, int band, int group)
 {
     if (ctu != 64 || band != 9) band = kFsBand;  // the compiled bands
     FullSearchPlan p{};
@@ -544,11 +631,20 @@ FullSearchPlan full_search_plan(int bit_depth, int ctu, int R, int band)
         if (K >= band) v = std::min(v, R - band + 1);
         return v;
     };
-    int rows = 0;
-    for (int w = 0; w < p.warp_tiles; ++w) {
-        const int tf = w * 32, tl = std::min(w * 32 + 31, p.ntasks - 1);
-        rows = std::max(rows, dy0(tl) - dy0(tf) + band - 1 + ctu);
-    }
+    // window rows of a CTA holding `g` consecutive warp tiles
+    auto rows_for = [&](int g) {
+        int rows = 0;
+        for (int w0 = 0; w0 < p.warp_tiles; w0 += g) {
+            const int tf = w0 * 32, tl = std::min((w0 + g) * 32 - 1, p.ntasks - 1);
+            rows = std::max(rows, dy0(tl) - dy0(tf) + band - 1 + ctu);
+        }
+        return rows;
+    };
+    group = std::max(1, std::min(group, p.warp_tiles));
+    while (group > 1 && rows_for(group) > ctu + 4 * band - 1) --group;  // the kernels' window bound
+    p.group = group;
+    p.ctas_per_ctu = (p.warp_tiles + group - 1) / group;
+    const int rows = rows_for(group);
     p.P4 = ctu + 2 * RPc;
     p.box_w = p.P4;
     p.box_h = rows;
@@ -558,7 +654,8 @@ FullSearchPlan full_search_plan(int bit_depth, int ctu, int R, int band)
     p.phase1_rows = p.stage_off / (4 * p.P4);
     const int cur_bytes = ctu * ctu * es;
     const int a8_bytes = es == 2 ? (ctu / 8) * (ctu / 8) * 4 : 0;
-    p.buf_bytes = (p.e_bytes + cur_bytes + a8_bytes + 127) / 128 * 128;
+    const int xch_bytes = group > 1 ? 4 * band * 32 * 4 : 0;  // else the exchange reuses the window
+    p.buf_bytes = (p.e_bytes + cur_bytes + a8_bytes + xch_bytes + 127) / 128 * 128;
     p.smem_bytes = p.buf_bytes + 128;  // + alignment slack
     return p;
 }
@@ -567,6 +664,7 @@ void fill_full_search_batch(FullSearchBatch &b, const FullSearchPlan &p, int R)
 {
     b.R = R;
     b.band = p.band;
+    b.group = p.group;
     b.Rp = p.Rp;
     b.ntasks = p.ntasks;
     b.warp_tiles = p.warp_tiles;
@@ -615,15 +713,17 @@ int encode_item_maps(FullSearchBatch &b, int k, const void *cur, const void *ref
 
 cudaError_t prepare_full_search(int bit_depth, int ctu, int R)
 {
-    // raises the shared-memory attributes outside any capture
-    full_search_ctas_per_sm(bit_depth, ctu, R, kFsBand);
-    if (ctu == 64) full_search_ctas_per_sm(bit_depth, ctu, R, 9);
+    // raises the shared-memory attributes (largest: the widest group) outside any capture
+    for (int g = 1; g <= kFsMaxGroup; ++g) {
+        full_search_ctas_per_sm(bit_depth, ctu, R, kFsBand, g);
+        if (ctu == 64) full_search_ctas_per_sm(bit_depth, ctu, R, 9, g);
+    }
     return cudaGetLastError();
 }
 
-int full_search_ctas_per_sm(int bit_depth, int ctu, int R, int band)
+int full_search_ctas_per_sm(int bit_depth, int ctu, int R, int band, int group)
 {
-    const FullSearchPlan p = full_search_plan(bit_depth, ctu, R, band);
+    const FullSearchPlan p = full_search_plan(bit_depth, ctu, R, band, group);
     OccupancyOp f{p.smem_bytes, 1};
     dispatch(bit_depth, ctu, p.Rp, p.band, f);
     return f.n;
@@ -632,7 +732,7 @@ int full_search_ctas_per_sm(int bit_depth, int ctu, int R, int band)
 cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchBatch &b, cudaStream_t s)
 {
     if (b.n < 1 || b.n > kMaxItems || b.total <= 0) return cudaErrorInvalidValue;
-    const FullSearchPlan p = full_search_plan(bit_depth, ctu, b.R, b.band);
+    const FullSearchPlan p = full_search_plan(bit_depth, ctu, b.R, b.band, b.group);
     LaunchOp f{b, p.smem_bytes, s};
     return dispatch(bit_depth, ctu, p.Rp, p.band, f);
 }

@@ -127,7 +127,7 @@ extern "C" ladder_status analyze_reference_noalloc(const void *cur, const void *
     fb.n = 1;
     fill_full_search_batch(fb, plan, search_range);
     fb.status = d_status;
-    fb.total = nctus * plan.warp_tiles;
+    fb.total = nctus * plan.ctas_per_ctu;
     fb.item[0] = FullSearchItem{width, height, d_keys, 0};
     if (encode_item_maps(fb, 0, cur, ref, width, height, pitch_bytes, bit_depth, ctu_size, plan) != 0)
         return LADDER_E_CUDA;

@@ -102,7 +102,7 @@ SIGNATURES = [
 ]
 
 KERNEL_KINDS = ("full_search", "decide", "dependent", "fill_keys", "dep_rules", "dep_decide")
-TUNE_KNOBS = {"fs_band": 0, "dep_band": 1, "dep_range": 2, "dep_ctas_per_sm": 3}
+TUNE_KNOBS = {"fs_band": 0, "dep_band": 1, "dep_range": 2, "dep_ctas_per_sm": 3, "fs_group": 4, "fs_fuse": 5}
 
 _lib = None
 

@@ -19,6 +19,11 @@ SETTINGS = [
     {"dep_band": 17},
     {"dep_band": 9},
     {"dep_ctas_per_sm": 1},
+    {"fs_group": 2},
+    {"fs_group": 4},
+    {"fs_group": 3, "fs_band": 9},
+    {"fs_fuse": 0},
+    {"fs_fuse": 0, "fs_group": 2},
     {"fs_band": 9, "dep_range": 32, "dep_band": 17, "dep_ctas_per_sm": 2},
 ]
 
@@ -59,7 +64,7 @@ def test_knobs_do_not_change_decisions(src, rungs, bd, R, r):
 
 def test_bad_knobs_are_refused():
     with L.Ladder([(64, 64)], 0, ctu_size=32, max_frames=1) as lad:
-        for knobs in ({"fs_band": 9}, {"fs_band": 11}, {"dep_range": 8}, {"dep_band": 5}, {"dep_ctas_per_sm": 9}):
+        for knobs in ({"fs_band": 9}, {"fs_band": 11}, {"dep_range": 8}, {"dep_band": 5}, {"dep_ctas_per_sm": 9}, {"fs_group": 5}):
             with pytest.raises(L.LadderError):
                 lad.set_tuning(**knobs)
         assert lad.tuning() == tune.DEFAULTS
