@@ -113,47 +113,49 @@ __device__ __forceinline__ int ld_sample(const char *base, long pitch, int x, in
     return static_cast<int>(__ldg(reinterpret_cast<const T *>(base + static_cast<long>(y) * pitch) + x));
 }
 
-// SATD of the 8x8 block at (px, py) against the reference displaced by
-// (mvx, mvy), computed by the 8 lanes of an aligned lane group (lane & 7 =
-// row); every lane of the group returns the block's SATD.  Samples are read
-// with clamping (current: replicate to the 8-aligned size; reference: frame
-// edge).  `gmask` is the group's lane mask.
-//   mode 0: 8x8 Hadamard T = H8 D H8^T, (sum |T|) >> 2
-//   mode 1: two 4x4 Hadamards per 8x4 half, (sum of both) >> 1, halves added
+// One row of an 8x8 block for the SATD: the current samples and the
+// displaced reference samples, packed SPW per word.
 template <typename T>
-__device__ int satd8_group(const void *cur, const void *ref, long pitch, int W, int H, int px, int py, int mvx,
-                           int mvy, int mode, unsigned gmask)
+struct SatdRow {
+    static constexpr int WPR = 8 / Traits<T>::SPW;
+    uint32_t cw[WPR], rw[WPR];
+};
+
+// Loads the row (lane & 7) of the 8x8 block at (px, py) and of the
+// reference displaced by (mvx, mvy).  Samples are read with clamping
+// (current: replicate to the 8-aligned size; reference: frame edge).
+template <typename T>
+__device__ __forceinline__ void satd8_load(const void *cur, const void *ref, long pitch, int W, int H, int px,
+                                           int py, int mvx, int mvy, SatdRow<T> &w)
 {
     const char *cb = static_cast<const char *>(cur);
     const char *rb = static_cast<const char *>(ref);
-    constexpr int SPW = Traits<T>::SPW, BITS = 32 / SPW, WPR = 8 / SPW;
+    constexpr int SPW = Traits<T>::SPW, BITS = 32 / SPW, WPR = SatdRow<T>::WPR;
     const int y = threadIdx.x & 7;
     const int cy = min(py + y, H - 1);
     const int ry = min(max(py + y + mvy, 0), H - 1);
     const int rx0 = px + mvx;
-    int v[8];
-    uint32_t cw[WPR], rw[WPR];
     if (px + 8 <= W) {  // current row: one aligned vector load
         const char *row = cb + static_cast<long>(cy) * pitch + static_cast<long>(px) * sizeof(T);
         if constexpr (WPR == 2) {
             const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row));
-            cw[0] = q.x;
-            cw[1] = q.y;
+            w.cw[0] = q.x;
+            w.cw[1] = q.y;
         } else {
             const uint4 q = __ldg(reinterpret_cast<const uint4 *>(row));
-            cw[0] = q.x;
-            cw[1] = q.y;
-            cw[2] = q.z;
-            cw[3] = q.w;
+            w.cw[0] = q.x;
+            w.cw[1] = q.y;
+            w.cw[2] = q.z;
+            w.cw[3] = q.w;
         }
     } else {
 #pragma unroll
         for (int m = 0; m < WPR; ++m) {
-            uint32_t w = 0;
+            uint32_t v = 0;
 #pragma unroll
             for (int e = 0; e < SPW; ++e)
-                w |= static_cast<uint32_t>(ld_sample<T>(cb, pitch, min(px + m * SPW + e, W - 1), cy)) << (e * BITS);
-            cw[m] = w;
+                v |= static_cast<uint32_t>(ld_sample<T>(cb, pitch, min(px + m * SPW + e, W - 1), cy)) << (e * BITS);
+            w.cw[m] = v;
         }
     }
     if (rx0 >= 0 && (rx0 / SPW + WPR + 1) * SPW <= W) {  // reference row: aligned words + one funnel shift
@@ -163,23 +165,36 @@ __device__ int satd8_group(const void *cur, const void *ref, long pitch, int W, 
 #pragma unroll
         for (int m = 0; m <= WPR; ++m) raw[m] = __ldg(rp + m);
 #pragma unroll
-        for (int m = 0; m < WPR; ++m) rw[m] = __funnelshift_r(raw[m], raw[m + 1], sh);
+        for (int m = 0; m < WPR; ++m) w.rw[m] = __funnelshift_r(raw[m], raw[m + 1], sh);
     } else {
 #pragma unroll
         for (int m = 0; m < WPR; ++m) {
-            uint32_t w = 0;
+            uint32_t v = 0;
 #pragma unroll
             for (int e = 0; e < SPW; ++e)
-                w |= static_cast<uint32_t>(ld_sample<T>(rb, pitch, min(max(rx0 + m * SPW + e, 0), W - 1), ry))
+                v |= static_cast<uint32_t>(ld_sample<T>(rb, pitch, min(max(rx0 + m * SPW + e, 0), W - 1), ry))
                      << (e * BITS);
-            rw[m] = w;
+            w.rw[m] = v;
         }
     }
+}
+
+// SATD of the 8x8 residual whose rows the 8 lanes of an aligned lane group
+// hold (lane & 7 = row); every lane of the group returns the block's SATD.
+// `gmask` is the group's lane mask.
+//   mode 0: 8x8 Hadamard T = H8 D H8^T, (sum |T|) >> 2
+//   mode 1: two 4x4 Hadamards per 8x4 half, (sum of both) >> 1, halves added
+template <typename T>
+__device__ __forceinline__ int satd8_reduce(const SatdRow<T> &w, int mode, unsigned gmask)
+{
+    constexpr int SPW = Traits<T>::SPW, BITS = 32 / SPW;
+    const int y = threadIdx.x & 7;
+    int v[8];
 #pragma unroll
     for (int x = 0; x < 8; ++x) {
         const int m = x / SPW, sh = (x % SPW) * BITS;
         const int mask = (1 << BITS) - 1;
-        v[x] = static_cast<int>((cw[m] >> sh) & mask) - static_cast<int>((rw[m] >> sh) & mask);
+        v[x] = static_cast<int>((w.cw[m] >> sh) & mask) - static_cast<int>((w.rw[m] >> sh) & mask);
     }
     if (mode == 0) {
         fwht<8>(v);  // along the row
@@ -231,7 +246,7 @@ struct CtuState {
     int32_t satd[Ctu<CTU>::NKEY], sad[Ctu<CTU>::NKEY], best[Ctu<CTU>::NKEY];
     int16_t mvx[Ctu<CTU>::NKEY], mvy[Ctu<CTU>::NKEY];
     uint8_t flags[Ctu<CTU>::NKEY], split[Ctu<CTU>::NKEY];
-    uint16_t pairs[(Ctu<CTU>::DMAX + 1) * Ctu<CTU>::NB8];  // (depth, 8x8) pairs needing a SATD
+    uint16_t pairs[(Ctu<CTU>::DMAX + 1) * Ctu<CTU>::NB8];  // distinct (8x8 block, vector): block | depths << 8
     int npairs;
 };
 
@@ -248,54 +263,79 @@ struct DecideIO {
 __device__ __forceinline__ int key_index(int d, int li) { return key_offset(d) + li; }
 
 // The decision step for one CTU, given flags / vectors / SADs in `st`
-// (satd[] must be zero).  All threads of the CTA take part.
+// (satd[] must be zero).  All threads of the CTA take part; NP is the
+// number of SATD entries each 8-lane group has in flight.
 //   SATD   -- Sec. 5.4.1 SATD equation; Sec. 5.4.2 satd8 / satd_8x4 listings
 //   cost   -- J = SATD + ((lambdaQ16[qp] * bits + 2^15) >> 16), bits = se()
 //             lengths of the quarter-pel components (predictor (0,0))
 //   split  -- Sec. 2.1: split iff it may and (it is not a leaf candidate or
 //             the children's best sum is strictly lower), or it must
-template <typename T, int CTU>
+template <typename T, int CTU, int NP = 4>
 __device__ void ctu_decide(CtuState<CTU> &st, const DecideIO &io, int x0, int y0)
 {
     using C = Ctu<CTU>;
     const RungGeom &g = *io.g;
     const int tid = threadIdx.x, nthr = blockDim.x;
 
-    // SATD: list the (depth, 8x8 block) pairs of evaluated CUs, then one
-    // 8-lane group per pair, two pairs at a time so their loads overlap
+    // SATD.  Every evaluated CU covering an 8x8 block needs that block's
+    // SATD at the CU's vector; a CU and its sub-CUs often keep the same
+    // vector, so the list holds one entry per distinct (block, vector):
+    // block | (depths sharing the vector) << 8.  SATD sums are exact, so the
+    // order of the additions does not matter.
     if (tid == 0) st.npairs = 0;
     __syncthreads();
-    for (int t = tid; t < (C::DMAX + 1) * C::NB8; t += nthr) {
-        const int d = t / C::NB8, b = t % C::NB8;
-        const int S = CTU >> d;
-        const int i = key_index(d, (((b / C::N8) * 8) / S) * (1 << d) + ((b % C::N8) * 8) / S);
-        if (st.flags[i] & kRuleEvaluated) st.pairs[atomicAdd(&st.npairs, 1)] = static_cast<uint16_t>(t);
+    for (int b = tid; b < C::NB8; b += nthr) {
+        const int bx = b % C::N8, by = b / C::N8;
+        int ci[C::DMAX + 1];
+        unsigned left = 0;
+#pragma unroll
+        for (int d = 0; d <= C::DMAX; ++d) {
+            const int S = CTU >> d;
+            ci[d] = key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S);
+            if (st.flags[ci[d]] & kRuleEvaluated) left |= 1u << d;
+        }
+#pragma unroll
+        for (int d = 0; d <= C::DMAX; ++d) {
+            if (!((left >> d) & 1u)) continue;
+            unsigned mask = 1u << d;
+#pragma unroll
+            for (int e = d + 1; e <= C::DMAX; ++e)
+                if (((left >> e) & 1u) && st.mvx[ci[e]] == st.mvx[ci[d]] && st.mvy[ci[e]] == st.mvy[ci[d]])
+                    mask |= 1u << e;
+            left &= ~mask;
+            st.pairs[atomicAdd(&st.npairs, 1)] = static_cast<uint16_t>(b | (mask << 8));
+        }
     }
     __syncthreads();
+    // one 8-lane group per entry, NP entries at a time: all their
+    // loads are issued before the first transform
     const unsigned gmask = 0xffu << (tid & 24);
     const int ng = nthr >> 3, np = st.npairs;
-    for (int p = tid >> 3; p < np; p += 2 * ng) {
-        const bool two = p + ng < np;
-        int px[2], py[2], mx[2], my[2], ci[2];
+    for (int p = tid >> 3; p < np; p += NP * ng) {
+        SatdRow<T> w[NP];
+        unsigned ent[NP];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int t = st.pairs[(k == 1 && two) ? p + ng : p];
-            const int d = t / C::NB8, b = t % C::NB8;
-            const int bx = b % C::N8, by = b / C::N8;
-            const int S = CTU >> d;
-            ci[k] = key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S);
-            px[k] = x0 + 8 * bx;
-            py[k] = y0 + 8 * by;
-            mx[k] = st.mvx[ci[k]];
-            my[k] = st.mvy[ci[k]];
+        for (int k = 0; k < NP; ++k) {
+            const int q = p + k * ng;
+            ent[k] = st.pairs[q < np ? q : p];
+            const int b = ent[k] & 0xff, d = __ffs(ent[k] >> 8) - 1;
+            const int bx = b % C::N8, by = b / C::N8, S = CTU >> d;
+            const int i = key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S);
+            satd8_load<T>(io.cur, io.ref, io.pitch_bytes, g.W, g.H, x0 + 8 * bx, y0 + 8 * by, st.mvx[i], st.mvy[i],
+                          w[k]);
         }
-        const int v0 = satd8_group<T>(io.cur, io.ref, io.pitch_bytes, g.W, g.H, px[0], py[0], mx[0], my[0],
-                                      io.satd_mode, gmask);
-        const int v1 = satd8_group<T>(io.cur, io.ref, io.pitch_bytes, g.W, g.H, px[1], py[1], mx[1], my[1],
-                                      io.satd_mode, gmask);
-        if ((tid & 7) == 0) {
-            atomicAdd(&st.satd[ci[0]], v0);
-            if (two) atomicAdd(&st.satd[ci[1]], v1);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const int v = satd8_reduce<T>(w[k], io.satd_mode, gmask);
+            if ((tid & 7) == 0 && p + k * ng < np) {
+                const int b = ent[k] & 0xff, bx = b % C::N8, by = b / C::N8;
+#pragma unroll
+                for (int d = 0; d <= C::DMAX; ++d) {
+                    if (!((ent[k] >> (8 + d)) & 1u)) continue;
+                    const int S = CTU >> d;
+                    atomicAdd(&st.satd[key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S)], v);
+                }
+            }
         }
     }
     __syncthreads();

@@ -191,7 +191,7 @@ static_assert(sizeof(FullSearchBatch) <= 32764, "full-search batch exceeds the k
 // The decisions of one CTU after its search (fuse_decide): decode the keys
 // (and reset them to ~0 for the next search), then SATD, cost, split and
 // leaf maps.  `st` lies in the CTA's shared memory.
-template <typename T, int CTU>
+template <typename T, int CTU, int NP>
 __device__ __forceinline__ void decide_ctu(const FullSearchBatch &b, const FullSearchItem &a, int ctu_idx, int x0,
                                            int y0, dev::CtuState<CTU> &st)
 {
@@ -227,7 +227,7 @@ __device__ __forceinline__ void decide_ctu(const FullSearchBatch &b, const FullS
     }
     __syncthreads();
     dev::DecideIO io{a.cur, a.ref, a.pitch_bytes, &g, a.qp, b.satd_mode, c_lambda_q16, decisions_at(a.block, ri.off)};
-    dev::ctu_decide<T, CTU>(st, io, x0, y0);
+    dev::ctu_decide<T, CTU, NP>(st, io, x0, y0);
 }
 
 template <typename T, int CTU, int RP, int BAND>
@@ -530,7 +530,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
         if (!s_last) return;
         __threadfence();  // every other CTA's key updates before the reads
         if (tid == 0) *done = 0;  // zero for the next search of this block
-        decide_ctu<T, CTU>(b, a, ctu_idx, x0, y0, *reinterpret_cast<dev::CtuState<CTU> *>(sm));
+        // the 9-row band's main loop leaves fewer registers: two SATD entries in flight
+        decide_ctu<T, CTU, BAND == 9 ? 2 : 4>(b, a, ctu_idx, x0, y0, *reinterpret_cast<dev::CtuState<CTU> *>(sm));
     }
 }
 
