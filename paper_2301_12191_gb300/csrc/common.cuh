@@ -35,6 +35,19 @@ template <> __device__ __forceinline__ uint32_t sad_acc<2>(uint32_t a, uint32_t 
     return d;
 }
 
+// First statement of every kernel of this library (launched by
+// launch_chained): wait until the previous kernel in the stream has
+// completed and its writes are visible, then let the next kernel be
+// scheduled.  Every CTA passes the wait before it can finish, so each kernel
+// completes only after its predecessor, and at most one kernel waits behind
+// a running one.  Data written by earlier kernels is read with L2 loads
+// (__ldcg) or atomics, never through the non-coherent read-only path.
+__device__ __forceinline__ void chain_entry()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -432,11 +445,11 @@ __device__ __forceinline__ Rule derive_rule(const RungGeom &g, const DepRefs &rf
     const int ym = min(static_cast<int>(static_cast<unsigned>((2 * y0 + S) * rf.Hr) / static_cast<unsigned>(2 * g.H)),
                        rf.Hr - 1);
     const int li = (ym >> 3) * rf.cols8_r + (xm >> 3);
-    const int depth_r = rf.leaf_depth[li];
+    const int depth_r = __ldcg(rf.leaf_depth + li);
     Rule r;
     if (rf.use_ref_mv) {
-        r.cx = scale_component(rf.leaf_mvx[li], g.W, rf.Wr);
-        r.cy = scale_component(rf.leaf_mvy[li], g.H, rf.Hr);
+        r.cx = scale_component(__ldcg(rf.leaf_mvx + li), g.W, rf.Wr);
+        r.cy = scale_component(__ldcg(rf.leaf_mvy + li), g.H, rf.Hr);
     } else {
         r.cx = r.cy = 0;
     }

@@ -16,6 +16,7 @@ __constant__ int c_lambda_q16[52] = {
 template <typename T, int CTU>
 __global__ void __launch_bounds__(kThreads) k_decide(const __grid_constant__ DecideBatch b)
 {
+    dev::chain_entry();
     using C = dev::Ctu<CTU>;
     __shared__ dev::CtuState<CTU> st;
     int ii = 0;  // the batch item of this CTA
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(kThreads) k_decide(const __grid_constant__ Dec
         st.satd[i] = 0;
         // read the key and reset it to ~0 for the next search
         unsigned long long *kp = const_cast<unsigned long long *>(keys) + static_cast<long>(ctu_idx) * C::NKEY + i;
-        const unsigned long long key = *kp;
+        const unsigned long long key = __ldcg(kp);
         *kp = ~0ull;
         if (flags & kRuleEvaluated) {
             const int rem = static_cast<int>(static_cast<uint32_t>(key & 0xffffffffu) % static_cast<uint32_t>(K * K));
@@ -65,6 +66,7 @@ __global__ void __launch_bounds__(kThreads) k_decide(const __grid_constant__ Dec
 
 __global__ void k_fill_keys(const __grid_constant__ FillBatch b)
 {
+    dev::chain_entry();
     for (int k = 0; k < b.n; ++k)
         for (long i = static_cast<long>(blockIdx.x) * blockDim.x + threadIdx.x; i < b.item[k].n;
              i += static_cast<long>(gridDim.x) * blockDim.x)
@@ -74,8 +76,7 @@ __global__ void k_fill_keys(const __grid_constant__ FillBatch b)
 template <typename T, int CTU>
 cudaError_t decide_t(const DecideBatch &b, cudaStream_t s)
 {
-    k_decide<T, CTU><<<b.total_ctas, kThreads, 0, s>>>(b);
-    return cudaGetLastError();
+    return launch_chained(k_decide<T, CTU>, dim3(b.total_ctas), dim3(kThreads), 0, s, b);
 }
 
 }  // namespace
@@ -99,8 +100,7 @@ cudaError_t launch_fill_keys(const FillBatch &b, cudaStream_t s)
     long most = 0;
     for (int k = 0; k < b.n; ++k) most = std::max(most, b.item[k].n);
     const int blocks = static_cast<int>(std::max<long>(1, std::min<long>((most + kThreads - 1) / kThreads, 1024)));
-    k_fill_keys<<<blocks, kThreads, 0, s>>>(b);
-    return cudaGetLastError();
+    return launch_chained(k_fill_keys, dim3(blocks), dim3(kThreads), 0, s, b);
 }
 
 }  // namespace ladder_impl

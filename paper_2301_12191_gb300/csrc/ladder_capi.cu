@@ -56,9 +56,11 @@ struct ladder {
     // before it (on whatever stream that ran)
     cudaEvent_t dep_done = nullptr;
     bool dep_recorded = false;
+    cudaStream_t dep_stream = nullptr;  // stream of the last recorded dependent batch
     // every argmin key is ~0 at rest (searches reset them after use); after a
     // failed launch that may not hold, and the next launch fills them first
     bool keys_dirty = true;
+    bool counts_dirty = false;  // task counters not known to be zero (zeroed with the arena at init)
     unsigned long long *d_tasks[kSizeClasses] = {};
     unsigned int *d_pos[kSizeClasses] = {};
     unsigned int *d_sums[kSizeClasses] = {};
@@ -372,7 +374,7 @@ ladder_status launch_dependents(ladder_t *l, const Job *jobs, int n, cudaStream_
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cap);
     const bool chain = cap == cudaStreamCaptureStatusNone;
-    if (chain && l->dep_recorded) {
+    if (chain && l->dep_recorded && l->dep_stream != s) {  // same stream: ordered already
         const cudaError_t e = cudaStreamWaitEvent(s, l->dep_done, 0);
         if (e != cudaSuccess) return cuda_fail(l, e, "dependent ordering");
     }
@@ -408,8 +410,14 @@ ladder_status launch_dependents(ladder_t *l, const Job *jobs, int n, cudaStream_
             total += g.ctu_cols * g.ctu_rows;
         }
         b.total_ctas = total;
-        cudaError_t e = cudaMemsetAsync(l->d_counts, 0, kSizeClasses * sizeof(unsigned int), s);
-        if (e != cudaSuccess) return cuda_fail(l, e, "task counters");
+        // the counters rest at zero (each batch's decision kernel resets them)
+        // unless a launch of an earlier batch failed
+        cudaError_t e = cudaSuccess;
+        if (l->counts_dirty) {
+            e = cudaMemsetAsync(l->d_counts, 0, kSizeClasses * sizeof(unsigned int), s);
+            if (e != cudaSuccess) return cuda_fail(l, e, "task counters");
+        }
+        l->counts_dirty = true;
         e = traced(l, 4, s, [&] { return launch_dependent_rules(l->geo.ctu_size, b, s); });
         if (e == cudaSuccess) e = traced(l, 2, s, [&] { return launch_dependent_search(l->geo.bit_depth, b, s); });
         if (e == cudaSuccess)
@@ -418,11 +426,13 @@ ladder_status launch_dependents(ladder_t *l, const Job *jobs, int n, cudaStream_
             l->keys_dirty = true;
             return cuda_fail(l, e, "dependent launch");
         }
+        l->counts_dirty = false;
     }
     if (chain) {
         const cudaError_t e = cudaEventRecord(l->dep_done, s);
         if (e != cudaSuccess) return cuda_fail(l, e, "dependent ordering");
         l->dep_recorded = true;
+        l->dep_stream = s;
     }
     for (int k = 0; k < n; ++k) jobs[k].slot->rungs[jobs[k].rung].analysed = 2;
     return LADDER_OK;

@@ -11,6 +11,28 @@ namespace ladder_impl {
 constexpr int kMaxDepths = 4;
 constexpr int kThreads = 256;  // every analysis kernel runs 256-thread CTAs
 
+// Launches a kernel of this library on stream s as a programmatic dependent
+// of the kernel before it in the stream: its CTAs may be scheduled while
+// that kernel drains.  Every kernel starts with dev::chain_entry(), which
+// waits for the previous kernel to complete (its memory operations visible)
+// before anything touches global memory, so stream order is kept.
+template <typename... Params, typename... Args>
+inline cudaError_t launch_chained(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                  Args &&...args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
 // Device status word values (mirror ladder_status).
 constexpr int kStatusOk = 0;
 constexpr int kStatusTimeout = -6;

@@ -59,6 +59,7 @@ constexpr int kRulesCtus = 8;
 template <int CTU>
 __global__ void __launch_bounds__(32 * kRulesCtus) k_dep_rules(const __grid_constant__ DependentBatch b)
 {
+    dev::chain_entry();
     using C = dev::Ctu<CTU>;
     constexpr int NK = C::NKEY;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -205,6 +206,31 @@ __device__ __forceinline__ uint32_t shift_in(uint32_t lo, uint32_t hi, uint32_t 
     return umad(hi, m, umulhi(lo, m));
 }
 
+// Division by a divisor fixed for the whole launch as a multiply-high, an
+// add and two shifts (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", 1994, Sec. 4): exact for every 32-bit
+// numerator and every divisor >= 1.
+struct FastDiv {
+    uint32_t m, s1, s2;
+};
+
+FastDiv make_fastdiv(uint32_t d)
+{
+    int l = 0;  // ceil(log2 d)
+    while ((1ull << l) < d) ++l;
+    FastDiv f;
+    f.m = static_cast<uint32_t>((((1ull << l) - d) << 32) / d + 1);
+    f.s1 = l > 0 ? 1 : 0;
+    f.s2 = l > 0 ? l - 1 : 0;
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fast_div(uint32_t x, const FastDiv &f)
+{
+    const uint32_t t = __umulhi(f.m, x);
+    return (t + ((x - t) >> f.s1)) >> f.s2;
+}
+
 __device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
 {
     uint32_t d;
@@ -212,86 +238,24 @@ __device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
     return d;
 }
 
-template <typename T>
-__device__ __forceinline__ uint32_t sample_word(const char *plane, long pitch, int W, int H, int x, int y)
-{
-    // SPW samples starting at (x, y), coordinates clamped into the frame
-    constexpr int SPW = 4 / sizeof(T);
-    const T *row = reinterpret_cast<const T *>(plane + static_cast<long>(min(max(y, 0), H - 1)) * pitch);
-    uint32_t w = 0;
-#pragma unroll
-    for (int e = 0; e < SPW; ++e) w |= static_cast<uint32_t>(row[min(max(x + e, 0), W - 1)]) << (e * 8 * sizeof(T));
-    return w;
-}
+// ---- block SADs --------------------------------------------------------------
+// A lane's work per column of NBV stacked 8x8 current blocks: the SADs of the
+// TY candidates (x, y + i), i < TY, in row-major order over the window rows
+// y .. y + 8 NBV + TY - 2, so each reference row is fetched once and used by
+// every candidate it overlaps.  The row fetch is a functor: the fast one reads
+// aligned words and shifts them on the multiply-add pipe; the frame-edge one
+// clamps every sample position into the frame.
 
-// Frame-edge case of the block SADs (coordinates clamped sample by sample):
-// rolled loops, kept out of line so that the unrolled fast paths stay small.
-// Writes the block's SAD of candidate (x, y + i) to out[i].
-template <typename T, int TY>
-__device__ __noinline__ void block_sads_edge(const char *cur, const char *ref, long pitch, int W, int H, int bx,
-                                             int by, int x, int y, uint32_t one, uint32_t *out)
-{
-    constexpr int NW = sizeof(T) == 1 ? 2 : 4;  // words per block row
-    constexpr int SPW = 4 / sizeof(T);
-    uint32_t sa = 0;
-    if constexpr (sizeof(T) == 2)
-        for (int j = 0; j < 8; ++j)
-            for (int q = 0; q < NW; ++q) sa += sample_word<T>(cur, pitch, W, H, bx + q * SPW, by + j);
-    for (int i = 0; i < TY; ++i) {
-        uint32_t s = 0, sb = 0;
-        for (int j = 0; j < 8; ++j) {
-            for (int q = 0; q < NW; ++q) {
-                const uint32_t cw = sample_word<T>(cur, pitch, W, H, bx + q * SPW, by + j);
-                const uint32_t w = sample_word<T>(ref, pitch, W, H, x + q * SPW, y + i + j);
-                if constexpr (sizeof(T) == 1) {
-                    s = dev::sad_acc<4>(cw, w, s);
-                } else {
-                    s = umad(min_u16x2(cw, w), one, s);  // packed sum(min)
-                    sb += w;                             // packed sum(b)
-                }
-            }
-        }
-        if constexpr (sizeof(T) == 1) {
-            out[i] = s;
-        } else {
-            const uint32_t d = umad(s, 0xfffffffeu, sa + sb);
-            out[i] = (d & 0xffffu) + (d >> 16);
-        }
-    }
-}
-
-// Adds the 8x8 block SADs at (bx, by) of the TY candidates (x, y + i),
-// i < TY, to acc (8-bit samples).
-// Adds the SADs of the 8-wide, 8*NBV-high column of current blocks at
-// (bx, by) for the TY candidates (x, y + i), i < TY, to acc (8-bit samples).
-template <int TY, int NBV>
-__device__ __forceinline__ void block_sads_u8(const char *cur, const char *ref, long pitch, int W, int H, int bx,
-                                              int by, int x, int y, uint32_t (&acc)[TY])
+// 8-bit: acc[i] += sum over the column of |cur - ref| at candidate i.
+template <int TY, int NBV, typename RowFn>
+__device__ __forceinline__ void sads_core_u8(const uint2 (&c)[8 * NBV], RowFn row, uint32_t (&acc)[TY])
 {
     constexpr int CR = 8 * NBV, NR = CR + TY - 1;
-    const int q = (x - 1) >> 2;  // words q .. q+2 hold samples x .. x+7
-    const bool fast = bx + 8 <= W && x >= 1 && 4 * q + 12 <= W && y >= 0 && y + NR <= H;
-    if (!fast) {
-#pragma unroll 1
-        for (int v = 0; v < NBV; ++v) {
-            uint32_t e[TY];
-            block_sads_edge<uint8_t, TY>(cur, ref, pitch, W, H, bx, by + 8 * v, x, y + 8 * v, 1u, e);
-#pragma unroll
-            for (int i = 0; i < TY; ++i) acc[i] += e[i];
-        }
-        return;
-    }
-    uint2 c[CR];
-#pragma unroll
-    for (int j = 0; j < CR; ++j)
-        c[j] = __ldg(reinterpret_cast<const uint2 *>(cur + static_cast<long>(min(by + j, H - 1)) * pitch + bx));
-    const uint32_t m = 1u << (32 - 8 * (x - 4 * q));  // x - 4q in 1..4
-    const uint32_t *rp = reinterpret_cast<const uint32_t *>(ref + static_cast<long>(y) * pitch) + q;
-    const long wp = pitch / 4;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        const uint32_t a0 = __ldg(rp + r * wp), a1 = __ldg(rp + r * wp + 1), a2 = __ldg(rp + r * wp + 2);
-        const uint32_t w0 = shift_in(a0, a1, m), w1 = shift_in(a1, a2, m);
+        uint32_t w0, w1;
+        row(r, w0, w1);
+        // all candidates on word 0, then on word 1: no back-to-back dependence
 #pragma unroll
         for (int i = 0; i < TY; ++i) {
             const int j = r - i;
@@ -305,42 +269,22 @@ __device__ __forceinline__ void block_sads_u8(const char *cur, const char *ref, 
     }
 }
 
-// 10-bit samples: SAD = sum(a) + sum(b) - 2 sum(min(a, b)) per packed half.
-template <int TY>
-__device__ __forceinline__ void block_sads_u16(const char *cur, const char *ref, long pitch, int W, int H, int bx,
-                                               int by, int x, int y, uint32_t one, uint32_t (&acc)[TY])
+// 10-bit, one block: SAD = sum(a) + sum(b) - 2 sum(min(a, b)) per packed
+// half; sa = packed sums of the current block's (even, odd) columns.
+template <int TY, typename RowFn>
+__device__ __forceinline__ void sads_core_u16(const uint4 (&c)[8], uint32_t sa, uint32_t one, RowFn row,
+                                              uint32_t (&acc)[TY])
 {
     constexpr int NR = 8 + TY - 1;
-    const int q = (x - 1) >> 1;  // words q .. q+4 hold samples x .. x+7
-    const bool fast = bx + 8 <= W && x >= 1 && 2 * q + 10 <= W && y >= 0 && y + NR <= H;
-    if (!fast) {
-        uint32_t e[TY];
-        block_sads_edge<uint16_t, TY>(cur, ref, pitch, W, H, bx, by, x, y, one, e);
-#pragma unroll
-        for (int i = 0; i < TY; ++i) acc[i] += e[i];
-        return;
-    }
-    uint4 c[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-        c[j] = __ldg(reinterpret_cast<const uint4 *>(cur + static_cast<long>(min(by + j, H - 1)) * pitch + 2 * bx));
-    uint32_t sa = 0;  // packed sums of the current block's even / odd columns
-#pragma unroll
-    for (int j = 0; j < 8; ++j) sa += (c[j].x + c[j].y) + (c[j].z + c[j].w);
     uint32_t mn[TY];
 #pragma unroll
     for (int i = 0; i < TY; ++i) mn[i] = 0;
     uint32_t rs[NR];
     uint32_t sb = 0;
-    const uint32_t m = (x - 2 * q == 1) ? (1u << 16) : 1u;
-    const uint32_t *rp = reinterpret_cast<const uint32_t *>(ref + static_cast<long>(y) * pitch) + q;
-    const long wp = pitch / 4;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        const uint32_t a0 = __ldg(rp + r * wp), a1 = __ldg(rp + r * wp + 1), a2 = __ldg(rp + r * wp + 2),
-                       a3 = __ldg(rp + r * wp + 3), a4 = __ldg(rp + r * wp + 4);
-        const uint32_t w0 = shift_in(a0, a1, m), w1 = shift_in(a1, a2, m), w2 = shift_in(a2, a3, m),
-                       w3 = shift_in(a3, a4, m);
+        uint32_t w0, w1, w2, w3;
+        row(r, w0, w1, w2, w3);
         rs[r] = umad(w0, one, w1) + umad(w2, one, w3);
 #pragma unroll
         for (int i = 0; i < TY; ++i) {
@@ -372,6 +316,153 @@ __device__ __forceinline__ void block_sads_u16(const char *cur, const char *ref,
     }
 }
 
+// Frame-edge columns (8-bit).  Reference: the clamped positions
+// p_e = clamp(x + e, 0, W - 1), e < 8, lie within 8 bytes of p_0, so each
+// row is three aligned words (word indices capped at the row's last
+// sample), one funnel shift to p_0 and a byte permute.  Rows clamp into
+// [0, H).  Current: rows and columns clamp into the frame (replication
+// into the 8-aligned pad).  Writes the column's SADs to out[i].
+template <int TY, int NBV>
+__device__ __noinline__ void column_sads_edge_u8(const char *cur, const char *ref, long pitch, int W, int H, int bx,
+                                                 int by, int x, int y, uint32_t *out)
+{
+    constexpr int CR = 8 * NBV;
+    const int p0 = min(max(x, 0), W - 1);
+    const int q = p0 >> 2, qmax = (W - 1) >> 2, q1 = min(q + 1, qmax), q2 = min(q + 2, qmax);
+    const uint32_t sh = 8u * static_cast<uint32_t>(p0 & 3);
+    uint32_t rsel0 = 0, rsel1 = 0, csel0 = 0, csel1 = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        rsel0 |= static_cast<uint32_t>(min(max(x + e, 0), W - 1) - p0) << (4 * e);
+        rsel1 |= static_cast<uint32_t>(min(max(x + 4 + e, 0), W - 1) - p0) << (4 * e);
+        csel0 |= static_cast<uint32_t>(min(bx + e, W - 1) - bx) << (4 * e);
+        csel1 |= static_cast<uint32_t>(min(bx + 4 + e, W - 1) - bx) << (4 * e);
+    }
+    uint2 c[CR];
+#pragma unroll
+    for (int j = 0; j < CR; ++j) {
+        // bx + 8 <= W8 <= pitch: the aligned 8-byte load stays inside the row
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(cur + static_cast<long>(min(by + j, H - 1)) * pitch + bx));
+        c[j].x = __byte_perm(v.x, v.y, csel0);
+        c[j].y = __byte_perm(v.x, v.y, csel1);
+    }
+    uint32_t acc[TY];
+#pragma unroll
+    for (int i = 0; i < TY; ++i) acc[i] = 0;
+    sads_core_u8<TY, NBV>(c, [&](int r, uint32_t &w0, uint32_t &w1) {
+        const uint32_t *rp = reinterpret_cast<const uint32_t *>(ref + static_cast<long>(min(max(y + r, 0), H - 1)) * pitch);
+        const uint32_t a0 = __ldg(rp + q), a1 = __ldg(rp + q1), a2 = __ldg(rp + q2);
+        const uint32_t v0 = __funnelshift_r(a0, a1, sh), v1 = __funnelshift_r(a1, a2, sh);
+        w0 = __byte_perm(v0, v1, rsel0);
+        w1 = __byte_perm(v0, v1, rsel1);
+    }, acc);
+#pragma unroll
+    for (int i = 0; i < TY; ++i) out[i] = acc[i];
+}
+
+// Frame-edge blocks (10-bit): samples gathered one by one at clamped
+// positions (columns once per block, rows once per row).
+template <int TY>
+__device__ __noinline__ void block_sads_edge_u16(const char *cur, const char *ref, long pitch, int W, int H, int bx,
+                                                 int by, int x, int y, uint32_t one, uint32_t *out)
+{
+    int cc[8], rc[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        cc[e] = min(bx + e, W - 1);
+        rc[e] = min(max(x + e, 0), W - 1);
+    }
+    uint4 c[8];
+    uint32_t sa = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint16_t *row = reinterpret_cast<const uint16_t *>(cur + static_cast<long>(min(by + j, H - 1)) * pitch);
+        uint32_t w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            w[k] = static_cast<uint32_t>(__ldg(row + cc[2 * k])) | (static_cast<uint32_t>(__ldg(row + cc[2 * k + 1])) << 16);
+        c[j] = make_uint4(w[0], w[1], w[2], w[3]);
+        sa += (w[0] + w[1]) + (w[2] + w[3]);
+    }
+    uint32_t acc[TY];
+#pragma unroll
+    for (int i = 0; i < TY; ++i) acc[i] = 0;
+    sads_core_u16<TY>(c, sa, one, [&](int r, uint32_t &w0, uint32_t &w1, uint32_t &w2, uint32_t &w3) {
+        const uint16_t *row = reinterpret_cast<const uint16_t *>(ref + static_cast<long>(min(max(y + r, 0), H - 1)) * pitch);
+        w0 = static_cast<uint32_t>(__ldg(row + rc[0])) | (static_cast<uint32_t>(__ldg(row + rc[1])) << 16);
+        w1 = static_cast<uint32_t>(__ldg(row + rc[2])) | (static_cast<uint32_t>(__ldg(row + rc[3])) << 16);
+        w2 = static_cast<uint32_t>(__ldg(row + rc[4])) | (static_cast<uint32_t>(__ldg(row + rc[5])) << 16);
+        w3 = static_cast<uint32_t>(__ldg(row + rc[6])) | (static_cast<uint32_t>(__ldg(row + rc[7])) << 16);
+    }, acc);
+#pragma unroll
+    for (int i = 0; i < TY; ++i) out[i] = acc[i];
+}
+
+// Adds the SADs of the 8-wide, 8*NBV-high column of current blocks at
+// (bx, by) for the TY candidates (x, y + i), i < TY, to acc (8-bit samples).
+template <int TY, int NBV>
+__device__ __forceinline__ void block_sads_u8(const char *cur, const char *ref, long pitch, int W, int H, int bx,
+                                              int by, int x, int y, uint32_t (&acc)[TY])
+{
+    constexpr int CR = 8 * NBV, NR = CR + TY - 1;
+    const int q = (x - 1) >> 2;  // words q .. q+2 hold samples x .. x+7
+    const bool fast = bx + 8 <= W && x >= 1 && 4 * q + 12 <= W && y >= 0 && y + NR <= H;
+    if (!fast) {
+        uint32_t e[TY];
+        column_sads_edge_u8<TY, NBV>(cur, ref, pitch, W, H, bx, by, x, y, e);
+#pragma unroll
+        for (int i = 0; i < TY; ++i) acc[i] += e[i];
+        return;
+    }
+    uint2 c[CR];
+#pragma unroll
+    for (int j = 0; j < CR; ++j)
+        c[j] = __ldg(reinterpret_cast<const uint2 *>(cur + static_cast<long>(min(by + j, H - 1)) * pitch + bx));
+    const uint32_t m = 1u << (32 - 8 * (x - 4 * q));  // x - 4q in 1..4
+    const uint32_t *rp = reinterpret_cast<const uint32_t *>(ref + static_cast<long>(y) * pitch) + q;
+    const long wp = pitch / 4;
+    sads_core_u8<TY, NBV>(c, [&](int r, uint32_t &w0, uint32_t &w1) {
+        const uint32_t a0 = __ldg(rp + r * wp), a1 = __ldg(rp + r * wp + 1), a2 = __ldg(rp + r * wp + 2);
+        w0 = shift_in(a0, a1, m);
+        w1 = shift_in(a1, a2, m);
+    }, acc);
+}
+
+// 10-bit samples, one 8x8 block.
+template <int TY>
+__device__ __forceinline__ void block_sads_u16(const char *cur, const char *ref, long pitch, int W, int H, int bx,
+                                               int by, int x, int y, uint32_t one, uint32_t (&acc)[TY])
+{
+    constexpr int NR = 8 + TY - 1;
+    const int q = (x - 1) >> 1;  // words q .. q+4 hold samples x .. x+7
+    const bool fast = bx + 8 <= W && x >= 1 && 2 * q + 10 <= W && y >= 0 && y + NR <= H;
+    if (!fast) {
+        uint32_t e[TY];
+        block_sads_edge_u16<TY>(cur, ref, pitch, W, H, bx, by, x, y, one, e);
+#pragma unroll
+        for (int i = 0; i < TY; ++i) acc[i] += e[i];
+        return;
+    }
+    uint4 c[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        c[j] = __ldg(reinterpret_cast<const uint4 *>(cur + static_cast<long>(min(by + j, H - 1)) * pitch + 2 * bx));
+    uint32_t sa = 0;  // packed sums of the current block's even / odd columns
+#pragma unroll
+    for (int j = 0; j < 8; ++j) sa += (c[j].x + c[j].y) + (c[j].z + c[j].w);
+    const uint32_t m = (x - 2 * q == 1) ? (1u << 16) : 1u;
+    const uint32_t *rp = reinterpret_cast<const uint32_t *>(ref + static_cast<long>(y) * pitch) + q;
+    const long wp = pitch / 4;
+    sads_core_u16<TY>(c, sa, one, [&](int r, uint32_t &w0, uint32_t &w1, uint32_t &w2, uint32_t &w3) {
+        const uint32_t a0 = __ldg(rp + r * wp), a1 = __ldg(rp + r * wp + 1), a2 = __ldg(rp + r * wp + 2),
+                       a3 = __ldg(rp + r * wp + 3), a4 = __ldg(rp + r * wp + 4);
+        w0 = shift_in(a0, a1, m);
+        w1 = shift_in(a1, a2, m);
+        w2 = shift_in(a2, a3, m);
+        w3 = shift_in(a3, a4, m);
+    }, acc);
+}
+
 // Bits of the largest SAD of an S x S CU.
 __device__ __forceinline__ int sad_bits(int S, int bit_depth)
 {
@@ -380,7 +471,7 @@ __device__ __forceinline__ int sad_bits(int S, int bit_depth)
 
 template <typename T, int TY>
 __device__ __forceinline__ void search_tile(const DependentBatch &b, int c, int lt, unsigned int ncu, int per_cu,
-                                            int rb, int lane)
+                                            const FastDiv &div_cu, const FastDiv &div_k, int rb, int lane)
 {
     const int r = b.r, K = 2 * r + 1;
     // CUs larger than the range are searched as range x range pieces
@@ -388,20 +479,21 @@ __device__ __forceinline__ void search_tile(const DependentBatch &b, int c, int 
     const int nrs = S / RS, nr = nrs * nrs;
     const int per_task = nr * per_cu;  // lanes of one CU
     const long ntask = static_cast<long>(ncu) * per_task;
-    auto task_of = [&](int l) { return min(static_cast<long>(lt) * 32 + l, ntask - 1); };
     const long traw = static_cast<long>(lt) * 32 + lane;
-    const long t = task_of(lane);
-    const unsigned int u = static_cast<unsigned int>(t / per_task);
-    int rem = static_cast<int>(t - static_cast<long>(u) * per_task);
-    const int rg = rem / per_cu;
-    rem -= rg * per_cu;
-    const int band = rem / K, dxi = rem - band * K;
-    const unsigned long long task = b.tasks[c][u];
+    const long t = min(traw, ntask - 1);
+    // lane t of the class = ((CU u, piece rg), band, dxi): t / per_cu = u * nr + rg (nr a power of 4)
+    const uint32_t q = t <= 0xffffffffL ? fast_div(static_cast<uint32_t>(t), div_cu)
+                                        : static_cast<uint32_t>(t / per_cu);
+    const unsigned int u = q >> (2 * (31 - __clz(nrs)));
+    const int rg = static_cast<int>(q & static_cast<uint32_t>(nr - 1));
+    const int rem = static_cast<int>(t - static_cast<long>(q) * per_cu);
+    const int band = static_cast<int>(fast_div(static_cast<uint32_t>(rem), div_k)), dxi = rem - band * K;
+    const unsigned long long task = __ldcg(b.tasks[c] + u);
     const uint32_t lo = static_cast<uint32_t>(task), hi = static_cast<uint32_t>(task >> 32);
     const DependentItem &a = b.item[lo & 0xffu];
     const RungInfo &rinf = b.rung[a.rung];
     const RungGeom &g = rinf.g;
-    const unsigned int p = b.pos[c][u];
+    const unsigned int p = __ldcg(b.pos[c] + u);
     const int cu_x = static_cast<int>(p & 0xffffu) + (rg % nrs) * RS;  // this piece's origin
     const int cu_y = static_cast<int>(p >> 16) + (rg / nrs) * RS;
     const int cx = static_cast<int16_t>(hi & 0xffffu), cy = static_cast<int16_t>(hi >> 16);
@@ -496,16 +588,18 @@ __device__ __forceinline__ void search_tile(const DependentBatch &b, int c, int 
 }
 
 template <typename T, int TY>
-__global__ void __launch_bounds__(kSearchThreads, 2) k_dep_search(const __grid_constant__ DependentBatch b)
+__global__ void __launch_bounds__(kSearchThreads, 2)
+    k_dep_search(const __grid_constant__ DependentBatch b, const FastDiv div_cu, const FastDiv div_k)
 {
+    dev::chain_entry();
     const int lane = threadIdx.x & 31;
     const int r = b.r, K = 2 * r + 1;
     const int per_cu = K * ((K + TY - 1) / TY);
     const int code_max = 4 * r * K + 4 * r + 1;
     const int rb = 32 - __clz(code_max);
     // per size class: CUs and warp tiles (scalars: no local-memory arrays)
-    const unsigned int n0 = min(__ldg(b.counts + 0), b.cap[0]), n1 = min(__ldg(b.counts + 1), b.cap[1]),
-                       n2 = min(__ldg(b.counts + 2), b.cap[2]), n3 = min(__ldg(b.counts + 3), b.cap[3]);
+    const unsigned int n0 = min(__ldcg(b.counts + 0), b.cap[0]), n1 = min(__ldcg(b.counts + 1), b.cap[1]),
+                       n2 = min(__ldcg(b.counts + 2), b.cap[2]), n3 = min(__ldcg(b.counts + 3), b.cap[3]);
     // lanes per CU: per_cu per piece (pieces of 32x32 / 64x64 CUs: (S / range)^2)
     const long p2 = b.range >= 32 ? 1 : 4, p3 = b.range >= 32 ? 4 : 16;
     const long t0 = (static_cast<long>(n0) * per_cu + 31) / 32, t1 = (static_cast<long>(n1) * per_cu + 31) / 32,
@@ -533,7 +627,7 @@ __global__ void __launch_bounds__(kSearchThreads, 2) k_dep_search(const __grid_c
             c = 0;
             ncu = n0;
         }
-        search_tile<T, TY>(b, c, static_cast<int>(lt), ncu, per_cu, rb, lane);
+        search_tile<T, TY>(b, c, static_cast<int>(lt), ncu, per_cu, div_cu, div_k, rb, lane);
     }
 }
 
@@ -541,6 +635,10 @@ __global__ void __launch_bounds__(kSearchThreads, 2) k_dep_search(const __grid_c
 template <typename T, int CTU>
 __global__ void __launch_bounds__(kDecideThreads) k_dep_decide(const __grid_constant__ DependentBatch b)
 {
+    dev::chain_entry();
+    // the search has completed: its task counters go back to zero for the
+    // next batch (they rest at zero between batches)
+    if (blockIdx.x == 0 && threadIdx.x < kSizeClasses) b.counts[threadIdx.x] = 0;
     using C = dev::Ctu<CTU>;
     const DependentItem &a = b.item[item_of(b)];
     const RungInfo &rinf = b.rung[a.rung];
@@ -556,40 +654,50 @@ __global__ void __launch_bounds__(kDecideThreads) k_dep_decide(const __grid_cons
     const uint8_t *in_fl = reinterpret_cast<const uint8_t *>(a.block + rinf.off.dep_flags) + kbase;
     const unsigned long long *keys = reinterpret_cast<const unsigned long long *>(a.block + rinf.off.keys) + kbase;
     const int *in_slot = reinterpret_cast<const int *>(a.block + rinf.off.dep_slot) + kbase;
-    // CUs searched in ranges: argmin of (SAD, |dx|+|dy|, dy, dx) over the
-    // CU's table, one warp per CU
-    __shared__ unsigned long long s_best[C::NKEY];
-    constexpr int NBIG = key_offset(C::DMAX - kFirstSummedClass + 1);
-    const int lane = tid & 31, warp = tid >> 5;
-    auto summed = [&](int i) { return i < NBIG && in_slot[i] >= 0 && (CTU >> depth_of(i, C::DMAX)) > b.range; };
-    for (int i = warp; i < NBIG; i += kDecideThreads / 32) {
-        const int pos = in_slot[i];
-        if (!summed(i) || !(in_fl[i] & kRuleEvaluated)) continue;
-        const unsigned int *sum = b.sums[C::DMAX - depth_of(i, C::DMAX)] + static_cast<long>(pos) * (K * K);
-        unsigned long long best = ~0ull;
-        for (int k = lane; k < K * K; k += 32) {
-            const int dxo = k % K - r, dyo = k / K - r;
-            const uint32_t tb = static_cast<uint32_t>((abs(dxo) + abs(dyo)) * K * K + k);
-            const unsigned long long key = (static_cast<unsigned long long>(sum[k]) << 32) | tb;
-            best = key < best ? key : best;
-        }
+    // rule flags and list places of the CTU's CUs, one round of L2 loads
+    constexpr int NBIG = key_offset(C::DMAX - kFirstSummedClass + 1);  // CUs of 32x32 and up
+    __shared__ uint8_t s_fl[C::NKEY];
+    __shared__ int s_slot[NBIG > 0 ? NBIG : 1];  // 16x16 CTUs have no CU of 32x32
+    __shared__ unsigned long long s_best[NBIG > 0 ? NBIG : 1];
+    for (int i = tid; i < C::NKEY; i += kDecideThreads) {
+        s_fl[i] = __ldcg(in_fl + i);
+        if (i < NBIG) s_slot[i] = __ldcg(in_slot + i);
+    }
+    __syncthreads();
+    // CUs searched in pieces: argmin of (SAD, |dx|+|dy|, dy, dx) over the
+    // CU's sum table, 16 lanes per CU
+    auto summed = [&](int i) { return i < NBIG && s_slot[i] >= 0 && (CTU >> depth_of(i, C::DMAX)) > b.range; };
+    {
+        const int hl = tid & 15;
+        const unsigned hmask = 0xffffu << (tid & 16);
+        for (int i = tid >> 4; i < NBIG; i += kDecideThreads / 16) {
+            if (!summed(i) || !(s_fl[i] & kRuleEvaluated)) continue;  // the same for the 16 lanes
+            const unsigned int *sum = b.sums[C::DMAX - depth_of(i, C::DMAX)] + static_cast<long>(s_slot[i]) * (K * K);
+            unsigned long long best = ~0ull;
+            for (int k = hl; k < K * K; k += 16) {
+                const int dxo = k % K - r, dyo = k / K - r;
+                const uint32_t tb = static_cast<uint32_t>((abs(dxo) + abs(dyo)) * K * K + k);
+                const unsigned long long key = (static_cast<unsigned long long>(__ldcg(sum + k)) << 32) | tb;
+                best = key < best ? key : best;
+            }
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
-            best = v < best ? v : best;
+            for (int o = 8; o >= 1; o >>= 1) {
+                const unsigned long long v = __shfl_xor_sync(hmask, best, o);
+                best = v < best ? v : best;
+            }
+            if (hl == 0) s_best[i] = best;
         }
-        if (lane == 0) s_best[i] = best;
     }
     __syncthreads();
     for (int i = tid; i < C::NKEY; i += kDecideThreads) {
-        const uint8_t f = in_fl[i];
+        const uint8_t f = s_fl[i];
         st.flags[i] = f;
         st.satd[i] = 0;
         if (f & kRuleEvaluated) {
-            const unsigned long long key = summed(i) ? s_best[i] : keys[i];
+            const unsigned long long key = summed(i) ? s_best[i] : __ldcg(keys + i);
             const int rem = static_cast<int>(static_cast<uint32_t>(key & 0xffffffffu) % static_cast<uint32_t>(K * K));
-            st.mvx[i] = static_cast<int16_t>(in_cx[i] + rem % K - r);
-            st.mvy[i] = static_cast<int16_t>(in_cy[i] + rem / K - r);
+            st.mvx[i] = static_cast<int16_t>(__ldcg(in_cx + i) + rem % K - r);
+            st.mvy[i] = static_cast<int16_t>(__ldcg(in_cy + i) + rem / K - r);
             st.sad[i] = static_cast<int32_t>(key >> 32);
         } else {
             st.mvx[i] = INT16_MIN;
@@ -637,8 +745,10 @@ template <typename T, int TY> cudaError_t search_t(const DependentBatch &b, cuda
 {
     const int fit = search_ctas_per_sm<T, TY>();
     const int grid = sm_count() * (b.ctas_per_sm > 0 ? std::min(b.ctas_per_sm, fit) : fit);
-    k_dep_search<T, TY><<<grid, kSearchThreads, 0, s>>>(b);
-    return cudaGetLastError();
+    // divisors of the lane decode: lanes per CU piece, candidate columns
+    const uint32_t K = 2 * b.r + 1, per_cu = K * ((K + TY - 1) / TY);
+    return launch_chained(k_dep_search<T, TY>, dim3(grid), dim3(kSearchThreads), 0, s, b, make_fastdiv(per_cu),
+                          make_fastdiv(K));
 }
 
 template <typename T> cudaError_t search_bd(const DependentBatch &b, cudaStream_t s)
@@ -658,10 +768,8 @@ cudaError_t launch_dependent_rules(int ctu, const DependentBatch &b, cudaStream_
 {
     if (b.n < 1 || b.n > kMaxDepItems || b.total_ctas <= 0) return cudaErrorInvalidValue;
     const int grid = (b.total_ctas + kRulesCtus - 1) / kRulesCtus;
-    if (ctu == 64) k_dep_rules<64><<<grid, 32 * kRulesCtus, 0, s>>>(b);
-    else if (ctu == 32) k_dep_rules<32><<<grid, 32 * kRulesCtus, 0, s>>>(b);
-    else k_dep_rules<16><<<grid, 32 * kRulesCtus, 0, s>>>(b);
-    return cudaGetLastError();
+    auto kern = ctu == 64 ? k_dep_rules<64> : ctu == 32 ? k_dep_rules<32> : k_dep_rules<16>;
+    return launch_chained(kern, dim3(grid), dim3(32 * kRulesCtus), 0, s, b);
 }
 
 cudaError_t launch_dependent_search(int bit_depth, const DependentBatch &b, cudaStream_t s)
@@ -673,16 +781,11 @@ cudaError_t launch_dependent_search(int bit_depth, const DependentBatch &b, cuda
 cudaError_t launch_dependent_decide(int bit_depth, int ctu, const DependentBatch &b, cudaStream_t s)
 {
     if (b.n < 1 || b.n > kMaxDepItems || b.total_ctas <= 0) return cudaErrorInvalidValue;
-    if (bit_depth == 8) {
-        if (ctu == 64) k_dep_decide<uint8_t, 64><<<b.total_ctas, kDecideThreads, 0, s>>>(b);
-        else if (ctu == 32) k_dep_decide<uint8_t, 32><<<b.total_ctas, kDecideThreads, 0, s>>>(b);
-        else k_dep_decide<uint8_t, 16><<<b.total_ctas, kDecideThreads, 0, s>>>(b);
-    } else {
-        if (ctu == 64) k_dep_decide<uint16_t, 64><<<b.total_ctas, kDecideThreads, 0, s>>>(b);
-        else if (ctu == 32) k_dep_decide<uint16_t, 32><<<b.total_ctas, kDecideThreads, 0, s>>>(b);
-        else k_dep_decide<uint16_t, 16><<<b.total_ctas, kDecideThreads, 0, s>>>(b);
-    }
-    return cudaGetLastError();
+    auto kern = bit_depth == 8 ? (ctu == 64 ? k_dep_decide<uint8_t, 64>
+                                            : ctu == 32 ? k_dep_decide<uint8_t, 32> : k_dep_decide<uint8_t, 16>)
+                               : (ctu == 64 ? k_dep_decide<uint16_t, 64>
+                                            : ctu == 32 ? k_dep_decide<uint16_t, 32> : k_dep_decide<uint16_t, 16>);
+    return launch_chained(kern, dim3(b.total_ctas), dim3(kDecideThreads), 0, s, b);
 }
 
 cudaError_t prepare_kernels(int bit_depth, int ctu, int R, int r)

@@ -236,6 +236,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
     using S = Shape<T, CTU, RP, BAND>;
     constexpr int TY = S::TY, P4 = S::P4, ES = S::ES, NT = S::NT;
     constexpr int NR = 8 + TY - 1;  // window rows read per 8x8 block
+    dev::chain_entry();
 
     extern __shared__ __align__(128) uint8_t smem_raw[];
     uint8_t *const sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -570,8 +571,7 @@ cudaError_t launch_t(const FullSearchBatch &b, int smem, cudaStream_t s)
     if (e != cudaSuccess) return e;
     const int n2 = (b.box_h - std::min(b.phase1_rows, b.box_h)) * S::CPR;
     if (n2 > S::MAXC * S::NT || b.box_h > S::MAX_ROWS || 4 * S::TY * 32 * 4 > b.e_bytes) return cudaErrorInvalidValue;
-    k_full_search<T, CTU, RP, BAND><<<b.total, S::NT, smem, s>>>(b);
-    return cudaGetLastError();
+    return launch_chained(k_full_search<T, CTU, RP, BAND>, dim3(b.total), dim3(S::NT), smem, s, b);
 }
 
 // Dispatch on (bit depth, CTU, window margin class, band): 64x64 CTUs have
