@@ -126,129 +126,138 @@ __device__ __forceinline__ int ld_sample(const char *base, long pitch, int x, in
     return static_cast<int>(__ldg(reinterpret_cast<const T *>(base + static_cast<long>(y) * pitch) + x));
 }
 
-// One row of an 8x8 block for the SATD: the current samples and the
-// displaced reference samples, packed SPW per word.
+// Sample k of a packed word as the float 2^23 + sample (a byte permute
+// into the bit pattern of 2^23): exact, and the difference of two such
+// floats is the exact integer difference of the samples.
 template <typename T>
-struct SatdRow {
-    static constexpr int WPR = 8 / Traits<T>::SPW;
-    uint32_t cw[WPR], rw[WPR];
-};
-
-// Loads the row (lane & 7) of the 8x8 block at (px, py) and of the
-// reference displaced by (mvx, mvy).  Samples are read with clamping
-// (current: replicate to the 8-aligned size; reference: frame edge).
-template <typename T>
-__device__ __forceinline__ void satd8_load(const void *cur, const void *ref, long pitch, int W, int H, int px,
-                                           int py, int mvx, int mvy, SatdRow<T> &w)
+__device__ __forceinline__ float sample_f(uint32_t w, int k)
 {
-    const char *cb = static_cast<const char *>(cur);
-    const char *rb = static_cast<const char *>(ref);
-    constexpr int SPW = Traits<T>::SPW, BITS = 32 / SPW, WPR = SatdRow<T>::WPR;
-    const int y = threadIdx.x & 7;
-    const int cy = min(py + y, H - 1);
-    const int ry = min(max(py + y + mvy, 0), H - 1);
-    const int rx0 = px + mvx;
-    if (px + 8 <= W) {  // current row: one aligned vector load
-        const char *row = cb + static_cast<long>(cy) * pitch + static_cast<long>(px) * sizeof(T);
-        if constexpr (WPR == 2) {
-            const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row));
-            w.cw[0] = q.x;
-            w.cw[1] = q.y;
-        } else {
-            const uint4 q = __ldg(reinterpret_cast<const uint4 *>(row));
-            w.cw[0] = q.x;
-            w.cw[1] = q.y;
-            w.cw[2] = q.z;
-            w.cw[3] = q.w;
-        }
-    } else {
-#pragma unroll
-        for (int m = 0; m < WPR; ++m) {
-            uint32_t v = 0;
-#pragma unroll
-            for (int e = 0; e < SPW; ++e)
-                v |= static_cast<uint32_t>(ld_sample<T>(cb, pitch, min(px + m * SPW + e, W - 1), cy)) << (e * BITS);
-            w.cw[m] = v;
-        }
-    }
-    if (rx0 >= 0 && (rx0 / SPW + WPR + 1) * SPW <= W) {  // reference row: aligned words + one funnel shift
-        const uint32_t *rp = reinterpret_cast<const uint32_t *>(rb + static_cast<long>(ry) * pitch) + rx0 / SPW;
-        const int sh = (rx0 & (SPW - 1)) * BITS;
-        uint32_t raw[WPR + 1];
-#pragma unroll
-        for (int m = 0; m <= WPR; ++m) raw[m] = __ldg(rp + m);
-#pragma unroll
-        for (int m = 0; m < WPR; ++m) w.rw[m] = __funnelshift_r(raw[m], raw[m + 1], sh);
-    } else {
-#pragma unroll
-        for (int m = 0; m < WPR; ++m) {
-            uint32_t v = 0;
-#pragma unroll
-            for (int e = 0; e < SPW; ++e)
-                v |= static_cast<uint32_t>(ld_sample<T>(rb, pitch, min(max(rx0 + m * SPW + e, 0), W - 1), ry))
-                     << (e * BITS);
-            w.rw[m] = v;
-        }
-    }
+    // selector: sample bytes into bytes 0 (and 1), zero, 0x4b (byte 7 of the pair)
+    const uint32_t sel = sizeof(T) == 1 ? 0x7540u + static_cast<uint32_t>(k)
+                                        : 0x7400u + static_cast<uint32_t>(2 * k) + (static_cast<uint32_t>(2 * k + 1) << 4);
+    return __int_as_float(static_cast<int>(__byte_perm(w, 0x4b000000u, sel)));
 }
 
-// SATD of the 8x8 residual whose rows the 8 lanes of an aligned lane group
-// hold (lane & 7 = row); every lane of the group returns the block's SATD.
-// `gmask` is the group's lane mask.
+// SATD of the 8x8 block at (px, py) against the reference displaced by
+// (mvx, mvy), by one thread.  Samples are read with clamping (current:
+// replicate to the 8-aligned size; reference: frame edge).  The residual
+// and every butterfly sum are integers below 2^24 in magnitude, so they are
+// exact in fp32: the transform runs as fp32 adds on the FMA pipes.
 //   mode 0: 8x8 Hadamard T = H8 D H8^T, (sum |T|) >> 2
 //   mode 1: two 4x4 Hadamards per 8x4 half, (sum of both) >> 1, halves added
 template <typename T>
-__device__ __forceinline__ int satd8_reduce(const SatdRow<T> &w, int mode, unsigned gmask)
+__device__ __forceinline__ int satd8_thread(const void *cur, const void *ref, long pitch, int W, int H, int px, int py,
+                                            int mvx, int mvy, int mode)
 {
-    constexpr int SPW = Traits<T>::SPW, BITS = 32 / SPW;
-    const int y = threadIdx.x & 7;
-    int v[8];
+    const char *cb = static_cast<const char *>(cur);
+    const char *rb = static_cast<const char *>(ref);
+    constexpr int SPW = Traits<T>::SPW, BITS = 32 / SPW, WPR = 8 / SPW;
+    const int rx0 = px + mvx;
+    const bool cur_fast = px + 8 <= W;
+    const bool ref_fast = rx0 >= 0 && (rx0 / SPW + WPR + 1) * SPW <= W;
+    const int sh = (rx0 & (SPW - 1)) * BITS;
+    float v[64];
 #pragma unroll
-    for (int x = 0; x < 8; ++x) {
-        const int m = x / SPW, sh = (x % SPW) * BITS;
-        const int mask = (1 << BITS) - 1;
-        v[x] = static_cast<int>((w.cw[m] >> sh) & mask) - static_cast<int>((w.rw[m] >> sh) & mask);
-    }
-    if (mode == 0) {
-        fwht<8>(v);  // along the row
+    for (int y = 0; y < 8; ++y) {
+        const int cy = min(py + y, H - 1);
+        const int ry = min(max(py + y + mvy, 0), H - 1);
+        uint32_t cw[WPR], rw[WPR];
+        if (cur_fast) {  // one aligned vector load
+            const char *row = cb + static_cast<long>(cy) * pitch + static_cast<long>(px) * sizeof(T);
+            if constexpr (WPR == 2) {
+                const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row));
+                cw[0] = q.x;
+                cw[1] = q.y;
+            } else {
+                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(row));
+                cw[0] = q.x;
+                cw[1] = q.y;
+                cw[2] = q.z;
+                cw[3] = q.w;
+            }
+        } else {
 #pragma unroll
-        for (int s = 4; s >= 1; s >>= 1) {  // along the column: butterflies across lanes
-            const bool upper = y & s;
+            for (int m = 0; m < WPR; ++m) {
+                uint32_t w = 0;
 #pragma unroll
-            for (int x = 0; x < 8; ++x) {
-                const int o = __shfl_xor_sync(gmask, v[x], s);
-                v[x] = upper ? o - v[x] : v[x] + o;
+                for (int e = 0; e < SPW; ++e)
+                    w |= static_cast<uint32_t>(ld_sample<T>(cb, pitch, min(px + m * SPW + e, W - 1), cy)) << (e * BITS);
+                cw[m] = w;
             }
         }
-        int sum = 0;
+        if (ref_fast) {  // aligned words + one funnel shift
+            const uint32_t *rp = reinterpret_cast<const uint32_t *>(rb + static_cast<long>(ry) * pitch) + rx0 / SPW;
+            uint32_t raw[WPR + 1];
 #pragma unroll
-        for (int x = 0; x < 8; ++x) sum += abs(v[x]);
+            for (int m = 0; m <= WPR; ++m) raw[m] = __ldg(rp + m);
 #pragma unroll
-        for (int s = 4; s >= 1; s >>= 1) sum += __shfl_xor_sync(gmask, sum, s);
-        return sum >> 2;
-    }
-    int lo[4] = {v[0], v[1], v[2], v[3]}, hi[4] = {v[4], v[5], v[6], v[7]};
-    fwht<4>(lo);
-    fwht<4>(hi);
+            for (int m = 0; m < WPR; ++m) rw[m] = __funnelshift_r(raw[m], raw[m + 1], sh);
+        } else {
 #pragma unroll
-    for (int s = 2; s >= 1; s >>= 1) {  // columns of each 4-row half
-        const bool upper = y & s;
+            for (int m = 0; m < WPR; ++m) {
+                uint32_t w = 0;
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
-            const int ol = __shfl_xor_sync(gmask, lo[x], s);
-            const int oh = __shfl_xor_sync(gmask, hi[x], s);
-            lo[x] = upper ? ol - lo[x] : lo[x] + ol;
-            hi[x] = upper ? oh - hi[x] : hi[x] + oh;
+                for (int e = 0; e < SPW; ++e)
+                    w |= static_cast<uint32_t>(ld_sample<T>(rb, pitch, min(max(rx0 + m * SPW + e, 0), W - 1), ry))
+                         << (e * BITS);
+                rw[m] = w;
+            }
         }
+#pragma unroll
+        for (int x = 0; x < 8; ++x) v[8 * y + x] = sample_f<T>(cw[x / SPW], x % SPW) - sample_f<T>(rw[x / SPW], x % SPW);
     }
-    int sum = 0;
+    auto bfly = [&](int i, int j) {
+        const float a = v[i], b = v[j];
+        v[i] = a + b;
+        v[j] = a - b;
+    };
+    if (mode == 0) {
 #pragma unroll
-    for (int x = 0; x < 4; ++x) sum += abs(lo[x]) + abs(hi[x]);
+        for (int y = 0; y < 8; ++y)  // rows
 #pragma unroll
-    for (int s = 2; s >= 1; s >>= 1) sum += __shfl_xor_sync(gmask, sum, s);  // one 8x4 half
-    sum >>= 1;
-    sum += __shfl_xor_sync(gmask, sum, 4);                                  // both halves
-    return sum;
+            for (int s = 4; s >= 1; s >>= 1)
+#pragma unroll
+                for (int x = 0; x < 8; ++x)
+                    if (!(x & s)) bfly(8 * y + x, 8 * y + x + s);
+#pragma unroll
+        for (int x = 0; x < 8; ++x)  // columns
+#pragma unroll
+            for (int s = 4; s >= 1; s >>= 1)
+#pragma unroll
+                for (int y = 0; y < 8; ++y)
+                    if (!(y & s)) bfly(8 * y + x, 8 * (y + s) + x);
+        // exact sums (integers below 2^24): any order, here a short tree
+        float part[8];
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+            part[y] = (fabsf(v[8 * y]) + fabsf(v[8 * y + 1])) + (fabsf(v[8 * y + 2]) + fabsf(v[8 * y + 3])) +
+                      ((fabsf(v[8 * y + 4]) + fabsf(v[8 * y + 5])) + (fabsf(v[8 * y + 6]) + fabsf(v[8 * y + 7])));
+        }
+        const float sum = ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
+        return __float2int_rn(sum) >> 2;
+    }
+#pragma unroll
+    for (int y = 0; y < 8; ++y)  // rows of each 4-wide half
+#pragma unroll
+        for (int s = 2; s >= 1; s >>= 1)
+#pragma unroll
+            for (int x = 0; x < 8; ++x)
+                if (!(x & s)) bfly(8 * y + x, 8 * y + x + s);
+#pragma unroll
+    for (int x = 0; x < 8; ++x)  // columns of each 4-row half
+#pragma unroll
+        for (int s = 2; s >= 1; s >>= 1)
+#pragma unroll
+            for (int y = 0; y < 8; ++y)
+                if (!(y & s)) bfly(8 * y + x, 8 * (y + s) + x);
+    float part[8];  // rows; rows 0-3 and 4-7 are the two 8x4 halves
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
+        part[y] = (fabsf(v[8 * y]) + fabsf(v[8 * y + 1])) + (fabsf(v[8 * y + 2]) + fabsf(v[8 * y + 3])) +
+                  ((fabsf(v[8 * y + 4]) + fabsf(v[8 * y + 5])) + (fabsf(v[8 * y + 6]) + fabsf(v[8 * y + 7])));
+    }
+    const float top = (part[0] + part[1]) + (part[2] + part[3]), bottom = (part[4] + part[5]) + (part[6] + part[7]);
+    return (__float2int_rn(top) >> 1) + (__float2int_rn(bottom) >> 1);
 }
 
 constexpr uint8_t kPresent = 8;  // CU lies (at least partly) inside the 8-aligned frame
@@ -276,14 +285,13 @@ struct DecideIO {
 __device__ __forceinline__ int key_index(int d, int li) { return key_offset(d) + li; }
 
 // The decision step for one CTU, given flags / vectors / SADs in `st`
-// (satd[] must be zero).  All threads of the CTA take part; NP is the
-// number of SATD entries each 8-lane group has in flight.
+// (satd[] must be zero).  All threads of the CTA take part.
 //   SATD   -- Sec. 5.4.1 SATD equation; Sec. 5.4.2 satd8 / satd_8x4 listings
 //   cost   -- J = SATD + ((lambdaQ16[qp] * bits + 2^15) >> 16), bits = se()
 //             lengths of the quarter-pel components (predictor (0,0))
 //   split  -- Sec. 2.1: split iff it may and (it is not a leaf candidate or
 //             the children's best sum is strictly lower), or it must
-template <typename T, int CTU, int NP = 4>
+template <typename T, int CTU>
 __device__ void ctu_decide(CtuState<CTU> &st, const DecideIO &io, int x0, int y0)
 {
     using C = Ctu<CTU>;
@@ -320,35 +328,19 @@ __device__ void ctu_decide(CtuState<CTU> &st, const DecideIO &io, int x0, int y0
         }
     }
     __syncthreads();
-    // one 8-lane group per entry, NP entries at a time: all their
-    // loads are issued before the first transform
-    const unsigned gmask = 0xffu << (tid & 24);
-    const int ng = nthr >> 3, np = st.npairs;
-    for (int p = tid >> 3; p < np; p += NP * ng) {
-        SatdRow<T> w[NP];
-        unsigned ent[NP];
+    // one thread per entry
+    for (int p = tid; p < st.npairs; p += nthr) {
+        const unsigned ent = st.pairs[p];
+        const int b = ent & 0xff, bx = b % C::N8, by = b / C::N8;
+        const int d0 = __ffs(ent >> 8) - 1, S0 = CTU >> d0;
+        const int i0 = key_index(d0, ((by * 8) / S0) * (1 << d0) + (bx * 8) / S0);
+        const int v = satd8_thread<T>(io.cur, io.ref, io.pitch_bytes, g.W, g.H, x0 + 8 * bx, y0 + 8 * by, st.mvx[i0],
+                                      st.mvy[i0], io.satd_mode);
 #pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            const int q = p + k * ng;
-            ent[k] = st.pairs[q < np ? q : p];
-            const int b = ent[k] & 0xff, d = __ffs(ent[k] >> 8) - 1;
-            const int bx = b % C::N8, by = b / C::N8, S = CTU >> d;
-            const int i = key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S);
-            satd8_load<T>(io.cur, io.ref, io.pitch_bytes, g.W, g.H, x0 + 8 * bx, y0 + 8 * by, st.mvx[i], st.mvy[i],
-                          w[k]);
-        }
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            const int v = satd8_reduce<T>(w[k], io.satd_mode, gmask);
-            if ((tid & 7) == 0 && p + k * ng < np) {
-                const int b = ent[k] & 0xff, bx = b % C::N8, by = b / C::N8;
-#pragma unroll
-                for (int d = 0; d <= C::DMAX; ++d) {
-                    if (!((ent[k] >> (8 + d)) & 1u)) continue;
-                    const int S = CTU >> d;
-                    atomicAdd(&st.satd[key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S)], v);
-                }
-            }
+        for (int d = 0; d <= C::DMAX; ++d) {
+            if (!((ent >> (8 + d)) & 1u)) continue;
+            const int S = CTU >> d;
+            atomicAdd(&st.satd[key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S)], v);
         }
     }
     __syncthreads();

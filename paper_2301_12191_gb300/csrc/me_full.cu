@@ -191,7 +191,7 @@ static_assert(sizeof(FullSearchBatch) <= 32764, "full-search batch exceeds the k
 // The decisions of one CTU after its search (fuse_decide): decode the keys
 // (and reset them to ~0 for the next search), then SATD, cost, split and
 // leaf maps.  `st` lies in the CTA's shared memory.
-template <typename T, int CTU, int NP>
+template <typename T, int CTU>
 __device__ __forceinline__ void decide_ctu(const FullSearchBatch &b, const FullSearchItem &a, int ctu_idx, int x0,
                                            int y0, dev::CtuState<CTU> &st)
 {
@@ -227,7 +227,7 @@ __device__ __forceinline__ void decide_ctu(const FullSearchBatch &b, const FullS
     }
     __syncthreads();
     dev::DecideIO io{a.cur, a.ref, a.pitch_bytes, &g, a.qp, b.satd_mode, c_lambda_q16, decisions_at(a.block, ri.off)};
-    dev::ctu_decide<T, CTU, NP>(st, io, x0, y0);
+    dev::ctu_decide<T, CTU>(st, io, x0, y0);
 }
 
 template <typename T, int CTU, int RP, int BAND>
@@ -378,111 +378,131 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
             s16[i] = 0;
             s32[i] = 0;
         }
-    #pragma unroll 1
-        for (int bq = 0; bq < S::NBQ; ++bq) {
-            const int zx = (bq & 1) | ((bq >> 1) & 2), zy = ((bq >> 1) & 1) | ((bq >> 2) & 2);
-            const int bx = zx * 8, by = zy * 8;
-            const bool present = x0 + qx + bx < W8 && y0 + qy + by < H8;
-            uint32_t acc[TY];
+        // SADs of the lane's candidates for the 8x8 block at (bx, by) of the
+        // quadrant (acc starts at zero), and the block's 8x8 key
+        auto block_sads = [&](int bx, int by, uint32_t(&acc)[TY]) {
+            const uint32_t *bp = lp + by * P4 + bx;
+            const T *cp = curs + (qy + by) * CTU + qx + bx;
+            if constexpr (ES == 1) {
+                uint2 c[8];
     #pragma unroll
-            for (int i = 0; i < TY; ++i) acc[i] = 0;
-            if (present) {
-                const uint32_t *bp = lp + by * P4 + bx;
-                const T *cp = curs + (qy + by) * CTU + qx + bx;
-                if constexpr (ES == 1) {
-                    uint2 c[8];
+                for (int j = 0; j < 8; ++j) c[j] = *reinterpret_cast<const uint2 *>(cp + j * CTU);
     #pragma unroll
-                    for (int j = 0; j < 8; ++j) c[j] = *reinterpret_cast<const uint2 *>(cp + j * CTU);
+                for (int r = 0; r < NR; ++r) {
+                    const uint32_t w0 = bp[r * P4], w1 = bp[r * P4 + 4];
+                    // all candidates on word 0, then on word 1: no back-to-back dependence
     #pragma unroll
-                    for (int r = 0; r < NR; ++r) {
-                        const uint32_t w0 = bp[r * P4], w1 = bp[r * P4 + 4];
-                        // all candidates on word 0, then on word 1: no back-to-back dependence
-    #pragma unroll
-                        for (int i = 0; i < TY; ++i) {
-                            const int j = r - i;
-                            if (j >= 0 && j < 8) acc[i] = sad_acc<4>(c[j].x, w0, acc[i]);
-                        }
-    #pragma unroll
-                        for (int i = 0; i < TY; ++i) {
-                            const int j = r - i;
-                            if (j >= 0 && j < 8) acc[i] = sad_acc<4>(c[j].y, w1, acc[i]);
-                        }
-                    }
-                } else {
-                    uint4 c[8];
-    #pragma unroll
-                    for (int j = 0; j < 8; ++j) c[j] = *reinterpret_cast<const uint4 *>(cp + j * CTU);
-                    const uint32_t sa = a8[((qy + by) / 8) * (CTU / 8) + (qx + bx) / 8];
-                    // candidate i is complete after window row i + 7: there
-                    // SAD = sum(a) + sum(b) - 2 sum(min), per packed half
-                    uint32_t rs[NR];
-                    uint32_t sb = 0;
-    #pragma unroll
-                    for (int r = 0; r < NR; ++r) {
-                        const uint32_t w0 = bp[r * P4], w1 = bp[r * P4 + 2], w2 = bp[r * P4 + 4], w3 = bp[r * P4 + 6];
-                        rs[r] = (w0 + w1) + (w2 + w3);
-    #pragma unroll
-                        for (int i = 0; i < TY; ++i) {
-                            const int j = r - i;
-                            if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].x, w0), one, acc[i]);
-                        }
-    #pragma unroll
-                        for (int i = 0; i < TY; ++i) {
-                            const int j = r - i;
-                            if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].y, w1), one, acc[i]);
-                        }
-    #pragma unroll
-                        for (int i = 0; i < TY; ++i) {
-                            const int j = r - i;
-                            if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].z, w2), one, acc[i]);
-                        }
-    #pragma unroll
-                        for (int i = 0; i < TY; ++i) {
-                            const int j = r - i;
-                            if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].w, w3), one, acc[i]);
-                        }
-                        if (r < 8) sb += rs[r];
-                        else sb = sb + rs[r] - rs[r - 8];
-                        if (r >= 7) {
-                            const int i = r - 7;
-                            const uint32_t d = umad(acc[i], 0xfffffffeu, sa + sb);
-                            acc[i] = (d & 0xffffu) + (d >> 16);
-                        }
-                    }
-                }
-                // 8x8 key
-                const uint32_t key = __reduce_min_sync(0xffffffffu, lane_key32<TY>(acc, code, m16, all_valid, dy0, R));
-                if (lane == 0) atomicMin(&s_k8[((qy + by) / 8) * (CTU / 8) + (qx + bx) / 8], key);
-            }
-    #pragma unroll
-            for (int i = 0; i < TY; ++i) s16[i] = umad(acc[i], one, s16[i]);
-
-            if constexpr (S::Q >= 16) {
-                if ((bq & 3) == 3) {  // 16x16 CU complete
-                    const int cx = (qx + bx) / 16, cy = (qy + by) / 16;
-                    if (x0 + cx * 16 < W8 && y0 + cy * 16 < H8) {
-                        unsigned long long key;
-                        if constexpr (S::K16_32) key = __reduce_min_sync(0xffffffffu, lane_key32<TY>(s16, code, m16, all_valid, dy0, R));
-                        else key = warp_min_u64(lane_key64<TY>(s16, code, m16, all_valid, dy0, R));
-                        if (lane == 0) atomicMin(&s_kup[key_offset(S::DMAX - 1) + cy * (CTU / 16) + cx], key);
+                    for (int i = 0; i < TY; ++i) {
+                        const int j = r - i;
+                        if (j >= 0 && j < 8) acc[i] = sad_acc<4>(c[j].x, w0, acc[i]);
                     }
     #pragma unroll
                     for (int i = 0; i < TY; ++i) {
-                        s32[i] = umad(s16[i], one, s32[i]);
-                        s16[i] = 0;
+                        const int j = r - i;
+                        if (j >= 0 && j < 8) acc[i] = sad_acc<4>(c[j].y, w1, acc[i]);
+                    }
+                }
+            } else {
+                uint4 c[8];
+    #pragma unroll
+                for (int j = 0; j < 8; ++j) c[j] = *reinterpret_cast<const uint4 *>(cp + j * CTU);
+                const uint32_t sa = a8[((qy + by) / 8) * (CTU / 8) + (qx + bx) / 8];
+                // candidate i is complete after window row i + 7: there
+                // SAD = sum(a) + sum(b) - 2 sum(min), per packed half
+                uint32_t rs[NR];
+                uint32_t sb = 0;
+    #pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const uint32_t w0 = bp[r * P4], w1 = bp[r * P4 + 2], w2 = bp[r * P4 + 4], w3 = bp[r * P4 + 6];
+                    rs[r] = (w0 + w1) + (w2 + w3);
+    #pragma unroll
+                    for (int i = 0; i < TY; ++i) {
+                        const int j = r - i;
+                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].x, w0), one, acc[i]);
+                    }
+    #pragma unroll
+                    for (int i = 0; i < TY; ++i) {
+                        const int j = r - i;
+                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].y, w1), one, acc[i]);
+                    }
+    #pragma unroll
+                    for (int i = 0; i < TY; ++i) {
+                        const int j = r - i;
+                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].z, w2), one, acc[i]);
+                    }
+    #pragma unroll
+                    for (int i = 0; i < TY; ++i) {
+                        const int j = r - i;
+                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].w, w3), one, acc[i]);
+                    }
+                    if (r < 8) sb += rs[r];
+                    else sb = sb + rs[r] - rs[r - 8];
+                    if (r >= 7) {
+                        const int i = r - 7;
+                        const uint32_t d = umad(acc[i], 0xfffffffeu, sa + sb);
+                        acc[i] = (d & 0xffffu) + (d >> 16);
                     }
                 }
             }
-            if constexpr (S::Q >= 32) {
-                if ((bq & 15) == 15) {  // 32x32 CU complete
-                    const int cx = (qx + bx) / 32, cy = (qy + by) / 32;
-                    if (x0 + cx * 32 < W8 && y0 + cy * 32 < H8) {
-                        const unsigned long long key = warp_min_u64(lane_key64<TY>(s32, code, m16, all_valid, dy0, R));
-                        if (lane == 0) atomicMin(&s_kup[key_offset(S::DMAX - 2) + cy * (CTU / 32) + cx], key);
-                    }
+            const uint32_t key = __reduce_min_sync(0xffffffffu, lane_key32<TY>(acc, code, m16, all_valid, dy0, R));
+            if (lane == 0) atomicMin(&s_k8[((qy + by) / 8) * (CTU / 8) + (qx + bx) / 8], key);
+        };
+        auto key16 = [&](int cx, int cy) {  // 16x16 CU (cx, cy) of the CTU complete in s16
+            if (x0 + cx * 16 < W8 && y0 + cy * 16 < H8) {
+                unsigned long long key;
+                if constexpr (S::K16_32) key = __reduce_min_sync(0xffffffffu, lane_key32<TY>(s16, code, m16, all_valid, dy0, R));
+                else key = warp_min_u64(lane_key64<TY>(s16, code, m16, all_valid, dy0, R));
+                if (lane == 0) atomicMin(&s_kup[key_offset(S::DMAX - 1) + cy * (CTU / 16) + cx], key);
+            }
+    #pragma unroll
+            for (int i = 0; i < TY; ++i) {
+                s32[i] = umad(s16[i], one, s32[i]);
+                s16[i] = 0;
+            }
+        };
+        auto key32 = [&]() {  // the quadrant's 32x32 CU complete in s32
+            const int cx = qx / 32, cy = qy / 32;
+            if (x0 + cx * 32 < W8 && y0 + cy * 32 < H8) {
+                const unsigned long long key = warp_min_u64(lane_key64<TY>(s32, code, m16, all_valid, dy0, R));
+                if (lane == 0) atomicMin(&s_kup[key_offset(S::DMAX - 2) + cy * (CTU / 32) + cx], key);
+            }
+        };
+        // blocks in Z order.  8-bit: 16x16 CUs of 4 blocks as an inner loop;
+        // 10-bit (longer block bodies): one loop over the quadrant's blocks
+        if constexpr (ES == 1) {
+            constexpr int B16 = S::NBQ >= 4 ? 4 : S::NBQ;  // 8x8 blocks per 16x16 CU inside a quadrant
+            constexpr int N16 = S::NBQ / B16;
+    #pragma unroll 1
+            for (int q16 = 0; q16 < N16; ++q16) {
+    #pragma unroll 1
+                for (int b4 = 0; b4 < B16; ++b4) {
+                    const int bq = q16 * B16 + b4;
+                    const int bx = ((bq & 1) | ((bq >> 1) & 2)) * 8, by = (((bq >> 1) & 1) | ((bq >> 2) & 2)) * 8;
+                    if (x0 + qx + bx >= W8 || y0 + qy + by >= H8) continue;  // block outside the frame: adds 0
+                    uint32_t acc[TY];
+    #pragma unroll
+                    for (int i = 0; i < TY; ++i) acc[i] = 0;
+                    block_sads(bx, by, acc);
+    #pragma unroll
+                    for (int i = 0; i < TY; ++i) s16[i] = umad(acc[i], one, s16[i]);
                 }
+                if constexpr (S::Q >= 16) key16((qx + 16 * (q16 & 1)) / 16, (qy + 16 * (q16 >> 1)) / 16);
+            }
+        } else {
+    #pragma unroll 1
+            for (int bq = 0; bq < S::NBQ; ++bq) {
+                const int bx = ((bq & 1) | ((bq >> 1) & 2)) * 8, by = (((bq >> 1) & 1) | ((bq >> 2) & 2)) * 8;
+                uint32_t acc[TY];
+    #pragma unroll
+                for (int i = 0; i < TY; ++i) acc[i] = 0;
+                if (x0 + qx + bx < W8 && y0 + qy + by < H8) block_sads(bx, by, acc);
+    #pragma unroll
+                for (int i = 0; i < TY; ++i) s16[i] = umad(acc[i], one, s16[i]);
+                if constexpr (S::Q >= 16)
+                    if ((bq & 3) == 3) key16((qx + bx) / 16, (qy + by) / 16);
             }
         }
+        if constexpr (S::Q >= 32) key32();
 
         // CTU level: the four quadrants' sums (warp 0 has read the previous
         // tile's exchange once every warp passes the first barrier)
@@ -531,8 +551,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
         if (!s_last) return;
         __threadfence();  // every other CTA's key updates before the reads
         if (tid == 0) *done = 0;  // zero for the next search of this block
-        // the 9-row band's main loop leaves fewer registers: two SATD entries in flight
-        decide_ctu<T, CTU, BAND == 9 ? 2 : 4>(b, a, ctu_idx, x0, y0, *reinterpret_cast<dev::CtuState<CTU> *>(sm));
+        decide_ctu<T, CTU>(b, a, ctu_idx, x0, y0, *reinterpret_cast<dev::CtuState<CTU> *>(sm));
     }
 }
 
