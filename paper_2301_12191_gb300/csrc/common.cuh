@@ -260,6 +260,21 @@ __device__ __forceinline__ int satd8_thread(const void *cur, const void *ref, lo
     return (__float2int_rn(top) >> 1) + (__float2int_rn(bottom) >> 1);
 }
 
+// Index of the batch item whose CTA range holds this CTA (items in order of
+// cta_begin): a binary search over the item table in parameter space.
+template <typename Item>
+__device__ __forceinline__ int item_of_cta(const Item *item, int n)
+{
+    int lo = 0, hi = n - 1;
+    const int c = static_cast<int>(blockIdx.x);
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (c >= item[mid].cta_begin) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 constexpr uint8_t kPresent = 8;  // CU lies (at least partly) inside the 8-aligned frame
 
 // Per-CTU state of the decision step, in shared memory.
@@ -418,12 +433,11 @@ struct Rule {
     bool allowed_leaf, allowed_split;
 };
 
-__device__ __forceinline__ int scale_component(int v, int to, int from)
+__device__ __forceinline__ int scale_component(int v, int to, int from, const FastDiv &div_2from)
 {
     // |v| <= 32768 and sizes <= 8192: 2|v|*to + from < 2^31
     const unsigned av = static_cast<unsigned>(v < 0 ? -v : v);
-    const int s = static_cast<int>((2u * av * static_cast<unsigned>(to) + static_cast<unsigned>(from)) /
-                                   (2u * static_cast<unsigned>(from)));
+    const int s = static_cast<int>(fast_div(2u * av * static_cast<unsigned>(to) + static_cast<unsigned>(from), div_2from));
     const int r = v < 0 ? -s : s;
     return min(max(r, -256), 256);
 }
@@ -432,16 +446,14 @@ __device__ __forceinline__ Rule derive_rule(const RungGeom &g, const DepRefs &rf
 {
     // sizes are <= 8192, so the products below stay inside 32 bits
     const int S = g.ctu >> d;
-    const int xm = min(static_cast<int>(static_cast<unsigned>((2 * x0 + S) * rf.Wr) / static_cast<unsigned>(2 * g.W)),
-                       rf.Wr - 1);
-    const int ym = min(static_cast<int>(static_cast<unsigned>((2 * y0 + S) * rf.Hr) / static_cast<unsigned>(2 * g.H)),
-                       rf.Hr - 1);
+    const int xm = min(static_cast<int>(fast_div(static_cast<unsigned>((2 * x0 + S) * rf.Wr), g.div_2w)), rf.Wr - 1);
+    const int ym = min(static_cast<int>(fast_div(static_cast<unsigned>((2 * y0 + S) * rf.Hr), g.div_2h)), rf.Hr - 1);
     const int li = (ym >> 3) * rf.cols8_r + (xm >> 3);
     const int depth_r = __ldcg(rf.leaf_depth + li);
     Rule r;
     if (rf.use_ref_mv) {
-        r.cx = scale_component(__ldcg(rf.leaf_mvx + li), g.W, rf.Wr);
-        r.cy = scale_component(__ldcg(rf.leaf_mvy + li), g.H, rf.Hr);
+        r.cx = scale_component(__ldcg(rf.leaf_mvx + li), g.W, rf.Wr, rf.div_2wr);
+        r.cy = scale_component(__ldcg(rf.leaf_mvy + li), g.H, rf.Hr, rf.div_2hr);
     } else {
         r.cx = r.cy = 0;
     }

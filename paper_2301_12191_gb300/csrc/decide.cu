@@ -19,8 +19,7 @@ __global__ void __launch_bounds__(kThreads) k_decide(const __grid_constant__ Dec
     dev::chain_entry();
     using C = dev::Ctu<CTU>;
     __shared__ dev::CtuState<CTU> st;
-    int ii = 0;  // the batch item of this CTA
-    while (ii + 1 < b.n && static_cast<int>(blockIdx.x) >= b.item[ii + 1].cta_begin) ++ii;
+    const int ii = dev::item_of_cta(b.item, b.n);  // the batch item of this CTA
     const DecideItem &item = b.item[ii];
     const RungInfo &ri = b.rung[item.rung];
     const RungGeom &g = ri.g;

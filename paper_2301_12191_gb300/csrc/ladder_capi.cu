@@ -171,6 +171,8 @@ RungGeom make_geom(int W, int H, int ctu)
     }
     g.cols8 = g.W8 / 8;
     g.rows8 = g.H8 / 8;
+    g.div_2w = make_fastdiv(2u * static_cast<uint32_t>(W));
+    g.div_2h = make_fastdiv(2u * static_cast<uint32_t>(H));
     return g;
 }
 

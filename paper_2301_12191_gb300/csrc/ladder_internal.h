@@ -54,6 +54,34 @@ enum : uint8_t {
     kRuleReachable = 4,  // every ancestor may split
 };
 
+// Division by a divisor fixed for a whole launch as a multiply-high, an
+// add and two shifts (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", 1994, Sec. 4): exact for every 32-bit
+// numerator and every divisor >= 1.  make_fastdiv runs on the host,
+// fast_div on the device.
+struct FastDiv {
+    uint32_t m, s1, s2;
+};
+
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    int l = 0;  // ceil(log2 d)
+    while ((1ull << l) < d) ++l;
+    FastDiv f;
+    f.m = static_cast<uint32_t>((((1ull << l) - d) << 32) / d + 1);
+    f.s1 = l > 0 ? 1 : 0;
+    f.s2 = l > 0 ? l - 1 : 0;
+    return f;
+}
+
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t fast_div(uint32_t x, const FastDiv &f)
+{
+    const uint32_t t = __umulhi(f.m, x);
+    return (t + ((x - t) >> f.s1)) >> f.s2;
+}
+#endif
+
 // Geometry of one rung (host and device).
 struct RungGeom {
     int W, H, W8, H8;
@@ -61,6 +89,7 @@ struct RungGeom {
     int ctu_cols, ctu_rows;
     int cols[kMaxDepths], rows[kMaxDepths];
     int cols8, rows8;
+    FastDiv div_2w, div_2h;  // division by 2W, 2H
 };
 
 // Device decision arrays of one (rung, frame slot).
@@ -216,6 +245,7 @@ struct DepRefs {
     const uint8_t *leaf_depth;
     const int16_t *leaf_mvx, *leaf_mvy;
     int depth_lo, depth_hi, use_ref_mv;
+    FastDiv div_2wr, div_2hr;  // division by 2 Wr, 2 Hr
 };
 
 struct DependentItem {

@@ -36,12 +36,7 @@ __constant__ int c_lambda_q16[52] = {
 constexpr int kSearchThreads = 256;
 constexpr int kDecideThreads = 128;
 
-__device__ __forceinline__ int item_of(const DependentBatch &b)
-{
-    int ri = 0;
-    while (ri + 1 < b.n && static_cast<int>(blockIdx.x) >= b.item[ri + 1].cta_begin) ++ri;
-    return ri;
-}
+__device__ __forceinline__ int item_of(const DependentBatch &b) { return dev::item_of_cta(b.item, b.n); }
 
 __device__ __forceinline__ int depth_of(int i, int dmax)
 {
@@ -51,39 +46,44 @@ __device__ __forceinline__ int depth_of(int i, int dmax)
 }
 
 // ---- 1. rules ---------------------------------------------------------------
-// One warp per CTU, kRulesCtus CTUs per CTA: the work per CTU is small, so
-// a CTA covers several and takes one task-list reservation per size class
-// for all of them (few global atomics on the shared counters).
-constexpr int kRulesCtus = 8;
+// One CTA per CTU, one thread per CU: the rule, reachability and flags, the
+// CU's place in its size class's task list (one global atomic per class and
+// CTA), and zeroed sum tables for the CUs searched in pieces.
+constexpr int kRulesThreads = 128;
 
 template <int CTU>
-__global__ void __launch_bounds__(32 * kRulesCtus) k_dep_rules(const __grid_constant__ DependentBatch b)
+__global__ void __launch_bounds__(kRulesThreads) k_dep_rules(const __grid_constant__ DependentBatch b)
 {
     dev::chain_entry();
     using C = dev::Ctu<CTU>;
     constexpr int NK = C::NKEY;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int gctu = blockIdx.x * kRulesCtus + w;  // CTU of this warp across the batch
-    const bool active = gctu < b.total_ctas;
+    static_assert(NK <= kRulesThreads, "one thread per CU");
+    constexpr int NBIG = key_offset(C::DMAX - kFirstSummedClass + 1);  // CUs of 32x32 and up
+    const int tid = threadIdx.x;
+    const bool mine = tid < NK;
 
-    __shared__ int16_t s_cx[kRulesCtus][NK], s_cy[kRulesCtus][NK];
-    __shared__ uint8_t s_leaf[kRulesCtus][NK], s_splitok[kRulesCtus][NK], s_flags[kRulesCtus][NK];
-    __shared__ int s_pos[kRulesCtus][NK];
+    __shared__ uint8_t s_leaf[NK], s_splitok[NK];
     __shared__ unsigned int s_cnt[kSizeClasses], s_base[kSizeClasses];
-    if (threadIdx.x < kSizeClasses) s_cnt[threadIdx.x] = 0;
+    __shared__ int s_big[NBIG > 0 ? NBIG : 1];  // list places of CUs searched in pieces (-1: none)
+    if (tid < kSizeClasses) s_cnt[tid] = 0;
 
-    int ri = 0;
-    while (active && ri + 1 < b.n && gctu >= b.item[ri + 1].cta_begin) ++ri;
+    const int ri = item_of(b);
     const DependentItem &a = b.item[ri];
     const RungInfo &rinf = b.rung[a.rung];
     const RungInfo &rref = b.rung[b.ref_rung];
     const RungGeom &g = rinf.g;
-    const int ctu_idx = gctu - a.cta_begin;
+    const int ctu_idx = static_cast<int>(blockIdx.x) - a.cta_begin;
     const int x0 = (ctu_idx % g.ctu_cols) * CTU, y0 = (ctu_idx / g.ctu_cols) * CTU;
     const long kbase = static_cast<long>(ctu_idx) * NK;
-    __syncthreads();
 
-    if (active) {
+    // the rule of CU tid
+    const int d = mine ? depth_of(tid, C::DMAX) : 0;
+    const int li = tid - key_offset(d), n = 1 << d, S = CTU >> d;
+    const int cu_x = x0 + (li % n) * S, cu_y = y0 + (li / n) * S;
+    const bool present = mine && cu_x < g.W8 && cu_y < g.H8;
+    uint8_t leaf = 0, splitok = 0;
+    int16_t cx = 0, cy = 0;
+    if (present) {
         DepRefs refs;
         refs.Wr = rref.g.W;
         refs.Hr = rref.g.H;
@@ -94,93 +94,74 @@ __global__ void __launch_bounds__(32 * kRulesCtus) k_dep_rules(const __grid_cons
         refs.depth_lo = b.depth_lo;
         refs.depth_hi = b.depth_hi;
         refs.use_ref_mv = b.use_ref_mv;
-        for (int i = lane; i < NK; i += 32) {
-            const int d = depth_of(i, C::DMAX);
-            const int li = i - key_offset(d), n = 1 << d, S = CTU >> d;
-            const int cu_x = x0 + (li % n) * S, cu_y = y0 + (li / n) * S;
-            const bool present = cu_x < g.W8 && cu_y < g.H8;
-            uint8_t leaf = 0, splitok = 0;
-            int16_t cx = 0, cy = 0;
-            if (present) {
-                const bool inside = cu_x + S <= g.W8 && cu_y + S <= g.H8;
-                const dev::Rule ru = dev::derive_rule(g, refs, d, cu_x, cu_y);
-                cx = static_cast<int16_t>(ru.cx);
-                cy = static_cast<int16_t>(ru.cy);
-                leaf = inside && ru.allowed_leaf;
-                splitok = d < C::DMAX && (!inside || ru.allowed_split);
-            }
-            s_cx[w][i] = cx;
-            s_cy[w][i] = cy;
-            s_leaf[w][i] = leaf;
-            s_splitok[w][i] = splitok;
-            s_flags[w][i] = present ? dev::kPresent : 0;
-        }
-        __syncwarp();
-        // reachability (every ancestor may split) and the rule flags
-        int16_t *const out_cx = reinterpret_cast<int16_t *>(a.block + rinf.off.dep_cx) + kbase;
-        int16_t *const out_cy = reinterpret_cast<int16_t *>(a.block + rinf.off.dep_cy) + kbase;
-        uint8_t *const out_fl = reinterpret_cast<uint8_t *>(a.block + rinf.off.dep_flags) + kbase;
-        unsigned long long *const keys = reinterpret_cast<unsigned long long *>(a.block + rinf.off.keys) + kbase;
-        for (int i = lane; i < NK; i += 32) {
-            uint8_t f = s_flags[w][i];
-            if (f & dev::kPresent) {
-                const int d = depth_of(i, C::DMAX);
-                const int li = i - key_offset(d), n = 1 << d;
-                const int cxl = li % n, cyl = li / n;
-                bool reach = true;
-                for (int e = 0; e < d; ++e)
-                    reach = reach && s_splitok[w][dev::key_index(e, (cyl >> (d - e)) * (1 << e) + (cxl >> (d - e)))];
-                if (reach) f |= kRuleReachable;
-                if (reach && s_leaf[w][i]) f |= kRuleEvaluated;
-                if (reach && s_splitok[w][i]) f |= kRuleCanSplit;
-                if (f & kRuleEvaluated) atomicAdd(&s_cnt[C::DMAX - d], 1u);  // size class of an S = CTU >> d CU
-            }
-            s_flags[w][i] = f;
-            out_cx[i] = s_cx[w][i];
-            out_cy[i] = s_cy[w][i];
-            out_fl[i] = f;
-            keys[i] = ~0ull;
-        }
+        refs.div_2wr = rref.g.div_2w;
+        refs.div_2hr = rref.g.div_2h;
+        const bool inside = cu_x + S <= g.W8 && cu_y + S <= g.H8;
+        const dev::Rule ru = dev::derive_rule(g, refs, d, cu_x, cu_y);
+        cx = static_cast<int16_t>(ru.cx);
+        cy = static_cast<int16_t>(ru.cy);
+        leaf = inside && ru.allowed_leaf;
+        splitok = d < C::DMAX && (!inside || ru.allowed_split);
+    }
+    if (mine) {
+        s_leaf[tid] = leaf;
+        s_splitok[tid] = splitok;
     }
     __syncthreads();
-    if (threadIdx.x < kSizeClasses) {
-        const unsigned int n = s_cnt[threadIdx.x];
+
+    // reachability (every ancestor may split) and the rule flags
+    uint8_t f = 0;
+    if (present) {
+        f = dev::kPresent;
+        const int cxl = li % n, cyl = li / n;
+        bool reach = true;
+        for (int e = 0; e < d; ++e)
+            reach = reach && s_splitok[dev::key_index(e, (cyl >> (d - e)) * (1 << e) + (cxl >> (d - e)))];
+        if (reach) f |= kRuleReachable;
+        if (reach && s_leaf[tid]) f |= kRuleEvaluated;
+        if (reach && s_splitok[tid]) f |= kRuleCanSplit;
+        if (f & kRuleEvaluated) atomicAdd(&s_cnt[C::DMAX - d], 1u);  // size class of an S = CTU >> d CU
+    }
+    if (mine) {
+        reinterpret_cast<int16_t *>(a.block + rinf.off.dep_cx)[kbase + tid] = cx;
+        reinterpret_cast<int16_t *>(a.block + rinf.off.dep_cy)[kbase + tid] = cy;
+        reinterpret_cast<uint8_t *>(a.block + rinf.off.dep_flags)[kbase + tid] = f;
+        reinterpret_cast<unsigned long long *>(a.block + rinf.off.keys)[kbase + tid] = ~0ull;
+    }
+    __syncthreads();
+    if (tid < kSizeClasses) {
+        const unsigned int cnt = s_cnt[tid];
         unsigned int base = 0;
-        if (n) base = atomicAdd(&b.counts[threadIdx.x], n);
-        if (n && base + n > b.cap[threadIdx.x]) atomicExch(b.status, kStatusTaskOverflow);
-        s_base[threadIdx.x] = base;
-        s_cnt[threadIdx.x] = 0;
+        if (cnt) base = atomicAdd(&b.counts[tid], cnt);
+        if (cnt && base + cnt > b.cap[tid]) atomicExch(b.status, kStatusTaskOverflow);
+        s_base[tid] = base;
+        s_cnt[tid] = 0;
     }
     __syncthreads();
-    if (!active) return;
-    for (int i = lane; i < NK; i += 32) {
-        s_pos[w][i] = -1;
-        if (!(s_flags[w][i] & kRuleEvaluated)) continue;
-        const int c = C::DMAX - depth_of(i, C::DMAX);  // size class: CU size 8 << c
-        const unsigned int pos = s_base[c] + atomicAdd(&s_cnt[c], 1u);
-        if (pos >= b.cap[c]) continue;
-        const uint32_t lo = static_cast<uint32_t>(ri) | (static_cast<uint32_t>(kbase + i) << 8);
-        const uint32_t hi = static_cast<uint32_t>(static_cast<uint16_t>(s_cx[w][i])) |
-                            (static_cast<uint32_t>(static_cast<uint16_t>(s_cy[w][i])) << 16);
-        b.tasks[c][pos] = (static_cast<unsigned long long>(hi) << 32) | lo;
-        {
-            const int d = depth_of(i, C::DMAX);
-            const int li = i - key_offset(d), n = 1 << d, S = CTU >> d;
-            b.pos[c][pos] = static_cast<unsigned int>(x0 + (li % n) * S) |
-                            (static_cast<unsigned int>(y0 + (li / n) * S) << 16);
+
+    // the CU's task: item | key slot << 8, centre in the high word; its origin
+    int pos = -1;
+    if (f & kRuleEvaluated) {
+        const int c = C::DMAX - d;  // size class: CU size 8 << c
+        const unsigned int p = s_base[c] + atomicAdd(&s_cnt[c], 1u);
+        if (p < b.cap[c]) {
+            const uint32_t lo = static_cast<uint32_t>(ri) | (static_cast<uint32_t>(kbase + tid) << 8);
+            const uint32_t hi = static_cast<uint32_t>(static_cast<uint16_t>(cx)) |
+                                (static_cast<uint32_t>(static_cast<uint16_t>(cy)) << 16);
+            b.tasks[c][p] = (static_cast<unsigned long long>(hi) << 32) | lo;
+            b.pos[c][p] = static_cast<unsigned int>(cu_x) | (static_cast<unsigned int>(cu_y) << 16);
+            pos = static_cast<int>(p);
         }
-        s_pos[w][i] = static_cast<int>(pos);
     }
-    __syncwarp();
-    // CUs searched in pieces: their list place, and a zeroed sum table
-    int *const out_slot = reinterpret_cast<int *>(a.block + rinf.off.dep_slot) + kbase;
+    if (mine) reinterpret_cast<int *>(a.block + rinf.off.dep_slot)[kbase + tid] = pos;
+    if (tid < NBIG) s_big[tid] = S > b.range ? pos : -1;
+    __syncthreads();
+    // zeroed sum tables of the CUs searched in pieces
     const int KK = (2 * b.r + 1) * (2 * b.r + 1);
-    for (int i = lane; i < NK; i += 32) out_slot[i] = s_pos[w][i];
-    constexpr int NBIG = key_offset(C::DMAX - kFirstSummedClass + 1);  // CUs of 32x32 and up
     for (int i = 0; i < NBIG; ++i) {
-        if (s_pos[w][i] < 0 || (CTU >> depth_of(i, C::DMAX)) <= b.range) continue;
-        unsigned int *sum = b.sums[C::DMAX - depth_of(i, C::DMAX)] + static_cast<long>(s_pos[w][i]) * KK;
-        for (int k = lane; k < KK; k += 32) sum[k] = 0;
+        if (s_big[i] < 0) continue;
+        unsigned int *sum = b.sums[C::DMAX - depth_of(i, C::DMAX)] + static_cast<long>(s_big[i]) * KK;
+        for (int k = tid; k < KK; k += kRulesThreads) sum[k] = 0;
     }
 }
 
@@ -204,31 +185,6 @@ __device__ __forceinline__ uint32_t umulhi(uint32_t a, uint32_t b)
 __device__ __forceinline__ uint32_t shift_in(uint32_t lo, uint32_t hi, uint32_t m)
 {
     return umad(hi, m, umulhi(lo, m));
-}
-
-// Division by a divisor fixed for the whole launch as a multiply-high, an
-// add and two shifts (Granlund and Montgomery, "Division by invariant
-// integers using multiplication", 1994, Sec. 4): exact for every 32-bit
-// numerator and every divisor >= 1.
-struct FastDiv {
-    uint32_t m, s1, s2;
-};
-
-FastDiv make_fastdiv(uint32_t d)
-{
-    int l = 0;  // ceil(log2 d)
-    while ((1ull << l) < d) ++l;
-    FastDiv f;
-    f.m = static_cast<uint32_t>((((1ull << l) - d) << 32) / d + 1);
-    f.s1 = l > 0 ? 1 : 0;
-    f.s2 = l > 0 ? l - 1 : 0;
-    return f;
-}
-
-__device__ __forceinline__ uint32_t fast_div(uint32_t x, const FastDiv &f)
-{
-    const uint32_t t = __umulhi(f.m, x);
-    return (t + ((x - t) >> f.s1)) >> f.s2;
 }
 
 __device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
@@ -767,9 +723,8 @@ template <typename T> cudaError_t search_bd(const DependentBatch &b, cudaStream_
 cudaError_t launch_dependent_rules(int ctu, const DependentBatch &b, cudaStream_t s)
 {
     if (b.n < 1 || b.n > kMaxDepItems || b.total_ctas <= 0) return cudaErrorInvalidValue;
-    const int grid = (b.total_ctas + kRulesCtus - 1) / kRulesCtus;
     auto kern = ctu == 64 ? k_dep_rules<64> : ctu == 32 ? k_dep_rules<32> : k_dep_rules<16>;
-    return launch_chained(kern, dim3(grid), dim3(32 * kRulesCtus), 0, s, b);
+    return launch_chained(kern, dim3(b.total_ctas), dim3(kRulesThreads), 0, s, b);
 }
 
 cudaError_t launch_dependent_search(int bit_depth, const DependentBatch &b, cudaStream_t s)

@@ -253,8 +253,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int R = b.R, K = 2 * R + 1;
-    int ii = 0;  // the frame of this CTA
-    while (ii + 1 < b.n && static_cast<int>(blockIdx.x) >= b.item[ii + 1].cta_begin) ++ii;
+    const int ii = dev::item_of_cta(b.item, b.n);  // the frame of this CTA
     const FullSearchItem &a = b.item[ii];
     const int local = blockIdx.x - a.cta_begin;
     // this CTA: warp tiles wt0 .. wt1-1 of one CTU, over one staged window
