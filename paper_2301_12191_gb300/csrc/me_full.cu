@@ -239,7 +239,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
     dev::chain_entry();
 
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    uint8_t *const sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    // 128-byte aligned base by pointer arithmetic on the shared array (the
+    // compiler keeps every derived pointer in the shared window)
+    uint8_t *const sm = smem_raw + ((128u - (dev::smem_addr(smem_raw) & 127u)) & 127u);
     uint32_t *const E = reinterpret_cast<uint32_t *>(sm);             // box_h rows x P4 words
     T *const stage = reinterpret_cast<T *>(sm + b.stage_off);         // box_h rows x P4 samples, inside E
     T *const curs = reinterpret_cast<T *>(sm + b.e_bytes);            // CTU x CTU samples
