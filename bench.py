@@ -34,7 +34,7 @@ from paper_2301_12191_gb300 import synth  # noqa: E402
 WORKLOADS = {
     # 1080p source pair -> 1080p / 720p / 540p / 360p rungs; 360p reference
     "ladder1080": dict(source=(1920, 1080), rungs=[(1920, 1080), (1280, 720), (960, 540), (640, 360)], ref=3,
-                       bit_depth=8, R=32, r=4, qp=27, ctu=64),
+                       bit_depth=8, R=32, r=4, qp=27, ctu=64, multi_qps=[22, 32, 37]),
     # 8 ladders x 5 consecutive frames (4 pairs each) of 1080p, one batched graph per step
     "batch8x5": dict(mode="batch", ladders=8, frames=5, source=(1920, 1080),
                      rungs=[(1920, 1080), (1280, 720), (960, 540), (640, 360)], ref=3, bit_depth=8, R=32, r=4,
@@ -321,6 +321,41 @@ def run_ours(args, wl):
     replicas.barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
 
+    # intra-resolution multi-QP sharing: the decisions of every rung at three
+    # more QPs from the resident analysis (one launch per rung), per frame
+    multi_qp = None
+    if wl.get("multi_qps"):
+        qps = wl["multi_qps"]
+        outs = {}
+        keep = []
+        for i in range(n_rungs):
+            dims, (c8, r8) = lad.grid(i)
+            row = []
+            for _ in qps:
+                o = L.QpDecisions()
+                for d, (c, r) in enumerate(dims):
+                    for k, dt in (("cost", torch.int32), ("best", torch.int32), ("split", torch.uint8)):
+                        a = torch.empty(c * r, dtype=dt, device=dev)
+                        keep.append(a)
+                        getattr(o, k)[d] = a.data_ptr()
+                for k, dt in (("leaf_depth", torch.uint8), ("leaf_mvx", torch.int16), ("leaf_mvy", torch.int16)):
+                    a = torch.empty(c8 * r8, dtype=dt, device=dev)
+                    keep.append(a)
+                    setattr(o, k, a.data_ptr())
+                row.append(o)
+            outs[i] = row
+        sh = torch.cuda.current_stream().cuda_stream
+
+        def step_qps(i):
+            step_multi(i)
+            for r in range(n_rungs):
+                L.ladder_decide_qps(lad.handle, r, 0, qps, outs[r], sh)
+
+        ms_qps = max_over_ranks(timed(step_qps, K, W))
+        multi_qp = {"qps": [qp] + list(qps), "master_qp": qp, "launches_per_step": n_rungs,
+                    "ms_per_step": ms_qps / K, "extra_ms_per_step": (ms_qps - ms_multi) / K,
+                    "ladder_frames_qps_per_s": world * K * (1 + len(qps)) / (ms_qps * 1e-3)}
+
     props = torch.cuda.get_device_properties(dev)
     clocks = clk.summary()
     sm_max = clocks.get("sm_max_mhz") or 2070.0
@@ -375,6 +410,7 @@ def run_ours(args, wl):
         },
         "multires_speedup_vs_independent": (ms_indep / indep_steps) / (ms_multi / K),
         "e2e": {"value": world * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "multi_qp": multi_qp,
         "gpu_launches": int(gpu_launches),
         "kernels": {k: {"launches": n, "ms_total": ms, "share": ms / max(1e-9, sum(v[1] for v in stats.values()))}
                     for k, (n, ms) in stats.items()},

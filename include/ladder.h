@@ -235,6 +235,34 @@ LADDER_API ladder_status analyze_independent(ladder_t *ladder, int rung, int fra
 LADDER_API ladder_status fetch_decisions(ladder_t *ladder, int rung, int frame_id, ladder_decisions *out,
                               void *cuda_stream);
 
+/* Decisions of one analysed rung at further QPs (intra-resolution analysis
+ * sharing, Sec. 4.2: the encodes of one resolution at several QPs share one
+ * analysis, with the median QP as the master encode).  The rung's resident
+ * motion search and its SATDs at the chosen vectors do not depend on the QP
+ * and are shared; for each qps[k] the cost J = SATD + ((lambdaQ16[qps[k]] *
+ * bits + 2^15) >> 16), the bottom-up split and the leaf maps are recomputed
+ * into out[k].  A dependent rung keeps its rules (derived from the reference
+ * decisions of the frame's own analysis).  So out[k] equals what analysing
+ * the rung at qps[k] gives for cost, best, split and the leaf maps, given
+ * the reference analysed at the master QP.
+ *   out[k]: caller-owned DEVICE arrays laid out as the same fields of
+ *   ladder_decisions (sizes per ladder_grid); every member for depths
+ *   0..dmax must be set.
+ * n in 1..LADDER_MAX_QPS, QPs in 0..51 (LADDER_E_INVAL); LADDER_E_STATE if
+ * the rung of frame_id has not been analysed.  Asynchronous on
+ * `cuda_stream` (one launch); the frame's analysis must be ordered before it
+ * on that stream. */
+#define LADDER_MAX_QPS 8
+typedef struct {
+    int32_t *cost[LADDER_MAX_DEPTHS];
+    int32_t *best[LADDER_MAX_DEPTHS];
+    uint8_t *split[LADDER_MAX_DEPTHS];
+    uint8_t *leaf_depth;
+    int16_t *leaf_mvx, *leaf_mvy;
+} ladder_qp_decisions;
+LADDER_API ladder_status ladder_decide_qps(ladder_t *ladder, int rung, int frame_id, int n, const int *qps,
+                                           const ladder_qp_decisions *out, void *cuda_stream);
+
 /* Grid of a rung: dims[2d], dims[2d+1] = cols_d, rows_d for d = 0..dmax, then
  * dims[2(dmax+1)], dims[2(dmax+1)+1] = 8x8 cols, rows; returns dmax in *n_depths - 1.
  * `dims` must hold 2 * LADDER_MAX_DEPTHS + 2 ints. */
@@ -260,7 +288,7 @@ LADDER_API const char *ladder_last_error(const ladder_t *ladder);
  * 0 full search, 1 SATD/cost/split of an independent rung, 2 refinement
  * search of dependent rungs, 3 key initialisation, 4 dependent constraint
  * derivation (rules, centres, task lists), 5 SATD/cost/split of dependent
- * rungs. */
+ * rungs, 6 cost/split at further QPs (ladder_decide_qps). */
 LADDER_API ladder_status ladder_profile_enable(ladder_t *ladder, int enable);
 
 /* Reads the launch count and the summed event time (ms; 0 when timing was

@@ -299,13 +299,87 @@ struct DecideIO {
 // Index of CU (d, local raster li) in the per-CTU key layout.
 __device__ __forceinline__ int key_index(int d, int li) { return key_offset(d) + li; }
 
-// The decision step for one CTU, given flags / vectors / SADs in `st`
-// (satd[] must be zero).  All threads of the CTA take part.
-//   SATD   -- Sec. 5.4.1 SATD equation; Sec. 5.4.2 satd8 / satd_8x4 listings
+// Cost, bottom-up split and leaf maps of one CTU at lambda lam (Q16), from
+// st: flags, vectors and, for evaluated CUs, SADs and SATDs.  All threads
+// of the CTA take part.  Writes cost, best and split per CU and the leaf
+// maps; `all` also writes the vectors, SADs, SATDs and evaluated flags.
 //   cost   -- J = SATD + ((lambdaQ16[qp] * bits + 2^15) >> 16), bits = se()
 //             lengths of the quarter-pel components (predictor (0,0))
 //   split  -- Sec. 2.1: split iff it may and (it is not a leaf candidate or
 //             the children's best sum is strictly lower), or it must
+template <int CTU>
+__device__ void ctu_split(CtuState<CTU> &st, int lam, const RungGeom &g, const DevDecisions &out, bool all, int x0,
+                          int y0)
+{
+    using C = Ctu<CTU>;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int d = C::DMAX; d >= 0; --d) {
+        const int n = 1 << d, S = CTU >> d;
+        for (int li = tid; li < n * n; li += nthr) {
+            const int i = key_index(d, li);
+            const uint8_t f = st.flags[i];
+            if (!(f & kPresent)) continue;
+            const bool ev = f & kRuleEvaluated;
+            int32_t J = INT32_MAX;
+            if (ev) {
+                const long long bits = se_bits(4 * st.mvx[i]) + se_bits(4 * st.mvy[i]);
+                J = st.satd[i] + static_cast<int32_t>((static_cast<long long>(lam) * bits + 32768) >> 16);
+            }
+            int32_t best = J;
+            uint8_t split = 0;
+            if (d < C::DMAX) {
+                const bool can_split = f & kRuleCanSplit;
+                int32_t children = 0;
+                if (can_split) {
+                    const int cxl = li % n, cyl = li / n;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int ci = key_index(d + 1, (2 * cyl + (q >> 1)) * (2 * n) + 2 * cxl + (q & 1));
+                        if (st.flags[ci] & kPresent) children += st.best[ci];
+                    }
+                }
+                split = can_split && (!ev || children < J);
+                best = !(f & kRuleReachable) ? INT32_MAX : (split ? children : J);
+            }
+            st.best[i] = best;
+            st.split[i] = split;
+            const long gi = static_cast<long>(y0 / S + li / n) * g.cols[d] + x0 / S + li % n;
+            if (all) {
+                out.mvx[d][gi] = st.mvx[i];
+                out.mvy[d][gi] = st.mvy[i];
+                out.sad[d][gi] = st.sad[i];
+                out.satd[d][gi] = ev ? st.satd[i] : INT32_MAX;
+                out.evaluated[d][gi] = ev ? 1 : 0;
+            }
+            out.cost[d][gi] = J;
+            out.best[d][gi] = best;
+            out.split[d][gi] = split;
+        }
+        __syncthreads();
+    }
+
+    for (int b = tid; b < C::NB8; b += nthr) {
+        const int bx = b % C::N8, by = b / C::N8;
+        const int px = x0 + 8 * bx, py = y0 + 8 * by;
+        if (px >= g.W8 || py >= g.H8) continue;
+        int d = 0, i = 0;
+        for (;;) {
+            const int S = CTU >> d;
+            i = key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S);
+            if (d == C::DMAX || !st.split[i]) break;
+            ++d;
+        }
+        const long li = static_cast<long>(py / 8) * g.cols8 + px / 8;
+        out.leaf_depth[li] = static_cast<uint8_t>(d);
+        out.leaf_mvx[li] = st.mvx[i];
+        out.leaf_mvy[li] = st.mvy[i];
+    }
+}
+
+// The decision step for one CTU, given flags / vectors / SADs in `st`
+// (satd[] must be zero): SATD at the chosen vectors, then ctu_split.  All
+// threads of the CTA take part.
+//   SATD   -- Sec. 5.4.1 SATD equation; Sec. 5.4.2 satd8 / satd_8x4 listings
 template <typename T, int CTU>
 __device__ void ctu_decide(CtuState<CTU> &st, const DecideIO &io, int x0, int y0)
 {
@@ -360,66 +434,7 @@ __device__ void ctu_decide(CtuState<CTU> &st, const DecideIO &io, int x0, int y0
     }
     __syncthreads();
 
-    const int lam = io.lambda_q16[io.qp];
-    for (int d = C::DMAX; d >= 0; --d) {
-        const int n = 1 << d, S = CTU >> d;
-        for (int li = tid; li < n * n; li += nthr) {
-            const int i = key_index(d, li);
-            const uint8_t f = st.flags[i];
-            if (!(f & kPresent)) continue;
-            const bool ev = f & kRuleEvaluated;
-            int32_t J = INT32_MAX;
-            if (ev) {
-                const long long bits = se_bits(4 * st.mvx[i]) + se_bits(4 * st.mvy[i]);
-                J = st.satd[i] + static_cast<int32_t>((static_cast<long long>(lam) * bits + 32768) >> 16);
-            }
-            int32_t best = J;
-            uint8_t split = 0;
-            if (d < C::DMAX) {
-                const bool can_split = f & kRuleCanSplit;
-                int32_t children = 0;
-                if (can_split) {
-                    const int cxl = li % n, cyl = li / n;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int ci = key_index(d + 1, (2 * cyl + (q >> 1)) * (2 * n) + 2 * cxl + (q & 1));
-                        if (st.flags[ci] & kPresent) children += st.best[ci];
-                    }
-                }
-                split = can_split && (!ev || children < J);
-                best = !(f & kRuleReachable) ? INT32_MAX : (split ? children : J);
-            }
-            st.best[i] = best;
-            st.split[i] = split;
-            const long gi = static_cast<long>(y0 / S + li / n) * g.cols[d] + x0 / S + li % n;
-            io.out.mvx[d][gi] = st.mvx[i];
-            io.out.mvy[d][gi] = st.mvy[i];
-            io.out.sad[d][gi] = st.sad[i];
-            io.out.satd[d][gi] = ev ? st.satd[i] : INT32_MAX;
-            io.out.cost[d][gi] = J;
-            io.out.best[d][gi] = best;
-            io.out.split[d][gi] = split;
-            io.out.evaluated[d][gi] = ev ? 1 : 0;
-        }
-        __syncthreads();
-    }
-
-    for (int b = tid; b < C::NB8; b += nthr) {
-        const int bx = b % C::N8, by = b / C::N8;
-        const int px = x0 + 8 * bx, py = y0 + 8 * by;
-        if (px >= g.W8 || py >= g.H8) continue;
-        int d = 0, i = 0;
-        for (;;) {
-            const int S = CTU >> d;
-            i = key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S);
-            if (d == C::DMAX || !st.split[i]) break;
-            ++d;
-        }
-        const long li = static_cast<long>(py / 8) * g.cols8 + px / 8;
-        io.out.leaf_depth[li] = static_cast<uint8_t>(d);
-        io.out.leaf_mvx[li] = st.mvx[i];
-        io.out.leaf_mvy[li] = st.mvy[i];
-    }
+    ctu_split<CTU>(st, io.lambda_q16[io.qp], *io.g, io.out, true, x0, y0);
 }
 
 // ---- dependent-mode constraint derivation --------------------------------

@@ -63,6 +63,44 @@ __global__ void __launch_bounds__(kThreads) k_decide(const __grid_constant__ Dec
     dev::ctu_decide<T, CTU>(st, io, x0, y0);
 }
 
+// Further-QP decisions (intra-resolution sharing, Sec. 4.2): CTU blockIdx.x
+// of the rung at QP b.qp[blockIdx.y], from the resident vectors and SATDs.
+template <int CTU>
+__global__ void __launch_bounds__(kThreads) k_decide_qps(const __grid_constant__ QpBatch b)
+{
+    dev::chain_entry();
+    using C = dev::Ctu<CTU>;
+    __shared__ dev::CtuState<CTU> st;
+    const RungGeom &g = b.g;
+    const int ctu_idx = blockIdx.x;
+    const int x0 = (ctu_idx % g.ctu_cols) * CTU, y0 = (ctu_idx / g.ctu_cols) * CTU;
+    const uint8_t *dep_flags = reinterpret_cast<const uint8_t *>(b.block + b.off.dep_flags) +
+                               static_cast<long>(ctu_idx) * C::NKEY;
+    for (int i = threadIdx.x; i < C::NKEY; i += kThreads) {
+        int d = 0;
+        while (d < C::DMAX && i >= key_offset(d + 1)) ++d;
+        const int li = i - key_offset(d), n = 1 << d, S = CTU >> d;
+        const int fx = x0 / S + li % n, fy = y0 / S + li / n;
+        const bool present = fx * S < g.W8 && fy * S < g.H8;
+        uint8_t flags = 0;
+        if (b.dependent) {
+            flags = __ldcg(dep_flags + i);
+        } else if (present) {
+            const bool inside = fx * S + S <= g.W8 && fy * S + S <= g.H8;
+            flags = dev::kPresent | kRuleReachable | (inside ? kRuleEvaluated : 0) | (d < C::DMAX ? kRuleCanSplit : 0);
+        }
+        st.flags[i] = flags;
+        if (flags & dev::kPresent) {
+            const long gi = static_cast<long>(fy) * g.cols[d] + fx;
+            st.mvx[i] = __ldcg(reinterpret_cast<const int16_t *>(b.block + b.off.mvx[d]) + gi);
+            st.mvy[i] = __ldcg(reinterpret_cast<const int16_t *>(b.block + b.off.mvy[d]) + gi);
+            st.satd[i] = __ldcg(reinterpret_cast<const int32_t *>(b.block + b.off.satd[d]) + gi);
+        }
+    }
+    __syncthreads();
+    dev::ctu_split<CTU>(st, c_lambda_q16[b.qp[blockIdx.y]], g, b.out[blockIdx.y], false, x0, y0);
+}
+
 __global__ void k_fill_keys(const __grid_constant__ FillBatch b)
 {
     dev::chain_entry();
@@ -91,6 +129,14 @@ cudaError_t launch_decide(int bit_depth, int ctu, const DecideBatch &b, cudaStre
     if (ctu == 64) return decide_t<uint16_t, 64>(b, s);
     if (ctu == 32) return decide_t<uint16_t, 32>(b, s);
     return decide_t<uint16_t, 16>(b, s);
+}
+
+cudaError_t launch_decide_qps(int ctu, const QpBatch &b, cudaStream_t s)
+{
+    if (b.n_qps < 1 || b.n_qps > kMaxQps) return cudaErrorInvalidValue;
+    const dim3 grid(b.g.ctu_cols * b.g.ctu_rows, b.n_qps);
+    auto kern = ctu == 64 ? k_decide_qps<64> : ctu == 32 ? k_decide_qps<32> : k_decide_qps<16>;
+    return launch_chained(kern, grid, dim3(kThreads), 0, s, b);
 }
 
 cudaError_t launch_fill_keys(const FillBatch &b, cudaStream_t s)

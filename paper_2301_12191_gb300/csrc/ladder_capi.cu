@@ -34,7 +34,8 @@ struct Slot {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-constexpr int kKinds = 6;  // full search, decide, dependent search, fill keys, dependent rules, dependent decide
+constexpr int kKinds = 7;  // full search, decide, dependent search, fill keys, dependent rules, dependent decide,
+                           // further-QP decisions
 
 struct ProfEvent {
     int kind;
@@ -832,6 +833,45 @@ ladder_status ladder_sync(ladder_t *l, void *cuda_stream)
         cudaStreamSynchronize(s);
         return device_status_error(l, status);
     }
+    return LADDER_OK;
+}
+
+ladder_status ladder_decide_qps(ladder_t *l, int rung, int frame_id, int n, const int *qps,
+                                const ladder_qp_decisions *out, void *cuda_stream)
+{
+    if (!l || !qps || !out) return LADDER_E_INVAL;
+    if (rung < 0 || rung >= l->geo.n_rungs) return fail(l, LADDER_E_INVAL, "rung %d out of range", rung);
+    if (n < 1 || n > kMaxQps) return fail(l, LADDER_E_INVAL, "%d QPs (1..%d)", n, kMaxQps);
+    Slot *slot = find_slot(l, frame_id);
+    if (!slot || !slot->rungs[rung].analysed)
+        return fail(l, LADDER_E_STATE, "rung %d of frame %d has not been analysed", rung, frame_id);
+    const RungGeom &g = l->info[rung].g;
+    QpBatch b{};
+    b.n_qps = n;
+    b.g = g;
+    b.off = l->info[rung].off;
+    b.block = slot->rungs[rung].block;
+    b.dependent = slot->rungs[rung].analysed == 2;
+    for (int k = 0; k < n; ++k) {
+        if (qps[k] < 0 || qps[k] > 51) return fail(l, LADDER_E_INVAL, "qp %d outside 0..51", qps[k]);
+        b.qp[k] = qps[k];
+        const ladder_qp_decisions &o = out[k];
+        if (!o.leaf_depth || !o.leaf_mvx || !o.leaf_mvy)
+            return fail(l, LADDER_E_INVAL, "qp %d: leaf arrays missing", qps[k]);
+        for (int d = 0; d <= g.dmax; ++d) {
+            if (!o.cost[d] || !o.best[d] || !o.split[d])
+                return fail(l, LADDER_E_INVAL, "qp %d: depth %d arrays missing", qps[k], d);
+            b.out[k].cost[d] = o.cost[d];
+            b.out[k].best[d] = o.best[d];
+            b.out[k].split[d] = o.split[d];
+        }
+        b.out[k].leaf_depth = o.leaf_depth;
+        b.out[k].leaf_mvx = o.leaf_mvx;
+        b.out[k].leaf_mvy = o.leaf_mvy;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const cudaError_t e = traced(l, 6, s, [&] { return launch_decide_qps(l->geo.ctu_size, b, s); });
+    if (e != cudaSuccess) return cuda_fail(l, e, "further-QP decisions");
     return LADDER_OK;
 }
 

@@ -295,6 +295,20 @@ cudaError_t launch_dependent_rules(int ctu, const DependentBatch &b, cudaStream_
 cudaError_t launch_dependent_search(int bit_depth, const DependentBatch &b, cudaStream_t s);
 cudaError_t launch_dependent_decide(int bit_depth, int ctu, const DependentBatch &b, cudaStream_t s);
 
+// Decisions of one analysed rung at further QPs: one CTA per (CTU, QP),
+// the resident vectors and SATDs, cost / split / leaf maps per QP.
+constexpr int kMaxQps = 8;
+struct QpBatch {
+    int n_qps;
+    int qp[kMaxQps];
+    RungGeom g;
+    DecOffsets off;
+    const char *block;       // the (slot, rung) decision block
+    int dependent;           // 1: rule flags of the dependent analysis; 0: flags of the geometry
+    DevDecisions out[kMaxQps];  // cost, best, split and leaf maps set
+};
+cudaError_t launch_decide_qps(int ctu, const QpBatch &b, cudaStream_t s);
+
 // Fills the keys of every block of a batch with ~0 (key initialisation).
 struct FillItem {
     unsigned long long *keys;

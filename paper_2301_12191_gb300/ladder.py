@@ -50,6 +50,12 @@ class Decisions(ctypes.Structure):
                 ("leaf_depth", ctypes.c_void_p), ("leaf_mvx", ctypes.c_void_p), ("leaf_mvy", ctypes.c_void_p)]
 
 
+class QpDecisions(ctypes.Structure):
+    _fields_ = [("cost", ctypes.c_void_p * MAX_DEPTHS), ("best", ctypes.c_void_p * MAX_DEPTHS),
+                ("split", ctypes.c_void_p * MAX_DEPTHS),
+                ("leaf_depth", ctypes.c_void_p), ("leaf_mvx", ctypes.c_void_p), ("leaf_mvy", ctypes.c_void_p)]
+
+
 class Job(ctypes.Structure):
     _fields_ = [("frame_id", ctypes.c_int), ("rung", ctypes.c_int), ("kind", ctypes.c_int), ("qp", ctypes.c_int),
                 ("cur", ctypes.c_void_p), ("ref", ctypes.c_void_p), ("pitch_bytes", ctypes.c_long)]
@@ -83,6 +89,8 @@ SIGNATURES = [
                                            ctypes.c_void_p, ctypes.c_long, ctypes.c_int, ctypes.c_void_p]),
     ("fetch_decisions", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Decisions),
                                        ctypes.c_void_p]),
+    ("ladder_decide_qps", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(QpDecisions), ctypes.c_void_p]),
     ("ladder_grid", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int)]),
     ("ladder_release_frame", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -101,7 +109,7 @@ SIGNATURES = [
     ("ladder_get_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
 ]
 
-KERNEL_KINDS = ("full_search", "decide", "dependent", "fill_keys", "dep_rules", "dep_decide")
+KERNEL_KINDS = ("full_search", "decide", "dependent", "fill_keys", "dep_rules", "dep_decide", "decide_qps")
 TUNE_KNOBS = {"fs_band": 0, "dep_band": 1, "dep_range": 2, "dep_ctas_per_sm": 3, "fs_group": 4, "fs_fuse": 5}
 
 _lib = None
@@ -170,6 +178,13 @@ def analyze_independent(h, rung, frame_id, cur_ptr, ref_ptr, pitch_bytes, qp, st
 
 def fetch_decisions(h, rung, frame_id, decisions: Decisions, stream=0):
     return _call(h, "fetch_decisions", h, rung, frame_id, ctypes.byref(decisions), stream)
+
+
+def ladder_decide_qps(h, rung, frame_id, qps, outs, stream=0):
+    n = len(qps)
+    arr = (ctypes.c_int * n)(*qps)
+    out = (QpDecisions * n)(*outs)
+    _call(h, "ladder_decide_qps", h, rung, frame_id, n, arr, out, stream)
 
 
 def ladder_grid(h, rung):
@@ -394,6 +409,40 @@ class Ladder:
     def kernel_stats(self, reset: bool = False) -> dict:
         """{kind: (launches, summed event ms)} since the last reset."""
         return {name: ladder_profile_read(self.handle, k, reset) for k, name in enumerate(KERNEL_KINDS)}
+
+    def decide_qps(self, rung, frame_id, qps, stream=None) -> dict:
+        """Cost, best, split and leaf maps of (rung, frame) at each QP of
+        `qps` from the resident analysis (intra-resolution multi-QP sharing),
+        as {qp: {field: numpy arrays laid out like fetch()}}."""
+        import torch
+
+        dims, (c8, r8) = self.grid(rung)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        tensors, outs = [], []
+        for _ in qps:
+            t = {"cost": [], "best": [], "split": []}
+            o = QpDecisions()
+            for d, (c, r) in enumerate(dims):
+                for k, dt in (("cost", torch.int32), ("best", torch.int32), ("split", torch.uint8)):
+                    a = torch.empty(c * r, dtype=dt, device=dev)
+                    t[k].append(a)
+                    getattr(o, k)[d] = a.data_ptr()
+            for k, dt in (("leaf_depth", torch.uint8), ("leaf_mvx", torch.int16), ("leaf_mvy", torch.int16)):
+                a = torch.empty(c8 * r8, dtype=dt, device=dev)
+                t[k] = a
+                setattr(o, k, a.data_ptr())
+            tensors.append(t)
+            outs.append(o)
+        s = _stream_handle(stream)
+        ladder_decide_qps(self.handle, rung, frame_id, list(qps), outs, s)
+        if stream is None:
+            torch.cuda.current_stream().synchronize()
+        else:
+            stream.synchronize()
+        res = {}
+        for q, t in zip(qps, tensors):
+            res[q] = {k: ([a.cpu().numpy() for a in v] if isinstance(v, list) else v.cpu().numpy()) for k, v in t.items()}
+        return res
 
     def fetch(self, rung, frame_id, stream=None) -> dict:
         """Decisions of (rung, frame) as numpy arrays, laid out like the
