@@ -44,6 +44,13 @@ WORKLOADS = {
                  rungs=[(3840, 2160), (2560, 1440), (1920, 1080), (1280, 720), (960, 540), (640, 360)], ref=5,
                  bit_depth=10, R=64, r=8, qps=[22, 27, 32, 37], sigmas=[8], global_range=8 * 3840 // 416,
                  patch_range=12 * 3840 // 416, ctu=64),
+    # uhd8 with the cascaded reference chain of the proposed multi-encoding
+    # scheme: 360p -> 720p -> 1440p and 360p -> 540p -> 1080p -> 2160p
+    "uhd8chain": dict(mode="batch", ladders=8, frames=2, source=(3840, 2160),
+                      rungs=[(3840, 2160), (2560, 1440), (1920, 1080), (1280, 720), (960, 540), (640, 360)], ref=5,
+                      parents=[2, 3, 4, 5, 5, -1],
+                      bit_depth=10, R=64, r=8, qps=[22, 27, 32, 37], sigmas=[8], global_range=8 * 3840 // 416,
+                      patch_range=12 * 3840 // 416, ctu=64),
     # serving: Poisson requests (200/s) for single rungs of 2160p->360p ladders,
     # 8- and 10-bit mixed, continuous batching on several streams
     "serve": dict(mode="serve", rate=200.0, seconds=10.0, source=(3840, 2160),
@@ -141,16 +148,25 @@ class ClockSampler:
 
 # ------------------------------------------------------------ oracle leg --
 def oracle_ladder_frame(wl, pairs, threads):
+    """One ladder frame by the oracle: the reference rung, then every other
+    rung as a dependent of its parent (the reference rung, or the parents of
+    a cascaded chain), parents first."""
     import oracle
     ref_i = wl["ref"]
+    qp = wl.get("qp", 27)
+    parents = wl.get("parents") or [-1 if i == ref_i else ref_i for i in range(len(pairs))]
+    out = {}
     w, h, c, f = pairs[ref_i]
-    ref_out = oracle.analyze(c, f, qp=wl["qp"], search_range=wl["R"], ctu=wl["ctu"], threads=threads)
-    for i, (w2, h2, c2, f2) in enumerate(pairs):
-        if i == ref_i:
-            continue
-        oracle.analyze(c2, f2, qp=wl["qp"], search_range=wl["r"], ctu=wl["ctu"], threads=threads,
-                       dep={"ref_size": (w, h), "leaf_depth": ref_out["leaf_depth"],
-                            "leaf_mvx": ref_out["leaf_mvx"], "leaf_mvy": ref_out["leaf_mvy"]})
+    out[ref_i] = oracle.analyze(c, f, qp=qp, search_range=wl["R"], ctu=wl["ctu"], threads=threads)
+    while len(out) < len(pairs):
+        for i, (w2, h2, c2, f2) in enumerate(pairs):
+            p = parents[i]
+            if i in out or p not in out:
+                continue
+            pw, ph = pairs[p][0], pairs[p][1]
+            out[i] = oracle.analyze(c2, f2, qp=qp, search_range=wl["r"], ctu=wl["ctu"], threads=threads,
+                                    dep={"ref_size": (pw, ph), "leaf_depth": out[p]["leaf_depth"],
+                                         "leaf_mvx": out[p]["leaf_mvx"], "leaf_mvy": out[p]["leaf_mvy"]})
 
 
 def cpu_baseline(wl, frames, budget_s=10.0):
@@ -499,6 +515,8 @@ def run_batch(args, wl):
              for k, (l, t, qp) in enumerate(reqs)]
     lad = L.Ladder(sizes, ref_i, bit_depth=wl["bit_depth"], ctu_size=wl["ctu"], search_range=wl["R"],
                    refine_range=wl["r"], max_frames=2 * n)
+    if wl.get("parents"):
+        lad.set_parents(wl["parents"])  # cascaded reference chain
     items_ind = [(n + k, qp, pl) for (k, qp, pl) in items]
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):

@@ -235,6 +235,18 @@ LADDER_API ladder_status analyze_independent(ladder_t *ladder, int rung, int fra
 LADDER_API ladder_status fetch_decisions(ladder_t *ladder, int rung, int frame_id, ladder_decisions *out,
                               void *cuda_stream);
 
+/* Cascaded reference chain (Sec. 6.5, the proposed multi-encoding scheme:
+ * the refined decisions of one resolution tier are the reference of the
+ * next, e.g. 540p -> 1080p -> 2160p).  parent[r] is the rung whose decisions
+ * the dependent analysis of rung r refines (its co-located leaf depths and
+ * vectors); parent[ref_rung] = -1, and following the parents must lead every
+ * rung to the reference rung (no cycles): LADDER_E_INVAL otherwise.  Default
+ * at init: the reference rung is every rung's parent.  A dependent analysis
+ * needs its parent's analysis of the same frame, resident or in the same
+ * call (the library then analyses the rungs tier by tier, parents first):
+ * LADDER_E_NOREF otherwise.  Applies to later calls. */
+LADDER_API ladder_status ladder_set_parents(ladder_t *ladder, const int *parent);
+
 /* Decisions of one analysed rung at further QPs (intra-resolution analysis
  * sharing, Sec. 4.2: the encodes of one resolution at several QPs share one
  * analysis, with the median QP as the master encode).  The rung's resident

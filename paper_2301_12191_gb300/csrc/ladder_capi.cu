@@ -56,6 +56,8 @@ struct ladder {
     // dependent launches share the task lists: each waits for the one
     // before it (on whatever stream that ran)
     cudaEvent_t dep_done = nullptr;
+    std::vector<int> parent;  // per rung: the rung whose decisions a dependent analysis refines (-1: reference)
+    std::vector<int> tier;    // per rung: steps from the reference rung along the parents
     bool dep_recorded = false;
     cudaStream_t dep_stream = nullptr;  // stream of the last recorded dependent batch
     // every argmin key is ~0 at rest (searches reset them after use); after a
@@ -368,9 +370,10 @@ ladder_status launch_independent(ladder_t *l, const Job *jobs, int n, cudaStream
     return LADDER_OK;
 }
 
-// Dependent analyses in batched launches of at most kMaxDepItems jobs:
-// counters reset, rules + task lists, search, decisions.
-ladder_status launch_dependents(ladder_t *l, const Job *jobs, int n, cudaStream_t s)
+// Dependent analyses of one tier (no job's parent among them) in batched
+// launches of at most kMaxDepItems jobs: rules + task lists, search,
+// decisions.
+ladder_status launch_dependent_tier(ladder_t *l, const Job *jobs, int n, cudaStream_t s)
 {
     // the task lists are per handle: wait for the previous dependent launch
     // (not inside a graph capture: a captured batch is one ordered stream)
@@ -390,7 +393,6 @@ ladder_status launch_dependents(ladder_t *l, const Job *jobs, int n, cudaStream_
         b.band = l->tune_dep_band;
         b.ctas_per_sm = l->tune_dep_ctas;
         b.satd_mode = l->geo.satd_mode;
-        b.ref_rung = l->geo.ref_rung;
         b.depth_lo = l->geo.dep_depth_lo;
         b.depth_hi = l->geo.dep_depth_hi;
         b.use_ref_mv = l->geo.dep_use_ref_mv;
@@ -408,8 +410,9 @@ ladder_status launch_dependents(ladder_t *l, const Job *jobs, int n, cudaStream_
         for (int k = 0; k < m; ++k) {
             const Job &jb = jobs[j0 + k];
             const RungGeom &g = l->info[jb.rung].g;
+            const int par = l->parent[jb.rung];
             b.item[k] = DependentItem{jb.cur, jb.ref, jb.pitch, jb.slot->rungs[jb.rung].block,
-                                      jb.slot->rungs[l->geo.ref_rung].block, jb.rung, jb.qp, total};
+                                      jb.slot->rungs[par].block, jb.rung, par, jb.qp, total};
             total += g.ctu_cols * g.ctu_rows;
         }
         b.total_ctas = total;
@@ -438,6 +441,26 @@ ladder_status launch_dependents(ladder_t *l, const Job *jobs, int n, cudaStream_
         l->dep_stream = s;
     }
     for (int k = 0; k < n; ++k) jobs[k].slot->rungs[jobs[k].rung].analysed = 2;
+    return LADDER_OK;
+}
+
+// Dependent analyses, tier by tier along the parents (a cascaded chain
+// refines a dependent rung's decisions at the next tier): each tier's
+// launches follow the previous tier's on the stream.
+ladder_status launch_dependents(ladder_t *l, const Job *jobs, int n, cudaStream_t s)
+{
+    int top = 0;
+    for (int k = 0; k < n; ++k) top = std::max(top, l->tier[jobs[k].rung]);
+    if (top <= 1) return launch_dependent_tier(l, jobs, n, s);
+    std::vector<Job> tier_jobs;
+    for (int t = 1; t <= top; ++t) {
+        tier_jobs.clear();
+        for (int k = 0; k < n; ++k)
+            if (l->tier[jobs[k].rung] == t) tier_jobs.push_back(jobs[k]);
+        if (tier_jobs.empty()) continue;
+        const ladder_status st = launch_dependent_tier(l, tier_jobs.data(), static_cast<int>(tier_jobs.size()), s);
+        if (st != LADDER_OK) return st;
+    }
     return LADDER_OK;
 }
 
@@ -519,6 +542,10 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
         }
     }
     char *p = base + fixed;
+    l->parent.assign(geometry->n_rungs, geometry->ref_rung);
+    l->parent[geometry->ref_rung] = -1;
+    l->tier.assign(geometry->n_rungs, 1);
+    l->tier[geometry->ref_rung] = 0;
     l->slots.resize(geometry->max_frames);
     for (auto &sl : l->slots) {
         sl.used = 0;
@@ -610,6 +637,13 @@ ladder_status analyze_dependents(ladder_t *l, int frame_id, int n, const int *ru
     Slot *slot = find_slot(l, frame_id);
     if (!slot || !slot->ref_done)
         return fail(l, LADDER_E_NOREF, "frame %d has no reference analysis", frame_id);
+    // each rung's parent: analysed for this frame, or in this call
+    for (int k = 0; k < n; ++k) {
+        const int p = l->parent[rungs[k]];
+        bool ok = slot->rungs[p].analysed != 0;
+        for (int j = 0; j < n && !ok; ++j) ok = rungs[j] == p;
+        if (!ok) return fail(l, LADDER_E_NOREF, "rung %d: its parent rung %d has no analysis of frame %d", rungs[k], p, frame_id);
+    }
     std::vector<Job> jobs;
     for (int k = 0; k < n; ++k) jobs.push_back(Job{slot, rungs[k], cur[k], ref[k], pitch_bytes[k], qp});
     return launch_dependents(l, jobs.data(), n, static_cast<cudaStream_t>(cuda_stream));
@@ -725,15 +759,16 @@ ladder_status ladder_analyze_jobs(ladder_t *l, const ladder_job *jobs, int n, vo
             new_frames.push_back(jobs[k].frame_id);
     if (static_cast<int>(new_frames.size()) > free_slots)
         return fail(l, LADDER_E_BUSY, "jobs need %zu free frame slots, %d free", new_frames.size(), free_slots);
-    // a dependent needs its frame's reference: already resident, or a
-    // reference-rung job in this same call
+    // a dependent needs its parent rung's decisions of its frame: already
+    // resident, or a job of this same call
     for (int k = 0; k < n; ++k) {
         if (jobs[k].kind != 1) continue;
+        const int p = l->parent[jobs[k].rung];
         Slot *sl = find_slot(l, jobs[k].frame_id);
-        bool ok = sl && sl->ref_done;
-        for (int j = 0; j < n && !ok; ++j)
-            ok = jobs[j].kind == 0 && jobs[j].rung == l->geo.ref_rung && jobs[j].frame_id == jobs[k].frame_id;
-        if (!ok) return fail(l, LADDER_E_NOREF, "job %d: frame %d has no reference analysis", k, jobs[k].frame_id);
+        bool ok = sl && sl->rungs[p].analysed != 0;
+        for (int j = 0; j < n && !ok; ++j) ok = jobs[j].rung == p && jobs[j].frame_id == jobs[k].frame_id;
+        if (!ok)
+            return fail(l, LADDER_E_NOREF, "job %d: parent rung %d has no analysis of frame %d", k, p, jobs[k].frame_id);
     }
     for (int k = 0; k < n; ++k) {
         const ladder_job &jb = jobs[k];
@@ -833,6 +868,34 @@ ladder_status ladder_sync(ladder_t *l, void *cuda_stream)
         cudaStreamSynchronize(s);
         return device_status_error(l, status);
     }
+    return LADDER_OK;
+}
+
+ladder_status ladder_set_parents(ladder_t *l, const int *parent)
+{
+    if (!l || !parent) return LADDER_E_INVAL;
+    const int n = l->geo.n_rungs, rr = l->geo.ref_rung;
+    std::vector<int> tier(n, -1);
+    for (int r = 0; r < n; ++r) {
+        if (r == rr) {
+            if (parent[r] != -1) return fail(l, LADDER_E_INVAL, "the reference rung %d takes parent -1", rr);
+            continue;
+        }
+        if (parent[r] < 0 || parent[r] >= n || parent[r] == r)
+            return fail(l, LADDER_E_INVAL, "rung %d: parent %d", r, parent[r]);
+    }
+    // tiers: steps to the reference rung; a cycle never reaches it
+    for (int r = 0; r < n; ++r) {
+        int t = 0, x = r;
+        while (x != rr && t <= n) {
+            x = parent[x];
+            ++t;
+        }
+        if (t > n) return fail(l, LADDER_E_INVAL, "the parents of rung %d form a cycle", r);
+        tier[r] = t;
+    }
+    l->parent.assign(parent, parent + n);
+    l->tier = tier;
     return LADDER_OK;
 }
 

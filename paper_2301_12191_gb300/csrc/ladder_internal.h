@@ -252,8 +252,9 @@ struct DependentItem {
     const void *cur, *ref;
     long pitch_bytes;
     char *block;             // this (slot, rung) block
-    const char *ref_block;   // the frame's reference-rung block
+    const char *ref_block;   // the frame's block of the parent rung (whose decisions this rung refines)
     int rung;
+    int parent;              // the parent rung
     int qp;
     int cta_begin;           // first CTA of this item in the per-CTU kernels (one CTA per CTU)
 };
@@ -275,7 +276,6 @@ struct DependentBatch {
     int band;               // candidate rows per lane task: 9 or 17
     int ctas_per_sm;        // search grid: CTAs per SM (0: as many as fit)
     int satd_mode;
-    int ref_rung;
     int depth_lo, depth_hi, use_ref_mv;
     int total_ctas;         // CTUs of the batch
     int *status;

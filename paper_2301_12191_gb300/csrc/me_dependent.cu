@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kRulesThreads) k_dep_rules(const __grid_consta
     const int ri = item_of(b);
     const DependentItem &a = b.item[ri];
     const RungInfo &rinf = b.rung[a.rung];
-    const RungInfo &rref = b.rung[b.ref_rung];
+    const RungInfo &rref = b.rung[a.parent];  // the rung whose decisions this one refines
     const RungGeom &g = rinf.g;
     const int ctu_idx = static_cast<int>(blockIdx.x) - a.cta_begin;
     const int x0 = (ctu_idx % g.ctu_cols) * CTU, y0 = (ctu_idx / g.ctu_cols) * CTU;

@@ -89,6 +89,7 @@ SIGNATURES = [
                                            ctypes.c_void_p, ctypes.c_long, ctypes.c_int, ctypes.c_void_p]),
     ("fetch_decisions", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Decisions),
                                        ctypes.c_void_p]),
+    ("ladder_set_parents", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     ("ladder_decide_qps", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(QpDecisions), ctypes.c_void_p]),
     ("ladder_grid", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -409,6 +410,13 @@ class Ladder:
     def kernel_stats(self, reset: bool = False) -> dict:
         """{kind: (launches, summed event ms)} since the last reset."""
         return {name: ladder_profile_read(self.handle, k, reset) for k, name in enumerate(KERNEL_KINDS)}
+
+    def set_parents(self, parent):
+        """parent[r]: the rung whose decisions rung r refines (-1 for the
+        reference rung); a cascaded chain analyses tier by tier."""
+        arr = (ctypes.c_int * len(self.rungs))(*parent)
+        _call(self.handle, "ladder_set_parents", self.handle, arr)
+        self.parent = list(parent)
 
     def decide_qps(self, rung, frame_id, qps, stream=None) -> dict:
         """Cost, best, split and leaf maps of (rung, frame) at each QP of
