@@ -69,8 +69,8 @@ L2_FLUSH_BYTES = 256 << 20
 # the hash of the kernel sources it was taken on: null once a kernel changes.
 KERNEL_SOURCES = {"full_search": ["me_full.cu", "common.cuh"], "dependent": ["me_dependent.cu", "common.cuh"]}
 TRAFFIC_NCU = {
-    ("full_search", "ladder1080", "20071cf5c7fd"): 585557,
-    ("dependent", "ladder1080", "74497a9cb6ec"): 8566528,
+    ("full_search", "ladder1080", "9dc7474d94aa"): 598699,
+    ("dependent", "ladder1080", "c2150367c40d"): 8556544,
 }
 
 
@@ -572,8 +572,11 @@ def run_batch(args, wl):
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     absdiff_per_instr = 4 if wl["bit_depth"] == 8 else 2
     peak = props.multi_processor_count * 64 * absdiff_per_instr * sm_max * 1e6 / 1e12
+    # algorithmic absdiffs of one step (all the kind's launches of the step:
+    # a cascaded chain runs one dependent search per tier) over its summed
+    # kernel time per step (the profile pass ran 3 steps)
     algo = {"full_search": 64 * evals_ref * n, "dependent": 64 * evals_dep * n}.get(kname)
-    achieved = (algo / (kms / klaunch * 1e-3) / 1e12) if (algo and klaunch) else None
+    achieved = (algo / (kms / 3 * 1e-3) / 1e12) if (algo and klaunch) else None
     result = {
         "metric": METRIC, "value": n * K / (ms_multi * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W,
         "ms_per_step": ms_multi / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -592,7 +595,8 @@ def run_batch(args, wl):
         "gpu_launches": launches_per_step * K,
         "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tabsdiff/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "algorithmic_absdiffs_per_launch": algo, "avg_launch_ms": (kms / klaunch) if klaunch else None},
+                     "algorithmic_absdiffs_per_step": algo, "kernel_ms_per_step": kms / 3,
+                     "launches_per_step": klaunch // 3},
         "clocks": dict(clocks, window="untimed soak + timed loops"),
     }
     if cpu:
