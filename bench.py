@@ -305,26 +305,72 @@ def run_ours(args, wl):
     stats = lad.kernel_stats(reset=True)
     lad.profile(False)
 
-    # end to end: pinned host planes in, every rung's decisions out
-    host = [[(torch.from_numpy(np.ascontiguousarray(c).view(np.int16) if c.dtype == np.uint16 else c).pin_memory(),
-              torch.from_numpy(np.ascontiguousarray(f).view(np.int16) if f.dtype == np.uint16 else f).pin_memory())
-             for (_, _, c, f) in fr] for fr in frames]
-    h2d = sum(int(c.numel() * c.element_size() + f.numel() * f.element_size()) for (c, f) in host[0])
-    d2h = 0
+    # end to end through the public API, pipelined like a serving loop: each
+    # step uploads its frame's planes (one copy of a packed pinned buffer
+    # holding every rung's cur/ref planes in device-plane layout), analyses
+    # it, and reads back every rung's decisions (ladder_fetch_frame_async, one
+    # copy per rung into pinned memory); uploads and read-backs run on their
+    # own streams and overlap the analyses of neighbouring steps; two frame
+    # slots and two device plane sets alternate.
+    def packed_layout(fr):
+        offs, off = [], 0
+        for (w, h, c, f) in fr:
+            es = 1 if c.dtype == np.uint8 else 2
+            pitch = (w * es + 127) // 128 * 128
+            offs.append((off, off + h * pitch, pitch, h, w, es))
+            off += 2 * h * pitch
+        return offs, off
+
+    lay, in_bytes = packed_layout(frames[0])
+
+    def pack_host(fr):
+        buf = torch.zeros(in_bytes, dtype=torch.uint8).pin_memory()
+        nb = buf.numpy()
+        for (oc, orf, pitch, h, w, es), (_, _, c, f) in zip(lay, fr):
+            for o, pl in ((oc, c), (orf, f)):
+                rows = nb[o:o + h * pitch].reshape(h, pitch)
+                rows[:, :w * es] = np.ascontiguousarray(pl).view(np.uint8).reshape(h, w * es)
+        return buf
+
+    def device_views(dbuf):
+        out = []
+        for (oc, orf, pitch, h, w, es) in lay:
+            dt = torch.uint8 if es == 1 else torch.int16
+            cv = dbuf[oc:oc + h * pitch].view(dt).view(h, pitch // es)[:, :w]
+            rv = dbuf[orf:orf + h * pitch].view(dt).view(h, pitch // es)[:, :w]
+            out.append((cv, rv))
+        return out
+
+    host_in = [pack_host(fr) for fr in frames]
+    dev_in = [torch.empty(in_bytes, dtype=torch.uint8, device=dev) for _ in range(2)]
+    dev_pl = [device_views(t) for t in dev_in]
+    fbytes = lad.frame_bytes()
+    host_out = [torch.empty(fbytes, dtype=torch.uint8).pin_memory() for _ in range(2)]
+    h2d, d2h = in_bytes, fbytes
+    comp = torch.cuda.current_stream()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("in", "comp", "out")}
+    for k in ev:
+        for e in ev[k]:
+            e.record(comp)
 
     def step_e2e(i):
-        nonlocal d2h
-        pl, hp = dplanes[i % n_frames], host[i % n_frames]
-        for (dc, dr), (hc, hr) in zip(pl, hp):
-            dc.copy_(hc, non_blocking=True)
-            dr.copy_(hr, non_blocking=True)
-        step_multi(i)
-        nbytes = 0
-        for r in range(n_rungs):
-            o = lad.fetch(r, 0)
-            nbytes += sum(a.nbytes for k in ("mvx", "mvy", "sad", "satd", "cost", "best", "split", "evaluated")
-                          for a in o[k]) + o["leaf_depth"].nbytes + o["leaf_mvx"].nbytes + o["leaf_mvy"].nbytes
-        d2h = nbytes
+        j = i % 2
+        with torch.cuda.stream(s_in):                  # upload: after this slot's last analysis
+            s_in.wait_event(ev["comp"][j])
+            dev_in[j].copy_(host_in[i % n_frames], non_blocking=True)
+            ev["in"][j].record(s_in)
+        comp.wait_event(ev["in"][j])                   # analyse: after the upload and the slot's last read-back
+        comp.wait_event(ev["out"][j])
+        pl = dev_pl[j]
+        lad.analyze_reference(j, pl[ref_i][0], pl[ref_i][1], qp)
+        lad.analyze_dependents(j, [(r, pl[r][0], pl[r][1]) for r in range(n_rungs) if r != ref_i], qp)
+        ev["comp"][j].record(comp)
+        s_out.wait_event(ev["comp"][j])                # read back every rung of the frame
+        lad.fetch_frame_async(j, host_out[j], s_out)
+        ev["out"][j].record(s_out)
+        if i >= 1:                                     # the previous step's decisions are on the host
+            ev["out"][1 - j].synchronize()
 
     for i in range(W):
         step_e2e(i)
@@ -333,9 +379,18 @@ def run_ours(args, wl):
     t0 = time.perf_counter()
     for i in range(K):
         step_e2e(i)
+    ev["out"][(K - 1) % 2].synchronize()
     torch.cuda.synchronize()
     replicas.barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_s_measured = time.perf_counter() - t0
+    # the read-back of the last step is that frame's analysis: check one rung
+    # of it against a synchronous fetch of the same slot
+    jl = (K - 1) % 2
+    got = lad.frame_views(host_out[jl].numpy())[ref_i]
+    want = lad.fetch(ref_i, jl)
+    if not all(np.array_equal(got[k][d], want[k][d]) for k in ("mvx", "sad", "best") for d in range(len(want[k]))):
+        raise RuntimeError("end-to-end read-back differs from the frame's decisions")
+    e2e_s = max_over_ranks(e2e_s_measured)
 
     # intra-resolution multi-QP sharing: the decisions of every rung at three
     # more QPs from the resident analysis (one launch per rung), per frame

@@ -275,6 +275,25 @@ typedef struct {
 LADDER_API ladder_status ladder_decide_qps(ladder_t *ladder, int rung, int frame_id, int n, const int *qps,
                                            const ladder_qp_decisions *out, void *cuda_stream);
 
+/* Asynchronous fetch of a whole frame (every rung's decisions), for callers
+ * that overlap copies with later analyses.  The frame is packed rung after
+ * rung, ladder_frame_bytes() bytes in all; ladder_decision_offsets() gives
+ * the byte offset, within the packed frame, of each array of a rung:
+ * offsets[8*d + k] for depth d = 0..3 and field k = mvx, mvy, sad, satd,
+ * cost, best, split, evaluated (-1 past the rung's deepest depth), then
+ * offsets[32..34] = leaf_depth, leaf_mvx, leaf_mvy (35 entries, element
+ * types and sizes as in ladder_decisions).  ladder_fetch_frame_async
+ * enqueues one device-to-host copy per rung on `cuda_stream` into host_dst
+ * (caller-owned, `bytes` >= ladder_frame_bytes; pinned memory keeps the
+ * copies asynchronous) and returns without waiting: the caller synchronises
+ * the stream (or an event) before reading, and orders the frame's next
+ * analysis after the copies.  Rungs of the frame that were not analysed are
+ * copied as they stand.  LADDER_E_STATE if the frame holds no slot. */
+LADDER_API long ladder_frame_bytes(const ladder_t *ladder);
+LADDER_API ladder_status ladder_decision_offsets(const ladder_t *ladder, int rung, long *offsets);
+LADDER_API ladder_status ladder_fetch_frame_async(ladder_t *ladder, int frame_id, void *host_dst, long bytes,
+                                                  void *cuda_stream);
+
 /* Grid of a rung: dims[2d], dims[2d+1] = cols_d, rows_d for d = 0..dmax, then
  * dims[2(dmax+1)], dims[2(dmax+1)+1] = 8x8 cols, rows; returns dmax in *n_depths - 1.
  * `dims` must hold 2 * LADDER_MAX_DEPTHS + 2 ints. */

@@ -976,6 +976,49 @@ ladder_status fetch_decisions(ladder_t *l, int rung, int frame_id, ladder_decisi
     return ladder_sync(l, cuda_stream);
 }
 
+long ladder_frame_bytes(const ladder_t *l)
+{
+    if (!l) return 0;
+    long total = 0;
+    for (int r = 0; r < l->geo.n_rungs; ++r) total += l->info[r].off.dec_bytes;
+    return total;
+}
+
+ladder_status ladder_decision_offsets(const ladder_t *l, int rung, long *offsets)
+{
+    if (!l || !offsets) return LADDER_E_INVAL;
+    if (rung < 0 || rung >= l->geo.n_rungs) return LADDER_E_INVAL;
+    long base = 0;
+    for (int r = 0; r < rung; ++r) base += l->info[r].off.dec_bytes;
+    const DecOffsets &o = l->info[rung].off;
+    for (int d = 0; d < kMaxDepths; ++d) {
+        const bool has = d <= l->info[rung].g.dmax;
+        const long f[8] = {o.mvx[d], o.mvy[d], o.sad[d], o.satd[d], o.cost[d], o.best[d], o.split[d], o.evaluated[d]};
+        for (int k = 0; k < 8; ++k) offsets[8 * d + k] = has ? base + f[k] : -1;
+    }
+    offsets[32] = base + o.leaf_depth;
+    offsets[33] = base + o.leaf_mvx;
+    offsets[34] = base + o.leaf_mvy;
+    return LADDER_OK;
+}
+
+ladder_status ladder_fetch_frame_async(ladder_t *l, int frame_id, void *host_dst, long bytes, void *cuda_stream)
+{
+    if (!l || !host_dst) return LADDER_E_INVAL;
+    if (bytes < ladder_frame_bytes(l)) return fail(l, LADDER_E_INVAL, "%ld bytes, the frame needs %ld", bytes, ladder_frame_bytes(l));
+    Slot *slot = find_slot(l, frame_id);
+    if (!slot) return fail(l, LADDER_E_STATE, "frame %d holds no slot", frame_id);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    char *dst = static_cast<char *>(host_dst);
+    for (int r = 0; r < l->geo.n_rungs; ++r) {
+        const long n = l->info[r].off.dec_bytes;
+        const cudaError_t e = cudaMemcpyAsync(dst, slot->rungs[r].block, static_cast<size_t>(n), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(l, e, "frame fetch copy");
+        dst += n;
+    }
+    return LADDER_OK;
+}
+
 ladder_status ladder_release_frame(ladder_t *l, int frame_id)
 {
     if (!l) return LADDER_E_INVAL;

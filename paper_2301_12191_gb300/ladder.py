@@ -90,6 +90,10 @@ SIGNATURES = [
     ("fetch_decisions", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Decisions),
                                        ctypes.c_void_p]),
     ("ladder_set_parents", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    ("ladder_frame_bytes", ctypes.c_long, [ctypes.c_void_p]),
+    ("ladder_decision_offsets", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_long)]),
+    ("ladder_fetch_frame_async", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_long,
+                                                ctypes.c_void_p]),
     ("ladder_decide_qps", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(QpDecisions), ctypes.c_void_p]),
     ("ladder_grid", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -451,6 +455,42 @@ class Ladder:
         for q, t in zip(qps, tensors):
             res[q] = {k: ([a.cpu().numpy() for a in v] if isinstance(v, list) else v.cpu().numpy()) for k, v in t.items()}
         return res
+
+    def frame_bytes(self) -> int:
+        """Bytes of one frame's packed decisions (every rung)."""
+        return int(load().ladder_frame_bytes(self.handle))
+
+    def frame_views(self, buf) -> list:
+        """numpy views, per rung, into a packed frame `buf` (a uint8 numpy
+        array of frame_bytes() bytes), laid out like fetch()."""
+        out = []
+        for r in range(len(self.rungs)):
+            offs = (ctypes.c_long * 35)()
+            _call(self.handle, "ladder_decision_offsets", self.handle, r, offs)
+            dims, (c8, r8) = self.grid(r)
+            v = {k: [] for k in ("mvx", "mvy", "sad", "satd", "cost", "best", "split", "evaluated")}
+            for d, (c, rr) in enumerate(dims):
+                n = c * rr
+                for k, (name, dt) in enumerate((("mvx", np.int16), ("mvy", np.int16), ("sad", np.int32),
+                                                 ("satd", np.int32), ("cost", np.int32), ("best", np.int32),
+                                                 ("split", np.uint8), ("evaluated", np.uint8))):
+                    o = offs[8 * d + k]
+                    v[name].append(buf[o:o + n * np.dtype(dt).itemsize].view(dt))
+            for k, (name, dt) in enumerate((("leaf_depth", np.uint8), ("leaf_mvx", np.int16), ("leaf_mvy", np.int16))):
+                o = offs[32 + k]
+                v[name] = buf[o:o + c8 * r8 * np.dtype(dt).itemsize].view(dt)
+            v["grid"] = dims
+            v["grid8"] = (c8, r8)
+            v["size"] = self.rungs[r]
+            out.append(v)
+        return out
+
+    def fetch_frame_async(self, frame_id, host, stream=None):
+        """Enqueues the copy of every rung's decisions of `frame_id` into
+        `host` (a pinned uint8 tensor of frame_bytes() bytes) on `stream`;
+        does not wait."""
+        _call(self.handle, "ladder_fetch_frame_async", self.handle, frame_id, host.data_ptr(), host.numel(),
+              _stream_handle(stream))
 
     def fetch(self, rung, frame_id, stream=None) -> dict:
         """Decisions of (rung, frame) as numpy arrays, laid out like the
