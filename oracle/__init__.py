@@ -39,6 +39,16 @@ class _Decisions(ctypes.Structure):
     ]
 
 
+class _Subpel(ctypes.Structure):
+    _fields_ = [
+        ("qmvx", ctypes.c_void_p * MAXD), ("qmvy", ctypes.c_void_p * MAXD),
+        ("satd", ctypes.c_void_p * MAXD), ("cost", ctypes.c_void_p * MAXD),
+        ("best", ctypes.c_void_p * MAXD), ("split", ctypes.c_void_p * MAXD),
+        ("leaf_depth", ctypes.c_void_p), ("leaf_qmvx", ctypes.c_void_p),
+        ("leaf_qmvy", ctypes.c_void_p),
+    ]
+
+
 class _Job(ctypes.Structure):
     _fields_ = [
         ("cur", ctypes.c_void_p), ("ref", ctypes.c_void_p),
@@ -87,6 +97,13 @@ def _load():
             fn.restype = ctypes.c_int32
         lib.oracle_derive_rule.argtypes = [ctypes.POINTER(_Job)] + [ctypes.c_int] * 3 + [ctypes.c_void_p]
         lib.oracle_derive_rule.restype = None
+        lib.oracle_refine_subpel.argtypes = [ctypes.POINTER(_Job), ctypes.POINTER(_Decisions),
+                                             ctypes.POINTER(_Subpel), ctypes.c_int]
+        lib.oracle_refine_subpel.restype = ctypes.c_int
+        lib.oracle_pred_sample.argtypes = [ctypes.POINTER(_Job)] + [ctypes.c_int] * 4
+        lib.oracle_pred_sample.restype = ctypes.c_int
+        lib.oracle_block_satd_q.argtypes = [ctypes.POINTER(_Job)] + [ctypes.c_int] * 5
+        lib.oracle_block_satd_q.restype = ctypes.c_int32
         _lib = lib
     return _lib
 
@@ -223,3 +240,61 @@ def derive_rule(dep_size, dep: dict, d: int, x0: int, y0: int, ctu: int = 64):
     _load().oracle_derive_rule(ctypes.byref(job), d, x0, y0, out.ctypes.data)
     del keep
     return tuple(int(v) for v in out)
+
+
+def refine_subpel(cur, ref, analysis: dict, *, qp: int, ctu: int = 64, satd_mode: int = 0,
+                  dep: dict | None = None, threads: int | None = None) -> dict:
+    """Quarter-pel refinement of an analysis of the same frame pair (as
+    returned by analyze() with the same qp / ctu / satd_mode / dep): per
+    depth ``qmvx, qmvy`` (quarter-pel units), ``satd``, ``cost``, ``best``,
+    ``split``, and per 8x8 ``leaf_depth, leaf_qmvx, leaf_qmvy``."""
+    lib = _load()
+    job, keep = _make_job(cur, ref, qp, ctu, 0, satd_mode, dep)
+    dims, (c8, r8) = grid(job.width, job.height, ctu)
+    dec = _Decisions()
+    for d in range(len(dims)):
+        for k in ("mvx", "mvy", "sad", "satd", "cost", "best", "split", "evaluated"):
+            a = np.ascontiguousarray(analysis[k][d])
+            keep.append(a)
+            getattr(dec, k)[d] = a.ctypes.data
+    for k in ("leaf_depth", "leaf_mvx", "leaf_mvy"):
+        a = np.ascontiguousarray(analysis[k])
+        keep.append(a)
+        setattr(dec, k, a.ctypes.data)
+    out = {k: [] for k in ("qmvx", "qmvy", "satd", "cost", "best", "split")}
+    sp = _Subpel()
+    for d, (c, r) in enumerate(dims):
+        for k, dt in (("qmvx", np.int16), ("qmvy", np.int16), ("satd", np.int32), ("cost", np.int32),
+                      ("best", np.int32), ("split", np.uint8)):
+            a = np.zeros(c * r, dtype=dt)
+            out[k].append(a)
+            getattr(sp, k)[d] = a.ctypes.data
+    for k, dt in (("leaf_depth", np.uint8), ("leaf_qmvx", np.int16), ("leaf_qmvy", np.int16)):
+        a = np.zeros(c8 * r8, dtype=dt)
+        out[k] = a
+        setattr(sp, k, a.ctypes.data)
+    if threads is None:
+        threads = os.cpu_count() or 1
+    rc = lib.oracle_refine_subpel(ctypes.byref(job), ctypes.byref(dec), ctypes.byref(sp), int(threads))
+    del keep
+    if rc != 0:
+        raise ValueError("oracle_refine_subpel rejected its arguments")
+    out["grid"] = dims
+    out["grid8"] = (c8, r8)
+    return out
+
+
+def pred_sample(ref, x: int, y: int, qx: int, qy: int) -> int:
+    """Quarter-pel prediction of sample (x, y) displaced by (qx, qy) quarter units."""
+    job, keep = _make_job(ref, ref, 0, 64, 0, 0, None)
+    r = int(_load().oracle_pred_sample(ctypes.byref(job), x, y, qx, qy))
+    del keep
+    return r
+
+
+def block_satd_q(cur, ref, x0, y0, size, qx, qy, satd_mode: int = 0) -> int:
+    """SATD of a size x size block against the quarter-pel prediction."""
+    job, keep = _make_job(cur, ref, 0, 64, 0, satd_mode, None)
+    r = int(_load().oracle_block_satd_q(ctypes.byref(job), x0, y0, size, qx, qy))
+    del keep
+    return r

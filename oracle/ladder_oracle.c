@@ -457,3 +457,234 @@ void oracle_derive_rule(const oracle_job *job, int d, int x0, int y0, int out[4]
     cu_rule r = derive_rule(job, d, x0, y0);
     out[0] = r.cx; out[1] = r.cy; out[2] = r.allowed_leaf; out[3] = r.allowed_split;
 }
+
+/* ------------------------------------------------------------------ */
+/* Quarter-pel refinement with SATD around the integer vector           */
+/* (Sec. 5.4.1: SAD finds the integer vectors, SATD the quarter-pel     */
+/* ones; the interpolation filters are among the kernels the encoder    */
+/* accelerates, Sec. 6.6).  Readings, the paper giving no filter or     */
+/* search pattern: the 8-tap luma filters of HEVC for the phases 0,     */
+/* 1/4, 1/2, 3/4, applied as the exact two-dimensional separable sum    */
+/* and rounded once; a half-pel round (the 8 neighbours at +-2 quarter  */
+/* units) then a quarter-pel round (+-1) around the best so far, each   */
+/* keeping the current best unless a candidate's cost is strictly lower */
+/* (candidates in raster order, dy then dx); cost = SATD + lambda *     */
+/* se-bits of the quarter-pel components.  The split is then decided    */
+/* again over the refined costs.                                        */
+/* ------------------------------------------------------------------ */
+static const int OR_FILT[4][8] = {
+    {0, 0, 0, 64, 0, 0, 0, 0},
+    {-1, 4, -10, 58, 17, -5, 1, 0},
+    {-1, 4, -11, 40, 40, -11, 4, -1},
+    {0, 1, -5, 17, 58, -10, 4, -1},
+};
+
+static int floor_div4(int v) { return v >= 0 ? v / 4 : -((-v + 3) / 4); }
+
+/* Prediction of the sample at (x, y) displaced by the quarter-pel vector
+ * (qx, qy): P = clip((sum_j f_fy[j] sum_i f_fx[i] Ref(X+i-3, Y+j-3) + 2^11)
+ * >> 12), X = x + floor(qx / 4), fx = qx - 4 floor(qx / 4) (likewise y);
+ * Ref clamped to the frame.  At an integer vector P is the sample itself. */
+static int pred_sample(const oracle_job *j, int x, int y, int qx, int qy)
+{
+    int X = x + floor_div4(qx), Y = y + floor_div4(qy);
+    int fx = qx - 4 * floor_div4(qx), fy = qy - 4 * floor_div4(qy);
+    long long sum = 0;
+    for (int jj = 0; jj < 8; jj++)
+        for (int ii = 0; ii < 8; ii++)
+            sum += (long long)OR_FILT[fy][jj] * OR_FILT[fx][ii] * ref_sample(j, X + ii - 3, Y + jj - 3);
+    long long p = sum + 2048;
+    p = p >= 0 ? p / 4096 : -((-p + 4095) / 4096);  /* floor */
+    long long maxv = (1 << j->bit_depth) - 1;
+    return (int)(p < 0 ? 0 : (p > maxv ? maxv : p));
+}
+
+/* SATD of the S x S CU at (x0, y0) against the quarter-pel prediction. */
+static int32_t block_satd_q(const oracle_job *j, int x0, int y0, int S, int qx, int qy)
+{
+    int32_t total = 0, d[64];
+    for (int by = 0; by < S; by += 8)
+        for (int bx = 0; bx < S; bx += 8) {
+            for (int y = 0; y < 8; y++)
+                for (int x = 0; x < 8; x++)
+                    d[y * 8 + x] = cur_sample(j, x0 + bx + x, y0 + by + y) -
+                                   pred_sample(j, x0 + bx + x, y0 + by + y, qx, qy);
+            total += j->satd_mode == 1 ? oracle_satd8_paper4x4(d) : oracle_satd8_had8(d);
+        }
+    return total;
+}
+
+/* J = SATD + round(lambda * (se(qx) + se(qy))), the components in quarter-pel units. */
+static int32_t rd_cost_q(int32_t satd, int qp, int qx, int qy)
+{
+    long long prod = oracle_lambda_q16(qp) * (long long)(oracle_se_bits(qx) + oracle_se_bits(qy));
+    return satd + (int32_t)((prod + 32768) >> 16);
+}
+
+typedef struct {
+    int16_t *qmvx[OR_MAXD], *qmvy[OR_MAXD];
+    int32_t *satd[OR_MAXD], *cost[OR_MAXD], *best[OR_MAXD];
+    uint8_t *split[OR_MAXD];
+    uint8_t *leaf_depth;
+    int16_t *leaf_qmvx, *leaf_qmvy;
+} oracle_subpel;
+
+typedef struct {
+    const oracle_job *job;
+    const oracle_decisions *in;
+    oracle_subpel *out;
+    int W8, H8, dmax, ctu_cols, ctu_rows;
+    int next_row;
+    pthread_mutex_t lock;
+} subpel_ctx;
+
+static int grid_cols_s(const subpel_ctx *c, int d) { int S = c->job->ctu >> d; return (c->W8 + S - 1) / S; }
+
+/* The two rounds of one evaluated CU, from its integer vector and SATD. */
+static void subpel_search(const oracle_job *j, int x0, int y0, int S, int mvx, int mvy, int32_t satd0,
+                          int *oqx, int *oqy, int32_t *osatd, int32_t *oj)
+{
+    int bx = 4 * mvx, by = 4 * mvy;
+    int32_t bs = satd0, bj = rd_cost_q(satd0, j->qp, bx, by);
+    for (int step = 2; step >= 1; step--) {
+        int cx = bx, cy = by;
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                if (!dx && !dy) continue;
+                int qx = cx + step * dx, qy = cy + step * dy;
+                int32_t s = block_satd_q(j, x0, y0, S, qx, qy);
+                int32_t J = rd_cost_q(s, j->qp, qx, qy);
+                if (J < bj) { bj = J; bs = s; bx = qx; by = qy; }
+            }
+    }
+    *oqx = bx; *oqy = by; *osatd = bs; *oj = bj;
+}
+
+/* The quadtree again (same reachability, rules and forced splits as
+ * analyse_cu), with each evaluated CU's cost taken after its refinement. */
+static int32_t refine_cu(subpel_ctx *c, int d, int x0, int y0, int reachable)
+{
+    const oracle_job *j = c->job;
+    oracle_subpel *o = c->out;
+    int S = j->ctu >> d;
+    long idx = (long)(y0 / S) * grid_cols_s(c, d) + x0 / S;
+    int inside = x0 + S <= c->W8 && y0 + S <= c->H8;
+    cu_rule rule = derive_rule(j, d, x0, y0);
+    int evaluated = c->in->evaluated[d][idx];
+    int32_t J = INT32_MAX;
+    if (evaluated) {
+        int qx, qy;
+        int32_t s;
+        subpel_search(j, x0, y0, S, c->in->mvx[d][idx], c->in->mvy[d][idx], c->in->satd[d][idx], &qx, &qy, &s, &J);
+        o->qmvx[d][idx] = (int16_t)qx;
+        o->qmvy[d][idx] = (int16_t)qy;
+        o->satd[d][idx] = s;
+        o->cost[d][idx] = J;
+    } else {
+        o->qmvx[d][idx] = INT16_MIN;
+        o->qmvy[d][idx] = INT16_MIN;
+        o->satd[d][idx] = INT32_MAX;
+        o->cost[d][idx] = INT32_MAX;
+    }
+    if (d == c->dmax) {
+        o->best[d][idx] = J;
+        return J;
+    }
+    int forced = !inside;
+    int can_split = reachable && (forced || rule.allowed_split);
+    int32_t children = 0;
+    int h = S / 2;
+    for (int q = 0; q < 4; q++) {
+        int cx0 = x0 + (q & 1) * h, cy0 = y0 + (q >> 1) * h;
+        if (cx0 < c->W8 && cy0 < c->H8) {
+            int32_t b = refine_cu(c, d + 1, cx0, cy0, can_split);
+            if (can_split) children += b;
+        }
+    }
+    int split = can_split && (!evaluated || children < J);
+    o->split[d][idx] = (uint8_t)split;
+    int32_t best = !reachable ? INT32_MAX : (split ? children : J);
+    o->best[d][idx] = best;
+    return best;
+}
+
+static void refine_leaves(subpel_ctx *c, int d, int x0, int y0)
+{
+    const oracle_job *j = c->job;
+    oracle_subpel *o = c->out;
+    int S = j->ctu >> d;
+    long idx = (long)(y0 / S) * grid_cols_s(c, d) + x0 / S;
+    if (d < c->dmax && o->split[d][idx]) {
+        int h = S / 2;
+        for (int q = 0; q < 4; q++) {
+            int cx0 = x0 + (q & 1) * h, cy0 = y0 + (q >> 1) * h;
+            if (cx0 < c->W8 && cy0 < c->H8) refine_leaves(c, d + 1, cx0, cy0);
+        }
+        return;
+    }
+    int cols8 = c->W8 / 8;
+    for (int y = y0; y < y0 + S && y < c->H8; y += 8)
+        for (int x = x0; x < x0 + S && x < c->W8; x += 8) {
+            long li = (long)(y / 8) * cols8 + x / 8;
+            o->leaf_depth[li] = (uint8_t)d;
+            o->leaf_qmvx[li] = o->qmvx[d][idx];
+            o->leaf_qmvy[li] = o->qmvy[d][idx];
+        }
+}
+
+static void *refine_worker(void *arg)
+{
+    subpel_ctx *c = (subpel_ctx *)arg;
+    for (;;) {
+        pthread_mutex_lock(&c->lock);
+        int row = c->next_row++;
+        pthread_mutex_unlock(&c->lock);
+        if (row >= c->ctu_rows) break;
+        for (int col = 0; col < c->ctu_cols; col++) {
+            int x0 = col * c->job->ctu, y0 = row * c->job->ctu;
+            refine_cu(c, 0, x0, y0, 1);
+            refine_leaves(c, 0, x0, y0);
+        }
+    }
+    return NULL;
+}
+
+/* Quarter-pel refinement of an analysis `in` of the same job (its integer
+ * vectors, SATDs and evaluated flags); returns 0, or -1 on bad arguments. */
+int oracle_refine_subpel(const oracle_job *job, const oracle_decisions *in, oracle_subpel *out, int threads)
+{
+    if (!valid_job(job) || !in || !out) return -1;
+    subpel_ctx c;
+    memset(&c, 0, sizeof c);
+    c.job = job;
+    c.in = in;
+    c.out = out;
+    c.W8 = (job->width + 7) / 8 * 8;
+    c.H8 = (job->height + 7) / 8 * 8;
+    c.dmax = ilog2i(job->ctu / 8);
+    c.ctu_cols = (c.W8 + job->ctu - 1) / job->ctu;
+    c.ctu_rows = (c.H8 + job->ctu - 1) / job->ctu;
+    pthread_mutex_init(&c.lock, NULL);
+    if (threads <= 1) {
+        refine_worker(&c);
+    } else {
+        pthread_t *t = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)threads);
+        if (!t) return -1;
+        for (int i = 0; i < threads; i++) pthread_create(&t[i], NULL, refine_worker, &c);
+        for (int i = 0; i < threads; i++) pthread_join(t[i], NULL);
+        free(t);
+    }
+    pthread_mutex_destroy(&c.lock);
+    return 0;
+}
+
+/* Probes for the pinning tests. */
+int oracle_pred_sample(const oracle_job *job, int x, int y, int qx, int qy)
+{
+    return pred_sample(job, x, y, qx, qy);
+}
+
+int32_t oracle_block_satd_q(const oracle_job *job, int x0, int y0, int S, int qx, int qy)
+{
+    return block_satd_q(job, x0, y0, S, qx, qy);
+}
