@@ -275,6 +275,35 @@ typedef struct {
 LADDER_API ladder_status ladder_decide_qps(ladder_t *ladder, int rung, int frame_id, int n, const int *qps,
                                            const ladder_qp_decisions *out, void *cuda_stream);
 
+/* Quarter-pel refinement with SATD of one analysed rung (SATD finds the
+ * quarter-pel vectors, Sec. 5.4.1).  Every evaluated CU starts at its
+ * integer vector (4 mv in quarter-pel units) with its cost; a half-pel round
+ * tries the 8 neighbours at +-2 quarter units and a quarter-pel round the 8
+ * at +-1 around the best so far, each candidate replacing the best only with
+ * a strictly lower cost J = SATD + ((lambdaQ16[qp] * (se(qx) + se(qy)) +
+ * 2^15) >> 16) (candidates in raster order).  The prediction at a
+ * fractional position is the two-dimensional 8-tap luma filter of HEVC
+ * (phases 0, 1/4, 1/2, 3/4) summed exactly and rounded once, clip(floor((sum
+ * + 2^11) / 2^12)), the reference clamped to the frame.  The split is then
+ * decided again over the refined costs, with the rung's own flags (and a
+ * dependent rung's rules).  cur / ref / pitch_bytes: the rung's planes (as
+ * analysed); qp: the QP of the analysis.  out: caller-owned DEVICE arrays
+ * laid out as the same fields of ladder_decisions, qmvx / qmvy in
+ * quarter-pel units (INT16_MIN where not evaluated), satd / cost at the
+ * refined vector; every member for depths 0..dmax must be set.
+ * Asynchronous on cuda_stream (one launch); LADDER_E_STATE if the rung of
+ * frame_id has not been analysed. */
+typedef struct {
+    int16_t *qmvx[LADDER_MAX_DEPTHS], *qmvy[LADDER_MAX_DEPTHS];
+    int32_t *satd[LADDER_MAX_DEPTHS], *cost[LADDER_MAX_DEPTHS], *best[LADDER_MAX_DEPTHS];
+    uint8_t *split[LADDER_MAX_DEPTHS];
+    uint8_t *leaf_depth;
+    int16_t *leaf_qmvx, *leaf_qmvy;
+} ladder_subpel_decisions;
+LADDER_API ladder_status ladder_refine_subpel(ladder_t *ladder, int rung, int frame_id, const void *cur,
+                                              const void *ref, long pitch_bytes, int qp,
+                                              const ladder_subpel_decisions *out, void *cuda_stream);
+
 /* Asynchronous fetch of a whole frame (every rung's decisions), for callers
  * that overlap copies with later analyses.  The frame is packed rung after
  * rung, ladder_frame_bytes() bytes in all; ladder_decision_offsets() gives
@@ -319,7 +348,8 @@ LADDER_API const char *ladder_last_error(const ladder_t *ladder);
  * 0 full search, 1 SATD/cost/split of an independent rung, 2 refinement
  * search of dependent rungs, 3 key initialisation, 4 dependent constraint
  * derivation (rules, centres, task lists), 5 SATD/cost/split of dependent
- * rungs, 6 cost/split at further QPs (ladder_decide_qps). */
+ * rungs, 6 cost/split at further QPs (ladder_decide_qps), 7 quarter-pel
+ * refinement (ladder_refine_subpel). */
 LADDER_API ladder_status ladder_profile_enable(ladder_t *ladder, int enable);
 
 /* Reads the launch count and the summed event time (ms; 0 when timing was

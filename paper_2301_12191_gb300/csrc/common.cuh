@@ -138,6 +138,8 @@ __device__ __forceinline__ float sample_f(uint32_t w, int k)
     return __int_as_float(static_cast<int>(__byte_perm(w, 0x4b000000u, sel)));
 }
 
+__device__ __forceinline__ int satd8_transform(float (&v)[64], int mode);
+
 // SATD of the 8x8 block at (px, py) against the reference displaced by
 // (mvx, mvy), by one thread.  Samples are read with clamping (current:
 // replicate to the 8-aligned size; reference: frame edge).  The residual
@@ -206,6 +208,15 @@ __device__ __forceinline__ int satd8_thread(const void *cur, const void *ref, lo
 #pragma unroll
         for (int x = 0; x < 8; ++x) v[8 * y + x] = sample_f<T>(cw[x / SPW], x % SPW) - sample_f<T>(rw[x / SPW], x % SPW);
     }
+    return satd8_transform(v, mode);
+}
+
+// The Hadamard part of the SATD of an 8x8 residual held in fp32 (integers
+// below 2^24 in magnitude, so every add is exact).
+//   mode 0: 8x8 Hadamard T = H8 D H8^T, (sum |T|) >> 2
+//   mode 1: two 4x4 Hadamards per 8x4 half, (sum of both) >> 1, halves added
+__device__ __forceinline__ int satd8_transform(float (&v)[64], int mode)
+{
     auto bfly = [&](int i, int j) {
         const float a = v[i], b = v[j];
         v[i] = a + b;
@@ -299,17 +310,24 @@ struct DecideIO {
 // Index of CU (d, local raster li) in the per-CTU key layout.
 __device__ __forceinline__ int key_index(int d, int li) { return key_offset(d) + li; }
 
+// What ctu_split writes besides cost, best, split and the leaf maps.
+enum : int {
+    kSplitWriteVectors = 1,  // mvx, mvy and SATD per CU
+    kSplitWriteAll = 3,      // also SAD and the evaluated flags
+};
+
 // Cost, bottom-up split and leaf maps of one CTU at lambda lam (Q16), from
 // st: flags, vectors and, for evaluated CUs, SADs and SATDs.  All threads
-// of the CTA take part.  Writes cost, best and split per CU and the leaf
-// maps; `all` also writes the vectors, SADs, SATDs and evaluated flags.
+// of the CTA take part.  Writes cost, best and split per CU, the leaf maps
+// and the fields `write` names.  `qpel`: the vectors are in quarter-pel
+// units (the rate term takes them as they are), else in integer samples.
 //   cost   -- J = SATD + ((lambdaQ16[qp] * bits + 2^15) >> 16), bits = se()
 //             lengths of the quarter-pel components (predictor (0,0))
 //   split  -- Sec. 2.1: split iff it may and (it is not a leaf candidate or
 //             the children's best sum is strictly lower), or it must
 template <int CTU>
-__device__ void ctu_split(CtuState<CTU> &st, int lam, const RungGeom &g, const DevDecisions &out, bool all, int x0,
-                          int y0)
+__device__ void ctu_split(CtuState<CTU> &st, int lam, const RungGeom &g, const DevDecisions &out, int write, int x0,
+                          int y0, bool qpel = false)
 {
     using C = Ctu<CTU>;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -322,7 +340,8 @@ __device__ void ctu_split(CtuState<CTU> &st, int lam, const RungGeom &g, const D
             const bool ev = f & kRuleEvaluated;
             int32_t J = INT32_MAX;
             if (ev) {
-                const long long bits = se_bits(4 * st.mvx[i]) + se_bits(4 * st.mvy[i]);
+                const int u = qpel ? 1 : 4;
+                const long long bits = se_bits(u * st.mvx[i]) + se_bits(u * st.mvy[i]);
                 J = st.satd[i] + static_cast<int32_t>((static_cast<long long>(lam) * bits + 32768) >> 16);
             }
             int32_t best = J;
@@ -344,11 +363,13 @@ __device__ void ctu_split(CtuState<CTU> &st, int lam, const RungGeom &g, const D
             st.best[i] = best;
             st.split[i] = split;
             const long gi = static_cast<long>(y0 / S + li / n) * g.cols[d] + x0 / S + li % n;
-            if (all) {
+            if (write & kSplitWriteVectors) {
                 out.mvx[d][gi] = st.mvx[i];
                 out.mvy[d][gi] = st.mvy[i];
-                out.sad[d][gi] = st.sad[i];
                 out.satd[d][gi] = ev ? st.satd[i] : INT32_MAX;
+            }
+            if ((write & kSplitWriteAll) == kSplitWriteAll) {
+                out.sad[d][gi] = st.sad[i];
                 out.evaluated[d][gi] = ev ? 1 : 0;
             }
             out.cost[d][gi] = J;
@@ -434,7 +455,7 @@ __device__ void ctu_decide(CtuState<CTU> &st, const DecideIO &io, int x0, int y0
     }
     __syncthreads();
 
-    ctu_split<CTU>(st, io.lambda_q16[io.qp], *io.g, io.out, true, x0, y0);
+    ctu_split<CTU>(st, io.lambda_q16[io.qp], *io.g, io.out, kSplitWriteAll, x0, y0);
 }
 
 // ---- dependent-mode constraint derivation --------------------------------

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kThreads) k_decide_qps(const __grid_constant__
         }
     }
     __syncthreads();
-    dev::ctu_split<CTU>(st, c_lambda_q16[b.qp[blockIdx.y]], g, b.out[blockIdx.y], false, x0, y0);
+    dev::ctu_split<CTU>(st, c_lambda_q16[b.qp[blockIdx.y]], g, b.out[blockIdx.y], 0, x0, y0);
 }
 
 __global__ void k_fill_keys(const __grid_constant__ FillBatch b)

@@ -34,8 +34,8 @@ struct Slot {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-constexpr int kKinds = 7;  // full search, decide, dependent search, fill keys, dependent rules, dependent decide,
-                           // further-QP decisions
+constexpr int kKinds = 8;  // full search, decide, dependent search, fill keys, dependent rules, dependent decide,
+                           // further-QP decisions, quarter-pel refinement
 
 struct ProfEvent {
     int kind;
@@ -974,6 +974,47 @@ ladder_status fetch_decisions(ladder_t *l, int rung, int frame_id, ladder_decisi
     copy(out->leaf_mvx, o.leaf_mvx, n8 * 2);
     copy(out->leaf_mvy, o.leaf_mvy, n8 * 2);
     return ladder_sync(l, cuda_stream);
+}
+
+ladder_status ladder_refine_subpel(ladder_t *l, int rung, int frame_id, const void *cur, const void *ref,
+                                   long pitch_bytes, int qp, const ladder_subpel_decisions *out, void *cuda_stream)
+{
+    if (!l || !out) return LADDER_E_INVAL;
+    ladder_status st = check_planes(l, rung, cur, ref, pitch_bytes, qp);
+    if (st != LADDER_OK) return st;
+    Slot *slot = find_slot(l, frame_id);
+    if (!slot || !slot->rungs[rung].analysed)
+        return fail(l, LADDER_E_STATE, "rung %d of frame %d has not been analysed", rung, frame_id);
+    const RungGeom &g = l->info[rung].g;
+    SubpelBatch b{};
+    b.g = g;
+    b.off = l->info[rung].off;
+    b.block = slot->rungs[rung].block;
+    b.dependent = slot->rungs[rung].analysed == 2;
+    b.qp = qp;
+    b.satd_mode = l->geo.satd_mode;
+    b.cur = cur;
+    b.ref = ref;
+    b.pitch_bytes = pitch_bytes;
+    if (!out->leaf_depth || !out->leaf_qmvx || !out->leaf_qmvy)
+        return fail(l, LADDER_E_INVAL, "leaf arrays missing");
+    for (int d = 0; d <= g.dmax; ++d) {
+        if (!out->qmvx[d] || !out->qmvy[d] || !out->satd[d] || !out->cost[d] || !out->best[d] || !out->split[d])
+            return fail(l, LADDER_E_INVAL, "depth %d arrays missing", d);
+        b.out.mvx[d] = out->qmvx[d];
+        b.out.mvy[d] = out->qmvy[d];
+        b.out.satd[d] = out->satd[d];
+        b.out.cost[d] = out->cost[d];
+        b.out.best[d] = out->best[d];
+        b.out.split[d] = out->split[d];
+    }
+    b.out.leaf_depth = out->leaf_depth;
+    b.out.leaf_mvx = out->leaf_qmvx;
+    b.out.leaf_mvy = out->leaf_qmvy;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const cudaError_t e = traced(l, 7, s, [&] { return launch_subpel(l->geo.bit_depth, l->geo.ctu_size, b, s); });
+    if (e != cudaSuccess) return cuda_fail(l, e, "quarter-pel refinement");
+    return LADDER_OK;
 }
 
 long ladder_frame_bytes(const ladder_t *l)

@@ -309,6 +309,19 @@ struct QpBatch {
 };
 cudaError_t launch_decide_qps(int ctu, const QpBatch &b, cudaStream_t s);
 
+// Quarter-pel refinement of one analysed rung: one CTA per CTU.
+struct SubpelBatch {
+    RungGeom g;
+    DecOffsets off;
+    const char *block;       // the (slot, rung) decision block
+    int dependent;           // 1: rule flags of the dependent analysis; 0: flags of the geometry
+    int qp, satd_mode;
+    const void *cur, *ref;
+    long pitch_bytes;
+    DevDecisions out;        // mvx, mvy (quarter-pel), satd, cost, best, split and leaf maps set
+};
+cudaError_t launch_subpel(int bit_depth, int ctu, const SubpelBatch &b, cudaStream_t s);
+
 // Fills the keys of every block of a batch with ~0 (key initialisation).
 struct FillItem {
     unsigned long long *keys;

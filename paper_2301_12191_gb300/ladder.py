@@ -56,6 +56,13 @@ class QpDecisions(ctypes.Structure):
                 ("leaf_depth", ctypes.c_void_p), ("leaf_mvx", ctypes.c_void_p), ("leaf_mvy", ctypes.c_void_p)]
 
 
+class SubpelDecisions(ctypes.Structure):
+    _fields_ = [("qmvx", ctypes.c_void_p * MAX_DEPTHS), ("qmvy", ctypes.c_void_p * MAX_DEPTHS),
+                ("satd", ctypes.c_void_p * MAX_DEPTHS), ("cost", ctypes.c_void_p * MAX_DEPTHS),
+                ("best", ctypes.c_void_p * MAX_DEPTHS), ("split", ctypes.c_void_p * MAX_DEPTHS),
+                ("leaf_depth", ctypes.c_void_p), ("leaf_qmvx", ctypes.c_void_p), ("leaf_qmvy", ctypes.c_void_p)]
+
+
 class Job(ctypes.Structure):
     _fields_ = [("frame_id", ctypes.c_int), ("rung", ctypes.c_int), ("kind", ctypes.c_int), ("qp", ctypes.c_int),
                 ("cur", ctypes.c_void_p), ("ref", ctypes.c_void_p), ("pitch_bytes", ctypes.c_long)]
@@ -90,6 +97,9 @@ SIGNATURES = [
     ("fetch_decisions", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Decisions),
                                        ctypes.c_void_p]),
     ("ladder_set_parents", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    ("ladder_refine_subpel", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_long, ctypes.c_int,
+                                            ctypes.POINTER(SubpelDecisions), ctypes.c_void_p]),
     ("ladder_frame_bytes", ctypes.c_long, [ctypes.c_void_p]),
     ("ladder_decision_offsets", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_long)]),
     ("ladder_fetch_frame_async", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_long,
@@ -114,7 +124,8 @@ SIGNATURES = [
     ("ladder_get_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
 ]
 
-KERNEL_KINDS = ("full_search", "decide", "dependent", "fill_keys", "dep_rules", "dep_decide", "decide_qps")
+KERNEL_KINDS = ("full_search", "decide", "dependent", "fill_keys", "dep_rules", "dep_decide", "decide_qps",
+                "subpel")
 TUNE_KNOBS = {"fs_band": 0, "dep_band": 1, "dep_range": 2, "dep_ctas_per_sm": 3, "fs_group": 4, "fs_fuse": 5}
 
 _lib = None
@@ -455,6 +466,42 @@ class Ladder:
         for q, t in zip(qps, tensors):
             res[q] = {k: ([a.cpu().numpy() for a in v] if isinstance(v, list) else v.cpu().numpy()) for k, v in t.items()}
         return res
+
+    def subpel_buffers(self, rung):
+        """Device arrays for ladder_refine_subpel of `rung`: (tensors dict,
+        SubpelDecisions struct pointing at them)."""
+        import torch
+
+        dims, (c8, r8) = self.grid(rung)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        t = {k: [] for k in ("qmvx", "qmvy", "satd", "cost", "best", "split")}
+        o = SubpelDecisions()
+        for d, (c, r) in enumerate(dims):
+            for k, dt in (("qmvx", torch.int16), ("qmvy", torch.int16), ("satd", torch.int32),
+                          ("cost", torch.int32), ("best", torch.int32), ("split", torch.uint8)):
+                a = torch.empty(c * r, dtype=dt, device=dev)
+                t[k].append(a)
+                getattr(o, k)[d] = a.data_ptr()
+        for k, dt in (("leaf_depth", torch.uint8), ("leaf_qmvx", torch.int16), ("leaf_qmvy", torch.int16)):
+            a = torch.empty(c8 * r8, dtype=dt, device=dev)
+            t[k] = a
+            setattr(o, k, a.data_ptr())
+        return t, o
+
+    def refine_subpel(self, rung, frame_id, cur, ref, qp, stream=None, buffers=None) -> dict:
+        """Quarter-pel refinement of an analysed (rung, frame): returns the
+        refined arrays as numpy (qmvx / qmvy in quarter-pel units) after
+        waiting for the stream; `buffers` = subpel_buffers(rung) to reuse."""
+        import torch
+
+        t, o = buffers if buffers is not None else self.subpel_buffers(rung)
+        s = _stream_handle(stream)
+        _call(self.handle, "ladder_refine_subpel", self.handle, rung, frame_id, cur.data_ptr(), ref.data_ptr(),
+              _pitch_bytes(cur), qp, ctypes.byref(o), s)
+        (stream or torch.cuda.current_stream()).synchronize()
+        out = {k: ([a.cpu().numpy() for a in v] if isinstance(v, list) else v.cpu().numpy()) for k, v in t.items()}
+        out["grid"], out["grid8"] = self.grid(rung)
+        return out
 
     def frame_bytes(self) -> int:
         """Bytes of one frame's packed decisions (every rung)."""
