@@ -15,6 +15,7 @@ has) on the host cores for the same workload.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -34,7 +35,7 @@ from paper_2301_12191_gb300 import synth  # noqa: E402
 WORKLOADS = {
     # 1080p source pair -> 1080p / 720p / 540p / 360p rungs; 360p reference
     "ladder1080": dict(source=(1920, 1080), rungs=[(1920, 1080), (1280, 720), (960, 540), (640, 360)], ref=3,
-                       bit_depth=8, R=32, r=4, qp=27, ctu=64, multi_qps=[22, 32, 37]),
+                       bit_depth=8, R=32, r=4, qp=27, ctu=64, multi_qps=[22, 32, 37], subpel=True),
     # 8 ladders x 5 consecutive frames (4 pairs each) of 1080p, one batched graph per step
     "batch8x5": dict(mode="batch", ladders=8, frames=5, source=(1920, 1080),
                      rungs=[(1920, 1080), (1280, 720), (960, 540), (640, 360)], ref=3, bit_depth=8, R=32, r=4,
@@ -427,6 +428,31 @@ def run_ours(args, wl):
                     "ms_per_step": ms_qps / K, "extra_ms_per_step": (ms_qps - ms_multi) / K,
                     "ladder_frames_qps_per_s": world * K * (1 + len(qps)) / (ms_qps * 1e-3)}
 
+    # quarter-pel refinement with SATD of every rung of the frame (one launch
+    # per rung, after the frame's analysis), per frame
+    subpel = None
+    if wl.get("subpel"):
+        bufs = [lad.subpel_buffers(r) for r in range(n_rungs)]
+        sh2 = torch.cuda.current_stream().cuda_stream
+
+        def step_subpel(i):
+            step_multi(i)
+            pl = dplanes[i % n_frames]
+            for r in range(n_rungs):
+                L._call(lad.handle, "ladder_refine_subpel", lad.handle, r, 0, pl[r][0].data_ptr(),
+                        pl[r][1].data_ptr(), L._pitch_bytes(pl[r][0]), qp, ctypes.byref(bufs[r][1]), sh2)
+
+        ms_sp = max_over_ranks(timed(step_subpel, K, W))
+        lad.kernel_stats(reset=True)
+        lad.profile(True)
+        timed(step_subpel, 3, 0)
+        st_sp = lad.kernel_stats(reset=True)
+        lad.profile(False)
+        n_sp, t_sp = st_sp.get("subpel", (0, 0.0))
+        subpel = {"launches_per_step": n_rungs, "ms_per_step": ms_sp / K, "extra_ms_per_step": (ms_sp - ms_multi) / K,
+                  "kernel_ms_per_step": t_sp / 3 if n_sp else None,
+                  "ladder_frames_per_s": world * K / (ms_sp * 1e-3)}
+
     props = torch.cuda.get_device_properties(dev)
     clocks = clk.summary()
     sm_max = clocks.get("sm_max_mhz") or 2070.0
@@ -482,6 +508,7 @@ def run_ours(args, wl):
         "multires_speedup_vs_independent": (ms_indep / indep_steps) / (ms_multi / K),
         "e2e": {"value": world * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "multi_qp": multi_qp,
+        "subpel": subpel,
         "gpu_launches": int(gpu_launches),
         "kernels": {k: {"launches": n, "ms_total": ms, "share": ms / max(1e-9, sum(v[1] for v in stats.values()))}
                     for k, (n, ms) in stats.items()},
