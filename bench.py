@@ -183,7 +183,35 @@ def cpu_baseline(wl, frames, budget_s=10.0):
             break
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{n} whole ladder frame(s) of the bench workload ({dt:.1f} s)"}
+            "sample": f"{n} whole ladder frame(s) of the bench workload ({dt:.1f} s)",
+            "one_core": one_core_baseline(wl, frames[0])}
+
+
+def one_core_baseline(wl, pairs, every=16):
+    """The oracle on one host core, estimated from a sample: every
+    `every`-th CTU of each rung analysed single-threaded (the dependents'
+    rules read reference decisions made beforehand, untimed), the time
+    scaled by the CTUs per rung."""
+    import oracle
+    ref_i, qp, ctu = wl["ref"], wl.get("qp", 27), wl["ctu"]
+    w, h, c, f = pairs[ref_i]
+    ref_out = oracle.analyze(c, f, qp=qp, search_range=wl["R"], ctu=ctu, threads=os.cpu_count() or 1)
+    total = 0.0
+    sampled = 0
+    for i, (w2, h2, c2, f2) in enumerate(pairs):
+        cols, rows = (w2 + 7) // 8 * 8, (h2 + 7) // 8 * 8
+        cols, rows = (cols + ctu - 1) // ctu, (rows + ctu - 1) // ctu
+        mask = np.zeros(cols * rows, np.uint8)
+        mask[::every] = 1
+        dep = None if i == ref_i else {"ref_size": (w, h), "leaf_depth": ref_out["leaf_depth"],
+                                       "leaf_mvx": ref_out["leaf_mvx"], "leaf_mvy": ref_out["leaf_mvy"]}
+        t0 = time.perf_counter()
+        oracle.analyze(c2, f2, qp=qp, search_range=wl["R"] if i == ref_i else wl["r"], ctu=ctu, threads=1,
+                       ctu_mask=mask, dep=dep)
+        total += (time.perf_counter() - t0) * mask.size / int(mask.sum())
+        sampled += int(mask.sum())
+    return {"value": 1.0 / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"every {every}th CTU of each rung ({sampled} CTUs), time scaled to the whole frame"}
 
 
 # --------------------------------------------------------- device helpers --

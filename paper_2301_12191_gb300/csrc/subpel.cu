@@ -36,6 +36,16 @@ __constant__ int c_lambda_q16_sp[52] = {
 
 __device__ __forceinline__ int floor4(int v) { return v >> 2; }  // arithmetic shift: floor(v / 4)
 
+// Sample k of a packed word as a float: its bits placed under the exponent
+// of 2^23 by a byte permute, then 2^23 subtracted (exact, no conversion).
+template <typename T>
+__device__ __forceinline__ float word_sample(uint32_t w, int k)
+{
+    const uint32_t sel = sizeof(T) == 1 ? 0x7540u + static_cast<uint32_t>(k)
+                                        : 0x7400u + static_cast<uint32_t>(2 * k) + (static_cast<uint32_t>(2 * k + 1) << 4);
+    return __int_as_float(static_cast<int>(__byte_perm(w, 0x4b000000u, sel))) - 8388608.f;
+}
+
 // 16 consecutive samples X0 .. X0+15 of row y as floats (2^23 + sample
 // would lose nothing, but plain values are exact too: samples < 2^10).
 template <typename T>
@@ -55,7 +65,7 @@ __device__ __forceinline__ void ref_row16(const char *ref, long pitch, int W, in
             for (int m = 0; m < 4; ++m) {
                 const uint32_t a = __funnelshift_r(w[m], w[m + 1], sh);
 #pragma unroll
-                for (int e = 0; e < 4; ++e) s[4 * m + e] = static_cast<float>((a >> (8 * e)) & 0xffu);
+                for (int e = 0; e < 4; ++e) s[4 * m + e] = word_sample<T>(a, e);
             }
             return;
         }
@@ -70,8 +80,8 @@ __device__ __forceinline__ void ref_row16(const char *ref, long pitch, int W, in
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
                 const uint32_t a = __funnelshift_r(w[m], w[m + 1], sh);
-                s[2 * m] = static_cast<float>(a & 0xffffu);
-                s[2 * m + 1] = static_cast<float>(a >> 16);
+                s[2 * m] = word_sample<T>(a, 0);
+                s[2 * m + 1] = word_sample<T>(a, 1);
             }
             return;
         }
@@ -122,15 +132,39 @@ __device__ int satd8_qpel(const char *cur, const char *ref, long pitch, int W, i
     // prediction = clip(floor(acc / 4096 + 1/2)) (exact: acc is an integer, the scaling a power of 2)
     const float maxv = sizeof(T) == 1 ? 255.f : 1023.f;
     const bool cur_fast = px + 8 <= W;
+    constexpr int SPW = dev::Traits<T>::SPW, WPR = 8 / SPW;
 #pragma unroll
     for (int y = 0; y < 8; ++y) {
         const int cy = min(py + y, H - 1);
-        const T *crow = reinterpret_cast<const T *>(cur + static_cast<long>(cy) * pitch);
+        const char *crow = cur + static_cast<long>(cy) * pitch;
+        uint32_t cw[WPR];
+        if (cur_fast) {  // px is a multiple of 8: aligned vector loads
+            if constexpr (WPR == 2) {
+                const uint2 q = __ldg(reinterpret_cast<const uint2 *>(crow + px));
+                cw[0] = q.x;
+                cw[1] = q.y;
+            } else {
+                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(crow + 2 * px));
+                cw[0] = q.x;
+                cw[1] = q.y;
+                cw[2] = q.z;
+                cw[3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < WPR; ++m) {
+                uint32_t w = 0;
+#pragma unroll
+                for (int e = 0; e < SPW; ++e)
+                    w |= static_cast<uint32_t>(__ldg(reinterpret_cast<const T *>(crow) + min(px + m * SPW + e, W - 1)))
+                         << (e * 32 / SPW);
+                cw[m] = w;
+            }
+        }
 #pragma unroll
         for (int x = 0; x < 8; ++x) {
             const float p = fminf(fmaxf(floorf(fmaf(acc[8 * y + x], 1.f / 4096.f, 0.5f)), 0.f), maxv);
-            const float c = static_cast<float>(__ldg(crow + (cur_fast ? px + x : min(px + x, W - 1))));
-            acc[8 * y + x] = c - p;
+            acc[8 * y + x] = word_sample<T>(cw[x / SPW], x % SPW) - p;
         }
     }
     return dev::satd8_transform(acc, mode);
@@ -143,7 +177,7 @@ __device__ __forceinline__ int32_t rate_q(int lam, int qx, int qy)
 }
 
 template <typename T, int CTU>
-__global__ void __launch_bounds__(kSubpelThreads) k_subpel(const __grid_constant__ SubpelBatch b)
+__global__ void __launch_bounds__(kSubpelThreads, 1) k_subpel(const __grid_constant__ SubpelBatch b)
 {
     dev::chain_entry();
     using C = dev::Ctu<CTU>;
@@ -210,6 +244,8 @@ __global__ void __launch_bounds__(kSubpelThreads) k_subpel(const __grid_constant
     for (int step = 2; step >= 1; --step) {
         for (int k = tid; k < C::NKEY * 8; k += kSubpelThreads) (&s_cand[0][0])[k] = 0;
         __syncthreads();
+        // the 8 candidates of one (CU, block) in neighbouring threads: their
+        // reference windows overlap in L1
         for (int w = tid; w < ne * 8; w += kSubpelThreads) {
             const unsigned e = s_ent[w >> 3];
             const int c = w & 7, i = e & 127, blk = e >> 7;
