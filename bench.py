@@ -70,8 +70,8 @@ L2_FLUSH_BYTES = 256 << 20
 # the hash of the kernel sources it was taken on: null once a kernel changes.
 KERNEL_SOURCES = {"full_search": ["me_full.cu", "common.cuh"], "dependent": ["me_dependent.cu", "common.cuh"]}
 TRAFFIC_NCU = {
-    ("full_search", "ladder1080", "9dc7474d94aa"): 598699,
-    ("dependent", "ladder1080", "c2150367c40d"): 8556544,
+    ("full_search", "ladder1080", "7ee2bebe4949"): 602726,
+    ("dependent", "ladder1080", "5d980a981aa3"): 8559936,
 }
 
 
@@ -456,8 +456,8 @@ def run_ours(args, wl):
                     "ms_per_step": ms_qps / K, "extra_ms_per_step": (ms_qps - ms_multi) / K,
                     "ladder_frames_qps_per_s": world * K * (1 + len(qps)) / (ms_qps * 1e-3)}
 
-    # quarter-pel refinement with SATD of every rung of the frame (one launch
-    # per rung, after the frame's analysis), per frame
+    # quarter-pel refinement with SATD of every rung of the frame (two
+    # launches per rung: interpolated planes, refinement), per frame
     subpel = None
     if wl.get("subpel"):
         bufs = [lad.subpel_buffers(r) for r in range(n_rungs)]
@@ -468,7 +468,8 @@ def run_ours(args, wl):
             pl = dplanes[i % n_frames]
             for r in range(n_rungs):
                 L._call(lad.handle, "ladder_refine_subpel", lad.handle, r, 0, pl[r][0].data_ptr(),
-                        pl[r][1].data_ptr(), L._pitch_bytes(pl[r][0]), qp, ctypes.byref(bufs[r][1]), sh2)
+                        pl[r][1].data_ptr(), L._pitch_bytes(pl[r][0]), qp, ctypes.byref(bufs[r][1]),
+                        bufs[r][2].data_ptr(), bufs[r][2].numel(), sh2)
 
         ms_sp = max_over_ranks(timed(step_subpel, K, W))
         lad.kernel_stats(reset=True)
@@ -477,7 +478,7 @@ def run_ours(args, wl):
         st_sp = lad.kernel_stats(reset=True)
         lad.profile(False)
         n_sp, t_sp = st_sp.get("subpel", (0, 0.0))
-        subpel = {"launches_per_step": n_rungs, "ms_per_step": ms_sp / K, "extra_ms_per_step": (ms_sp - ms_multi) / K,
+        subpel = {"launches_per_step": 2 * n_rungs, "ms_per_step": ms_sp / K, "extra_ms_per_step": (ms_sp - ms_multi) / K,
                   "kernel_ms_per_step": t_sp / 3 if n_sp else None,
                   "ladder_frames_per_s": world * K / (ms_sp * 1e-3)}
 

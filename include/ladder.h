@@ -291,8 +291,12 @@ LADDER_API ladder_status ladder_decide_qps(ladder_t *ladder, int rung, int frame
  * laid out as the same fields of ladder_decisions, qmvx / qmvy in
  * quarter-pel units (INT16_MIN where not evaluated), satd / cost at the
  * refined vector; every member for depths 0..dmax must be set.
- * Asynchronous on cuda_stream (one launch); LADDER_E_STATE if the rung of
- * frame_id has not been analysed. */
+ * workspace: caller-owned DEVICE scratch of at least
+ * ladder_subpel_workspace_bytes(ladder, rung) bytes, 256-byte aligned
+ * (LADDER_E_INVAL otherwise), that receives the 16 interpolated phase planes
+ * of ref; calls that share a workspace must be ordered (one stream).
+ * Asynchronous on cuda_stream (two launches: interpolation, refinement);
+ * LADDER_E_STATE if the rung of frame_id has not been analysed. */
 typedef struct {
     int16_t *qmvx[LADDER_MAX_DEPTHS], *qmvy[LADDER_MAX_DEPTHS];
     int32_t *satd[LADDER_MAX_DEPTHS], *cost[LADDER_MAX_DEPTHS], *best[LADDER_MAX_DEPTHS];
@@ -300,9 +304,14 @@ typedef struct {
     uint8_t *leaf_depth;
     int16_t *leaf_qmvx, *leaf_qmvy;
 } ladder_subpel_decisions;
+/* Bytes of the workspace ladder_refine_subpel needs for `rung`: 16 planes
+ * of (W + 8) x (H + 8) samples, the positions -4 .. W+3 by -4 .. H+3 of each
+ * quarter-pel phase (0 for a bad handle or rung). */
+LADDER_API long ladder_subpel_workspace_bytes(const ladder_t *ladder, int rung);
 LADDER_API ladder_status ladder_refine_subpel(ladder_t *ladder, int rung, int frame_id, const void *cur,
                                               const void *ref, long pitch_bytes, int qp,
-                                              const ladder_subpel_decisions *out, void *cuda_stream);
+                                              const ladder_subpel_decisions *out, void *workspace,
+                                              long workspace_bytes, void *cuda_stream);
 
 /* Asynchronous fetch of a whole frame (every rung's decisions), for callers
  * that overlap copies with later analyses.  The frame is packed rung after

@@ -976,12 +976,24 @@ ladder_status fetch_decisions(ladder_t *l, int rung, int frame_id, ladder_decisi
     return ladder_sync(l, cuda_stream);
 }
 
+long ladder_subpel_workspace_bytes(const ladder_t *l, int rung)
+{
+    if (!l || rung < 0 || rung >= l->geo.n_rungs) return 0;
+    const RungGeom &g = l->info[rung].g;
+    return subpel_workspace_layout(l->geo.bit_depth, g.W, g.H, nullptr, nullptr);
+}
+
 ladder_status ladder_refine_subpel(ladder_t *l, int rung, int frame_id, const void *cur, const void *ref,
-                                   long pitch_bytes, int qp, const ladder_subpel_decisions *out, void *cuda_stream)
+                                   long pitch_bytes, int qp, const ladder_subpel_decisions *out, void *workspace,
+                                   long workspace_bytes, void *cuda_stream)
 {
     if (!l || !out) return LADDER_E_INVAL;
     ladder_status st = check_planes(l, rung, cur, ref, pitch_bytes, qp);
     if (st != LADDER_OK) return st;
+    const long need = ladder_subpel_workspace_bytes(l, rung);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || workspace_bytes < need)
+        return fail(l, LADDER_E_INVAL, "workspace must be 256-byte aligned and hold %ld bytes (got %ld)", need,
+                    workspace_bytes);
     Slot *slot = find_slot(l, frame_id);
     if (!slot || !slot->rungs[rung].analysed)
         return fail(l, LADDER_E_STATE, "rung %d of frame %d has not been analysed", rung, frame_id);
@@ -996,6 +1008,8 @@ ladder_status ladder_refine_subpel(ladder_t *l, int rung, int frame_id, const vo
     b.cur = cur;
     b.ref = ref;
     b.pitch_bytes = pitch_bytes;
+    b.planes = static_cast<char *>(workspace);
+    subpel_workspace_layout(l->geo.bit_depth, g.W, g.H, &b.plane_pitch, &b.plane_bytes);
     if (!out->leaf_depth || !out->leaf_qmvx || !out->leaf_qmvy)
         return fail(l, LADDER_E_INVAL, "leaf arrays missing");
     for (int d = 0; d <= g.dmax; ++d) {

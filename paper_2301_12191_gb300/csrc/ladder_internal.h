@@ -318,8 +318,16 @@ struct SubpelBatch {
     int qp, satd_mode;
     const void *cur, *ref;
     long pitch_bytes;
+    // the 16 interpolated planes of ref (phase fy * 4 + fx), each covering
+    // the positions -4 .. W+3 by -4 .. H+3 (subpel_workspace_layout)
+    char *planes;
+    long plane_pitch, plane_bytes;
     DevDecisions out;        // mvx, mvy (quarter-pel), satd, cost, best, split and leaf maps set
 };
+// Bytes of the interpolation workspace of a W x H plane (16 planes), with the
+// row pitch and the bytes of one plane.
+long subpel_workspace_layout(int bit_depth, int W, int H, long *plane_pitch, long *plane_bytes);
+// Two launches: the interpolated planes, then the refinement.
 cudaError_t launch_subpel(int bit_depth, int ctu, const SubpelBatch &b, cudaStream_t s);
 
 // Fills the keys of every block of a batch with ~0 (key initialisation).

@@ -2,33 +2,30 @@
 // finds the quarter-pel vectors, Sec. 5.4.1; the interpolation filters are
 // among the encoder's accelerated kernels, Sec. 6.6).
 //
-// One CTA per CTU.  Every evaluated CU starts at its integer vector (in
-// quarter-pel units, 4 mv) and cost J = SATD + lambda * se-bits; a half-pel
-// round tries the 8 neighbours at +-2 quarter units, a quarter-pel round
-// the 8 neighbours at +-1 of the best so far; a candidate replaces the best
-// only with a strictly lower cost (candidates in raster order).  The split
-// is then decided again over the refined costs (ctu_split).
+// Every evaluated CU starts at its integer vector (in quarter-pel units,
+// 4 mv) and cost J = SATD + lambda * se-bits; a half-pel round tries the 8
+// neighbours at +-2 quarter units, a quarter-pel round the 8 neighbours at
+// +-1 of the best so far; a candidate replaces the best only with a
+// strictly lower cost (candidates in raster order).  The split is then
+// decided again over the refined costs (ctu_split).
 //
 // Prediction (reading: the 8-tap luma filters of HEVC for the phases 0,
 // 1/4, 1/2, 3/4): P = clip(floor((sum_j f_fy[j] sum_i f_fx[i] Ref(X + i - 3,
 // Y + j - 3) + 2^11) / 2^12)) with the reference clamped to the frame.  The
 // two sums are exact in fp32 (|sum| <= 112^2 x 1023 < 2^24), so the
-// filtering runs as fp32 multiply-adds.  Work items are (CU, 8x8 block,
-// candidate) triples, one thread each; block SATDs are summed per CU and
-// candidate in shared memory.
+// filtering runs as fp32 multiply-adds.
+//
+// Two launches.  k_interp writes the 16 phase planes of the reference once
+// (as an encoder interpolates its reference frames once); k_subpel, one CTA
+// per CTU, evaluates (CU, 8x8 block, candidate) work items, one thread each,
+// as the SATD of the current block against a block of one plane, and sums
+// the block SATDs per CU and candidate in shared memory.
 #include "common.cuh"
 
 namespace ladder_impl {
 namespace {
 
-constexpr int kSubpelThreads = 256;
-
-__constant__ float c_qfilt[4][8] = {
-    {0.f, 0.f, 0.f, 64.f, 0.f, 0.f, 0.f, 0.f},
-    {-1.f, 4.f, -10.f, 58.f, 17.f, -5.f, 1.f, 0.f},
-    {-1.f, 4.f, -11.f, 40.f, 40.f, -11.f, 4.f, -1.f},
-    {0.f, 1.f, -5.f, 17.f, 58.f, -10.f, 4.f, -1.f},
-};
+constexpr int kSubpelThreads = 512;
 
 __constant__ int c_lambda_q16_sp[52] = {
 #include "lambda_table.inc"
@@ -36,108 +33,159 @@ __constant__ int c_lambda_q16_sp[52] = {
 
 __device__ __forceinline__ int floor4(int v) { return v >> 2; }  // arithmetic shift: floor(v / 4)
 
-// Sample k of a packed word as a float: its bits placed under the exponent
-// of 2^23 by a byte permute, then 2^23 subtracted (exact, no conversion).
-template <typename T>
-__device__ __forceinline__ float word_sample(uint32_t w, int k)
+// ---- interpolated planes --------------------------------------------------
+// P_(fx,fy)(X, Y) for every phase and every position -4 <= X <= W+3,
+// -4 <= Y <= H+3, stored at plane column X + 4, row Y + 4.  Past those
+// bounds every tap of the filter reads a clamped edge sample, so the value
+// no longer changes: a position outside the plane reads the nearest stored
+// one.  The filter runs as two exact fp32 passes over a tile staged in
+// shared memory (a horizontal pass for the 4 x phases, then a vertical
+// pass for the 4 y phases) and the sum is rounded once.
+
+constexpr int kInterpTW = 32, kInterpTH = 64, kInterpThreads = 256;
+constexpr int kInterpSP = kInterpTW + 12;  // staged row: TW + 7 samples, padded (conflict-free float4 reads)
+constexpr int kInterpHP = kInterpTW + 4;   // horizontal-pass row, padded
+constexpr int kInterpRows = kInterpTH + 7;
+constexpr int kInterpSmem = (kInterpRows * kInterpSP + 4 * kInterpRows * kInterpHP) * 4;
+
+// Tap i of the HEVC luma filter of phase f / 4 (a constant wherever f and i are)
+__device__ __forceinline__ constexpr float qtap(int f, int i)
 {
-    const uint32_t sel = sizeof(T) == 1 ? 0x7540u + static_cast<uint32_t>(k)
-                                        : 0x7400u + static_cast<uint32_t>(2 * k) + (static_cast<uint32_t>(2 * k + 1) << 4);
-    return __int_as_float(static_cast<int>(__byte_perm(w, 0x4b000000u, sel))) - 8388608.f;
+    constexpr float t[4][8] = {
+        {0.f, 0.f, 0.f, 64.f, 0.f, 0.f, 0.f, 0.f},
+        {-1.f, 4.f, -10.f, 58.f, 17.f, -5.f, 1.f, 0.f},
+        {-1.f, 4.f, -11.f, 40.f, 40.f, -11.f, 4.f, -1.f},
+        {0.f, 1.f, -5.f, 17.f, 58.f, -10.f, 4.f, -1.f},
+    };
+    return t[f][i];
 }
 
-// 16 consecutive samples X0 .. X0+15 of row y as floats (2^23 + sample
-// would lose nothing, but plain values are exact too: samples < 2^10).
 template <typename T>
-__device__ __forceinline__ void ref_row16(const char *ref, long pitch, int W, int H, int X0, int y, float (&s)[16])
+__global__ void __launch_bounds__(kInterpThreads, 3) k_interp(const __grid_constant__ SubpelBatch b)
 {
-    constexpr int SPW = dev::Traits<T>::SPW;
-    const char *row = ref + static_cast<long>(min(max(y, 0), H - 1)) * pitch;
-    if constexpr (SPW == 4) {
-        const int q = X0 >> 2;
-        if (X0 >= 0 && 4 * q + 20 <= W) {
-            const uint32_t *rp = reinterpret_cast<const uint32_t *>(row) + q;
-            uint32_t w[5];
+    dev::chain_entry();
+    extern __shared__ __align__(16) float interp_smem[];
+    float *const s_in = interp_smem;                         // [kInterpRows][kInterpSP]
+    float *const s_h = interp_smem + kInterpRows * kInterpSP;  // [4][kInterpRows][kInterpHP]
+    const int W = b.g.W, H = b.g.H, Wp = W + 8, Hp = H + 8;
+    const int u0 = blockIdx.x * kInterpTW, v0 = blockIdx.y * kInterpTH;
+    const int Xs = u0 - 4, Ys = v0 - 4;  // frame position of the tile's first output
+    const T *ref = static_cast<const T *>(b.ref);
+    const long rpitch = b.pitch_bytes / static_cast<long>(sizeof(T));
+    // staged reference: rows Ys-3 .. Ys+TH+3, columns Xs-3 .. Xs+TW+3, clamped
+    constexpr int kStaged = kInterpRows * (kInterpTW + 7);
+    constexpr int kPer = (kStaged + kInterpThreads - 1) / kInterpThreads;
+    T sv[kPer];
 #pragma unroll
-            for (int m = 0; m < 5; ++m) w[m] = __ldg(rp + m);
-            const uint32_t sh = 8u * static_cast<uint32_t>(X0 & 3);
+    for (int n = 0; n < kPer; ++n) {  // every load in flight before the first store
+        const int k = min(static_cast<int>(threadIdx.x) + n * kInterpThreads, kStaged - 1);
+        const int r = k / (kInterpTW + 7), c = k - r * (kInterpTW + 7);
+        const int y = min(max(Ys - 3 + r, 0), H - 1), x = min(max(Xs - 3 + c, 0), W - 1);
+        sv[n] = __ldg(ref + static_cast<long>(y) * rpitch + x);
+    }
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const uint32_t a = __funnelshift_r(w[m], w[m + 1], sh);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) s[4 * m + e] = word_sample<T>(a, e);
-            }
-            return;
-        }
-    } else {
-        const int q = X0 >> 1;
-        if (X0 >= 0 && 2 * q + 18 <= W) {
-            const uint32_t *rp = reinterpret_cast<const uint32_t *>(row) + q;
-            uint32_t w[9];
-#pragma unroll
-            for (int m = 0; m < 9; ++m) w[m] = __ldg(rp + m);
-            const uint32_t sh = 16u * static_cast<uint32_t>(X0 & 1);
-#pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const uint32_t a = __funnelshift_r(w[m], w[m + 1], sh);
-                s[2 * m] = word_sample<T>(a, 0);
-                s[2 * m + 1] = word_sample<T>(a, 1);
-            }
-            return;
+    for (int n = 0; n < kPer; ++n) {
+        const int k = threadIdx.x + n * kInterpThreads;
+        if (k < kStaged) {
+            const int r = k / (kInterpTW + 7), c = k - r * (kInterpTW + 7);
+            s_in[r * kInterpSP + c] = static_cast<float>(sv[n]);
         }
     }
-    const T *rt = reinterpret_cast<const T *>(row);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) s[k] = static_cast<float>(__ldg(rt + min(max(X0 + k, 0), W - 1)));
-}
-
-// SATD of the 8x8 block at (px, py) against the quarter-pel prediction at
-// (qx, qy), by one thread.
-template <typename T>
-__device__ int satd8_qpel(const char *cur, const char *ref, long pitch, int W, int H, int px, int py, int qx, int qy,
-                          int mode)
-{
-    const int X0 = px + floor4(qx) - 3, Y0 = py + floor4(qy) - 3;
-    const int fx = qx & 3, fy = qy & 3;
-    float hf[8], vf[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        hf[i] = c_qfilt[fx][i];
-        vf[i] = c_qfilt[fy][i];
-    }
-    float acc[64];
-#pragma unroll
-    for (int i = 0; i < 64; ++i) acc[i] = 0.f;
-#pragma unroll
-    for (int r = 0; r < 15; ++r) {
+    __syncthreads();
+    // horizontal pass: 8 outputs of one staged row for the 4 x phases
+    for (int k = threadIdx.x; k < kInterpRows * (kInterpTW / 8); k += kInterpThreads) {
+        const int r = k >> 2, xg = (k & 3) * 8;
         float s[16];
-        ref_row16<T>(ref, pitch, W, H, X0, Y0 + r, s);
-        float h[8];
+        const float4 *src = reinterpret_cast<const float4 *>(s_in + r * kInterpSP + xg);
 #pragma unroll
-        for (int x = 0; x < 8; ++x) {
-            float t = 0.f;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) t = fmaf(hf[i], s[x + i], t);
-            h[x] = t;
+        for (int m = 0; m < 4; ++m) {
+            const float4 q = src[m];
+            s[4 * m] = q.x;
+            s[4 * m + 1] = q.y;
+            s[4 * m + 2] = q.z;
+            s[4 * m + 3] = q.w;
         }
+#pragma unroll
+        for (int fx = 0; fx < 4; ++fx) {
+            float h[8];
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                float t = 0.f;
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (qtap(fx, i) != 0.f) t = fmaf(qtap(fx, i), s[x + i], t);
+                h[x] = t;
+            }
+            float4 *dst = reinterpret_cast<float4 *>(s_h + (fx * kInterpRows + r) * kInterpHP + xg);
+            dst[0] = make_float4(h[0], h[1], h[2], h[3]);
+            dst[1] = make_float4(h[4], h[5], h[6], h[7]);
+        }
+    }
+    __syncthreads();
+    // vertical pass: 8 rows x 4 columns of one x phase for the 4 y phases
+    const int xq = threadIdx.x & 7, yg = (threadIdx.x >> 3) & 7, fx = threadIdx.x >> 6;
+    float4 col[15];
+#pragma unroll
+    for (int j = 0; j < 15; ++j)
+        col[j] = *reinterpret_cast<const float4 *>(s_h + (fx * kInterpRows + yg * 8 + j) * kInterpHP + xq * 4);
+    const int u = u0 + xq * 4;
+    // Rounding: the accumulator starts at 2^11, and one multiply-add rounded
+    // toward -inf gives 1.5 * 2^23 + floor(sum / 2^12) exactly (the result
+    // stays in [2^23, 2^24), where the spacing of floats is 1), so the
+    // sample is the low bits of the float's pattern after clamping.
+    constexpr float kBias = 12582912.f;  // 1.5 * 2^23
+    constexpr float kMax = kBias + (sizeof(T) == 1 ? 255.f : 1023.f);
+#pragma unroll
+    for (int fy = 0; fy < 4; ++fy) {
+        char *plane = b.planes + static_cast<long>(fy * 4 + fx) * b.plane_bytes;
 #pragma unroll
         for (int y = 0; y < 8; ++y) {
-            const int j = r - y;
-            if (j >= 0 && j < 8) {
+            float a[4] = {2048.f, 2048.f, 2048.f, 2048.f};
 #pragma unroll
-                for (int x = 0; x < 8; ++x) acc[8 * y + x] = fmaf(vf[j], h[x], acc[8 * y + x]);
+            for (int j = 0; j < 8; ++j) {
+                if (qtap(fy, j) == 0.f) continue;
+                const float f = qtap(fy, j);
+                a[0] = fmaf(f, col[y + j].x, a[0]);
+                a[1] = fmaf(f, col[y + j].y, a[1]);
+                a[2] = fmaf(f, col[y + j].z, a[2]);
+                a[3] = fmaf(f, col[y + j].w, a[3]);
+            }
+            uint32_t q[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                q[e] = __float_as_uint(fminf(fmaxf(__fmaf_rd(a[e], 1.f / 4096.f, kBias), kBias), kMax));
+            const int v = v0 + yg * 8 + y;
+            if (v >= Hp || u >= Wp) continue;
+            char *row = plane + static_cast<long>(v) * b.plane_pitch;
+            if constexpr (sizeof(T) == 1) {
+                const uint32_t lo = __byte_perm(q[0], q[1], 0x0040u), hi = __byte_perm(q[2], q[3], 0x0040u);
+                *reinterpret_cast<uint32_t *>(row + u) = __byte_perm(lo, hi, 0x5410u);
+            } else {
+                *reinterpret_cast<uint2 *>(row + 2 * u) =
+                    make_uint2(__byte_perm(q[0], q[1], 0x5410u), __byte_perm(q[2], q[3], 0x5410u));
             }
         }
     }
-    // prediction = clip(floor(acc / 4096 + 1/2)) (exact: acc is an integer, the scaling a power of 2)
-    const float maxv = sizeof(T) == 1 ? 255.f : 1023.f;
+}
+
+// SATD of the 8x8 block at (px, py) of cur against the block of an
+// interpolated plane whose first sample is at plane column pu, row pv, by
+// one thread.  Plane rows and columns are clamped to the plane.
+template <typename T>
+__device__ int satd8_plane(const char *cur, long pitch, int W, int H, int px, int py, const char *plane, long ppitch,
+                           int Wp, int Hp, int pu, int pv, int mode)
+{
+    constexpr int SPW = dev::Traits<T>::SPW, BITS = 32 / SPW, WPR = 8 / SPW;
     const bool cur_fast = px + 8 <= W;
-    constexpr int SPW = dev::Traits<T>::SPW, WPR = 8 / SPW;
+    const bool pl_fast = pu >= 0 && pu + 8 <= Wp;
+    const uint32_t sh = static_cast<uint32_t>((pu & (SPW - 1)) * BITS);
+    float v[64];
 #pragma unroll
     for (int y = 0; y < 8; ++y) {
         const int cy = min(py + y, H - 1);
         const char *crow = cur + static_cast<long>(cy) * pitch;
-        uint32_t cw[WPR];
+        const char *prow = plane + static_cast<long>(min(max(pv + y, 0), Hp - 1)) * ppitch;
+        uint32_t cw[WPR], pw[WPR];
         if (cur_fast) {  // px is a multiple of 8: aligned vector loads
             if constexpr (WPR == 2) {
                 const uint2 q = __ldg(reinterpret_cast<const uint2 *>(crow + px));
@@ -157,17 +205,36 @@ __device__ int satd8_qpel(const char *cur, const char *ref, long pitch, int W, i
 #pragma unroll
                 for (int e = 0; e < SPW; ++e)
                     w |= static_cast<uint32_t>(__ldg(reinterpret_cast<const T *>(crow) + min(px + m * SPW + e, W - 1)))
-                         << (e * 32 / SPW);
+                         << (e * BITS);
                 cw[m] = w;
             }
         }
+        // The planes were written by the previous launch: plain (coherent,
+        // L1-cached) loads after the grid dependency wait, never the
+        // non-coherent path.
+        if (pl_fast) {  // aligned words + one funnel shift
+            const uint32_t *rp = reinterpret_cast<const uint32_t *>(prow) + pu / SPW;
+            uint32_t raw[WPR + 1];
 #pragma unroll
-        for (int x = 0; x < 8; ++x) {
-            const float p = fminf(fmaxf(floorf(fmaf(acc[8 * y + x], 1.f / 4096.f, 0.5f)), 0.f), maxv);
-            acc[8 * y + x] = word_sample<T>(cw[x / SPW], x % SPW) - p;
+            for (int m = 0; m <= WPR; ++m) raw[m] = rp[m];
+#pragma unroll
+            for (int m = 0; m < WPR; ++m) pw[m] = __funnelshift_r(raw[m], raw[m + 1], sh);
+        } else {
+#pragma unroll
+            for (int m = 0; m < WPR; ++m) {
+                uint32_t w = 0;
+#pragma unroll
+                for (int e = 0; e < SPW; ++e)
+                    w |= static_cast<uint32_t>(reinterpret_cast<const T *>(prow)[min(max(pu + m * SPW + e, 0), Wp - 1)])
+                         << (e * BITS);
+                pw[m] = w;
+            }
         }
+#pragma unroll
+        for (int x = 0; x < 8; ++x)
+            v[8 * y + x] = dev::sample_f<T>(cw[x / SPW], x % SPW) - dev::sample_f<T>(pw[x / SPW], x % SPW);
     }
-    return dev::satd8_transform(acc, mode);
+    return dev::satd8_transform(v, mode);
 }
 
 __device__ __forceinline__ int32_t rate_q(int lam, int qx, int qy)
@@ -193,7 +260,6 @@ __global__ void __launch_bounds__(kSubpelThreads, 1) k_subpel(const __grid_const
     const int lam = c_lambda_q16_sp[b.qp];
     const uint8_t *dep_flags = reinterpret_cast<const uint8_t *>(b.block + b.off.dep_flags) +
                                static_cast<long>(ctu_idx) * C::NKEY;
-    if (tid == 0) s_ne = 0;
     // the CU's flags, its integer vector in quarter units and its cost
     for (int i = tid; i < C::NKEY; i += kSubpelThreads) {
         int d = 0;
@@ -224,36 +290,59 @@ __global__ void __launch_bounds__(kSubpelThreads, 1) k_subpel(const __grid_const
         }
     }
     __syncthreads();
-    // (CU, 8x8 block) entries of the evaluated CUs: CU | block << 7
-    for (int i = tid; i < C::NKEY; i += kSubpelThreads) {
-        if (!(st.flags[i] & kRuleEvaluated)) continue;
-        int d = 0;
-        while (d < C::DMAX && i >= key_offset(d + 1)) ++d;
-        const int li = i - key_offset(d), n = 1 << d, S = CTU >> d, nb = S / 8;
-        const int bx0 = (li % n) * nb, by0 = (li / n) * nb;
-        const int base = atomicAdd(&s_ne, nb * nb);
-        for (int k = 0; k < nb * nb; ++k) {
-            const int blk = (by0 + k / nb) * C::N8 + bx0 + k % nb;
-            s_ent[base + k] = static_cast<uint16_t>(i | (blk << 7));
-        }
-    }
-    __syncthreads();
-    const int ne = s_ne;
-    const char *cur = static_cast<const char *>(b.cur), *ref = static_cast<const char *>(b.ref);
+    const char *cur = static_cast<const char *>(b.cur);
 #pragma unroll 1
     for (int step = 2; step >= 1; --step) {
+        if (tid == 0) s_ne = 0;
         for (int k = tid; k < C::NKEY * 8; k += kSubpelThreads) (&s_cand[0][0])[k] = 0;
         __syncthreads();
-        // the 8 candidates of one (CU, block) in neighbouring threads: their
-        // reference windows overlap in L1
+        // Work list: one entry per distinct (8x8 block, centre) among the
+        // evaluated CUs covering the block (a CU and its sub-CUs often share
+        // a centre): block | (depths sharing it) << 8.  Block SATDs are exact
+        // integers, so the order of the additions does not matter.
+        for (int blk = tid; blk < C::NB8; blk += kSubpelThreads) {
+            const int bx = blk % C::N8, by = blk / C::N8;
+            int ci[C::DMAX + 1];
+            unsigned left = 0;
+#pragma unroll
+            for (int d = 0; d <= C::DMAX; ++d) {
+                const int S = CTU >> d;
+                ci[d] = dev::key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S);
+                if (st.flags[ci[d]] & kRuleEvaluated) left |= 1u << d;
+            }
+#pragma unroll
+            for (int d = 0; d <= C::DMAX; ++d) {
+                if (!((left >> d) & 1u)) continue;
+                unsigned mask = 1u << d;
+#pragma unroll
+                for (int e = d + 1; e <= C::DMAX; ++e)
+                    if (((left >> e) & 1u) && st.mvx[ci[e]] == st.mvx[ci[d]] && st.mvy[ci[e]] == st.mvy[ci[d]])
+                        mask |= 1u << e;
+                left &= ~mask;
+                s_ent[atomicAdd(&s_ne, 1)] = static_cast<uint16_t>(blk | (mask << 8));
+            }
+        }
+        __syncthreads();
+        const int ne = s_ne;
+        // the 8 candidates of one entry in neighbouring threads: their plane
+        // reads overlap in L1
         for (int w = tid; w < ne * 8; w += kSubpelThreads) {
             const unsigned e = s_ent[w >> 3];
-            const int c = w & 7, i = e & 127, blk = e >> 7;
+            const int c = w & 7, blk = e & 0xff, bx = blk % C::N8, by = blk / C::N8;
+            const int d0 = __ffs(e >> 8) - 1, S0 = CTU >> d0;
+            const int i0 = dev::key_index(d0, ((by * 8) / S0) * (1 << d0) + (bx * 8) / S0);
             const int cc = c < 4 ? c : c + 1;  // raster 3x3 without the centre
-            const int qx = st.mvx[i] + step * (cc % 3 - 1), qy = st.mvy[i] + step * (cc / 3 - 1);
-            const int v = satd8_qpel<T>(cur, ref, b.pitch_bytes, g.W, g.H, x0 + 8 * (blk % C::N8),
-                                        y0 + 8 * (blk / C::N8), qx, qy, b.satd_mode);
-            atomicAdd(&s_cand[i][c], v);
+            const int qx = st.mvx[i0] + step * (cc % 3 - 1), qy = st.mvy[i0] + step * (cc / 3 - 1);
+            const int px = x0 + 8 * bx, py = y0 + 8 * by;
+            const char *plane = b.planes + static_cast<long>((qy & 3) * 4 + (qx & 3)) * b.plane_bytes;
+            const int v = satd8_plane<T>(cur, b.pitch_bytes, g.W, g.H, px, py, plane, b.plane_pitch, g.W + 8,
+                                         g.H + 8, px + floor4(qx) + 4, py + floor4(qy) + 4, b.satd_mode);
+#pragma unroll
+            for (int d = d0; d <= C::DMAX; ++d) {
+                if (!((e >> (8 + d)) & 1u)) continue;
+                const int S = CTU >> d;
+                atomicAdd(&s_cand[dev::key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S)][c], v);
+            }
         }
         __syncthreads();
         for (int i = tid; i < C::NKEY; i += kSubpelThreads) {
@@ -285,13 +374,39 @@ __global__ void __launch_bounds__(kSubpelThreads, 1) k_subpel(const __grid_const
 
 }  // namespace
 
+long subpel_workspace_layout(int bit_depth, int W, int H, long *plane_pitch, long *plane_bytes)
+{
+    const long ss = bit_depth == 8 ? 1 : 2;
+    // W + 8 stored columns, 8 more for the word loads past a row's last block
+    const long pitch = ((static_cast<long>(W) + 16) * ss + 63) / 64 * 64;
+    const long bytes = (pitch * (H + 8) + 255) / 256 * 256;
+    if (plane_pitch) *plane_pitch = pitch;
+    if (plane_bytes) *plane_bytes = bytes;
+    return 16 * bytes;
+}
+
+template <typename T> cudaError_t interp_smem_attr()
+{
+    static const cudaError_t e =
+        cudaFuncSetAttribute(k_interp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kInterpSmem);
+    return e;
+}
+
 cudaError_t launch_subpel(int bit_depth, int ctu, const SubpelBatch &b, cudaStream_t s)
 {
+    const dim3 igrid((b.g.W + 8 + kInterpTW - 1) / kInterpTW, (b.g.H + 8 + kInterpTH - 1) / kInterpTH);
     const dim3 grid(b.g.ctu_cols * b.g.ctu_rows);
+    cudaError_t e;
     if (bit_depth == 8) {
+        if ((e = interp_smem_attr<uint8_t>()) != cudaSuccess) return e;
+        if ((e = launch_chained(k_interp<uint8_t>, igrid, dim3(kInterpThreads), kInterpSmem, s, b)) != cudaSuccess)
+            return e;
         auto kern = ctu == 64 ? k_subpel<uint8_t, 64> : ctu == 32 ? k_subpel<uint8_t, 32> : k_subpel<uint8_t, 16>;
         return launch_chained(kern, grid, dim3(kSubpelThreads), 0, s, b);
     }
+    if ((e = interp_smem_attr<uint16_t>()) != cudaSuccess) return e;
+    if ((e = launch_chained(k_interp<uint16_t>, igrid, dim3(kInterpThreads), kInterpSmem, s, b)) != cudaSuccess)
+        return e;
     auto kern = ctu == 64 ? k_subpel<uint16_t, 64> : ctu == 32 ? k_subpel<uint16_t, 32> : k_subpel<uint16_t, 16>;
     return launch_chained(kern, grid, dim3(kSubpelThreads), 0, s, b);
 }

@@ -99,7 +99,9 @@ SIGNATURES = [
     ("ladder_set_parents", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     ("ladder_refine_subpel", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_long, ctypes.c_int,
-                                            ctypes.POINTER(SubpelDecisions), ctypes.c_void_p]),
+                                            ctypes.POINTER(SubpelDecisions), ctypes.c_void_p, ctypes.c_long,
+                                            ctypes.c_void_p]),
+    ("ladder_subpel_workspace_bytes", ctypes.c_long, [ctypes.c_void_p, ctypes.c_int]),
     ("ladder_frame_bytes", ctypes.c_long, [ctypes.c_void_p]),
     ("ladder_decision_offsets", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_long)]),
     ("ladder_fetch_frame_async", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_long,
@@ -469,7 +471,7 @@ class Ladder:
 
     def subpel_buffers(self, rung):
         """Device arrays for ladder_refine_subpel of `rung`: (tensors dict,
-        SubpelDecisions struct pointing at them)."""
+        SubpelDecisions struct pointing at them, interpolation workspace)."""
         import torch
 
         dims, (c8, r8) = self.grid(rung)
@@ -486,7 +488,8 @@ class Ladder:
             a = torch.empty(c8 * r8, dtype=dt, device=dev)
             t[k] = a
             setattr(o, k, a.data_ptr())
-        return t, o
+        ws = torch.empty(int(load().ladder_subpel_workspace_bytes(self.handle, rung)), dtype=torch.uint8, device=dev)
+        return t, o, ws
 
     def refine_subpel(self, rung, frame_id, cur, ref, qp, stream=None, buffers=None) -> dict:
         """Quarter-pel refinement of an analysed (rung, frame): returns the
@@ -494,10 +497,10 @@ class Ladder:
         waiting for the stream; `buffers` = subpel_buffers(rung) to reuse."""
         import torch
 
-        t, o = buffers if buffers is not None else self.subpel_buffers(rung)
+        t, o, ws = buffers if buffers is not None else self.subpel_buffers(rung)
         s = _stream_handle(stream)
         _call(self.handle, "ladder_refine_subpel", self.handle, rung, frame_id, cur.data_ptr(), ref.data_ptr(),
-              _pitch_bytes(cur), qp, ctypes.byref(o), s)
+              _pitch_bytes(cur), qp, ctypes.byref(o), ws.data_ptr(), ws.numel(), s)
         (stream or torch.cuda.current_stream()).synchronize()
         out = {k: ([a.cpu().numpy() for a in v] if isinstance(v, list) else v.cpu().numpy()) for k, v in t.items()}
         out["grid"], out["grid8"] = self.grid(rung)

@@ -55,3 +55,62 @@ def test_subpel_needs_an_analysis():
         c, f = L.device_plane(p.cur), L.device_plane(p.ref)
         with pytest.raises(L.LadderError):
             lad.refine_subpel(0, 0, c, f, 27)
+
+
+@pytest.mark.parametrize("bd,W,H,gmv,ctu", [(8, 72, 40, (14, -11), 32), (10, 40, 24, (-13, 9), 16),
+                                             (8, 18, 16, (3, -2), 16)])
+def test_subpel_edges(bd, W, H, gmv, ctu):
+    """Vectors that reach past the frame (prediction from clamped samples),
+    ragged CTUs and a frame of the smallest size a ladder accepts."""
+    p = synth.frame_pair(29, W, H, bit_depth=bd, global_mv=gmv, patch_size=8)
+    R, qp = 16, 25
+    with L.Ladder([(W, H)], 0, bit_depth=bd, ctu_size=ctu, search_range=R, max_frames=1) as lad:
+        c, f = L.device_plane(p.cur), L.device_plane(p.ref)
+        lad.analyze_reference(0, c, f, qp)
+        got = lad.refine_subpel(0, 0, c, f, qp)
+    ana = oracle.analyze(p.cur, p.ref, qp=qp, search_range=R, ctu=ctu)
+    want = oracle.refine_subpel(p.cur, p.ref, ana, qp=qp, ctu=ctu)
+    _check(got, want, f"{W}x{H} bd{bd}")
+
+
+def test_subpel_workspace_checked():
+    import ctypes
+    with L.Ladder([(64, 48)], 0, ctu_size=32, search_range=4, max_frames=1) as lad:
+        p = synth.frame_pair(4, 64, 48)
+        c, f = L.device_plane(p.cur), L.device_plane(p.ref)
+        lad.analyze_reference(0, c, f, 27)
+        need = int(L.load().ladder_subpel_workspace_bytes(lad.handle, 0))
+        assert need >= 16 * 56 * 72 and int(L.load().ladder_subpel_workspace_bytes(lad.handle, 1)) == 0
+        t, o, ws = lad.subpel_buffers(0)
+        with pytest.raises(L.LadderError):
+            L._call(lad.handle, "ladder_refine_subpel", lad.handle, 0, 0, c.data_ptr(), f.data_ptr(),
+                    L._pitch_bytes(c), 27, ctypes.byref(o), ws.data_ptr(), need - 1, None)
+        with pytest.raises(L.LadderError):
+            L._call(lad.handle, "ladder_refine_subpel", lad.handle, 0, 0, c.data_ptr(), f.data_ptr(),
+                    L._pitch_bytes(c), 27, ctypes.byref(o), ws.data_ptr() + 16, need, None)
+
+
+def test_subpel_workspace_reused_across_frames():
+    """One workspace, two frames with different references, back to back on
+    one stream: each refinement sees its own interpolated planes."""
+    W, H, R, qp = 136, 72, 8, 27
+    ps = [synth.frame_pair(40 + k, W, H, global_mv=(3 - 5 * k, 2 * k - 1)) for k in range(2)]
+    with L.Ladder([(W, H)], 0, ctu_size=32, search_range=R, max_frames=2) as lad:
+        dev = [(L.device_plane(p.cur), L.device_plane(p.ref)) for p in ps]
+        bufs = [lad.subpel_buffers(0) for _ in range(2)]
+        ws = bufs[0][2]
+        for k in range(2):
+            lad.analyze_reference(k, *dev[k], qp)
+        import ctypes
+        s = torch.cuda.current_stream()
+        for k in range(2):
+            L._call(lad.handle, "ladder_refine_subpel", lad.handle, 0, k, dev[k][0].data_ptr(), dev[k][1].data_ptr(),
+                    L._pitch_bytes(dev[k][0]), qp, ctypes.byref(bufs[k][1]), ws.data_ptr(), ws.numel(),
+                    ctypes.c_void_p(s.cuda_stream))
+        s.synchronize()
+        got = [{k: ([a.cpu().numpy() for a in v] if isinstance(v, list) else v.cpu().numpy())
+                for k, v in bufs[i][0].items()} for i in range(2)]
+    for k, p in enumerate(ps):
+        ana = oracle.analyze(p.cur, p.ref, qp=qp, search_range=R, ctu=32)
+        want = oracle.refine_subpel(p.cur, p.ref, ana, qp=qp, ctu=32)
+        _check(got[k], want, f"frame {k}")
