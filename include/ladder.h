@@ -313,6 +313,27 @@ LADDER_API ladder_status ladder_refine_subpel(ladder_t *ladder, int rung, int fr
                                               const ladder_subpel_decisions *out, void *workspace,
                                               long workspace_bytes, void *cuda_stream);
 
+/* Several quarter-pel refinements in one pair of launches (e.g. every rung
+ * of a frame): job k is ladder_refine_subpel(ladder, jobs[k].rung,
+ * jobs[k].frame_id, jobs[k].cur, jobs[k].ref, jobs[k].pitch_bytes,
+ * jobs[k].qp, jobs[k].out, jobs[k].workspace, jobs[k].workspace_bytes),
+ * with the same checks; the jobs' workspaces and outputs must not overlap.
+ * Small rungs leave most of the GPU idle on their own; batched, their CTAs
+ * run beside the large rungs'.  1 <= n <= LADDER_MAX_SUBPEL_JOBS
+ * (LADDER_E_INVAL otherwise); nothing is launched if any job fails its
+ * checks. */
+#define LADDER_MAX_SUBPEL_JOBS 16
+typedef struct {
+    int frame_id, rung, qp;
+    const void *cur, *ref;
+    long pitch_bytes;
+    const ladder_subpel_decisions *out;
+    void *workspace;
+    long workspace_bytes;
+} ladder_subpel_job;
+LADDER_API ladder_status ladder_refine_subpel_batch(ladder_t *ladder, int n, const ladder_subpel_job *jobs,
+                                                    void *cuda_stream);
+
 /* Asynchronous fetch of a whole frame (every rung's decisions), for callers
  * that overlap copies with later analyses.  The frame is packed rung after
  * rung, ladder_frame_bytes() bytes in all; ladder_decision_offsets() gives

@@ -983,52 +983,103 @@ long ladder_subpel_workspace_bytes(const ladder_t *l, int rung)
     return subpel_workspace_layout(l->geo.bit_depth, g.W, g.H, nullptr, nullptr);
 }
 
-ladder_status ladder_refine_subpel(ladder_t *l, int rung, int frame_id, const void *cur, const void *ref,
-                                   long pitch_bytes, int qp, const ladder_subpel_decisions *out, void *workspace,
-                                   long workspace_bytes, void *cuda_stream)
+namespace {
+
+// Validates one refinement job and fills its launch item (CTA ranges unset).
+ladder_status subpel_item(ladder_t *l, const ladder_subpel_job &j, SubpelItem &it)
 {
-    if (!l || !out) return LADDER_E_INVAL;
-    ladder_status st = check_planes(l, rung, cur, ref, pitch_bytes, qp);
+    ladder_status st = check_planes(l, j.rung, j.cur, j.ref, j.pitch_bytes, j.qp);
     if (st != LADDER_OK) return st;
-    const long need = ladder_subpel_workspace_bytes(l, rung);
-    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || workspace_bytes < need)
+    const ladder_subpel_decisions *out = j.out;
+    if (!out) return fail(l, LADDER_E_INVAL, "null output arrays");
+    const long need = ladder_subpel_workspace_bytes(l, j.rung);
+    if (!j.workspace || (reinterpret_cast<uintptr_t>(j.workspace) & 255) || j.workspace_bytes < need)
         return fail(l, LADDER_E_INVAL, "workspace must be 256-byte aligned and hold %ld bytes (got %ld)", need,
-                    workspace_bytes);
-    Slot *slot = find_slot(l, frame_id);
-    if (!slot || !slot->rungs[rung].analysed)
-        return fail(l, LADDER_E_STATE, "rung %d of frame %d has not been analysed", rung, frame_id);
-    const RungGeom &g = l->info[rung].g;
-    SubpelBatch b{};
-    b.g = g;
-    b.off = l->info[rung].off;
-    b.block = slot->rungs[rung].block;
-    b.dependent = slot->rungs[rung].analysed == 2;
-    b.qp = qp;
-    b.satd_mode = l->geo.satd_mode;
-    b.cur = cur;
-    b.ref = ref;
-    b.pitch_bytes = pitch_bytes;
-    b.planes = static_cast<char *>(workspace);
-    subpel_workspace_layout(l->geo.bit_depth, g.W, g.H, &b.plane_pitch, &b.plane_bytes);
+                    j.workspace_bytes);
+    Slot *slot = find_slot(l, j.frame_id);
+    if (!slot || !slot->rungs[j.rung].analysed)
+        return fail(l, LADDER_E_STATE, "rung %d of frame %d has not been analysed", j.rung, j.frame_id);
+    const RungGeom &g = l->info[j.rung].g;
+    it = SubpelItem{};
+    it.g = g;
+    it.off = l->info[j.rung].off;
+    it.block = slot->rungs[j.rung].block;
+    it.dependent = slot->rungs[j.rung].analysed == 2;
+    it.qp = j.qp;
+    it.cur = j.cur;
+    it.ref = j.ref;
+    it.pitch_bytes = j.pitch_bytes;
+    it.planes = static_cast<char *>(j.workspace);
+    subpel_workspace_layout(l->geo.bit_depth, g.W, g.H, &it.plane_pitch, &it.plane_bytes);
     if (!out->leaf_depth || !out->leaf_qmvx || !out->leaf_qmvy)
         return fail(l, LADDER_E_INVAL, "leaf arrays missing");
     for (int d = 0; d <= g.dmax; ++d) {
         if (!out->qmvx[d] || !out->qmvy[d] || !out->satd[d] || !out->cost[d] || !out->best[d] || !out->split[d])
             return fail(l, LADDER_E_INVAL, "depth %d arrays missing", d);
-        b.out.mvx[d] = out->qmvx[d];
-        b.out.mvy[d] = out->qmvy[d];
-        b.out.satd[d] = out->satd[d];
-        b.out.cost[d] = out->cost[d];
-        b.out.best[d] = out->best[d];
-        b.out.split[d] = out->split[d];
+        it.out.mvx[d] = out->qmvx[d];
+        it.out.mvy[d] = out->qmvy[d];
+        it.out.satd[d] = out->satd[d];
+        it.out.cost[d] = out->cost[d];
+        it.out.best[d] = out->best[d];
+        it.out.split[d] = out->split[d];
     }
-    b.out.leaf_depth = out->leaf_depth;
-    b.out.leaf_mvx = out->leaf_qmvx;
-    b.out.leaf_mvy = out->leaf_qmvy;
+    it.out.leaf_depth = out->leaf_depth;
+    it.out.leaf_mvx = out->leaf_qmvx;
+    it.out.leaf_mvy = out->leaf_qmvy;
+    return LADDER_OK;
+}
+
+}  // namespace
+
+ladder_status ladder_refine_subpel_batch(ladder_t *l, int n, const ladder_subpel_job *jobs, void *cuda_stream)
+{
+    if (!l || !jobs) return LADDER_E_INVAL;
+    if (n < 1 || n > LADDER_MAX_SUBPEL_JOBS)
+        return fail(l, LADDER_E_INVAL, "%d jobs: 1 .. %d per call", n, LADDER_MAX_SUBPEL_JOBS);
+    static_assert(LADDER_MAX_SUBPEL_JOBS == kMaxSubpelItems, "job table size");
+    static_assert(sizeof(SubpelBatch) <= 32000, "kernel parameter space");
+    auto *b = new (std::nothrow) SubpelBatch{};
+    if (!b) return fail(l, LADDER_E_NOMEM, "batch table");
+    // independently analysed jobs (every depth evaluated: the longest CTAs) first
+    int order[LADDER_MAX_SUBPEL_JOBS], m = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int k = 0; k < n; ++k) {
+            const Slot *slot = find_slot(l, jobs[k].frame_id);
+            const bool indep = slot && jobs[k].rung >= 0 && jobs[k].rung < l->geo.n_rungs &&
+                               slot->rungs[jobs[k].rung].analysed == 1;
+            if (indep == (pass == 0)) order[m++] = k;
+        }
+    int ctas = 0, ictas = 0;
+    for (int k = 0; k < n; ++k) {
+        SubpelItem &it = b->item[k];
+        const ladder_status st = subpel_item(l, jobs[order[k]], it);
+        if (st != LADDER_OK) {
+            delete b;
+            return st;
+        }
+        int rows = 0;
+        subpel_interp_tiles(it.g.W, it.g.H, &it.icols, &rows);
+        it.cta_begin = ctas;
+        it.icta_begin = ictas;
+        ctas += it.g.ctu_cols * it.g.ctu_rows;
+        ictas += it.icols * rows;
+    }
+    b->n = n;
+    b->satd_mode = l->geo.satd_mode;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    const cudaError_t e = traced(l, 7, s, [&] { return launch_subpel(l->geo.bit_depth, l->geo.ctu_size, b, s); });
+    const cudaError_t e =
+        traced(l, 7, s, [&] { return launch_subpel(l->geo.bit_depth, l->geo.ctu_size, *b, ctas, ictas, s); });
+    delete b;
     if (e != cudaSuccess) return cuda_fail(l, e, "quarter-pel refinement");
     return LADDER_OK;
+}
+
+ladder_status ladder_refine_subpel(ladder_t *l, int rung, int frame_id, const void *cur, const void *ref,
+                                   long pitch_bytes, int qp, const ladder_subpel_decisions *out, void *workspace,
+                                   long workspace_bytes, void *cuda_stream)
+{
+    const ladder_subpel_job j{frame_id, rung, qp, cur, ref, pitch_bytes, out, workspace, workspace_bytes};
+    return ladder_refine_subpel_batch(l, 1, &j, cuda_stream);
 }
 
 long ladder_frame_bytes(const ladder_t *l)

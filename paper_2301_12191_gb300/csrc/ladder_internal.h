@@ -310,12 +310,15 @@ struct QpBatch {
 cudaError_t launch_decide_qps(int ctu, const QpBatch &b, cudaStream_t s);
 
 // Quarter-pel refinement of one analysed rung: one CTA per CTU.
-struct SubpelBatch {
+// One (frame, rung) job of a quarter-pel refinement launch.
+struct SubpelItem {
+    int cta_begin;           // first refinement CTA (one per CTU)
+    int icta_begin, icols;   // first interpolation CTA; interpolation tiles per row
     RungGeom g;
     DecOffsets off;
     const char *block;       // the (slot, rung) decision block
     int dependent;           // 1: rule flags of the dependent analysis; 0: flags of the geometry
-    int qp, satd_mode;
+    int qp;
     const void *cur, *ref;
     long pitch_bytes;
     // the 16 interpolated planes of ref (phase fy * 4 + fx), each covering
@@ -324,11 +327,20 @@ struct SubpelBatch {
     long plane_pitch, plane_bytes;
     DevDecisions out;        // mvx, mvy (quarter-pel), satd, cost, best, split and leaf maps set
 };
+constexpr int kMaxSubpelItems = 16;
+struct SubpelBatch {
+    int n;
+    int satd_mode;
+    SubpelItem item[kMaxSubpelItems];
+};
 // Bytes of the interpolation workspace of a W x H plane (16 planes), with the
 // row pitch and the bytes of one plane.
 long subpel_workspace_layout(int bit_depth, int W, int H, long *plane_pitch, long *plane_bytes);
-// Two launches: the interpolated planes, then the refinement.
-cudaError_t launch_subpel(int bit_depth, int ctu, const SubpelBatch &b, cudaStream_t s);
+// Interpolation tiles of a W x H plane: (columns, rows).
+void subpel_interp_tiles(int W, int H, int *cols, int *rows);
+// Two launches: the interpolated planes of every job, then the refinements
+// (the items' CTA ranges set by the caller, in item order).
+cudaError_t launch_subpel(int bit_depth, int ctu, const SubpelBatch &b, int ctas, int interp_ctas, cudaStream_t s);
 
 // Fills the keys of every block of a batch with ~0 (key initialisation).
 struct FillItem {

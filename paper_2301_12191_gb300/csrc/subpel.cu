@@ -60,15 +60,30 @@ __device__ __forceinline__ constexpr float qtap(int f, int i)
     return t[f][i];
 }
 
+// Index of the job whose CTA range (interpolation or refinement) holds this CTA.
+__device__ __forceinline__ int job_of_cta(const SubpelBatch &bb, bool interp)
+{
+    int lo = 0, hi = bb.n - 1;
+    const int c = static_cast<int>(blockIdx.x);
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (c >= (interp ? bb.item[mid].icta_begin : bb.item[mid].cta_begin)) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kInterpThreads, 3) k_interp(const __grid_constant__ SubpelBatch b)
+__global__ void __launch_bounds__(kInterpThreads, 3) k_interp(const __grid_constant__ SubpelBatch bb)
 {
     dev::chain_entry();
     extern __shared__ __align__(16) float interp_smem[];
     float *const s_in = interp_smem;                         // [kInterpRows][kInterpSP]
     float *const s_h = interp_smem + kInterpRows * kInterpSP;  // [4][kInterpRows][kInterpHP]
+    const SubpelItem &b = bb.item[job_of_cta(bb, true)];
     const int W = b.g.W, H = b.g.H, Wp = W + 8, Hp = H + 8;
-    const int u0 = blockIdx.x * kInterpTW, v0 = blockIdx.y * kInterpTH;
+    const int tile = static_cast<int>(blockIdx.x) - b.icta_begin;
+    const int u0 = (tile % b.icols) * kInterpTW, v0 = (tile / b.icols) * kInterpTH;
     const int Xs = u0 - 4, Ys = v0 - 4;  // frame position of the tile's first output
     const T *ref = static_cast<const T *>(b.ref);
     const long rpitch = b.pitch_bytes / static_cast<long>(sizeof(T));
@@ -244,7 +259,7 @@ __device__ __forceinline__ int32_t rate_q(int lam, int qx, int qy)
 }
 
 template <typename T, int CTU>
-__global__ void __launch_bounds__(kSubpelThreads, 1) k_subpel(const __grid_constant__ SubpelBatch b)
+__global__ void __launch_bounds__(kSubpelThreads, 1) k_subpel(const __grid_constant__ SubpelBatch bb)
 {
     dev::chain_entry();
     using C = dev::Ctu<CTU>;
@@ -253,9 +268,10 @@ __global__ void __launch_bounds__(kSubpelThreads, 1) k_subpel(const __grid_const
     __shared__ int32_t s_cand[C::NKEY][8];
     __shared__ uint16_t s_ent[(C::DMAX + 1) * C::NB8];
     __shared__ int s_ne;
+    const SubpelItem &b = bb.item[job_of_cta(bb, false)];
     const RungGeom &g = b.g;
     const int tid = threadIdx.x;
-    const int ctu_idx = blockIdx.x;
+    const int ctu_idx = static_cast<int>(blockIdx.x) - b.cta_begin;
     const int x0 = (ctu_idx % g.ctu_cols) * CTU, y0 = (ctu_idx / g.ctu_cols) * CTU;
     const int lam = c_lambda_q16_sp[b.qp];
     const uint8_t *dep_flags = reinterpret_cast<const uint8_t *>(b.block + b.off.dep_flags) +
@@ -336,7 +352,7 @@ __global__ void __launch_bounds__(kSubpelThreads, 1) k_subpel(const __grid_const
             const int px = x0 + 8 * bx, py = y0 + 8 * by;
             const char *plane = b.planes + static_cast<long>((qy & 3) * 4 + (qx & 3)) * b.plane_bytes;
             const int v = satd8_plane<T>(cur, b.pitch_bytes, g.W, g.H, px, py, plane, b.plane_pitch, g.W + 8,
-                                         g.H + 8, px + floor4(qx) + 4, py + floor4(qy) + 4, b.satd_mode);
+                                         g.H + 8, px + floor4(qx) + 4, py + floor4(qy) + 4, bb.satd_mode);
 #pragma unroll
             for (int d = d0; d <= C::DMAX; ++d) {
                 if (!((e >> (8 + d)) & 1u)) continue;
@@ -392,23 +408,29 @@ template <typename T> cudaError_t interp_smem_attr()
     return e;
 }
 
-cudaError_t launch_subpel(int bit_depth, int ctu, const SubpelBatch &b, cudaStream_t s)
+void subpel_interp_tiles(int W, int H, int *cols, int *rows)
 {
-    const dim3 igrid((b.g.W + 8 + kInterpTW - 1) / kInterpTW, (b.g.H + 8 + kInterpTH - 1) / kInterpTH);
-    const dim3 grid(b.g.ctu_cols * b.g.ctu_rows);
+    *cols = (W + 8 + kInterpTW - 1) / kInterpTW;
+    *rows = (H + 8 + kInterpTH - 1) / kInterpTH;
+}
+
+cudaError_t launch_subpel(int bit_depth, int ctu, const SubpelBatch &b, int ctas, int interp_ctas, cudaStream_t s)
+{
     cudaError_t e;
     if (bit_depth == 8) {
         if ((e = interp_smem_attr<uint8_t>()) != cudaSuccess) return e;
-        if ((e = launch_chained(k_interp<uint8_t>, igrid, dim3(kInterpThreads), kInterpSmem, s, b)) != cudaSuccess)
+        if ((e = launch_chained(k_interp<uint8_t>, dim3(interp_ctas), dim3(kInterpThreads), kInterpSmem, s, b)) !=
+            cudaSuccess)
             return e;
         auto kern = ctu == 64 ? k_subpel<uint8_t, 64> : ctu == 32 ? k_subpel<uint8_t, 32> : k_subpel<uint8_t, 16>;
-        return launch_chained(kern, grid, dim3(kSubpelThreads), 0, s, b);
+        return launch_chained(kern, dim3(ctas), dim3(kSubpelThreads), 0, s, b);
     }
     if ((e = interp_smem_attr<uint16_t>()) != cudaSuccess) return e;
-    if ((e = launch_chained(k_interp<uint16_t>, igrid, dim3(kInterpThreads), kInterpSmem, s, b)) != cudaSuccess)
+    if ((e = launch_chained(k_interp<uint16_t>, dim3(interp_ctas), dim3(kInterpThreads), kInterpSmem, s, b)) !=
+        cudaSuccess)
         return e;
     auto kern = ctu == 64 ? k_subpel<uint16_t, 64> : ctu == 32 ? k_subpel<uint16_t, 32> : k_subpel<uint16_t, 16>;
-    return launch_chained(kern, grid, dim3(kSubpelThreads), 0, s, b);
+    return launch_chained(kern, dim3(ctas), dim3(kSubpelThreads), 0, s, b);
 }
 
 }  // namespace ladder_impl

@@ -63,6 +63,16 @@ class SubpelDecisions(ctypes.Structure):
                 ("leaf_depth", ctypes.c_void_p), ("leaf_qmvx", ctypes.c_void_p), ("leaf_qmvy", ctypes.c_void_p)]
 
 
+class SubpelJob(ctypes.Structure):
+    _fields_ = [("frame_id", ctypes.c_int), ("rung", ctypes.c_int), ("qp", ctypes.c_int),
+                ("cur", ctypes.c_void_p), ("ref", ctypes.c_void_p), ("pitch_bytes", ctypes.c_long),
+                ("out", ctypes.POINTER(SubpelDecisions)), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_long)]
+
+
+MAX_SUBPEL_JOBS = 16
+
+
 class Job(ctypes.Structure):
     _fields_ = [("frame_id", ctypes.c_int), ("rung", ctypes.c_int), ("kind", ctypes.c_int), ("qp", ctypes.c_int),
                 ("cur", ctypes.c_void_p), ("ref", ctypes.c_void_p), ("pitch_bytes", ctypes.c_long)]
@@ -102,6 +112,8 @@ SIGNATURES = [
                                             ctypes.POINTER(SubpelDecisions), ctypes.c_void_p, ctypes.c_long,
                                             ctypes.c_void_p]),
     ("ladder_subpel_workspace_bytes", ctypes.c_long, [ctypes.c_void_p, ctypes.c_int]),
+    ("ladder_refine_subpel_batch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(SubpelJob),
+                                                  ctypes.c_void_p]),
     ("ladder_frame_bytes", ctypes.c_long, [ctypes.c_void_p]),
     ("ladder_decision_offsets", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_long)]),
     ("ladder_fetch_frame_async", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_long,
@@ -505,6 +517,31 @@ class Ladder:
         out = {k: ([a.cpu().numpy() for a in v] if isinstance(v, list) else v.cpu().numpy()) for k, v in t.items()}
         out["grid"], out["grid8"] = self.grid(rung)
         return out
+
+    def subpel_jobs(self, specs, buffers):
+        """ctypes array of SubpelJob for ladder_refine_subpel_batch: specs =
+        [(frame_id, rung, cur, ref, qp)], buffers[k] = subpel_buffers(rung)."""
+        jobs = (SubpelJob * len(specs))()
+        for k, ((frame_id, rung, cur, ref, qp), (_, o, ws)) in enumerate(zip(specs, buffers)):
+            jobs[k] = SubpelJob(frame_id, rung, qp, cur.data_ptr(), ref.data_ptr(), _pitch_bytes(cur),
+                                ctypes.pointer(o), ws.data_ptr(), ws.numel())
+        return jobs
+
+    def refine_subpel_batch(self, specs, stream=None, buffers=None) -> list:
+        """Several refinements in one pair of launches: specs = [(frame_id,
+        rung, cur, ref, qp)]; returns one dict per job as refine_subpel."""
+        import torch
+
+        buffers = buffers if buffers is not None else [self.subpel_buffers(sp[1]) for sp in specs]
+        jobs = self.subpel_jobs(specs, buffers)
+        _call(self.handle, "ladder_refine_subpel_batch", self.handle, len(specs), jobs, _stream_handle(stream))
+        (stream or torch.cuda.current_stream()).synchronize()
+        res = []
+        for (frame_id, rung, *_), (t, _, _) in zip(specs, buffers):
+            out = {k: ([a.cpu().numpy() for a in v] if isinstance(v, list) else v.cpu().numpy()) for k, v in t.items()}
+            out["grid"], out["grid8"] = self.grid(rung)
+            res.append(out)
+        return res
 
     def frame_bytes(self) -> int:
         """Bytes of one frame's packed decisions (every rung)."""

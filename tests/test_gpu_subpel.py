@@ -39,6 +39,8 @@ def test_subpel_matches_oracle(bd, satd, ctu):
         lad.analyze_reference(0, *planes[2], qp)
         lad.analyze_dependents(0, [(i, planes[i][0], planes[i][1]) for i in (0, 1)], qp)
         got = [lad.refine_subpel(i, 0, planes[i][0], planes[i][1], qp) for i in range(3)]
+        # the same three refinements as one batched call (independent rung first inside)
+        got_batch = lad.refine_subpel_batch([(0, i, planes[i][0], planes[i][1], qp) for i in (0, 2, 1)])
     ref_ana = oracle.analyze(pairs[2][2], pairs[2][3], qp=qp, search_range=R, ctu=ctu, satd_mode=satd)
     want = {2: oracle.refine_subpel(pairs[2][2], pairs[2][3], ref_ana, qp=qp, ctu=ctu, satd_mode=satd)}
     for i in (0, 1):
@@ -47,6 +49,8 @@ def test_subpel_matches_oracle(bd, satd, ctu):
         want[i] = oracle.refine_subpel(pairs[i][2], pairs[i][3], ana, qp=qp, ctu=ctu, satd_mode=satd, dep=dep)
     for i in range(3):
         _check(got[i], want[i], f"rung {i} bd{bd} satd{satd}")
+    for k, i in enumerate((0, 2, 1)):
+        _check(got_batch[k], want[i], f"batched rung {i} bd{bd} satd{satd}")
 
 
 def test_subpel_needs_an_analysis():
@@ -114,3 +118,24 @@ def test_subpel_workspace_reused_across_frames():
         ana = oracle.analyze(p.cur, p.ref, qp=qp, search_range=R, ctu=32)
         want = oracle.refine_subpel(p.cur, p.ref, ana, qp=qp, ctu=32)
         _check(got[k], want, f"frame {k}")
+
+
+def test_subpel_batch_checked():
+    """Job counts outside 1..16 and a job that fails its checks launch nothing."""
+    import ctypes
+    with L.Ladder([(64, 48), (32, 24)], 1, ctu_size=32, search_range=4, refine_range=2, max_frames=1) as lad:
+        p = synth.frame_pair(4, 64, 48)
+        q = synth.frame_pair(5, 32, 24)
+        c, f = L.device_plane(p.cur), L.device_plane(p.ref)
+        c2, f2 = L.device_plane(q.cur), L.device_plane(q.ref)
+        lad.analyze_reference(0, c2, f2, 27)
+        bufs = [lad.subpel_buffers(0), lad.subpel_buffers(1)]
+        jobs = lad.subpel_jobs([(0, 1, c2, f2, 27), (0, 0, c, f, 27)], bufs)
+        for n in (0, L.MAX_SUBPEL_JOBS + 1):
+            with pytest.raises(L.LadderError):
+                L._call(lad.handle, "ladder_refine_subpel_batch", lad.handle, n, jobs, None)
+        with pytest.raises(L.LadderError):  # rung 0 of frame 0 has not been analysed
+            L._call(lad.handle, "ladder_refine_subpel_batch", lad.handle, 2, jobs, None)
+        # the analysed job alone goes through
+        L._call(lad.handle, "ladder_refine_subpel_batch", lad.handle, 1, jobs, None)
+        torch.cuda.synchronize()
