@@ -310,6 +310,16 @@ struct DecideIO {
 // Index of CU (d, local raster li) in the per-CTU key layout.
 __device__ __forceinline__ int key_index(int d, int li) { return key_offset(d) + li; }
 
+// Key of the depth-d CU that covers 8x8 block (bx, by) of a CTU: the block
+// coordinates shifted by log2 of the CU's size in blocks (no division).
+template <int CTU>
+__device__ __forceinline__ int key_of_block(int d, int bx, int by)
+{
+    constexpr int kLog2N8 = CTU == 64 ? 3 : (CTU == 32 ? 2 : 1);
+    const int sh = kLog2N8 - d;
+    return key_index(d, ((by >> sh) << d) + (bx >> sh));
+}
+
 // What ctu_split writes besides cost, best, split and the leaf maps.
 enum : int {
     kSplitWriteVectors = 1,  // mvx, mvy and SATD per CU
@@ -385,8 +395,7 @@ __device__ void ctu_split(CtuState<CTU> &st, int lam, const RungGeom &g, const D
         if (px >= g.W8 || py >= g.H8) continue;
         int d = 0, i = 0;
         for (;;) {
-            const int S = CTU >> d;
-            i = key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S);
+            i = key_of_block<CTU>(d, bx, by);
             if (d == C::DMAX || !st.split[i]) break;
             ++d;
         }
@@ -421,8 +430,7 @@ __device__ void ctu_decide(CtuState<CTU> &st, const DecideIO &io, int x0, int y0
         unsigned left = 0;
 #pragma unroll
         for (int d = 0; d <= C::DMAX; ++d) {
-            const int S = CTU >> d;
-            ci[d] = key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S);
+            ci[d] = key_of_block<CTU>(d, bx, by);
             if (st.flags[ci[d]] & kRuleEvaluated) left |= 1u << d;
         }
 #pragma unroll
@@ -442,15 +450,13 @@ __device__ void ctu_decide(CtuState<CTU> &st, const DecideIO &io, int x0, int y0
     for (int p = tid; p < st.npairs; p += nthr) {
         const unsigned ent = st.pairs[p];
         const int b = ent & 0xff, bx = b % C::N8, by = b / C::N8;
-        const int d0 = __ffs(ent >> 8) - 1, S0 = CTU >> d0;
-        const int i0 = key_index(d0, ((by * 8) / S0) * (1 << d0) + (bx * 8) / S0);
+        const int i0 = key_of_block<CTU>(__ffs(ent >> 8) - 1, bx, by);
         const int v = satd8_thread<T>(io.cur, io.ref, io.pitch_bytes, g.W, g.H, x0 + 8 * bx, y0 + 8 * by, st.mvx[i0],
                                       st.mvy[i0], io.satd_mode);
 #pragma unroll
         for (int d = 0; d <= C::DMAX; ++d) {
             if (!((ent >> (8 + d)) & 1u)) continue;
-            const int S = CTU >> d;
-            atomicAdd(&st.satd[key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S)], v);
+            atomicAdd(&st.satd[key_of_block<CTU>(d, bx, by)], v);
         }
     }
     __syncthreads();

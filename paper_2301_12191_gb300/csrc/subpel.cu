@@ -25,7 +25,7 @@
 namespace ladder_impl {
 namespace {
 
-constexpr int kSubpelThreads = 512;
+constexpr int kSubpelThreads = 256;
 
 __constant__ int c_lambda_q16_sp[52] = {
 #include "lambda_table.inc"
@@ -259,7 +259,7 @@ __device__ __forceinline__ int32_t rate_q(int lam, int qx, int qy)
 }
 
 template <typename T, int CTU>
-__global__ void __launch_bounds__(kSubpelThreads, 1) k_subpel(const __grid_constant__ SubpelBatch bb)
+__global__ void __launch_bounds__(kSubpelThreads, 2) k_subpel(const __grid_constant__ SubpelBatch bb)
 {
     dev::chain_entry();
     using C = dev::Ctu<CTU>;
@@ -322,8 +322,7 @@ __global__ void __launch_bounds__(kSubpelThreads, 1) k_subpel(const __grid_const
             unsigned left = 0;
 #pragma unroll
             for (int d = 0; d <= C::DMAX; ++d) {
-                const int S = CTU >> d;
-                ci[d] = dev::key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S);
+                ci[d] = dev::key_of_block<CTU>(d, bx, by);
                 if (st.flags[ci[d]] & kRuleEvaluated) left |= 1u << d;
             }
 #pragma unroll
@@ -345,8 +344,7 @@ __global__ void __launch_bounds__(kSubpelThreads, 1) k_subpel(const __grid_const
         for (int w = tid; w < ne * 8; w += kSubpelThreads) {
             const unsigned e = s_ent[w >> 3];
             const int c = w & 7, blk = e & 0xff, bx = blk % C::N8, by = blk / C::N8;
-            const int d0 = __ffs(e >> 8) - 1, S0 = CTU >> d0;
-            const int i0 = dev::key_index(d0, ((by * 8) / S0) * (1 << d0) + (bx * 8) / S0);
+            const int i0 = dev::key_of_block<CTU>(__ffs(e >> 8) - 1, bx, by);
             const int cc = c < 4 ? c : c + 1;  // raster 3x3 without the centre
             const int qx = st.mvx[i0] + step * (cc % 3 - 1), qy = st.mvy[i0] + step * (cc / 3 - 1);
             const int px = x0 + 8 * bx, py = y0 + 8 * by;
@@ -354,11 +352,8 @@ __global__ void __launch_bounds__(kSubpelThreads, 1) k_subpel(const __grid_const
             const int v = satd8_plane<T>(cur, b.pitch_bytes, g.W, g.H, px, py, plane, b.plane_pitch, g.W + 8,
                                          g.H + 8, px + floor4(qx) + 4, py + floor4(qy) + 4, bb.satd_mode);
 #pragma unroll
-            for (int d = d0; d <= C::DMAX; ++d) {
-                if (!((e >> (8 + d)) & 1u)) continue;
-                const int S = CTU >> d;
-                atomicAdd(&s_cand[dev::key_index(d, ((by * 8) / S) * (1 << d) + (bx * 8) / S)][c], v);
-            }
+            for (int d = 0; d <= C::DMAX; ++d)
+                if ((e >> (8 + d)) & 1u) atomicAdd(&s_cand[dev::key_of_block<CTU>(d, bx, by)][c], v);
         }
         __syncthreads();
         for (int i = tid; i < C::NKEY; i += kSubpelThreads) {
