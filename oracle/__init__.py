@@ -59,7 +59,7 @@ class _Job(ctypes.Structure):
         ("ref_leaf_depth", ctypes.c_void_p), ("ref_leaf_mvx", ctypes.c_void_p),
         ("ref_leaf_mvy", ctypes.c_void_p),
         ("depth_lo", ctypes.c_int), ("depth_hi", ctypes.c_int), ("use_ref_mv", ctypes.c_int),
-        ("ctu_mask", ctypes.c_void_p),
+        ("ctu_mask", ctypes.c_void_p), ("mvp", ctypes.c_int),
     ]
 
 
@@ -104,6 +104,9 @@ def _load():
         lib.oracle_pred_sample.restype = ctypes.c_int
         lib.oracle_block_satd_q.argtypes = [ctypes.POINTER(_Job)] + [ctypes.c_int] * 5
         lib.oracle_block_satd_q.restype = ctypes.c_int32
+        lib.oracle_spatial_mvp.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p] * 2 + [ctypes.c_int] * 3 + [
+            ctypes.POINTER(ctypes.c_int)]
+        lib.oracle_spatial_mvp.restype = None
         _lib = lib
     return _lib
 
@@ -150,19 +153,21 @@ def _make_job(cur, ref, qp, ctu, search_range, satd_mode, dep):
 
 
 def analyze(cur, ref, *, qp: int, search_range: int, ctu: int = 64, satd_mode: int = 0,
-            dep: dict | None = None, threads: int | None = None, ctu_mask=None) -> dict:
+            dep: dict | None = None, threads: int | None = None, ctu_mask=None, mvp: int = 0) -> dict:
     """Analyse one frame pair.
 
     ``dep`` (dependent mode) holds ``ref_size=(Wr, Hr)`` and the reference
     rung's per-8x8 ``leaf_depth``, ``leaf_mvx``, ``leaf_mvy`` plus optional
     ``depth_lo``, ``depth_hi``, ``use_ref_mv``; ``search_range`` is then the
-    refinement range r around the centre.
+    refinement range r around the centre.  ``mvp=1`` takes the rate term's
+    predictor from the spatial neighbours (CTUs decided in raster order).
     Returns per-depth lists ``mvx, mvy, sad, satd, cost, best, split,
     evaluated`` (CU raster order) and per-8x8 ``leaf_depth, leaf_mvx, leaf_mvy``.
     """
     lib = _load()
     job, keep = _make_job(cur, ref, qp, ctu, search_range, satd_mode, dep)
     dims, (c8, r8) = grid(job.width, job.height, ctu)
+    job.mvp = int(mvp)
     if ctu_mask is not None:
         m = np.ascontiguousarray(np.asarray(ctu_mask, dtype=np.uint8).reshape(-1))
         if m.size != dims[0][0] * dims[0][1]:
@@ -282,6 +287,20 @@ def refine_subpel(cur, ref, analysis: dict, *, qp: int, ctu: int = 64, satd_mode
     out["grid"] = dims
     out["grid8"] = (c8, r8)
     return out
+
+
+def spatial_mvp(width: int, height: int, ctu: int, leaf_mvx, leaf_mvy, x0: int, y0: int, size: int):
+    """Spatial predictor (pmx, pmy) of the CU (size at x0, y0) over the given
+    per-8x8 leaf vectors of a width x height frame."""
+    c8 = (width + 7) // 8
+    r8 = (height + 7) // 8
+    mx = np.ascontiguousarray(np.asarray(leaf_mvx, dtype=np.int16).reshape(-1))
+    my = np.ascontiguousarray(np.asarray(leaf_mvy, dtype=np.int16).reshape(-1))
+    if mx.size != c8 * r8 or my.size != c8 * r8:
+        raise ValueError("leaf maps must have one entry per 8x8 block")
+    out = (ctypes.c_int * 2)()
+    _load().oracle_spatial_mvp(width, height, ctu, mx.ctypes.data, my.ctypes.data, x0, y0, size, out)
+    return int(out[0]), int(out[1])
 
 
 def pred_sample(ref, x: int, y: int, qx: int, qy: int) -> int:

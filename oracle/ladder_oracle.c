@@ -63,6 +63,9 @@ typedef struct {
     int use_ref_mv;                     /* 1: centre = scaled reference MV */
     /* optional CTU sample: analyse only CTUs with ctu_mask[row * cols + col] != 0 */
     const uint8_t *ctu_mask;
+    /* MV predictor of the rate term: 0 = (0, 0); 1 = spatial (median of
+     * neighbouring leaf vectors, CTUs decided in wavefront order) */
+    int mvp;
 } oracle_job;
 
 /* ------------------------------------------------------------------ */
@@ -211,6 +214,63 @@ static int32_t rd_cost(int32_t satd, int qp, int mvx, int mvy)
     return satd + (int32_t)((prod + 32768) >> 16);
 }
 
+/* Spatial MV predictor (reading for the wavefront CTU order of WPP,
+ * Sec. 2.2: a CTU starts once the CTU above and to its right is done).
+ * The predictor of the CU of size S at (x0, y0) is the component-wise
+ * median of the final leaf vectors at three neighbouring positions, as in
+ * the spatial candidates of HEVC's AMVP:
+ *   A1 = (x0 - 1, y0 + S - 1)   left of the CU's bottom-left sample
+ *   B1 = (x0 + S - 1, y0 - 1)   above the CU's top-right sample
+ *   B0 = (x0 + S, y0 - 1)       above-right
+ * A position counts as vector (0, 0) unless it is available: inside the
+ * 8-aligned frame, outside the CU's own CTU (the CTU is one motion
+ * estimation region whose CUs are analysed in parallel), and in a CTU that
+ * is decided before the CU's CTU in wavefront order -- the CTU to the left
+ * in the same row, or a CTU of the row above at most one column to the
+ * right.  leaf_mvx / leaf_mvy: the frame's per-8x8 leaf vectors (only the
+ * available positions are read). */
+static int med3(int a, int b, int c)
+{
+    int lo = a < b ? a : b, hi = a < b ? b : a;
+    return c < lo ? lo : (c > hi ? hi : c);
+}
+
+static int mvp_available(int ctu, int W8, int H8, int x0, int y0, int px, int py)
+{
+    if (px < 0 || py < 0 || px >= W8 || py >= H8) return 0;
+    int cx = x0 / ctu, cy = y0 / ctu, qx = px / ctu, qy = py / ctu;
+    if (qx == cx && qy == cy) return 0;
+    if (qy == cy) return qx < cx;
+    if (qy == cy - 1) return qx <= cx + 1;
+    return qy < cy - 1;
+}
+
+static void spatial_mvp(int ctu, int W8, int H8, const int16_t *leaf_mvx, const int16_t *leaf_mvy, int x0,
+                        int y0, int S, int *pmx, int *pmy)
+{
+    const int px[3] = {x0 - 1, x0 + S - 1, x0 + S};
+    const int py[3] = {y0 + S - 1, y0 - 1, y0 - 1};
+    int vx[3], vy[3], cols8 = W8 / 8;
+    for (int k = 0; k < 3; k++) {
+        vx[k] = vy[k] = 0;
+        if (mvp_available(ctu, W8, H8, x0, y0, px[k], py[k])) {
+            long li = (long)(py[k] / 8) * cols8 + px[k] / 8;
+            vx[k] = leaf_mvx[li];
+            vy[k] = leaf_mvy[li];
+        }
+    }
+    *pmx = med3(vx[0], vx[1], vx[2]);
+    *pmy = med3(vy[0], vy[1], vy[2]);
+}
+
+/* J with the predictor (pmx, pmy): bits = se() lengths of the quarter-pel
+ * components of the vector minus the predictor. */
+static int32_t rd_cost_pred(int32_t satd, int qp, int mvx, int mvy, int pmx, int pmy)
+{
+    long long bits = oracle_se_bits(4 * (mvx - pmx)) + oracle_se_bits(4 * (mvy - pmy));
+    return satd + (int32_t)((oracle_lambda_q16(qp) * bits + 32768) >> 16);
+}
+
 /* ------------------------------------------------------------------ */
 /* Dependent-mode constraint derivation (Sec. 4.3 / 6.3, App. A.1-A.2)  */
 /* ------------------------------------------------------------------ */
@@ -322,7 +382,13 @@ static int32_t analyse_cu(oracle_ctx *c, int d, int x0, int y0, int reachable)
         int32_t sad;
         motion_search(j, x0, y0, S, rule.cx, rule.cy, &mvx, &mvy, &sad);
         int32_t satd = block_satd(j, x0, y0, S, mvx, mvy);
-        J = rd_cost(satd, j->qp, mvx, mvy);
+        if (j->mvp) {
+            int pmx, pmy;
+            spatial_mvp(j->ctu, c->W8, c->H8, o->leaf_mvx, o->leaf_mvy, x0, y0, S, &pmx, &pmy);
+            J = rd_cost_pred(satd, j->qp, mvx, mvy, pmx, pmy);
+        } else {
+            J = rd_cost(satd, j->qp, mvx, mvy);
+        }
         o->mvx[d][idx] = (int16_t)mvx;
         o->mvy[d][idx] = (int16_t)mvy;
         o->sad[d][idx] = sad;
@@ -409,6 +475,8 @@ static int valid_job(const oracle_job *j)
     if (j->qp < 0 || j->qp > 51 || j->range < 0 || j->range > 128) return 0;
     if (j->dep && (!j->ref_leaf_depth || !j->ref_leaf_mvx || !j->ref_leaf_mvy ||
                    j->ref_width <= 0 || j->ref_height <= 0)) return 0;
+    if (j->mvp != 0 && j->mvp != 1) return 0;
+    if (j->mvp && j->ctu_mask) return 0;  /* predictors need every earlier CTU */
     return 1;
 }
 
@@ -427,7 +495,9 @@ int oracle_analyze(const oracle_job *job, oracle_decisions *out, int threads)
     c.ctu_cols = (c.W8 + job->ctu - 1) / job->ctu;
     c.ctu_rows = (c.H8 + job->ctu - 1) / job->ctu;
     pthread_mutex_init(&c.lock, NULL);
-    if (threads <= 1) {
+    /* spatial predictor: CTUs one by one in raster order (every CTU a CU's
+     * predictor reads is decided before it) */
+    if (threads <= 1 || job->mvp) {
         worker(&c);
     } else {
         pthread_t *t = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)threads);
@@ -438,6 +508,14 @@ int oracle_analyze(const oracle_job *job, oracle_decisions *out, int threads)
     }
     pthread_mutex_destroy(&c.lock);
     return 0;
+}
+
+/* Probe: the spatial predictor of the CU (S at x0, y0) of a width x height
+ * frame with CTU size ctu, over caller-given per-8x8 leaf vectors. */
+void oracle_spatial_mvp(int width, int height, int ctu, const int16_t *leaf_mvx, const int16_t *leaf_mvy, int x0,
+                        int y0, int S, int out[2])
+{
+    spatial_mvp(ctu, (width + 7) / 8 * 8, (height + 7) / 8 * 8, leaf_mvx, leaf_mvy, x0, y0, S, &out[0], &out[1]);
 }
 
 /* Single-CU probes used by the pinning tests. */
