@@ -247,6 +247,26 @@ LADDER_API ladder_status fetch_decisions(ladder_t *ladder, int rung, int frame_i
  * LADDER_E_NOREF otherwise.  Applies to later calls. */
 LADDER_API ladder_status ladder_set_parents(ladder_t *ladder, const int *parent);
 
+/* MV predictor of the rate term of later analyses.  mode 0 (default): the
+ * predictor (0, 0), every CTU decided independently.  mode 1: a spatial
+ * predictor with the wavefront CTU order of WPP (Sec. 2.2: a CTU starts once
+ * the CTU above and to its right is done).  The predictor of a CU of size S
+ * at (x, y) is the component-wise median of the final leaf vectors at
+ * A1 = (x-1, y+S-1), B1 = (x+S-1, y-1) and B0 = (x+S, y-1); a position counts
+ * as (0, 0) unless it lies inside the 8-aligned frame, outside the CU's own
+ * CTU (one motion estimation region, analysed in parallel) and in the CTU to
+ * the left or in the row above at most one column to the right.  bits =
+ * se(4 (mvx - pmx)) + se(4 (mvy - pmy)).  The search (SAD) and the SATD do
+ * not use the rate, so only cost, best, split and the leaf maps change: after
+ * the parallel search and SATD of a batch, one more launch decides them row
+ * by row, each row waiting for the row above (a cooperative launch; a wait
+ * that runs out sets the device status to LADDER_E_TIMEOUT, read by
+ * ladder_sync).  Independent and dependent analyses both take it (a tier's
+ * decisions are final before the next tier derives its rules from them);
+ * ladder_decide_qps, ladder_refine_subpel and analyze_reference_noalloc keep
+ * the predictor (0, 0).  LADDER_E_INVAL for another mode. */
+LADDER_API ladder_status ladder_set_mv_predictor(ladder_t *ladder, int mode);
+
 /* Decisions of one analysed rung at further QPs (intra-resolution analysis
  * sharing, Sec. 4.2: the encodes of one resolution at several QPs share one
  * analysis, with the median QP as the master encode).  The rung's resident
@@ -379,7 +399,8 @@ LADDER_API const char *ladder_last_error(const ladder_t *ladder);
  * search of dependent rungs, 3 key initialisation, 4 dependent constraint
  * derivation (rules, centres, task lists), 5 SATD/cost/split of dependent
  * rungs, 6 cost/split at further QPs (ladder_decide_qps), 7 quarter-pel
- * refinement (ladder_refine_subpel). */
+ * refinement (ladder_refine_subpel), 8 decisions with the spatial MV
+ * predictor (ladder_set_mv_predictor). */
 LADDER_API ladder_status ladder_profile_enable(ladder_t *ladder, int enable);
 
 /* Reads the launch count and the summed event time (ms; 0 when timing was

@@ -331,13 +331,15 @@ enum : int {
 // of the CTA take part.  Writes cost, best and split per CU, the leaf maps
 // and the fields `write` names.  `qpel`: the vectors are in quarter-pel
 // units (the rate term takes them as they are), else in integer samples.
+// pmx / pmy: per-CU predictors (shared memory, the vectors' units), or
+// null for the predictor (0, 0).
 //   cost   -- J = SATD + ((lambdaQ16[qp] * bits + 2^15) >> 16), bits = se()
-//             lengths of the quarter-pel components (predictor (0,0))
+//             lengths of the quarter-pel components of vector - predictor
 //   split  -- Sec. 2.1: split iff it may and (it is not a leaf candidate or
 //             the children's best sum is strictly lower), or it must
 template <int CTU>
 __device__ void ctu_split(CtuState<CTU> &st, int lam, const RungGeom &g, const DevDecisions &out, int write, int x0,
-                          int y0, bool qpel = false)
+                          int y0, bool qpel = false, const int16_t *pmx = nullptr, const int16_t *pmy = nullptr)
 {
     using C = Ctu<CTU>;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -351,7 +353,8 @@ __device__ void ctu_split(CtuState<CTU> &st, int lam, const RungGeom &g, const D
             int32_t J = INT32_MAX;
             if (ev) {
                 const int u = qpel ? 1 : 4;
-                const long long bits = se_bits(u * st.mvx[i]) + se_bits(u * st.mvy[i]);
+                const int px = pmx ? pmx[i] : 0, py = pmy ? pmy[i] : 0;
+                const long long bits = se_bits(u * (st.mvx[i] - px)) + se_bits(u * (st.mvy[i] - py));
                 J = st.satd[i] + static_cast<int32_t>((static_cast<long long>(lam) * bits + 32768) >> 16);
             }
             int32_t best = J;

@@ -34,8 +34,8 @@ struct Slot {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-constexpr int kKinds = 8;  // full search, decide, dependent search, fill keys, dependent rules, dependent decide,
-                           // further-QP decisions, quarter-pel refinement
+constexpr int kKinds = 9;  // full search, decide, dependent search, fill keys, dependent rules, dependent decide,
+                           // further-QP decisions, quarter-pel refinement, spatial-predictor decisions
 
 struct ProfEvent {
     int kind;
@@ -74,6 +74,8 @@ struct ladder {
     // kernel shapes (ladder_set_tuning): results never depend on them
     int tune_fs_band = kFsBand, tune_fs_group = 0, tune_fs_fuse = 1, tune_dep_band = 0, tune_dep_range = 16,
         tune_dep_ctas = 0;
+    int mv_predictor = 0;  // 0: (0, 0); 1: spatial, decided in wavefront order (ladder_set_mv_predictor)
+    int mvp_capacity = 0;  // resident CTAs of the wavefront kernel
     char *host_stage = nullptr;  // pinned staging for fetch_decisions
     size_t host_stage_bytes = 0;
     // tracing
@@ -213,6 +215,7 @@ size_t layout(const RungGeom &g, DecOffsets &o)
     o.dep_flags = take(nk);
     o.dep_slot = take(nk * 4);
     o.done = take(static_cast<size_t>(g.ctu_cols) * g.ctu_rows * 4);
+    o.mvp_flag = take((static_cast<size_t>(g.ctu_cols) * g.ctu_rows + 2) * 4);
     return off;
 }
 
@@ -281,6 +284,44 @@ struct Job {
     long pitch;
     int qp;
 };
+
+// Decisions with the spatial MV predictor of analysed jobs (their vectors
+// and SATDs resident): cooperative launches of one CTA per CTU row, as many
+// jobs per launch as fit on the device at once.
+ladder_status launch_mvp(ladder_t *l, const Job *jobs, int n, int dependent, cudaStream_t s)
+{
+    if (l->mvp_capacity <= 0) l->mvp_capacity = decide_mvp_capacity(l->geo.ctu_size, l->sm_count);
+    auto *b = new (std::nothrow) MvpBatch{};
+    if (!b) return fail(l, LADDER_E_NOMEM, "wavefront batch table");
+    for (int r = 0; r < l->geo.n_rungs; ++r) b->rung[r] = l->info[r];
+    b->status = l->d_status;
+    int k = 0;
+    while (k < n) {
+        int m = 0, ctas = 0;
+        while (k + m < n && m < kMaxMvpItems) {
+            const Job &jb = jobs[k + m];
+            const int rows = l->info[jb.rung].g.ctu_rows;
+            if (m > 0 && ctas + rows > l->mvp_capacity) break;
+            RungBuffers &rb = jb.slot->rungs[jb.rung];
+            b->item[m] = MvpItem{rb.block, jb.rung, jb.qp, dependent, ctas};
+            ctas += rows;
+            ++m;
+        }
+        if (ctas > l->mvp_capacity) {
+            delete b;
+            return fail(l, LADDER_E_INVAL, "%d CTU rows exceed the %d resident wavefront CTAs", ctas, l->mvp_capacity);
+        }
+        b->n = m;
+        const cudaError_t e = traced(l, 8, s, [&] { return launch_decide_mvp(l->geo.ctu_size, *b, ctas, s); });
+        if (e != cudaSuccess) {
+            delete b;
+            return cuda_fail(l, e, "spatial-predictor decisions");
+        }
+        k += m;
+    }
+    delete b;
+    return LADDER_OK;
+}
 
 // Full search + decisions of independently analysed jobs, in batched
 // launches of at most kMaxItems jobs.
@@ -366,6 +407,10 @@ ladder_status launch_independent(ladder_t *l, const Job *jobs, int n, cudaStream
         }
     }
     l->keys_dirty = false;  // every search above left its keys at ~0
+    if (l->mv_predictor) {
+        const ladder_status st = launch_mvp(l, jobs, n, 0, s);
+        if (st != LADDER_OK) return st;
+    }
     for (int k = 0; k < n; ++k) jobs[k].slot->rungs[jobs[k].rung].analysed = 1;
     return LADDER_OK;
 }
@@ -439,6 +484,10 @@ ladder_status launch_dependent_tier(ladder_t *l, const Job *jobs, int n, cudaStr
         if (e != cudaSuccess) return cuda_fail(l, e, "dependent ordering");
         l->dep_recorded = true;
         l->dep_stream = s;
+    }
+    if (l->mv_predictor) {  // before the next tier reads these leaf maps
+        const ladder_status st = launch_mvp(l, jobs, n, 1, s);
+        if (st != LADDER_OK) return st;
     }
     for (int k = 0; k < n; ++k) jobs[k].slot->rungs[jobs[k].rung].analysed = 2;
     return LADDER_OK;
@@ -896,6 +945,14 @@ ladder_status ladder_set_parents(ladder_t *l, const int *parent)
     }
     l->parent.assign(parent, parent + n);
     l->tier = tier;
+    return LADDER_OK;
+}
+
+ladder_status ladder_set_mv_predictor(ladder_t *l, int mode)
+{
+    if (!l) return LADDER_E_INVAL;
+    if (mode != 0 && mode != 1) return fail(l, LADDER_E_INVAL, "mv predictor mode %d: 0 or 1", mode);
+    l->mv_predictor = mode;
     return LADDER_OK;
 }
 

@@ -109,6 +109,9 @@ struct DecOffsets {
     long leaf_depth, leaf_mvx, leaf_mvy;
     long keys;
     long done;  // per CTU: full-search CTAs finished (zero at rest)
+    // spatial-predictor decisions: per CTU the generation that last decided
+    // it, then the block's generation and its count of finished rows
+    long mvp_flag;
     // dependent rungs: per CTU and key slot, the search centre, rule flags
     // and (CUs of 32x32 and up) the CU's place in its task list
     long dep_cx, dep_cy, dep_flags, dep_slot;
@@ -333,6 +336,26 @@ struct SubpelBatch {
     int satd_mode;
     SubpelItem item[kMaxSubpelItems];
 };
+// ---- spatial MV predictor (wavefront re-decision) -------------------------
+// One item = one analysed (frame slot, rung), decided again with the
+// spatial predictor: one CTA per CTU row, rows in wavefront lockstep.
+struct MvpItem {
+    char *block;
+    int rung, qp, dependent;
+    int cta_begin;  // CTA of the item's first CTU row
+};
+constexpr int kMaxMvpItems = kMaxDepItems;
+struct MvpBatch {
+    int n;
+    int *status;
+    RungInfo rung[kMaxRungs];
+    MvpItem item[kMaxMvpItems];
+};
+// Cooperative launch of ctas CTAs (every CTA resident: rows wait on rows).
+cudaError_t launch_decide_mvp(int ctu, const MvpBatch &b, int ctas, cudaStream_t s);
+// CTAs of the wavefront kernel that fit on the device at once.
+int decide_mvp_capacity(int ctu, int sm_count);
+
 // Bytes of the interpolation workspace of a W x H plane (16 planes), with the
 // row pitch and the bytes of one plane.
 long subpel_workspace_layout(int bit_depth, int W, int H, long *plane_pitch, long *plane_bytes);

@@ -107,6 +107,7 @@ SIGNATURES = [
     ("fetch_decisions", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Decisions),
                                        ctypes.c_void_p]),
     ("ladder_set_parents", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    ("ladder_set_mv_predictor", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("ladder_refine_subpel", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_long, ctypes.c_int,
                                             ctypes.POINTER(SubpelDecisions), ctypes.c_void_p, ctypes.c_long,
@@ -139,7 +140,7 @@ SIGNATURES = [
 ]
 
 KERNEL_KINDS = ("full_search", "decide", "dependent", "fill_keys", "dep_rules", "dep_decide", "decide_qps",
-                "subpel")
+                "subpel", "decide_mvp")
 TUNE_KNOBS = {"fs_band": 0, "dep_band": 1, "dep_range": 2, "dep_ctas_per_sm": 3, "fs_group": 4, "fs_fuse": 5}
 
 _lib = None
@@ -446,6 +447,12 @@ class Ladder:
         arr = (ctypes.c_int * len(self.rungs))(*parent)
         _call(self.handle, "ladder_set_parents", self.handle, arr)
         self.parent = list(parent)
+
+    def set_mv_predictor(self, mode: int):
+        """0: predictor (0, 0); 1: spatial predictor, CTUs decided in
+        wavefront order (later analyses)."""
+        _call(self.handle, "ladder_set_mv_predictor", self.handle, int(mode))
+        self.mv_predictor = int(mode)
 
     def decide_qps(self, rung, frame_id, qps, stream=None) -> dict:
         """Cost, best, split and leaf maps of (rung, frame) at each QP of

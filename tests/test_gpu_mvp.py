@@ -1,0 +1,112 @@
+"""Spatial MV predictor with the wavefront CTU order (WPP, Sec. 2.2): the
+CUDA path -- parallel search and SATD, then one launch that decides cost,
+split and leaf maps row by row -- equals the oracle's analysis with mvp=1
+(CTUs decided one by one in raster order), field for field, for
+independent rungs, dependent rungs of a cascaded chain (per call and
+batched), after switching back to the predictor (0, 0), and for a replayed
+CUDA graph."""
+import pytest
+
+import oracle
+from paper_2301_12191_gb300 import synth
+from helpers import assert_decisions_equal, dep_from
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2301_12191_gb300 import ladder as L  # noqa: E402
+
+
+@pytest.mark.parametrize("W,H,ctu,R,bd,satd,qp,seed", [
+    (400, 224, 64, 12, 8, 0, 30, 1),   # 7 x 4 CTUs, ragged both ways
+    (320, 180, 32, 8, 10, 0, 27, 2),   # 10 x 6 CTUs, 10-bit
+    (200, 136, 16, 6, 8, 1, 32, 3),    # 13 x 9 CTUs of 16x16, PAPER4x4 SATD
+    (130, 66, 32, 5, 8, 0, 22, 4),     # ragged 8-alignment
+    (64, 64, 64, 4, 8, 0, 27, 5),      # one CTU: no neighbour available
+    (1280, 64, 64, 8, 8, 0, 37, 6),    # one row of 20 CTUs
+    (64, 1280, 64, 8, 8, 0, 37, 7),    # one column of 20 CTUs (every row waits)
+])
+def test_mvp_independent(W, H, ctu, R, bd, satd, qp, seed):
+    fp = synth.frame_pair(seed, W, H, bd, global_range=4, patch_range=6, patch_size=24)
+    with L.Ladder([(W, H)], 0, bit_depth=bd, ctu_size=ctu, search_range=R, satd_mode=satd,
+                  max_frames=1) as lad:
+        lad.set_mv_predictor(1)
+        cur, ref = L.device_plane(fp.cur), L.device_plane(fp.ref)
+        lad.analyze_reference(0, cur, ref, qp)
+        gpu = lad.fetch(0, 0)
+        assert lad.kernel_stats()["decide_mvp"][0] == 1  # one wavefront launch after the search
+    ora = oracle.analyze(fp.cur, fp.ref, qp=qp, search_range=R, ctu=ctu, satd_mode=satd, mvp=1)
+    assert_decisions_equal(gpu, ora, ctu, where=f"{W}x{H} ctu{ctu} bd{bd}")
+
+
+PARENT = [2, 3, 3, -1]
+
+
+def _oracle_chain(pairs, sizes, R, r, qp, mvp):
+    out = [None] * 4
+    out[3] = oracle.analyze(pairs[3][2], pairs[3][3], qp=qp, search_range=R, mvp=mvp)
+    for i in (2, 1, 0):  # parents before children
+        p = PARENT[i]
+        out[i] = oracle.analyze(pairs[i][2], pairs[i][3], qp=qp, search_range=r, dep=dep_from(out[p], sizes[p]),
+                                mvp=mvp)
+    return out
+
+
+def test_mvp_chain_per_call_batched_and_back_to_zero():
+    pairs, _ = synth.ladder_pairs(43, source=(1280, 720), rungs=[(960, 540), (640, 360), (320, 180)])
+    sizes = [(w, h) for (w, h, _, _) in pairs]
+    R, r, qp = 8, 3, 30
+    with L.Ladder(sizes, 3, search_range=R, refine_range=r, max_frames=3) as lad:
+        lad.set_parents(PARENT)
+        lad.set_mv_predictor(1)
+        planes = [(L.device_plane(c), L.device_plane(f)) for (_, _, c, f) in pairs]
+        lad.analyze_reference(0, *planes[3], qp)
+        lad.analyze_dependents(0, [(i, planes[i][0], planes[i][1]) for i in (0, 1, 2)], qp)  # tiers inside
+        lad.analyze_batch([(1, qp, planes)])
+        per_call = [lad.fetch(i, 0) for i in range(4)]
+        batched = [lad.fetch(i, 1) for i in range(4)]
+        lad.set_mv_predictor(0)
+        lad.analyze_batch([(2, qp, planes)])
+        zero = [lad.fetch(i, 2) for i in range(4)]
+        with pytest.raises(L.LadderError):
+            lad.set_mv_predictor(2)
+    ora = _oracle_chain(pairs, sizes, R, r, qp, 1)
+    ora0 = _oracle_chain(pairs, sizes, R, r, qp, 0)
+    for i in range(4):
+        assert_decisions_equal(per_call[i], ora[i], 64, where=f"per call rung {i}")
+        assert_decisions_equal(batched[i], ora[i], 64, where=f"batched rung {i}")
+        assert_decisions_equal(zero[i], ora0[i], 64, where=f"predictor (0,0) rung {i}")
+
+
+def test_mvp_graph_replay_new_content():
+    """A captured graph bakes its launch parameters: each replay must still
+    wait for its own rows (a generation per launch, kept on the device)."""
+    pairs, _ = synth.ladder_pairs(44, source=(640, 360), rungs=[(480, 270), (320, 180)])
+    sizes = [(w, h) for (w, h, _, _) in pairs]
+    R, r, qp = 8, 3, 32
+    with L.Ladder(sizes, 2, search_range=R, refine_range=r, max_frames=1) as lad:
+        lad.set_mv_predictor(1)
+        planes = [(L.device_plane(c), L.device_plane(f)) for (_, _, c, f) in pairs]
+        stream = torch.cuda.Stream()
+        graph = lad.capture_batch([(0, qp, planes)], stream)
+        graph.launch(stream)
+        stream.synchronize()
+        first = [lad.fetch(i, 0) for i in range(3)]
+        other, _ = synth.ladder_pairs(45, source=(640, 360), rungs=[(480, 270), (320, 180)])
+        for i, (_, _, c, f) in enumerate(other):
+            planes[i][0].copy_(L.device_plane(c))
+            planes[i][1].copy_(L.device_plane(f))
+        graph.launch(stream)
+        graph.launch(stream)
+        stream.synchronize()
+        second = [lad.fetch(i, 0) for i in range(3)]
+        graph.close()
+        lad.sync(stream)  # raises if a wavefront wait ran out
+    for got, src in ((first, pairs), (second, other)):
+        ref = oracle.analyze(src[2][2], src[2][3], qp=qp, search_range=R, mvp=1)
+        assert_decisions_equal(got[2], ref, 64, where="graph reference rung")
+        for i in (0, 1):
+            ora = oracle.analyze(src[i][2], src[i][3], qp=qp, search_range=r, dep=dep_from(ref, sizes[2]), mvp=1)
+            assert_decisions_equal(got[i], ora, 64, where=f"graph rung {i}")
