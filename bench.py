@@ -35,11 +35,11 @@ from paper_2301_12191_gb300 import synth  # noqa: E402
 WORKLOADS = {
     # 1080p source pair -> 1080p / 720p / 540p / 360p rungs; 360p reference
     "ladder1080": dict(source=(1920, 1080), rungs=[(1920, 1080), (1280, 720), (960, 540), (640, 360)], ref=3,
-                       bit_depth=8, R=32, r=4, qp=27, ctu=64, multi_qps=[22, 32, 37], subpel=True),
+                       bit_depth=8, R=32, r=4, qp=27, ctu=64, multi_qps=[22, 32, 37], subpel=True, mvp=True),
     # 8 ladders x 5 consecutive frames (4 pairs each) of 1080p, one batched graph per step
     "batch8x5": dict(mode="batch", ladders=8, frames=5, source=(1920, 1080),
                      rungs=[(1920, 1080), (1280, 720), (960, 540), (640, 360)], ref=3, bit_depth=8, R=32, r=4,
-                     qps=[22, 27, 32, 37], sigmas=[1, 4, 8], global_range=16, patch_range=24, ctu=64),
+                     qps=[22, 27, 32, 37], sigmas=[1, 4, 8], global_range=16, patch_range=24, ctu=64, mvp=True),
     # 8 frame pairs of 2160p 10-bit -> six rungs; 360p reference at +-64, dependents +-8
     "uhd8": dict(mode="batch", ladders=8, frames=2, source=(3840, 2160),
                  rungs=[(3840, 2160), (2560, 1440), (1920, 1080), (1280, 720), (960, 540), (640, 360)], ref=5,
@@ -481,6 +481,23 @@ def run_ours(args, wl):
                   "kernel_ms_per_step": t_sp / 3 if n_sp else None,
                   "ladder_frames_per_s": world * K / (ms_sp * 1e-3)}
 
+    # spatial MV predictor with the wavefront CTU order: the same step with
+    # every rung's cost / split decided row by row (one more launch per tier)
+    mvp = None
+    if wl.get("mvp"):
+        lad.set_mv_predictor(1)
+        ms_mvp = max_over_ranks(timed(step_multi, K, W))
+        lad.kernel_stats(reset=True)
+        lad.profile(True)
+        timed(step_multi, 3, 0)
+        st_mvp = lad.kernel_stats(reset=True)
+        lad.profile(False)
+        lad.set_mv_predictor(0)
+        n_w, t_w = st_mvp.get("decide_mvp", (0, 0.0))
+        mvp = {"launches_per_step": n_w // 3, "ms_per_step": ms_mvp / K, "extra_ms_per_step": (ms_mvp - ms_multi) / K,
+               "wavefront_kernel_ms_per_step": t_w / 3 if n_w else None,
+               "ladder_frames_per_s": world * K / (ms_mvp * 1e-3)}
+
     props = torch.cuda.get_device_properties(dev)
     clocks = clk.summary()
     sm_max = clocks.get("sm_max_mhz") or 2070.0
@@ -537,6 +554,7 @@ def run_ours(args, wl):
         "e2e": {"value": world * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "multi_qp": multi_qp,
         "subpel": subpel,
+        "spatial_mvp": mvp,
         "gpu_launches": int(gpu_launches),
         "kernels": {k: {"launches": n, "ms_total": ms, "share": ms / max(1e-9, sum(v[1] for v in stats.values()))}
                     for k, (n, ms) in stats.items()},
@@ -677,6 +695,26 @@ def run_batch(args, wl):
     launches_per_step = sum(nl for nl, _ in stats.values()) // 3
     dom = max(stats.items(), key=lambda kv: kv[1][1])
     kname, (klaunch, kms) = dom
+    # spatial MV predictor with the wavefront CTU order: the same step with
+    # every rung's cost / split decided row by row (one more launch per tier)
+    mvp = None
+    if wl.get("mvp"):
+        lad.set_mv_predictor(1)
+        g_mvp = lad.capture_batch(items, stream)
+        ms_mvp = timed(lambda: g_mvp.launch(stream), K, W)
+        lad.kernel_stats(reset=True)
+        lad.profile(True)
+        for _ in range(3):
+            lad.analyze_batch(items, stream)
+        st_mvp = lad.kernel_stats(reset=True)
+        lad.profile(False)
+        lad.set_mv_predictor(0)
+        g_mvp.close()
+        n_w, t_w = st_mvp.get("decide_mvp", (0, 0.0))
+        mvp = {"launches_per_step": n_w // 3, "ms_per_step": ms_mvp / K, "extra_ms_per_step": (ms_mvp - ms_multi) / K,
+               "wavefront_kernel_ms_per_step": t_w / 3 if n_w else None,
+               "ladder_frames_per_s": n * K / (ms_mvp * 1e-3)}
+
     props = torch.cuda.get_device_properties(dev)
     clocks = clk.summary()
     sm_max = clocks.get("sm_max_mhz") or 2070.0
@@ -703,6 +741,7 @@ def run_batch(args, wl):
         "kernels": {k: {"launches": nl, "ms_total": ms, "share": ms / max(1e-9, sum(v[1] for v in stats.values()))}
                     for k, (nl, ms) in stats.items()},
         "gpu_launches": launches_per_step * K,
+        "spatial_mvp": mvp,
         "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tabsdiff/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
                      "algorithmic_absdiffs_per_step": algo, "kernel_ms_per_step": kms / 3,

@@ -343,7 +343,8 @@ __device__ void ctu_split(CtuState<CTU> &st, int lam, const RungGeom &g, const D
 {
     using C = Ctu<CTU>;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    for (int d = C::DMAX; d >= 0; --d) {
+#pragma unroll
+    for (int d = C::DMAX; d >= 0; --d) {  // unrolled: n and S are constants, the index math shifts
         const int n = 1 << d, S = CTU >> d;
         for (int li = tid; li < n * n; li += nthr) {
             const int i = key_index(d, li);

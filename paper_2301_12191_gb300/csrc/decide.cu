@@ -113,125 +113,188 @@ __global__ void __launch_bounds__(kThreads) k_decide_qps(const __grid_constant__
 // the left in the same row, or in the row above at most one column right.
 // Only the rate term changes (the search is by SAD, the SATD is at the
 // found vector), so the kernel decides cost, split and leaf maps again from
-// the resident vectors and SATDs: one CTA walks one CTU row left to right,
-// each CTU waiting for the row above to have finished the CTU above-right.
-// Every launch decides a new generation of the block (read from the block
-// at the start, published by the last row to finish), and a CTU's flag holds
-// the generation that decided it: flags of earlier launches, a replayed
-// graph's included, never pass for this one.
+// the resident vectors and SATDs: one CTA walks one CTU row left to right.
+//
+// The positions a CTU reads are the right column of its left neighbour
+// (decided by the same CTA: kept in shared memory), the bottom row of the
+// CTU above and the first bottom block of the CTU above-right.  Each CTU
+// publishes its bottom-row leaf vectors as 64-bit words (generation << 32 |
+// vector), one store each: a reader polls the words it needs until they
+// carry this launch's generation, which also delivers the vector (no fence,
+// no second read).  The generation is read from the block at the start and
+// published by the last row to finish, so words of earlier launches (a
+// replayed graph's included) never pass for this one.
 
 constexpr int kMvpThreads = 128;
-constexpr int kMvpSpin = 1 << 22;  // polls (about 0.2 us each) before a wait gives up
+constexpr int kMvpSpin = 1 << 22;  // polls (an L2 round trip each, under a microsecond) before a wait gives up
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p)
 {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
+__device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_release32(unsigned *p, unsigned v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ int median3(int a, int b, int c) { return max(min(a, b), min(max(a, b), c)); }
 
+__device__ __forceinline__ uint32_t pack_mv(int mvx, int mvy)
+{
+    return static_cast<uint32_t>(static_cast<uint16_t>(mvx)) | (static_cast<uint32_t>(static_cast<uint16_t>(mvy)) << 16);
+}
+__device__ __forceinline__ int mv_x(uint32_t v) { return static_cast<int16_t>(v & 0xffffu); }
+__device__ __forceinline__ int mv_y(uint32_t v) { return static_cast<int16_t>(v >> 16); }
+
+// Leaf vector of 8x8 block (bx, by) of the CTU in st (split flags decided).
 template <int CTU>
-__global__ void __launch_bounds__(kMvpThreads) k_decide_mvp(const __grid_constant__ MvpBatch b)
+__device__ __forceinline__ uint32_t leaf_mv(const dev::CtuState<CTU> &st, int bx, int by)
 {
     using C = dev::Ctu<CTU>;
+    int d = 0, i = 0;
+    for (;;) {
+        i = dev::key_of_block<CTU>(d, bx, by);
+        if (d == C::DMAX || !st.split[i]) break;
+        ++d;
+    }
+    return pack_mv(st.mvx[i], st.mvy[i]);
+}
+
+template <int CTU>
+__global__ void __launch_bounds__(kMvpThreads, 12) k_decide_mvp(const __grid_constant__ MvpBatch b)
+{
+    using C = dev::Ctu<CTU>;
+    constexpr int N8 = C::N8;
     constexpr int kLog2Ctu = CTU == 64 ? 6 : (CTU == 32 ? 5 : 4);
     __shared__ dev::CtuState<CTU> st;
     __shared__ int16_t s_pmx[C::NKEY], s_pmy[C::NKEY];
+    __shared__ uint32_t s_left[N8];       // right column of the left CTU
+    __shared__ uint32_t s_above[N8 + 1];  // bottom row of the CTU above, first bottom block of the one above-right
     __shared__ int s_stop;
     const MvpItem &it = b.item[dev::item_of_cta(b.item, b.n)];
     const RungInfo &ri = b.rung[it.rung];
     const RungGeom &g = ri.g;
     const DevDecisions out = decisions_at(it.block, ri.off);
-    unsigned *done = reinterpret_cast<unsigned *>(it.block + ri.off.mvp_flag);
-    unsigned *gen = done + g.ctu_cols * g.ctu_rows, *rows_done = gen + 1;
+    const int nctu = g.ctu_cols * g.ctu_rows;
+    unsigned long long *hand = reinterpret_cast<unsigned long long *>(it.block + ri.off.mvp_flag);  // [CTU][N8]
+    unsigned *gen = reinterpret_cast<unsigned *>(hand + static_cast<long>(nctu) * N8), *rows_done = gen + 1;
     const uint8_t *dep_flags = reinterpret_cast<const uint8_t *>(it.block + ri.off.dep_flags);
     const int tid = threadIdx.x;
     const int cy = static_cast<int>(blockIdx.x) - it.cta_begin;
     const int lam = c_lambda_q16[it.qp];
     const unsigned target = __ldcg(gen) + 1u;  // published by the previous launch on this block
+    // this thread's CU key (NKEY <= threads): its depth and place in the CTU
+    static_assert(C::NKEY <= kMvpThreads, "one key per thread");
+    const int ki = tid;
+    int kd = 0;
+    while (kd < C::DMAX && ki >= key_offset(kd + 1)) ++kd;
+    const int kli = ki - key_offset(kd), kn = 1 << kd, kS = CTU >> kd;
+    // resident state of key ki of CTU column cx, as loads into registers
+    // (issued one CTU ahead: their latency hides behind the current CTU)
+    uint8_t p_flags = 0;
+    int16_t p_mvx = 0, p_mvy = 0;
+    int32_t p_satd = 0;
+    auto fetch = [&](int cx) {
+        p_flags = 0;
+        if (ki >= C::NKEY) return;
+        const int fx = cx * kn + kli % kn, fy = cy * kn + kli / kn;
+        const bool present = fx * kS < g.W8 && fy * kS < g.H8;
+        if (it.dependent) {
+            p_flags = __ldcg(dep_flags + static_cast<long>(cy * g.ctu_cols + cx) * C::NKEY + ki);
+        } else if (present) {
+            const bool inside = fx * kS + kS <= g.W8 && fy * kS + kS <= g.H8;
+            p_flags = dev::kPresent | kRuleReachable | (inside ? kRuleEvaluated : 0) | (kd < C::DMAX ? kRuleCanSplit : 0);
+        }
+        if (present) {
+            const long gi = static_cast<long>(fy) * g.cols[kd] + fx;
+            p_mvx = __ldcg(out.mvx[kd] + gi);
+            p_mvy = __ldcg(out.mvy[kd] + gi);
+            p_satd = __ldcg(out.satd[kd] + gi);
+        }
+    };
+    auto stage = [&]() {
+        if (ki >= C::NKEY) return;
+        st.flags[ki] = p_flags;
+        st.mvx[ki] = p_mvx;
+        st.mvy[ki] = p_mvy;
+        st.satd[ki] = p_satd;
+    };
     if (tid == 0) s_stop = 0;
+    fetch(0);
+    stage();
+    __syncthreads();
     for (int cx = 0; cx < g.ctu_cols; ++cx) {
         const int ctu_idx = cy * g.ctu_cols + cx;
         const int x0 = cx * CTU, y0 = cy * CTU;
-        // wait for the row above to have decided the CTU above-right (the
-        // rest of this CTU's neighbours are before it in one of the rows)
-        if (tid == 0 && cy > 0) {
-            const unsigned *f = done + (cy - 1) * g.ctu_cols + min(cx + 1, g.ctu_cols - 1);
-            int ok = 0;
-            for (int n = 0; n < kMvpSpin; ++n) {
-                if (ld_acquire(f) == target) {
-                    ok = 1;
-                    break;
+        if (cx + 1 < g.ctu_cols) fetch(cx + 1);
+        // the vectors this CTU reads from the row above (threads 0..N8)
+        if (cy > 0 && tid <= N8) {
+            const int qcx = tid < N8 ? cx : cx + 1, qb = tid < N8 ? tid : 0;
+            uint32_t v = 0;
+            if (qcx < g.ctu_cols && qcx * CTU + 8 * qb < g.W8) {
+                const unsigned long long *w = hand + (static_cast<long>(cy - 1) * g.ctu_cols + qcx) * N8 + qb;
+                bool ok = false;
+                for (int n = 0; n < kMvpSpin; ++n) {
+                    const unsigned long long x = ld_relaxed64(w);
+                    if (static_cast<unsigned>(x >> 32) == target) {
+                        v = static_cast<uint32_t>(x);
+                        ok = true;
+                        break;
+                    }
+                    // another row gave up (checked now and then: each check is a round trip)
+                    if ((n & 255) == 255 && *reinterpret_cast<volatile int *>(b.status) != kStatusOk) break;
                 }
-                if (*reinterpret_cast<volatile int *>(b.status) != kStatusOk) break;  // another row gave up
-                __nanosleep(128);
+                if (!ok) {
+                    atomicCAS(b.status, kStatusOk, kStatusTimeout);
+                    s_stop = 1;
+                }
             }
-            if (!ok) {
-                atomicCAS(b.status, kStatusOk, kStatusTimeout);
-                s_stop = 1;
-            }
+            s_above[tid] = v;
         }
         __syncthreads();
         if (s_stop) break;
-        for (int i = tid; i < C::NKEY; i += kMvpThreads) {
-            int d = 0;
-            while (d < C::DMAX && i >= key_offset(d + 1)) ++d;
-            const int li = i - key_offset(d), n = 1 << d, S = CTU >> d;
-            const int fx = (x0 >> (kLog2Ctu - d)) + li % n, fy = (y0 >> (kLog2Ctu - d)) + li / n;
-            const bool present = fx * S < g.W8 && fy * S < g.H8;
-            uint8_t flags = 0;
-            if (it.dependent) {
-                flags = __ldcg(dep_flags + static_cast<long>(ctu_idx) * C::NKEY + i);
-            } else if (present) {
-                const bool inside = fx * S + S <= g.W8 && fy * S + S <= g.H8;
-                flags = dev::kPresent | kRuleReachable | (inside ? kRuleEvaluated : 0) |
-                        (d < C::DMAX ? kRuleCanSplit : 0);
-            }
-            st.flags[i] = flags;
-            s_pmx[i] = s_pmy[i] = 0;
-            if (flags & dev::kPresent) {
-                const long gi = static_cast<long>(fy) * g.cols[d] + fx;
-                st.mvx[i] = __ldcg(out.mvx[d] + gi);
-                st.mvy[i] = __ldcg(out.mvy[d] + gi);
-                st.satd[i] = __ldcg(out.satd[d] + gi);
-            }
-            if (flags & kRuleEvaluated) {
-                const int x = fx * S, y = fy * S;
-                const int px[3] = {x - 1, x + S - 1, x + S}, py[3] = {y + S - 1, y - 1, y - 1};
-                int vx[3], vy[3];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const int qx = px[k] >> kLog2Ctu, qy = py[k] >> kLog2Ctu;  // CTU of the position
-                    const bool in_frame = px[k] >= 0 && py[k] >= 0 && px[k] < g.W8 && py[k] < g.H8;
-                    const bool before = (qy == cy && qx < cx) || (qy == cy - 1 && qx <= cx + 1);
-                    vx[k] = vy[k] = 0;
-                    if (in_frame && before) {
-                        const long l8 = static_cast<long>(py[k] >> 3) * g.cols8 + (px[k] >> 3);
-                        vx[k] = __ldcg(out.leaf_mvx + l8);
-                        vy[k] = __ldcg(out.leaf_mvy + l8);
-                    }
-                }
-                s_pmx[i] = static_cast<int16_t>(median3(vx[0], vx[1], vx[2]));
-                s_pmy[i] = static_cast<int16_t>(median3(vy[0], vy[1], vy[2]));
+        // predictors of the evaluated CUs (an evaluated CU lies inside the
+        // 8-aligned frame, so A1 and B1 do whenever they are outside its CTU)
+        if (ki < C::NKEY) {
+            s_pmx[ki] = s_pmy[ki] = 0;
+            if (st.flags[ki] & kRuleEvaluated) {
+                const int lx = (kli % kn) * kS, ly = (kli / kn) * kS;  // CU position inside the CTU
+                const uint32_t a1 = (lx == 0 && cx > 0) ? s_left[(ly + kS - 1) >> 3] : 0u;
+                const bool top = ly == 0 && cy > 0;
+                const uint32_t b1 = top ? s_above[(lx + kS - 1) >> 3] : 0u;
+                uint32_t b0 = 0u;
+                if (top && x0 + lx + kS < g.W8) b0 = lx + kS < CTU ? s_above[(lx + kS) >> 3] : s_above[N8];
+                s_pmx[ki] = static_cast<int16_t>(median3(mv_x(a1), mv_x(b1), mv_x(b0)));
+                s_pmy[ki] = static_cast<int16_t>(median3(mv_y(a1), mv_y(b1), mv_y(b0)));
             }
         }
         __syncthreads();
         dev::ctu_split<CTU>(st, lam, g, out, 0, x0, y0, false, s_pmx, s_pmy);
-        __threadfence();  // this CTU's decisions, before its flag
         __syncthreads();
-        if (tid == 0) st_release(done + ctu_idx, target);
+        // publish the bottom row for the row below; keep the right column
+        if (tid < N8) {
+            if (cy + 1 < g.ctu_rows && x0 + 8 * tid < g.W8)
+                st_relaxed64(hand + static_cast<long>(ctu_idx) * N8 + tid,
+                             (static_cast<unsigned long long>(target) << 32) | leaf_mv<CTU>(st, tid, N8 - 1));
+        } else if (tid < 2 * N8) {
+            s_left[tid - N8] = leaf_mv<CTU>(st, N8 - 1, tid - N8);
+        }
+        __syncthreads();
+        if (cx + 1 < g.ctu_cols) stage();  // the next CTU's state
+        __syncthreads();
     }
     // the last row to finish (decided or given up) publishes the generation
     if (tid == 0 && atomicAdd(rows_done, 1u) == static_cast<unsigned>(g.ctu_rows) - 1u) {
         *rows_done = 0;
-        st_release(gen, target);
+        st_release32(gen, target);
     }
 }
 

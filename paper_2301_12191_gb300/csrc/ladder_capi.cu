@@ -215,7 +215,8 @@ size_t layout(const RungGeom &g, DecOffsets &o)
     o.dep_flags = take(nk);
     o.dep_slot = take(nk * 4);
     o.done = take(static_cast<size_t>(g.ctu_cols) * g.ctu_rows * 4);
-    o.mvp_flag = take((static_cast<size_t>(g.ctu_cols) * g.ctu_rows + 2) * 4);
+    // per CTU one word per bottom-row 8x8 block (ctu / 8 of them), then 2 counters
+    o.mvp_flag = take(static_cast<size_t>(g.ctu_cols) * g.ctu_rows * g.ctu + 8);
     return off;
 }
 

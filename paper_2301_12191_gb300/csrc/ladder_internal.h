@@ -109,8 +109,9 @@ struct DecOffsets {
     long leaf_depth, leaf_mvx, leaf_mvy;
     long keys;
     long done;  // per CTU: full-search CTAs finished (zero at rest)
-    // spatial-predictor decisions: per CTU the generation that last decided
-    // it, then the block's generation and its count of finished rows
+    // spatial-predictor decisions: per CTU its bottom-row leaf vectors as
+    // (generation << 32 | vector) words, then the block's generation and its
+    // count of finished rows
     long mvp_flag;
     // dependent rungs: per CTU and key slot, the search centre, rule flags
     // and (CUs of 32x32 and up) the CU's place in its task list
