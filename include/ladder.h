@@ -373,6 +373,36 @@ LADDER_API ladder_status ladder_decision_offsets(const ladder_t *ladder, int run
 LADDER_API ladder_status ladder_fetch_frame_async(ladder_t *ladder, int frame_id, void *host_dst, long bytes,
                                                   void *cuda_stream);
 
+/* Frame pipeline (no counterpart in the paper: the runtime around the
+ * analyses that a serving or encoding loop needs, in the spirit of x265's
+ * frame threads).  `depth` frame slots (1..8), frame ids base_frame_id ..
+ * base_frame_id + depth - 1, each with a device input buffer of in_bytes and
+ * its own analysis stream (owned by the pipeline); one upload stream and one
+ * read-back stream.  A frame's input is one packed host buffer holding every
+ * rung's cur and ref planes: rung r's planes start at cur_off[r] / ref_off[r]
+ * with row pitch pitch[r] bytes (offsets 16-byte aligned, pitch a multiple
+ * of 16 and >= width * sample bytes, planes inside in_bytes).
+ * ladder_pipeline_submit copies host_in (pinned, in_bytes) to the next
+ * slot's buffer, analyses the reference rung and then the dependent rungs at
+ * qp on the slot's stream, and copies the frame's packed decisions
+ * (ladder_frame_bytes, laid out per ladder_decision_offsets) to host_out
+ * (pinned).  Uploads, the analyses of neighbouring frames and read-backs
+ * overlap.  submit blocks the host only until the slot's previous frame is
+ * done (its host_out complete) and returns a ticket; ladder_pipeline_wait
+ * returns once the ticket's decisions are in its host_out; host_in may be
+ * reused then.  Device timeouts are reported by ladder_sync.  Errors:
+ * LADDER_E_INVAL (sizes, layout, depth), LADDER_E_CUDA; the analyses' own
+ * errors (LADDER_E_BUSY without free frame slots) pass through. */
+typedef struct ladder_pipeline ladder_pipeline_t;
+LADDER_API ladder_status ladder_pipeline_create(ladder_t *ladder, int depth, int base_frame_id, long in_bytes,
+                                                const long *cur_off, const long *ref_off, const long *pitch,
+                                                ladder_pipeline_t **out);
+LADDER_API ladder_status ladder_pipeline_submit(ladder_pipeline_t *pipe, const void *host_in, int qp,
+                                                void *host_out, long *ticket);
+LADDER_API ladder_status ladder_pipeline_wait(ladder_pipeline_t *pipe, long ticket);
+/* Waits for the pipeline's work and frees it (not the ladder).  NULL is ignored. */
+LADDER_API void ladder_pipeline_destroy(ladder_pipeline_t *pipe);
+
 /* Grid of a rung: dims[2d], dims[2d+1] = cols_d, rows_d for d = 0..dmax, then
  * dims[2(dmax+1)], dims[2(dmax+1)+1] = 8x8 cols, rows; returns dmax in *n_depths - 1.
  * `dims` must hold 2 * LADDER_MAX_DEPTHS + 2 ints. */

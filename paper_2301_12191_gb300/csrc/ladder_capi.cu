@@ -1183,6 +1183,146 @@ ladder_status ladder_fetch_frame_async(ladder_t *l, int frame_id, void *host_dst
     return LADDER_OK;
 }
 
+struct ladder_pipeline {
+    ladder_t *l = nullptr;
+    int depth = 0, base = 0;
+    long in_bytes = 0, out_bytes = 0;
+    std::vector<long> cur_off, ref_off, pitch;
+    std::vector<char *> dev_in;
+    std::vector<cudaStream_t> comp;  // one analysis stream per slot
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    std::vector<cudaEvent_t> ev_in, ev_comp, ev_out;
+    std::vector<long> slot_ticket;  // the last ticket of each slot (-1: none yet)
+    long next = 0;
+};
+
+namespace {
+
+void pipeline_free(ladder_pipeline *p)
+{
+    if (!p) return;
+    for (cudaStream_t s : p->comp)
+        if (s) cudaStreamSynchronize(s);
+    if (p->s_in) cudaStreamSynchronize(p->s_in);
+    if (p->s_out) cudaStreamSynchronize(p->s_out);
+    for (char *b : p->dev_in) cudaFree(b);
+    for (cudaStream_t s : p->comp)
+        if (s) cudaStreamDestroy(s);
+    if (p->s_in) cudaStreamDestroy(p->s_in);
+    if (p->s_out) cudaStreamDestroy(p->s_out);
+    for (auto *v : {&p->ev_in, &p->ev_comp, &p->ev_out})
+        for (cudaEvent_t e : *v)
+            if (e) cudaEventDestroy(e);
+    delete p;
+}
+
+}  // namespace
+
+ladder_status ladder_pipeline_create(ladder_t *l, int depth, int base_frame_id, long in_bytes, const long *cur_off,
+                                     const long *ref_off, const long *pitch, ladder_pipeline_t **out)
+{
+    if (!l || !out || !cur_off || !ref_off || !pitch) return LADDER_E_INVAL;
+    *out = nullptr;
+    if (depth < 1 || depth > 8) return fail(l, LADDER_E_INVAL, "pipeline depth %d: 1 .. 8", depth);
+    if (in_bytes <= 0) return fail(l, LADDER_E_INVAL, "input bytes %ld", in_bytes);
+    const int ss = l->geo.bit_depth == 8 ? 1 : 2;
+    for (int r = 0; r < l->geo.n_rungs; ++r) {
+        const long w = l->rungs[r].width, h = l->rungs[r].height;
+        if (pitch[r] < w * ss || (pitch[r] & 15))
+            return fail(l, LADDER_E_INVAL, "rung %d: pitch %ld (multiple of 16, >= %ld)", r, pitch[r], w * ss);
+        for (const long o : {cur_off[r], ref_off[r]})
+            if (o < 0 || (o & 15) || o + pitch[r] * h > in_bytes)
+                return fail(l, LADDER_E_INVAL, "rung %d: plane at %ld outside the %ld-byte input", r, o, in_bytes);
+    }
+    auto *p = new (std::nothrow) ladder_pipeline();
+    if (!p) return LADDER_E_NOMEM;
+    p->l = l;
+    p->depth = depth;
+    p->base = base_frame_id;
+    p->in_bytes = in_bytes;
+    p->out_bytes = ladder_frame_bytes(l);
+    p->cur_off.assign(cur_off, cur_off + l->geo.n_rungs);
+    p->ref_off.assign(ref_off, ref_off + l->geo.n_rungs);
+    p->pitch.assign(pitch, pitch + l->geo.n_rungs);
+    p->slot_ticket.assign(depth, -1);
+    p->dev_in.assign(depth, nullptr);
+    p->comp.assign(depth, nullptr);
+    for (auto *v : {&p->ev_in, &p->ev_comp, &p->ev_out}) v->assign(depth, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < depth && e == cudaSuccess; ++j) {
+        e = cudaMalloc(&p->dev_in[j], static_cast<size_t>(in_bytes));
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->comp[j], cudaStreamNonBlocking);
+        for (auto *v : {&p->ev_in, &p->ev_comp, &p->ev_out})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&(*v)[j], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        pipeline_free(p);
+        return cuda_fail(l, e, "pipeline buffers and streams");
+    }
+    *out = p;
+    return LADDER_OK;
+}
+
+ladder_status ladder_pipeline_submit(ladder_pipeline_t *p, const void *host_in, int qp, void *host_out, long *ticket)
+{
+    if (!p || !host_in || !host_out) return LADDER_E_INVAL;
+    ladder_t *l = p->l;
+    const int j = static_cast<int>(p->next % p->depth), frame_id = p->base + j;
+    cudaError_t e = cudaSuccess;
+    if (p->slot_ticket[j] >= 0) e = cudaEventSynchronize(p->ev_out[j]);  // the slot's previous frame is home
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->dev_in[j], host_in, static_cast<size_t>(p->in_bytes),
+                                              cudaMemcpyHostToDevice, p->s_in);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_in[j], p->s_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->comp[j], p->ev_in[j], 0);
+    if (e != cudaSuccess) return cuda_fail(l, e, "pipeline upload");
+    const int rr = l->geo.ref_rung, n = l->geo.n_rungs;
+    char *in = p->dev_in[j];
+    ladder_status st = analyze_reference(l, frame_id, in + p->cur_off[rr], in + p->ref_off[rr], p->pitch[rr], qp,
+                                         p->comp[j]);
+    if (st != LADDER_OK) return st;
+    if (n > 1) {
+        std::vector<int> rungs;
+        std::vector<const void *> curs, refs;
+        std::vector<long> pitches;
+        for (int r = 0; r < n; ++r) {
+            if (r == rr) continue;
+            rungs.push_back(r);
+            curs.push_back(in + p->cur_off[r]);
+            refs.push_back(in + p->ref_off[r]);
+            pitches.push_back(p->pitch[r]);
+        }
+        st = analyze_dependents(l, frame_id, static_cast<int>(rungs.size()), rungs.data(), curs.data(), refs.data(),
+                                pitches.data(), qp, p->comp[j]);
+        if (st != LADDER_OK) return st;
+    }
+    e = cudaEventRecord(p->ev_comp[j], p->comp[j]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->s_out, p->ev_comp[j], 0);
+    if (e != cudaSuccess) return cuda_fail(l, e, "pipeline ordering");
+    st = ladder_fetch_frame_async(l, frame_id, host_out, p->out_bytes, p->s_out);
+    if (st != LADDER_OK) return st;
+    e = cudaEventRecord(p->ev_out[j], p->s_out);
+    if (e != cudaSuccess) return cuda_fail(l, e, "pipeline read-back");
+    p->slot_ticket[j] = p->next;
+    if (ticket) *ticket = p->next;
+    ++p->next;
+    return LADDER_OK;
+}
+
+ladder_status ladder_pipeline_wait(ladder_pipeline_t *p, long ticket)
+{
+    if (!p) return LADDER_E_INVAL;
+    if (ticket < 0 || ticket >= p->next) return fail(p->l, LADDER_E_INVAL, "ticket %ld not submitted", ticket);
+    const int j = static_cast<int>(ticket % p->depth);
+    if (p->slot_ticket[j] != ticket) return LADDER_OK;  // a later frame of the slot waited for it already
+    const cudaError_t e = cudaEventSynchronize(p->ev_out[j]);
+    if (e != cudaSuccess) return cuda_fail(p->l, e, "pipeline wait");
+    return LADDER_OK;
+}
+
+void ladder_pipeline_destroy(ladder_pipeline_t *p) { pipeline_free(p); }
+
 ladder_status ladder_release_frame(ladder_t *l, int frame_id)
 {
     if (!l) return LADDER_E_INVAL;

@@ -113,6 +113,13 @@ SIGNATURES = [
                                             ctypes.POINTER(SubpelDecisions), ctypes.c_void_p, ctypes.c_long,
                                             ctypes.c_void_p]),
     ("ladder_subpel_workspace_bytes", ctypes.c_long, [ctypes.c_void_p, ctypes.c_int]),
+    ("ladder_pipeline_create", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_long,
+                                              ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long),
+                                              ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_void_p)]),
+    ("ladder_pipeline_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                              ctypes.POINTER(ctypes.c_long)]),
+    ("ladder_pipeline_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_long]),
+    ("ladder_pipeline_destroy", None, [ctypes.c_void_p]),
     ("ladder_refine_subpel_batch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(SubpelJob),
                                                   ctypes.c_void_p]),
     ("ladder_frame_bytes", ctypes.c_long, [ctypes.c_void_p]),
@@ -293,6 +300,46 @@ def _pitch_bytes(t) -> int:
     return int(t.stride(0) * t.element_size())
 
 
+class Pipeline:
+    """A frame pipeline (ladder_pipeline_create): submit(host_in, qp,
+    host_out) uploads one packed frame, analyses every rung and reads the
+    frame's packed decisions back, overlapped with its neighbours; wait(ticket)
+    blocks until that frame's decisions are in its host_out."""
+
+    def __init__(self, ladder, handle):
+        self.ladder = ladder
+        self.handle = handle
+        self._ticket = ctypes.c_long()
+
+    def submit(self, host_in, qp: int, host_out) -> int:
+        """host_in / host_out: pinned CPU tensors (or raw addresses)."""
+        src = host_in.data_ptr() if hasattr(host_in, "data_ptr") else int(host_in)
+        dst = host_out.data_ptr() if hasattr(host_out, "data_ptr") else int(host_out)
+        _call(self.ladder.handle, "ladder_pipeline_submit", self.handle, src, int(qp), dst,
+              ctypes.byref(self._ticket))
+        return self._ticket.value
+
+    def wait(self, ticket: int):
+        _call(self.ladder.handle, "ladder_pipeline_wait", self.handle, int(ticket))
+
+    def close(self):
+        if self.handle:
+            load().ladder_pipeline_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Graph:
     """A captured batch (ladder_capture_batch); launch() replays it."""
 
@@ -447,6 +494,17 @@ class Ladder:
         arr = (ctypes.c_int * len(self.rungs))(*parent)
         _call(self.handle, "ladder_set_parents", self.handle, arr)
         self.parent = list(parent)
+
+    def pipeline(self, depth: int, base_frame_id: int, in_bytes: int, cur_off, ref_off, pitch) -> "Pipeline":
+        """Frame pipeline over frame ids base_frame_id .. + depth - 1; the
+        packed input holds rung r's planes at cur_off[r] / ref_off[r] with
+        row pitch pitch[r] bytes."""
+        n = len(self.rungs)
+        arr = lambda v: (ctypes.c_long * n)(*[int(x) for x in v])
+        h = ctypes.c_void_p()
+        _call(self.handle, "ladder_pipeline_create", self.handle, int(depth), int(base_frame_id), int(in_bytes),
+              arr(cur_off), arr(ref_off), arr(pitch), ctypes.byref(h))
+        return Pipeline(self, h.value)
 
     def set_mv_predictor(self, mode: int):
         """0: predictor (0, 0); 1: spatial predictor, CTUs decided in
