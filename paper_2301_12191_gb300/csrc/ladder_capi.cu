@@ -44,6 +44,21 @@ struct ProfEvent {
 
 }  // namespace
 
+// One set of dependent task lists: the counters, tasks, positions and sum
+// tables a dependent batch fills and consumes.  A batch waits for the last
+// batch of its set when that ran on another stream.
+struct DepSet {
+    unsigned int *counts = nullptr;  // one per CU size class
+    unsigned long long *tasks[kSizeClasses] = {};
+    unsigned int *pos[kSizeClasses] = {};
+    unsigned int *sums[kSizeClasses] = {};
+    bool counts_dirty = false;  // counters not known to be zero (zeroed with the arena at init)
+    cudaEvent_t done = nullptr;
+    bool recorded = false;
+    cudaStream_t stream = nullptr;  // stream of the set's last recorded batch
+};
+constexpr int kDepSets = 2;
+
 struct ladder {
     ladder_geometry geo;
     std::vector<ladder_rung> rungs;
@@ -52,22 +67,18 @@ struct ladder {
     void *arena = nullptr;
     size_t arena_bytes = 0;
     int *d_status = nullptr;
-    unsigned int *d_counts = nullptr;  // dependent task counters (one per CU size class)
     // dependent launches share the task lists: each waits for the one
     // before it (on whatever stream that ran)
-    cudaEvent_t dep_done = nullptr;
     std::vector<int> parent;  // per rung: the rung whose decisions a dependent analysis refines (-1: reference)
     std::vector<int> tier;    // per rung: steps from the reference rung along the parents
-    bool dep_recorded = false;
-    cudaStream_t dep_stream = nullptr;  // stream of the last recorded dependent batch
     // every argmin key is ~0 at rest (searches reset them after use); after a
     // failed launch that may not hold, and the next launch fills them first
     bool keys_dirty = true;
-    bool counts_dirty = false;  // task counters not known to be zero (zeroed with the arena at init)
-    unsigned long long *d_tasks[kSizeClasses] = {};
-    unsigned int *d_pos[kSizeClasses] = {};
-    unsigned int *d_sums[kSizeClasses] = {};
-    unsigned int task_cap[kSizeClasses] = {};
+    // dependent task lists: kDepSets sets taken in turn by dependent batches,
+    // so batches on different streams (consecutive frames) run side by side
+    DepSet dep[kDepSets];
+    int next_dep_set = 0;
+    unsigned int task_cap[kSizeClasses] = {};  // entries per list (every set)
     std::string err;
     int sm_count = 0;
     int fs_ctas_per_sm = 1;      // resident full-search CTAs per SM
@@ -421,13 +432,15 @@ ladder_status launch_independent(ladder_t *l, const Job *jobs, int n, cudaStream
 // decisions.
 ladder_status launch_dependent_tier(ladder_t *l, const Job *jobs, int n, cudaStream_t s)
 {
-    // the task lists are per handle: wait for the previous dependent launch
-    // (not inside a graph capture: a captured batch is one ordered stream)
+    // the task lists come in sets taken in turn: wait for the set's previous
+    // batch (not inside a graph capture: a captured batch is one ordered stream)
+    DepSet &ds = l->dep[l->next_dep_set];
+    l->next_dep_set = (l->next_dep_set + 1) % kDepSets;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cap);
     const bool chain = cap == cudaStreamCaptureStatusNone;
-    if (chain && l->dep_recorded && l->dep_stream != s) {  // same stream: ordered already
-        const cudaError_t e = cudaStreamWaitEvent(s, l->dep_done, 0);
+    if (chain && ds.recorded && ds.stream != s) {  // same stream: ordered already
+        const cudaError_t e = cudaStreamWaitEvent(s, ds.done, 0);
         if (e != cudaSuccess) return cuda_fail(l, e, "dependent ordering");
     }
     for (int j0 = 0; j0 < n; j0 += kMaxDepItems) {
@@ -443,12 +456,12 @@ ladder_status launch_dependent_tier(ladder_t *l, const Job *jobs, int n, cudaStr
         b.depth_hi = l->geo.dep_depth_hi;
         b.use_ref_mv = l->geo.dep_use_ref_mv;
         b.status = l->d_status;
-        b.counts = l->d_counts;
+        b.counts = ds.counts;
         b.one = 1;
         for (int c = 0; c < kSizeClasses; ++c) {
-            b.tasks[c] = l->d_tasks[c];
-            b.pos[c] = l->d_pos[c];
-            b.sums[c] = l->d_sums[c];
+            b.tasks[c] = ds.tasks[c];
+            b.pos[c] = ds.pos[c];
+            b.sums[c] = ds.sums[c];
             b.cap[c] = l->task_cap[c];
         }
         for (int r = 0; r < l->geo.n_rungs; ++r) b.rung[r] = l->info[r];
@@ -465,11 +478,11 @@ ladder_status launch_dependent_tier(ladder_t *l, const Job *jobs, int n, cudaStr
         // the counters rest at zero (each batch's decision kernel resets them)
         // unless a launch of an earlier batch failed
         cudaError_t e = cudaSuccess;
-        if (l->counts_dirty) {
-            e = cudaMemsetAsync(l->d_counts, 0, kSizeClasses * sizeof(unsigned int), s);
+        if (ds.counts_dirty) {
+            e = cudaMemsetAsync(ds.counts, 0, kSizeClasses * sizeof(unsigned int), s);
             if (e != cudaSuccess) return cuda_fail(l, e, "task counters");
         }
-        l->counts_dirty = true;
+        ds.counts_dirty = true;
         e = traced(l, 4, s, [&] { return launch_dependent_rules(l->geo.ctu_size, b, s); });
         if (e == cudaSuccess) e = traced(l, 2, s, [&] { return launch_dependent_search(l->geo.bit_depth, b, s); });
         if (e == cudaSuccess)
@@ -478,13 +491,13 @@ ladder_status launch_dependent_tier(ladder_t *l, const Job *jobs, int n, cudaStr
             l->keys_dirty = true;
             return cuda_fail(l, e, "dependent launch");
         }
-        l->counts_dirty = false;
+        ds.counts_dirty = false;
     }
     if (chain) {
-        const cudaError_t e = cudaEventRecord(l->dep_done, s);
+        const cudaError_t e = cudaEventRecord(ds.done, s);
         if (e != cudaSuccess) return cuda_fail(l, e, "dependent ordering");
-        l->dep_recorded = true;
-        l->dep_stream = s;
+        ds.recorded = true;
+        ds.stream = s;
     }
     if (l->mv_predictor) {  // before the next tier reads these leaf maps
         const ladder_status st = launch_mvp(l, jobs, n, 1, s);
@@ -564,8 +577,8 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
                                                        : 0;
         const size_t cap = dep_ctus * per_ctu * geometry->max_frames;
         l->task_cap[c] = static_cast<unsigned int>(std::min<size_t>(cap, 0xffffffffu));
-        task_bytes += align_up(cap * 8, 256) + align_up(cap * 4, 256);
-        if (c >= kFirstSummedClass) task_bytes += align_up(cap * kr2 * 4, 256);
+        task_bytes += kDepSets * (align_up(cap * 8, 256) + align_up(cap * 4, 256));
+        if (c >= kFirstSummedClass) task_bytes += kDepSets * align_up(cap * kr2 * 4, 256);
     }
     const size_t fixed = 256 + task_bytes;
     l->arena_bytes = fixed + per_slot * geometry->max_frames;
@@ -577,17 +590,21 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
     }
     char *base = static_cast<char *>(l->arena);
     l->d_status = reinterpret_cast<int *>(base);
-    l->d_counts = reinterpret_cast<unsigned int *>(base + 64);
+    static_assert(64 + kDepSets * 64 <= 256, "counters inside the arena header");
     {
         char *tp = base + 256;
-        for (int c = 0; c < kSizeClasses; ++c) {
-            l->d_tasks[c] = reinterpret_cast<unsigned long long *>(tp);
-            tp += align_up(static_cast<size_t>(l->task_cap[c]) * 8, 256);
-            l->d_pos[c] = reinterpret_cast<unsigned int *>(tp);
-            tp += align_up(static_cast<size_t>(l->task_cap[c]) * 4, 256);
-            if (c >= kFirstSummedClass) {
-                l->d_sums[c] = reinterpret_cast<unsigned int *>(tp);
-                tp += align_up(static_cast<size_t>(l->task_cap[c]) * kr2 * 4, 256);
+        for (int k = 0; k < kDepSets; ++k) {
+            DepSet &ds = l->dep[k];
+            ds.counts = reinterpret_cast<unsigned int *>(base + 64 + 64 * k);
+            for (int c = 0; c < kSizeClasses; ++c) {
+                ds.tasks[c] = reinterpret_cast<unsigned long long *>(tp);
+                tp += align_up(static_cast<size_t>(l->task_cap[c]) * 8, 256);
+                ds.pos[c] = reinterpret_cast<unsigned int *>(tp);
+                tp += align_up(static_cast<size_t>(l->task_cap[c]) * 4, 256);
+                if (c >= kFirstSummedClass) {
+                    ds.sums[c] = reinterpret_cast<unsigned int *>(tp);
+                    tp += align_up(static_cast<size_t>(l->task_cap[c]) * kr2 * 4, 256);
+                }
             }
         }
     }
@@ -619,7 +636,8 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
     }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     e = cudaMemsetAsync(l->arena, 0, l->arena_bytes, s);  // counters and per-CTU done counts at zero
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&l->dep_done, cudaEventDisableTiming);
+    for (auto &ds : l->dep)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ds.done, cudaEventDisableTiming);
     // every key of every slot to ~0 (searches keep that at rest)
     if (e == cudaSuccess) {
         FillBatch fill{};
@@ -640,7 +658,8 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
         l->keys_dirty = e != cudaSuccess;
     }
     if (e != cudaSuccess) {
-        if (l->dep_done) cudaEventDestroy(l->dep_done);
+        for (auto &ds : l->dep)
+            if (ds.done) cudaEventDestroy(ds.done);
         cudaFreeHost(l->host_stage);
         cudaFree(l->arena);
         delete l;
@@ -1410,7 +1429,8 @@ void ladder_destroy(ladder_t *l)
     cudaDeviceSynchronize();
     drain_events(l);
     for (cudaEvent_t e : l->spare) cudaEventDestroy(e);
-    if (l->dep_done) cudaEventDestroy(l->dep_done);
+    for (auto &ds : l->dep)
+        if (ds.done) cudaEventDestroy(ds.done);
     cudaFreeHost(l->host_stage);
     cudaFree(l->arena);
     delete l;
