@@ -21,7 +21,11 @@
  * without waiting, except fetch_decisions (waits for its copies) and
  * ladder_sync.  The analyses of one frame must be enqueued on one stream, or
  * the caller orders the streams itself (the dependent reads device state that
- * the reference analysis writes).
+ * the reference analysis writes).  Different frames may go to different
+ * streams and then run side by side: the library orders what their analyses
+ * share (the dependent task lists come in two sets taken in turn; a batch
+ * waits for the previous batch of its set).  Captured graphs of one handle
+ * take no such waits: replay them one at a time.
  *
  * Memory: the caller owns the input planes (device pointers, typically from
  * PyTorch tensors) and must keep them alive and unmodified until the stream
