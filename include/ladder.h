@@ -25,7 +25,8 @@
  * streams and then run side by side: the library orders what their analyses
  * share (the dependent task lists come in two sets taken in turn; a batch
  * waits for the previous batch of its set).  Captured graphs of one handle
- * take no such waits: replay them one at a time.
+ * take no such waits: replay them one at a time, and not while other
+ * analyses of the handle are in flight on another stream.
  *
  * Memory: the caller owns the input planes (device pointers, typically from
  * PyTorch tensors) and must keep them alive and unmodified until the stream
