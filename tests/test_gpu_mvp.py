@@ -110,3 +110,27 @@ def test_mvp_graph_replay_new_content():
         for i in (0, 1):
             ora = oracle.analyze(src[i][2], src[i][3], qp=qp, search_range=r, dep=dep_from(ref, sizes[2]), mvp=1)
             assert_decisions_equal(got[i], ora, 64, where=f"graph rung {i}")
+
+
+def test_mvp_batch_wider_than_the_device():
+    """64 frames of 2160p in one batch: 2176 CTU rows, more than the wavefront
+    CTAs that fit on the device at once, so the decisions run as several
+    cooperative launches.  Every frame equals the same frame analysed alone."""
+    W, H, R, qp = 3840, 2160, 4, 30
+    srcs = [synth.frame_pair(80 + k, W, H, global_range=3, patch_range=4) for k in range(4)]
+    planes = [(L.device_plane(p.cur), L.device_plane(p.ref)) for p in srcs]
+    with L.Ladder([(W, H)], 0, search_range=R, max_frames=64) as lad:
+        lad.set_mv_predictor(1)
+        lad.kernel_stats(reset=True)
+        lad.analyze_batch_independent([(f, qp, [planes[f % 4]]) for f in range(64)])
+        launches = lad.kernel_stats(reset=True)["decide_mvp"][0]
+        got = {f: lad.fetch(0, f) for f in (0, 1, 2, 3, 33, 62, 63)}
+        for f in range(64):
+            lad.release_frame(f)
+        alone = []
+        for k in range(4):
+            lad.analyze_reference(k, *planes[k], qp)
+            alone.append(lad.fetch(0, k))
+    assert launches >= 2, "the batch should need more than one wavefront launch"
+    for f, dec in got.items():
+        assert_decisions_equal(dec, alone[f % 4], 64, where=f"batched frame {f}")
