@@ -65,6 +65,7 @@ WORKLOADS = {
 METRIC = "ladder frames/sec (multi-resolution inter analysis)"
 UNIT = "ladder_frames/s"
 E2E_DEPTH = 4  # frame slots of the end-to-end pipeline
+PIPE_STREAMS = 3  # streams (and frame slots) of the pipelined device measurement
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM bytes (read + write) of one launch from an ncu capture of the bench
@@ -245,7 +246,7 @@ def run_ours(args, wl):
 
     sizes = [(w, h) for (w, h, _, _) in frames[0]]
     lad = L.Ladder(sizes, wl["ref"], bit_depth=wl["bit_depth"], ctu_size=wl["ctu"], search_range=wl["R"],
-                   refine_range=wl["r"], max_frames=E2E_DEPTH)
+                   refine_range=wl["r"], max_frames=max(E2E_DEPTH, PIPE_STREAMS + 1))
     # the pipelined measurement cycles through more distinct frames than fit
     # in L2 (no flush inside its timed region)
     n_dev = max(n_frames, wl.get("pipelined_frames", n_frames))
@@ -262,7 +263,7 @@ def run_ours(args, wl):
         lad.analyze_reference(frame_id, pl[ref_i][0], pl[ref_i][1], qp)
         lad.analyze_dependents(frame_id, [(i, pl[i][0], pl[i][1]) for i in range(n_rungs) if i != ref_i], qp)
 
-    def step_indep(fi, frame_id=2):
+    def step_indep(fi, frame_id=PIPE_STREAMS):
         pl = dplanes[fi % n_frames]
         for i in range(n_rungs):
             lad.analyze_independent(i, frame_id, pl[i][0], pl[i][1], qp)
@@ -292,14 +293,14 @@ def run_ours(args, wl):
         return replicas.max_over_ranks(v, dev)
 
     # Frame-level parallelism (as x265 encodes several frames at once):
-    # consecutive ladder frames alternate between two streams and two frame
-    # slots, so one frame's full search overlaps the previous frame's
+    # consecutive ladder frames take turns on PIPE_STREAMS streams and frame
+    # slots, so one frame's full search overlaps the previous frames'
     # dependent kernels.  Timed as one region from the first launch to the
     # last completion; the inputs cycle through n_dev distinct frames.
-    pipe_streams = [stream, torch.cuda.Stream(dev)]
+    pipe_streams = [stream] + [torch.cuda.Stream(dev) for _ in range(PIPE_STREAMS - 1)]
 
     def step_pipe(i):
-        j = i % 2
+        j = i % PIPE_STREAMS
         with torch.cuda.stream(pipe_streams[j]):
             pl = dplanes[i % n_dev]
             lad.analyze_reference(j, pl[ref_i][0], pl[ref_i][1], qp)
@@ -313,13 +314,15 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
-        joined = torch.cuda.Event()
         t0.record(pipe_streams[0])
-        pipe_streams[1].wait_event(t0)
+        for ps in pipe_streams[1:]:
+            ps.wait_event(t0)
         for i in range(W, W + K):
             step_pipe(i)
-        joined.record(pipe_streams[1])
-        pipe_streams[0].wait_event(joined)
+        for ps in pipe_streams[1:]:
+            joined = torch.cuda.Event()
+            joined.record(ps)
+            pipe_streams[0].wait_event(joined)
         t1.record(pipe_streams[0])
         torch.cuda.synchronize()
         replicas.barrier()
@@ -366,10 +369,10 @@ def run_ours(args, wl):
         ms_pipe = timed_pipe(K, W)
         launches1 = sum(n for n, _ in lad.kernel_stats().values())
         # the last pipelined frame's decisions equal a serial analysis of the same frame
-        last = [lad.fetch(r, (W + K - 1) % 2) for r in range(n_rungs)]
-        step_multi(W + K - 1, frame_id=2)
+        last = [lad.fetch(r, (W + K - 1) % PIPE_STREAMS) for r in range(n_rungs)]
+        step_multi(W + K - 1, frame_id=PIPE_STREAMS)
         torch.cuda.synchronize()
-        again = [lad.fetch(r, 2) for r in range(n_rungs)]
+        again = [lad.fetch(r, PIPE_STREAMS) for r in range(n_rungs)]
         if not all(np.array_equal(a[k][d], b[k][d]) for a, b in zip(last, again) for k in ("mvx", "cost", "split")
                    for d in range(len(a[k]))):
             raise RuntimeError("pipelined decisions differ from a serial analysis of the same frame")
@@ -567,7 +570,7 @@ def run_ours(args, wl):
             "l2": (f"inputs larger than L2 ({n_dev} distinct ladder frames, {dev_in_bytes / 2**20:.0f} MiB of "
                    "planes) for the pipelined value; the serial steps flush L2 between steps (256 MiB write, "
                    "outside the step events)"),
-            "pipelining": "consecutive ladder frames alternate between two streams and two frame slots",
+            "pipelining": f"consecutive ladder frames take turns on {PIPE_STREAMS} streams and frame slots",
             "parallelism": f"replicas x{world} (independent ladders per GPU)",
             "tuning": tuning,
         },

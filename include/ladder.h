@@ -23,8 +23,9 @@
  * the caller orders the streams itself (the dependent reads device state that
  * the reference analysis writes).  Different frames may go to different
  * streams and then run side by side: the library orders what their analyses
- * share (the dependent task lists come in two sets taken in turn; a batch
- * waits for the previous batch of its set).  Captured graphs of one handle
+ * share (the dependent task lists come in three sets: a batch takes its
+ * stream's last set, else an unused one, else the least recently used one
+ * after that set's last batch).  Captured graphs of one handle
  * take no such waits: replay them one at a time, and not while other
  * analyses of the handle are in flight on another stream.
  *

@@ -45,8 +45,9 @@ struct ProfEvent {
 }  // namespace
 
 // One set of dependent task lists: the counters, tasks, positions and sum
-// tables a dependent batch fills and consumes.  A batch waits for the last
-// batch of its set when that ran on another stream.
+// tables a dependent batch fills and consumes.  A batch takes the set its
+// stream used last (no wait: one stream is ordered), else a set not used
+// yet, else the least recently used one, waiting for that set's last batch.
 struct DepSet {
     unsigned int *counts = nullptr;  // one per CU size class
     unsigned long long *tasks[kSizeClasses] = {};
@@ -56,8 +57,9 @@ struct DepSet {
     cudaEvent_t done = nullptr;
     bool recorded = false;
     cudaStream_t stream = nullptr;  // stream of the set's last recorded batch
+    unsigned long long last_use = 0;
 };
-constexpr int kDepSets = 2;
+constexpr int kDepSets = 3;
 
 struct ladder {
     ladder_geometry geo;
@@ -77,7 +79,7 @@ struct ladder {
     // dependent task lists: kDepSets sets taken in turn by dependent batches,
     // so batches on different streams (consecutive frames) run side by side
     DepSet dep[kDepSets];
-    int next_dep_set = 0;
+    unsigned long long dep_clock = 0;
     unsigned int task_cap[kSizeClasses] = {};  // entries per list (every set)
     std::string err;
     int sm_count = 0;
@@ -432,10 +434,21 @@ ladder_status launch_independent(ladder_t *l, const Job *jobs, int n, cudaStream
 // decisions.
 ladder_status launch_dependent_tier(ladder_t *l, const Job *jobs, int n, cudaStream_t s)
 {
-    // the task lists come in sets taken in turn: wait for the set's previous
-    // batch (not inside a graph capture: a captured batch is one ordered stream)
-    DepSet &ds = l->dep[l->next_dep_set];
-    l->next_dep_set = (l->next_dep_set + 1) % kDepSets;
+    // the task lists come in sets: the stream's own set, else a fresh one,
+    // else the least recently used, whose last batch this one waits for (not
+    // inside a graph capture: a captured batch is one ordered stream)
+    int pick = -1;
+    for (int k = 0; k < kDepSets && pick < 0; ++k)
+        if (l->dep[k].recorded && l->dep[k].stream == s) pick = k;
+    for (int k = 0; k < kDepSets && pick < 0; ++k)
+        if (!l->dep[k].recorded) pick = k;
+    if (pick < 0) {
+        pick = 0;
+        for (int k = 1; k < kDepSets; ++k)
+            if (l->dep[k].last_use < l->dep[pick].last_use) pick = k;
+    }
+    DepSet &ds = l->dep[pick];
+    ds.last_use = ++l->dep_clock;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cap);
     const bool chain = cap == cudaStreamCaptureStatusNone;
