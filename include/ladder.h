@@ -406,7 +406,8 @@ LADDER_API ladder_status ladder_pipeline_create(ladder_t *ladder, int depth, int
 LADDER_API ladder_status ladder_pipeline_submit(ladder_pipeline_t *pipe, const void *host_in, int qp,
                                                 void *host_out, long *ticket);
 LADDER_API ladder_status ladder_pipeline_wait(ladder_pipeline_t *pipe, long ticket);
-/* Waits for the pipeline's work and frees it (not the ladder).  NULL is ignored. */
+/* Waits for the pipeline's work and frees it (not the ladder; destroy every
+ * pipeline of a ladder before the ladder itself).  NULL is ignored. */
 LADDER_API void ladder_pipeline_destroy(ladder_pipeline_t *pipe);
 
 /* Grid of a rung: dims[2d], dims[2d+1] = cols_d, rows_d for d = 0..dmax, then
