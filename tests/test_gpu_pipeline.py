@@ -39,7 +39,9 @@ def _pack(pairs, layout, es):
     return buf
 
 
-@pytest.mark.parametrize("bd,depth", [(8, 2), (10, 3)])
+# depths 4 and 5 run more analysis streams than the handle has dependent
+# task-list sets (3): batches then take the least recently used set
+@pytest.mark.parametrize("bd,depth", [(8, 2), (10, 3), (8, 4), (8, 5)])
 def test_pipeline_frames_equal_oracle(bd, depth):
     es = 1 if bd == 8 else 2
     frames = [synth.ladder_pairs(60 + k, source=(480, 272), rungs=[(320, 180), (240, 136)], bit_depth=bd)[0]
@@ -49,14 +51,14 @@ def test_pipeline_frames_equal_oracle(bd, depth):
     layout = _layout(sizes, es)
     host_in = [_pack(fr, layout, es) for fr in frames]
     with L.Ladder(sizes, 2, bit_depth=bd, search_range=R, refine_range=r, max_frames=depth + 1) as lad:
-        outs = [torch.empty(lad.frame_bytes(), dtype=torch.uint8).pin_memory() for _ in range(7)]
+        outs = [torch.empty(lad.frame_bytes(), dtype=torch.uint8).pin_memory() for _ in range(9)]
         with lad.pipeline(depth, 10, layout[3], *layout[:3]) as pipe:
-            tickets = [pipe.submit(host_in[k % 5], qp, outs[k]) for k in range(7)]
+            tickets = [pipe.submit(host_in[k % 5], qp, outs[k]) for k in range(9)]
             for t in tickets:
                 pipe.wait(t)
         lad.sync()
         got = [lad.frame_views(o.numpy()) for o in outs]
-    for k in range(7):
+    for k in range(9):
         fr = frames[k % 5]
         ref = oracle.analyze(fr[2][2], fr[2][3], qp=qp, search_range=R)
         assert_decisions_equal(got[k][2], ref, 64, where=f"frame {k} reference")
