@@ -259,7 +259,7 @@ __device__ __forceinline__ int32_t rate_q(int lam, int qx, int qy)
 }
 
 template <typename T, int CTU>
-__global__ void __launch_bounds__(kSubpelThreads, 2) k_subpel(const __grid_constant__ SubpelBatch bb)
+__global__ void __launch_bounds__(kSubpelThreads, 3) k_subpel(const __grid_constant__ SubpelBatch bb)
 {
     dev::chain_entry();
     using C = dev::Ctu<CTU>;
