@@ -74,7 +74,7 @@ PAPER_CONTEXT = {
     "simd_kernels": "SAD 2.40x-6.46x and SATD 3.45x-10.22x faster than C++ (Arowana XVC, SSE4/AVX2)",
 }
 UNIT = "ladder_frames/s"
-E2E_DEPTH = 4  # frame slots of the end-to-end pipeline
+E2E_DEPTH = 5  # frame slots of the end-to-end pipeline
 PIPE_STREAMS = 3  # streams (and frame slots) of the pipelined device measurement
 L2_FLUSH_BYTES = 256 << 20
 
