@@ -524,6 +524,7 @@ def run_ours(args, wl):
     if wl.get("mvp"):
         lad.set_mv_predictor(1)
         ms_mvp = max_over_ranks(timed(step_multi, K, W))
+        ms_mvp_pipe = max_over_ranks(timed_pipe(K, W))
         lad.kernel_stats(reset=True)
         lad.profile(True)
         timed(step_multi, 3, 0)
@@ -533,7 +534,8 @@ def run_ours(args, wl):
         n_w, t_w = st_mvp.get("decide_mvp", (0, 0.0))
         mvp = {"launches_per_step": n_w // 3, "ms_per_step": ms_mvp / K, "extra_ms_per_step": (ms_mvp - ms_multi) / K,
                "wavefront_kernel_ms_per_step": t_w / 3 if n_w else None,
-               "ladder_frames_per_s": world * K / (ms_mvp * 1e-3)}
+               "ladder_frames_per_s": world * K / (ms_mvp * 1e-3),
+               "pipelined_ladder_frames_per_s": world * K / (ms_mvp_pipe * 1e-3)}
 
     props = torch.cuda.get_device_properties(dev)
     clocks = clk.summary()
