@@ -316,9 +316,10 @@ def run_ours(args, wl):
             lad.analyze_reference(j, pl[ref_i][0], pl[ref_i][1], qp)
             lad.analyze_dependents(j, [(r, pl[r][0], pl[r][1]) for r in range(n_rungs) if r != ref_i], qp)
 
-    def timed_pipe(K, W):
+    def timed_pipe(K, W, step=None):
+        step = step or step_pipe
         for i in range(W):
-            step_pipe(i)
+            step(i)
         torch.cuda.synchronize()
         replicas.barrier()
         torch.cuda.synchronize()
@@ -328,7 +329,7 @@ def run_ours(args, wl):
         for ps in pipe_streams[1:]:
             ps.wait_event(t0)
         for i in range(W, W + K):
-            step_pipe(i)
+            step(i)
         for ps in pipe_streams[1:]:
             joined = torch.cuda.Event()
             joined.record(ps)
@@ -514,9 +515,23 @@ def run_ours(args, wl):
         st_sp = lad.kernel_stats(reset=True)
         lad.profile(False)
         n_sp, t_sp = st_sp.get("subpel", (0, 0.0))
+        # the same with consecutive frames pipelined: each slot refines on its
+        # own stream into its own outputs and workspaces
+        slot_bufs = [[lad.subpel_buffers(r) for r in range(n_rungs)] for _ in range(PIPE_STREAMS)]
+        slot_jobs = [[lad.subpel_jobs([(j, r, pl[r][0], pl[r][1], qp) for r in range(n_rungs)], slot_bufs[j])
+                      for pl in dplanes] for j in range(PIPE_STREAMS)]
+
+        def step_pipe_sp(i):
+            step_pipe(i)
+            j = i % PIPE_STREAMS
+            L._call(lad.handle, "ladder_refine_subpel_batch", lad.handle, n_rungs, slot_jobs[j][i % n_dev],
+                    pipe_streams[j].cuda_stream)
+
+        ms_sp_pipe = max_over_ranks(timed_pipe(K, W, step_pipe_sp))
         subpel = {"launches_per_step": 2, "ms_per_step": ms_sp / K, "extra_ms_per_step": (ms_sp - ms_multi) / K,
                   "kernel_ms_per_step": t_sp / 3 if n_sp else None,
-                  "ladder_frames_per_s": world * K / (ms_sp * 1e-3)}
+                  "ladder_frames_per_s": world * K / (ms_sp * 1e-3),
+                  "pipelined_ladder_frames_per_s": world * K / (ms_sp_pipe * 1e-3)}
 
     # spatial MV predictor with the wavefront CTU order: the same step with
     # every rung's cost / split decided row by row (one more launch per tier)
