@@ -16,7 +16,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared_functions():
     src = open(os.path.join(ROOT, "include", "ladder.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:LADDER_API\s+)?(?:ladder_status|void|const char\s*\*)\s*\*?\s*(\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:LADDER_API\s+)?(?:ladder_status|void|long|const char\s*\*)\s*\*?\s*(\w+)\s*\(",
+                                 src, re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -40,6 +41,28 @@ def test_library_exports_every_declared_symbol(lib):
 def test_binding_covers_every_declared_symbol():
     bound = {n for n, _, _ in L.SIGNATURES}
     assert set(_declared_functions()) <= bound
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """A C99 program includes the header and links against the library."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text('#include "ladder.h"\n'
+                   'int main(void) {\n'
+                   '    ladder_t *l = 0;\n'
+                   '    ladder_subpel_job job = {0};\n'
+                   '    (void)job;\n'
+                   '    return ladder_frame_bytes(l) == 0 && ladder_set_mv_predictor(l, 0) != LADDER_OK ? 0 : 1;\n'
+                   '}\n')
+    exe = tmp_path / "abi"
+    subprocess.check_call([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                           os.path.join(ROOT, "include"), str(src), lbuild.LIB, "-o", str(exe),
+                           "-Wl,-rpath," + os.path.dirname(lbuild.LIB)])
+    assert os.path.exists(exe)
 
 
 def test_version_string(lib):
