@@ -793,7 +793,7 @@ def run_batch(args, wl):
     result = {
         "metric": METRIC, "value": n * K / (ms_multi * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W,
         "ms_per_step": ms_multi / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u8" if wl["bit_depth"] == 8 else "u16", "data": "synthetic (seeded sequences, see DESIGN.md)",
+        "dtype": "u8" if wl["bit_depth"] == 8 else "u16", "data": "synthetic (seeded sinusoid-texture sequences with planted global/patch motion and noise; ladder by Q16 bilinear)",
         "config": {"workload": args.config, "ladder_frames_per_step": n, "rungs": [f"{w}x{h}" for (w, h) in sizes],
                    "reference_rung": f"{sizes[ref_i][0]}x{sizes[ref_i][1]}", "search_range": wl["R"],
                    "refine_range": wl["r"], "bit_depth": wl["bit_depth"],
