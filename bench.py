@@ -79,7 +79,7 @@ PIPE_STREAMS = 3  # streams (and frame slots) of the pipelined device measuremen
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM bytes (read + write) of one launch from an ncu capture of the bench
-# command (profiles/ladder1080_launch_list.md), keyed by kernel, workload and
+# command (the launch-list summary under profiles/), keyed by kernel, workload and
 # the hash of the kernel sources it was taken on: null once a kernel changes.
 KERNEL_SOURCES = {"full_search": ["me_full.cu", "common.cuh"], "dependent": ["me_dependent.cu", "common.cuh"]}
 TRAFFIC_NCU = {
