@@ -269,8 +269,9 @@ LADDER_API ladder_status ladder_set_parents(ladder_t *ladder, const int *parent)
  * that runs out sets the device status to LADDER_E_TIMEOUT, read by
  * ladder_sync).  Independent and dependent analyses both take it (a tier's
  * decisions are final before the next tier derives its rules from them);
- * ladder_decide_qps, ladder_refine_subpel and analyze_reference_noalloc keep
- * the predictor (0, 0).  LADDER_E_INVAL for another mode. */
+ * ladder_decide_qps decides every further QP with it too (one wavefront
+ * launch per QP, in order); ladder_refine_subpel and analyze_reference_noalloc
+ * keep the predictor (0, 0).  LADDER_E_INVAL for another mode. */
 LADDER_API ladder_status ladder_set_mv_predictor(ladder_t *ladder, int mode);
 
 /* Decisions of one analysed rung at further QPs (intra-resolution analysis

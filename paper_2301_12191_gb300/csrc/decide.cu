@@ -182,7 +182,8 @@ __global__ void __launch_bounds__(kMvpThreads, 12) k_decide_mvp(const __grid_con
     const MvpItem &it = b.item[dev::item_of_cta(b.item, b.n)];
     const RungInfo &ri = b.rung[it.rung];
     const RungGeom &g = ri.g;
-    const DevDecisions out = decisions_at(it.block, ri.off);
+    const DevDecisions res = decisions_at(it.block, ri.off);  // the resident vectors and SATDs
+    const DevDecisions out = b.use_out ? b.out : res;           // where the decisions go
     const int nctu = g.ctu_cols * g.ctu_rows;
     unsigned long long *hand = reinterpret_cast<unsigned long long *>(it.block + ri.off.mvp_flag);  // [CTU][N8]
     unsigned *gen = reinterpret_cast<unsigned *>(hand + static_cast<long>(nctu) * N8), *rows_done = gen + 1;
@@ -215,9 +216,9 @@ __global__ void __launch_bounds__(kMvpThreads, 12) k_decide_mvp(const __grid_con
         }
         if (present) {
             const long gi = static_cast<long>(fy) * g.cols[kd] + fx;
-            p_mvx = __ldcg(out.mvx[kd] + gi);
-            p_mvy = __ldcg(out.mvy[kd] + gi);
-            p_satd = __ldcg(out.satd[kd] + gi);
+            p_mvx = __ldcg(res.mvx[kd] + gi);
+            p_mvy = __ldcg(res.mvy[kd] + gi);
+            p_satd = __ldcg(res.satd[kd] + gi);
         }
     };
     auto stage = [&]() {

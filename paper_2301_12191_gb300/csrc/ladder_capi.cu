@@ -1023,6 +1023,32 @@ ladder_status ladder_decide_qps(ladder_t *l, int rung, int frame_id, int n, cons
         b.out[k].leaf_mvy = o.leaf_mvy;
     }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (l->mv_predictor) {
+        // spatial predictor: one wavefront launch per QP, in order on the
+        // stream (each takes a new generation of the block's hand-off area)
+        if (l->mvp_capacity <= 0) l->mvp_capacity = decide_mvp_capacity(l->geo.ctu_size, l->sm_count);
+        if (g.ctu_rows > l->mvp_capacity)
+            return fail(l, LADDER_E_INVAL, "%d CTU rows exceed the %d resident wavefront CTAs", g.ctu_rows,
+                        l->mvp_capacity);
+        auto *mb = new (std::nothrow) MvpBatch{};
+        if (!mb) return fail(l, LADDER_E_NOMEM, "wavefront batch table");
+        for (int r = 0; r < l->geo.n_rungs; ++r) mb->rung[r] = l->info[r];
+        mb->status = l->d_status;
+        mb->n = 1;
+        mb->use_out = 1;
+        for (int k = 0; k < n; ++k) {
+            mb->item[0] = MvpItem{slot->rungs[rung].block, rung, qps[k], b.dependent, 0};
+            mb->out = b.out[k];
+            const cudaError_t e =
+                traced(l, 8, s, [&] { return launch_decide_mvp(l->geo.ctu_size, *mb, g.ctu_rows, s); });
+            if (e != cudaSuccess) {
+                delete mb;
+                return cuda_fail(l, e, "further-QP decisions with the spatial predictor");
+            }
+        }
+        delete mb;
+        return LADDER_OK;
+    }
     const cudaError_t e = traced(l, 6, s, [&] { return launch_decide_qps(l->geo.ctu_size, b, s); });
     if (e != cudaSuccess) return cuda_fail(l, e, "further-QP decisions");
     return LADDER_OK;

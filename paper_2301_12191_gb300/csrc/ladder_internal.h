@@ -349,6 +349,10 @@ constexpr int kMaxMvpItems = kMaxDepItems;
 struct MvpBatch {
     int n;
     int *status;
+    // use_out: decisions at item 0's QP into `out` (cost, best, split, leaf
+    // maps; n must be 1) instead of in place (further-QP decisions)
+    int use_out;
+    DevDecisions out;
     RungInfo rung[kMaxRungs];
     MvpItem item[kMaxMvpItems];
 };

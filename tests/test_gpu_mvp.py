@@ -5,6 +5,7 @@ split and leaf maps row by row -- equals the oracle's analysis with mvp=1
 independent rungs, dependent rungs of a cascaded chain (per call and
 batched), after switching back to the predictor (0, 0), and for a replayed
 CUDA graph."""
+import numpy as np
 import pytest
 
 import oracle
@@ -113,10 +114,11 @@ def test_mvp_graph_replay_new_content():
 
 
 def test_mvp_batch_wider_than_the_device():
-    """64 frames of 2160p in one batch: 2176 CTU rows, more than the wavefront
-    CTAs that fit on the device at once, so the decisions run as several
-    cooperative launches.  Every frame equals the same frame analysed alone."""
-    W, H, R, qp = 3840, 2160, 4, 30
+    """64 frames of 1920x2496 in one batch: 64 x 39 = 2496 CTU rows, more than
+    the wavefront CTAs that can ever be resident (16 per SM: 2048 threads of
+    128), so the decisions run as several cooperative launches.  Every frame
+    equals the same frame analysed alone."""
+    W, H, R, qp = 1920, 2496, 4, 30
     srcs = [synth.frame_pair(80 + k, W, H, global_range=3, patch_range=4) for k in range(4)]
     planes = [(L.device_plane(p.cur), L.device_plane(p.ref)) for p in srcs]
     with L.Ladder([(W, H)], 0, search_range=R, max_frames=64) as lad:
@@ -134,3 +136,39 @@ def test_mvp_batch_wider_than_the_device():
     assert launches >= 2, "the batch should need more than one wavefront launch"
     for f, dec in got.items():
         assert_decisions_equal(dec, alone[f % 4], 64, where=f"batched frame {f}")
+
+
+@pytest.mark.parametrize("bd", [8, 10])
+def test_mvp_further_qps(bd):
+    """With the spatial predictor on, the decisions at further QPs equal the
+    oracle's analysis at each QP with the predictor (a dependent rung keeps
+    the rules of the reference decided at the master QP)."""
+    pairs, _ = synth.ladder_pairs(46, source=(640, 360), rungs=[(480, 270), (320, 180)], bit_depth=bd)
+    sizes = [(w, h) for (w, h, _, _) in pairs]
+    R, r, master, others = 10, 3, 27, [22, 37]
+    with L.Ladder(sizes, 2, bit_depth=bd, search_range=R, refine_range=r, max_frames=1) as lad:
+        lad.set_mv_predictor(1)
+        planes = [(L.device_plane(c), L.device_plane(f)) for (_, _, c, f) in pairs]
+        lad.analyze_reference(0, *planes[2], master)
+        lad.analyze_dependents(0, [(i, planes[i][0], planes[i][1]) for i in (0, 1)], master)
+        lad.kernel_stats(reset=True)
+        got = {i: lad.decide_qps(i, 0, others + [master]) for i in range(3)}
+        assert lad.kernel_stats()["decide_mvp"][0] == 3 * 3  # one launch per QP and rung
+        master_fetch = [lad.fetch(i, 0) for i in range(3)]
+    ref_master = oracle.analyze(pairs[2][2], pairs[2][3], qp=master, search_range=R, mvp=1)
+    for q in others + [master]:
+        for i in range(3):
+            c, f = pairs[i][2], pairs[i][3]
+            if i == 2:
+                ora = oracle.analyze(c, f, qp=q, search_range=R, mvp=1)
+            else:
+                ora = oracle.analyze(c, f, qp=q, search_range=r, dep=dep_from(ref_master, sizes[2]), mvp=1)
+            for k in ("cost", "best", "split"):
+                for d in range(len(ora["grid"])):
+                    assert np.array_equal(np.asarray(got[i][q][k][d]), np.asarray(ora[k][d])), (i, q, k, d)
+            for k in ("leaf_depth", "leaf_mvx", "leaf_mvy"):
+                assert np.array_equal(np.asarray(got[i][q][k]), np.asarray(ora[k])), (i, q, k)
+    for i in range(3):  # the master QP again: the analysis's own decisions
+        for k in ("cost", "best", "split"):
+            for d in range(len(master_fetch[i]["grid"])):
+                assert np.array_equal(np.asarray(got[i][master][k][d]), np.asarray(master_fetch[i][k][d]))
