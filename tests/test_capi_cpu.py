@@ -92,3 +92,22 @@ def test_odd_rung_size_rejected(lib):
     h = ctypes.c_void_p()
     lib.ladder_init.restype = ctypes.c_int
     assert lib.ladder_init(ctypes.byref(g), None, ctypes.byref(h)) == -1
+
+
+def test_null_handles_are_refused_without_touching_a_device():
+    """Every entry point that takes a handle refuses NULL with LADDER_E_INVAL
+    (and the size queries answer 0) before any CUDA call."""
+    lib = L.load()
+    E_INVAL = -1
+    assert lib.ladder_set_mv_predictor(None, 0) == E_INVAL
+    assert lib.ladder_set_parents(None, None) == E_INVAL
+    assert lib.ladder_subpel_workspace_bytes(None, 0) == 0
+    assert lib.ladder_frame_bytes(None) == 0
+    assert lib.ladder_refine_subpel_batch(None, 1, None, None) == E_INVAL
+    assert lib.ladder_decide_qps(None, 0, 0, 1, None, None, None) == E_INVAL
+    out = ctypes.c_void_p()
+    assert lib.ladder_pipeline_create(None, 2, 0, 1024, None, None, None, ctypes.byref(out)) == E_INVAL
+    assert lib.ladder_pipeline_submit(None, None, 27, None, None) == E_INVAL
+    assert lib.ladder_pipeline_wait(None, 0) == E_INVAL
+    lib.ladder_pipeline_destroy(None)
+    lib.ladder_destroy(None)
