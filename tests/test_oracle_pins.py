@@ -114,6 +114,19 @@ def test_lambda_anchors_and_doubling():
         assert abs(lam[q + 6] - 2 * lam[q]) <= 2
 
 
+def test_library_lambda_table_equals_the_oracle():
+    """The CUDA library keeps lambda as a frozen integer table (written once
+    by its generator script); the oracle computes it from the formula.  The
+    two copies must agree at every QP."""
+    import re
+    path = os.path.join(os.path.dirname(GOLDEN), os.pardir, "paper_2301_12191_gb300", "csrc", "lambda_table.inc")
+    with open(path) as f:
+        body = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    table = [int(v) for v in re.findall(r"-?\d+", body)]
+    assert len(table) == 52
+    assert table == [oracle.lambda_q16(q) for q in range(52)]
+
+
 # ------------------------------------------------------------ helpers ----
 def _brute_indep(cur, ref, R, ctu):
     """Exhaustive search written independently: edge-padded planes and a
@@ -350,6 +363,67 @@ def test_unconstrained_dependent_equals_independent():
             assert np.array_equal(indep[k][d], dep[k][d]), (k, d)
     for k in ("leaf_depth", "leaf_mvx", "leaf_mvy"):
         assert np.array_equal(indep[k], dep[k])
+
+
+def _brute_dep(cur, ref, x0, y0, S, cx, cy, r):
+    """Exhaustive refinement around the centre (cx, cy), written
+    independently: edge-clamped reference reads and the key (SAD, |ox|+|oy|,
+    oy, ox) over the offsets (ox, oy) from the centre."""
+    H, W = cur.shape
+    ys = np.arange(y0, y0 + S)
+    xs = np.arange(x0, x0 + S)
+    blk = cur[np.ix_(np.minimum(ys, H - 1), np.minimum(xs, W - 1))].astype(np.int64)
+    best = None
+    for oy in range(-r, r + 1):
+        for ox in range(-r, r + 1):
+            ry = np.clip(ys + cy + oy, 0, H - 1)
+            rx = np.clip(xs + cx + ox, 0, W - 1)
+            sad = int(np.abs(blk - ref[np.ix_(ry, rx)].astype(np.int64)).sum())
+            key = (sad, abs(ox) + abs(oy), oy, ox)
+            if best is None or key < best:
+                best = key
+    return cx + best[3], cy + best[2], best[0]
+
+
+@pytest.mark.parametrize("content", ["flat", "columns", "levels3"])
+def test_dependent_tie_break_is_relative_to_the_centre(content):
+    """Ratio-2 dependent rung whose co-located reference leaves carry
+    non-zero vectors, on content where many candidates tie: every evaluated
+    CU must return the brute-force argmin of (SAD, L1 offset from the
+    centre, dy, dx).  On flat content every SAD is 0, so the vector is the
+    centre itself (a tie-break on the absolute vector would move it)."""
+    rng = np.random.default_rng(71)
+    Wr, Hr, Wd, Hd, r = 40, 32, 80, 64, 3
+    n8 = (Wr // 8) * (Hr // 8)
+    lmx = rng.integers(-3, 4, n8).astype(np.int16)
+    lmy = rng.integers(-3, 4, n8).astype(np.int16)
+    lmy[lmy == 0] = 2
+    dep = {"ref_size": (Wr, Hr), "leaf_depth": np.full(n8, 3, np.uint8), "leaf_mvx": lmx, "leaf_mvy": lmy}
+    if content == "flat":
+        ref = np.full((Hd, Wd), 100, np.uint8)
+        cur = ref.copy()
+    elif content == "columns":
+        ref = np.tile((40 * (np.arange(Wd) % 4)).astype(np.uint8), (Hd, 1))
+        cur = ref.copy()
+    else:
+        ref = rng.integers(0, 3, (Hd, Wd)).astype(np.uint8)
+        cur = np.roll(ref, (1, -2), axis=(0, 1)) ^ (rng.random((Hd, Wd)) < 0.2).astype(np.uint8)
+    out = oracle.analyze(cur, ref, qp=30, search_range=r, ctu=64, dep=dep, threads=2)
+    checked = moved = 0
+    for d in range(4):
+        S = 64 >> d
+        cols, rows = out["grid"][d]
+        for i in np.flatnonzero(out["evaluated"][d]):
+            x0, y0 = (i % cols) * S, (i // cols) * S
+            cx, cy, _, _ = oracle.derive_rule((Wd, Hd), dep, d, x0, y0)
+            want = _brute_dep(cur, ref, x0, y0, S, cx, cy, r)
+            got = (int(out["mvx"][d][i]), int(out["mvy"][d][i]), int(out["sad"][d][i]))
+            assert got == want, (content, d, x0, y0, (cx, cy), got, want)
+            checked += 1
+            moved += cy != 0
+            if content == "flat":
+                assert got[:2] == (cx, cy)
+    assert checked >= 40 and moved >= 20
 
 
 def test_deq_worked_examples():

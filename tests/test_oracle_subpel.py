@@ -83,6 +83,27 @@ def test_planted_quarter_pel_motion_found(qx, qy):
     assert hits >= 0.9 * total, (hits, total)
 
 
+@pytest.mark.parametrize("qx,qy", [(2, 1), (-2, 5), (6, -3), (-3, -6)])
+def test_quarter_round_centres_on_the_half_pel_best(qx, qy):
+    """Planted vectors with one component at a half-pel position and the
+    other at a quarter-pel one: a half-pel component is at least 2 quarter
+    units from every integer vector, so the quarter-pel round reaches the
+    planted vector only when it is centred on the half-pel round's best (a
+    quarter round around the integer vector stops one quarter unit short)."""
+    assert qx % 4 == 2 or qy % 4 == 2
+    cur, ref = _planted_quarter_pel(64, qx, qy)
+    ana = oracle.analyze(cur, ref, qp=22, search_range=4, ctu=32)
+    sp = oracle.refine_subpel(cur, ref, ana, qp=22, ctu=32)
+    cols, rows = sp["grid"][2]
+    hits = total = 0
+    for by in range(2, rows - 2):
+        for bx in range(2, cols - 2):
+            i = by * cols + bx
+            total += 1
+            hits += sp["qmvx"][2][i] == qx and sp["qmvy"][2][i] == qy and sp["satd"][2][i] == 0
+    assert hits >= 0.9 * total, (hits, total)
+
+
 def test_refinement_never_raises_the_cost():
     fp = synth.frame_pair(62, 96, 64, 8)
     ana = oracle.analyze(fp.cur, fp.ref, qp=27, search_range=6, ctu=32)
