@@ -224,6 +224,25 @@ typedef enum {
 LADDER_API ladder_status ladder_set_tuning(ladder_t *ladder, int knob, int value);
 LADDER_API ladder_status ladder_get_tuning(const ladder_t *ladder, int knob, int *value);
 
+/* Test controls for the failure paths (no counterpart in the paper): they
+ * exist so that a test can make a bounded device wait run out on purpose and
+ * see it reported, with nothing faulting or hanging.
+ *   LADDER_DEBUG_WAIT_POLLS    polls of each wavefront wait (spatial MV
+ *                              predictor) before it gives up: 0 (default,
+ *                              2^22 polls, about a second) or 64 .. 2^22
+ *   LADDER_DEBUG_LOST_HANDOFF  1: the wavefront rows wait for a hand-off that
+ *                              no row publishes, so every wait of a row
+ *                              below the first runs out, sets the device
+ *                              status to LADDER_E_TIMEOUT and stops its row
+ *                              (the decisions of that launch are not to be
+ *                              trusted); 0 (default): normal operation
+ * Apply to later launches.  LADDER_E_INVAL for an unknown control or value. */
+typedef enum {
+    LADDER_DEBUG_WAIT_POLLS = 0,
+    LADDER_DEBUG_LOST_HANDOFF = 1
+} ladder_debug_control;
+LADDER_API ladder_status ladder_set_debug(ladder_t *ladder, int control, int value);
+
 /* Device bytes the handle holds (decision buffers of every frame slot). */
 LADDER_API long ladder_device_bytes(const ladder_t *ladder);
 
@@ -397,9 +416,14 @@ LADDER_API ladder_status ladder_fetch_frame_async(ladder_t *ladder, int frame_id
  * overlap.  submit blocks the host only until the slot's previous frame is
  * done (its host_out complete) and returns a ticket; ladder_pipeline_wait
  * returns once the ticket's decisions are in its host_out; host_in may be
- * reused then.  Device timeouts are reported by ladder_sync.  Errors:
- * LADDER_E_INVAL (sizes, layout, depth), LADDER_E_CUDA; the analyses' own
- * errors (LADDER_E_BUSY without free frame slots) pass through. */
+ * reused then.  The device status word is read back with every frame's
+ * decisions: a bounded device wait that ran out (the decisions of the frames
+ * then in flight are not to be trusted) is reported once, as
+ * LADDER_E_TIMEOUT, by the wait for a frame that read it back, or else by
+ * the next submit that finds it (which then enqueues nothing); the word is
+ * cleared when it is reported.  Errors: LADDER_E_INVAL (sizes, layout,
+ * depth), LADDER_E_CUDA; the analyses' own errors (LADDER_E_BUSY without
+ * free frame slots) pass through. */
 typedef struct ladder_pipeline ladder_pipeline_t;
 LADDER_API ladder_status ladder_pipeline_create(ladder_t *ladder, int depth, int base_frame_id, long in_bytes,
                                                 const long *cur_off, const long *ref_off, const long *pitch,
@@ -424,7 +448,9 @@ LADDER_API ladder_status ladder_release_frame(ladder_t *ladder, int frame_id);
  * LADDER_E_TIMEOUT), clearing it. */
 LADDER_API ladder_status ladder_sync(ladder_t *ladder, void *cuda_stream);
 
-/* Frees every buffer; waits for the device first.  NULL is ignored. */
+/* Waits for the work the handle's calls enqueued (on the streams they were
+ * given, and its graphs' replays), then frees every buffer.  Other work on
+ * the device is not waited for.  NULL is ignored. */
 LADDER_API void ladder_destroy(ladder_t *ladder);
 
 /* Text of the last error on this handle ("" if none).  Valid until the next call. */
@@ -460,16 +486,38 @@ LADDER_API ladder_status ladder_profile_read(ladder_t *ladder, int kind, long *l
  * that loads the library holds it until exit): frames of at most 3083 CTUs
  * of 64x64 (a 3840x2160 frame has 2040; about 4x that count at CTU 32) fit; larger ones
  * return LADDER_E_INVAL, like any argument the other entry points refuse.
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  All calls
- * share the array and it keeps the last call's contents (each call resets
- * what must start empty); calls whose work overlaps on the GPU race on it, so
- * order them.  A bounded device wait that runs out is recorded in the
- * array's status word but not reported by this call. */
+ * Every call looks up the array's device address in the current device's
+ * context; the first lookup in a context loads the module there, so make the
+ * first call on a device before any stream capture.  All calls share the
+ * array and it keeps the last call's contents (each call resets what must
+ * start empty); calls whose work overlaps on the GPU race on it, so order
+ * them.  A bounded device wait that runs out (its decisions are then not to
+ * be trusted) sets the array's status word, which stays set until
+ * analyze_reference_noalloc_status reads it. */
 LADDER_API ladder_status analyze_reference_noalloc(const void *cur, const void *ref, int width, int height,
                                                    long pitch_bytes, int bit_depth, int ctu_size, int search_range,
                                                    int qp, int satd_mode, const ladder_decisions *out,
                                                    void *cuda_stream);
+
+/* Status of the allocation-free analyses on the current device since the
+ * last query: waits for `cuda_stream` (order it after the calls to check),
+ * then returns LADDER_OK, or LADDER_E_TIMEOUT if a bounded device wait of one
+ * of them ran out (their decisions are not to be trusted), clearing the
+ * status word.  Allocates nothing.  LADDER_E_CUDA if a CUDA call fails. */
+LADDER_API ladder_status analyze_reference_noalloc_status(void *cuda_stream);
+
+/* Measures, on the current device, the throughput of the packed
+ * absolute-difference accumulate in the form the motion searches issue it
+ * (no counterpart in the paper: the denominator of the integer-ALU
+ * roofline, confirmed in the same run as the kernels it bounds).
+ * bit_depth 8: vabsdiff4 .add, 4 absolute differences per instruction;
+ * 10: min.u16x2 + mad.lo, the sum(min(a, b)) term of the 10-bit SAD
+ * (sum(a) + sum(b) - 2 sum(min(a, b))), 2 per pair.  Sixteen independent
+ * chains per thread, eight 256-thread CTAs per SM, one warm-up and one timed
+ * launch with CUDA events on `cuda_stream`; waits for them.  Writes absolute
+ * differences per second to *absdiffs_per_s.  LADDER_E_INVAL for another
+ * bit depth or a NULL output, LADDER_E_CUDA if a CUDA call fails. */
+LADDER_API ladder_status ladder_measure_sad_rate(int bit_depth, void *cuda_stream, double *absdiffs_per_s);
 
 /* Library version string. */
 LADDER_API const char *ladder_version(void);

@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(kThreads) k_decide(const __grid_constant__ Dec
     const DecideItem &item = b.item[ii];
     const RungInfo &ri = b.rung[item.rung];
     const RungGeom &g = ri.g;
-    const unsigned long long *keys = reinterpret_cast<const unsigned long long *>(item.block + ri.off.keys);
+    const unsigned long long *keys = reinterpret_cast<const unsigned long long *>(array_at(item.block, ri.off.keys));
     const int tid = threadIdx.x;
     const int ctu_idx = blockIdx.x - item.cta_begin;
     const int x0 = (ctu_idx % g.ctu_cols) * CTU, y0 = (ctu_idx / g.ctu_cols) * CTU;
@@ -126,7 +126,6 @@ __global__ void __launch_bounds__(kThreads) k_decide_qps(const __grid_constant__
 // replayed graph's included) never pass for this one.
 
 constexpr int kMvpThreads = 128;
-constexpr int kMvpSpin = 1 << 22;  // polls (an L2 round trip each, under a microsecond) before a wait gives up
 
 __device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p)
 {
@@ -192,6 +191,9 @@ __global__ void __launch_bounds__(kMvpThreads, 12) k_decide_mvp(const __grid_con
     const int cy = static_cast<int>(blockIdx.x) - it.cta_begin;
     const int lam = c_lambda_q16[it.qp];
     const unsigned target = __ldcg(gen) + 1u;  // published by the previous launch on this block
+    // the generation a reader waits for: this launch's, unless a test asks
+    // for one that no row publishes (every wait then runs out)
+    const unsigned want = target + (b.lost_handoff ? 1u : 0u);
     // this thread's CU key (NKEY <= threads): its depth and place in the CTU
     static_assert(C::NKEY <= kMvpThreads, "one key per thread");
     const int ki = tid;
@@ -243,9 +245,9 @@ __global__ void __launch_bounds__(kMvpThreads, 12) k_decide_mvp(const __grid_con
             if (qcx < g.ctu_cols && qcx * CTU + 8 * qb < g.W8) {
                 const unsigned long long *w = hand + (static_cast<long>(cy - 1) * g.ctu_cols + qcx) * N8 + qb;
                 bool ok = false;
-                for (int n = 0; n < kMvpSpin; ++n) {
+                for (int n = 0; n < b.spin; ++n) {
                     const unsigned long long x = ld_relaxed64(w);
-                    if (static_cast<unsigned>(x >> 32) == target) {
+                    if (static_cast<unsigned>(x >> 32) == want) {
                         v = static_cast<uint32_t>(x);
                         ok = true;
                         break;

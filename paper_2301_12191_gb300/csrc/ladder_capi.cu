@@ -42,6 +42,14 @@ struct ProfEvent {
     cudaEvent_t start, stop;
 };
 
+// The last work a handle enqueued on one stream: ladder_destroy waits for
+// these events (the handle's own work) rather than for the whole device.
+struct StreamMark {
+    cudaStream_t stream;
+    cudaEvent_t done;
+};
+constexpr size_t kMaxMarks = 16;
+
 }  // namespace
 
 // One set of dependent task lists: the counters, tasks, positions and sum
@@ -88,6 +96,9 @@ struct ladder {
     int tune_fs_band = kFsBand, tune_fs_group = 0, tune_fs_fuse = 1, tune_dep_band = 0, tune_dep_range = 16,
         tune_dep_ctas = 0;
     int mv_predictor = 0;  // 0: (0, 0); 1: spatial, decided in wavefront order (ladder_set_mv_predictor)
+    // test controls (ladder_set_debug)
+    int dbg_wait_polls = 0;   // 0: kMvpSpinDefault
+    int dbg_lost_handoff = 0;
     int mvp_capacity = 0;  // resident CTAs of the wavefront kernel
     char *host_stage = nullptr;  // pinned staging for fetch_decisions
     size_t host_stage_bytes = 0;
@@ -97,9 +108,14 @@ struct ladder {
     double total_ms[kKinds] = {};
     std::vector<ProfEvent> pending;
     std::vector<cudaEvent_t> spare;
+    // streams the handle's calls enqueued work on (not inside a capture, nor
+    // a pipeline's own streams, which the pipeline waits for itself)
+    std::vector<StreamMark> marks;
+    int quiet = 0;
 };
 
 struct ladder_graph {
+    ladder_t *l = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -156,6 +172,43 @@ cudaError_t traced(ladder_t *l, int kind, cudaStream_t s, F &&launch)
     cudaEventRecord(pe.stop, s);
     l->pending.push_back(pe);
     return e;
+}
+
+// Records, after a public call's work on stream s, an event that
+// ladder_destroy waits for.
+void mark_stream(ladder_t *l, cudaStream_t s)
+{
+    if (l->quiet) return;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return;  // a graph: its launches are marked instead
+    for (auto &m : l->marks)
+        if (m.stream == s) {
+            cudaEventRecord(m.done, s);
+            return;
+        }
+    if (l->marks.size() >= kMaxMarks) {  // the oldest stream: wait for it now
+        cudaEventSynchronize(l->marks.front().done);
+        cudaEventDestroy(l->marks.front().done);
+        l->marks.erase(l->marks.begin());
+    }
+    StreamMark m{s, nullptr};
+    if (cudaEventCreateWithFlags(&m.done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    cudaEventRecord(m.done, s);
+    l->marks.push_back(m);
+}
+
+// The status of a call that enqueued work on s: marks the stream on success.
+ladder_status marked(ladder_t *l, cudaStream_t s, ladder_status st)
+{
+    if (st == LADDER_OK) mark_stream(l, s);
+    return st;
 }
 
 void drain_events(ladder_t *l)
@@ -309,6 +362,8 @@ ladder_status launch_mvp(ladder_t *l, const Job *jobs, int n, int dependent, cud
     if (!b) return fail(l, LADDER_E_NOMEM, "wavefront batch table");
     for (int r = 0; r < l->geo.n_rungs; ++r) b->rung[r] = l->info[r];
     b->status = l->d_status;
+    b->spin = l->dbg_wait_polls > 0 ? l->dbg_wait_polls : kMvpSpinDefault;
+    b->lost_handoff = l->dbg_lost_handoff;
     int k = 0;
     while (k < n) {
         int m = 0, ctas = 0;
@@ -693,7 +748,7 @@ ladder_status analyze_independent(ladder_t *l, int rung, int frame_id, const voi
     Job job{slot, rung, cur, ref, pitch_bytes, qp};
     st = launch_independent(l, &job, 1, static_cast<cudaStream_t>(cuda_stream));
     if (st == LADDER_OK && rung == l->geo.ref_rung) slot->ref_done = 1;
-    return st;
+    return marked(l, static_cast<cudaStream_t>(cuda_stream), st);
 }
 
 ladder_status analyze_reference(ladder_t *l, int frame_id, const void *cur, const void *ref, long pitch_bytes,
@@ -728,7 +783,8 @@ ladder_status analyze_dependents(ladder_t *l, int frame_id, int n, const int *ru
     }
     std::vector<Job> jobs;
     for (int k = 0; k < n; ++k) jobs.push_back(Job{slot, rungs[k], cur[k], ref[k], pitch_bytes[k], qp});
-    return launch_dependents(l, jobs.data(), n, static_cast<cudaStream_t>(cuda_stream));
+    return marked(l, static_cast<cudaStream_t>(cuda_stream),
+                  launch_dependents(l, jobs.data(), n, static_cast<cudaStream_t>(cuda_stream)));
 }
 
 ladder_status analyze_dependent(ladder_t *l, int rung, int frame_id, const void *cur, const void *ref,
@@ -776,7 +832,7 @@ ladder_status ladder_analyze_batch(ladder_t *l, const ladder_request *reqs, int 
     if (st != LADDER_OK) return st;
     for (int k = 0; k < n; ++k) slots[k]->ref_done = 1;
     if (!dj.empty()) st = launch_dependents(l, dj.data(), static_cast<int>(dj.size()), s);
-    return st;
+    return marked(l, s, st);
 }
 
 ladder_status ladder_analyze_batch_independent(ladder_t *l, const ladder_request *reqs, int n, void *cuda_stream)
@@ -811,7 +867,7 @@ ladder_status ladder_analyze_batch_independent(ladder_t *l, const ladder_request
                                           static_cast<cudaStream_t>(cuda_stream));
     if (st == LADDER_OK)
         for (int k = 0; k < n; ++k) slots[k]->ref_done = 1;
-    return st;
+    return marked(l, static_cast<cudaStream_t>(cuda_stream), st);
 }
 
 ladder_status ladder_analyze_jobs(ladder_t *l, const ladder_job *jobs, int n, void *cuda_stream)
@@ -864,8 +920,8 @@ ladder_status ladder_analyze_jobs(ladder_t *l, const ladder_job *jobs, int n, vo
         for (const Job &jb : ij)
             if (jb.rung == l->geo.ref_rung) jb.slot->ref_done = 1;
     }
-    if (!dj.empty()) return launch_dependents(l, dj.data(), static_cast<int>(dj.size()), s);
-    return LADDER_OK;
+    if (!dj.empty()) return marked(l, s, launch_dependents(l, dj.data(), static_cast<int>(dj.size()), s));
+    return marked(l, s, LADDER_OK);
 }
 
 ladder_status ladder_capture_batch(ladder_t *l, const ladder_request *reqs, int n, void *cuda_stream,
@@ -896,6 +952,7 @@ ladder_status ladder_capture_batch(ladder_t *l, const ladder_request *reqs, int 
         cudaGraphDestroy(graph);
         return LADDER_E_NOMEM;
     }
+    g->l = l;
     g->graph = graph;
     e = cudaGraphInstantiate(&g->exec, graph, 0);
     if (e != cudaSuccess) {
@@ -910,8 +967,10 @@ ladder_status ladder_capture_batch(ladder_t *l, const ladder_request *reqs, int 
 ladder_status ladder_graph_launch(ladder_graph_t *g, void *cuda_stream)
 {
     if (!g || !g->exec) return LADDER_E_INVAL;
-    return cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess ? LADDER_OK
-                                                                                          : LADDER_E_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaGraphLaunch(g->exec, s) != cudaSuccess) return LADDER_E_CUDA;
+    if (g->l) mark_stream(g->l, s);
+    return LADDER_OK;
 }
 
 void ladder_graph_destroy(ladder_graph_t *g)
@@ -1034,6 +1093,8 @@ ladder_status ladder_decide_qps(ladder_t *l, int rung, int frame_id, int n, cons
         if (!mb) return fail(l, LADDER_E_NOMEM, "wavefront batch table");
         for (int r = 0; r < l->geo.n_rungs; ++r) mb->rung[r] = l->info[r];
         mb->status = l->d_status;
+        mb->spin = l->dbg_wait_polls > 0 ? l->dbg_wait_polls : kMvpSpinDefault;
+        mb->lost_handoff = l->dbg_lost_handoff;
         mb->n = 1;
         mb->use_out = 1;
         for (int k = 0; k < n; ++k) {
@@ -1047,11 +1108,11 @@ ladder_status ladder_decide_qps(ladder_t *l, int rung, int frame_id, int n, cons
             }
         }
         delete mb;
-        return LADDER_OK;
+        return marked(l, s, LADDER_OK);
     }
     const cudaError_t e = traced(l, 6, s, [&] { return launch_decide_qps(l->geo.ctu_size, b, s); });
     if (e != cudaSuccess) return cuda_fail(l, e, "further-QP decisions");
-    return LADDER_OK;
+    return marked(l, s, LADDER_OK);
 }
 
 ladder_status fetch_decisions(ladder_t *l, int rung, int frame_id, ladder_decisions *out, void *cuda_stream)
@@ -1187,7 +1248,7 @@ ladder_status ladder_refine_subpel_batch(ladder_t *l, int n, const ladder_subpel
         traced(l, 7, s, [&] { return launch_subpel(l->geo.bit_depth, l->geo.ctu_size, *b, ctas, ictas, s); });
     delete b;
     if (e != cudaSuccess) return cuda_fail(l, e, "quarter-pel refinement");
-    return LADDER_OK;
+    return marked(l, s, LADDER_OK);
 }
 
 ladder_status ladder_refine_subpel(ladder_t *l, int rung, int frame_id, const void *cur, const void *ref,
@@ -1238,7 +1299,7 @@ ladder_status ladder_fetch_frame_async(ladder_t *l, int frame_id, void *host_dst
         if (e != cudaSuccess) return cuda_fail(l, e, "frame fetch copy");
         dst += n;
     }
-    return LADDER_OK;
+    return marked(l, s, LADDER_OK);
 }
 
 struct ladder_pipeline {
@@ -1252,6 +1313,11 @@ struct ladder_pipeline {
     std::vector<cudaEvent_t> ev_in, ev_comp, ev_out;
     std::vector<long> slot_ticket;  // the last ticket of each slot (-1: none yet)
     long next = 0;
+    // per slot: the device status word as read back after the slot's last
+    // frame (pinned), and whether it has been reported yet
+    int *h_status = nullptr;
+    std::vector<char> reported;
+    int pending = 0;  // a non-zero status of a frame whose ticket was not waited for
 };
 
 namespace {
@@ -1264,6 +1330,7 @@ void pipeline_free(ladder_pipeline *p)
     if (p->s_in) cudaStreamSynchronize(p->s_in);
     if (p->s_out) cudaStreamSynchronize(p->s_out);
     for (char *b : p->dev_in) cudaFree(b);
+    if (p->h_status) cudaFreeHost(p->h_status);
     for (cudaStream_t s : p->comp)
         if (s) cudaStreamDestroy(s);
     if (p->s_in) cudaStreamDestroy(p->s_in);
@@ -1303,6 +1370,7 @@ ladder_status ladder_pipeline_create(ladder_t *l, int depth, int base_frame_id, 
     p->ref_off.assign(ref_off, ref_off + l->geo.n_rungs);
     p->pitch.assign(pitch, pitch + l->geo.n_rungs);
     p->slot_ticket.assign(depth, -1);
+    p->reported.assign(depth, 1);
     p->dev_in.assign(depth, nullptr);
     p->comp.assign(depth, nullptr);
     for (auto *v : {&p->ev_in, &p->ev_comp, &p->ev_out}) v->assign(depth, nullptr);
@@ -1315,6 +1383,8 @@ ladder_status ladder_pipeline_create(ladder_t *l, int depth, int base_frame_id, 
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocHost(&p->h_status, sizeof(int) * depth);
+    if (e == cudaSuccess) memset(p->h_status, 0, sizeof(int) * depth);
     if (e != cudaSuccess) {
         pipeline_free(p);
         return cuda_fail(l, e, "pipeline buffers and streams");
@@ -1323,20 +1393,57 @@ ladder_status ladder_pipeline_create(ladder_t *l, int depth, int base_frame_id, 
     return LADDER_OK;
 }
 
+namespace {
+
+// Status read back with slot j's last frame (complete): a non-zero word is
+// kept to be reported once, and the device word is cleared.
+void pipeline_collect(ladder_pipeline *p, int j)
+{
+    if (p->reported[j]) return;
+    p->reported[j] = 1;
+    if (p->h_status[j] == kStatusOk) return;
+    if (!p->pending) p->pending = p->h_status[j];
+    cudaMemsetAsync(p->l->d_status, 0, sizeof(int), p->s_out);
+    cudaStreamSynchronize(p->s_out);
+}
+
+// Reports (once) a device status that frames of the pipeline read back.
+ladder_status pipeline_take_pending(ladder_pipeline *p)
+{
+    if (!p->pending) return LADDER_OK;
+    const int st = p->pending;
+    p->pending = 0;
+    return device_status_error(p->l, st);
+}
+
+}  // namespace
+
 ladder_status ladder_pipeline_submit(ladder_pipeline_t *p, const void *host_in, int qp, void *host_out, long *ticket)
 {
     if (!p || !host_in || !host_out) return LADDER_E_INVAL;
     ladder_t *l = p->l;
     const int j = static_cast<int>(p->next % p->depth), frame_id = p->base + j;
     cudaError_t e = cudaSuccess;
-    if (p->slot_ticket[j] >= 0) e = cudaEventSynchronize(p->ev_out[j]);  // the slot's previous frame is home
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p->dev_in[j], host_in, static_cast<size_t>(p->in_bytes),
-                                              cudaMemcpyHostToDevice, p->s_in);
+    if (p->slot_ticket[j] >= 0) {
+        e = cudaEventSynchronize(p->ev_out[j]);  // the slot's previous frame is home
+        if (e != cudaSuccess) return cuda_fail(l, e, "pipeline slot");
+        pipeline_collect(p, j);
+    }
+    // a bounded device wait that ran out in an earlier frame: report it
+    // before taking more work (nothing of this frame is enqueued)
+    ladder_status pst = pipeline_take_pending(p);
+    if (pst != LADDER_OK) return pst;
+    e = cudaMemcpyAsync(p->dev_in[j], host_in, static_cast<size_t>(p->in_bytes), cudaMemcpyHostToDevice, p->s_in);
     if (e == cudaSuccess) e = cudaEventRecord(p->ev_in[j], p->s_in);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->comp[j], p->ev_in[j], 0);
     if (e != cudaSuccess) return cuda_fail(l, e, "pipeline upload");
     const int rr = l->geo.ref_rung, n = l->geo.n_rungs;
     char *in = p->dev_in[j];
+    struct Quiet {  // the pipeline waits for its own streams: no per-call marks
+        ladder_t *l;
+        explicit Quiet(ladder_t *x) : l(x) { ++l->quiet; }
+        ~Quiet() { --l->quiet; }
+    } quiet(l);
     ladder_status st = analyze_reference(l, frame_id, in + p->cur_off[rr], in + p->ref_off[rr], p->pitch[rr], qp,
                                          p->comp[j]);
     if (st != LADDER_OK) return st;
@@ -1360,8 +1467,11 @@ ladder_status ladder_pipeline_submit(ladder_pipeline_t *p, const void *host_in, 
     if (e != cudaSuccess) return cuda_fail(l, e, "pipeline ordering");
     st = ladder_fetch_frame_async(l, frame_id, host_out, p->out_bytes, p->s_out);
     if (st != LADDER_OK) return st;
-    e = cudaEventRecord(p->ev_out[j], p->s_out);
+    // the status word after this frame's analyses, read back with its decisions
+    e = cudaMemcpyAsync(&p->h_status[j], l->d_status, sizeof(int), cudaMemcpyDeviceToHost, p->s_out);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_out[j], p->s_out);
     if (e != cudaSuccess) return cuda_fail(l, e, "pipeline read-back");
+    p->reported[j] = 0;
     p->slot_ticket[j] = p->next;
     if (ticket) *ticket = p->next;
     ++p->next;
@@ -1373,10 +1483,12 @@ ladder_status ladder_pipeline_wait(ladder_pipeline_t *p, long ticket)
     if (!p) return LADDER_E_INVAL;
     if (ticket < 0 || ticket >= p->next) return fail(p->l, LADDER_E_INVAL, "ticket %ld not submitted", ticket);
     const int j = static_cast<int>(ticket % p->depth);
-    if (p->slot_ticket[j] != ticket) return LADDER_OK;  // a later frame of the slot waited for it already
-    const cudaError_t e = cudaEventSynchronize(p->ev_out[j]);
-    if (e != cudaSuccess) return cuda_fail(p->l, e, "pipeline wait");
-    return LADDER_OK;
+    if (p->slot_ticket[j] == ticket) {  // else a later frame of the slot waited for it already
+        const cudaError_t e = cudaEventSynchronize(p->ev_out[j]);
+        if (e != cudaSuccess) return cuda_fail(p->l, e, "pipeline wait");
+        pipeline_collect(p, j);
+    }
+    return pipeline_take_pending(p);
 }
 
 void ladder_pipeline_destroy(ladder_pipeline_t *p) { pipeline_free(p); }
@@ -1446,6 +1558,24 @@ ladder_status ladder_set_tuning(ladder_t *l, int knob, int value)
     }
 }
 
+ladder_status ladder_set_debug(ladder_t *l, int control, int value)
+{
+    if (!l) return LADDER_E_INVAL;
+    switch (control) {
+    case LADDER_DEBUG_WAIT_POLLS:
+        if (value != 0 && (value < 64 || value > kMvpSpinDefault))
+            return fail(l, LADDER_E_INVAL, "wait polls %d (0, or 64 .. %d)", value, kMvpSpinDefault);
+        l->dbg_wait_polls = value;
+        return LADDER_OK;
+    case LADDER_DEBUG_LOST_HANDOFF:
+        if (value != 0 && value != 1) return fail(l, LADDER_E_INVAL, "lost hand-off %d (0 or 1)", value);
+        l->dbg_lost_handoff = value;
+        return LADDER_OK;
+    default:
+        return fail(l, LADDER_E_INVAL, "unknown debug control %d", control);
+    }
+}
+
 ladder_status ladder_get_tuning(const ladder_t *l, int knob, int *value)
 {
     if (!l || !value) return LADDER_E_INVAL;
@@ -1465,7 +1595,14 @@ long ladder_device_bytes(const ladder_t *l) { return l ? static_cast<long>(l->ar
 void ladder_destroy(ladder_t *l)
 {
     if (!l) return;
-    cudaDeviceSynchronize();
+    // the handle's own work only: other handles' streams keep running
+    for (auto &m : l->marks) {
+        cudaEventSynchronize(m.done);
+        cudaEventDestroy(m.done);
+    }
+    l->marks.clear();
+    for (auto &ds : l->dep)
+        if (ds.done && ds.recorded) cudaEventSynchronize(ds.done);
     drain_events(l);
     for (cudaEvent_t e : l->spare) cudaEventDestroy(e);
     for (auto &ds : l->dep)

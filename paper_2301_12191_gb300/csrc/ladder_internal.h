@@ -124,22 +124,30 @@ struct RungInfo {
     DecOffsets off;
 };
 
+// Address of the array at `off` in a block; a null base means the offsets
+// are the arrays' own device addresses (caller-owned arrays that live in no
+// block, as with the allocation-free entry point).
+__host__ __device__ inline char *array_at(char *base, long off)
+{
+    return base ? base + off : reinterpret_cast<char *>(static_cast<uintptr_t>(off));
+}
+
 __host__ __device__ inline DevDecisions decisions_at(char *base, const DecOffsets &o)
 {
     DevDecisions d{};
     for (int k = 0; k < kMaxDepths; ++k) {
-        d.mvx[k] = reinterpret_cast<int16_t *>(base + o.mvx[k]);
-        d.mvy[k] = reinterpret_cast<int16_t *>(base + o.mvy[k]);
-        d.sad[k] = reinterpret_cast<int32_t *>(base + o.sad[k]);
-        d.satd[k] = reinterpret_cast<int32_t *>(base + o.satd[k]);
-        d.cost[k] = reinterpret_cast<int32_t *>(base + o.cost[k]);
-        d.best[k] = reinterpret_cast<int32_t *>(base + o.best[k]);
-        d.split[k] = reinterpret_cast<uint8_t *>(base + o.split[k]);
-        d.evaluated[k] = reinterpret_cast<uint8_t *>(base + o.evaluated[k]);
+        d.mvx[k] = reinterpret_cast<int16_t *>(array_at(base, o.mvx[k]));
+        d.mvy[k] = reinterpret_cast<int16_t *>(array_at(base, o.mvy[k]));
+        d.sad[k] = reinterpret_cast<int32_t *>(array_at(base, o.sad[k]));
+        d.satd[k] = reinterpret_cast<int32_t *>(array_at(base, o.satd[k]));
+        d.cost[k] = reinterpret_cast<int32_t *>(array_at(base, o.cost[k]));
+        d.best[k] = reinterpret_cast<int32_t *>(array_at(base, o.best[k]));
+        d.split[k] = reinterpret_cast<uint8_t *>(array_at(base, o.split[k]));
+        d.evaluated[k] = reinterpret_cast<uint8_t *>(array_at(base, o.evaluated[k]));
     }
-    d.leaf_depth = reinterpret_cast<uint8_t *>(base + o.leaf_depth);
-    d.leaf_mvx = reinterpret_cast<int16_t *>(base + o.leaf_mvx);
-    d.leaf_mvy = reinterpret_cast<int16_t *>(base + o.leaf_mvy);
+    d.leaf_depth = reinterpret_cast<uint8_t *>(array_at(base, o.leaf_depth));
+    d.leaf_mvx = reinterpret_cast<int16_t *>(array_at(base, o.leaf_mvx));
+    d.leaf_mvy = reinterpret_cast<int16_t *>(array_at(base, o.leaf_mvy));
     return d;
 }
 
@@ -226,7 +234,7 @@ cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchBatch &b,
 struct DecideItem {
     const void *cur, *ref;
     long pitch_bytes;
-    char *block;          // the (slot, rung) block: decisions + keys
+    char *block;          // the (slot, rung) block: decisions + keys (null: the offsets are addresses)
     int rung;
     int qp;
     int cta_begin;        // first CTA of this item (one CTA per CTU)
@@ -346,9 +354,13 @@ struct MvpItem {
     int cta_begin;  // CTA of the item's first CTU row
 };
 constexpr int kMaxMvpItems = kMaxDepItems;
+constexpr int kMvpSpinDefault = 1 << 22;  // polls (an L2 round trip each, under a microsecond) before a wait gives up
 struct MvpBatch {
     int n;
     int *status;
+    int spin;          // polls of one wait before it gives up (kMvpSpinDefault unless a test lowers it)
+    int lost_handoff;  // test control: 1 = rows wait for a hand-off generation no row publishes
+
     // use_out: decisions at item 0's QP into `out` (cost, best, split, leaf
     // maps; n must be 1) instead of in place (further-QP decisions)
     int use_out;

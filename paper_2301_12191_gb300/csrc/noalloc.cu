@@ -14,14 +14,15 @@
 // argmin keys.  Its size caps the frame: at most kNoallocMaxKeyBytes /
 // (8 * keys per CTU) CTUs (3083 CTUs of 64x64; a 3840x2160 frame has 2040).
 // Every call reuses the same array and leaves its contents behind; the keys
-// are reset at the start of each call.  Two calls whose work overlaps on the
-// GPU (different streams, no ordering) race on the array: order them.
+// are reset at the start of each call.  The status word is not: a bounded
+// wait that runs out sets it and it stays set until
+// analyze_reference_noalloc_status reads and clears it.  Two calls whose
+// work overlaps on the GPU (different streams, no ordering) race on the
+// array: order them.
 #include "../../include/ladder.h"
 #include "ladder_internal.h"
 
 #include <cudaTypedefs.h>
-
-#include <mutex>
 
 using namespace ladder_impl;
 
@@ -33,32 +34,44 @@ constexpr size_t kNoallocMaxKeyBytes = kNoallocScratchBytes - kNoallocStatusByte
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_lock;
-unsigned char *g_noalloc_ptr[kMaxDevices] = {};  // device address of the scratch, per device
-
-
-// Device address of the scratch array on the current device: looked up once
-// per device with that device current (host code may not use the symbol
-// itself, which is only a host-side stand-in for the device array).
+// Device address of the scratch array in the current device's context (host
+// code may not use the symbol itself, which is only a host-side stand-in for
+// the device array).  Looked up on every call: the address belongs to the
+// context, and a context that was reset and created again (cudaDeviceReset)
+// loads the module anew, possibly elsewhere.  The first lookup in a context
+// loads the module there.
 ladder_status scratch_for_current_device(unsigned char **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LADDER_E_CUDA;
-    std::lock_guard<std::mutex> guard(g_noalloc_lock);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return LADDER_E_CUDA;
-        }
-        g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return LADDER_E_CUDA;
     }
-    *out = g_noalloc_ptr[dev];
+    *out = static_cast<unsigned char *>(p);
     return LADDER_OK;
 }
 
 }  // namespace
+
+extern "C" ladder_status analyze_reference_noalloc_status(void *cuda_stream)
+{
+    unsigned char *scratch = nullptr;
+    ladder_status st = scratch_for_current_device(&scratch);
+    if (st != LADDER_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int status = 0;
+    cudaError_t e = cudaMemcpyAsync(&status, scratch, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && status != kStatusOk) {
+        e = cudaMemsetAsync(scratch, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return LADDER_E_CUDA;
+    }
+    return status == kStatusOk ? LADDER_OK : LADDER_E_TIMEOUT;
+}
 
 extern "C" ladder_status analyze_reference_noalloc(const void *cur, const void *ref, int width, int height,
                                                    long pitch_bytes, int bit_depth, int ctu_size, int search_range,
@@ -133,20 +146,19 @@ extern "C" ladder_status analyze_reference_noalloc(const void *cur, const void *
         return LADDER_E_CUDA;
 
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    cudaError_t e = cudaMemsetAsync(d_status, 0, sizeof(int), s);
     FillBatch fill{};
     fill.n = 1;
     fill.item[0] = FillItem{d_keys, nkeys};
-    if (e == cudaSuccess) e = launch_fill_keys(fill, s);
+    cudaError_t e = launch_fill_keys(fill, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return LADDER_E_CUDA;
     }
     e = launch_full_search(bit_depth, ctu_size, fb, s);
     if (e == cudaSuccess) {
-        // the decision kernel reads its outputs as offsets from a block base;
-        // here every array is the caller's, so the base is 0 and the offsets
-        // are the caller's addresses
+        // the decision kernel reads its arrays as offsets from a block base;
+        // here every array is the caller's (or the scratch's), so there is
+        // no block: a null base makes the offsets the arrays' addresses
         DecideBatch db{};
         db.n = 1;
         db.range = search_range;

@@ -141,14 +141,18 @@ SIGNATURES = [
                                                  ctypes.c_long, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, ctypes.c_int, ctypes.POINTER(Decisions),
                                                  ctypes.c_void_p]),
+    ("analyze_reference_noalloc_status", ctypes.c_int, [ctypes.c_void_p]),
+    ("ladder_measure_sad_rate", ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     ("ladder_version", ctypes.c_char_p, []),
     ("ladder_set_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     ("ladder_get_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("ladder_set_debug", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
 ]
 
 KERNEL_KINDS = ("full_search", "decide", "dependent", "fill_keys", "dep_rules", "dep_decide", "decide_qps",
                 "subpel", "decide_mvp")
 TUNE_KNOBS = {"fs_band": 0, "dep_band": 1, "dep_range": 2, "dep_ctas_per_sm": 3, "fs_group": 4, "fs_fuse": 5}
+DEBUG_CONTROLS = {"wait_polls": 0, "lost_handoff": 1}
 
 _lib = None
 
@@ -265,6 +269,22 @@ def analyze_reference_noalloc(cur_ptr, ref_ptr, width, height, pitch_bytes, bit_
     if st != 0:
         raise LadderError(st, "analyze_reference_noalloc")
     return st
+
+
+def ladder_measure_sad_rate(bit_depth: int, stream=0) -> float:
+    """Absolute differences per second of the searches' packed SAD
+    instruction form on the current device (see include/ladder.h)."""
+    v = ctypes.c_double()
+    st = load().ladder_measure_sad_rate(int(bit_depth), stream, ctypes.byref(v))
+    if st != 0:
+        raise LadderError(st, "ladder_measure_sad_rate")
+    return v.value
+
+
+def analyze_reference_noalloc_status(stream=0) -> int:
+    """Status of the allocation-free analyses since the last query (0, or
+    -6 if a bounded device wait ran out); waits for `stream`, clears it."""
+    return int(load().analyze_reference_noalloc_status(stream))
 
 
 # ---- torch convenience ----------------------------------------------------
@@ -460,6 +480,12 @@ class Ladder:
         are identical for every setting."""
         for name, value in knobs.items():
             _call(self.handle, "ladder_set_tuning", self.handle, TUNE_KNOBS[name], int(value))
+
+    def set_debug(self, **controls):
+        """Test controls of the failure paths, e.g. set_debug(wait_polls=4096,
+        lost_handoff=1) makes the wavefront waits run out (include/ladder.h)."""
+        for name, value in controls.items():
+            _call(self.handle, "ladder_set_debug", self.handle, DEBUG_CONTROLS[name], int(value))
 
     def tuning(self) -> dict:
         out = {}

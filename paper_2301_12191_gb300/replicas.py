@@ -12,6 +12,9 @@ MASTER_ADDR, MASTER_PORT).
 from __future__ import annotations
 
 import os
+import socket
+import subprocess
+import sys
 
 
 def env():
@@ -51,6 +54,17 @@ def max_over_ranks(value: float, device=None) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(value: float, device=None) -> float:
+    """The sum of every rank's value (e.g. the units it processed)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
     """Whole-job throughput: the units all ranks processed over the slowest
     rank's time."""
@@ -61,3 +75,23 @@ def finish():
     import torch.distributed as dist
     if dist.is_initialized():
         dist.destroy_process_group()
+
+
+def free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def launch_command(script: str, argv, n: int, port: int | None = None):
+    """Command line that runs `script argv` as n ranks of one node: one
+    process per GPU, rendezvous on 127.0.0.1 (each rank reads RANK,
+    LOCAL_RANK and WORLD_SIZE from its environment)."""
+    port = port or free_port()
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={int(n)}",
+            "--master-addr", "127.0.0.1", f"--master-port={port}", script, *argv]
+
+
+def spawn(script: str, argv, n: int, **kw) -> subprocess.CompletedProcess:
+    """Runs `script argv` as n ranks (launch_command) and waits for them."""
+    return subprocess.run(launch_command(script, argv, n), **kw)

@@ -29,11 +29,12 @@ def _oracle_chain(pairs, sizes, R, r, qp):
     return out
 
 
-def test_chain_equals_oracle_per_call_and_batched():
-    pairs, _ = synth.ladder_pairs(41, source=(1280, 720), rungs=[(960, 540), (640, 360), (320, 180)])
+@pytest.mark.parametrize("bd,R,r,qp", [(8, 8, 3, 30), (10, 16, 8, 22)])
+def test_chain_equals_oracle_per_call_and_batched(bd, R, r, qp):
+    pairs, _ = synth.ladder_pairs(41, source=(1280, 720), rungs=[(960, 540), (640, 360), (320, 180)],
+                                  bit_depth=bd)
     sizes = [(w, h) for (w, h, _, _) in pairs]
-    R, r, qp = 8, 3, 30
-    with L.Ladder(sizes, 3, search_range=R, refine_range=r, max_frames=2) as lad:
+    with L.Ladder(sizes, 3, bit_depth=bd, search_range=R, refine_range=r, max_frames=2) as lad:
         lad.set_parents(PARENT)
         planes = [(L.device_plane(c), L.device_plane(f)) for (_, _, c, f) in pairs]
         lad.analyze_reference(0, *planes[3], qp)

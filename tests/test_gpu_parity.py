@@ -115,6 +115,8 @@ def _ladder_case(seed, src, rungs, ref_idx, bd, R, r, qp, ctu=64, lo=0, hi=1, us
     (10, 8, 2, 0, 2, 1, 0),
     (8, 8, 9, 0, 0, 1, 0),     # r > 8 exercises the 17-wide column chunks
     (8, 8, 0, 0, 1, 1, 0),     # r = 0: reuse the scaled vector as is
+    (10, 16, 8, 0, 1, 1, 0),   # 10-bit r = 8: the 17-row band of 16-bit samples the UHD ladder uses
+    (10, 16, 8, -1, 2, 1, 1),  # the same with a wider depth window and PAPER4x4
 ])
 def test_dependent_small_ladder(bd, R, r, lo, hi, use_mv, satd):
     pairs, gpu, oras, _ = _ladder_case(21, (640, 360), [(480, 270), (320, 180), (160, 90)], 2, bd, R, r, 27,

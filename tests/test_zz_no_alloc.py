@@ -27,7 +27,7 @@ FIELDS = (("mvx", torch.int16), ("mvy", torch.int16), ("sad", torch.int32), ("sa
           ("cost", torch.int32), ("best", torch.int32), ("split", torch.uint8), ("evaluated", torch.uint8))
 
 
-def _noalloc_run(fp, ctu, R, qp, satd_mode, dims, grid8):
+def _noalloc_run(fp, ctu, R, qp, satd_mode, dims, grid8, check_status=True):
     """Caller-owned device outputs, filled by the allocation-free call."""
     dev = {k: [torch.full((c * r,), -7, dtype=dt, device="cuda") for (c, r) in dims] for k, dt in FIELDS}
     n8 = grid8[0] * grid8[1]
@@ -46,6 +46,8 @@ def _noalloc_run(fp, ctu, R, qp, satd_mode, dims, grid8):
                                 int(cur.stride(0) * cur.element_size()), fp.bit_depth, ctu, R, qp, satd_mode, dec,
                                 int(stream.cuda_stream))
     torch.cuda.synchronize()
+    if check_status:   # no bounded wait ran out (the status query allocates nothing either)
+        assert L.analyze_reference_noalloc_status(int(stream.cuda_stream)) == 0
     out = {k: [t.cpu().numpy() for t in dev[k]] for k, _ in FIELDS}
     out.update({k: t.cpu().numpy() for k, t in leaf.items()})
     out["grid"] = dims
@@ -71,6 +73,15 @@ def test_noalloc_equals_regular_entry_point_on_two_calls(W, H, bd, ctu, R, qp, s
         reg = _regular_run(fp, ctu, R, qp, satd)
         got = _noalloc_run(fp, ctu, R, qp, satd, reg["grid"], reg["grid8"])
         assert_decisions_equal(got, reg, ctu, where=f"noalloc {W}x{H} bd{bd}")
+
+
+def test_noalloc_near_its_limit_2160p_10bit():
+    """3840x2160 10-bit at CTU 64 (2040 of the 3083 CTUs the scratch holds),
+    every CTU against the regular entry point."""
+    fp = synth.frame_pair(303, 3840, 2160, 10, global_range=8, patch_range=12, patch_size=64)
+    reg = _regular_run(fp, 64, 8, 27, 0)
+    got = _noalloc_run(fp, 64, 8, 27, 0, reg["grid"], reg["grid8"])
+    assert_decisions_equal(got, reg, 64, where="noalloc 2160p 10-bit")
 
 
 def test_noalloc_refuses_frames_beyond_its_scratch():
