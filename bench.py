@@ -789,6 +789,8 @@ def run_batch(args, wl, name, ctx):
 
     rank, world, local = ctx
     dev = torch.device("cuda", local)
+    if args.ladders:
+        wl = dict(wl, ladders=args.ladders)  # smaller batches for profiler captures
     frames, reqs = batch_requests(wl, seed0=3000 + 1000 * rank)
     n = len(reqs)
     sizes = list(wl["rungs"])
@@ -809,20 +811,12 @@ def run_batch(args, wl, name, ctx):
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
         lad.analyze_batch(items, stream)                 # eager once (sets up slots)
-        lad.analyze_batch_independent(items_ind, stream)
+        if not args.only_multires:
+            lad.analyze_batch_independent(items_ind, stream)
     stream.synchronize()
     lad.sync(stream)
     tuning = autotune(args, lad, lambda: lad.analyze_batch(items, stream), f"frames{n}", stream)
     g_multi = lad.capture_batch(items, stream)
-    # algorithmic work: the full search at its 8x8 level, the dependents'
-    # evaluated CUs (request 0 as the sample, scaled to the batch)
-    evals_ref = full_evals(*sizes[ref_i], wl["R"])
-    evals_dep = 0
-    for r in range(len(sizes)):
-        if r != ref_i:
-            evals_dep += evals_of(lad.fetch(r, 0), wl["ctu"], wl["r"])
-    evals_multi = n * (evals_ref + evals_dep)
-    evals_indep = n * sum(full_evals(w, h, wl["R"]) for (w, h) in sizes)
 
     def timed(fn, K, W):
         for _ in range(W):
@@ -846,13 +840,23 @@ def run_batch(args, wl, name, ctx):
         return replicas.max_over_ranks(v, dev)
 
     K, W = args.steps, args.warmup
-    indep_steps = max(3, K // 2)
     if args.only_multires:
+        # warm-up and timed graph replays only: one eager batch, then W + K
+        # replays of 4 launches each (the profiler's launch list)
         ms = max_over_ranks(timed(lambda: g_multi.launch(stream), K, W))
+        lad.sync(stream)
         g_multi.close()
         lad.close()
         return {"metric": METRIC, "value": world * n * K / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": K,
-                "warmup": W, "ms_per_step": ms / K, "only": "multires"}
+                "warmup": W, "ms_per_step": ms / K, "only": "multires", "ladder_frames_per_step": n}
+    # algorithmic work: the full search at its 8x8 level, the dependents'
+    # evaluated CUs of every request of the batch (per request, averaged)
+    evals_ref = full_evals(*sizes[ref_i], wl["R"])
+    evals_dep = sum(evals_of(lad.fetch(r, k), wl["ctu"], wl["r"]) for k in range(n)
+                    for r in range(len(sizes)) if r != ref_i) / n
+    evals_multi = n * (evals_ref + evals_dep)
+    evals_indep = n * sum(full_evals(w, h, wl["R"]) for (w, h) in sizes)
+    indep_steps = max(3, K // 2)
     with ClockSampler(local) as clk:
         t_end = time.perf_counter() + args.soak
         while time.perf_counter() < t_end:
@@ -1125,6 +1129,8 @@ def main():
     ap.add_argument("--soak", type=float, default=1.5, help="untimed seconds of load before timing (clock sampling)")
     ap.add_argument("--only-multires", action="store_true",
                     help="run only warm-up + the timed multi-resolution steps (for profiler launch lists)")
+    ap.add_argument("--ladders", type=int, default=0,
+                    help="batched workloads: ladders per step instead of the workload's (smaller profiler cases)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -212,6 +212,10 @@ LADDER_API void ladder_graph_destroy(ladder_graph_t *graph);
  *   LADDER_TUNE_FS_FUSE          1 (default): the last full-search CTA of
  *                                each CTU also takes the CTU's decisions;
  *                                0: separate key-fill and decision kernels
+ *   LADDER_TUNE_DEP_STAGED       1 (default): the 10-bit dependent search
+ *                                stages each tile's reference windows in
+ *                                shared memory (refinement ranges of 4 and
+ *                                more); 0: it reads them through L1
  * LADDER_E_INVAL for an unknown knob or value. */
 typedef enum {
     LADDER_TUNE_FS_BAND = 0,
@@ -219,7 +223,8 @@ typedef enum {
     LADDER_TUNE_DEP_RANGE = 2,
     LADDER_TUNE_DEP_CTAS_PER_SM = 3,
     LADDER_TUNE_FS_GROUP = 4,
-    LADDER_TUNE_FS_FUSE = 5
+    LADDER_TUNE_FS_FUSE = 5,
+    LADDER_TUNE_DEP_STAGED = 6
 } ladder_tune_knob;
 LADDER_API ladder_status ladder_set_tuning(ladder_t *ladder, int knob, int value);
 LADDER_API ladder_status ladder_get_tuning(const ladder_t *ladder, int knob, int *value);

@@ -94,7 +94,7 @@ struct ladder {
     int fs_ctas_per_sm = 1;      // resident full-search CTAs per SM
     // kernel shapes (ladder_set_tuning): results never depend on them
     int tune_fs_band = kFsBand, tune_fs_group = 0, tune_fs_fuse = 1, tune_dep_band = 0, tune_dep_range = 16,
-        tune_dep_ctas = 0;
+        tune_dep_ctas = 0, tune_dep_staged = 1;
     int mv_predictor = 0;  // 0: (0, 0); 1: spatial, decided in wavefront order (ladder_set_mv_predictor)
     // test controls (ladder_set_debug)
     int dbg_wait_polls = 0;   // 0: kMvpSpinDefault
@@ -519,6 +519,7 @@ ladder_status launch_dependent_tier(ladder_t *l, const Job *jobs, int n, cudaStr
         b.range = l->tune_dep_range;
         b.band = l->tune_dep_band;
         b.ctas_per_sm = l->tune_dep_ctas;
+        b.staged = l->tune_dep_staged;
         b.satd_mode = l->geo.satd_mode;
         b.depth_lo = l->geo.dep_depth_lo;
         b.depth_hi = l->geo.dep_depth_hi;
@@ -1553,6 +1554,10 @@ ladder_status ladder_set_tuning(ladder_t *l, int knob, int value)
         if (value != 0 && value != 1) return fail(l, LADDER_E_INVAL, "fuse %d (0 or 1)", value);
         l->tune_fs_fuse = value;
         return LADDER_OK;
+    case LADDER_TUNE_DEP_STAGED:
+        if (value != 0 && value != 1) return fail(l, LADDER_E_INVAL, "staged %d (0 or 1)", value);
+        l->tune_dep_staged = value;
+        return LADDER_OK;
     default:
         return fail(l, LADDER_E_INVAL, "unknown tuning knob %d", knob);
     }
@@ -1586,6 +1591,7 @@ ladder_status ladder_get_tuning(const ladder_t *l, int knob, int *value)
     case LADDER_TUNE_DEP_CTAS_PER_SM: *value = l->tune_dep_ctas; return LADDER_OK;
     case LADDER_TUNE_FS_GROUP: *value = l->tune_fs_group; return LADDER_OK;
     case LADDER_TUNE_FS_FUSE: *value = l->tune_fs_fuse; return LADDER_OK;
+    case LADDER_TUNE_DEP_STAGED: *value = l->tune_dep_staged; return LADDER_OK;
     default: return LADDER_E_INVAL;
     }
 }

@@ -287,6 +287,7 @@ struct DependentBatch {
     int range;              // CUs larger than this (16 or 32) are searched in pieces of this side
     int band;               // candidate rows per lane task: 9 or 17
     int ctas_per_sm;        // search grid: CTAs per SM (0: as many as fit)
+    int staged;             // 1: each tile's windows staged in shared memory first (10-bit, r >= 4); 0: read from L1
     int satd_mode;
     int depth_lo, depth_hi, use_ref_mv;
     int total_ctas;         // CTUs of the batch

@@ -587,6 +587,350 @@ __global__ void __launch_bounds__(kSearchThreads, 2)
     }
 }
 
+// ---- 2b. staged search (10-bit) ----------------------------------------------
+// A CTA takes tiles of kStageThreads consecutive lane tasks of one size
+// class.  The lanes of a CU piece are contiguous, so a tile touches a few
+// pieces.  Each piece's reference window (every row and column its
+// candidates read) and its current samples are staged in shared memory
+// first, with the frame-edge rules applied there once (reference rows and
+// columns clamped into the frame, current samples replicated into the
+// 8-aligned pad):
+//   raw0  the window's rows from an 8-sample-aligned column ax, sample
+//         pairs (s[ax + 2m], s[ax + 2m + 1]) per word (16-byte async copies
+//         of whole row chunks when the window lies inside the frame);
+//   raw1  the same rows shifted by one sample, (s[ax + 2m + 1], s[ax + 2m + 2]),
+//         built from raw0 in shared memory;
+//   cur   the piece's current rows, sample pairs per word.
+// A lane whose candidate column starts at an even offset from ax reads its 8
+// samples of a row as 4 aligned words of raw0, an odd one as 4 aligned words
+// of raw1: no shifts, no frame-edge path and no divergence in the candidate
+// loop.
+constexpr int kStageThreads = 256;
+constexpr int kMaxStageSlots = 32;  // pieces one tile may touch (lanes per piece >= 9)
+
+// Shared-memory layout of one staged piece (words).
+struct StageShape {
+    int RS;    // piece side
+    int WR;    // window rows
+    int WW;    // samples a candidate column may start at past the window's first column, + 1
+    int NC;    // 8-sample chunks per raw row (the window's first column lies up to 7 past ax)
+    int RW;    // words per raw row (at least 4 NC, a multiple of 4: rows stay 16-byte aligned)
+    int CNC;   // 8-sample chunks per current row (RS / 8)
+    int CW;    // words per current row (RS / 2)
+    int O1;    // offset of raw1
+    int OC;    // offset of the current rows
+    int PW;    // words per piece slot (a multiple of 4)
+    int UPS;   // staging units (16-byte chunks) per slot: WR NC reference + RS CNC current
+};
+
+__host__ __device__ inline StageShape stage_shape(int RS, int r, int TY)
+{
+    StageShape s;
+    s.RS = RS;
+    // candidate rows reach RS - 1 + r below the piece; a single band taller
+    // than 2r + 1 reads TY - 1 - r rows further (those candidates are dropped)
+    s.WR = RS + (2 * r > TY - 1 ? 2 * r : TY - 1);
+    s.WW = RS + 2 * r - 1;
+    s.NC = (s.WW + 15) / 8;
+    // Banks: a warp's lanes read consecutive words, the even-offset ones in
+    // raw0, the odd-offset ones in raw1 (16 banks away), and a second band
+    // TY rows lower: a row stride of 8 (mod 16) words puts that band's words
+    // beside the first band's instead of on them.
+    s.RW = ((4 * s.NC + 7) & ~15) + 8;
+    s.CNC = RS / 8;
+    s.CW = RS / 2;
+    s.O1 = ((s.WR * s.RW + 15) & ~31) + 16;
+    s.OC = (s.O1 + s.WR * s.RW + 3) & ~3;
+    s.PW = (s.OC + RS * s.CW + 3) & ~3;
+    s.UPS = s.WR * s.NC + RS * s.CNC;
+    return s;
+}
+
+// Pieces a tile of kStageThreads lane tasks may touch, per_cu lanes each.
+__host__ __device__ inline int stage_slots(int per_cu) { return (kStageThreads - 1) / per_cu + 2; }
+
+// Divisors of the staging loops, one per size class (host-made).
+struct StageDivs {
+    FastDiv ups[kSizeClasses];   // staging units per slot
+    FastDiv nc[kSizeClasses];    // chunks per reference row
+    FastDiv wr[kSizeClasses];    // window rows per slot
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dev::smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+}
+
+// 10-bit SADs of one 8x8 current block for the TY candidates of a lane over
+// its staged window rows (see sads_core_u16; the packed halves of sum(a) +
+// sum(b) - 2 sum(min(a, b)) are folded by one dp2a).  ep: the lane's first
+// word of its first row; words 0, 1, 2, 3 hold its 8 samples.
+template <int TY>
+__device__ __forceinline__ void sads_staged_u16(const uint4 (&c)[8], uint32_t sa, uint32_t one, const uint32_t *ep,
+                                                int rw, uint32_t (&acc)[TY])
+{
+    constexpr int NR = 8 + TY - 1;
+    uint32_t mn[TY];
+#pragma unroll
+    for (int i = 0; i < TY; ++i) mn[i] = 0;
+    uint32_t rs[NR];
+    uint32_t sb = 0;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const uint32_t *q = ep + r * rw;
+        const uint32_t w0 = q[0], w1 = q[1], w2 = q[2], w3 = q[3];
+        rs[r] = (w0 + w1) + (w2 + w3);
+#pragma unroll
+        for (int i = 0; i < TY; ++i) {
+            const int j = r - i;
+            if (j >= 0 && j < 8) mn[i] = umad(min_u16x2(c[j].x, w0), one, mn[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < TY; ++i) {
+            const int j = r - i;
+            if (j >= 0 && j < 8) mn[i] = umad(min_u16x2(c[j].y, w1), one, mn[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < TY; ++i) {
+            const int j = r - i;
+            if (j >= 0 && j < 8) mn[i] = umad(min_u16x2(c[j].z, w2), one, mn[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < TY; ++i) {
+            const int j = r - i;
+            if (j >= 0 && j < 8) mn[i] = umad(min_u16x2(c[j].w, w3), one, mn[i]);
+        }
+        sb = r < 8 ? sb + rs[r] : sb + rs[r] - rs[r - 8];
+        if (r >= 7) {
+            const int i = r - 7;  // candidate i is complete
+            acc[i] = __dp2a_lo(umad(mn[i], 0xfffffffeu, sa + sb), 0x0101u, acc[i]);
+        }
+    }
+}
+
+template <int TY>
+__global__ void __launch_bounds__(kStageThreads, 2)
+    k_dep_search_st16(const __grid_constant__ DependentBatch b, const FastDiv div_cu, const FastDiv div_k,
+                      const __grid_constant__ StageDivs dv)
+{
+    dev::chain_entry();
+    extern __shared__ __align__(16) uint32_t s_win[];
+    __shared__ const char *s_ref[kMaxStageSlots], *s_cur[kMaxStageSlots];
+    __shared__ long s_pitch[kMaxStageSlots];
+    __shared__ int s_W[kMaxStageSlots], s_H[kMaxStageSlots], s_wy0[kMaxStageSlots], s_ax[kMaxStageSlots];
+    __shared__ int s_off[kMaxStageSlots], s_cux[kMaxStageSlots], s_cuy[kMaxStageSlots], s_edge[kMaxStageSlots];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r = b.r, K = 2 * r + 1;
+    const int per_cu = K * ((K + TY - 1) / TY);
+    const int code_max = 4 * r * K + 4 * r + 1;
+    const int rb = 32 - __clz(code_max);
+    const unsigned int n0 = min(__ldcg(b.counts + 0), b.cap[0]), n1 = min(__ldcg(b.counts + 1), b.cap[1]),
+                       n2 = min(__ldcg(b.counts + 2), b.cap[2]), n3 = min(__ldcg(b.counts + 3), b.cap[3]);
+    const long p2 = b.range >= 32 ? 1 : 4, p3 = b.range >= 32 ? 4 : 16;
+    const long l0 = static_cast<long>(n0) * per_cu, l1 = static_cast<long>(n1) * per_cu,
+               l2 = static_cast<long>(n2) * p2 * per_cu, l3 = static_cast<long>(n3) * p3 * per_cu;
+    constexpr long TT = kStageThreads;
+    const long t0n = (l0 + TT - 1) / TT, t1n = (l1 + TT - 1) / TT, t2n = (l2 + TT - 1) / TT, t3n = (l3 + TT - 1) / TT;
+    const long total = t0n + t1n + t2n + t3n;
+#pragma unroll 1
+    // largest CUs first; consecutive tiles go to different CTAs
+    for (long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        long lt = tile, ntask;
+        int c;
+        if (lt < t3n) {
+            c = 3, ntask = l3;
+        } else if ((lt -= t3n) < t2n) {
+            c = 2, ntask = l2;
+        } else if ((lt -= t2n) < t1n) {
+            c = 1, ntask = l1;
+        } else {
+            lt -= t1n;
+            c = 0, ntask = l0;
+        }
+        const int S = 8 << c, RS = S < b.range ? S : b.range;
+        const int nrs = S / RS, nr = nrs * nrs, lg = 31 - __clz(nrs);
+        const StageShape sh = stage_shape(RS, r, TY);
+        const long tf = lt * TT, tl = min(tf + TT - 1, ntask - 1);
+        const uint32_t q0 = fast_div(static_cast<uint32_t>(tf), div_cu), q1 = fast_div(static_cast<uint32_t>(tl), div_cu);
+        const int nslots = static_cast<int>(q1 - q0) + 1;
+        if (tid < nslots) {  // the slot's piece: planes, window origin, frame-edge flags
+            const uint32_t q = q0 + tid;
+            const unsigned int u = q >> (2 * lg);
+            const int rg = static_cast<int>(q & static_cast<uint32_t>(nr - 1));
+            const unsigned long long task = __ldcg(b.tasks[c] + u);
+            const uint32_t hi = static_cast<uint32_t>(task >> 32);
+            const unsigned int p = __ldcg(b.pos[c] + u);
+            const DependentItem &a = b.item[static_cast<uint32_t>(task) & 0xffu];
+            const RungGeom &g = b.rung[a.rung].g;
+            const int cux = static_cast<int>(p & 0xffffu) + (rg % nrs) * RS;
+            const int cuy = static_cast<int>(p >> 16) + (rg / nrs) * RS;
+            const int wx0 = cux + static_cast<int16_t>(hi & 0xffffu) - r;
+            const int ax = wx0 & ~7;
+            s_ref[tid] = static_cast<const char *>(a.ref);
+            s_cur[tid] = static_cast<const char *>(a.cur);
+            s_pitch[tid] = a.pitch_bytes;
+            s_W[tid] = g.W;
+            s_H[tid] = g.H;
+            s_wy0[tid] = cuy + static_cast<int16_t>(hi >> 16) - r;
+            s_ax[tid] = ax;
+            s_off[tid] = wx0 - ax;
+            s_cux[tid] = cux;
+            s_cuy[tid] = cuy;
+            // bit 0: the window's samples [wx0, wx0 + WW] leave the frame's columns;
+            // bit 1: the piece's current columns pass the frame's right edge
+            s_edge[tid] = ((wx0 < 0 || wx0 + sh.WW > g.W - 1) ? 1 : 0) | (cux + RS > g.W ? 2 : 0);
+        }
+        __syncthreads();
+        // stage raw0 and the current rows: 16-byte chunks, async copies inside the frame
+        const int nref = sh.WR * sh.NC;
+#pragma unroll 1
+        for (int uu = tid; uu < nslots * sh.UPS; uu += kStageThreads) {
+            const int slot = static_cast<int>(fast_div(static_cast<uint32_t>(uu), dv.ups[c]));
+            const int rem = uu - slot * sh.UPS;
+            const char *plane;
+            int x, y, W = s_W[slot];
+            uint32_t *dst = s_win + slot * sh.PW;
+            bool fast;
+            if (rem < nref) {
+                const int row = static_cast<int>(fast_div(static_cast<uint32_t>(rem), dv.nc[c]));
+                const int ch = rem - row * sh.NC;
+                y = min(max(s_wy0[slot] + row, 0), s_H[slot] - 1);
+                x = s_ax[slot] + 8 * ch;
+                plane = s_ref[slot];
+                dst += row * sh.RW + 4 * ch;
+                fast = !(s_edge[slot] & 1);
+                if (fast && x >= W) continue;  // past every sample a lane reads
+            } else {
+                const int rem2 = rem - nref;
+                const int j = rem2 >> (31 - __clz(sh.CNC)), ch = rem2 & (sh.CNC - 1);
+                y = min(s_cuy[slot] + j, s_H[slot] - 1);
+                x = s_cux[slot] + 8 * ch;
+                plane = s_cur[slot];
+                dst += sh.OC + j * sh.CW + 4 * ch;
+                fast = x + 8 <= W;
+            }
+            const uint16_t *row_p = reinterpret_cast<const uint16_t *>(plane + static_cast<long>(y) * s_pitch[slot]);
+            if (fast) {
+                cp_async16(dst, row_p + x);
+            } else {  // sample by sample at clamped columns
+                uint4 v;
+                uint32_t *w = reinterpret_cast<uint32_t *>(&v);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    w[k] = static_cast<uint32_t>(__ldg(row_p + min(max(x + 2 * k, 0), W - 1))) |
+                           (static_cast<uint32_t>(__ldg(row_p + min(max(x + 2 * k + 1, 0), W - 1))) << 16);
+                *reinterpret_cast<uint4 *>(dst) = v;
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        // raw1: every raw row shifted by one sample, four words at a time
+#pragma unroll 1
+        for (int uu = tid; uu < nslots * nref; uu += kStageThreads) {
+            const int g4 = static_cast<int>(fast_div(static_cast<uint32_t>(uu), dv.nc[c]));  // (slot, row)
+            const int grp = uu - g4 * sh.NC;
+            const int slot = static_cast<int>(fast_div(static_cast<uint32_t>(g4), dv.wr[c]));
+            const int row = g4 - slot * sh.WR;
+            const uint32_t *src = s_win + slot * sh.PW + row * sh.RW + 4 * grp;
+            const uint4 a4 = *reinterpret_cast<const uint4 *>(src);
+            const uint32_t e = 4 * grp + 4 < sh.RW ? src[4] : 0u;  // the row's last word: never read shifted
+            uint4 o;
+            o.x = __byte_perm(a4.x, a4.y, 0x5432);
+            o.y = __byte_perm(a4.y, a4.z, 0x5432);
+            o.z = __byte_perm(a4.z, a4.w, 0x5432);
+            o.w = __byte_perm(a4.w, e, 0x5432);
+            *reinterpret_cast<uint4 *>(s_win + slot * sh.PW + sh.O1 + row * sh.RW + 4 * grp) = o;
+        }
+        __syncthreads();
+
+        // the lane's task: (piece, band, dx)
+        const long traw = tf + tid;
+        const long t = min(traw, ntask - 1);
+        const uint32_t q = fast_div(static_cast<uint32_t>(t), div_cu);
+        const int slot = static_cast<int>(q - q0);
+        const int rem = static_cast<int>(t - static_cast<long>(q) * per_cu);
+        const int band = static_cast<int>(fast_div(static_cast<uint32_t>(rem), div_k)), dxi = rem - band * K;
+        const int dxo = dxi - r;
+        const int b0 = band * TY - r;
+        const int dy0 = K >= TY ? min(b0, r - TY + 1) : b0;
+        // the lane's first sample of a block row, counted from the raw rows' column ax
+        const int xs = s_off[slot] + dxo + r;
+        const int par = xs & 1;
+        const uint32_t *win = s_win + slot * sh.PW + (par ? sh.O1 : 0) + (xs >> 1);
+        const uint32_t *curw = s_win + slot * sh.PW + sh.OC;
+        uint32_t acc[TY];
+#pragma unroll
+        for (int i = 0; i < TY; ++i) acc[i] = 0;
+        const int nb = RS / 8;
+#pragma unroll 1
+        for (int blk = 0; blk < nb * nb; ++blk) {
+            const int bx = 8 * (blk % nb), by = 8 * (blk / nb);
+            uint4 cv[8];
+            uint32_t sa = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                cv[j] = *reinterpret_cast<const uint4 *>(curw + (by + j) * sh.CW + bx / 2);
+                sa += (cv[j].x + cv[j].y) + (cv[j].z + cv[j].w);
+            }
+            sads_staged_u16<TY>(cv, sa, b.one, win + (by + dy0 + r) * sh.RW + bx / 2, sh.RW, acc);
+        }
+
+        const unsigned int ucu = q >> (2 * lg);
+        const unsigned long long task = __ldcg(b.tasks[c] + ucu);
+        const uint32_t lo = static_cast<uint32_t>(task);
+        const DependentItem &a = b.item[lo & 0xffu];
+        const RungInfo &rinf = b.rung[a.rung];
+        if (nr > 1) {
+            // this piece's SADs into the CU's table, every candidate once
+            if (traw < ntask) {
+                unsigned int *sum = b.sums[c] + static_cast<long>(ucu) * (K * K);
+#pragma unroll
+                for (int i = 0; i < TY; ++i) {
+                    const int dyo = dy0 + i;
+                    if (dyo >= b0 && dyo <= r) atomicAdd(sum + (dyo + r) * K + dxi, acc[i]);
+                }
+            }
+        } else {
+            const uint32_t cbase = static_cast<uint32_t>(abs(dxo) * 2 * K + 2 * (dy0 + r) + (dxo > 0));
+            unsigned long long best = ~0ull;
+#pragma unroll
+            for (int i = 0; i < TY; ++i) {
+                const int dyo = dy0 + i;
+                if (dyo > r) continue;
+                const uint32_t code = umad(static_cast<uint32_t>(abs(dyo)), 2u * K, cbase + 2u * i);
+                const unsigned long long key = (static_cast<unsigned long long>(acc[i]) << rb) | code;
+                best = key < best ? key : best;
+            }
+            // segmented min over the lanes of this CU in the warp
+            const long wfirst = tf + 32 * warp;  // the warp's first task
+            const long cu_first = static_cast<long>(q) * per_cu - wfirst;
+            const int first = static_cast<int>(max(cu_first, 0L));
+            const int last = static_cast<int>(min(cu_first + per_cu - 1, ntask - 1 - wfirst));
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long v = __shfl_down_sync(0xffffffffu, best, o);
+                if (lane + o <= last) best = v < best ? v : best;
+            }
+            if (lane == first && best != ~0ull) {
+                const uint32_t sad = static_cast<uint32_t>(best >> rb);
+                const int code = static_cast<int>(best & ((1ull << rb) - 1));
+                const int l1 = code / (2 * K), rr = code - l1 * 2 * K;
+                const int dyv = (rr >> 1) - r;
+                const int adx = l1 - abs(dyv);
+                const int dxv = (rr & 1) ? adx : -adx;
+                const uint32_t tb = static_cast<uint32_t>(l1 * K * K + (dyv + r) * K + (dxv + r));
+                unsigned long long *keys = reinterpret_cast<unsigned long long *>(a.block + rinf.off.keys);
+                atomicMin(keys + (lo >> 8), (static_cast<unsigned long long>(sad) << 32) | tb);
+            }
+        }
+        __syncthreads();  // the next tile restages the slots
+    }
+}
+
 // ---- 3. decide --------------------------------------------------------------
 template <typename T, int CTU>
 __global__ void __launch_bounds__(kDecideThreads) k_dep_decide(const __grid_constant__ DependentBatch b)
@@ -707,13 +1051,69 @@ template <typename T, int TY> cudaError_t search_t(const DependentBatch &b, cuda
                           make_fastdiv(K));
 }
 
+// Dynamic shared memory a staged-search CTA may take: the device's opt-in
+// limit less the kernel's static shared memory.
+int smem_optin()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 48 << 10;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            v = 48 << 10;
+        cudaFuncAttributes fa{};
+        size_t fixed = 1024;
+        if (cudaFuncGetAttributes(&fa, k_dep_search_st16<kDepBand>) == cudaSuccess) fixed = fa.sharedSizeBytes;
+        n = v - static_cast<int>(fixed);
+    }
+    return n;
+}
+
+// Dynamic shared memory of a staged search: the most pieces a tile touches
+// times the largest piece of any size class (0 if it does not fit a CTA).
+template <int TY> size_t staged_smem_bytes(const DependentBatch &b)
+{
+    const int K = 2 * b.r + 1, per_cu = K * ((K + TY - 1) / TY);
+    const int slots = stage_slots(per_cu);
+    if (slots > kMaxStageSlots) return 0;
+    int pw = 0;
+    for (int S = 8; S <= 64; S <<= 1) pw = std::max(pw, stage_shape(S < b.range ? S : b.range, b.r, TY).PW);
+    const size_t bytes = static_cast<size_t>(slots) * pw * 4;
+    return bytes <= static_cast<size_t>(smem_optin()) ? bytes : 0;
+}
+
+template <int TY> cudaError_t search_staged(const DependentBatch &b, size_t smem, cudaStream_t s)
+{
+    int fit = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_dep_search_st16<TY>, kStageThreads, smem) !=
+            cudaSuccess ||
+        fit < 1)
+        fit = 1;
+    const int grid = sm_count() * (b.ctas_per_sm > 0 ? std::min(b.ctas_per_sm, fit) : fit);
+    const uint32_t K = 2 * b.r + 1, per_cu = K * ((K + TY - 1) / TY);
+    StageDivs dv{};
+    for (int c = 0; c < kSizeClasses; ++c) {
+        const int S = 8 << c;
+        const StageShape sh = stage_shape(S < b.range ? S : b.range, b.r, TY);
+        dv.ups[c] = make_fastdiv(static_cast<uint32_t>(sh.UPS));
+        dv.nc[c] = make_fastdiv(static_cast<uint32_t>(sh.NC));
+        dv.wr[c] = make_fastdiv(static_cast<uint32_t>(sh.WR));
+    }
+    return launch_chained(k_dep_search_st16<TY>, dim3(grid), dim3(kStageThreads), smem, s, b, make_fastdiv(per_cu),
+                          make_fastdiv(K), dv);
+}
+
 template <typename T> cudaError_t search_bd(const DependentBatch &b, cudaStream_t s)
 {
-    // 10-bit bodies are twice as long per candidate row: bands of 9 rows
-    // keep the unrolled loop inside the instruction cache
     // bands of 9 rows when 2r + 1 <= 9 or when asked for; 10-bit bodies are
     // twice as long per row, so 10-bit takes 9 unless asked for 17
     const bool nine = 2 * b.r + 1 <= 9 || b.band == 9 || (sizeof(T) == 2 && b.band != kDepBand);
+    if (sizeof(T) == 2 && b.staged && b.r >= 4) {
+        // staged windows (refinement ranges of 4 and more: at least 9 lanes
+        // per piece, so a tile touches few pieces), when they fit a CTA
+        const size_t smem = nine ? staged_smem_bytes<9>(b) : staged_smem_bytes<kDepBand>(b);
+        if (smem > 0) return nine ? search_staged<9>(b, smem, s) : search_staged<kDepBand>(b, smem, s);
+    }
     if (nine) return search_t<T, 9>(b, s);
     return search_t<T, kDepBand>(b, s);
 }
@@ -754,6 +1154,12 @@ cudaError_t prepare_kernels(int bit_depth, int ctu, int R, int r)
     } else {
         search_ctas_per_sm<uint16_t, 9>();
         search_ctas_per_sm<uint16_t, kDepBand>();
+        // the staged search sizes its shared memory per launch, up to the opt-in limit
+        e = cudaFuncSetAttribute(k_dep_search_st16<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_dep_search_st16<kDepBand>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem_optin());
+        if (e != cudaSuccess) return e;
     }
     (void)r;
     return cudaGetLastError();

@@ -151,7 +151,8 @@ SIGNATURES = [
 
 KERNEL_KINDS = ("full_search", "decide", "dependent", "fill_keys", "dep_rules", "dep_decide", "decide_qps",
                 "subpel", "decide_mvp")
-TUNE_KNOBS = {"fs_band": 0, "dep_band": 1, "dep_range": 2, "dep_ctas_per_sm": 3, "fs_group": 4, "fs_fuse": 5}
+TUNE_KNOBS = {"fs_band": 0, "dep_band": 1, "dep_range": 2, "dep_ctas_per_sm": 3, "fs_group": 4, "fs_fuse": 5,
+              "dep_staged": 6}
 DEBUG_CONTROLS = {"wait_polls": 0, "lost_handoff": 1}
 
 _lib = None

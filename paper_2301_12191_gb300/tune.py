@@ -1,10 +1,11 @@
 """Autotuner of the kernel shapes (written for this library).
 
-The library exposes six shape knobs (`ladder_set_tuning`): the full
+The library exposes seven shape knobs (`ladder_set_tuning`): the full
 search's band height (candidate rows per lane task), its warp tiles per CTA
 and whether its last CTA per CTU also takes the CTU's decisions,
 the dependent search's band height, the piece size large dependent CUs are
-split into, and the dependent search's grid size.  None of them changes a result; they trade
+split into, the dependent search's grid size and whether it stages its
+windows in shared memory.  None of them changes a result; they trade
 load balance (how many tiles a launch has, how long the longest one is)
 against per-candidate overhead, and the best setting depends on the
 workload: one 1080p ladder frame has too few CTUs to fill the GPU with long
@@ -33,8 +34,10 @@ SPACE = {
     "dep_range": (16, 32),
     "dep_band": (0, 17, 9),
     "dep_ctas_per_sm": (0, 1, 2),
+    "dep_staged": (1, 0),
 }
-DEFAULTS = {"fs_band": 13, "fs_group": 0, "fs_fuse": 1, "dep_range": 16, "dep_band": 0, "dep_ctas_per_sm": 0}
+DEFAULTS = {"fs_band": 13, "fs_group": 0, "fs_fuse": 1, "dep_range": 16, "dep_band": 0, "dep_ctas_per_sm": 0,
+            "dep_staged": 1}
 
 
 def default_cache_path() -> str:
