@@ -212,10 +212,12 @@ LADDER_API void ladder_graph_destroy(ladder_graph_t *graph);
  *   LADDER_TUNE_FS_FUSE          1 (default): the last full-search CTA of
  *                                each CTU also takes the CTU's decisions;
  *                                0: separate key-fill and decision kernels
- *   LADDER_TUNE_DEP_STAGED       1 (default): the 10-bit dependent search
- *                                stages each tile's reference windows in
- *                                shared memory (refinement ranges of 4 and
- *                                more); 0: it reads them through L1
+ *   LADDER_TUNE_DEP_STAGED       10-bit dependent search, refinement ranges
+ *                                of 4 and more: 1 (default) stages each
+ *                                tile's reference windows in shared memory,
+ *                                2 does so into two buffers (the next tile's
+ *                                copies in flight during the current one),
+ *                                0 reads the windows through L1
  * LADDER_E_INVAL for an unknown knob or value. */
 typedef enum {
     LADDER_TUNE_FS_BAND = 0,

@@ -1555,7 +1555,7 @@ ladder_status ladder_set_tuning(ladder_t *l, int knob, int value)
         l->tune_fs_fuse = value;
         return LADDER_OK;
     case LADDER_TUNE_DEP_STAGED:
-        if (value != 0 && value != 1) return fail(l, LADDER_E_INVAL, "staged %d (0 or 1)", value);
+        if (value < 0 || value > 2) return fail(l, LADDER_E_INVAL, "staged %d (0, 1 or 2)", value);
         l->tune_dep_staged = value;
         return LADDER_OK;
     default:

@@ -594,7 +594,8 @@ __global__ void __launch_bounds__(kSearchThreads, 2)
 // candidates read) and its current samples are staged in shared memory
 // first, with the frame-edge rules applied there once (reference rows and
 // columns clamped into the frame, current samples replicated into the
-// 8-aligned pad):
+// 8-aligned pad); a CTA works on two buffers, the next tile's copies in
+// flight while the current tile is computed:
 //   raw0  the window's rows from an 8-sample-aligned column ax, sample
 //         pairs (s[ax + 2m], s[ax + 2m + 1]) per word (16-byte async copies
 //         of whole row chunks when the window lies inside the frame);
@@ -605,7 +606,7 @@ __global__ void __launch_bounds__(kSearchThreads, 2)
 // samples of a row as 4 aligned words of raw0, an odd one as 4 aligned words
 // of raw1: no shifts, no frame-edge path and no divergence in the candidate
 // loop.
-constexpr int kStageThreads = 256;
+constexpr int kStageThreads = 128;  // small tiles: several CTAs per SM, staging overlaps compute
 constexpr int kMaxStageSlots = 32;  // pieces one tile may touch (lanes per piece >= 9)
 
 // Shared-memory layout of one staged piece (words).
@@ -620,7 +621,6 @@ struct StageShape {
     int O1;    // offset of raw1
     int OC;    // offset of the current rows
     int PW;    // words per piece slot (a multiple of 4)
-    int UPS;   // staging units (16-byte chunks) per slot: WR NC reference + RS CNC current
 };
 
 __host__ __device__ inline StageShape stage_shape(int RS, int r, int TY)
@@ -633,16 +633,15 @@ __host__ __device__ inline StageShape stage_shape(int RS, int r, int TY)
     s.WW = RS + 2 * r - 1;
     s.NC = (s.WW + 15) / 8;
     // Banks: a warp's lanes read consecutive words, the even-offset ones in
-    // raw0, the odd-offset ones in raw1 (16 banks away), and a second band
-    // TY rows lower: a row stride of 8 (mod 16) words puts that band's words
-    // beside the first band's instead of on them.
-    s.RW = ((4 * s.NC + 7) & ~15) + 8;
+    // raw0, the odd-offset ones in raw1 (16 banks away); with several bands
+    // (2r + 1 > TY) a warp also holds a band TY rows lower, and a row stride
+    // of 8 (mod 16) words puts its words beside the first band's.
+    s.RW = 2 * r + 1 > TY ? ((4 * s.NC + 7) & ~15) + 8 : 4 * s.NC;
     s.CNC = RS / 8;
     s.CW = RS / 2;
     s.O1 = ((s.WR * s.RW + 15) & ~31) + 16;
     s.OC = (s.O1 + s.WR * s.RW + 3) & ~3;
     s.PW = (s.OC + RS * s.CW + 3) & ~3;
-    s.UPS = s.WR * s.NC + RS * s.CNC;
     return s;
 }
 
@@ -651,18 +650,13 @@ __host__ __device__ inline int stage_slots(int per_cu) { return (kStageThreads -
 
 // Divisors of the staging loops, one per size class (host-made).
 struct StageDivs {
-    FastDiv ups[kSizeClasses];   // staging units per slot
-    FastDiv nc[kSizeClasses];    // chunks per reference row
-    FastDiv wr[kSizeClasses];    // window rows per slot
+    FastDiv cps[kSizeClasses];   // copy columns per slot: row groups x (reference + current chunks per row)
+    FastDiv c1[kSizeClasses];    // shift columns per slot: row groups x reference chunks per row
 };
 
 __device__ __forceinline__ void cp_async16(uint32_t *dst, const void *src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dev::smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
 }
 
 // 10-bit SADs of one 8x8 current block for the TY candidates of a lane over
@@ -712,222 +706,339 @@ __device__ __forceinline__ void sads_staged_u16(const uint4 (&c)[8], uint32_t sa
     }
 }
 
+// One tile of the staged search: its size class, its lane tasks and the
+// pieces they touch.
+struct StageTile {
+    int c;          // size class
+    long tf, ntask; // first lane task of the tile, lane tasks of the class
+    uint32_t q0;    // first piece
+    int nslots;     // pieces touched
+    int RS, nrs, nr, lg;
+    StageShape sh;
+};
+
+// Per-slot parameters of the pieces staged in one buffer.
+struct StageSlots {
+    const char *ref[kMaxStageSlots], *cur[kMaxStageSlots];
+    long pitch[kMaxStageSlots];
+    int W[kMaxStageSlots], H[kMaxStageSlots], wy0[kMaxStageSlots], ax[kMaxStageSlots];
+    int off[kMaxStageSlots], cux[kMaxStageSlots], cuy[kMaxStageSlots], edge[kMaxStageSlots];
+    int any_edge;  // some slot needs the frame-edge fix-up
+};
+
 template <int TY>
-__global__ void __launch_bounds__(kStageThreads, 2)
-    k_dep_search_st16(const __grid_constant__ DependentBatch b, const FastDiv div_cu, const FastDiv div_k,
-                      const __grid_constant__ StageDivs dv)
+__device__ __forceinline__ StageTile stage_tile(const DependentBatch &b, long tile, int per_cu, const FastDiv &div_cu,
+                                                const long *ln, const long *tn)
 {
-    dev::chain_entry();
-    extern __shared__ __align__(16) uint32_t s_win[];
-    __shared__ const char *s_ref[kMaxStageSlots], *s_cur[kMaxStageSlots];
-    __shared__ long s_pitch[kMaxStageSlots];
-    __shared__ int s_W[kMaxStageSlots], s_H[kMaxStageSlots], s_wy0[kMaxStageSlots], s_ax[kMaxStageSlots];
-    __shared__ int s_off[kMaxStageSlots], s_cux[kMaxStageSlots], s_cuy[kMaxStageSlots], s_edge[kMaxStageSlots];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int r = b.r, K = 2 * r + 1;
-    const int per_cu = K * ((K + TY - 1) / TY);
-    const int code_max = 4 * r * K + 4 * r + 1;
-    const int rb = 32 - __clz(code_max);
-    const unsigned int n0 = min(__ldcg(b.counts + 0), b.cap[0]), n1 = min(__ldcg(b.counts + 1), b.cap[1]),
-                       n2 = min(__ldcg(b.counts + 2), b.cap[2]), n3 = min(__ldcg(b.counts + 3), b.cap[3]);
-    const long p2 = b.range >= 32 ? 1 : 4, p3 = b.range >= 32 ? 4 : 16;
-    const long l0 = static_cast<long>(n0) * per_cu, l1 = static_cast<long>(n1) * per_cu,
-               l2 = static_cast<long>(n2) * p2 * per_cu, l3 = static_cast<long>(n3) * p3 * per_cu;
-    constexpr long TT = kStageThreads;
-    const long t0n = (l0 + TT - 1) / TT, t1n = (l1 + TT - 1) / TT, t2n = (l2 + TT - 1) / TT, t3n = (l3 + TT - 1) / TT;
-    const long total = t0n + t1n + t2n + t3n;
+    StageTile t;
+    long lt = tile;
+    int c = 3;
+    while (c > 0 && lt >= tn[c]) lt -= tn[c--];  // largest CUs first
+    t.c = c;
+    t.ntask = ln[c];
+    t.tf = lt * kStageThreads;
+    const int S = 8 << c;
+    t.RS = S < b.range ? S : b.range;
+    t.nrs = S / t.RS;
+    t.nr = t.nrs * t.nrs;
+    t.lg = 31 - __clz(t.nrs);
+    t.sh = stage_shape(t.RS, b.r, TY);
+    const long tl = min(t.tf + kStageThreads - 1, t.ntask - 1);
+    t.q0 = fast_div(static_cast<uint32_t>(t.tf), div_cu);
+    t.nslots = static_cast<int>(fast_div(static_cast<uint32_t>(tl), div_cu) - t.q0) + 1;
+    return t;
+}
+
+// The tile's pieces: planes, window origin, frame-edge flags (threads
+// below nslots, one piece each).
+__device__ __forceinline__ void stage_slots_setup(const DependentBatch &b, const StageTile &t, StageSlots &ss)
+{
+    const int tid = threadIdx.x;
+    if (tid == 0) ss.any_edge = 0;
+    __syncthreads();
+    if (tid < t.nslots) {
+        const uint32_t q = t.q0 + tid;
+        const unsigned int u = q >> (2 * t.lg);
+        const int rg = static_cast<int>(q & static_cast<uint32_t>(t.nr - 1));
+        const unsigned long long task = __ldcg(b.tasks[t.c] + u);
+        const uint32_t hi = static_cast<uint32_t>(task >> 32);
+        const unsigned int p = __ldcg(b.pos[t.c] + u);
+        const DependentItem &a = b.item[static_cast<uint32_t>(task) & 0xffu];
+        const RungGeom &g = b.rung[a.rung].g;
+        const int cux = static_cast<int>(p & 0xffffu) + (rg % t.nrs) * t.RS;
+        const int cuy = static_cast<int>(p >> 16) + (rg / t.nrs) * t.RS;
+        const int wx0 = cux + static_cast<int16_t>(hi & 0xffffu) - b.r;
+        const int ax = wx0 & ~7;
+        ss.ref[tid] = static_cast<const char *>(a.ref);
+        ss.cur[tid] = static_cast<const char *>(a.cur);
+        ss.pitch[tid] = a.pitch_bytes;
+        ss.W[tid] = g.W;
+        ss.H[tid] = g.H;
+        ss.wy0[tid] = cuy + static_cast<int16_t>(hi >> 16) - b.r;
+        ss.ax[tid] = ax;
+        ss.off[tid] = wx0 - ax;
+        ss.cux[tid] = cux;
+        ss.cuy[tid] = cuy;
+        // bit 0: a raw word holds a sample outside the frame's columns;
+        // bit 1: the piece's current columns pass the frame's right edge
+        const int e = ((ax < 0 || ax + 8 * t.sh.NC > g.W) ? 1 : 0) | (cux + t.RS > g.W ? 2 : 0);
+        ss.edge[tid] = e;
+        if (e) ss.any_edge = 1;
+    }
+}
+
+// Issues the async copies of every 16-byte chunk of the tile's raw0 and
+// current rows that lies inside its frame (rows clamped into the frame);
+// chunks outside are left to the fix-up.  A thread takes one column of
+// chunks (slot, chunk, a quarter of the rows) and walks its rows.
+constexpr int kStageRowGroups = 4;
+
+__device__ __forceinline__ void stage_copy(const StageTile &t, const StageSlots &ss, uint32_t *buf,
+                                           const FastDiv &div_cps)
+{
+    const StageShape &sh = t.sh;
+    const int cps = kStageRowGroups * (sh.NC + sh.CNC);  // columns per slot
 #pragma unroll 1
-    // largest CUs first; consecutive tiles go to different CTAs
-    for (long tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        long lt = tile, ntask;
-        int c;
-        if (lt < t3n) {
-            c = 3, ntask = l3;
-        } else if ((lt -= t3n) < t2n) {
-            c = 2, ntask = l2;
-        } else if ((lt -= t2n) < t1n) {
-            c = 1, ntask = l1;
-        } else {
-            lt -= t1n;
-            c = 0, ntask = l0;
-        }
-        const int S = 8 << c, RS = S < b.range ? S : b.range;
-        const int nrs = S / RS, nr = nrs * nrs, lg = 31 - __clz(nrs);
-        const StageShape sh = stage_shape(RS, r, TY);
-        const long tf = lt * TT, tl = min(tf + TT - 1, ntask - 1);
-        const uint32_t q0 = fast_div(static_cast<uint32_t>(tf), div_cu), q1 = fast_div(static_cast<uint32_t>(tl), div_cu);
-        const int nslots = static_cast<int>(q1 - q0) + 1;
-        if (tid < nslots) {  // the slot's piece: planes, window origin, frame-edge flags
-            const uint32_t q = q0 + tid;
-            const unsigned int u = q >> (2 * lg);
-            const int rg = static_cast<int>(q & static_cast<uint32_t>(nr - 1));
-            const unsigned long long task = __ldcg(b.tasks[c] + u);
-            const uint32_t hi = static_cast<uint32_t>(task >> 32);
-            const unsigned int p = __ldcg(b.pos[c] + u);
-            const DependentItem &a = b.item[static_cast<uint32_t>(task) & 0xffu];
-            const RungGeom &g = b.rung[a.rung].g;
-            const int cux = static_cast<int>(p & 0xffffu) + (rg % nrs) * RS;
-            const int cuy = static_cast<int>(p >> 16) + (rg / nrs) * RS;
-            const int wx0 = cux + static_cast<int16_t>(hi & 0xffffu) - r;
-            const int ax = wx0 & ~7;
-            s_ref[tid] = static_cast<const char *>(a.ref);
-            s_cur[tid] = static_cast<const char *>(a.cur);
-            s_pitch[tid] = a.pitch_bytes;
-            s_W[tid] = g.W;
-            s_H[tid] = g.H;
-            s_wy0[tid] = cuy + static_cast<int16_t>(hi >> 16) - r;
-            s_ax[tid] = ax;
-            s_off[tid] = wx0 - ax;
-            s_cux[tid] = cux;
-            s_cuy[tid] = cuy;
-            // bit 0: the window's samples [wx0, wx0 + WW] leave the frame's columns;
-            // bit 1: the piece's current columns pass the frame's right edge
-            s_edge[tid] = ((wx0 < 0 || wx0 + sh.WW > g.W - 1) ? 1 : 0) | (cux + RS > g.W ? 2 : 0);
-        }
-        __syncthreads();
-        // stage raw0 and the current rows: 16-byte chunks, async copies inside the frame
-        const int nref = sh.WR * sh.NC;
+    for (int col = threadIdx.x; col < t.nslots * cps; col += kStageThreads) {
+        const int slot = static_cast<int>(fast_div(static_cast<uint32_t>(col), div_cps));
+        const int k = col - slot * cps;
+        const int grp = k & (kStageRowGroups - 1), ch = k / kStageRowGroups;
+        const int W = ss.W[slot], H = ss.H[slot];
+        const long pitch = ss.pitch[slot];
+        const bool ref = ch < sh.NC;
+        const int x = ref ? ss.ax[slot] + 8 * ch : ss.cux[slot] + 8 * (ch - sh.NC);
+        if (x < 0 || x >= W) continue;  // x is a multiple of 8: a chunk that starts in the row ends in its pitch
+        const int rows = ref ? sh.WR : t.RS;
+        const int per = (rows + kStageRowGroups - 1) / kStageRowGroups, row0 = grp * per;
+        const int nrows = min(per, rows - row0);
+        const int y0 = (ref ? ss.wy0[slot] : ss.cuy[slot]) + row0;
+        const char *src = (ref ? ss.ref[slot] : ss.cur[slot]) + 2 * static_cast<long>(x);
+        const int stride = ref ? sh.RW : sh.CW;
+        uint32_t *dst = buf + slot * sh.PW + (ref ? 0 : sh.OC) + row0 * stride + 4 * (ref ? ch : ch - sh.NC);
 #pragma unroll 1
-        for (int uu = tid; uu < nslots * sh.UPS; uu += kStageThreads) {
-            const int slot = static_cast<int>(fast_div(static_cast<uint32_t>(uu), dv.ups[c]));
-            const int rem = uu - slot * sh.UPS;
-            const char *plane;
-            int x, y, W = s_W[slot];
-            uint32_t *dst = s_win + slot * sh.PW;
-            bool fast;
-            if (rem < nref) {
-                const int row = static_cast<int>(fast_div(static_cast<uint32_t>(rem), dv.nc[c]));
-                const int ch = rem - row * sh.NC;
-                y = min(max(s_wy0[slot] + row, 0), s_H[slot] - 1);
-                x = s_ax[slot] + 8 * ch;
-                plane = s_ref[slot];
-                dst += row * sh.RW + 4 * ch;
-                fast = !(s_edge[slot] & 1);
-                if (fast && x >= W) continue;  // past every sample a lane reads
-            } else {
-                const int rem2 = rem - nref;
-                const int j = rem2 >> (31 - __clz(sh.CNC)), ch = rem2 & (sh.CNC - 1);
-                y = min(s_cuy[slot] + j, s_H[slot] - 1);
-                x = s_cux[slot] + 8 * ch;
-                plane = s_cur[slot];
-                dst += sh.OC + j * sh.CW + 4 * ch;
-                fast = x + 8 <= W;
+        for (int i = 0; i < nrows; ++i, dst += stride)
+            cp_async16(dst, src + static_cast<long>(min(max(y0 + i, 0), H - 1)) * pitch);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Frame edges: every raw0 word with a sample outside the frame's columns,
+// and every current word past its right edge, from clamped samples (edge
+// slots only; one warp per row).
+__device__ __forceinline__ void stage_fixup(const StageTile &t, const StageSlots &ss, uint32_t *buf)
+{
+    const StageShape &sh = t.sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kWarps = kStageThreads / 32;
+#pragma unroll 1
+    for (int slot = 0; slot < t.nslots; ++slot) {
+        const int e = ss.edge[slot];
+        if (!e) continue;
+        const int W = ss.W[slot];
+#pragma unroll 1
+        for (int row = warp; row < sh.WR + t.RS; row += kWarps) {
+            const bool ref_row = row < sh.WR;
+            if (ref_row ? !(e & 1) : !(e & 2)) continue;
+            const int y = ref_row ? min(max(ss.wy0[slot] + row, 0), ss.H[slot] - 1)
+                                  : min(ss.cuy[slot] + row - sh.WR, ss.H[slot] - 1);
+            const uint16_t *src = reinterpret_cast<const uint16_t *>((ref_row ? ss.ref[slot] : ss.cur[slot]) +
+                                                                     static_cast<long>(y) * ss.pitch[slot]);
+            uint32_t *dst = buf + slot * sh.PW + (ref_row ? row * sh.RW : sh.OC + (row - sh.WR) * sh.CW);
+            const int x0 = ref_row ? ss.ax[slot] : ss.cux[slot];
+            const int nw = ref_row ? 4 * sh.NC : sh.CW;
+            for (int m = lane; m < nw; m += 32) {
+                const int p = x0 + 2 * m;
+                if (p >= 0 && p + 1 < W) continue;  // copied as it stands
+                dst[m] = static_cast<uint32_t>(__ldg(src + min(max(p, 0), W - 1))) |
+                         (static_cast<uint32_t>(__ldg(src + min(max(p + 1, 0), W - 1))) << 16);
             }
-            const uint16_t *row_p = reinterpret_cast<const uint16_t *>(plane + static_cast<long>(y) * s_pitch[slot]);
-            if (fast) {
-                cp_async16(dst, row_p + x);
-            } else {  // sample by sample at clamped columns
-                uint4 v;
-                uint32_t *w = reinterpret_cast<uint32_t *>(&v);
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    w[k] = static_cast<uint32_t>(__ldg(row_p + min(max(x + 2 * k, 0), W - 1))) |
-                           (static_cast<uint32_t>(__ldg(row_p + min(max(x + 2 * k + 1, 0), W - 1))) << 16);
-                *reinterpret_cast<uint4 *>(dst) = v;
-            }
         }
-        cp_async_wait_all();
-        __syncthreads();
-        // raw1: every raw row shifted by one sample, four words at a time
+    }
+}
+
+// raw1: every raw row shifted by one sample, four words at a time; a
+// thread takes one column (slot, four words, a quarter of the rows).
+__device__ __forceinline__ void stage_raw1(const StageTile &t, uint32_t *buf, const FastDiv &div_c1)
+{
+    const StageShape &sh = t.sh;
+    const int cps = kStageRowGroups * sh.NC;
+    const int per = (sh.WR + kStageRowGroups - 1) / kStageRowGroups;
 #pragma unroll 1
-        for (int uu = tid; uu < nslots * nref; uu += kStageThreads) {
-            const int g4 = static_cast<int>(fast_div(static_cast<uint32_t>(uu), dv.nc[c]));  // (slot, row)
-            const int grp = uu - g4 * sh.NC;
-            const int slot = static_cast<int>(fast_div(static_cast<uint32_t>(g4), dv.wr[c]));
-            const int row = g4 - slot * sh.WR;
-            const uint32_t *src = s_win + slot * sh.PW + row * sh.RW + 4 * grp;
+    for (int col = threadIdx.x; col < t.nslots * cps; col += kStageThreads) {
+        const int slot = static_cast<int>(fast_div(static_cast<uint32_t>(col), div_c1));
+        const int k = col - slot * cps;
+        const int grp = k / kStageRowGroups, row0 = (k & (kStageRowGroups - 1)) * per;
+        const int nrows = min(per, sh.WR - row0);
+        const bool last = grp + 1 >= sh.NC;  // the row's last word: never read shifted
+        const uint32_t *src = buf + slot * sh.PW + row0 * sh.RW + 4 * grp;
+        uint32_t *dst = buf + slot * sh.PW + sh.O1 + row0 * sh.RW + 4 * grp;
+#pragma unroll 1
+        for (int i = 0; i < nrows; ++i, src += sh.RW, dst += sh.RW) {
             const uint4 a4 = *reinterpret_cast<const uint4 *>(src);
-            const uint32_t e = 4 * grp + 4 < sh.RW ? src[4] : 0u;  // the row's last word: never read shifted
+            const uint32_t e = last ? 0u : src[4];
             uint4 o;
             o.x = __byte_perm(a4.x, a4.y, 0x5432);
             o.y = __byte_perm(a4.y, a4.z, 0x5432);
             o.z = __byte_perm(a4.z, a4.w, 0x5432);
             o.w = __byte_perm(a4.w, e, 0x5432);
-            *reinterpret_cast<uint4 *>(s_win + slot * sh.PW + sh.O1 + row * sh.RW + 4 * grp) = o;
+            *reinterpret_cast<uint4 *>(dst) = o;
         }
-        __syncthreads();
+    }
+}
 
-        // the lane's task: (piece, band, dx)
-        const long traw = tf + tid;
-        const long t = min(traw, ntask - 1);
-        const uint32_t q = fast_div(static_cast<uint32_t>(t), div_cu);
-        const int slot = static_cast<int>(q - q0);
-        const int rem = static_cast<int>(t - static_cast<long>(q) * per_cu);
-        const int band = static_cast<int>(fast_div(static_cast<uint32_t>(rem), div_k)), dxi = rem - band * K;
-        const int dxo = dxi - r;
-        const int b0 = band * TY - r;
-        const int dy0 = K >= TY ? min(b0, r - TY + 1) : b0;
-        // the lane's first sample of a block row, counted from the raw rows' column ax
-        const int xs = s_off[slot] + dxo + r;
-        const int par = xs & 1;
-        const uint32_t *win = s_win + slot * sh.PW + (par ? sh.O1 : 0) + (xs >> 1);
-        const uint32_t *curw = s_win + slot * sh.PW + sh.OC;
-        uint32_t acc[TY];
+// The SADs of one lane's task over the staged tile, into its CU's key or
+// sum table.
+template <int TY>
+__device__ __forceinline__ void stage_compute(const DependentBatch &b, const StageTile &t, const StageSlots &ss,
+                                              const uint32_t *buf, int per_cu, const FastDiv &div_cu,
+                                              const FastDiv &div_k, int rb)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r = b.r, K = 2 * r + 1;
+    const StageShape &sh = t.sh;
+    const long traw = t.tf + tid;
+    const long tt = min(traw, t.ntask - 1);
+    const uint32_t q = fast_div(static_cast<uint32_t>(tt), div_cu);
+    const int slot = static_cast<int>(q - t.q0);
+    const int rem = static_cast<int>(tt - static_cast<long>(q) * per_cu);
+    const int band = static_cast<int>(fast_div(static_cast<uint32_t>(rem), div_k)), dxi = rem - band * K;
+    const int dxo = dxi - r;
+    const int b0 = band * TY - r;
+    const int dy0 = K >= TY ? min(b0, r - TY + 1) : b0;
+    // the lane's first sample of a block row, counted from the raw rows' column ax
+    const int xs = ss.off[slot] + dxo + r;
+    const uint32_t *win = buf + slot * sh.PW + ((xs & 1) ? sh.O1 : 0) + (xs >> 1);
+    const uint32_t *curw = buf + slot * sh.PW + sh.OC;
+    uint32_t acc[TY];
 #pragma unroll
-        for (int i = 0; i < TY; ++i) acc[i] = 0;
-        const int nb = RS / 8;
+    for (int i = 0; i < TY; ++i) acc[i] = 0;
+    const int nb = t.RS / 8;
 #pragma unroll 1
-        for (int blk = 0; blk < nb * nb; ++blk) {
-            const int bx = 8 * (blk % nb), by = 8 * (blk / nb);
-            uint4 cv[8];
-            uint32_t sa = 0;
+    for (int blk = 0; blk < nb * nb; ++blk) {
+        const int bx = 8 * (blk % nb), by = 8 * (blk / nb);
+        uint4 cv[8];
+        uint32_t sa = 0;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                cv[j] = *reinterpret_cast<const uint4 *>(curw + (by + j) * sh.CW + bx / 2);
-                sa += (cv[j].x + cv[j].y) + (cv[j].z + cv[j].w);
-            }
-            sads_staged_u16<TY>(cv, sa, b.one, win + (by + dy0 + r) * sh.RW + bx / 2, sh.RW, acc);
+        for (int j = 0; j < 8; ++j) {
+            cv[j] = *reinterpret_cast<const uint4 *>(curw + (by + j) * sh.CW + bx / 2);
+            sa += (cv[j].x + cv[j].y) + (cv[j].z + cv[j].w);
         }
+        sads_staged_u16<TY>(cv, sa, b.one, win + (by + dy0 + r) * sh.RW + bx / 2, sh.RW, acc);
+    }
 
-        const unsigned int ucu = q >> (2 * lg);
-        const unsigned long long task = __ldcg(b.tasks[c] + ucu);
-        const uint32_t lo = static_cast<uint32_t>(task);
-        const DependentItem &a = b.item[lo & 0xffu];
-        const RungInfo &rinf = b.rung[a.rung];
-        if (nr > 1) {
-            // this piece's SADs into the CU's table, every candidate once
-            if (traw < ntask) {
-                unsigned int *sum = b.sums[c] + static_cast<long>(ucu) * (K * K);
-#pragma unroll
-                for (int i = 0; i < TY; ++i) {
-                    const int dyo = dy0 + i;
-                    if (dyo >= b0 && dyo <= r) atomicAdd(sum + (dyo + r) * K + dxi, acc[i]);
-                }
-            }
-        } else {
-            const uint32_t cbase = static_cast<uint32_t>(abs(dxo) * 2 * K + 2 * (dy0 + r) + (dxo > 0));
-            unsigned long long best = ~0ull;
+    const unsigned int ucu = q >> (2 * t.lg);
+    const unsigned long long task = __ldcg(b.tasks[t.c] + ucu);
+    const uint32_t lo = static_cast<uint32_t>(task);
+    const DependentItem &a = b.item[lo & 0xffu];
+    const RungInfo &rinf = b.rung[a.rung];
+    if (t.nr > 1) {
+        // this piece's SADs into the CU's table, every candidate once
+        if (traw < t.ntask) {
+            unsigned int *sum = b.sums[t.c] + static_cast<long>(ucu) * (K * K);
 #pragma unroll
             for (int i = 0; i < TY; ++i) {
                 const int dyo = dy0 + i;
-                if (dyo > r) continue;
-                const uint32_t code = umad(static_cast<uint32_t>(abs(dyo)), 2u * K, cbase + 2u * i);
-                const unsigned long long key = (static_cast<unsigned long long>(acc[i]) << rb) | code;
-                best = key < best ? key : best;
-            }
-            // segmented min over the lanes of this CU in the warp
-            const long wfirst = tf + 32 * warp;  // the warp's first task
-            const long cu_first = static_cast<long>(q) * per_cu - wfirst;
-            const int first = static_cast<int>(max(cu_first, 0L));
-            const int last = static_cast<int>(min(cu_first + per_cu - 1, ntask - 1 - wfirst));
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long v = __shfl_down_sync(0xffffffffu, best, o);
-                if (lane + o <= last) best = v < best ? v : best;
-            }
-            if (lane == first && best != ~0ull) {
-                const uint32_t sad = static_cast<uint32_t>(best >> rb);
-                const int code = static_cast<int>(best & ((1ull << rb) - 1));
-                const int l1 = code / (2 * K), rr = code - l1 * 2 * K;
-                const int dyv = (rr >> 1) - r;
-                const int adx = l1 - abs(dyv);
-                const int dxv = (rr & 1) ? adx : -adx;
-                const uint32_t tb = static_cast<uint32_t>(l1 * K * K + (dyv + r) * K + (dxv + r));
-                unsigned long long *keys = reinterpret_cast<unsigned long long *>(a.block + rinf.off.keys);
-                atomicMin(keys + (lo >> 8), (static_cast<unsigned long long>(sad) << 32) | tb);
+                if (dyo >= b0 && dyo <= r) atomicAdd(sum + (dyo + r) * K + dxi, acc[i]);
             }
         }
-        __syncthreads();  // the next tile restages the slots
+        return;
+    }
+    const uint32_t cbase = static_cast<uint32_t>(abs(dxo) * 2 * K + 2 * (dy0 + r) + (dxo > 0));
+    unsigned long long best = ~0ull;
+#pragma unroll
+    for (int i = 0; i < TY; ++i) {
+        const int dyo = dy0 + i;
+        if (dyo > r) continue;
+        const uint32_t code = umad(static_cast<uint32_t>(abs(dyo)), 2u * K, cbase + 2u * i);
+        const unsigned long long key = (static_cast<unsigned long long>(acc[i]) << rb) | code;
+        best = key < best ? key : best;
+    }
+    // segmented min over the lanes of this CU in the warp
+    const long wfirst = t.tf + 32 * warp;  // the warp's first task
+    const long cu_first = static_cast<long>(q) * per_cu - wfirst;
+    const int first = static_cast<int>(max(cu_first, 0L));
+    const int last = static_cast<int>(min(cu_first + per_cu - 1, t.ntask - 1 - wfirst));
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long v = __shfl_down_sync(0xffffffffu, best, o);
+        if (lane + o <= last) best = v < best ? v : best;
+    }
+    if (lane == first && best != ~0ull) {
+        const uint32_t sad = static_cast<uint32_t>(best >> rb);
+        const int code = static_cast<int>(best & ((1ull << rb) - 1));
+        const int l1 = code / (2 * K), rr = code - l1 * 2 * K;
+        const int dyv = (rr >> 1) - r;
+        const int adx = l1 - abs(dyv);
+        const int dxv = (rr & 1) ? adx : -adx;
+        const uint32_t tb = static_cast<uint32_t>(l1 * K * K + (dyv + r) * K + (dxv + r));
+        unsigned long long *keys = reinterpret_cast<unsigned long long *>(a.block + rinf.off.keys);
+        atomicMin(keys + (lo >> 8), (static_cast<unsigned long long>(sad) << 32) | tb);
+    }
+}
+
+// pipelined = 1: two buffers of staged pieces, the next tile's async copies
+// filling one while the current tile is computed from the other; 0: one
+// buffer (less shared memory: more CTAs per SM overlap one another's
+// staging instead).  `half`: words of one buffer.
+template <int TY>
+__global__ void __launch_bounds__(kStageThreads, 2)
+    k_dep_search_st16(const __grid_constant__ DependentBatch b, const FastDiv div_cu, const FastDiv div_k,
+                      const __grid_constant__ StageDivs dv, int half, int pipelined)
+{
+    dev::chain_entry();
+    extern __shared__ __align__(16) uint32_t s_win[];
+    __shared__ StageSlots s_slots[2];
+    __shared__ long s_ln[kSizeClasses], s_tn[kSizeClasses];  // lane tasks and tiles per size class
+    const int r = b.r, K = 2 * r + 1;
+    const int per_cu = K * ((K + TY - 1) / TY);
+    const int code_max = 4 * r * K + 4 * r + 1;
+    const int rb = 32 - __clz(code_max);
+    if (threadIdx.x < kSizeClasses) {
+        const int c = threadIdx.x;
+        const long pieces = c < 2 ? 1 : (b.range >= 32 ? (c == 2 ? 1 : 4) : (c == 2 ? 4 : 16));
+        s_ln[c] = static_cast<long>(min(__ldcg(b.counts + c), b.cap[c])) * pieces * per_cu;
+        s_tn[c] = (s_ln[c] + kStageThreads - 1) / kStageThreads;
+    }
+    __syncthreads();
+    const long total = s_tn[0] + s_tn[1] + s_tn[2] + s_tn[3];
+    long tile = blockIdx.x;
+    if (tile >= total) return;  // the whole CTA: nothing to do
+    int bi = 0;
+    StageTile t = stage_tile<TY>(b, tile, per_cu, div_cu, s_ln, s_tn);
+    stage_slots_setup(b, t, s_slots[0]);
+    __syncthreads();
+    stage_copy(t, s_slots[0], s_win, dv.cps[t.c]);
+#pragma unroll 1
+    for (;;) {
+        uint32_t *buf = s_win + bi * half;
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
+        if (s_slots[bi].any_edge) {
+            stage_fixup(t, s_slots[bi], buf);
+            __syncthreads();
+        }
+        stage_raw1(t, buf, dv.c1[t.c]);
+        __syncthreads();
+        // the next tile of this CTA into the other buffer, in flight during this one
+        const long next = tile + gridDim.x;
+        if (pipelined && next < total) {
+            const StageTile tnext = stage_tile<TY>(b, next, per_cu, div_cu, s_ln, s_tn);
+            stage_slots_setup(b, tnext, s_slots[bi ^ 1]);
+            __syncthreads();
+            stage_copy(tnext, s_slots[bi ^ 1], s_win + (bi ^ 1) * half, dv.cps[tnext.c]);
+        }
+        stage_compute<TY>(b, t, s_slots[bi], buf, per_cu, div_cu, div_k, rb);
+        if (next >= total) break;
+        __syncthreads();  // the buffer and its slots are restaged (now, or by the tile after next)
+        t = stage_tile<TY>(b, next, per_cu, div_cu, s_ln, s_tn);  // recomputed: nothing held across the compute
+        tile = next;
+        if (pipelined) {
+            bi ^= 1;
+        } else {
+            stage_slots_setup(b, t, s_slots[0]);
+            __syncthreads();
+            stage_copy(t, s_slots[0], s_win, dv.cps[t.c]);
+        }
     }
 }
 
@@ -1071,6 +1182,7 @@ int smem_optin()
 
 // Dynamic shared memory of a staged search: the most pieces a tile touches
 // times the largest piece of any size class (0 if it does not fit a CTA).
+// (one buffer for b.staged == 1, two for 2; 0 if they do not fit a CTA).
 template <int TY> size_t staged_smem_bytes(const DependentBatch &b)
 {
     const int K = 2 * b.r + 1, per_cu = K * ((K + TY - 1) / TY);
@@ -1078,7 +1190,7 @@ template <int TY> size_t staged_smem_bytes(const DependentBatch &b)
     if (slots > kMaxStageSlots) return 0;
     int pw = 0;
     for (int S = 8; S <= 64; S <<= 1) pw = std::max(pw, stage_shape(S < b.range ? S : b.range, b.r, TY).PW);
-    const size_t bytes = static_cast<size_t>(slots) * pw * 4;
+    const size_t bytes = (b.staged == 2 ? 2 : 1) * static_cast<size_t>(slots) * pw * 4;
     return bytes <= static_cast<size_t>(smem_optin()) ? bytes : 0;
 }
 
@@ -1095,12 +1207,13 @@ template <int TY> cudaError_t search_staged(const DependentBatch &b, size_t smem
     for (int c = 0; c < kSizeClasses; ++c) {
         const int S = 8 << c;
         const StageShape sh = stage_shape(S < b.range ? S : b.range, b.r, TY);
-        dv.ups[c] = make_fastdiv(static_cast<uint32_t>(sh.UPS));
-        dv.nc[c] = make_fastdiv(static_cast<uint32_t>(sh.NC));
-        dv.wr[c] = make_fastdiv(static_cast<uint32_t>(sh.WR));
+        dv.cps[c] = make_fastdiv(static_cast<uint32_t>(kStageRowGroups * (sh.NC + sh.CNC)));
+        dv.c1[c] = make_fastdiv(static_cast<uint32_t>(kStageRowGroups * sh.NC));
     }
+    const int pipelined = b.staged == 2 ? 1 : 0;
+    const int half = static_cast<int>(smem / (pipelined ? 8 : 4));  // words of one buffer
     return launch_chained(k_dep_search_st16<TY>, dim3(grid), dim3(kStageThreads), smem, s, b, make_fastdiv(per_cu),
-                          make_fastdiv(K), dv);
+                          make_fastdiv(K), dv, half, pipelined);
 }
 
 template <typename T> cudaError_t search_bd(const DependentBatch &b, cudaStream_t s)

@@ -34,7 +34,7 @@ SPACE = {
     "dep_range": (16, 32),
     "dep_band": (0, 17, 9),
     "dep_ctas_per_sm": (0, 1, 2),
-    "dep_staged": (1, 0),
+    "dep_staged": (1, 2, 0),
 }
 DEFAULTS = {"fs_band": 13, "fs_group": 0, "fs_fuse": 1, "dep_range": 16, "dep_band": 0, "dep_ctas_per_sm": 0,
             "dep_staged": 1}

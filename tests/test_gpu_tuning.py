@@ -26,6 +26,8 @@ SETTINGS = [
     {"fs_fuse": 0, "fs_group": 2},
     {"fs_band": 9, "dep_range": 32, "dep_band": 17, "dep_ctas_per_sm": 2},
     {"dep_staged": 0},
+    {"dep_staged": 2},
+    {"dep_staged": 2, "dep_band": 17},
     {"dep_staged": 0, "dep_band": 17},
     {"dep_range": 32, "dep_band": 17},
 ]
