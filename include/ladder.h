@@ -61,7 +61,8 @@ typedef enum {
     LADDER_E_BUSY = -4,    /* no free frame slot */
     LADDER_E_CUDA = -5,    /* a CUDA runtime call failed; see ladder_last_error */
     LADDER_E_TIMEOUT = -6, /* a bounded device wait ran out (device status word) */
-    LADDER_E_STATE = -7    /* call out of order (e.g. fetch before analysis) */
+    LADDER_E_STATE = -7,   /* call out of order (e.g. fetch before analysis) */
+    LADDER_E_BOUNDS = -8   /* debug builds only: a device-side bounds check failed (the access was skipped) */
 } ladder_status;
 
 #define LADDER_MAX_DEPTHS 4 /* CU depths 0..3 for a 64x64 CTU: 64, 32, 16, 8 */
@@ -260,12 +261,29 @@ LADDER_API long ladder_device_bytes(const ladder_t *ladder);
 LADDER_API ladder_status analyze_independent(ladder_t *ladder, int rung, int frame_id, const void *cur,
                                   const void *ref, long pitch_bytes, int qp, void *cuda_stream);
 
-/* Copies the decisions of (rung, frame_id) into caller-owned host arrays
+/* Analysis save (the x265 analysis-save side of App. A.1: the decisions a
+ * master encode hands to the encodes that reuse them): copies the decisions
+ * of (rung, frame_id) into caller-owned host arrays
  * (sizes per ladder_grid); NULL members are skipped.  Waits for the copies on
  * `cuda_stream`, then checks the device status word: LADDER_E_TIMEOUT if a
  * bounded device wait ran out, LADDER_E_STATE if the rung was not analysed. */
 LADDER_API ladder_status fetch_decisions(ladder_t *ladder, int rung, int frame_id, ladder_decisions *out,
                               void *cuda_stream);
+
+/* Analysis load (the x265 analysis-load side of App. A.1: encodes that
+ * reuse a master encode's analysis read it back instead of analysing
+ * again): makes a reference analysis saved by fetch_decisions -- caller-owned
+ * HOST arrays of the reference rung, laid out as fetch_decisions writes them,
+ * every member up to depth log2(ctu_size/8) set -- the resident reference of
+ * frame `frame_id`, as if analyze_reference had produced it: dependents of
+ * the frame can then be analysed (resuming a ladder without its reference
+ * analysis, e.g. after a restart).  Claims a frame slot like
+ * analyze_reference (LADDER_E_BUSY if none is free).  Copies on
+ * `cuda_stream` and waits for the copy.  LADDER_E_INVAL for a missing array.
+ * The arrays are taken as given: decisions that no analysis of this geometry
+ * could give make the dependents' rules read them as they are. */
+LADDER_API ladder_status ladder_load_reference(ladder_t *ladder, int frame_id, const ladder_decisions *in,
+                                               void *cuda_stream);
 
 /* Cascaded reference chain (Sec. 6.5, the proposed multi-encoding scheme:
  * the refined decisions of one resolution tier are the reference of the
@@ -447,7 +465,9 @@ LADDER_API void ladder_pipeline_destroy(ladder_pipeline_t *pipe);
  * `dims` must hold 2 * LADDER_MAX_DEPTHS + 2 ints. */
 LADDER_API ladder_status ladder_grid(const ladder_t *ladder, int rung, int *dims, int *n_depths);
 
-/* Frees the frame slot of `frame_id` (its resident reference decisions).
+/* Frees the frame slot of `frame_id`: the frame's resident decisions, which
+ * stand in for the analysis file the master encode writes for the encodes
+ * that reuse it (App. A.1), are no longer needed.
  * Enqueued work that still reads the slot must have completed (ladder_sync). */
 LADDER_API ladder_status ladder_release_frame(ladder_t *ladder, int frame_id);
 
@@ -463,7 +483,10 @@ LADDER_API void ladder_destroy(ladder_t *ladder);
 /* Text of the last error on this handle ("" if none).  Valid until the next call. */
 LADDER_API const char *ladder_last_error(const ladder_t *ladder);
 
-/* Kernel timing (tracing).  Launches are always counted per kernel kind;
+/* Tracing.  Every call that enqueues or waits for device work opens an
+ * NVTX range named after the call (NVTX 3; free unless a profiler that reads
+ * NVTX is attached), so a timeline shows each call beside its kernels.
+ * Kernel timing: launches are always counted per kernel kind;
  * when timing is enabled every launch is also bracketed by CUDA events on
  * its own stream (a few microseconds per launch, off by default).  Kinds:
  * 0 full search, 1 SATD/cost/split of an independent rung, 2 refinement

@@ -1,6 +1,11 @@
 """Builds libladder.so in-tree for sm_103a: one nvcc per translation unit, in
 parallel, then one link.  Used by ``__graft_entry__.build()`` and by the
-binding when the library is missing or older than its sources."""
+binding when the library is missing or older than its sources.
+
+``build(debug=True)`` builds libladder_debug.so, the same sources compiled
+with LADDER_BOUNDS_CHECK=1: device-side checks of array indexes and plane
+offsets that record LADDER_E_BOUNDS in the status word and skip the access
+(the stand-in for a memory checker on GPUs where none can run)."""
 from __future__ import annotations
 
 import concurrent.futures
@@ -13,6 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libladder.so")
+OUT_DIR_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libladder_debug.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -37,22 +44,26 @@ def _deps():
         os.path.join(ROOT, "include", "ladder.h"), __file__]
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def stale(debug: bool = False) -> bool:
+    lib = LIB_DEBUG if debug else LIB
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    if not force and not stale():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, debug: bool = False) -> str:
+    lib, out_dir = (LIB_DEBUG, OUT_DIR_DEBUG) if debug else (LIB, OUT_DIR)
+    if not force and not stale(debug):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    if debug:
+        extra += ["-DLADDER_BOUNDS_CHECK=1"]
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -65,14 +76,21 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         for _, log in results:
             if log:
                 sys.stderr.write(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *[o for o, _ in results]]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build_all(force: bool = False) -> None:
+    """The release and the bounds-checked debug library, side by side."""
+    with concurrent.futures.ThreadPoolExecutor(max_workers=2) as ex:
+        for f in [ex.submit(build, force=force, debug=d) for d in (False, True)]:
+            f.result()
 
 
 if __name__ == "__main__":
-    print(build(force=True, verbose=True, ptxas_info="-v" in sys.argv))
+    print(build(force=True, verbose=True, ptxas_info="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -149,7 +149,7 @@ __device__ __forceinline__ int satd8_transform(float (&v)[64], int mode);
 //   mode 1: two 4x4 Hadamards per 8x4 half, (sum of both) >> 1, halves added
 template <typename T>
 __device__ __forceinline__ int satd8_thread(const void *cur, const void *ref, long pitch, int W, int H, int px, int py,
-                                            int mvx, int mvy, int mode)
+                                            int mvx, int mvy, int mode, int *status = nullptr)
 {
     const char *cb = static_cast<const char *>(cur);
     const char *rb = static_cast<const char *>(ref);
@@ -158,6 +158,13 @@ __device__ __forceinline__ int satd8_thread(const void *cur, const void *ref, lo
     const bool cur_fast = px + 8 <= W;
     const bool ref_fast = rx0 >= 0 && (rx0 / SPW + WPR + 1) * SPW <= W;
     const int sh = (rx0 & (SPW - 1)) * BITS;
+    // debug builds: the rows are clamped into [0, H); the fast paths' row
+    // spans (8 current samples from px, WPR + 1 reference words from
+    // rx0 / SPW) must end inside the row's pitch
+    if ((cur_fast && !in_range(status, static_cast<long>(px + 8) * sizeof(T) - 1, pitch)) ||
+        (ref_fast && !in_range(status, static_cast<long>(rx0 / SPW + WPR + 1) * 4 - 1, pitch)) ||
+        !in_range(status, px, W))
+        return 0;
     float v[64];
 #pragma unroll
     for (int y = 0; y < 8; ++y) {
@@ -305,6 +312,7 @@ struct DecideIO {
     int qp, satd_mode;
     const int *lambda_q16;  // 52 entries
     DevDecisions out;
+    int *status;            // debug builds record failed bounds checks here (may be null)
 };
 
 // Index of CU (d, local raster li) in the per-CTU key layout.
@@ -339,7 +347,8 @@ enum : int {
 //             the children's best sum is strictly lower), or it must
 template <int CTU>
 __device__ void ctu_split(CtuState<CTU> &st, int lam, const RungGeom &g, const DevDecisions &out, int write, int x0,
-                          int y0, bool qpel = false, const int16_t *pmx = nullptr, const int16_t *pmy = nullptr)
+                          int y0, bool qpel = false, const int16_t *pmx = nullptr, const int16_t *pmy = nullptr,
+                          int *status = nullptr)
 {
     using C = Ctu<CTU>;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -377,6 +386,7 @@ __device__ void ctu_split(CtuState<CTU> &st, int lam, const RungGeom &g, const D
             st.best[i] = best;
             st.split[i] = split;
             const long gi = static_cast<long>(y0 / S + li / n) * g.cols[d] + x0 / S + li % n;
+            if (!in_range(status, gi, static_cast<long>(g.cols[d]) * g.rows[d])) continue;
             if (write & kSplitWriteVectors) {
                 out.mvx[d][gi] = st.mvx[i];
                 out.mvy[d][gi] = st.mvy[i];
@@ -404,6 +414,7 @@ __device__ void ctu_split(CtuState<CTU> &st, int lam, const RungGeom &g, const D
             ++d;
         }
         const long li = static_cast<long>(py / 8) * g.cols8 + px / 8;
+        if (!in_range(status, li, static_cast<long>(g.cols8) * g.rows8)) continue;
         out.leaf_depth[li] = static_cast<uint8_t>(d);
         out.leaf_mvx[li] = st.mvx[i];
         out.leaf_mvy[li] = st.mvy[i];
@@ -446,17 +457,18 @@ __device__ void ctu_decide(CtuState<CTU> &st, const DecideIO &io, int x0, int y0
                 if (((left >> e) & 1u) && st.mvx[ci[e]] == st.mvx[ci[d]] && st.mvy[ci[e]] == st.mvy[ci[d]])
                     mask |= 1u << e;
             left &= ~mask;
-            st.pairs[atomicAdd(&st.npairs, 1)] = static_cast<uint16_t>(b | (mask << 8));
+            const int slot = atomicAdd(&st.npairs, 1);
+            if (in_range(io.status, slot, (C::DMAX + 1) * C::NB8)) st.pairs[slot] = static_cast<uint16_t>(b | (mask << 8));
         }
     }
     __syncthreads();
     // one thread per entry
-    for (int p = tid; p < st.npairs; p += nthr) {
+    for (int p = tid; p < min(st.npairs, (C::DMAX + 1) * C::NB8); p += nthr) {
         const unsigned ent = st.pairs[p];
         const int b = ent & 0xff, bx = b % C::N8, by = b / C::N8;
         const int i0 = key_of_block<CTU>(__ffs(ent >> 8) - 1, bx, by);
         const int v = satd8_thread<T>(io.cur, io.ref, io.pitch_bytes, g.W, g.H, x0 + 8 * bx, y0 + 8 * by, st.mvx[i0],
-                                      st.mvy[i0], io.satd_mode);
+                                      st.mvy[i0], io.satd_mode, io.status);
 #pragma unroll
         for (int d = 0; d <= C::DMAX; ++d) {
             if (!((ent >> (8 + d)) & 1u)) continue;
@@ -465,7 +477,7 @@ __device__ void ctu_decide(CtuState<CTU> &st, const DecideIO &io, int x0, int y0
     }
     __syncthreads();
 
-    ctu_split<CTU>(st, io.lambda_q16[io.qp], *io.g, io.out, kSplitWriteAll, x0, y0);
+    ctu_split<CTU>(st, io.lambda_q16[io.qp], *io.g, io.out, kSplitWriteAll, x0, y0, false, nullptr, nullptr, io.status);
 }
 
 // ---- dependent-mode constraint derivation --------------------------------
@@ -494,7 +506,8 @@ __device__ __forceinline__ Rule derive_rule(const RungGeom &g, const DepRefs &rf
     const int S = g.ctu >> d;
     const int xm = min(static_cast<int>(fast_div(static_cast<unsigned>((2 * x0 + S) * rf.Wr), g.div_2w)), rf.Wr - 1);
     const int ym = min(static_cast<int>(fast_div(static_cast<unsigned>((2 * y0 + S) * rf.Hr), g.div_2h)), rf.Hr - 1);
-    const int li = (ym >> 3) * rf.cols8_r + (xm >> 3);
+    int li = (ym >> 3) * rf.cols8_r + (xm >> 3);
+    if (!in_range(rf.status, li, rf.n8_r)) li = 0;
     const int depth_r = __ldcg(rf.leaf_depth + li);
     Rule r;
     if (rf.use_ref_mv) {

@@ -44,9 +44,11 @@ __global__ void __launch_bounds__(kThreads) k_decide(const __grid_constant__ Dec
         st.flags[i] = flags;
         st.satd[i] = 0;
         // read the key and reset it to ~0 for the next search
-        unsigned long long *kp = const_cast<unsigned long long *>(keys) + static_cast<long>(ctu_idx) * C::NKEY + i;
+        const long ki = static_cast<long>(ctu_idx) * C::NKEY + i;
+        const bool kin = in_range(b.status, ki, static_cast<long>(g.ctu_cols) * g.ctu_rows * C::NKEY);
+        unsigned long long *kp = const_cast<unsigned long long *>(keys) + (kin ? ki : 0);
         const unsigned long long key = __ldcg(kp);
-        *kp = ~0ull;
+        if (kin) *kp = ~0ull;
         if (flags & kRuleEvaluated) {
             const int rem = static_cast<int>(static_cast<uint32_t>(key & 0xffffffffu) % static_cast<uint32_t>(K * K));
             st.mvx[i] = static_cast<int16_t>(rem % K - b.range);
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(kThreads) k_decide(const __grid_constant__ Dec
     }
     __syncthreads();
     dev::DecideIO io{item.cur, item.ref, item.pitch_bytes, &g, item.qp, b.satd_mode, c_lambda_q16,
-                     decisions_at(item.block, ri.off)};
+                     decisions_at(item.block, ri.off), b.status};
     dev::ctu_decide<T, CTU>(st, io, x0, y0);
 }
 

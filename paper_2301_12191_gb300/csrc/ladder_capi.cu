@@ -6,6 +6,7 @@
 #include "ladder_internal.h"
 
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cstdarg>
@@ -122,6 +123,13 @@ struct ladder_graph {
 
 namespace {
 
+// An NVTX range around a public call (no cost without an attached tool):
+// profilers show each call's host span beside its kernels.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+};
+
 ladder_status fail(ladder_t *l, ladder_status st, const char *fmt, ...)
 {
     if (l) {
@@ -139,6 +147,7 @@ ladder_status fail(ladder_t *l, ladder_status st, const char *fmt, ...)
 ladder_status device_status_error(ladder_t *l, int status)
 {
     if (status == kStatusTaskOverflow) return fail(l, LADDER_E_STATE, "a dependent task list overflowed");
+    if (status == kStatusBounds) return fail(l, LADDER_E_BOUNDS, "a device-side bounds check failed");
     return fail(l, LADDER_E_TIMEOUT, "a bounded device wait ran out");
 }
 
@@ -423,6 +432,7 @@ ladder_status launch_independent(ladder_t *l, const Job *jobs, int n, cudaStream
         db.n = m;
         db.range = R;
         db.satd_mode = l->geo.satd_mode;
+        db.status = l->d_status;
         for (int r = 0; r < l->geo.n_rungs; ++r) db.rung[r] = l->info[r];
         int total = 0, total_ctas = 0;
         for (int k = 0; k < m; ++k) {
@@ -600,10 +610,14 @@ ladder_status launch_dependents(ladder_t *l, const Job *jobs, int n, cudaStream_
 
 extern "C" {
 
-const char *ladder_version(void) { return "ladder 0.2 (sm_103a)"; }
+const char *ladder_version(void)
+{
+    return LADDER_BOUNDS_CHECK ? "ladder 0.3 (sm_103a, bounds-checked debug build)" : "ladder 0.3 (sm_103a)";
+}
 
 ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, ladder_t **out)
 {
+    TraceRange trace("ladder_init");
     if (!out) return LADDER_E_INVAL;
     *out = nullptr;
     ladder_status st = validate_geometry(geometry);
@@ -741,6 +755,7 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
 ladder_status analyze_independent(ladder_t *l, int rung, int frame_id, const void *cur, const void *ref,
                                   long pitch_bytes, int qp, void *cuda_stream)
 {
+    TraceRange trace("analyze_independent");
     if (!l) return LADDER_E_INVAL;
     ladder_status st = check_planes(l, rung, cur, ref, pitch_bytes, qp);
     if (st != LADDER_OK) return st;
@@ -762,6 +777,7 @@ ladder_status analyze_reference(ladder_t *l, int frame_id, const void *cur, cons
 ladder_status analyze_dependents(ladder_t *l, int frame_id, int n, const int *rungs, const void *const *cur,
                                  const void *const *ref, const long *pitch_bytes, int qp, void *cuda_stream)
 {
+    TraceRange trace("analyze_dependents");
     if (!l) return LADDER_E_INVAL;
     if (n < 1 || n > kMaxRungs || !rungs || !cur || !ref || !pitch_bytes)
         return fail(l, LADDER_E_INVAL, "dependent batch of %d rungs (1..%d)", n, kMaxRungs);
@@ -796,6 +812,7 @@ ladder_status analyze_dependent(ladder_t *l, int rung, int frame_id, const void 
 
 ladder_status ladder_analyze_batch(ladder_t *l, const ladder_request *reqs, int n, void *cuda_stream)
 {
+    TraceRange trace("ladder_analyze_batch");
     if (!l) return LADDER_E_INVAL;
     const int nd = l->geo.n_rungs - 1;
     if (!reqs || n < 1 || n > kMaxItems || n * nd > kMaxDepItems)
@@ -838,6 +855,7 @@ ladder_status ladder_analyze_batch(ladder_t *l, const ladder_request *reqs, int 
 
 ladder_status ladder_analyze_batch_independent(ladder_t *l, const ladder_request *reqs, int n, void *cuda_stream)
 {
+    TraceRange trace("ladder_analyze_batch_independent");
     if (!l) return LADDER_E_INVAL;
     if (!reqs || n < 1 || n > kMaxItems) return fail(l, LADDER_E_INVAL, "batch of %d frames (1..%d)", n, kMaxItems);
     for (int k = 0; k < n; ++k) {
@@ -873,6 +891,7 @@ ladder_status ladder_analyze_batch_independent(ladder_t *l, const ladder_request
 
 ladder_status ladder_analyze_jobs(ladder_t *l, const ladder_job *jobs, int n, void *cuda_stream)
 {
+    TraceRange trace("ladder_analyze_jobs");
     if (!l) return LADDER_E_INVAL;
     if (!jobs || n < 0) return fail(l, LADDER_E_INVAL, "bad job list");
     if (n == 0) return LADDER_OK;
@@ -928,6 +947,7 @@ ladder_status ladder_analyze_jobs(ladder_t *l, const ladder_job *jobs, int n, vo
 ladder_status ladder_capture_batch(ladder_t *l, const ladder_request *reqs, int n, void *cuda_stream,
                                    ladder_graph_t **out)
 {
+    TraceRange trace("ladder_capture_batch");
     if (!l || !out) return LADDER_E_INVAL;
     *out = nullptr;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -967,6 +987,7 @@ ladder_status ladder_capture_batch(ladder_t *l, const ladder_request *reqs, int 
 
 ladder_status ladder_graph_launch(ladder_graph_t *g, void *cuda_stream)
 {
+    TraceRange trace("ladder_graph_launch");
     if (!g || !g->exec) return LADDER_E_INVAL;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     if (cudaGraphLaunch(g->exec, s) != cudaSuccess) return LADDER_E_CUDA;
@@ -999,6 +1020,7 @@ ladder_status ladder_grid(const ladder_t *l, int rung, int *dims, int *n_depths)
 
 ladder_status ladder_sync(ladder_t *l, void *cuda_stream)
 {
+    TraceRange trace("ladder_sync");
     if (!l) return LADDER_E_INVAL;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     int status = 0;
@@ -1052,6 +1074,7 @@ ladder_status ladder_set_mv_predictor(ladder_t *l, int mode)
 ladder_status ladder_decide_qps(ladder_t *l, int rung, int frame_id, int n, const int *qps,
                                 const ladder_qp_decisions *out, void *cuda_stream)
 {
+    TraceRange trace("ladder_decide_qps");
     if (!l || !qps || !out) return LADDER_E_INVAL;
     if (rung < 0 || rung >= l->geo.n_rungs) return fail(l, LADDER_E_INVAL, "rung %d out of range", rung);
     if (n < 1 || n > kMaxQps) return fail(l, LADDER_E_INVAL, "%d QPs (1..%d)", n, kMaxQps);
@@ -1118,6 +1141,7 @@ ladder_status ladder_decide_qps(ladder_t *l, int rung, int frame_id, int n, cons
 
 ladder_status fetch_decisions(ladder_t *l, int rung, int frame_id, ladder_decisions *out, void *cuda_stream)
 {
+    TraceRange trace("fetch_decisions");
     if (!l || !out) return LADDER_E_INVAL;
     if (rung < 0 || rung >= l->geo.n_rungs) return fail(l, LADDER_E_INVAL, "rung %d out of range", rung);
     Slot *slot = find_slot(l, frame_id);
@@ -1152,6 +1176,48 @@ ladder_status fetch_decisions(ladder_t *l, int rung, int frame_id, ladder_decisi
     copy(out->leaf_mvx, o.leaf_mvx, n8 * 2);
     copy(out->leaf_mvy, o.leaf_mvy, n8 * 2);
     return ladder_sync(l, cuda_stream);
+}
+
+ladder_status ladder_load_reference(ladder_t *l, int frame_id, const ladder_decisions *in, void *cuda_stream)
+{
+    TraceRange trace("ladder_load_reference");
+    if (!l || !in) return LADDER_E_INVAL;
+    const int rung = l->geo.ref_rung;
+    const RungGeom &g = l->info[rung].g;
+    const DecOffsets &o = l->info[rung].off;
+    for (int d = 0; d <= g.dmax; ++d)
+        if (!in->mvx[d] || !in->mvy[d] || !in->sad[d] || !in->satd[d] || !in->cost[d] || !in->best[d] ||
+            !in->split[d] || !in->evaluated[d])
+            return fail(l, LADDER_E_INVAL, "depth %d arrays missing", d);
+    if (!in->leaf_depth || !in->leaf_mvx || !in->leaf_mvy) return fail(l, LADDER_E_INVAL, "leaf arrays missing");
+    Slot *slot = claim_slot(l, frame_id);
+    if (!slot) return fail(l, LADDER_E_BUSY, "no free frame slot for frame %d", frame_id);
+    // the caller's arrays into the pinned staging buffer in the block's
+    // layout, then one copy into the frame's reference-rung block
+    auto put = [&](long off, const void *src, size_t bytes) { memcpy(l->host_stage + off, src, bytes); };
+    for (int d = 0; d <= g.dmax; ++d) {
+        const size_t n = static_cast<size_t>(g.cols[d]) * g.rows[d];
+        put(o.mvx[d], in->mvx[d], n * 2);
+        put(o.mvy[d], in->mvy[d], n * 2);
+        put(o.sad[d], in->sad[d], n * 4);
+        put(o.satd[d], in->satd[d], n * 4);
+        put(o.cost[d], in->cost[d], n * 4);
+        put(o.best[d], in->best[d], n * 4);
+        put(o.split[d], in->split[d], n);
+        put(o.evaluated[d], in->evaluated[d], n);
+    }
+    const size_t n8 = static_cast<size_t>(g.cols8) * g.rows8;
+    put(o.leaf_depth, in->leaf_depth, n8);
+    put(o.leaf_mvx, in->leaf_mvx, n8 * 2);
+    put(o.leaf_mvy, in->leaf_mvy, n8 * 2);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaMemcpyAsync(slot->rungs[rung].block, l->host_stage, static_cast<size_t>(o.dec_bytes),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the staging buffer is free again
+    if (e != cudaSuccess) return cuda_fail(l, e, "reference load copy");
+    slot->rungs[rung].analysed = 1;
+    slot->ref_done = 1;
+    return LADDER_OK;
 }
 
 long ladder_subpel_workspace_bytes(const ladder_t *l, int rung)
@@ -1211,6 +1277,7 @@ ladder_status subpel_item(ladder_t *l, const ladder_subpel_job &j, SubpelItem &i
 
 ladder_status ladder_refine_subpel_batch(ladder_t *l, int n, const ladder_subpel_job *jobs, void *cuda_stream)
 {
+    TraceRange trace("ladder_refine_subpel_batch");
     if (!l || !jobs) return LADDER_E_INVAL;
     if (n < 1 || n > LADDER_MAX_SUBPEL_JOBS)
         return fail(l, LADDER_E_INVAL, "%d jobs: 1 .. %d per call", n, LADDER_MAX_SUBPEL_JOBS);
@@ -1288,6 +1355,7 @@ ladder_status ladder_decision_offsets(const ladder_t *l, int rung, long *offsets
 
 ladder_status ladder_fetch_frame_async(ladder_t *l, int frame_id, void *host_dst, long bytes, void *cuda_stream)
 {
+    TraceRange trace("ladder_fetch_frame_async");
     if (!l || !host_dst) return LADDER_E_INVAL;
     if (bytes < ladder_frame_bytes(l)) return fail(l, LADDER_E_INVAL, "%ld bytes, the frame needs %ld", bytes, ladder_frame_bytes(l));
     Slot *slot = find_slot(l, frame_id);
@@ -1421,6 +1489,7 @@ ladder_status pipeline_take_pending(ladder_pipeline *p)
 
 ladder_status ladder_pipeline_submit(ladder_pipeline_t *p, const void *host_in, int qp, void *host_out, long *ticket)
 {
+    TraceRange trace("ladder_pipeline_submit");
     if (!p || !host_in || !host_out) return LADDER_E_INVAL;
     ladder_t *l = p->l;
     const int j = static_cast<int>(p->next % p->depth), frame_id = p->base + j;
@@ -1481,6 +1550,7 @@ ladder_status ladder_pipeline_submit(ladder_pipeline_t *p, const void *host_in, 
 
 ladder_status ladder_pipeline_wait(ladder_pipeline_t *p, long ticket)
 {
+    TraceRange trace("ladder_pipeline_wait");
     if (!p) return LADDER_E_INVAL;
     if (ticket < 0 || ticket >= p->next) return fail(p->l, LADDER_E_INVAL, "ticket %ld not submitted", ticket);
     const int j = static_cast<int>(ticket % p->depth);
@@ -1600,6 +1670,7 @@ long ladder_device_bytes(const ladder_t *l) { return l ? static_cast<long>(l->ar
 
 void ladder_destroy(ladder_t *l)
 {
+    TraceRange trace("ladder_destroy");
     if (!l) return;
     // the handle's own work only: other handles' streams keep running
     for (auto &m : l->marks) {

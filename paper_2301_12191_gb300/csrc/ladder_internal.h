@@ -37,6 +37,30 @@ inline cudaError_t launch_chained(void (*kernel)(Params...), dim3 grid, dim3 blo
 constexpr int kStatusOk = 0;
 constexpr int kStatusTimeout = -6;
 constexpr int kStatusTaskOverflow = -7;  // a dependent task list ran out of room (sized so it cannot)
+constexpr int kStatusBounds = -8;        // debug builds: an index failed its bounds check (the access was skipped)
+
+// Debug builds (compiled with LADDER_BOUNDS_CHECK=1) check array indexes and
+// plane offsets on the device: a failed check records kStatusBounds in the
+// launch's status word (first failure wins) and the caller skips the
+// access.  Release builds compile every check to `true`.
+#ifndef LADDER_BOUNDS_CHECK
+#define LADDER_BOUNDS_CHECK 0
+#endif
+#ifdef __CUDACC__
+__device__ __forceinline__ bool in_range(int *status, long i, long n)
+{
+#if LADDER_BOUNDS_CHECK
+    if (i >= 0 && i < n) return true;
+    if (status) atomicCAS(status, kStatusOk, kStatusBounds);
+    return false;
+#else
+    (void)status;
+    (void)i;
+    (void)n;
+    return true;
+#endif
+}
+#endif
 
 // Per-CTU layout of the candidate keys written by the motion search and read
 // by the decision kernel: depth d occupies (4^d - 1) / 3 ... (4^(d+1) - 1) / 3,
@@ -245,6 +269,7 @@ struct DecideBatch {
     int range;            // R: decodes the keys
     int satd_mode;
     int total_ctas;
+    int *status;          // device status word (debug builds record failed bounds checks)
     RungInfo rung[kMaxRungs];
     DecideItem item[kMaxItems];
 };
@@ -258,6 +283,8 @@ struct DepRefs {
     const int16_t *leaf_mvx, *leaf_mvy;
     int depth_lo, depth_hi, use_ref_mv;
     FastDiv div_2wr, div_2hr;  // division by 2 Wr, 2 Hr
+    long n8_r;                 // 8x8 blocks of the reference rung (bounds checks)
+    int *status;
 };
 
 struct DependentItem {

@@ -96,6 +96,8 @@ __global__ void __launch_bounds__(kRulesThreads) k_dep_rules(const __grid_consta
         refs.use_ref_mv = b.use_ref_mv;
         refs.div_2wr = rref.g.div_2w;
         refs.div_2hr = rref.g.div_2h;
+        refs.n8_r = static_cast<long>(rref.g.cols8) * rref.g.rows8;
+        refs.status = b.status;
         const bool inside = cu_x + S <= g.W8 && cu_y + S <= g.H8;
         const dev::Rule ru = dev::derive_rule(g, refs, d, cu_x, cu_y);
         cx = static_cast<int16_t>(ru.cx);
@@ -122,7 +124,8 @@ __global__ void __launch_bounds__(kRulesThreads) k_dep_rules(const __grid_consta
         if (reach && s_splitok[tid]) f |= kRuleCanSplit;
         if (f & kRuleEvaluated) atomicAdd(&s_cnt[C::DMAX - d], 1u);  // size class of an S = CTU >> d CU
     }
-    if (mine) {
+    const long nk_frame = static_cast<long>(g.ctu_cols) * g.ctu_rows * NK;  // key slots of the frame
+    if (mine && in_range(b.status, kbase + tid, nk_frame)) {
         reinterpret_cast<int16_t *>(a.block + rinf.off.dep_cx)[kbase + tid] = cx;
         reinterpret_cast<int16_t *>(a.block + rinf.off.dep_cy)[kbase + tid] = cy;
         reinterpret_cast<uint8_t *>(a.block + rinf.off.dep_flags)[kbase + tid] = f;
@@ -153,14 +156,16 @@ __global__ void __launch_bounds__(kRulesThreads) k_dep_rules(const __grid_consta
             pos = static_cast<int>(p);
         }
     }
-    if (mine) reinterpret_cast<int *>(a.block + rinf.off.dep_slot)[kbase + tid] = pos;
+    if (mine && in_range(b.status, kbase + tid, nk_frame)) reinterpret_cast<int *>(a.block + rinf.off.dep_slot)[kbase + tid] = pos;
     if (tid < NBIG) s_big[tid] = S > b.range ? pos : -1;
     __syncthreads();
     // zeroed sum tables of the CUs searched in pieces
     const int KK = (2 * b.r + 1) * (2 * b.r + 1);
     for (int i = 0; i < NBIG; ++i) {
         if (s_big[i] < 0) continue;
-        unsigned int *sum = b.sums[C::DMAX - depth_of(i, C::DMAX)] + static_cast<long>(s_big[i]) * KK;
+        const int cls = C::DMAX - depth_of(i, C::DMAX);
+        if (!in_range(b.status, s_big[i], b.cap[cls])) continue;
+        unsigned int *sum = b.sums[cls] + static_cast<long>(s_big[i]) * KK;
         for (int k = tid; k < KK; k += kRulesThreads) sum[k] = 0;
     }
 }
@@ -444,6 +449,7 @@ __device__ __forceinline__ void search_tile(const DependentBatch &b, int c, int 
     const int rg = static_cast<int>(q & static_cast<uint32_t>(nr - 1));
     const int rem = static_cast<int>(t - static_cast<long>(q) * per_cu);
     const int band = static_cast<int>(fast_div(static_cast<uint32_t>(rem), div_k)), dxi = rem - band * K;
+    if (!in_range(b.status, u, b.cap[c])) return;  // (debug builds) a lane's CU lies in its task list
     const unsigned long long task = __ldcg(b.tasks[c] + u);
     const uint32_t lo = static_cast<uint32_t>(task), hi = static_cast<uint32_t>(task >> 32);
     const DependentItem &a = b.item[lo & 0xffu];
@@ -490,7 +496,8 @@ __device__ __forceinline__ void search_tile(const DependentBatch &b, int c, int 
 #pragma unroll
             for (int i = 0; i < TY; ++i) {
                 const int dyo = dy0 + i;
-                if (dyo >= b0 && dyo <= r) atomicAdd(sum + (dyo + r) * K + dxi, acc[i]);
+                if (dyo >= b0 && dyo <= r && in_range(b.status, (dyo + r) * K + dxi, K * K))
+                    atomicAdd(sum + (dyo + r) * K + dxi, acc[i]);
             }
         }
         return;
@@ -539,7 +546,8 @@ __device__ __forceinline__ void search_tile(const DependentBatch &b, int c, int 
         const int dxv = (rr & 1) ? adx : -adx;
         const uint32_t tb = static_cast<uint32_t>(l1 * K * K + (dyv + r) * K + (dxv + r));
         unsigned long long *keys = reinterpret_cast<unsigned long long *>(a.block + rinf.off.keys);
-        atomicMin(keys + (lo >> 8), (static_cast<unsigned long long>(sad) << 32) | tb);
+        const long nk = static_cast<long>(rinf.g.ctu_cols) * rinf.g.ctu_rows * keys_per_ctu(rinf.g.dmax);
+        if (in_range(b.status, lo >> 8, nk)) atomicMin(keys + (lo >> 8), (static_cast<unsigned long long>(sad) << 32) | tb);
     }
 }
 
@@ -909,6 +917,14 @@ __device__ __forceinline__ void stage_compute(const DependentBatch &b, const Sta
     const int xs = ss.off[slot] + dxo + r;
     const uint32_t *win = buf + slot * sh.PW + ((xs & 1) ? sh.O1 : 0) + (xs >> 1);
     const uint32_t *curw = buf + slot * sh.PW + sh.OC;
+    // debug builds: the lane's slot is staged, and its last window word lies
+    // in its raw rows (else it reads the slot's first words; recorded)
+    if (!in_range(b.status, slot, t.nslots) ||
+        !in_range(b.status, (t.RS - 8 + dy0 + r + TY + 6) * sh.RW + (xs >> 1) + (t.RS - 8) / 2 + 3,
+                  sh.WR * sh.RW)) {
+        win = buf;
+        curw = buf;
+    }
     uint32_t acc[TY];
 #pragma unroll
     for (int i = 0; i < TY; ++i) acc[i] = 0;
@@ -933,12 +949,13 @@ __device__ __forceinline__ void stage_compute(const DependentBatch &b, const Sta
     const RungInfo &rinf = b.rung[a.rung];
     if (t.nr > 1) {
         // this piece's SADs into the CU's table, every candidate once
-        if (traw < t.ntask) {
+        if (traw < t.ntask && in_range(b.status, ucu, b.cap[t.c])) {
             unsigned int *sum = b.sums[t.c] + static_cast<long>(ucu) * (K * K);
 #pragma unroll
             for (int i = 0; i < TY; ++i) {
                 const int dyo = dy0 + i;
-                if (dyo >= b0 && dyo <= r) atomicAdd(sum + (dyo + r) * K + dxi, acc[i]);
+                if (dyo >= b0 && dyo <= r && in_range(b.status, (dyo + r) * K + dxi, K * K))
+                    atomicAdd(sum + (dyo + r) * K + dxi, acc[i]);
             }
         }
         return;
@@ -972,7 +989,8 @@ __device__ __forceinline__ void stage_compute(const DependentBatch &b, const Sta
         const int dxv = (rr & 1) ? adx : -adx;
         const uint32_t tb = static_cast<uint32_t>(l1 * K * K + (dyv + r) * K + (dxv + r));
         unsigned long long *keys = reinterpret_cast<unsigned long long *>(a.block + rinf.off.keys);
-        atomicMin(keys + (lo >> 8), (static_cast<unsigned long long>(sad) << 32) | tb);
+        const long nk = static_cast<long>(rinf.g.ctu_cols) * rinf.g.ctu_rows * keys_per_ctu(rinf.g.dmax);
+        if (in_range(b.status, lo >> 8, nk)) atomicMin(keys + (lo >> 8), (static_cast<unsigned long long>(sad) << 32) | tb);
     }
 }
 
@@ -1058,7 +1076,9 @@ __global__ void __launch_bounds__(kDecideThreads) k_dep_decide(const __grid_cons
     const int tid = threadIdx.x;
     const int ctu_idx = blockIdx.x - a.cta_begin;
     const int x0 = (ctu_idx % g.ctu_cols) * CTU, y0 = (ctu_idx / g.ctu_cols) * CTU;
-    const long kbase = static_cast<long>(ctu_idx) * C::NKEY;
+    long kbase = static_cast<long>(ctu_idx) * C::NKEY;
+    // debug builds: the CTU's key slots lie in the frame's
+    if (!in_range(b.status, kbase + C::NKEY - 1, static_cast<long>(g.ctu_cols) * g.ctu_rows * C::NKEY)) kbase = 0;
     const int r = b.r, K = 2 * r + 1;
     const int16_t *in_cx = reinterpret_cast<const int16_t *>(a.block + rinf.off.dep_cx) + kbase;
     const int16_t *in_cy = reinterpret_cast<const int16_t *>(a.block + rinf.off.dep_cy) + kbase;
@@ -1083,6 +1103,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_dep_decide(const __grid_cons
         const unsigned hmask = 0xffffu << (tid & 16);
         for (int i = tid >> 4; i < NBIG; i += kDecideThreads / 16) {
             if (!summed(i) || !(s_fl[i] & kRuleEvaluated)) continue;  // the same for the 16 lanes
+            if (!in_range(b.status, s_slot[i], b.cap[C::DMAX - depth_of(i, C::DMAX)])) continue;
             const unsigned int *sum = b.sums[C::DMAX - depth_of(i, C::DMAX)] + static_cast<long>(s_slot[i]) * (K * K);
             unsigned long long best = ~0ull;
             for (int k = hl; k < K * K; k += 16) {
@@ -1121,7 +1142,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_dep_decide(const __grid_cons
     for (int i = tid; i < C::NKEY; i += kDecideThreads)
         const_cast<unsigned long long *>(keys)[i] = ~0ull;
     dev::DecideIO io{a.cur, a.ref, a.pitch_bytes, &rinf.g, a.qp, b.satd_mode, c_lambda_q16,
-                     decisions_at(a.block, rinf.off)};
+                     decisions_at(a.block, rinf.off), b.status};
     dev::ctu_decide<T, CTU>(st, io, x0, y0);
 }
 

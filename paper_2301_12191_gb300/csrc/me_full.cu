@@ -226,7 +226,8 @@ __device__ __forceinline__ void decide_ctu(const FullSearchBatch &b, const FullS
         }
     }
     __syncthreads();
-    dev::DecideIO io{a.cur, a.ref, a.pitch_bytes, &g, a.qp, b.satd_mode, c_lambda_q16, decisions_at(a.block, ri.off)};
+    dev::DecideIO io{a.cur, a.ref, a.pitch_bytes, &g, a.qp, b.satd_mode, c_lambda_q16, decisions_at(a.block, ri.off),
+                     b.status};
     dev::ctu_decide<T, CTU>(st, io, x0, y0);
 }
 
@@ -373,6 +374,14 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
             code[i] = static_cast<uint32_t>((abs(dx) + abs(dy)) * 2 * K + 2 * (dy + R) + (dx > 0));
         }
         const uint32_t *lp = E + (dy0 + R - rlo + qy) * P4 + (dx + b.Rp + qx);
+        // debug builds: the lane's first and last window words lie in the
+        // staged window (else it reads from the window's origin: the failure
+        // is recorded; the CTA's barriers below still run)
+        if (!in_range(b.status, (dy0 + R - rlo + qy) * P4 + (dx + b.Rp + qx), b.e_bytes / 4) ||
+            !in_range(b.status, (dy0 + R - rlo + qy + S::Q - 8 + NR - 1) * P4 + (dx + b.Rp + qx + S::Q - 8) +
+                                    (ES == 1 ? 4 : 6),
+                      b.e_bytes / 4))
+            lp = E;
         uint32_t s16[TY], s32[TY];
     #pragma unroll
         for (int i = 0; i < TY; ++i) {
@@ -528,6 +537,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
 
     // Re-encode (SAD << 16 | code) as (SAD << 32 | tie-break) and merge.
     unsigned long long *out = a.keys + static_cast<long>(ctu_idx) * S::NKEY;
+    const long nkeys = static_cast<long>(ctu_cols) * ((H8 + CTU - 1) / CTU) * S::NKEY;  // the frame's keys
     constexpr int NUP = keys_per_ctu(S::DMAX - 1);
     for (int i = tid; i < S::NKEY; i += NT) {
         const unsigned long long v = i < NUP ? s_kup[i] : static_cast<unsigned long long>(s_k8[i - NUP]);
@@ -539,7 +549,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
         const int adx = l1 - abs(dyv);
         const int dxv = (rem & 1) ? adx : -adx;
         const uint32_t tb = static_cast<uint32_t>(l1 * K * K + (dyv + R) * K + (dxv + R));
-        atomicMin(out + i, (static_cast<unsigned long long>(sad) << 32) | tb);
+        if (in_range(b.status, static_cast<long>(ctu_idx) * S::NKEY + i, nkeys))
+            atomicMin(out + i, (static_cast<unsigned long long>(sad) << 32) | tb);
     }
     if (b.fuse_decide) {
         // the last CTA of this CTU to finish takes its decisions

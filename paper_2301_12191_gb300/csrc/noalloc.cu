@@ -70,7 +70,8 @@ extern "C" ladder_status analyze_reference_noalloc_status(void *cuda_stream)
         cudaGetLastError();
         return LADDER_E_CUDA;
     }
-    return status == kStatusOk ? LADDER_OK : LADDER_E_TIMEOUT;
+    if (status == kStatusOk) return LADDER_OK;
+    return status == kStatusBounds ? LADDER_E_BOUNDS : LADDER_E_TIMEOUT;
 }
 
 extern "C" ladder_status analyze_reference_noalloc(const void *cur, const void *ref, int width, int height,
@@ -164,6 +165,7 @@ extern "C" ladder_status analyze_reference_noalloc(const void *cur, const void *
         db.range = search_range;
         db.satd_mode = satd_mode;
         db.total_ctas = nctus;
+        db.status = d_status;
         RungInfo &ri = db.rung[0];
         ri.g = g;
         for (int d = 0; d <= g.dmax; ++d) {

@@ -21,7 +21,8 @@ from . import build as _build
 
 MAX_DEPTHS = 4
 STATUS = {0: "LADDER_OK", -1: "LADDER_E_INVAL", -2: "LADDER_E_NOMEM", -3: "LADDER_E_NOREF",
-          -4: "LADDER_E_BUSY", -5: "LADDER_E_CUDA", -6: "LADDER_E_TIMEOUT", -7: "LADDER_E_STATE"}
+          -4: "LADDER_E_BUSY", -5: "LADDER_E_CUDA", -6: "LADDER_E_TIMEOUT", -7: "LADDER_E_STATE",
+          -8: "LADDER_E_BOUNDS"}
 
 
 class LadderError(RuntimeError):
@@ -107,6 +108,8 @@ SIGNATURES = [
     ("fetch_decisions", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Decisions),
                                        ctypes.c_void_p]),
     ("ladder_set_parents", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    ("ladder_load_reference", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Decisions),
+                                             ctypes.c_void_p]),
     ("ladder_set_mv_predictor", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("ladder_refine_subpel", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_long, ctypes.c_int,
@@ -158,21 +161,29 @@ DEBUG_CONTROLS = {"wait_polls": 0, "lost_handoff": 1}
 _lib = None
 
 
+def debug_build_requested() -> bool:
+    """LADDER_DEBUG_BUILD=1 in the environment selects the bounds-checked
+    debug build of the library (libladder_debug.so) for this process."""
+    return os.environ.get("LADDER_DEBUG_BUILD", "0") not in ("", "0")
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if debug_build_requested() else _build.LIB
 
 
 def load(build_if_missing: bool = True):
-    """Loads libladder.so (building it first when it is missing or stale and
-    nvcc is available); raises if it cannot be loaded."""
+    """Loads libladder.so, or libladder_debug.so when LADDER_DEBUG_BUILD=1
+    (building it first when it is missing or stale and nvcc is available);
+    raises if it cannot be loaded."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
-    if build_if_missing and _build.stale():
-        _build.build()
+    debug = debug_build_requested()
+    path = library_path()
+    if build_if_missing and _build.stale(debug=debug):
+        _build.build(debug=debug)
     if not os.path.exists(path):
-        raise OSError(f"libladder.so not found at {path}; run __graft_entry__.build()")
+        raise OSError(f"{os.path.basename(path)} not found at {path}; run __graft_entry__.build()")
     lib = ctypes.CDLL(path)
     for name, res, args in SIGNATURES:
         fn = getattr(lib, name)
@@ -669,6 +680,29 @@ class Ladder:
         `host` (a pinned uint8 tensor of frame_bytes() bytes) on `stream`;
         does not wait."""
         _call(self.handle, "ladder_fetch_frame_async", self.handle, frame_id, host.data_ptr(), host.numel(),
+              _stream_handle(stream))
+
+    def load_reference(self, frame_id, saved: dict, stream=None):
+        """Makes a reference analysis saved by fetch() (the reference rung's
+        arrays) the resident reference of frame_id (ladder_load_reference)."""
+        dims, (c8, r8) = self.grid(self.ref_rung)
+        dec = Decisions()
+        keep = []
+        for d in range(len(dims)):
+            for k, dt in (("mvx", np.int16), ("mvy", np.int16), ("sad", np.int32), ("satd", np.int32),
+                          ("cost", np.int32), ("best", np.int32), ("split", np.uint8), ("evaluated", np.uint8)):
+                a = np.ascontiguousarray(saved[k][d], dtype=dt)
+                if a.size != dims[d][0] * dims[d][1]:
+                    raise ValueError(f"{k}[{d}] has {a.size} entries, the grid {dims[d]}")
+                keep.append(a)
+                getattr(dec, k)[d] = a.ctypes.data
+        for k, dt in (("leaf_depth", np.uint8), ("leaf_mvx", np.int16), ("leaf_mvy", np.int16)):
+            a = np.ascontiguousarray(saved[k], dtype=dt)
+            if a.size != c8 * r8:
+                raise ValueError(f"{k} has {a.size} entries, the 8x8 grid {c8}x{r8}")
+            keep.append(a)
+            setattr(dec, k, a.ctypes.data)
+        _call(self.handle, "ladder_load_reference", self.handle, int(frame_id), ctypes.byref(dec),
               _stream_handle(stream))
 
     def fetch(self, rung, frame_id, stream=None) -> dict:

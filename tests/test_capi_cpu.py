@@ -111,3 +111,19 @@ def test_null_handles_are_refused_without_touching_a_device():
     assert lib.ladder_pipeline_wait(None, 0) == E_INVAL
     lib.ladder_pipeline_destroy(None)
     lib.ladder_destroy(None)
+
+
+def test_debug_build_compiles_the_bounds_checks_in():
+    """libladder_debug.so (the same sources with LADDER_BOUNDS_CHECK=1) says
+    so in its version string and exports every symbol the header declares."""
+    import ctypes
+    from paper_2301_12191_gb300 import build as B
+    B.build(debug=True)
+    lib = ctypes.CDLL(B.LIB_DEBUG)
+    lib.ladder_version.restype = ctypes.c_char_p
+    assert b"bounds-checked" in lib.ladder_version()
+    rel = ctypes.CDLL(B.LIB)
+    rel.ladder_version.restype = ctypes.c_char_p
+    assert b"bounds-checked" not in rel.ladder_version()
+    for name in _declared_functions():
+        getattr(lib, name)
