@@ -501,10 +501,7 @@ def run_ours(args, wl, name, ctx, extra=False):
     # level only (the SAD tree gets 16/32/64 for free); a dependent rung
     # searches every evaluated CU separately.
     step_multi(0)
-    if extra:
-        tuning = {"knobs": lad.tuning(), "tuned": False}
-    else:
-        tuning = autotune(args, lad, lambda: step_multi(0), "frames1", stream)
+    tuning = autotune(args, lad, lambda: step_multi(0), "frames1", stream)
     evals_ref = full_evals(*sizes[ref_i], wl["R"])
     evals_dep = 0
     for i in range(n_rungs):
@@ -1111,7 +1108,7 @@ def summary_of(res):
     """The core figures of a workload measured beside the main line."""
     keep = ("value", "unit", "ms_per_step", "dtype", "config", "serial", "independent",
             "multires_speedup_vs_independent", "e2e", "roofline", "path_roofline", "gpu_launches", "kernels",
-            "clocks")
+            "clocks", "setup")
     return {k: res[k] for k in keep if k in res}
 
 
