@@ -798,7 +798,11 @@ __device__ __forceinline__ void stage_slots_setup(const DependentBatch &b, const
 // Issues the async copies of every 16-byte chunk of the tile's raw0 and
 // current rows that lies inside its frame (rows clamped into the frame);
 // chunks outside are left to the fix-up.  A thread takes one column of
-// chunks (slot, chunk, a quarter of the rows) and walks its rows.
+// chunks (slot, chunk, every fourth row from its row group) and walks its
+// rows.  Interleaved rows put the four row groups of a chunk column
+// RW, 2 RW and 3 RW words apart, in different banks for the row pitches
+// the shapes give (a contiguous quarter of the rows each would put them a
+// multiple of 32 words apart: four-way bank conflicts).
 constexpr int kStageRowGroups = 4;
 
 __device__ __forceinline__ void stage_copy(const StageTile &t, const StageSlots &ss, uint32_t *buf,
@@ -817,14 +821,12 @@ __device__ __forceinline__ void stage_copy(const StageTile &t, const StageSlots 
         const int x = ref ? ss.ax[slot] + 8 * ch : ss.cux[slot] + 8 * (ch - sh.NC);
         if (x < 0 || x >= W) continue;  // x is a multiple of 8: a chunk that starts in the row ends in its pitch
         const int rows = ref ? sh.WR : t.RS;
-        const int per = (rows + kStageRowGroups - 1) / kStageRowGroups, row0 = grp * per;
-        const int nrows = min(per, rows - row0);
-        const int y0 = (ref ? ss.wy0[slot] : ss.cuy[slot]) + row0;
+        const int y0 = (ref ? ss.wy0[slot] : ss.cuy[slot]) + grp;
         const char *src = (ref ? ss.ref[slot] : ss.cur[slot]) + 2 * static_cast<long>(x);
         const int stride = ref ? sh.RW : sh.CW;
-        uint32_t *dst = buf + slot * sh.PW + (ref ? 0 : sh.OC) + row0 * stride + 4 * (ref ? ch : ch - sh.NC);
+        uint32_t *dst = buf + slot * sh.PW + (ref ? 0 : sh.OC) + grp * stride + 4 * (ref ? ch : ch - sh.NC);
 #pragma unroll 1
-        for (int i = 0; i < nrows; ++i, dst += stride)
+        for (int i = 0; grp + i < rows; i += kStageRowGroups, dst += kStageRowGroups * stride)
             cp_async16(dst, src + static_cast<long>(min(max(y0 + i, 0), H - 1)) * pitch);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -865,23 +867,23 @@ __device__ __forceinline__ void stage_fixup(const StageTile &t, const StageSlots
 }
 
 // raw1: every raw row shifted by one sample, four words at a time; a
-// thread takes one column (slot, four words, a quarter of the rows).
+// thread takes one column (slot, four words, every fourth row from its row
+// group, as in the copies).
 __device__ __forceinline__ void stage_raw1(const StageTile &t, uint32_t *buf, const FastDiv &div_c1)
 {
     const StageShape &sh = t.sh;
     const int cps = kStageRowGroups * sh.NC;
-    const int per = (sh.WR + kStageRowGroups - 1) / kStageRowGroups;
 #pragma unroll 1
     for (int col = threadIdx.x; col < t.nslots * cps; col += kStageThreads) {
         const int slot = static_cast<int>(fast_div(static_cast<uint32_t>(col), div_c1));
         const int k = col - slot * cps;
-        const int grp = k / kStageRowGroups, row0 = (k & (kStageRowGroups - 1)) * per;
-        const int nrows = min(per, sh.WR - row0);
+        const int grp = k / kStageRowGroups, row0 = k & (kStageRowGroups - 1);
         const bool last = grp + 1 >= sh.NC;  // the row's last word: never read shifted
         const uint32_t *src = buf + slot * sh.PW + row0 * sh.RW + 4 * grp;
         uint32_t *dst = buf + slot * sh.PW + sh.O1 + row0 * sh.RW + 4 * grp;
+        const int step = kStageRowGroups * sh.RW;
 #pragma unroll 1
-        for (int i = 0; i < nrows; ++i, src += sh.RW, dst += sh.RW) {
+        for (int i = row0; i < sh.WR; i += kStageRowGroups, src += step, dst += step) {
             const uint4 a4 = *reinterpret_cast<const uint4 *>(src);
             const uint32_t e = last ? 0u : src[4];
             uint4 o;
@@ -998,8 +1000,10 @@ __device__ __forceinline__ void stage_compute(const DependentBatch &b, const Sta
 // filling one while the current tile is computed from the other; 0: one
 // buffer (less shared memory: more CTAs per SM overlap one another's
 // staging instead).  `half`: words of one buffer.
+// Four CTAs per SM (at most 128 registers a thread): with fewer, the
+// staging of one CTA's tile is not hidden behind the others' compute.
 template <int TY>
-__global__ void __launch_bounds__(kStageThreads, 2)
+__global__ void __launch_bounds__(kStageThreads, 4)
     k_dep_search_st16(const __grid_constant__ DependentBatch b, const FastDiv div_cu, const FastDiv div_k,
                       const __grid_constant__ StageDivs dv, int half, int pipelined)
 {

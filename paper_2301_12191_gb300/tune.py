@@ -14,7 +14,11 @@ tiles, a batch of 32 frames has plenty.
 `tune()` times a caller-supplied step (one batch of the real workload) for
 each candidate setting by coordinate descent: knobs are tried one at a time,
 each against the best values found so far, and a knob keeps its new value
-only if the step gets faster by more than the noise margin.  Each timing is
+only if the step gets faster by more than the noise margin.  The dependent
+search's piece size and band height are tried jointly (every pair): the
+best band depends on the piece size through the shared memory a tile
+needs, so one knob at a time can stop at a pair that is worse than one it
+never tried.  Each timing is
 the median of `reps` runs bracketed by CUDA events on the step's stream.
 Results are cached in a JSON file keyed by the device name and a
 caller-chosen workload key, so a later run with the same shape only applies
@@ -31,13 +35,23 @@ SPACE = {
     "fs_band": (13, 9),
     "fs_group": (0, 1, 2, 3),
     "fs_fuse": (1, 0),
-    "dep_range": (16, 32),
-    "dep_band": (0, 17, 9),
+    ("dep_range", "dep_band"): tuple((rg, bd) for rg in (16, 32) for bd in (0, 17, 9)),
     "dep_ctas_per_sm": (0, 1, 2),
     "dep_staged": (1, 2, 0),
 }
 DEFAULTS = {"fs_band": 13, "fs_group": 0, "fs_fuse": 1, "dep_range": 16, "dep_band": 0, "dep_ctas_per_sm": 0,
             "dep_staged": 1}
+
+
+def knob_values(name: str) -> tuple:
+    """Every value the search may give knob `name` (alone or in a joint pair)."""
+    for key, values in SPACE.items():
+        if key == name:
+            return tuple(values)
+        if isinstance(key, tuple) and name in key:
+            i = key.index(name)
+            return tuple(sorted({v[i] for v in values}))
+    raise KeyError(name)
 
 
 def default_cache_path() -> str:
@@ -121,10 +135,12 @@ def tune(ladder, run_step, *, tag: str, stream=None, space=None, reps=5, warmup=
     best_ms = timer(run_step)
     trials = [(dict(best), best_ms)]
     for name, values in space.items():
+        names = name if isinstance(name, tuple) else (name,)
         for v in values:
-            if v == best[name]:
+            v = v if isinstance(name, tuple) else (v,)
+            if all(best[n] == x for n, x in zip(names, v)):
                 continue
-            cand = dict(best, **{name: v})
+            cand = dict(best, **dict(zip(names, v)))
             try:
                 ladder.set_tuning(**cand)
             except LadderError:

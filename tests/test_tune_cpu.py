@@ -40,7 +40,9 @@ def test_coordinate_descent_and_cache(tmp_path):
                             "dep_ctas_per_sm": 0, "dep_staged": 1}
     assert res["ms"] == pytest.approx(7.0)
     assert lad.knobs == res["knobs"] and not res["cached"]
-    assert len(res["trials"]) == 1 + 1 + 3 + 1 + 1 + 2 + 2 + 2
+    # baseline, fs_band, fs_group, fs_fuse, the five other (piece size, band)
+    # pairs, grid size, staging
+    assert len(res["trials"]) == 1 + 1 + 3 + 1 + 5 + 2 + 2
     # the cache answers the same workload key without timing anything
     lad2 = FakeLadder()
     res2 = tune.tune(lad2, None, tag="t1", timer=lambda fn: pytest.fail("timed"), device="fake", cache_path=path)
@@ -61,3 +63,18 @@ def test_invalid_shapes_are_skipped(tmp_path):
 def test_workload_key_names_the_geometry():
     key = tune.workload_key(FakeLadder(), "frames32")
     assert "bd8" in key and "R32" in key and "1280x720" in key and key.endswith("frames32")
+
+
+def test_piece_size_and_band_are_tried_jointly(tmp_path):
+    # pieces of 32 help at the default band, but the best pair is pieces of
+    # 16 with bands of 17 (pieces of 32 with bands of 17 do not fit): one
+    # knob at a time would keep (32, 0)
+    def pair_cost(knobs):
+        return {(16, 0): 10.0, (32, 0): 9.0, (16, 17): 8.0, (32, 17): 12.0,
+                (16, 9): 10.0, (32, 9): 9.0}[(knobs["dep_range"], knobs["dep_band"])]
+
+    lad = FakeLadder()
+    res = tune.tune(lad, None, tag="pairs", timer=lambda fn: pair_cost(lad.knobs), device="fake",
+                    cache_path=str(tmp_path / "cache.json"), use_cache=False)
+    assert (res["knobs"]["dep_range"], res["knobs"]["dep_band"]) == (16, 17)
+    assert res["ms"] == pytest.approx(8.0)
