@@ -1066,7 +1066,7 @@ __global__ void __launch_bounds__(kStageThreads, 4)
 
 // ---- 3. decide --------------------------------------------------------------
 template <typename T, int CTU>
-__global__ void __launch_bounds__(kDecideThreads) k_dep_decide(const __grid_constant__ DependentBatch b)
+__global__ void __launch_bounds__(kDecideThreads, 4) k_dep_decide(const __grid_constant__ DependentBatch b)
 {
     dev::chain_entry();
     // the search has completed: its task counters go back to zero for the
@@ -1100,21 +1100,36 @@ __global__ void __launch_bounds__(kDecideThreads) k_dep_decide(const __grid_cons
     }
     __syncthreads();
     // CUs searched in pieces: argmin of (SAD, |dx|+|dy|, dy, dx) over the
-    // CU's sum table, 16 lanes per CU
+    // CU's sum table, 16 lanes per CU.  A lane loads kScanBatch entries
+    // before it uses any (one L2 round trip per batch, two for r = 8).
     auto summed = [&](int i) { return i < NBIG && s_slot[i] >= 0 && (CTU >> depth_of(i, C::DMAX)) > b.range; };
     {
+        constexpr int kScanBatch = 10;
         const int hl = tid & 15;
         const unsigned hmask = 0xffffu << (tid & 16);
+        const int KK = K * K;
+        // candidate row of entry k: (k + 1/2) / K in fp32 is at least 1/(2K)
+        // from an integer for k < 2^16, so the truncation is exact
+        const float inv_k = 1.0f / static_cast<float>(K);
         for (int i = tid >> 4; i < NBIG; i += kDecideThreads / 16) {
             if (!summed(i) || !(s_fl[i] & kRuleEvaluated)) continue;  // the same for the 16 lanes
             if (!in_range(b.status, s_slot[i], b.cap[C::DMAX - depth_of(i, C::DMAX)])) continue;
-            const unsigned int *sum = b.sums[C::DMAX - depth_of(i, C::DMAX)] + static_cast<long>(s_slot[i]) * (K * K);
+            const unsigned int *sum = b.sums[C::DMAX - depth_of(i, C::DMAX)] + static_cast<long>(s_slot[i]) * KK;
             unsigned long long best = ~0ull;
-            for (int k = hl; k < K * K; k += 16) {
-                const int dxo = k % K - r, dyo = k / K - r;
-                const uint32_t tb = static_cast<uint32_t>((abs(dxo) + abs(dyo)) * K * K + k);
-                const unsigned long long key = (static_cast<unsigned long long>(__ldcg(sum + k)) << 32) | tb;
-                best = key < best ? key : best;
+            for (int k0 = hl; k0 < KK; k0 += 16 * kScanBatch) {
+                unsigned int v[kScanBatch];
+#pragma unroll
+                for (int u = 0; u < kScanBatch; ++u) v[u] = k0 + 16 * u < KK ? __ldcg(sum + k0 + 16 * u) : 0u;
+#pragma unroll
+                for (int u = 0; u < kScanBatch; ++u) {
+                    const int k = k0 + 16 * u;
+                    if (k >= KK) break;
+                    const int dy = static_cast<int>((static_cast<float>(k) + 0.5f) * inv_k);
+                    const int dxo = k - dy * K - r, dyo = dy - r;
+                    const uint32_t tb = static_cast<uint32_t>((abs(dxo) + abs(dyo)) * KK + k);
+                    const unsigned long long key = (static_cast<unsigned long long>(v[u]) << 32) | tb;
+                    best = key < best ? key : best;
+                }
             }
 #pragma unroll
             for (int o = 8; o >= 1; o >>= 1) {
