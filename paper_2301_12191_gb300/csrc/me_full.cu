@@ -231,8 +231,10 @@ __device__ __forceinline__ void decide_ctu(const FullSearchBatch &b, const FullS
     dev::ctu_decide<T, CTU>(st, io, x0, y0);
 }
 
+// 8-bit: four CTAs per SM; 10-bit: three (at most 168 registers), which
+// the shared memory of bands of 9 with two warp tiles per CTA allows
 template <typename T, int CTU, int RP, int BAND>
-__global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(const __grid_constant__ FullSearchBatch b)
+__global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 3) k_full_search(const __grid_constant__ FullSearchBatch b)
 {
     using S = Shape<T, CTU, RP, BAND>;
     constexpr int TY = S::TY, P4 = S::P4, ES = S::ES, NT = S::NT;
@@ -514,21 +516,21 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 2) k_full_search(con
         }
         if constexpr (S::Q >= 32) key32();
 
-        // CTU level: the four quadrants' sums (warp 0 has read the previous
-        // tile's exchange once every warp passes the first barrier)
+        // CTU level: the four quadrants' sums; warps 1-3 pass theirs to warp
+        // 0 (which has read the previous tile's exchange once every warp
+        // passes the first barrier)
         __syncthreads();
-        {
-            const uint32_t(&top)[TY] = (S::Q >= 16) ? s32 : s16;
+        const uint32_t(&top)[TY] = (S::Q >= 16) ? s32 : s16;
+        if (warp > 0) {
     #pragma unroll
-            for (int i = 0; i < TY; ++i) s_xch[(warp * TY + i) * 32 + lane] = top[i];
+            for (int i = 0; i < TY; ++i) s_xch[((warp - 1) * TY + i) * 32 + lane] = top[i];
         }
         __syncthreads();
         if (warp == 0) {
             uint32_t tot[TY];
     #pragma unroll
             for (int i = 0; i < TY; ++i)
-                tot[i] = s_xch[i * 32 + lane] + s_xch[(TY + i) * 32 + lane] + s_xch[(2 * TY + i) * 32 + lane] +
-                         s_xch[(3 * TY + i) * 32 + lane];
+                tot[i] = top[i] + s_xch[i * 32 + lane] + s_xch[(TY + i) * 32 + lane] + s_xch[(2 * TY + i) * 32 + lane];
             const unsigned long long key = warp_min_u64(lane_key64<TY>(tot, code, m16, all_valid, dy0, R));
             if (lane == 0) atomicMin(&s_kup[0], key);
         }
@@ -601,7 +603,7 @@ cudaError_t launch_t(const FullSearchBatch &b, int smem, cudaStream_t s)
     cudaError_t e = ensure_smem<T, CTU, RP, BAND>(smem);
     if (e != cudaSuccess) return e;
     const int n2 = (b.box_h - std::min(b.phase1_rows, b.box_h)) * S::CPR;
-    if (n2 > S::MAXC * S::NT || b.box_h > S::MAX_ROWS || 4 * S::TY * 32 * 4 > b.e_bytes) return cudaErrorInvalidValue;
+    if (n2 > S::MAXC * S::NT || b.box_h > S::MAX_ROWS || 3 * S::TY * 32 * 4 > b.e_bytes) return cudaErrorInvalidValue;
     return launch_chained(k_full_search<T, CTU, RP, BAND>, dim3(b.total), dim3(S::NT), smem, s, b);
 }
 
@@ -686,7 +688,7 @@ FullSearchPlan full_search_plan(int bit_depth, int ctu, int R, int band, int gro
     p.phase1_rows = p.stage_off / (4 * p.P4);
     const int cur_bytes = ctu * ctu * es;
     const int a8_bytes = es == 2 ? (ctu / 8) * (ctu / 8) * 4 : 0;
-    const int xch_bytes = group > 1 ? 4 * band * 32 * 4 : 0;  // else the exchange reuses the window
+    const int xch_bytes = group > 1 ? 3 * band * 32 * 4 : 0;  // else the exchange reuses the window
     p.buf_bytes = (p.e_bytes + cur_bytes + a8_bytes + xch_bytes + 127) / 128 * 128;
     p.smem_bytes = p.buf_bytes + 128;  // + alignment slack
     return p;
