@@ -248,13 +248,16 @@ def derive_rule(dep_size, dep: dict, d: int, x0: int, y0: int, ctu: int = 64):
 
 
 def refine_subpel(cur, ref, analysis: dict, *, qp: int, ctu: int = 64, satd_mode: int = 0,
-                  dep: dict | None = None, threads: int | None = None) -> dict:
+                  dep: dict | None = None, threads: int | None = None, mvp: int = 0) -> dict:
     """Quarter-pel refinement of an analysis of the same frame pair (as
-    returned by analyze() with the same qp / ctu / satd_mode / dep): per
-    depth ``qmvx, qmvy`` (quarter-pel units), ``satd``, ``cost``, ``best``,
-    ``split``, and per 8x8 ``leaf_depth, leaf_qmvx, leaf_qmvy``."""
+    returned by analyze() with the same qp / ctu / satd_mode / dep / mvp):
+    per depth ``qmvx, qmvy`` (quarter-pel units), ``satd``, ``cost``,
+    ``best``, ``split``, and per 8x8 ``leaf_depth, leaf_qmvx, leaf_qmvy``.
+    ``mvp=1``: the rate term of every candidate takes the spatial predictor
+    formed from the refined quarter-pel leaf vectors of the earlier CTUs."""
     lib = _load()
     job, keep = _make_job(cur, ref, qp, ctu, 0, satd_mode, dep)
+    job.mvp = int(mvp)
     dims, (c8, r8) = grid(job.width, job.height, ctu)
     dec = _Decisions()
     for d in range(len(dims)):

@@ -618,12 +618,14 @@ typedef struct {
 
 static int grid_cols_s(const subpel_ctx *c, int d) { int S = c->job->ctu >> d; return (c->W8 + S - 1) / S; }
 
-/* The two rounds of one evaluated CU, from its integer vector and SATD. */
-static void subpel_search(const oracle_job *j, int x0, int y0, int S, int mvx, int mvy, int32_t satd0,
-                          int *oqx, int *oqy, int32_t *osatd, int32_t *oj)
+/* The two rounds of one evaluated CU, from its integer vector and SATD;
+ * (pqx, pqy): the predictor of the rate term, quarter-pel units ((0, 0)
+ * unless the spatial predictor is on). */
+static void subpel_search(const oracle_job *j, int x0, int y0, int S, int mvx, int mvy, int32_t satd0, int pqx,
+                          int pqy, int *oqx, int *oqy, int32_t *osatd, int32_t *oj)
 {
     int bx = 4 * mvx, by = 4 * mvy;
-    int32_t bs = satd0, bj = rd_cost_q(satd0, j->qp, bx, by);
+    int32_t bs = satd0, bj = rd_cost_q(satd0, j->qp, bx - pqx, by - pqy);
     for (int step = 2; step >= 1; step--) {
         int cx = bx, cy = by;
         for (int dy = -1; dy <= 1; dy++)
@@ -631,7 +633,7 @@ static void subpel_search(const oracle_job *j, int x0, int y0, int S, int mvx, i
                 if (!dx && !dy) continue;
                 int qx = cx + step * dx, qy = cy + step * dy;
                 int32_t s = block_satd_q(j, x0, y0, S, qx, qy);
-                int32_t J = rd_cost_q(s, j->qp, qx, qy);
+                int32_t J = rd_cost_q(s, j->qp, qx - pqx, qy - pqy);
                 if (J < bj) { bj = J; bs = s; bx = qx; by = qy; }
             }
     }
@@ -651,9 +653,14 @@ static int32_t refine_cu(subpel_ctx *c, int d, int x0, int y0, int reachable)
     int evaluated = c->in->evaluated[d][idx];
     int32_t J = INT32_MAX;
     if (evaluated) {
-        int qx, qy;
+        int qx, qy, pqx = 0, pqy = 0;
         int32_t s;
-        subpel_search(j, x0, y0, S, c->in->mvx[d][idx], c->in->mvy[d][idx], c->in->satd[d][idx], &qx, &qy, &s, &J);
+        /* spatial predictor: the median of the refined quarter-pel leaf
+         * vectors of the earlier CTUs, read as the integer analysis reads
+         * its leaf vectors */
+        if (j->mvp) spatial_mvp(j->ctu, c->W8, c->H8, o->leaf_qmvx, o->leaf_qmvy, x0, y0, S, &pqx, &pqy);
+        subpel_search(j, x0, y0, S, c->in->mvx[d][idx], c->in->mvy[d][idx], c->in->satd[d][idx], pqx, pqy, &qx,
+                      &qy, &s, &J);
         o->qmvx[d][idx] = (int16_t)qx;
         o->qmvy[d][idx] = (int16_t)qy;
         o->satd[d][idx] = s;
@@ -728,7 +735,11 @@ static void *refine_worker(void *arg)
 }
 
 /* Quarter-pel refinement of an analysis `in` of the same job (its integer
- * vectors, SATDs and evaluated flags); returns 0, or -1 on bad arguments. */
+ * vectors, SATDs and evaluated flags); returns 0, or -1 on bad arguments.
+ * With the spatial predictor (job->mvp) the rate term of every candidate
+ * takes the predictor of the integer analysis, formed from the refined
+ * quarter-pel leaf vectors, and the CTUs are refined one by one in raster
+ * order (every CTU a predictor reads is refined before the CU's CTU). */
 int oracle_refine_subpel(const oracle_job *job, const oracle_decisions *in, oracle_subpel *out, int threads)
 {
     if (!valid_job(job) || !in || !out) return -1;
@@ -743,7 +754,7 @@ int oracle_refine_subpel(const oracle_job *job, const oracle_decisions *in, orac
     c.ctu_cols = (c.W8 + job->ctu - 1) / job->ctu;
     c.ctu_rows = (c.H8 + job->ctu - 1) / job->ctu;
     pthread_mutex_init(&c.lock, NULL);
-    if (threads <= 1) {
+    if (threads <= 1 || job->mvp) {
         refine_worker(&c);
     } else {
         pthread_t *t = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)threads);

@@ -139,3 +139,127 @@ def test_refined_split_is_optimal_over_all_partitions():
     opts = _enumerate(J, 0, 0, 0, dmax)
     assert len(opts) == 17
     assert sp["best"][0][0] == min(opts)
+
+
+# -------------------------------------------- spatial predictor -----
+# The refinement with the spatial MV predictor, re-derived here from its
+# definition with Python's own arithmetic: the predictor of a CU is the
+# component-wise median of the refined quarter-pel leaf vectors at A1, B1,
+# B0 (available: inside the 8-aligned frame, outside the CU's CTU, in an
+# earlier CTU of the wavefront), every candidate's rate is taken against it,
+# and the two rounds (half-pel, then quarter-pel around the best so far)
+# keep the first strictly lower cost.  Only the quarter-pel SATD probe of the
+# oracle is reused (it is pinned by the filter and search cases above).
+def _py_se_bits(v):
+    k = 2 * v - 1 if v > 0 else -2 * v
+    return 2 * ((k + 1).bit_length() - 1) + 1
+
+
+def _py_lambda_q16(qp):
+    return math.floor(65536.0 * math.sqrt(0.57 * 2.0 ** ((qp - 12) / 3.0)) + 0.5)
+
+
+def _available(ctu, W8, H8, x0, y0, px, py):
+    if px < 0 or py < 0 or px >= W8 or py >= H8:
+        return False
+    cx, cy, qx, qy = x0 // ctu, y0 // ctu, px // ctu, py // ctu
+    if (qx, qy) == (cx, cy):
+        return False
+    if qy == cy:
+        return qx < cx
+    if qy == cy - 1:
+        return qx <= cx + 1
+    return qy < cy - 1
+
+
+def _py_predictor(sp, ctu, W8, H8, x0, y0, S):
+    cols8 = W8 // 8
+    vx, vy = [], []
+    for px, py in ((x0 - 1, y0 + S - 1), (x0 + S - 1, y0 - 1), (x0 + S, y0 - 1)):
+        if _available(ctu, W8, H8, x0, y0, px, py):
+            li = (py // 8) * cols8 + px // 8
+            vx.append(int(sp["leaf_qmvx"][li]))
+            vy.append(int(sp["leaf_qmvy"][li]))
+        else:
+            vx.append(0)
+            vy.append(0)
+    return sorted(vx)[1], sorted(vy)[1]
+
+
+def _py_two_rounds(cur, ref, x0, y0, S, mvx, mvy, satd0, qp, pqx, pqy):
+    lam = _py_lambda_q16(qp)
+
+    def cost(s, qx, qy):
+        return s + ((lam * (_py_se_bits(qx - pqx) + _py_se_bits(qy - pqy)) + 32768) >> 16)
+
+    bx, by, bs = 4 * mvx, 4 * mvy, satd0
+    bj = cost(satd0, bx, by)
+    for step in (2, 1):
+        cx, cy = bx, by
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if dx == 0 and dy == 0:
+                    continue
+                qx, qy = cx + step * dx, cy + step * dy
+                s = oracle.block_satd_q(cur, ref, x0, y0, S, qx, qy)
+                j = cost(s, qx, qy)
+                if j < bj:
+                    bx, by, bs, bj = qx, qy, s, j
+    return bx, by, bs, bj
+
+
+def _check_spatial_refinement(cur, ref, qp, ctu, R):
+    H, W = cur.shape
+    W8, H8 = (W + 7) // 8 * 8, (H + 7) // 8 * 8
+    ana = oracle.analyze(cur, ref, qp=qp, search_range=R, ctu=ctu, mvp=1)
+    sp = oracle.refine_subpel(cur, ref, ana, qp=qp, ctu=ctu, mvp=1)
+    dmax = int(math.log2(ctu // 8))
+    checked = 0
+    for d in range(dmax + 1):
+        S = ctu >> d
+        cols, rows = sp["grid"][d]
+        for i in np.flatnonzero(ana["evaluated"][d] == 1):
+            x0, y0 = (i % cols) * S, (i // cols) * S
+            pqx, pqy = _py_predictor(sp, ctu, W8, H8, x0, y0, S)
+            want = _py_two_rounds(cur, ref, x0, y0, S, int(ana["mvx"][d][i]), int(ana["mvy"][d][i]),
+                                  int(ana["satd"][d][i]), qp, pqx, pqy)
+            got = (int(sp["qmvx"][d][i]), int(sp["qmvy"][d][i]), int(sp["satd"][d][i]), int(sp["cost"][d][i]))
+            assert got == want, (d, i, got, want, (pqx, pqy))
+            checked += 1
+    # the split over the refined costs: best = min(J, children's best) where split
+    for d in range(dmax):
+        cols, rows = sp["grid"][d]
+        ccols = sp["grid"][d + 1][0]
+        for i in range(cols * rows):
+            x, y = i % cols, i // cols
+            kids = [(2 * y + (q >> 1)) * ccols + 2 * x + (q & 1) for q in range(4)]
+            if sp["split"][d][i]:
+                assert sp["best"][d][i] == sum(int(sp["best"][d + 1][k]) for k in kids)
+            elif ana["evaluated"][d][i]:
+                assert sp["best"][d][i] == sp["cost"][d][i]
+    return ana, sp, checked
+
+
+@pytest.mark.parametrize("bd,ctu,qp", [(8, 16, 37), (10, 32, 32)])
+def test_spatial_predictor_refinement_rederived(bd, ctu, qp):
+    fp = synth.frame_pair(71 + bd, 96, 64, bd, global_range=3, patch_range=5, patch_size=16, n_patches=2)
+    ana, sp, checked = _check_spatial_refinement(fp.cur, fp.ref, qp, ctu, 4)
+    assert checked >= 20
+    # not vacuous: the predictor moves some CU's refined vector or cost
+    sp0 = oracle.refine_subpel(fp.cur, fp.ref, ana, qp=qp, ctu=ctu, mvp=0)
+    assert any(not np.array_equal(sp["cost"][d], sp0["cost"][d]) for d in range(len(sp["grid"])))
+
+
+def test_spatial_refinement_of_the_first_ctu_has_no_predictor():
+    """CTU (0, 0) reads no available position: its refinement is the one with
+    the predictor (0, 0), whatever the later CTUs hold."""
+    fp = synth.frame_pair(75, 96, 64, 8, global_range=3, patch_range=5, patch_size=16, n_patches=2)
+    ana = oracle.analyze(fp.cur, fp.ref, qp=37, search_range=4, ctu=32, mvp=1)
+    sp1 = oracle.refine_subpel(fp.cur, fp.ref, ana, qp=37, ctu=32, mvp=1)
+    sp0 = oracle.refine_subpel(fp.cur, fp.ref, ana, qp=37, ctu=32, mvp=0)
+    for d in range(len(sp1["grid"])):
+        n = 1 << d
+        cols = sp1["grid"][d][0]
+        idx = [y * cols + x for y in range(n) for x in range(n)]
+        for k in ("qmvx", "qmvy", "satd", "cost", "best", "split"):
+            assert np.array_equal(sp1[k][d][idx], sp0[k][d][idx]), (k, d)
