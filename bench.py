@@ -605,6 +605,10 @@ def run_ours(args, wl, name, ctx, extra=False):
             timed(step_multi, 3, 0)
             st_mvp = lad.kernel_stats(reset=True)
             lad.profile(False)
+            # the quarter-pel refinement with the spatial predictor over the
+            # refined vectors (SATD tables, then a wavefront launch per frame)
+            subpel_mvp = measure_subpel(wl, lad, dplanes, n_dev, step_multi, step_pipe, pipe_streams, timed,
+                                        timed_pipe, max_over_ranks, ms_mvp, K, W, world)
             lad.set_mv_predictor(0)
             n_w, t_w = st_mvp.get("decide_mvp", (0, 0.0))
             mvp = {"launches_per_step": n_w // 3, "ms_per_step": ms_mvp / K,
@@ -612,6 +616,9 @@ def run_ours(args, wl, name, ctx, extra=False):
                    "wavefront_kernel_ms_per_step": t_w / 3 if n_w else None,
                    "ladder_frames_per_s": world * K / (ms_mvp * 1e-3),
                    "pipelined_ladder_frames_per_s": world * K / (ms_mvp_pipe * 1e-3)}
+            if subpel_mvp:
+                subpel_mvp["launches_per_step"] = 3  # interpolation, SATD tables, wavefront
+                mvp["subpel"] = subpel_mvp
 
     props = torch.cuda.get_device_properties(dev)
     clocks = clk.summary()

@@ -314,8 +314,9 @@ LADDER_API ladder_status ladder_set_parents(ladder_t *ladder, const int *parent)
  * ladder_sync).  Independent and dependent analyses both take it (a tier's
  * decisions are final before the next tier derives its rules from them);
  * ladder_decide_qps decides every further QP with it too (one wavefront
- * launch per QP, in order); ladder_refine_subpel and analyze_reference_noalloc
- * keep the predictor (0, 0).  LADDER_E_INVAL for another mode. */
+ * launch per QP, in order); ladder_refine_subpel takes it over the refined
+ * quarter-pel vectors (see there); analyze_reference_noalloc keeps the
+ * predictor (0, 0).  LADDER_E_INVAL for another mode. */
 LADDER_API ladder_status ladder_set_mv_predictor(ladder_t *ladder, int mode);
 
 /* Decisions of one analysed rung at further QPs (intra-resolution analysis
@@ -362,12 +363,23 @@ LADDER_API ladder_status ladder_decide_qps(ladder_t *ladder, int rung, int frame
  * laid out as the same fields of ladder_decisions, qmvx / qmvy in
  * quarter-pel units (INT16_MIN where not evaluated), satd / cost at the
  * refined vector; every member for depths 0..dmax must be set.
+ * With the spatial MV predictor on (ladder_set_mv_predictor mode 1) every
+ * candidate's rate, the integer start included, is taken against the
+ * predictor of the integer decisions formed from the REFINED quarter-pel
+ * leaf vectors: bits = se(qx - pqx) + se(qy - pqy), the CTUs refined in the
+ * wavefront order of WPP (Sec. 2.2).  The SATDs of the 48 quarter-pel
+ * positions within +-3 of 4 mv are computed first for every evaluated CU,
+ * then one more (cooperative) launch decides the CTUs row by row; a wait
+ * that runs out sets the device status to LADDER_E_TIMEOUT.  Refinements of
+ * one rung of one frame must be ordered (they share its hand-off words).
  * workspace: caller-owned DEVICE scratch of at least
  * ladder_subpel_workspace_bytes(ladder, rung) bytes, 256-byte aligned
  * (LADDER_E_INVAL otherwise), that receives the 16 interpolated phase planes
- * of ref; calls that share a workspace must be ordered (one stream).
- * Asynchronous on cuda_stream (two launches: interpolation, refinement);
- * LADDER_E_STATE if the rung of frame_id has not been analysed. */
+ * of ref (and the SATD table of the spatial-predictor refinement); calls
+ * that share a workspace must be ordered (one stream).  Asynchronous on
+ * cuda_stream (two launches: interpolation, refinement; three with the
+ * spatial predictor); LADDER_E_STATE if the rung of frame_id has not been
+ * analysed. */
 typedef struct {
     int16_t *qmvx[LADDER_MAX_DEPTHS], *qmvy[LADDER_MAX_DEPTHS];
     int32_t *satd[LADDER_MAX_DEPTHS], *cost[LADDER_MAX_DEPTHS], *best[LADDER_MAX_DEPTHS];
@@ -377,7 +389,9 @@ typedef struct {
 } ladder_subpel_decisions;
 /* Bytes of the workspace ladder_refine_subpel needs for `rung`: 16 planes
  * of (W + 8) x (H + 8) samples, the positions -4 .. W+3 by -4 .. H+3 of each
- * quarter-pel phase (0 for a bad handle or rung). */
+ * quarter-pel phase, then 48 int32 SATDs per CU key of every CTU (the
+ * spatial-predictor refinement's table; counted in either mode) (0 for a bad
+ * handle or rung). */
 LADDER_API long ladder_subpel_workspace_bytes(const ladder_t *ladder, int rung);
 LADDER_API ladder_status ladder_refine_subpel(ladder_t *ladder, int rung, int frame_id, const void *cur,
                                               const void *ref, long pitch_bytes, int qp,

@@ -328,6 +328,50 @@ __device__ __forceinline__ int key_of_block(int d, int bx, int by)
     return key_index(d, ((by >> sh) << d) + (bx >> sh));
 }
 
+// ---- wavefront hand-off (the spatial MV predictor's CTU order) ----------------
+// Words a CTU row publishes for the row below (generation << 32 | packed
+// vector), relaxed 64-bit loads and stores, and the median of the three
+// predictor candidates.
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_release32(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int median3(int a, int b, int c) { return max(min(a, b), min(max(a, b), c)); }
+
+__device__ __forceinline__ uint32_t pack_mv(int mvx, int mvy)
+{
+    return static_cast<uint32_t>(static_cast<uint16_t>(mvx)) | (static_cast<uint32_t>(static_cast<uint16_t>(mvy)) << 16);
+}
+__device__ __forceinline__ int mv_x(uint32_t v) { return static_cast<int16_t>(v & 0xffffu); }
+__device__ __forceinline__ int mv_y(uint32_t v) { return static_cast<int16_t>(v >> 16); }
+
+// Leaf vector of 8x8 block (bx, by) of the CTU in st (split flags decided).
+template <int CTU>
+__device__ __forceinline__ uint32_t leaf_mv(const CtuState<CTU> &st, int bx, int by)
+{
+    using C = Ctu<CTU>;
+    int d = 0, i = 0;
+    for (;;) {
+        i = key_of_block<CTU>(d, bx, by);
+        if (d == C::DMAX || !st.split[i]) break;
+        ++d;
+    }
+    return pack_mv(st.mvx[i], st.mvy[i]);
+}
+
 // What ctu_split writes besides cost, best, split and the leaf maps.
 enum : int {
     kSplitWriteVectors = 1,  // mvx, mvy and SATD per CU

@@ -129,52 +129,11 @@ __global__ void __launch_bounds__(kThreads) k_decide_qps(const __grid_constant__
 
 constexpr int kMvpThreads = 128;
 
-__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ void st_release32(unsigned *p, unsigned v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ int median3(int a, int b, int c) { return max(min(a, b), min(max(a, b), c)); }
-
-__device__ __forceinline__ uint32_t pack_mv(int mvx, int mvy)
-{
-    return static_cast<uint32_t>(static_cast<uint16_t>(mvx)) | (static_cast<uint32_t>(static_cast<uint16_t>(mvy)) << 16);
-}
-__device__ __forceinline__ int mv_x(uint32_t v) { return static_cast<int16_t>(v & 0xffffu); }
-__device__ __forceinline__ int mv_y(uint32_t v) { return static_cast<int16_t>(v >> 16); }
-
-// Leaf vector of 8x8 block (bx, by) of the CTU in st (split flags decided).
-template <int CTU>
-__device__ __forceinline__ uint32_t leaf_mv(const dev::CtuState<CTU> &st, int bx, int by)
-{
-    using C = dev::Ctu<CTU>;
-    int d = 0, i = 0;
-    for (;;) {
-        i = dev::key_of_block<CTU>(d, bx, by);
-        if (d == C::DMAX || !st.split[i]) break;
-        ++d;
-    }
-    return pack_mv(st.mvx[i], st.mvy[i]);
-}
-
 template <int CTU>
 __global__ void __launch_bounds__(kMvpThreads, 12) k_decide_mvp(const __grid_constant__ MvpBatch b)
 {
     using C = dev::Ctu<CTU>;
     constexpr int N8 = C::N8;
-    constexpr int kLog2Ctu = CTU == 64 ? 6 : (CTU == 32 ? 5 : 4);
     __shared__ dev::CtuState<CTU> st;
     __shared__ int16_t s_pmx[C::NKEY], s_pmy[C::NKEY];
     __shared__ uint32_t s_left[N8];       // right column of the left CTU
@@ -248,7 +207,7 @@ __global__ void __launch_bounds__(kMvpThreads, 12) k_decide_mvp(const __grid_con
                 const unsigned long long *w = hand + (static_cast<long>(cy - 1) * g.ctu_cols + qcx) * N8 + qb;
                 bool ok = false;
                 for (int n = 0; n < b.spin; ++n) {
-                    const unsigned long long x = ld_relaxed64(w);
+                    const unsigned long long x = dev::ld_relaxed64(w);
                     if (static_cast<unsigned>(x >> 32) == want) {
                         v = static_cast<uint32_t>(x);
                         ok = true;
@@ -277,8 +236,8 @@ __global__ void __launch_bounds__(kMvpThreads, 12) k_decide_mvp(const __grid_con
                 const uint32_t b1 = top ? s_above[(lx + kS - 1) >> 3] : 0u;
                 uint32_t b0 = 0u;
                 if (top && x0 + lx + kS < g.W8) b0 = lx + kS < CTU ? s_above[(lx + kS) >> 3] : s_above[N8];
-                s_pmx[ki] = static_cast<int16_t>(median3(mv_x(a1), mv_x(b1), mv_x(b0)));
-                s_pmy[ki] = static_cast<int16_t>(median3(mv_y(a1), mv_y(b1), mv_y(b0)));
+                s_pmx[ki] = static_cast<int16_t>(dev::median3(dev::mv_x(a1), dev::mv_x(b1), dev::mv_x(b0)));
+                s_pmy[ki] = static_cast<int16_t>(dev::median3(dev::mv_y(a1), dev::mv_y(b1), dev::mv_y(b0)));
             }
         }
         __syncthreads();
@@ -287,10 +246,10 @@ __global__ void __launch_bounds__(kMvpThreads, 12) k_decide_mvp(const __grid_con
         // publish the bottom row for the row below; keep the right column
         if (tid < N8) {
             if (cy + 1 < g.ctu_rows && x0 + 8 * tid < g.W8)
-                st_relaxed64(hand + static_cast<long>(ctu_idx) * N8 + tid,
-                             (static_cast<unsigned long long>(target) << 32) | leaf_mv<CTU>(st, tid, N8 - 1));
+                dev::st_relaxed64(hand + static_cast<long>(ctu_idx) * N8 + tid,
+                             (static_cast<unsigned long long>(target) << 32) | dev::leaf_mv<CTU>(st, tid, N8 - 1));
         } else if (tid < 2 * N8) {
-            s_left[tid - N8] = leaf_mv<CTU>(st, N8 - 1, tid - N8);
+            s_left[tid - N8] = dev::leaf_mv<CTU>(st, N8 - 1, tid - N8);
         }
         __syncthreads();
         if (cx + 1 < g.ctu_cols) stage();  // the next CTU's state
@@ -299,7 +258,7 @@ __global__ void __launch_bounds__(kMvpThreads, 12) k_decide_mvp(const __grid_con
     // the last row to finish (decided or given up) publishes the generation
     if (tid == 0 && atomicAdd(rows_done, 1u) == static_cast<unsigned>(g.ctu_rows) - 1u) {
         *rows_done = 0;
-        st_release32(gen, target);
+        dev::st_release32(gen, target);
     }
 }
 

@@ -101,6 +101,7 @@ struct ladder {
     int dbg_wait_polls = 0;   // 0: kMvpSpinDefault
     int dbg_lost_handoff = 0;
     int mvp_capacity = 0;  // resident CTAs of the wavefront kernel
+    int subpel_mvp_capacity = 0;  // resident CTAs of the refinement's wavefront kernel
     char *host_stage = nullptr;  // pinned staging for fetch_decisions
     size_t host_stage_bytes = 0;
     // tracing
@@ -1224,7 +1225,10 @@ long ladder_subpel_workspace_bytes(const ladder_t *l, int rung)
 {
     if (!l || rung < 0 || rung >= l->geo.n_rungs) return 0;
     const RungGeom &g = l->info[rung].g;
-    return subpel_workspace_layout(l->geo.bit_depth, g.W, g.H, nullptr, nullptr);
+    // the 16 phase planes, then the SATD table of the refinement with the
+    // spatial predictor (always counted: the mode may change between calls)
+    return subpel_workspace_layout(l->geo.bit_depth, g.W, g.H, nullptr, nullptr) +
+           subpel_table_bytes(g.ctu_cols, g.ctu_rows, g.dmax);
 }
 
 namespace {
@@ -1245,6 +1249,7 @@ ladder_status subpel_item(ladder_t *l, const ladder_subpel_job &j, SubpelItem &i
         return fail(l, LADDER_E_STATE, "rung %d of frame %d has not been analysed", j.rung, j.frame_id);
     const RungGeom &g = l->info[j.rung].g;
     it = SubpelItem{};
+    it.rung = j.rung;
     it.g = g;
     it.off = l->info[j.rung].off;
     it.block = slot->rungs[j.rung].block;
@@ -1254,7 +1259,8 @@ ladder_status subpel_item(ladder_t *l, const ladder_subpel_job &j, SubpelItem &i
     it.ref = j.ref;
     it.pitch_bytes = j.pitch_bytes;
     it.planes = static_cast<char *>(j.workspace);
-    subpel_workspace_layout(l->geo.bit_depth, g.W, g.H, &it.plane_pitch, &it.plane_bytes);
+    const long planes_bytes = subpel_workspace_layout(l->geo.bit_depth, g.W, g.H, &it.plane_pitch, &it.plane_bytes);
+    it.table = reinterpret_cast<int32_t *>(it.planes + planes_bytes);  // 256-byte aligned: planes_bytes is
     if (!out->leaf_depth || !out->leaf_qmvx || !out->leaf_qmvy)
         return fail(l, LADDER_E_INVAL, "leaf arrays missing");
     for (int d = 0; d <= g.dmax; ++d) {
@@ -1270,6 +1276,50 @@ ladder_status subpel_item(ladder_t *l, const ladder_subpel_job &j, SubpelItem &i
     it.out.leaf_depth = out->leaf_depth;
     it.out.leaf_mvx = out->leaf_qmvx;
     it.out.leaf_mvy = out->leaf_qmvy;
+    return LADDER_OK;
+}
+
+// The refinement with the spatial predictor: the interpolation and every
+// job's SATD table in one pair of launches, then cooperative wavefront
+// launches of one CTA per CTU row, as many jobs per launch as fit on the
+// device at once (rows wait on the row above).
+ladder_status refine_subpel_mvp(ladder_t *l, const SubpelBatch &b, int ctas, int ictas, cudaStream_t s)
+{
+    if (l->subpel_mvp_capacity <= 0) l->subpel_mvp_capacity = subpel_mvp_capacity(l->geo.ctu_size, l->sm_count);
+    for (int k = 0; k < b.n; ++k)
+        if (b.item[k].g.ctu_rows > l->subpel_mvp_capacity)
+            return fail(l, LADDER_E_INVAL, "%d CTU rows exceed the %d resident wavefront CTAs", b.item[k].g.ctu_rows,
+                        l->subpel_mvp_capacity);
+    cudaError_t e = traced(l, 7, s, [&] {
+        return launch_subpel_table(l->geo.bit_depth, l->geo.ctu_size, b, ctas, ictas, s);
+    });
+    if (e != cudaSuccess) return cuda_fail(l, e, "quarter-pel SATD tables");
+    auto *mb = new (std::nothrow) SubpelMvpBatch{};
+    if (!mb) return fail(l, LADDER_E_NOMEM, "wavefront batch table");
+    for (int r = 0; r < l->geo.n_rungs; ++r) mb->rung[r] = l->info[r];
+    mb->status = l->d_status;
+    mb->spin = l->dbg_wait_polls > 0 ? l->dbg_wait_polls : kMvpSpinDefault;
+    mb->lost_handoff = l->dbg_lost_handoff;
+    int k = 0;
+    while (k < b.n) {
+        int m = 0, rows = 0;
+        while (k + m < b.n && m < kMaxSubpelItems) {
+            const SubpelItem &it = b.item[k + m];
+            if (m > 0 && rows + it.g.ctu_rows > l->subpel_mvp_capacity) break;
+            mb->item[m] = SubpelMvpItem{const_cast<char *>(it.block), it.rung, it.qp, it.dependent, rows, it.table,
+                                        it.out};
+            rows += it.g.ctu_rows;
+            ++m;
+        }
+        mb->n = m;
+        e = traced(l, 7, s, [&] { return launch_subpel_mvp(l->geo.ctu_size, *mb, rows, s); });
+        if (e != cudaSuccess) {
+            delete mb;
+            return cuda_fail(l, e, "quarter-pel refinement wavefront");
+        }
+        k += m;
+    }
+    delete mb;
     return LADDER_OK;
 }
 
@@ -1312,6 +1362,11 @@ ladder_status ladder_refine_subpel_batch(ladder_t *l, int n, const ladder_subpel
     b->n = n;
     b->satd_mode = l->geo.satd_mode;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (l->mv_predictor) {
+        const ladder_status st = refine_subpel_mvp(l, *b, ctas, ictas, s);
+        delete b;
+        return st == LADDER_OK ? marked(l, s, LADDER_OK) : st;
+    }
     const cudaError_t e =
         traced(l, 7, s, [&] { return launch_subpel(l->geo.bit_depth, l->geo.ctu_size, *b, ctas, ictas, s); });
     delete b;

@@ -352,6 +352,7 @@ cudaError_t launch_decide_qps(int ctu, const QpBatch &b, cudaStream_t s);
 // Quarter-pel refinement of one analysed rung: one CTA per CTU.
 // One (frame, rung) job of a quarter-pel refinement launch.
 struct SubpelItem {
+    int rung;
     int cta_begin;           // first refinement CTA (one per CTU)
     int icta_begin, icols;   // first interpolation CTA; interpolation tiles per row
     RungGeom g;
@@ -365,6 +366,9 @@ struct SubpelItem {
     // the positions -4 .. W+3 by -4 .. H+3 (subpel_workspace_layout)
     char *planes;
     long plane_pitch, plane_bytes;
+    // spatial predictor: the SATD of every position the two rounds can
+    // visit, kSubpelTab per evaluated CU (after the planes in the workspace)
+    int32_t *table;
     DevDecisions out;        // mvx, mvy (quarter-pel), satd, cost, best, split and leaf maps set
 };
 constexpr int kMaxSubpelItems = 16;
@@ -373,6 +377,45 @@ struct SubpelBatch {
     int satd_mode;
     SubpelItem item[kMaxSubpelItems];
 };
+// Quarter-pel positions within +-3 of 4 mv in each axis, 4 mv itself left
+// out: every position the half-pel round (+-2) and the quarter-pel round
+// (+-1 around any half-pel best) can visit.  Index: raster order over
+// (oy, ox) in [-3, 3]^2, skipping (0, 0).
+constexpr int kSubpelTab = 48;
+__host__ __device__ constexpr int subpel_tab_index(int ox, int oy)
+{
+    return (oy + 3) * 7 + (ox + 3) < 24 ? (oy + 3) * 7 + (ox + 3) : (oy + 3) * 7 + (ox + 3) - 1;
+}
+// Bytes of the SATD table of a rung (per CTU, keys_per_ctu x kSubpelTab int32).
+inline long subpel_table_bytes(int ctu_cols, int ctu_rows, int dmax)
+{
+    return (static_cast<long>(ctu_cols) * ctu_rows * keys_per_ctu(dmax) * kSubpelTab * 4 + 255) / 256 * 256;
+}
+// The refinement with the spatial predictor, decided CTU by CTU in wavefront
+// order from the tables (one CTA per CTU row, rows wait on the row above).
+struct SubpelMvpItem {
+    char *block;            // the (slot, rung) decision block: flags, integer vectors and SATDs, hand-off words
+    int rung, qp, dependent;
+    int cta_begin;          // CTA of the item's first CTU row
+    const int32_t *table;   // per CTU and key, kSubpelTab SATDs
+    DevDecisions out;
+};
+struct SubpelMvpBatch {
+    int n;
+    int *status;
+    int spin;          // polls of one wait before it gives up
+    int lost_handoff;  // test control: 1 = rows wait for a hand-off generation no row publishes
+    RungInfo rung[kMaxRungs];
+    SubpelMvpItem item[kMaxSubpelItems];
+};
+// The table launch (after the interpolation) and the cooperative wavefront
+// launch of ctas CTAs.
+cudaError_t launch_subpel_table(int bit_depth, int ctu, const SubpelBatch &b, int ctas, int interp_ctas,
+                                cudaStream_t s);
+cudaError_t launch_subpel_mvp(int ctu, const SubpelMvpBatch &b, int ctas, cudaStream_t s);
+// CTAs of the refinement wavefront kernel that fit on the device at once.
+int subpel_mvp_capacity(int ctu, int sm_count);
+
 // ---- spatial MV predictor (wavefront re-decision) -------------------------
 // One item = one analysed (frame slot, rung), decided again with the
 // spatial predictor: one CTA per CTU row, rows in wavefront lockstep.

@@ -139,3 +139,64 @@ def test_subpel_batch_checked():
         # the analysed job alone goes through
         L._call(lad.handle, "ladder_refine_subpel_batch", lad.handle, 1, jobs, None)
         torch.cuda.synchronize()
+
+
+# ------------------------------------------- spatial MV predictor -----
+@pytest.mark.parametrize("bd,satd,ctu", [(8, 0, 64), (10, 1, 32), (8, 0, 16)])
+def test_subpel_spatial_predictor_matches_oracle(bd, satd, ctu):
+    """With the spatial predictor on, the refinement (SATD tables, then the
+    wavefront over the refined quarter-pel vectors) equals the oracle's
+    refinement with mvp=1 of its own mvp=1 analysis: an independent and two
+    dependent rungs, per call and batched."""
+    pairs, _ = synth.ladder_pairs(73, source=(480, 270), rungs=[(400, 224), (320, 180)], bit_depth=bd)
+    sizes = [(w, h) for (w, h, _, _) in pairs]
+    R, r, qp = 8, 3, 36
+    with L.Ladder(sizes, 2, bit_depth=bd, ctu_size=ctu, search_range=R, refine_range=r, satd_mode=satd,
+                  max_frames=1) as lad:
+        lad.set_mv_predictor(1)
+        planes = [(L.device_plane(c), L.device_plane(f)) for (_, _, c, f) in pairs]
+        lad.analyze_reference(0, *planes[2], qp)
+        lad.analyze_dependents(0, [(i, planes[i][0], planes[i][1]) for i in (0, 1)], qp)
+        got = [lad.refine_subpel(i, 0, planes[i][0], planes[i][1], qp) for i in range(3)]
+        got_batch = lad.refine_subpel_batch([(0, i, planes[i][0], planes[i][1], qp) for i in (0, 2, 1)])
+        lad.sync()
+        # back to the predictor (0, 0): the two-round kernel again
+        lad.set_mv_predictor(0)
+        zero = lad.refine_subpel(2, 0, planes[2][0], planes[2][1], qp)
+    ref_ana = oracle.analyze(pairs[2][2], pairs[2][3], qp=qp, search_range=R, ctu=ctu, satd_mode=satd, mvp=1)
+    want = {2: oracle.refine_subpel(pairs[2][2], pairs[2][3], ref_ana, qp=qp, ctu=ctu, satd_mode=satd, mvp=1)}
+    for i in (0, 1):
+        dep = dep_from(ref_ana, sizes[2])
+        ana = oracle.analyze(pairs[i][2], pairs[i][3], qp=qp, search_range=r, ctu=ctu, satd_mode=satd, dep=dep,
+                             mvp=1)
+        want[i] = oracle.refine_subpel(pairs[i][2], pairs[i][3], ana, qp=qp, ctu=ctu, satd_mode=satd, dep=dep,
+                                       mvp=1)
+    for i in range(3):
+        _check(got[i], want[i], f"mvp rung {i} bd{bd} satd{satd} ctu{ctu}")
+    for k, i in enumerate((0, 2, 1)):
+        _check(got_batch[k], want[i], f"mvp batched rung {i} bd{bd} satd{satd} ctu{ctu}")
+    want0 = oracle.refine_subpel(pairs[2][2], pairs[2][3], ref_ana, qp=qp, ctu=ctu, satd_mode=satd, mvp=0)
+    _check(zero, want0, f"predictor (0, 0) after mode 1, bd{bd}")
+    # the predictor changes some refined cost (the case is not vacuous)
+    assert any(not np.array_equal(np.asarray(want[2]["cost"][d]), np.asarray(want0["cost"][d]))
+               for d in range(len(want0["grid"])))
+
+
+@pytest.mark.parametrize("bd,W,H,gmv,ctu", [(8, 72, 40, (14, -11), 32), (10, 40, 24, (-13, 9), 16),
+                                             (8, 200, 136, (-6, 5), 16)])
+def test_subpel_spatial_predictor_edges(bd, W, H, gmv, ctu):
+    """Ragged CTUs and vectors past the frame with the spatial predictor;
+    the last case has more CTU rows than columns (deep wavefront)."""
+    p = synth.frame_pair(31, W, H, bit_depth=bd, global_mv=gmv, patch_size=8)
+    R, qp = 16, 33
+    with L.Ladder([(W, H)], 0, bit_depth=bd, ctu_size=ctu, search_range=R, max_frames=1) as lad:
+        lad.set_mv_predictor(1)
+        c, f = L.device_plane(p.cur), L.device_plane(p.ref)
+        lad.analyze_reference(0, c, f, qp)
+        got = lad.refine_subpel(0, 0, c, f, qp)
+        again = lad.refine_subpel(0, 0, c, f, qp)  # a second launch on the same hand-off words
+        lad.sync()
+    ana = oracle.analyze(p.cur, p.ref, qp=qp, search_range=R, ctu=ctu, mvp=1)
+    want = oracle.refine_subpel(p.cur, p.ref, ana, qp=qp, ctu=ctu, mvp=1)
+    _check(got, want, f"mvp {W}x{H} bd{bd}")
+    _check(again, want, f"mvp again {W}x{H} bd{bd}")
