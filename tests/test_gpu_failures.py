@@ -99,3 +99,30 @@ def test_debug_controls_are_validated():
         lad.set_debug(wait_polls=64, lost_handoff=0)
         lad.set_debug(wait_polls=0)
     assert np.int32(TIMEOUT) == -6
+
+
+def test_refinement_wavefront_wait_runs_out_and_is_reported():
+    """The quarter-pel refinement with the spatial predictor has a wavefront
+    of its own: its rows' waits run out the same way, ladder_sync reports
+    it, and the next refinement with normal hand-offs matches the oracle."""
+    fp = synth.frame_pair(83, 256, 200, 8)
+    with L.Ladder([(256, 200)], 0, search_range=8, max_frames=1) as lad:
+        cur, ref = L.device_plane(fp.cur), L.device_plane(fp.ref)
+        lad.set_mv_predictor(1)
+        lad.analyze_reference(0, cur, ref, 30)
+        lad.sync()
+        lad.set_debug(wait_polls=POLLS, lost_handoff=1)
+        lad.refine_subpel(0, 0, cur, ref, 30)
+        with pytest.raises(L.LadderError) as e:
+            lad.sync()
+        assert e.value.status == TIMEOUT
+        lad.set_debug(wait_polls=0, lost_handoff=0)
+        got = lad.refine_subpel(0, 0, cur, ref, 30)
+        lad.sync()
+    ana = oracle.analyze(fp.cur, fp.ref, qp=30, search_range=8, mvp=1)
+    want = oracle.refine_subpel(fp.cur, fp.ref, ana, qp=30, mvp=1)
+    for k in ("qmvx", "qmvy", "satd", "cost", "best", "split"):
+        for d in range(len(want["grid"])):
+            assert np.array_equal(np.asarray(got[k][d]), want[k][d]), (k, d)
+    for k in ("leaf_depth", "leaf_qmvx", "leaf_qmvy"):
+        assert np.array_equal(np.asarray(got[k]), want[k]), k
