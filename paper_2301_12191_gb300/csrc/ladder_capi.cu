@@ -411,15 +411,22 @@ ladder_status launch_independent(ladder_t *l, const Job *jobs, int n, cudaStream
     // the tail of a small launch) unless the launch has several waves of
     // tiles, where sharing one staged window between 2 tiles saves work
     int group = l->tune_fs_group;
+    // 10-bit frames of whole 8x8 blocks read their current CTUs through L1
+    // (no shared copy: room for a third CTA per SM)
+    int cur_l1 = l->geo.bit_depth == 10 ? 1 : 0;
+    for (int k = 0; k < n; ++k)
+        if ((l->info[jobs[k].rung].g.W & 7) || (l->info[jobs[k].rung].g.H & 7)) cur_l1 = 0;
     if (group <= 0) {
-        const FullSearchPlan p1 = full_search_plan(l->geo.bit_depth, l->geo.ctu_size, R, l->tune_fs_band, 1);
+        const FullSearchPlan p1 =
+            full_search_plan(l->geo.bit_depth, l->geo.ctu_size, R, l->tune_fs_band, 1, cur_l1);
         long tiles = 0;
         for (int k = 0; k < n; ++k)
             tiles += static_cast<long>(l->info[jobs[k].rung].g.ctu_cols) * l->info[jobs[k].rung].g.ctu_rows *
                      p1.warp_tiles;
         group = tiles >= 6L * l->sm_count * std::max(1, l->fs_ctas_per_sm) ? 2 : 1;
     }
-    const FullSearchPlan plan = full_search_plan(l->geo.bit_depth, l->geo.ctu_size, R, l->tune_fs_band, group);
+    const FullSearchPlan plan =
+        full_search_plan(l->geo.bit_depth, l->geo.ctu_size, R, l->tune_fs_band, group, cur_l1);
     for (int j0 = 0; j0 < n; j0 += kMaxItems) {
         const int m = std::min(kMaxItems, n - j0);
         FillBatch fill{};

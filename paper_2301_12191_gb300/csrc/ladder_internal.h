@@ -211,6 +211,7 @@ struct FullSearchBatch {
     int stage_off;    // byte offset of the staged rows inside the expanded window
     int phase1_rows;  // expanded rows that end before the staged rows
     int buf_bytes;    // shared bytes of the expanded window + current CTU + block sums
+    int cur_l1;       // 10-bit: current CTU through L1 (every item's W and H multiples of 8)
     int total;        // CTAs of the batch
     uint32_t one;     // 1, as an operand the compiler cannot fold
     int *status;
@@ -232,13 +233,16 @@ struct FullSearchPlan {
     int box_w, box_h; // TMA box (samples x rows)
     int e_bytes, stage_off, phase1_rows, buf_bytes;
     int smem_bytes;   // dynamic shared memory of one CTA (two buffers)
+    int cur_l1;       // 10-bit: the current CTU read through L1 (no shared copy)
 };
 
 // Returns the plan for bit depth / CTU / R / band (13 or 9 candidate rows
 // per lane task; 9 only with 64x64 CTUs).
 // `group` warp tiles share one CTA and its window (reduced while the window
 // would exceed the kernels' bound).
-FullSearchPlan full_search_plan(int bit_depth, int ctu, int R, int band = kFsBand, int group = 1);
+// cur_l1 (10-bit, frames of whole 8x8 blocks): the current CTU is read
+// through L1 instead of a shared copy, which frees its shared memory.
+FullSearchPlan full_search_plan(int bit_depth, int ctu, int R, int band = kFsBand, int group = 1, int cur_l1 = 0);
 // Tiled 2-D tensor map of a W x H plane (8-bit: uint8, 10-bit: uint16
 // samples), box box_w x box_h samples, zero fill outside the plane.
 // Returns 0 on success, else the driver's error (or -1: encoder unavailable).
@@ -250,7 +254,7 @@ int encode_item_maps(FullSearchBatch &b, int k, const void *cur, const void *ref
 // Copies the plan's launch constants into a batch.
 void fill_full_search_batch(FullSearchBatch &b, const FullSearchPlan &p, int R);
 // Resident full-search CTAs per SM for this plan (occupancy calculator).
-int full_search_ctas_per_sm(int bit_depth, int ctu, int R, int band = kFsBand, int group = 1);
+int full_search_ctas_per_sm(int bit_depth, int ctu, int R, int band = kFsBand, int group = 1, int cur_l1 = 0);
 // One CTA per work item: b.total = sum over frames of CTUs x ceil(warp_tiles / group).
 cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchBatch &b, cudaStream_t s);
 

@@ -232,8 +232,10 @@ __device__ __forceinline__ void decide_ctu(const FullSearchBatch &b, const FullS
 }
 
 // 8-bit: four CTAs per SM; 10-bit: three (at most 168 registers), which
-// the shared memory of bands of 9 with two warp tiles per CTA allows
-template <typename T, int CTU, int RP, int BAND>
+// the shared memory allows with bands of 9, or with bands of 13 when the
+// current CTU is read through L1 (CL: frames of whole 8x8 blocks, so no
+// current sample needs the edge replication of the staged copy).
+template <typename T, int CTU, int RP, int BAND, bool CL>
 __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 3) k_full_search(const __grid_constant__ FullSearchBatch b)
 {
     using S = Shape<T, CTU, RP, BAND>;
@@ -247,8 +249,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 3) k_full_search(con
     uint8_t *const sm = smem_raw + ((128u - (dev::smem_addr(smem_raw) & 127u)) & 127u);
     uint32_t *const E = reinterpret_cast<uint32_t *>(sm);             // box_h rows x P4 words
     T *const stage = reinterpret_cast<T *>(sm + b.stage_off);         // box_h rows x P4 samples, inside E
-    T *const curs = reinterpret_cast<T *>(sm + b.e_bytes);            // CTU x CTU samples
-    uint32_t *const a8 = reinterpret_cast<uint32_t *>(sm + b.e_bytes + CTU * CTU * ES);  // 10-bit block sums
+    T *const curs = reinterpret_cast<T *>(sm + b.e_bytes);            // CTU x CTU samples (not with CL)
+    uint32_t *const a8 = reinterpret_cast<uint32_t *>(sm + b.e_bytes + (CL ? 0 : CTU * CTU * ES));  // 10-bit block sums
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t s_k8[S::NB8];                          // 8x8 keys
     __shared__ unsigned long long s_kup[keys_per_ctu(S::DMAX - 1)];  // larger CUs
@@ -287,9 +289,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 3) k_full_search(con
     for (int i = tid; i < keys_per_ctu(S::DMAX - 1); i += NT) s_kup[i] = ~0ull;
     __syncthreads();
     if (tid == 0) {
-        mbar_arrive_expect_tx(&bar, static_cast<uint32_t>((b.box_h * P4 + CTU * CTU) * ES));
+        mbar_arrive_expect_tx(&bar, static_cast<uint32_t>((b.box_h * P4 + (CL ? 0 : CTU * CTU)) * ES));
         tma_load_2d(stage, &b.map[ii], &bar, x0 - b.Rp, sy0);
-        tma_load_2d(curs, &b.cur_map[ii], &bar, x0, y0);
+        if constexpr (!CL) tma_load_2d(curs, &b.cur_map[ii], &bar, x0, y0);
     }
 
     const bool ok = mbar_wait_bounded(&bar, 0);
@@ -299,8 +301,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 3) k_full_search(con
         return;
     }
 
+    // CL: the current CTU's samples, row pitch cps (read through L1)
+    const long cps = a.pitch_bytes / ES;
+    const T *const curg = static_cast<const T *>(a.cur) + static_cast<long>(y0) * cps + x0;
     // Current CTU: edge replication into the 8-aligned pad.
-    if (x0 + CTU > a.W || y0 + CTU > a.H) {
+    if (!CL && (x0 + CTU > a.W || y0 + CTU > a.H)) {
         for (int i = tid; i < CTU * CTU; i += NT) {
             const int row = i / CTU, col = i - row * CTU;
             const int gx = x0 + col, gy = y0 + row;
@@ -351,9 +356,14 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 3) k_full_search(con
         for (int blk = tid; blk < S::NB8; blk += NT) {
             const int bx = (blk % (CTU / 8)) * 8, by = (blk / (CTU / 8)) * 8;
             uint32_t s = 0;
+            if (CL && (x0 + bx >= W8 || y0 + by >= H8)) {  // outside the frame: never read
+                a8[blk] = 0;
+                continue;
+            }
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(curs + (by + j) * CTU + bx);
+                const uint4 v = CL ? __ldg(reinterpret_cast<const uint4 *>(curg + (by + j) * cps + bx))
+                                   : *reinterpret_cast<const uint4 *>(curs + (by + j) * CTU + bx);
                 s += v.x + v.y + v.z + v.w;
             }
             a8[blk] = s;
@@ -394,11 +404,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 3) k_full_search(con
         // quadrant (acc starts at zero), and the block's 8x8 key
         auto block_sads = [&](int bx, int by, uint32_t(&acc)[TY]) {
             const uint32_t *bp = lp + by * P4 + bx;
-            const T *cp = curs + (qy + by) * CTU + qx + bx;
+            const T *cp = CL ? curg + (qy + by) * cps + qx + bx : curs + (qy + by) * CTU + qx + bx;
+            const long cstride = CL ? cps : CTU;
             if constexpr (ES == 1) {
                 uint2 c[8];
     #pragma unroll
-                for (int j = 0; j < 8; ++j) c[j] = *reinterpret_cast<const uint2 *>(cp + j * CTU);
+                for (int j = 0; j < 8; ++j) c[j] = *reinterpret_cast<const uint2 *>(cp + j * cstride);
     #pragma unroll
                 for (int r = 0; r < NR; ++r) {
                     const uint32_t w0 = bp[r * P4], w1 = bp[r * P4 + 4];
@@ -417,7 +428,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 3) k_full_search(con
             } else {
                 uint4 c[8];
     #pragma unroll
-                for (int j = 0; j < 8; ++j) c[j] = *reinterpret_cast<const uint4 *>(cp + j * CTU);
+                for (int j = 0; j < 8; ++j)
+                    c[j] = CL ? __ldg(reinterpret_cast<const uint4 *>(cp + j * cstride))
+                              : *reinterpret_cast<const uint4 *>(cp + j * CTU);
                 const uint32_t sa = a8[((qy + by) / 8) * (CTU / 8) + (qx + bx) / 8];
                 // candidate i is complete after window row i + 7: there
                 // SAD = sum(a) + sum(b) - 2 sum(min), per packed half
@@ -570,71 +583,80 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 3) k_full_search(con
 }
 
 // Largest dynamic shared memory already granted to a kernel instance.
-template <typename T, int CTU, int RP, int BAND> int &granted_smem()
+template <typename T, int CTU, int RP, int BAND, bool CL> int &granted_smem()
 {
     static int bytes = -1;
     return bytes;
 }
 
-template <typename T, int CTU, int RP, int BAND> cudaError_t ensure_smem(int smem)
+template <typename T, int CTU, int RP, int BAND, bool CL> cudaError_t ensure_smem(int smem)
 {
-    if (granted_smem<T, CTU, RP, BAND>() >= smem) return cudaSuccess;
+    if (granted_smem<T, CTU, RP, BAND, CL>() >= smem) return cudaSuccess;
     cudaError_t e =
-        cudaFuncSetAttribute(k_full_search<T, CTU, RP, BAND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) granted_smem<T, CTU, RP, BAND>() = smem;
+        cudaFuncSetAttribute(k_full_search<T, CTU, RP, BAND, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) granted_smem<T, CTU, RP, BAND, CL>() = smem;
     return e;
 }
 
-template <typename T, int CTU, int RP, int BAND> int occupancy_t(int smem)
+template <typename T, int CTU, int RP, int BAND, bool CL> int occupancy_t(int smem)
 {
-    if (ensure_smem<T, CTU, RP, BAND>(smem) != cudaSuccess) return 1;
+    if (ensure_smem<T, CTU, RP, BAND, CL>(smem) != cudaSuccess) return 1;
     int n = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_full_search<T, CTU, RP, BAND>, Shape<T, CTU, RP, BAND>::NT,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_full_search<T, CTU, RP, BAND, CL>, Shape<T, CTU, RP, BAND>::NT,
                                                       smem) !=
         cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
 
-template <typename T, int CTU, int RP, int BAND>
+template <typename T, int CTU, int RP, int BAND, bool CL>
 cudaError_t launch_t(const FullSearchBatch &b, int smem, cudaStream_t s)
 {
     using S = Shape<T, CTU, RP, BAND>;
-    cudaError_t e = ensure_smem<T, CTU, RP, BAND>(smem);
+    cudaError_t e = ensure_smem<T, CTU, RP, BAND, CL>(smem);
     if (e != cudaSuccess) return e;
     const int n2 = (b.box_h - std::min(b.phase1_rows, b.box_h)) * S::CPR;
     if (n2 > S::MAXC * S::NT || b.box_h > S::MAX_ROWS || 3 * S::TY * 32 * 4 > b.e_bytes) return cudaErrorInvalidValue;
-    return launch_chained(k_full_search<T, CTU, RP, BAND>, dim3(b.total), dim3(S::NT), smem, s, b);
+    return launch_chained(k_full_search<T, CTU, RP, BAND, CL>, dim3(b.total), dim3(S::NT), smem, s, b);
 }
 
-// Dispatch on (bit depth, CTU, window margin class, band): 64x64 CTUs have
-// bands of 13 (default) and 9 candidate rows, smaller CTUs only 13.
-template <typename F> cudaError_t dispatch(int bit_depth, int ctu, int Rp, int band, F &&f)
+// Dispatch on (bit depth, CTU, window margin class, band, current CTU
+// through L1): 64x64 CTUs have bands of 13 (default) and 9 candidate rows,
+// smaller CTUs only 13; the L1 form exists for 10-bit only.
+template <typename T, int CTU, int RP, int BAND, typename F> cudaError_t dispatch_cl(bool cl, F &&f)
+{
+    if constexpr (sizeof(T) == 2) {
+        if (cl) return f.template run<T, CTU, RP, BAND, true>();
+    }
+    return f.template run<T, CTU, RP, BAND, false>();
+}
+
+template <typename F> cudaError_t dispatch(int bit_depth, int ctu, int Rp, int band, bool cl, F &&f)
 {
     const bool wide = Rp > 32, b9 = band == 9;
     if (bit_depth == 8) {
         if (ctu == 64) {
-            if (wide) return b9 ? f.template run<uint8_t, 64, 64, 9>() : f.template run<uint8_t, 64, 64, 13>();
-            return b9 ? f.template run<uint8_t, 64, 32, 9>() : f.template run<uint8_t, 64, 32, 13>();
+            if (wide) return b9 ? dispatch_cl<uint8_t, 64, 64, 9>(false, f) : dispatch_cl<uint8_t, 64, 64, 13>(false, f);
+            return b9 ? dispatch_cl<uint8_t, 64, 32, 9>(false, f) : dispatch_cl<uint8_t, 64, 32, 13>(false, f);
         }
-        if (ctu == 32) return f.template run<uint8_t, 32, 64, 13>();
-        return f.template run<uint8_t, 16, 64, 13>();
+        if (ctu == 32) return dispatch_cl<uint8_t, 32, 64, 13>(false, f);
+        return dispatch_cl<uint8_t, 16, 64, 13>(false, f);
     }
     if (ctu == 64) {
-        if (wide) return b9 ? f.template run<uint16_t, 64, 64, 9>() : f.template run<uint16_t, 64, 64, 13>();
-        return b9 ? f.template run<uint16_t, 64, 32, 9>() : f.template run<uint16_t, 64, 32, 13>();
+        if (wide) return b9 ? dispatch_cl<uint16_t, 64, 64, 9>(cl, f) : dispatch_cl<uint16_t, 64, 64, 13>(cl, f);
+        return b9 ? dispatch_cl<uint16_t, 64, 32, 9>(cl, f) : dispatch_cl<uint16_t, 64, 32, 13>(cl, f);
     }
-    if (ctu == 32) return f.template run<uint16_t, 32, 64, 13>();
-    return f.template run<uint16_t, 16, 64, 13>();
+    if (ctu == 32) return dispatch_cl<uint16_t, 32, 64, 13>(cl, f);
+    return dispatch_cl<uint16_t, 16, 64, 13>(cl, f);
 }
 
 int rp_class(int ctu, int Rp) { return (ctu == 64 && Rp <= 32) ? 32 : 64; }
 
 struct OccupancyOp {
     int smem, n;
-    template <typename T, int CTU, int RP, int BAND> cudaError_t run()
+    template <typename T, int CTU, int RP, int BAND, bool CL> cudaError_t run()
     {
-        n = occupancy_t<T, CTU, RP, BAND>(smem);
+        n = occupancy_t<T, CTU, RP, BAND, CL>(smem);
         return cudaSuccess;
     }
 };
@@ -643,15 +665,19 @@ struct LaunchOp {
     const FullSearchBatch &b;
     int smem;
     cudaStream_t s;
-    template <typename T, int CTU, int RP, int BAND> cudaError_t run() { return launch_t<T, CTU, RP, BAND>(b, smem, s); }
+    template <typename T, int CTU, int RP, int BAND, bool CL> cudaError_t run()
+    {
+        return launch_t<T, CTU, RP, BAND, CL>(b, smem, s);
+    }
 };
 
 }  // namespace
 
-FullSearchPlan full_search_plan(int bit_depth, int ctu, int R, int band, int group)
+FullSearchPlan full_search_plan(int bit_depth, int ctu, int R, int band, int group, int cur_l1)
 {
     if (ctu != 64 || band != 9) band = kFsBand;  // the compiled bands
     FullSearchPlan p{};
+    p.cur_l1 = bit_depth == 10 && cur_l1 ? 1 : 0;  // the L1 form exists for 10-bit only
     const int es = bit_depth == 8 ? 1 : 2;
     const int K = 2 * R + 1;
     p.Rp = (R + 15) / 16 * 16;
@@ -686,7 +712,7 @@ FullSearchPlan full_search_plan(int bit_depth, int ctu, int R, int band, int gro
     const int stage_bytes = rows * p.P4 * es;
     p.stage_off = (p.e_bytes - stage_bytes) / 128 * 128;
     p.phase1_rows = p.stage_off / (4 * p.P4);
-    const int cur_bytes = ctu * ctu * es;
+    const int cur_bytes = p.cur_l1 ? 0 : ctu * ctu * es;
     const int a8_bytes = es == 2 ? (ctu / 8) * (ctu / 8) * 4 : 0;
     const int xch_bytes = group > 1 ? 3 * band * 32 * 4 : 0;  // else the exchange reuses the window
     p.buf_bytes = (p.e_bytes + cur_bytes + a8_bytes + xch_bytes + 127) / 128 * 128;
@@ -707,6 +733,7 @@ void fill_full_search_batch(FullSearchBatch &b, const FullSearchPlan &p, int R)
     b.stage_off = p.stage_off;
     b.phase1_rows = p.phase1_rows;
     b.buf_bytes = p.buf_bytes;
+    b.cur_l1 = p.cur_l1;
     b.one = 1;
 }
 
@@ -748,27 +775,33 @@ int encode_item_maps(FullSearchBatch &b, int k, const void *cur, const void *ref
 cudaError_t prepare_full_search(int bit_depth, int ctu, int R)
 {
     // raises the shared-memory attributes (largest: the widest group) outside any capture
-    for (int g = 1; g <= kFsMaxGroup; ++g) {
-        full_search_ctas_per_sm(bit_depth, ctu, R, kFsBand, g);
-        if (ctu == 64) full_search_ctas_per_sm(bit_depth, ctu, R, 9, g);
-    }
+    for (int g = 1; g <= kFsMaxGroup; ++g)
+        for (int cl = 0; cl <= (bit_depth == 10 ? 1 : 0); ++cl) {
+            full_search_ctas_per_sm(bit_depth, ctu, R, kFsBand, g, cl);
+            if (ctu == 64) full_search_ctas_per_sm(bit_depth, ctu, R, 9, g, cl);
+        }
     return cudaGetLastError();
 }
 
-int full_search_ctas_per_sm(int bit_depth, int ctu, int R, int band, int group)
+int full_search_ctas_per_sm(int bit_depth, int ctu, int R, int band, int group, int cur_l1)
 {
-    const FullSearchPlan p = full_search_plan(bit_depth, ctu, R, band, group);
+    const FullSearchPlan p = full_search_plan(bit_depth, ctu, R, band, group, cur_l1);
     OccupancyOp f{p.smem_bytes, 1};
-    dispatch(bit_depth, ctu, p.Rp, p.band, f);
+    dispatch(bit_depth, ctu, p.Rp, p.band, p.cur_l1 != 0, f);
     return f.n;
 }
 
 cudaError_t launch_full_search(int bit_depth, int ctu, const FullSearchBatch &b, cudaStream_t s)
 {
     if (b.n < 1 || b.n > kMaxItems || b.total <= 0) return cudaErrorInvalidValue;
-    const FullSearchPlan p = full_search_plan(bit_depth, ctu, b.R, b.band, b.group);
+    const FullSearchPlan p = full_search_plan(bit_depth, ctu, b.R, b.band, b.group, b.cur_l1);
+    if (p.cur_l1) {
+        // every frame of whole 8x8 blocks: no current sample needs replication
+        for (int k = 0; k < b.n; ++k)
+            if ((b.item[k].W & 7) || (b.item[k].H & 7)) return cudaErrorInvalidValue;
+    }
     LaunchOp f{b, p.smem_bytes, s};
-    return dispatch(bit_depth, ctu, p.Rp, p.band, f);
+    return dispatch(bit_depth, ctu, p.Rp, p.band, p.cur_l1 != 0, f);
 }
 
 }  // namespace ladder_impl
