@@ -89,14 +89,27 @@ L2_FLUSH_BYTES = 256 << 20
 DATA = ("synthetic (seeded sinusoid texture + planted global/patch motion + noise; rungs by Q16 bilinear "
         "downscaling)")
 
-# DRAM bytes (read + write) of one launch from an ncu capture of the bench
-# command (the launch-list summaries under profiles/), keyed by kernel, workload and
-# the hash of the kernel sources it was taken on: null once a kernel changes.
+# DRAM bytes (read + write) of one launch from an ncu capture (the summaries
+# under profiles/), keyed by kernel, workload and the hash of the kernel
+# sources it was taken on, with the kernel shapes of the capture: reported
+# only when the run's shapes are those and the sources unchanged.  The uhd8
+# figures come from the 3-ladder case (--ladders 3) scaled by 8/3: the work
+# of a launch grows with its ladders.
 KERNEL_SOURCES = {"full_search": ["me_full.cu", "common.cuh"], "dependent": ["me_dependent.cu", "common.cuh"]}
 TRAFFIC_NCU = {
-    ("full_search", "ladder1080", "e77cdf8865d0"): 599083,
-    ("dependent", "ladder1080", "45c78fadd63d"): 8583296,
+    ("dependent", "uhd8", "47f8f3bf03ec"): {"bytes": (460672768 + 52931584) * 8 // 3,
+                                            "knobs": {"dep_band": 17, "dep_range": 16, "dep_staged": 1}},
+    ("full_search", "uhd8", "bb216836b147"): {"bytes": 3009536 * 8 // 3, "knobs": {"fs_band": 13}},
 }
+
+
+def traffic_of(kname, name, knobs):
+    """The captured DRAM bytes of one launch of kernel kname in workload
+    name, or None (no capture of these sources with these shapes)."""
+    ent = TRAFFIC_NCU.get((kname, name, kernel_source_hash(kname)))
+    if not ent or any(knobs.get(k) != v for k, v in ent["knobs"].items()):
+        return None
+    return ent["bytes"]
 
 
 def kernel_source_hash(kernel):
@@ -372,6 +385,10 @@ def sad_peak(bit_depth, props, clocks, stream):
 def autotune(args, lad, step, tag, stream):
     """Kernel shapes for this workload from the project's autotuner (untimed;
     every shape gives identical decisions)."""
+    if args.knobs:
+        # fixed shapes (profiler captures that must match a given setting)
+        lad.set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.knobs.split(","))})
+        return {"knobs": lad.tuning(), "tuned": False, "fixed": args.knobs}
     if args.no_tune:
         return {"knobs": lad.tuning(), "tuned": False}
     from paper_2301_12191_gb300 import tune
@@ -634,7 +651,7 @@ def run_ours(args, wl, name, ctx, extra=False):
     else:
         algo = None
     achieved = (algo / (kms / klaunch * 1e-3) / 1e12) if (algo and klaunch) else None
-    traffic = TRAFFIC_NCU.get((kname, name, kernel_source_hash(kname)))
+    traffic = traffic_of(kname, name, tuning["knobs"])
 
     frames_per_s = world * K / (ms_pipe * 1e-3)
     result = {
@@ -951,7 +968,7 @@ def run_batch(args, wl, name, ctx):
         "gpu_launches": launches_per_step * K,
         "roofline": {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tabsdiff/s",
                      "frac": (achieved / peak) if achieved else None,
-                     "traffic": TRAFFIC_NCU.get((kname, name, kernel_source_hash(kname))),
+                     "traffic": traffic_of(kname, name, tuning["knobs"]),
                      "peak_note": peak_note, "peak_probe_in_run": peak_probe,
                      "algorithmic_absdiffs_per_step": algo, "kernel_ms_per_step": kms / 3,
                      "launches_per_step": klaunch // 3,
@@ -1129,6 +1146,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the workloads measured beside the main line")
     ap.add_argument("--no-tune", action="store_true", help="keep the default kernel shapes (skip the autotuner)")
+    ap.add_argument("--knobs", default="", help="fixed kernel shapes, e.g. dep_band=17,dep_range=16 (no autotuner)")
     ap.add_argument("--json-out", default=None)
     ap.add_argument("--soak", type=float, default=1.5, help="untimed seconds of load before timing (clock sampling)")
     ap.add_argument("--only-multires", action="store_true",
