@@ -464,8 +464,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 3) k_full_search(con
                     else sb = sb + rs[r] - rs[r - 8];
                     if (r >= 7) {
                         const int i = r - 7;
-                        const uint32_t d = umad(acc[i], 0xfffffffeu, sa + sb);
-                        acc[i] = (d & 0xffffu) + (d >> 16);
+                        // packed halves of sum(a) + sum(b) - 2 sum(min), added by one dp2a
+                        acc[i] = __dp2a_lo(umad(acc[i], 0xfffffffeu, sa + sb), 0x0101u, 0u);
                     }
                 }
             }
