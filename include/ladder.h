@@ -213,12 +213,13 @@ LADDER_API void ladder_graph_destroy(ladder_graph_t *graph);
  *   LADDER_TUNE_FS_FUSE          1 (default): the last full-search CTA of
  *                                each CTU also takes the CTU's decisions;
  *                                0: separate key-fill and decision kernels
- *   LADDER_TUNE_DEP_STAGED       10-bit dependent search, refinement ranges
- *                                of 4 and more: 1 (default) stages each
- *                                tile's reference windows in shared memory,
- *                                2 does so into two buffers (the next tile's
- *                                copies in flight during the current one),
- *                                0 reads the windows through L1
+ *   LADDER_TUNE_DEP_STAGED       dependent search, refinement ranges of 4
+ *                                and more (8- and 10-bit): 1 (default)
+ *                                stages each tile's reference windows in
+ *                                shared memory, 2 does so into two buffers
+ *                                (the next tile's copies in flight during
+ *                                the current one), 0 reads the windows
+ *                                through L1
  * LADDER_E_INVAL for an unknown knob or value. */
 typedef enum {
     LADDER_TUNE_FS_BAND = 0,

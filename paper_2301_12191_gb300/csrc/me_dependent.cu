@@ -25,6 +25,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace ladder_impl {
 namespace {
@@ -595,15 +596,14 @@ __global__ void __launch_bounds__(kSearchThreads, 2)
     }
 }
 
-// ---- 2b. staged search (10-bit) ----------------------------------------------
+// ---- 2b. staged search ------------------------------------------------------
 // A CTA takes tiles of kStageThreads consecutive lane tasks of one size
 // class.  The lanes of a CU piece are contiguous, so a tile touches a few
 // pieces.  Each piece's reference window (every row and column its
 // candidates read) and its current samples are staged in shared memory
 // first, with the frame-edge rules applied there once (reference rows and
 // columns clamped into the frame, current samples replicated into the
-// 8-aligned pad); a CTA works on two buffers, the next tile's copies in
-// flight while the current tile is computed:
+// 8-aligned pad).  10-bit (ES = 2):
 //   raw0  the window's rows from an 8-sample-aligned column ax, sample
 //         pairs (s[ax + 2m], s[ax + 2m + 1]) per word (16-byte async copies
 //         of whole row chunks when the window lies inside the frame);
@@ -613,7 +613,13 @@ __global__ void __launch_bounds__(kSearchThreads, 2)
 // A lane whose candidate column starts at an even offset from ax reads its 8
 // samples of a row as 4 aligned words of raw0, an odd one as 4 aligned words
 // of raw1: no shifts, no frame-edge path and no divergence in the candidate
-// loop.
+// loop.  8-bit (ES = 1): raw0 only, from a 16-sample-aligned column ax that
+// lies 1..16 samples left of the window; a lane reads 3 aligned words per
+// row and shifts them on the multiply-add pipe (as the L1 form does), which
+// leaves the ALU pipe to the packed absolute differences.  By default a CTA
+// stages into one buffer (several CTAs per SM overlap one another's staging);
+// dep_staged = 2 gives it two, the next tile's copies in flight while the
+// current tile is computed.
 constexpr int kStageThreads = 128;  // small tiles: several CTAs per SM, staging overlaps compute
 constexpr int kMaxStageSlots = 32;  // pieces one tile may touch (lanes per piece >= 9)
 
@@ -622,15 +628,16 @@ struct StageShape {
     int RS;    // piece side
     int WR;    // window rows
     int WW;    // samples a candidate column may start at past the window's first column, + 1
-    int NC;    // 8-sample chunks per raw row (the window's first column lies up to 7 past ax)
+    int NC;    // 16-byte chunks per raw row
     int RW;    // words per raw row (at least 4 NC, a multiple of 4: rows stay 16-byte aligned)
-    int CNC;   // 8-sample chunks per current row (RS / 8)
-    int CW;    // words per current row (RS / 2)
-    int O1;    // offset of raw1
+    int CNC;   // 16-byte chunks per current row
+    int CW;    // words per current row (4 CNC)
+    int O1;    // offset of raw1 (10-bit)
     int OC;    // offset of the current rows
     int PW;    // words per piece slot (a multiple of 4)
 };
 
+template <int ES>
 __host__ __device__ inline StageShape stage_shape(int RS, int r, int TY)
 {
     StageShape s;
@@ -639,17 +646,34 @@ __host__ __device__ inline StageShape stage_shape(int RS, int r, int TY)
     // than 2r + 1 reads TY - 1 - r rows further (those candidates are dropped)
     s.WR = RS + (2 * r > TY - 1 ? 2 * r : TY - 1);
     s.WW = RS + 2 * r - 1;
-    s.NC = (s.WW + 15) / 8;
-    // Banks: a warp's lanes read consecutive words, the even-offset ones in
-    // raw0, the odd-offset ones in raw1 (16 banks away); with several bands
-    // (2r + 1 > TY) a warp also holds a band TY rows lower, and a row stride
-    // of 8 (mod 16) words puts its words beside the first band's.
-    s.RW = 2 * r + 1 > TY ? ((4 * s.NC + 7) & ~15) + 8 : 4 * s.NC;
-    s.CNC = RS / 8;
-    s.CW = RS / 2;
-    s.O1 = ((s.WR * s.RW + 15) & ~31) + 16;
-    s.OC = (s.O1 + s.WR * s.RW + 3) & ~3;
-    s.PW = (s.OC + RS * s.CW + 3) & ~3;
+    if (ES == 2) {
+        // the window's first column lies up to 7 samples past ax
+        s.NC = (s.WW + 15) / 8;
+        // Banks: a warp's lanes read consecutive words, the even-offset ones in
+        // raw0, the odd-offset ones in raw1 (16 banks away); with several bands
+        // (2r + 1 > TY) a warp also holds a band TY rows lower, and a row stride
+        // of 8 (mod 16) words puts its words beside the first band's.
+        s.RW = 2 * r + 1 > TY ? ((4 * s.NC + 7) & ~15) + 8 : 4 * s.NC;
+        s.CNC = RS / 8;
+        s.CW = RS / 2;
+        s.O1 = ((s.WR * s.RW + 15) & ~31) + 16;
+        s.OC = (s.O1 + s.WR * s.RW + 3) & ~3;
+        s.PW = (s.OC + RS * s.CW + 3) & ~3;
+    } else {
+        // the window's first column lies 1..16 samples past ax; a lane's last
+        // word of a row ends at most RS + 2r + 18 samples past ax
+        s.NC = (RS + 2 * r + 19 + 15) / 16;
+        s.RW = 2 * r + 1 > TY ? ((4 * s.NC + 7) & ~15) + 8 : 4 * s.NC;
+        // current rows from a 16-sample-aligned column (an 8x8 CU's 8 samples
+        // lie in the first or second half of its chunk)
+        s.CNC = (RS + 15) / 16;
+        s.CW = 4 * s.CNC;
+        s.O1 = 0;
+        s.OC = (s.WR * s.RW + 3) & ~3;
+        // slots 8 (mod 32) words apart: the (up to four) pieces a warp holds
+        // read different banks
+        s.PW = ((s.OC + RS * s.CW + 23) & ~31) + 8;
+    }
     return s;
 }
 
@@ -731,10 +755,11 @@ struct StageSlots {
     long pitch[kMaxStageSlots];
     int W[kMaxStageSlots], H[kMaxStageSlots], wy0[kMaxStageSlots], ax[kMaxStageSlots];
     int off[kMaxStageSlots], cux[kMaxStageSlots], cuy[kMaxStageSlots], edge[kMaxStageSlots];
+    int coff[kMaxStageSlots];  // the piece's first current column past its staged chunk (8-bit: 0 or 8)
     int any_edge;  // some slot needs the frame-edge fix-up
 };
 
-template <int TY>
+template <int ES, int TY>
 __device__ __forceinline__ StageTile stage_tile(const DependentBatch &b, long tile, int per_cu, const FastDiv &div_cu,
                                                 const long *ln, const long *tn)
 {
@@ -750,7 +775,7 @@ __device__ __forceinline__ StageTile stage_tile(const DependentBatch &b, long ti
     t.nrs = S / t.RS;
     t.nr = t.nrs * t.nrs;
     t.lg = 31 - __clz(t.nrs);
-    t.sh = stage_shape(t.RS, b.r, TY);
+    t.sh = stage_shape<ES>(t.RS, b.r, TY);
     const long tl = min(t.tf + kStageThreads - 1, t.ntask - 1);
     t.q0 = fast_div(static_cast<uint32_t>(t.tf), div_cu);
     t.nslots = static_cast<int>(fast_div(static_cast<uint32_t>(tl), div_cu) - t.q0) + 1;
@@ -759,8 +784,10 @@ __device__ __forceinline__ StageTile stage_tile(const DependentBatch &b, long ti
 
 // The tile's pieces: planes, window origin, frame-edge flags (threads
 // below nslots, one piece each).
+template <int ES>
 __device__ __forceinline__ void stage_slots_setup(const DependentBatch &b, const StageTile &t, StageSlots &ss)
 {
+    constexpr int CS = 16 / ES;  // samples per 16-byte chunk
     const int tid = threadIdx.x;
     if (tid == 0) ss.any_edge = 0;
     __syncthreads();
@@ -776,7 +803,11 @@ __device__ __forceinline__ void stage_slots_setup(const DependentBatch &b, const
         const int cux = static_cast<int>(p & 0xffffu) + (rg % t.nrs) * t.RS;
         const int cuy = static_cast<int>(p >> 16) + (rg / t.nrs) * t.RS;
         const int wx0 = cux + static_cast<int16_t>(hi & 0xffffu) - b.r;
-        const int ax = wx0 & ~7;
+        // 10-bit: the 8-aligned column at or left of the window; 8-bit: the
+        // 16-aligned column 1..16 samples left of it (a lane's first word
+        // then starts left of its first sample)
+        const int ax = ES == 2 ? (wx0 & ~7) : ((wx0 - 1) & ~15);
+        const int cx0 = cux & ~(CS - 1);
         ss.ref[tid] = static_cast<const char *>(a.ref);
         ss.cur[tid] = static_cast<const char *>(a.cur);
         ss.pitch[tid] = a.pitch_bytes;
@@ -787,9 +818,10 @@ __device__ __forceinline__ void stage_slots_setup(const DependentBatch &b, const
         ss.off[tid] = wx0 - ax;
         ss.cux[tid] = cux;
         ss.cuy[tid] = cuy;
+        ss.coff[tid] = cux - cx0;
         // bit 0: a raw word holds a sample outside the frame's columns;
-        // bit 1: the piece's current columns pass the frame's right edge
-        const int e = ((ax < 0 || ax + 8 * t.sh.NC > g.W) ? 1 : 0) | (cux + t.RS > g.W ? 2 : 0);
+        // bit 1: a staged current word passes the frame's right edge
+        const int e = ((ax < 0 || ax + CS * t.sh.NC > g.W) ? 1 : 0) | (cx0 + CS * t.sh.CNC > g.W ? 2 : 0);
         ss.edge[tid] = e;
         if (e) ss.any_edge = 1;
     }
@@ -805,9 +837,11 @@ __device__ __forceinline__ void stage_slots_setup(const DependentBatch &b, const
 // multiple of 32 words apart: four-way bank conflicts).
 constexpr int kStageRowGroups = 4;
 
+template <int ES>
 __device__ __forceinline__ void stage_copy(const StageTile &t, const StageSlots &ss, uint32_t *buf,
                                            const FastDiv &div_cps)
 {
+    constexpr int CS = 16 / ES;  // samples per 16-byte chunk
     const StageShape &sh = t.sh;
     const int cps = kStageRowGroups * (sh.NC + sh.CNC);  // columns per slot
 #pragma unroll 1
@@ -818,11 +852,11 @@ __device__ __forceinline__ void stage_copy(const StageTile &t, const StageSlots 
         const int W = ss.W[slot], H = ss.H[slot];
         const long pitch = ss.pitch[slot];
         const bool ref = ch < sh.NC;
-        const int x = ref ? ss.ax[slot] + 8 * ch : ss.cux[slot] + 8 * (ch - sh.NC);
-        if (x < 0 || x >= W) continue;  // x is a multiple of 8: a chunk that starts in the row ends in its pitch
+        const int x = ref ? ss.ax[slot] + CS * ch : ss.cux[slot] - ss.coff[slot] + CS * (ch - sh.NC);
+        if (x < 0 || x >= W) continue;  // x is a multiple of CS: a chunk that starts in the row ends in its pitch
         const int rows = ref ? sh.WR : t.RS;
         const int y0 = (ref ? ss.wy0[slot] : ss.cuy[slot]) + grp;
-        const char *src = (ref ? ss.ref[slot] : ss.cur[slot]) + 2 * static_cast<long>(x);
+        const char *src = (ref ? ss.ref[slot] : ss.cur[slot]) + ES * static_cast<long>(x);
         const int stride = ref ? sh.RW : sh.CW;
         uint32_t *dst = buf + slot * sh.PW + (ref ? 0 : sh.OC) + grp * stride + 4 * (ref ? ch : ch - sh.NC);
 #pragma unroll 1
@@ -835,8 +869,11 @@ __device__ __forceinline__ void stage_copy(const StageTile &t, const StageSlots 
 // Frame edges: every raw0 word with a sample outside the frame's columns,
 // and every current word past its right edge, from clamped samples (edge
 // slots only; one warp per row).
+template <int ES>
 __device__ __forceinline__ void stage_fixup(const StageTile &t, const StageSlots &ss, uint32_t *buf)
 {
+    using T = typename std::conditional<ES == 1, uint8_t, uint16_t>::type;
+    constexpr int SPW = 4 / ES;  // samples per word
     const StageShape &sh = t.sh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int kWarps = kStageThreads / 32;
@@ -851,16 +888,19 @@ __device__ __forceinline__ void stage_fixup(const StageTile &t, const StageSlots
             if (ref_row ? !(e & 1) : !(e & 2)) continue;
             const int y = ref_row ? min(max(ss.wy0[slot] + row, 0), ss.H[slot] - 1)
                                   : min(ss.cuy[slot] + row - sh.WR, ss.H[slot] - 1);
-            const uint16_t *src = reinterpret_cast<const uint16_t *>((ref_row ? ss.ref[slot] : ss.cur[slot]) +
-                                                                     static_cast<long>(y) * ss.pitch[slot]);
+            const T *src = reinterpret_cast<const T *>((ref_row ? ss.ref[slot] : ss.cur[slot]) +
+                                                       static_cast<long>(y) * ss.pitch[slot]);
             uint32_t *dst = buf + slot * sh.PW + (ref_row ? row * sh.RW : sh.OC + (row - sh.WR) * sh.CW);
-            const int x0 = ref_row ? ss.ax[slot] : ss.cux[slot];
+            const int x0 = ref_row ? ss.ax[slot] : ss.cux[slot] - ss.coff[slot];
             const int nw = ref_row ? 4 * sh.NC : sh.CW;
             for (int m = lane; m < nw; m += 32) {
-                const int p = x0 + 2 * m;
-                if (p >= 0 && p + 1 < W) continue;  // copied as it stands
-                dst[m] = static_cast<uint32_t>(__ldg(src + min(max(p, 0), W - 1))) |
-                         (static_cast<uint32_t>(__ldg(src + min(max(p + 1, 0), W - 1))) << 16);
+                const int p = x0 + SPW * m;
+                if (p >= 0 && p + SPW - 1 < W) continue;  // copied as it stands
+                uint32_t v = 0;
+#pragma unroll
+                for (int e2 = 0; e2 < SPW; ++e2)
+                    v |= static_cast<uint32_t>(__ldg(src + min(max(p + e2, 0), W - 1))) << (8 * ES * e2);
+                dst[m] = v;
             }
         }
     }
@@ -898,7 +938,7 @@ __device__ __forceinline__ void stage_raw1(const StageTile &t, uint32_t *buf, co
 
 // The SADs of one lane's task over the staged tile, into its CU's key or
 // sum table.
-template <int TY>
+template <int ES, int TY>
 __device__ __forceinline__ void stage_compute(const DependentBatch &b, const StageTile &t, const StageSlots &ss,
                                               const uint32_t *buf, int per_cu, const FastDiv &div_cu,
                                               const FastDiv &div_k, int rb)
@@ -917,12 +957,15 @@ __device__ __forceinline__ void stage_compute(const DependentBatch &b, const Sta
     const int dy0 = K >= TY ? min(b0, r - TY + 1) : b0;
     // the lane's first sample of a block row, counted from the raw rows' column ax
     const int xs = ss.off[slot] + dxo + r;
-    const uint32_t *win = buf + slot * sh.PW + ((xs & 1) ? sh.O1 : 0) + (xs >> 1);
-    const uint32_t *curw = buf + slot * sh.PW + sh.OC;
+    // 10-bit: its first word in raw0 or raw1; 8-bit: the word before the one
+    // holding its first sample (q = (xs - 1) / 4, xs >= 1), shifted by m
+    const int wq = ES == 2 ? (xs >> 1) : ((xs - 1) >> 2);
+    const uint32_t *win = buf + slot * sh.PW + ((ES == 2 && (xs & 1)) ? sh.O1 : 0) + wq;
+    const uint32_t *curw = buf + slot * sh.PW + sh.OC + (ES == 2 ? 0 : ss.coff[slot] / 4);
     // debug builds: the lane's slot is staged, and its last window word lies
     // in its raw rows (else it reads the slot's first words; recorded)
     if (!in_range(b.status, slot, t.nslots) ||
-        !in_range(b.status, (t.RS - 8 + dy0 + r + TY + 6) * sh.RW + (xs >> 1) + (t.RS - 8) / 2 + 3,
+        !in_range(b.status, (t.RS - 8 + dy0 + r + TY + 6) * sh.RW + wq + (t.RS - 8) * ES / 4 + (ES == 2 ? 3 : 2),
                   sh.WR * sh.RW)) {
         win = buf;
         curw = buf;
@@ -931,17 +974,35 @@ __device__ __forceinline__ void stage_compute(const DependentBatch &b, const Sta
 #pragma unroll
     for (int i = 0; i < TY; ++i) acc[i] = 0;
     const int nb = t.RS / 8;
+    if constexpr (ES == 2) {
 #pragma unroll 1
-    for (int blk = 0; blk < nb * nb; ++blk) {
-        const int bx = 8 * (blk % nb), by = 8 * (blk / nb);
-        uint4 cv[8];
-        uint32_t sa = 0;
+        for (int blk = 0; blk < nb * nb; ++blk) {
+            const int bx = 8 * (blk % nb), by = 8 * (blk / nb);
+            uint4 cv[8];
+            uint32_t sa = 0;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            cv[j] = *reinterpret_cast<const uint4 *>(curw + (by + j) * sh.CW + bx / 2);
-            sa += (cv[j].x + cv[j].y) + (cv[j].z + cv[j].w);
+            for (int j = 0; j < 8; ++j) {
+                cv[j] = *reinterpret_cast<const uint4 *>(curw + (by + j) * sh.CW + bx / 2);
+                sa += (cv[j].x + cv[j].y) + (cv[j].z + cv[j].w);
+            }
+            sads_staged_u16<TY>(cv, sa, b.one, win + (by + dy0 + r) * sh.RW + bx / 2, sh.RW, acc);
         }
-        sads_staged_u16<TY>(cv, sa, b.one, win + (by + dy0 + r) * sh.RW + bx / 2, sh.RW, acc);
+    } else {
+        const uint32_t m = 1u << (32 - 8 * (xs - 4 * wq));  // xs - 4 wq in 1..4
+#pragma unroll 1
+        for (int blk = 0; blk < nb * nb; ++blk) {
+            const int bx = 8 * (blk % nb), by = 8 * (blk / nb);
+            uint2 cv[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) cv[j] = *reinterpret_cast<const uint2 *>(curw + (by + j) * sh.CW + bx / 4);
+            const uint32_t *rp = win + (by + dy0 + r) * sh.RW + bx / 4;
+            const int rw = sh.RW;
+            sads_core_u8<TY, 1>(cv, [&](int row, uint32_t &w0, uint32_t &w1) {
+                const uint32_t a0 = rp[row * rw], a1 = rp[row * rw + 1], a2 = rp[row * rw + 2];
+                w0 = shift_in(a0, a1, m);
+                w1 = shift_in(a1, a2, m);
+            }, acc);
+        }
     }
 
     const unsigned int ucu = q >> (2 * t.lg);
@@ -1002,11 +1063,12 @@ __device__ __forceinline__ void stage_compute(const DependentBatch &b, const Sta
 // staging instead).  `half`: words of one buffer.
 // Four CTAs per SM (at most 128 registers a thread): with fewer, the
 // staging of one CTA's tile is not hidden behind the others' compute.
-template <int TY>
+template <typename T, int TY>
 __global__ void __launch_bounds__(kStageThreads, 4)
-    k_dep_search_st16(const __grid_constant__ DependentBatch b, const FastDiv div_cu, const FastDiv div_k,
-                      const __grid_constant__ StageDivs dv, int half, int pipelined)
+    k_dep_search_staged(const __grid_constant__ DependentBatch b, const FastDiv div_cu, const FastDiv div_k,
+                        const __grid_constant__ StageDivs dv, int half, int pipelined)
 {
+    constexpr int ES = sizeof(T);
     dev::chain_entry();
     extern __shared__ __align__(16) uint32_t s_win[];
     __shared__ StageSlots s_slots[2];
@@ -1026,40 +1088,42 @@ __global__ void __launch_bounds__(kStageThreads, 4)
     long tile = blockIdx.x;
     if (tile >= total) return;  // the whole CTA: nothing to do
     int bi = 0;
-    StageTile t = stage_tile<TY>(b, tile, per_cu, div_cu, s_ln, s_tn);
-    stage_slots_setup(b, t, s_slots[0]);
+    StageTile t = stage_tile<ES, TY>(b, tile, per_cu, div_cu, s_ln, s_tn);
+    stage_slots_setup<ES>(b, t, s_slots[0]);
     __syncthreads();
-    stage_copy(t, s_slots[0], s_win, dv.cps[t.c]);
+    stage_copy<ES>(t, s_slots[0], s_win, dv.cps[t.c]);
 #pragma unroll 1
     for (;;) {
         uint32_t *buf = s_win + bi * half;
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
         if (s_slots[bi].any_edge) {
-            stage_fixup(t, s_slots[bi], buf);
+            stage_fixup<ES>(t, s_slots[bi], buf);
             __syncthreads();
         }
-        stage_raw1(t, buf, dv.c1[t.c]);
-        __syncthreads();
+        if constexpr (ES == 2) {
+            stage_raw1(t, buf, dv.c1[t.c]);
+            __syncthreads();
+        }
         // the next tile of this CTA into the other buffer, in flight during this one
         const long next = tile + gridDim.x;
         if (pipelined && next < total) {
-            const StageTile tnext = stage_tile<TY>(b, next, per_cu, div_cu, s_ln, s_tn);
-            stage_slots_setup(b, tnext, s_slots[bi ^ 1]);
+            const StageTile tnext = stage_tile<ES, TY>(b, next, per_cu, div_cu, s_ln, s_tn);
+            stage_slots_setup<ES>(b, tnext, s_slots[bi ^ 1]);
             __syncthreads();
-            stage_copy(tnext, s_slots[bi ^ 1], s_win + (bi ^ 1) * half, dv.cps[tnext.c]);
+            stage_copy<ES>(tnext, s_slots[bi ^ 1], s_win + (bi ^ 1) * half, dv.cps[tnext.c]);
         }
-        stage_compute<TY>(b, t, s_slots[bi], buf, per_cu, div_cu, div_k, rb);
+        stage_compute<ES, TY>(b, t, s_slots[bi], buf, per_cu, div_cu, div_k, rb);
         if (next >= total) break;
         __syncthreads();  // the buffer and its slots are restaged (now, or by the tile after next)
-        t = stage_tile<TY>(b, next, per_cu, div_cu, s_ln, s_tn);  // recomputed: nothing held across the compute
+        t = stage_tile<ES, TY>(b, next, per_cu, div_cu, s_ln, s_tn);  // recomputed: nothing held across the compute
         tile = next;
         if (pipelined) {
             bi ^= 1;
         } else {
-            stage_slots_setup(b, t, s_slots[0]);
+            stage_slots_setup<ES>(b, t, s_slots[0]);
             __syncthreads();
-            stage_copy(t, s_slots[0], s_win, dv.cps[t.c]);
+            stage_copy<ES>(t, s_slots[0], s_win, dv.cps[t.c]);
         }
     }
 }
@@ -1214,7 +1278,8 @@ int smem_optin()
             v = 48 << 10;
         cudaFuncAttributes fa{};
         size_t fixed = 1024;
-        if (cudaFuncGetAttributes(&fa, k_dep_search_st16<kDepBand>) == cudaSuccess) fixed = fa.sharedSizeBytes;
+        if (cudaFuncGetAttributes(&fa, k_dep_search_staged<uint16_t, kDepBand>) == cudaSuccess)
+            fixed = fa.sharedSizeBytes;
         n = v - static_cast<int>(fixed);
     }
     return n;
@@ -1223,21 +1288,22 @@ int smem_optin()
 // Dynamic shared memory of a staged search: the most pieces a tile touches
 // times the largest piece of any size class (0 if it does not fit a CTA).
 // (one buffer for b.staged == 1, two for 2; 0 if they do not fit a CTA).
-template <int TY> size_t staged_smem_bytes(const DependentBatch &b)
+template <typename T, int TY> size_t staged_smem_bytes(const DependentBatch &b)
 {
     const int K = 2 * b.r + 1, per_cu = K * ((K + TY - 1) / TY);
     const int slots = stage_slots(per_cu);
     if (slots > kMaxStageSlots) return 0;
     int pw = 0;
-    for (int S = 8; S <= 64; S <<= 1) pw = std::max(pw, stage_shape(S < b.range ? S : b.range, b.r, TY).PW);
+    for (int S = 8; S <= 64; S <<= 1)
+        pw = std::max(pw, stage_shape<sizeof(T)>(S < b.range ? S : b.range, b.r, TY).PW);
     const size_t bytes = (b.staged == 2 ? 2 : 1) * static_cast<size_t>(slots) * pw * 4;
     return bytes <= static_cast<size_t>(smem_optin()) ? bytes : 0;
 }
 
-template <int TY> cudaError_t search_staged(const DependentBatch &b, size_t smem, cudaStream_t s)
+template <typename T, int TY> cudaError_t search_staged(const DependentBatch &b, size_t smem, cudaStream_t s)
 {
     int fit = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_dep_search_st16<TY>, kStageThreads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_dep_search_staged<T, TY>, kStageThreads, smem) !=
             cudaSuccess ||
         fit < 1)
         fit = 1;
@@ -1246,13 +1312,13 @@ template <int TY> cudaError_t search_staged(const DependentBatch &b, size_t smem
     StageDivs dv{};
     for (int c = 0; c < kSizeClasses; ++c) {
         const int S = 8 << c;
-        const StageShape sh = stage_shape(S < b.range ? S : b.range, b.r, TY);
+        const StageShape sh = stage_shape<sizeof(T)>(S < b.range ? S : b.range, b.r, TY);
         dv.cps[c] = make_fastdiv(static_cast<uint32_t>(kStageRowGroups * (sh.NC + sh.CNC)));
         dv.c1[c] = make_fastdiv(static_cast<uint32_t>(kStageRowGroups * sh.NC));
     }
     const int pipelined = b.staged == 2 ? 1 : 0;
     const int half = static_cast<int>(smem / (pipelined ? 8 : 4));  // words of one buffer
-    return launch_chained(k_dep_search_st16<TY>, dim3(grid), dim3(kStageThreads), smem, s, b, make_fastdiv(per_cu),
+    return launch_chained(k_dep_search_staged<T, TY>, dim3(grid), dim3(kStageThreads), smem, s, b, make_fastdiv(per_cu),
                           make_fastdiv(K), dv, half, pipelined);
 }
 
@@ -1261,11 +1327,11 @@ template <typename T> cudaError_t search_bd(const DependentBatch &b, cudaStream_
     // bands of 9 rows when 2r + 1 <= 9 or when asked for; 10-bit bodies are
     // twice as long per row, so 10-bit takes 9 unless asked for 17
     const bool nine = 2 * b.r + 1 <= 9 || b.band == 9 || (sizeof(T) == 2 && b.band != kDepBand);
-    if (sizeof(T) == 2 && b.staged && b.r >= 4) {
+    if (b.staged && b.r >= 4) {
         // staged windows (refinement ranges of 4 and more: at least 9 lanes
         // per piece, so a tile touches few pieces), when they fit a CTA
-        const size_t smem = nine ? staged_smem_bytes<9>(b) : staged_smem_bytes<kDepBand>(b);
-        if (smem > 0) return nine ? search_staged<9>(b, smem, s) : search_staged<kDepBand>(b, smem, s);
+        const size_t smem = nine ? staged_smem_bytes<T, 9>(b) : staged_smem_bytes<T, kDepBand>(b);
+        if (smem > 0) return nine ? search_staged<T, 9>(b, smem, s) : search_staged<T, kDepBand>(b, smem, s);
     }
     if (nine) return search_t<T, 9>(b, s);
     return search_t<T, kDepBand>(b, s);
@@ -1301,19 +1367,25 @@ cudaError_t prepare_kernels(int bit_depth, int ctu, int R, int r)
     cudaError_t e = prepare_full_search(bit_depth, ctu, R);
     if (e != cudaSuccess) return e;
     sm_count();
+    // the staged search sizes its shared memory per launch, up to the opt-in limit
     if (bit_depth == 8) {
         search_ctas_per_sm<uint8_t, 9>();
         search_ctas_per_sm<uint8_t, kDepBand>();
+        e = cudaFuncSetAttribute(k_dep_search_staged<uint8_t, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem_optin());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_dep_search_staged<uint8_t, kDepBand>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
     } else {
         search_ctas_per_sm<uint16_t, 9>();
         search_ctas_per_sm<uint16_t, kDepBand>();
-        // the staged search sizes its shared memory per launch, up to the opt-in limit
-        e = cudaFuncSetAttribute(k_dep_search_st16<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+        e = cudaFuncSetAttribute(k_dep_search_staged<uint16_t, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem_optin());
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_dep_search_st16<kDepBand>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     smem_optin());
-        if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(k_dep_search_staged<uint16_t, kDepBand>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
     }
+    if (e != cudaSuccess) return e;
     (void)r;
     return cudaGetLastError();
 }

@@ -15,10 +15,11 @@ tiles, a batch of 32 frames has plenty.
 each candidate setting by coordinate descent: knobs are tried one at a time,
 each against the best values found so far, and a knob keeps its new value
 only if the step gets faster by more than the noise margin.  The dependent
-search's piece size and band height are tried jointly (every pair): the
-best band depends on the piece size through the shared memory a tile
-needs, so one knob at a time can stop at a pair that is worse than one it
-never tried.  Each timing is
+search's piece size, band height and form (staged in shared memory or read
+through L1) are tried jointly (every combination): the best band depends on
+the piece size through the shared memory a tile needs, and the best form
+on both, so one knob at a time can stop at a setting that is worse than
+one it never tried.  Each timing is
 the median of `reps` runs bracketed by CUDA events on the step's stream.
 Results are cached in a JSON file keyed by the device name and a
 caller-chosen workload key, so a later run with the same shape only applies
@@ -35,9 +36,9 @@ SPACE = {
     "fs_band": (13, 9),
     "fs_group": (0, 1, 2, 3),
     "fs_fuse": (1, 0),
-    ("dep_range", "dep_band"): tuple((rg, bd) for rg in (16, 32) for bd in (0, 17, 9)),
+    ("dep_range", "dep_band", "dep_staged"): tuple((rg, bd, st) for st in (1, 0, 2) for rg in (16, 32)
+                                                   for bd in (0, 17, 9)),
     "dep_ctas_per_sm": (0, 1, 2),
-    "dep_staged": (1, 2, 0),
 }
 DEFAULTS = {"fs_band": 13, "fs_group": 0, "fs_fuse": 1, "dep_range": 16, "dep_band": 0, "dep_ctas_per_sm": 0,
             "dep_staged": 1}

@@ -40,9 +40,9 @@ def test_coordinate_descent_and_cache(tmp_path):
                             "dep_ctas_per_sm": 0, "dep_staged": 1}
     assert res["ms"] == pytest.approx(7.0)
     assert lad.knobs == res["knobs"] and not res["cached"]
-    # baseline, fs_band, fs_group, fs_fuse, the five other (piece size, band)
-    # pairs, grid size, staging
-    assert len(res["trials"]) == 1 + 1 + 3 + 1 + 5 + 2 + 2
+    # baseline, fs_band, fs_group, fs_fuse, the 17 other (piece size, band,
+    # form) settings, grid size
+    assert len(res["trials"]) == 1 + 1 + 3 + 1 + 17 + 2
     # the cache answers the same workload key without timing anything
     lad2 = FakeLadder()
     res2 = tune.tune(lad2, None, tag="t1", timer=lambda fn: pytest.fail("timed"), device="fake", cache_path=path)
