@@ -218,6 +218,133 @@ __device__ __forceinline__ int satd8_thread(const void *cur, const void *ref, lo
     return satd8_transform(v, mode);
 }
 
+// The SATD of the 8x8 block at (px, py) by a pair of lanes (lane ^ 1, both
+// in `mask`): this lane loads and transforms rows 4h .. 4h + 3 (h = lane &
+// 1), so a lane keeps 32 values and issues half the loads of satd8_thread,
+// all of them before its first transform.  The butterflies and the exact
+// sums are those of satd8_thread; mode 0's vertical stage that pairs rows y
+// and y + 4 exchanges values between the two lanes.  Both lanes return the
+// block's SATD.
+template <typename T>
+__device__ __forceinline__ int satd8_pair(const void *cur, const void *ref, long pitch, int W, int H, int px, int py,
+                                          int mvx, int mvy, int mode, unsigned mask, int *status = nullptr)
+{
+    const char *cb = static_cast<const char *>(cur);
+    const char *rb = static_cast<const char *>(ref);
+    constexpr int SPW = Traits<T>::SPW, BITS = 32 / SPW, WPR = 8 / SPW;
+    const int h = threadIdx.x & 1;
+    int rx0 = px + mvx;
+    bool cur_fast = px + 8 <= W;
+    bool ref_fast = rx0 >= 0 && (rx0 / SPW + WPR + 1) * SPW <= W;
+    // debug builds: as satd8_thread, but a failed check only zeroes the
+    // result (both lanes still reach the exchange)
+    const bool ok = !((cur_fast && !in_range(status, static_cast<long>(px + 8) * sizeof(T) - 1, pitch)) ||
+                      (ref_fast && !in_range(status, static_cast<long>(rx0 / SPW + WPR + 1) * 4 - 1, pitch)) ||
+                      !in_range(status, px, W));
+    if (!ok) {  // read the frame's first block instead
+        px = 0;
+        rx0 = 0;
+        cur_fast = ref_fast = false;
+    }
+    const int sh = (rx0 & (SPW - 1)) * BITS;
+    float v[32];
+    uint32_t cw[4][WPR], rw[4][WPR];
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+        const int cy = min(py + 4 * h + y, H - 1);
+        const int ry = min(max(py + 4 * h + y + mvy, 0), H - 1);
+        if (cur_fast) {
+            const char *row = cb + static_cast<long>(cy) * pitch + static_cast<long>(px) * sizeof(T);
+            if constexpr (WPR == 2) {
+                const uint2 q = __ldg(reinterpret_cast<const uint2 *>(row));
+                cw[y][0] = q.x;
+                cw[y][1] = q.y;
+            } else {
+                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(row));
+                cw[y][0] = q.x;
+                cw[y][1] = q.y;
+                cw[y][2] = q.z;
+                cw[y][3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < WPR; ++m) {
+                uint32_t w = 0;
+#pragma unroll
+                for (int e = 0; e < SPW; ++e)
+                    w |= static_cast<uint32_t>(ld_sample<T>(cb, pitch, min(px + m * SPW + e, W - 1), cy)) << (e * BITS);
+                cw[y][m] = w;
+            }
+        }
+        if (ref_fast) {
+            const uint32_t *rp = reinterpret_cast<const uint32_t *>(rb + static_cast<long>(ry) * pitch) + rx0 / SPW;
+            uint32_t raw[WPR + 1];
+#pragma unroll
+            for (int m = 0; m <= WPR; ++m) raw[m] = __ldg(rp + m);
+#pragma unroll
+            for (int m = 0; m < WPR; ++m) rw[y][m] = __funnelshift_r(raw[m], raw[m + 1], sh);
+        } else {
+#pragma unroll
+            for (int m = 0; m < WPR; ++m) {
+                uint32_t w = 0;
+#pragma unroll
+                for (int e = 0; e < SPW; ++e)
+                    w |= static_cast<uint32_t>(ld_sample<T>(rb, pitch, min(max(rx0 + m * SPW + e, 0), W - 1), ry))
+                         << (e * BITS);
+                rw[y][m] = w;
+            }
+        }
+    }
+#pragma unroll
+    for (int y = 0; y < 4; ++y)
+#pragma unroll
+        for (int x = 0; x < 8; ++x)
+            v[8 * y + x] = sample_f<T>(cw[y][x / SPW], x % SPW) - sample_f<T>(rw[y][x / SPW], x % SPW);
+    auto bfly = [&](int i, int j) {
+        const float a = v[i], b = v[j];
+        v[i] = a + b;
+        v[j] = a - b;
+    };
+    const int top = mode == 0 ? 4 : 2;  // horizontal stages: the row, or each 4-wide half
+#pragma unroll
+    for (int y = 0; y < 4; ++y)
+#pragma unroll
+        for (int s = 4; s >= 1; s >>= 1)
+            if (s <= top) {
+#pragma unroll
+                for (int x = 0; x < 8; ++x)
+                    if (!(x & s)) bfly(8 * y + x, 8 * y + x + s);
+            }
+    if (mode == 0) {  // rows y and y + 4: lane 0 keeps the sums, lane 1 the differences
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const float o = __shfl_xor_sync(mask, v[k], 1);
+            v[k] = h ? o - v[k] : v[k] + o;
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < 8; ++x)  // the remaining vertical stages, inside this lane's 4 rows
+#pragma unroll
+        for (int s = 2; s >= 1; s >>= 1)
+#pragma unroll
+            for (int y = 0; y < 4; ++y)
+                if (!(y & s)) bfly(8 * y + x, 8 * (y + s) + x);
+    float part[4];
+#pragma unroll
+    for (int y = 0; y < 4; ++y)
+        part[y] = (fabsf(v[8 * y]) + fabsf(v[8 * y + 1])) + (fabsf(v[8 * y + 2]) + fabsf(v[8 * y + 3])) +
+                  ((fabsf(v[8 * y + 4]) + fabsf(v[8 * y + 5])) + (fabsf(v[8 * y + 6]) + fabsf(v[8 * y + 7])));
+    const float half_sum = (part[0] + part[1]) + (part[2] + part[3]);  // exact: integers below 2^24
+    int r;
+    if (mode == 0) {
+        r = __float2int_rn(half_sum + __shfl_xor_sync(mask, half_sum, 1)) >> 2;
+    } else {
+        const int mine = __float2int_rn(half_sum) >> 1;  // this 8x4 half
+        r = mine + __shfl_xor_sync(mask, mine, 1);
+    }
+    return ok ? r : 0;
+}
+
 // The Hadamard part of the SATD of an 8x8 residual held in fp32 (integers
 // below 2^24 in magnitude, so every add is exact).
 //   mode 0: 8x8 Hadamard T = H8 D H8^T, (sum |T|) >> 2
@@ -506,17 +633,26 @@ __device__ void ctu_decide(CtuState<CTU> &st, const DecideIO &io, int x0, int y0
         }
     }
     __syncthreads();
-    // one thread per entry
-    for (int p = tid; p < min(st.npairs, (C::DMAX + 1) * C::NB8); p += nthr) {
-        const unsigned ent = st.pairs[p];
-        const int b = ent & 0xff, bx = b % C::N8, by = b / C::N8;
-        const int i0 = key_of_block<CTU>(__ffs(ent >> 8) - 1, bx, by);
-        const int v = satd8_thread<T>(io.cur, io.ref, io.pitch_bytes, g.W, g.H, x0 + 8 * bx, y0 + 8 * by, st.mvx[i0],
-                                      st.mvy[i0], io.satd_mode, io.status);
+    // two lanes per entry (satd8_pair): every thread runs the same number of
+    // rounds, so the pair mask is taken with the whole warp present
+    const int nwork = 2 * min(st.npairs, (C::DMAX + 1) * C::NB8);
+    const int rounds = (nwork + nthr - 1) / nthr;
+    for (int it = 0; it < rounds; ++it) {
+        const int w = tid + it * nthr;
+        const unsigned mask = __ballot_sync(0xffffffffu, w < nwork);  // whole pairs: nwork and nthr are even
+        if (w < nwork) {
+            const unsigned ent = st.pairs[w >> 1];
+            const int b = ent & 0xff, bx = b % C::N8, by = b / C::N8;
+            const int i0 = key_of_block<CTU>(__ffs(ent >> 8) - 1, bx, by);
+            const int v = satd8_pair<T>(io.cur, io.ref, io.pitch_bytes, g.W, g.H, x0 + 8 * bx, y0 + 8 * by,
+                                        st.mvx[i0], st.mvy[i0], io.satd_mode, mask, io.status);
+            if (!(w & 1)) {
 #pragma unroll
-        for (int d = 0; d <= C::DMAX; ++d) {
-            if (!((ent >> (8 + d)) & 1u)) continue;
-            atomicAdd(&st.satd[key_of_block<CTU>(d, bx, by)], v);
+                for (int d = 0; d <= C::DMAX; ++d) {
+                    if (!((ent >> (8 + d)) & 1u)) continue;
+                    atomicAdd(&st.satd[key_of_block<CTU>(d, bx, by)], v);
+                }
+            }
         }
     }
     __syncthreads();
