@@ -692,48 +692,53 @@ __device__ __forceinline__ void cp_async16(uint32_t *dst, const void *src)
 }
 
 // 10-bit SADs of one 8x8 current block for the TY candidates of a lane over
-// its staged window rows (see sads_core_u16; the packed halves of sum(a) +
-// sum(b) - 2 sum(min(a, b)) are folded by one dp2a).  ep: the lane's first
-// word of its first row; words 0, 1, 2, 3 hold its 8 samples.
+// its staged window rows: sum(a) + sum(b) - 2 sum(min(a, b)) per packed half
+// (see sads_core_u16).  Candidate i's word starts at sum(a) and takes
+// -2 min(a, b) per sample pair on the multiply-add pipe (m2 = -2, a runtime
+// value); sum(b) over its rows i..i+7 is the difference of two prefixes P of
+// the packed row sums, added at its last row; one dp2a folds the halves.
+// Everything is modulo 2^32: each half of the final word is that half's
+// sum of |a - b| (at most 32 * 1023), so the wrap-arounds in between cancel.
+// ep: the lane's first word of its first row; words 0, 1, 2, 3 hold its 8
+// samples.
 template <int TY>
-__device__ __forceinline__ void sads_staged_u16(const uint4 (&c)[8], uint32_t sa, uint32_t one, const uint32_t *ep,
+__device__ __forceinline__ void sads_staged_u16(const uint4 (&c)[8], uint32_t sa, uint32_t m2, const uint32_t *ep,
                                                 int rw, uint32_t (&acc)[TY])
 {
     constexpr int NR = 8 + TY - 1;
-    uint32_t mn[TY];
+    uint32_t x[TY];
 #pragma unroll
-    for (int i = 0; i < TY; ++i) mn[i] = 0;
-    uint32_t rs[NR];
-    uint32_t sb = 0;
+    for (int i = 0; i < TY; ++i) x[i] = sa;
+    uint32_t pf[NR + 1];  // pf[r + 1]: packed sum of rows 0..r
+    pf[0] = 0;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const uint32_t *q = ep + r * rw;
         const uint32_t w0 = q[0], w1 = q[1], w2 = q[2], w3 = q[3];
-        rs[r] = (w0 + w1) + (w2 + w3);
+        pf[r + 1] = (pf[r] + w0 + w1) + (w2 + w3);
 #pragma unroll
         for (int i = 0; i < TY; ++i) {
             const int j = r - i;
-            if (j >= 0 && j < 8) mn[i] = umad(min_u16x2(c[j].x, w0), one, mn[i]);
+            if (j >= 0 && j < 8) x[i] = umad(min_u16x2(c[j].x, w0), m2, x[i]);
         }
 #pragma unroll
         for (int i = 0; i < TY; ++i) {
             const int j = r - i;
-            if (j >= 0 && j < 8) mn[i] = umad(min_u16x2(c[j].y, w1), one, mn[i]);
+            if (j >= 0 && j < 8) x[i] = umad(min_u16x2(c[j].y, w1), m2, x[i]);
         }
 #pragma unroll
         for (int i = 0; i < TY; ++i) {
             const int j = r - i;
-            if (j >= 0 && j < 8) mn[i] = umad(min_u16x2(c[j].z, w2), one, mn[i]);
+            if (j >= 0 && j < 8) x[i] = umad(min_u16x2(c[j].z, w2), m2, x[i]);
         }
 #pragma unroll
         for (int i = 0; i < TY; ++i) {
             const int j = r - i;
-            if (j >= 0 && j < 8) mn[i] = umad(min_u16x2(c[j].w, w3), one, mn[i]);
+            if (j >= 0 && j < 8) x[i] = umad(min_u16x2(c[j].w, w3), m2, x[i]);
         }
-        sb = r < 8 ? sb + rs[r] : sb + rs[r] - rs[r - 8];
         if (r >= 7) {
             const int i = r - 7;  // candidate i is complete
-            acc[i] = __dp2a_lo(umad(mn[i], 0xfffffffeu, sa + sb), 0x0101u, acc[i]);
+            acc[i] = __dp2a_lo(x[i] + (pf[r + 1] - pf[i]), 0x0101u, acc[i]);
         }
     }
 }
@@ -975,6 +980,7 @@ __device__ __forceinline__ void stage_compute(const DependentBatch &b, const Sta
     for (int i = 0; i < TY; ++i) acc[i] = 0;
     const int nb = t.RS / 8;
     if constexpr (ES == 2) {
+        const uint32_t m2 = 0u - 2u * b.one;  // -2, unknown to the compiler: kept on the multiply-add pipe
 #pragma unroll 1
         for (int blk = 0; blk < nb * nb; ++blk) {
             const int bx = 8 * (blk % nb), by = 8 * (blk / nb);
@@ -985,7 +991,7 @@ __device__ __forceinline__ void stage_compute(const DependentBatch &b, const Sta
                 cv[j] = *reinterpret_cast<const uint4 *>(curw + (by + j) * sh.CW + bx / 2);
                 sa += (cv[j].x + cv[j].y) + (cv[j].z + cv[j].w);
             }
-            sads_staged_u16<TY>(cv, sa, b.one, win + (by + dy0 + r) * sh.RW + bx / 2, sh.RW, acc);
+            sads_staged_u16<TY>(cv, sa, m2, win + (by + dy0 + r) * sh.RW + bx / 2, sh.RW, acc);
         }
     } else {
         const uint32_t m = 1u << (32 - 8 * (xs - 4 * wq));  // xs - 4 wq in 1..4

@@ -374,6 +374,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 3) k_full_search(con
     // ---- search: per warp tile, warp = quadrant, its 8x8 blocks in Z order ----
     const int qx = (warp & 1) * S::Q, qy = (warp >> 1) * S::Q;
     const uint32_t one = b.one, m16 = b.one << 16;
+    const uint32_t m2 = 0u - 2u * b.one;  // -2, unknown to the compiler: kept on the multiply-add pipe
     const bool all_valid = K >= TY;  // else rows past +R exist and never win
 #pragma unroll 1
     for (int wt = wt0; wt < wt1; ++wt) {
@@ -432,40 +433,43 @@ __global__ void __launch_bounds__(128, sizeof(T) == 1 ? 4 : 3) k_full_search(con
                     c[j] = CL ? __ldg(reinterpret_cast<const uint4 *>(cp + j * cstride))
                               : *reinterpret_cast<const uint4 *>(cp + j * CTU);
                 const uint32_t sa = a8[((qy + by) / 8) * (CTU / 8) + (qx + bx) / 8];
-                // candidate i is complete after window row i + 7: there
-                // SAD = sum(a) + sum(b) - 2 sum(min), per packed half
-                uint32_t rs[NR];
-                uint32_t sb = 0;
+                // SAD = sum(a) + sum(b) - 2 sum(min), per packed half, modulo
+                // 2^32 (each half of the final word is at most 32 * 1023):
+                // candidate i's word starts at sum(a) and takes -2 min per
+                // sample pair; at its last row i + 7 it takes sum(b) as the
+                // difference of two prefixes of the packed row sums, and one
+                // dp2a adds its halves
+    #pragma unroll
+                for (int i = 0; i < TY; ++i) acc[i] = sa;
+                uint32_t pf[NR + 1];  // pf[r + 1]: packed sum of window rows 0..r
+                pf[0] = 0;
     #pragma unroll
                 for (int r = 0; r < NR; ++r) {
                     const uint32_t w0 = bp[r * P4], w1 = bp[r * P4 + 2], w2 = bp[r * P4 + 4], w3 = bp[r * P4 + 6];
-                    rs[r] = (w0 + w1) + (w2 + w3);
+                    pf[r + 1] = (pf[r] + w0 + w1) + (w2 + w3);
     #pragma unroll
                     for (int i = 0; i < TY; ++i) {
                         const int j = r - i;
-                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].x, w0), one, acc[i]);
+                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].x, w0), m2, acc[i]);
                     }
     #pragma unroll
                     for (int i = 0; i < TY; ++i) {
                         const int j = r - i;
-                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].y, w1), one, acc[i]);
+                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].y, w1), m2, acc[i]);
                     }
     #pragma unroll
                     for (int i = 0; i < TY; ++i) {
                         const int j = r - i;
-                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].z, w2), one, acc[i]);
+                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].z, w2), m2, acc[i]);
                     }
     #pragma unroll
                     for (int i = 0; i < TY; ++i) {
                         const int j = r - i;
-                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].w, w3), one, acc[i]);
+                        if (j >= 0 && j < 8) acc[i] = umad(min_u16x2(c[j].w, w3), m2, acc[i]);
                     }
-                    if (r < 8) sb += rs[r];
-                    else sb = sb + rs[r] - rs[r - 8];
                     if (r >= 7) {
-                        const int i = r - 7;
-                        // packed halves of sum(a) + sum(b) - 2 sum(min), added by one dp2a
-                        acc[i] = __dp2a_lo(umad(acc[i], 0xfffffffeu, sa + sb), 0x0101u, 0u);
+                        const int i = r - 7;  // candidate i is complete
+                        acc[i] = __dp2a_lo(acc[i] + (pf[r + 1] - pf[i]), 0x0101u, 0u);
                     }
                 }
             }
