@@ -220,6 +220,14 @@ LADDER_API void ladder_graph_destroy(ladder_graph_t *graph);
  *                                (the next tile's copies in flight during
  *                                the current one), 0 reads the windows
  *                                through L1
+ *   LADDER_TUNE_DEP_INHERIT      1 (default): a dependent CU searched in
+ *                                pieces whose four sub-CUs are evaluated
+ *                                around its own centre is not searched; its
+ *                                candidate SADs are the sums of theirs (the
+ *                                same candidates over four disjoint quarters
+ *                                of its samples), added by the lanes that
+ *                                search the sub-CUs; 0: every evaluated CU
+ *                                is searched
  * LADDER_E_INVAL for an unknown knob or value. */
 typedef enum {
     LADDER_TUNE_FS_BAND = 0,
@@ -228,10 +236,23 @@ typedef enum {
     LADDER_TUNE_DEP_CTAS_PER_SM = 3,
     LADDER_TUNE_FS_GROUP = 4,
     LADDER_TUNE_FS_FUSE = 5,
-    LADDER_TUNE_DEP_STAGED = 6
+    LADDER_TUNE_DEP_STAGED = 6,
+    LADDER_TUNE_DEP_INHERIT = 7
 } ladder_tune_knob;
 LADDER_API ladder_status ladder_set_tuning(ladder_t *ladder, int knob, int value);
 LADDER_API ladder_status ladder_get_tuning(const ladder_t *ladder, int knob, int *value);
+
+/* Work the dependent searches did (no counterpart in the paper; for
+ * measurement): the SAD-candidate evaluations (one 8x8 block at one
+ * candidate, 64 absolute differences) of the CUs they searched since the
+ * previous call, over every dependent launch of the handle on any stream.
+ * CUs whose SADs were summed from their sub-CUs' (LADDER_TUNE_DEP_INHERIT)
+ * are not counted, as the SAD tree's larger CUs are not counted for the
+ * reference rung.  Waits for `cuda_stream` (launches on other streams are
+ * counted once they have run), writes the count to *evals and resets it.
+ * LADDER_E_INVAL for a null handle or pointer; LADDER_E_CUDA if the copy
+ * fails. */
+LADDER_API ladder_status ladder_dependent_evals(ladder_t *ladder, void *cuda_stream, unsigned long long *evals);
 
 /* Test controls for the failure paths (no counterpart in the paper): they
  * exist so that a test can make a bounded device wait run out on purpose and

@@ -236,10 +236,15 @@ def block_satd(cur, ref, x0, y0, size, mvx, mvy, satd_mode: int = 0) -> int:
     return r
 
 
+_dummies: dict = {}
+
+
 def derive_rule(dep_size, dep: dict, d: int, x0: int, y0: int, ctu: int = 64):
     """Dependent-mode rule of CU (d, x0, y0): (cx, cy, allowed_leaf, allowed_split)."""
     W, H = dep_size
-    dummy = np.zeros((H, W), dtype=np.uint8)
+    dummy = _dummies.get((W, H))
+    if dummy is None:  # a placeholder frame of the rung's size (the rule reads no samples)
+        dummy = _dummies.setdefault((W, H), np.zeros((H, W), dtype=np.uint8))
     job, keep = _make_job(dummy, dummy, 0, ctu, 0, 0, dep)
     out = np.zeros(4, dtype=np.int32)
     _load().oracle_derive_rule(ctypes.byref(job), d, x0, y0, out.ctypes.data)

@@ -58,10 +58,11 @@ constexpr size_t kMaxMarks = 16;
 // stream used last (no wait: one stream is ordered), else a set not used
 // yet, else the least recently used one, waiting for that set's last batch.
 struct DepSet {
-    unsigned int *counts = nullptr;  // one per CU size class
+    unsigned int *counts = nullptr;  // two per CU size class (tasks, inherited CUs)
     unsigned long long *tasks[kSizeClasses] = {};
     unsigned int *pos[kSizeClasses] = {};
     unsigned int *sums[kSizeClasses] = {};
+    unsigned long long *up[kSizeClasses] = {};  // classes kFirstUpClass .. kSizeClasses - 2
     bool counts_dirty = false;  // counters not known to be zero (zeroed with the arena at init)
     cudaEvent_t done = nullptr;
     bool recorded = false;
@@ -95,7 +96,8 @@ struct ladder {
     int fs_ctas_per_sm = 1;      // resident full-search CTAs per SM
     // kernel shapes (ladder_set_tuning): results never depend on them
     int tune_fs_band = kFsBand, tune_fs_group = 0, tune_fs_fuse = 1, tune_dep_band = 0, tune_dep_range = 16,
-        tune_dep_ctas = 0, tune_dep_staged = 1;
+        tune_dep_ctas = 0, tune_dep_staged = 1, tune_dep_inherit = 1;
+    unsigned long long *d_evals = nullptr;  // running count of the dependent searches' SAD-candidate evaluations
     int mv_predictor = 0;  // 0: (0, 0); 1: spatial, decided in wavefront order (ladder_set_mv_predictor)
     // test controls (ladder_set_debug)
     int dbg_wait_polls = 0;   // 0: kMvpSpinDefault
@@ -538,6 +540,8 @@ ladder_status launch_dependent_tier(ladder_t *l, const Job *jobs, int n, cudaStr
         b.band = l->tune_dep_band;
         b.ctas_per_sm = l->tune_dep_ctas;
         b.staged = l->tune_dep_staged;
+        b.inherit = l->tune_dep_inherit;
+        b.evals = l->d_evals;
         b.satd_mode = l->geo.satd_mode;
         b.depth_lo = l->geo.dep_depth_lo;
         b.depth_hi = l->geo.dep_depth_hi;
@@ -549,6 +553,7 @@ ladder_status launch_dependent_tier(ladder_t *l, const Job *jobs, int n, cudaStr
             b.tasks[c] = ds.tasks[c];
             b.pos[c] = ds.pos[c];
             b.sums[c] = ds.sums[c];
+            b.up[c] = ds.up[c];
             b.cap[c] = l->task_cap[c];
         }
         for (int r = 0; r < l->geo.n_rungs; ++r) b.rung[r] = l->info[r];
@@ -566,7 +571,7 @@ ladder_status launch_dependent_tier(ladder_t *l, const Job *jobs, int n, cudaStr
         // unless a launch of an earlier batch failed
         cudaError_t e = cudaSuccess;
         if (ds.counts_dirty) {
-            e = cudaMemsetAsync(ds.counts, 0, kSizeClasses * sizeof(unsigned int), s);
+            e = cudaMemsetAsync(ds.counts, 0, 2 * kSizeClasses * sizeof(unsigned int), s);
             if (e != cudaSuccess) return cuda_fail(l, e, "task counters");
         }
         ds.counts_dirty = true;
@@ -670,6 +675,7 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
         l->task_cap[c] = static_cast<unsigned int>(std::min<size_t>(cap, 0xffffffffu));
         task_bytes += kDepSets * (align_up(cap * 8, 256) + align_up(cap * 4, 256));
         if (c >= kFirstSummedClass) task_bytes += kDepSets * align_up(cap * kr2 * 4, 256);
+        if (c >= kFirstUpClass && c < kSizeClasses - 1) task_bytes += kDepSets * align_up(cap * 8, 256);
     }
     const size_t fixed = 256 + task_bytes;
     l->arena_bytes = fixed + per_slot * geometry->max_frames;
@@ -681,7 +687,9 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
     }
     char *base = static_cast<char *>(l->arena);
     l->d_status = reinterpret_cast<int *>(base);
-    static_assert(64 + kDepSets * 64 <= 256, "counters inside the arena header");
+    l->d_evals = reinterpret_cast<unsigned long long *>(base + 8);
+    static_assert(64 + kDepSets * 64 <= 256 && 2 * kSizeClasses * sizeof(unsigned int) <= 64,
+                  "counters inside the arena header");
     {
         char *tp = base + 256;
         for (int k = 0; k < kDepSets; ++k) {
@@ -695,6 +703,10 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
                 if (c >= kFirstSummedClass) {
                     ds.sums[c] = reinterpret_cast<unsigned int *>(tp);
                     tp += align_up(static_cast<size_t>(l->task_cap[c]) * kr2 * 4, 256);
+                }
+                if (c >= kFirstUpClass && c < kSizeClasses - 1) {
+                    ds.up[c] = reinterpret_cast<unsigned long long *>(tp);
+                    tp += align_up(static_cast<size_t>(l->task_cap[c]) * 8, 256);
                 }
             }
         }
@@ -1690,6 +1702,10 @@ ladder_status ladder_set_tuning(ladder_t *l, int knob, int value)
         if (value < 0 || value > 2) return fail(l, LADDER_E_INVAL, "staged %d (0, 1 or 2)", value);
         l->tune_dep_staged = value;
         return LADDER_OK;
+    case LADDER_TUNE_DEP_INHERIT:
+        if (value != 0 && value != 1) return fail(l, LADDER_E_INVAL, "inherit %d (0 or 1)", value);
+        l->tune_dep_inherit = value;
+        return LADDER_OK;
     default:
         return fail(l, LADDER_E_INVAL, "unknown tuning knob %d", knob);
     }
@@ -1724,8 +1740,23 @@ ladder_status ladder_get_tuning(const ladder_t *l, int knob, int *value)
     case LADDER_TUNE_FS_GROUP: *value = l->tune_fs_group; return LADDER_OK;
     case LADDER_TUNE_FS_FUSE: *value = l->tune_fs_fuse; return LADDER_OK;
     case LADDER_TUNE_DEP_STAGED: *value = l->tune_dep_staged; return LADDER_OK;
+    case LADDER_TUNE_DEP_INHERIT: *value = l->tune_dep_inherit; return LADDER_OK;
     default: return LADDER_E_INVAL;
     }
+}
+
+ladder_status ladder_dependent_evals(ladder_t *l, void *cuda_stream, unsigned long long *evals)
+{
+    if (!l || !evals) return LADDER_E_INVAL;
+    TraceRange tr("ladder_dependent_evals");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    unsigned long long v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, l->d_evals, sizeof v, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(l->d_evals, 0, sizeof v, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(l, e, "dependent evaluation count");
+    *evals = v;
+    return LADDER_OK;
 }
 
 long ladder_device_bytes(const ladder_t *l) { return l ? static_cast<long>(l->arena_bytes) : 0; }

@@ -76,6 +76,9 @@ enum : uint8_t {
     kRuleEvaluated = 1,  // reachable, inside the 8-aligned frame, allowed as a leaf
     kRuleCanSplit = 2,   // reachable and (forced or allowed to split)
     kRuleReachable = 4,  // every ancestor may split
+    // (8 is dev::kPresent)
+    kRuleInherited = 16,  // evaluated, searched in pieces, and its four sub-CUs are evaluated around the same
+                          // centre: its candidate SADs are their sums (the sub-CUs' lanes add into its table)
 };
 
 // Division by a divisor fixed for a whole launch as a multiply-high, an
@@ -307,9 +310,16 @@ struct DependentItem {
 // the centre (cx & 0xffff | cy << 16) in the high word.  CUs larger than the
 // batch's range (16 or 32) are searched in range x range pieces whose
 // candidate SADs add up in a per-CU table of (2r+1)^2 sums (classes 2 and 3
-// have table room).
+// have table room).  Such a CU whose four sub-CUs are evaluated around its
+// own centre is inherited: it has no task, its table (a slot counted down
+// from the top of the class's capacity) takes the sums of its sub-CUs'
+// SADs, added by the lanes that search them; up[c][task] names, for a
+// searched CU, the table slots of its inherited parent and grandparent
+// (0xffffffff: none; the chain stops at the first ancestor not inherited).
 constexpr int kSizeClasses = 4;
 constexpr int kFirstSummedClass = 2;
+constexpr int kFirstUpClass = kFirstSummedClass - 1;  // classes whose CUs may have an inherited ancestor
+constexpr uint32_t kNoUp = 0xffffffffu;
 constexpr int kDepBand = 17;  // candidate rows per lane task (9 for r <= 4)
 
 struct DependentBatch {
@@ -319,6 +329,7 @@ struct DependentBatch {
     int band;               // candidate rows per lane task: 9 or 17
     int ctas_per_sm;        // search grid: CTAs per SM (0: as many as fit)
     int staged;             // 1: each tile's windows staged in shared memory first (10-bit, r >= 4); 0: read from L1
+    int inherit;            // 1: CUs whose sub-CUs share their centre take their SADs as sums (kRuleInherited)
     int satd_mode;
     int depth_lo, depth_hi, use_ref_mv;
     int total_ctas;         // CTUs of the batch
@@ -326,8 +337,12 @@ struct DependentBatch {
     unsigned long long *tasks[kSizeClasses];  // per size class, capacity cap[c]
     unsigned int *pos[kSizeClasses];          // per task: the CU's origin, x | y << 16
     unsigned int *sums[kSizeClasses];         // classes >= kFirstSummedClass: cap[c] x (2r+1)^2
+    unsigned long long *up[kSizeClasses];     // classes kFirstUpClass .. kSizeClasses - 2: per task, the
+                                              // inherited ancestors' table slots (low word parent, high grandparent)
     unsigned int cap[kSizeClasses];
-    unsigned int *counts;   // kSizeClasses counters, zero before the rules kernel
+    unsigned int *counts;   // 2 kSizeClasses counters, zero before the rules kernel: tasks per class, then
+                            // inherited CUs per class (their table slots count down from cap[c] - 1)
+    unsigned long long *evals;  // running count of the SAD-candidate evaluations searched (8x8 block x candidate)
     uint32_t one;           // 1, as an operand the compiler cannot fold
     RungInfo rung[kMaxRungs];
     DependentItem item[kMaxDepItems];

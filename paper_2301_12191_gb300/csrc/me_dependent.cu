@@ -59,14 +59,18 @@ __global__ void __launch_bounds__(kRulesThreads) k_dep_rules(const __grid_consta
     using C = dev::Ctu<CTU>;
     constexpr int NK = C::NKEY;
     static_assert(NK <= kRulesThreads, "one thread per CU");
+    static_assert(((kRuleEvaluated | kRuleCanSplit | kRuleReachable | kRuleInherited) & dev::kPresent) == 0,
+                  "rule flags and the present flag share one byte");
     constexpr int NBIG = key_offset(C::DMAX - kFirstSummedClass + 1);  // CUs of 32x32 and up
     const int tid = threadIdx.x;
     const bool mine = tid < NK;
 
-    __shared__ uint8_t s_leaf[NK], s_splitok[NK];
-    __shared__ unsigned int s_cnt[kSizeClasses], s_base[kSizeClasses];
+    __shared__ uint8_t s_leaf[NK], s_splitok[NK], s_ev[NK], s_inh[NK];
+    __shared__ uint32_t s_ctr[NK];  // centres, cx | cy << 16
+    __shared__ int s_pos[NK];       // list places (searched) or table slots (inherited), -1: none
+    __shared__ unsigned int s_cnt[2 * kSizeClasses], s_base[2 * kSizeClasses];
     __shared__ int s_big[NBIG > 0 ? NBIG : 1];  // list places of CUs searched in pieces (-1: none)
-    if (tid < kSizeClasses) s_cnt[tid] = 0;
+    if (tid < 2 * kSizeClasses) s_cnt[tid] = 0;
 
     const int ri = item_of(b);
     const DependentItem &a = b.item[ri];
@@ -114,17 +118,36 @@ __global__ void __launch_bounds__(kRulesThreads) k_dep_rules(const __grid_consta
 
     // reachability (every ancestor may split) and the rule flags
     uint8_t f = 0;
+    const int cxl = li % n, cyl = li / n;
     if (present) {
         f = dev::kPresent;
-        const int cxl = li % n, cyl = li / n;
         bool reach = true;
         for (int e = 0; e < d; ++e)
             reach = reach && s_splitok[dev::key_index(e, (cyl >> (d - e)) * (1 << e) + (cxl >> (d - e)))];
         if (reach) f |= kRuleReachable;
         if (reach && s_leaf[tid]) f |= kRuleEvaluated;
         if (reach && s_splitok[tid]) f |= kRuleCanSplit;
-        if (f & kRuleEvaluated) atomicAdd(&s_cnt[C::DMAX - d], 1u);  // size class of an S = CTU >> d CU
     }
+    const uint32_t ctr = static_cast<uint32_t>(static_cast<uint16_t>(cx)) |
+                         (static_cast<uint32_t>(static_cast<uint16_t>(cy)) << 16);
+    if (mine) {
+        s_ev[tid] = f & kRuleEvaluated;
+        s_ctr[tid] = ctr;
+    }
+    __syncthreads();
+    // a CU searched in pieces whose four sub-CUs are evaluated around its own
+    // centre: its SADs are the sums of theirs (the same candidates over four
+    // disjoint quarters of its samples)
+    if (b.inherit && (f & kRuleEvaluated) && S > b.range && d < C::DMAX) {
+        bool all = true;
+        for (int q = 0; q < 4; ++q) {
+            const int ci = dev::key_index(d + 1, (2 * cyl + (q >> 1)) * (2 * n) + 2 * cxl + (q & 1));
+            all = all && s_ev[ci] && s_ctr[ci] == ctr;
+        }
+        if (all) f |= kRuleInherited;
+    }
+    const int c = C::DMAX - d;  // size class: CU size 8 << c
+    if (f & kRuleEvaluated) atomicAdd(&s_cnt[(f & kRuleInherited) ? kSizeClasses + c : c], 1u);
     const long nk_frame = static_cast<long>(g.ctu_cols) * g.ctu_rows * NK;  // key slots of the frame
     if (mine && in_range(b.status, kbase + tid, nk_frame)) {
         reinterpret_cast<int16_t *>(a.block + rinf.off.dep_cx)[kbase + tid] = cx;
@@ -133,34 +156,66 @@ __global__ void __launch_bounds__(kRulesThreads) k_dep_rules(const __grid_consta
         reinterpret_cast<unsigned long long *>(a.block + rinf.off.keys)[kbase + tid] = ~0ull;
     }
     __syncthreads();
-    if (tid < kSizeClasses) {
+    if (tid < 2 * kSizeClasses) {
+        const int cl = tid % kSizeClasses;
         const unsigned int cnt = s_cnt[tid];
         unsigned int base = 0;
         if (cnt) base = atomicAdd(&b.counts[tid], cnt);
-        if (cnt && base + cnt > b.cap[tid]) atomicExch(b.status, kStatusTaskOverflow);
+        if (cnt && base + cnt > b.cap[cl]) atomicExch(b.status, kStatusTaskOverflow);
         s_base[tid] = base;
         s_cnt[tid] = 0;
+        // the SAD-candidate evaluations (8x8 blocks x candidates) searched for
+        // this CTU's tasks of class tid
+        if (tid < kSizeClasses && cnt && b.evals) {
+            const unsigned long long K = 2 * b.r + 1;
+            atomicAdd(b.evals, (static_cast<unsigned long long>(cnt) << (2 * tid)) * K * K);
+        }
     }
     __syncthreads();
 
-    // the CU's task: item | key slot << 8, centre in the high word; its origin
+    // a searched CU's task: item | key slot << 8, centre in the high word; its
+    // origin.  An inherited CU: a table slot from the top of the class's room.
     int pos = -1;
     if (f & kRuleEvaluated) {
-        const int c = C::DMAX - d;  // size class: CU size 8 << c
-        const unsigned int p = s_base[c] + atomicAdd(&s_cnt[c], 1u);
-        if (p < b.cap[c]) {
-            const uint32_t lo = static_cast<uint32_t>(ri) | (static_cast<uint32_t>(kbase + tid) << 8);
-            const uint32_t hi = static_cast<uint32_t>(static_cast<uint16_t>(cx)) |
-                                (static_cast<uint32_t>(static_cast<uint16_t>(cy)) << 16);
-            b.tasks[c][p] = (static_cast<unsigned long long>(hi) << 32) | lo;
-            b.pos[c][p] = static_cast<unsigned int>(cu_x) | (static_cast<unsigned int>(cu_y) << 16);
-            pos = static_cast<int>(p);
+        if (f & kRuleInherited) {
+            const unsigned int k = s_base[kSizeClasses + c] + atomicAdd(&s_cnt[kSizeClasses + c], 1u);
+            if (k < b.cap[c]) pos = static_cast<int>(b.cap[c] - 1 - k);
+        } else {
+            const unsigned int p = s_base[c] + atomicAdd(&s_cnt[c], 1u);
+            if (p < b.cap[c]) {
+                const uint32_t lo = static_cast<uint32_t>(ri) | (static_cast<uint32_t>(kbase + tid) << 8);
+                b.tasks[c][p] = (static_cast<unsigned long long>(ctr) << 32) | lo;
+                b.pos[c][p] = static_cast<unsigned int>(cu_x) | (static_cast<unsigned int>(cu_y) << 16);
+                pos = static_cast<int>(p);
+            }
         }
     }
     if (mine && in_range(b.status, kbase + tid, nk_frame)) reinterpret_cast<int *>(a.block + rinf.off.dep_slot)[kbase + tid] = pos;
+    if (mine) {
+        s_pos[tid] = pos;
+        s_inh[tid] = (f & kRuleInherited) ? 1 : 0;
+    }
+    __syncthreads();
+    // a searched CU's inherited ancestors (parent, then grandparent while the
+    // parent is inherited too): its lanes add their SADs into their tables
+    if ((f & kRuleEvaluated) && !(f & kRuleInherited) && pos >= 0 && c >= kFirstUpClass && c < kSizeClasses - 1 &&
+        c < C::DMAX) {
+        uint32_t up1 = kNoUp, up2 = kNoUp;
+        if (d >= 1) {
+            const int pi = dev::key_index(d - 1, (cyl >> 1) * (n >> 1) + (cxl >> 1));
+            if (s_inh[pi] && s_pos[pi] >= 0) {
+                up1 = static_cast<uint32_t>(s_pos[pi]);
+                if (d >= 2) {
+                    const int gi = dev::key_index(d - 2, (cyl >> 2) * (n >> 2) + (cxl >> 2));
+                    if (s_inh[gi] && s_pos[gi] >= 0) up2 = static_cast<uint32_t>(s_pos[gi]);
+                }
+            }
+        }
+        b.up[c][pos] = static_cast<unsigned long long>(up1) | (static_cast<unsigned long long>(up2) << 32);
+    }
     if (tid < NBIG) s_big[tid] = S > b.range ? pos : -1;
     __syncthreads();
-    // zeroed sum tables of the CUs searched in pieces
+    // zeroed sum tables of the CUs searched in pieces and of the inherited ones
     const int KK = (2 * b.r + 1) * (2 * b.r + 1);
     for (int i = 0; i < NBIG; ++i) {
         if (s_big[i] < 0) continue;
@@ -431,6 +486,32 @@ __device__ __forceinline__ int sad_bits(int S, int bit_depth)
     return (S == 8 ? 6 : S == 16 ? 8 : S == 32 ? 10 : 12) + bit_depth;
 }
 
+// A searched CU's lane adds its candidates' SADs into the tables of the CU's
+// inherited ancestors (kRuleInherited), every candidate once: no padding
+// lanes (the caller's), no rows a clamped band shares with the band before
+// it, no rows past +r.
+template <int TY>
+__device__ __forceinline__ void add_to_ancestors(const DependentBatch &b, int c, unsigned int u, int dxi, int dy0,
+                                                 int b0, const uint32_t (&acc)[TY])
+{
+    if (c < kFirstUpClass || c >= kSizeClasses - 1 || !b.inherit) return;
+    const int r = b.r, K = 2 * r + 1;
+    const unsigned long long up = __ldcg(b.up[c] + u);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const uint32_t slot = static_cast<uint32_t>(up >> (32 * k));
+        const int cls = c + 1 + k;
+        if (slot == kNoUp || cls >= kSizeClasses || !in_range(b.status, slot, b.cap[cls])) return;
+        unsigned int *sum = b.sums[cls] + static_cast<long>(slot) * (K * K);
+#pragma unroll
+        for (int i = 0; i < TY; ++i) {
+            const int dyo = dy0 + i;
+            if (dyo >= b0 && dyo <= r && in_range(b.status, (dyo + r) * K + dxi, K * K))
+                atomicAdd(sum + (dyo + r) * K + dxi, acc[i]);
+        }
+    }
+}
+
 template <typename T, int TY>
 __device__ __forceinline__ void search_tile(const DependentBatch &b, int c, int lt, unsigned int ncu, int per_cu,
                                             const FastDiv &div_cu, const FastDiv &div_k, int rb, int lane)
@@ -488,6 +569,7 @@ __device__ __forceinline__ void search_tile(const DependentBatch &b, int c, int 
         }
     }
 
+    if (traw < ntask) add_to_ancestors<TY>(b, c, u, dxi, dy0, b0, acc);
     if (nr > 1) {
         // add this range's SADs to the CU's table; every candidate exactly
         // once: no padding lanes, no rows a clamped band shares with the
@@ -1012,6 +1094,7 @@ __device__ __forceinline__ void stage_compute(const DependentBatch &b, const Sta
     }
 
     const unsigned int ucu = q >> (2 * t.lg);
+    if (traw < t.ntask) add_to_ancestors<TY>(b, t.c, ucu, dxi, dy0, b0, acc);
     const unsigned long long task = __ldcg(b.tasks[t.c] + ucu);
     const uint32_t lo = static_cast<uint32_t>(task);
     const DependentItem &a = b.item[lo & 0xffu];
@@ -1141,7 +1224,7 @@ __global__ void __launch_bounds__(kDecideThreads, 8) k_dep_decide(const __grid_c
     dev::chain_entry();
     // the search has completed: its task counters go back to zero for the
     // next batch (they rest at zero between batches)
-    if (blockIdx.x == 0 && threadIdx.x < kSizeClasses) b.counts[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < 2 * kSizeClasses) b.counts[threadIdx.x] = 0;
     using C = dev::Ctu<CTU>;
     const DependentItem &a = b.item[item_of(b)];
     const RungInfo &rinf = b.rung[a.rung];

@@ -150,12 +150,14 @@ SIGNATURES = [
     ("ladder_set_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     ("ladder_get_tuning", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("ladder_set_debug", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    ("ladder_dependent_evals", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.POINTER(ctypes.c_ulonglong)]),
 ]
 
 KERNEL_KINDS = ("full_search", "decide", "dependent", "fill_keys", "dep_rules", "dep_decide", "decide_qps",
                 "subpel", "decide_mvp")
 TUNE_KNOBS = {"fs_band": 0, "dep_band": 1, "dep_range": 2, "dep_ctas_per_sm": 3, "fs_group": 4, "fs_fuse": 5,
-              "dep_staged": 6}
+              "dep_staged": 6, "dep_inherit": 7}
 DEBUG_CONTROLS = {"wait_polls": 0, "lost_handoff": 1}
 
 _lib = None
@@ -506,6 +508,14 @@ class Ladder:
             _call(self.handle, "ladder_get_tuning", self.handle, k, ctypes.byref(v))
             out[name] = v.value
         return out
+
+    def dependent_evals(self, stream=None) -> int:
+        """SAD-candidate evaluations the dependent searches made since the
+        previous call (CUs summed from their sub-CUs not counted); resets
+        the count."""
+        v = ctypes.c_ulonglong()
+        _call(self.handle, "ladder_dependent_evals", self.handle, _stream_handle(stream), ctypes.byref(v))
+        return int(v.value)
 
     def device_bytes(self) -> int:
         return int(load().ladder_device_bytes(self.handle))

@@ -41,17 +41,21 @@ SPACE = {
     "dep_ctas_per_sm": (0, 1, 2),
 }
 DEFAULTS = {"fs_band": 13, "fs_group": 0, "fs_fuse": 1, "dep_range": 16, "dep_band": 0, "dep_ctas_per_sm": 0,
-            "dep_staged": 1}
+            "dep_staged": 1, "dep_inherit": 1}
 
 
 def knob_values(name: str) -> tuple:
-    """Every value the search may give knob `name` (alone or in a joint pair)."""
+    """Every value the search may give knob `name` (alone or in a joint
+    pair); a knob outside the search keeps its default (dep_inherit: summing
+    a CU's SADs from its sub-CUs' only removes work, so it stays on)."""
     for key, values in SPACE.items():
         if key == name:
             return tuple(values)
         if isinstance(key, tuple) and name in key:
             i = key.index(name)
             return tuple(sorted({v[i] for v in values}))
+    if name in DEFAULTS:
+        return (DEFAULTS[name],)
     raise KeyError(name)
 
 

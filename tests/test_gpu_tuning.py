@@ -30,6 +30,8 @@ SETTINGS = [
     {"dep_staged": 2, "dep_band": 17},
     {"dep_staged": 0, "dep_band": 17},
     {"dep_range": 32, "dep_band": 17},
+    {"dep_inherit": 0},
+    {"dep_inherit": 0, "dep_range": 32, "dep_staged": 0},
 ]
 
 CASES = [
@@ -69,7 +71,8 @@ def test_knobs_do_not_change_decisions(src, rungs, bd, R, r):
 
 def test_bad_knobs_are_refused():
     with L.Ladder([(64, 64)], 0, ctu_size=32, max_frames=1) as lad:
-        for knobs in ({"fs_band": 9}, {"fs_band": 11}, {"dep_range": 8}, {"dep_band": 5}, {"dep_ctas_per_sm": 9}, {"fs_group": 5}):
+        for knobs in ({"fs_band": 9}, {"fs_band": 11}, {"dep_range": 8}, {"dep_band": 5}, {"dep_ctas_per_sm": 9}, {"fs_group": 5},
+                      {"dep_inherit": 2}):
             with pytest.raises(L.LadderError):
                 lad.set_tuning(**knobs)
         assert lad.tuning() == tune.DEFAULTS

@@ -37,7 +37,7 @@ def test_coordinate_descent_and_cache(tmp_path):
     path = str(tmp_path / "cache.json")
     res = tune.tune(lad, None, tag="t1", timer=timer, device="fake", cache_path=path)
     assert res["knobs"] == {"fs_band": 9, "fs_group": 0, "fs_fuse": 1, "dep_range": 32, "dep_band": 0,
-                            "dep_ctas_per_sm": 0, "dep_staged": 1}
+                            "dep_ctas_per_sm": 0, "dep_staged": 1, "dep_inherit": 1}
     assert res["ms"] == pytest.approx(7.0)
     assert lad.knobs == res["knobs"] and not res["cached"]
     # baseline, fs_band, fs_group, fs_fuse, the 17 other (piece size, band,
