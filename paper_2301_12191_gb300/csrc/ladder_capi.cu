@@ -58,7 +58,7 @@ constexpr size_t kMaxMarks = 16;
 // stream used last (no wait: one stream is ordered), else a set not used
 // yet, else the least recently used one, waiting for that set's last batch.
 struct DepSet {
-    unsigned int *counts = nullptr;  // two per CU size class (tasks, inherited CUs)
+    unsigned int *counts = nullptr;  // kDepCounters: tasks and inherited CUs per CU size class, next tile
     unsigned long long *tasks[kSizeClasses] = {};
     unsigned int *pos[kSizeClasses] = {};
     unsigned int *sums[kSizeClasses] = {};
@@ -571,7 +571,7 @@ ladder_status launch_dependent_tier(ladder_t *l, const Job *jobs, int n, cudaStr
         // unless a launch of an earlier batch failed
         cudaError_t e = cudaSuccess;
         if (ds.counts_dirty) {
-            e = cudaMemsetAsync(ds.counts, 0, 2 * kSizeClasses * sizeof(unsigned int), s);
+            e = cudaMemsetAsync(ds.counts, 0, kDepCounters * sizeof(unsigned int), s);
             if (e != cudaSuccess) return cuda_fail(l, e, "task counters");
         }
         ds.counts_dirty = true;
@@ -688,7 +688,7 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
     char *base = static_cast<char *>(l->arena);
     l->d_status = reinterpret_cast<int *>(base);
     l->d_evals = reinterpret_cast<unsigned long long *>(base + 8);
-    static_assert(64 + kDepSets * 64 <= 256 && 2 * kSizeClasses * sizeof(unsigned int) <= 64,
+    static_assert(64 + kDepSets * 64 <= 256 && kDepCounters * sizeof(unsigned int) <= 64,
                   "counters inside the arena header");
     {
         char *tp = base + 256;

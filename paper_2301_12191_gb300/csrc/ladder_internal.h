@@ -320,6 +320,10 @@ constexpr int kSizeClasses = 4;
 constexpr int kFirstSummedClass = 2;
 constexpr int kFirstUpClass = kFirstSummedClass - 1;  // classes whose CUs may have an inherited ancestor
 constexpr uint32_t kNoUp = 0xffffffffu;
+// counters of one set of task lists: tasks per class, inherited CUs per
+// class, then the staged search's next tile (zero before each batch)
+constexpr int kTileCounter = 2 * kSizeClasses;
+constexpr int kDepCounters = 2 * kSizeClasses + 1;
 constexpr int kDepBand = 17;  // candidate rows per lane task (9 for r <= 4)
 
 struct DependentBatch {
@@ -340,8 +344,8 @@ struct DependentBatch {
     unsigned long long *up[kSizeClasses];     // classes kFirstUpClass .. kSizeClasses - 2: per task, the
                                               // inherited ancestors' table slots (low word parent, high grandparent)
     unsigned int cap[kSizeClasses];
-    unsigned int *counts;   // 2 kSizeClasses counters, zero before the rules kernel: tasks per class, then
-                            // inherited CUs per class (their table slots count down from cap[c] - 1)
+    unsigned int *counts;   // kDepCounters counters, zero before the rules kernel: tasks per class, inherited
+                            // CUs per class (their table slots count down from cap[c] - 1), the next tile
     unsigned long long *evals;  // running count of the SAD-candidate evaluations searched (8x8 block x candidate)
     uint32_t one;           // 1, as an operand the compiler cannot fold
     RungInfo rung[kMaxRungs];

@@ -1162,6 +1162,7 @@ __global__ void __launch_bounds__(kStageThreads, 4)
     extern __shared__ __align__(16) uint32_t s_win[];
     __shared__ StageSlots s_slots[2];
     __shared__ long s_ln[kSizeClasses], s_tn[kSizeClasses];  // lane tasks and tiles per size class
+    __shared__ long s_next;  // this CTA's next tile
     const int r = b.r, K = 2 * r + 1;
     const int per_cu = K * ((K + TY - 1) / TY);
     const int code_max = 4 * r * K + 4 * r + 1;
@@ -1184,6 +1185,10 @@ __global__ void __launch_bounds__(kStageThreads, 4)
 #pragma unroll 1
     for (;;) {
         uint32_t *buf = s_win + bi * half;
+        // tiles after the first of each CTA are handed out in order as CTAs
+        // free up (the tiles of the largest CUs come first): the grid's
+        // tail is one tile of the smallest CUs
+        if (threadIdx.x == 0) s_next = gridDim.x + static_cast<long>(atomicAdd(b.counts + kTileCounter, 1u));
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
         if (s_slots[bi].any_edge) {
@@ -1195,7 +1200,7 @@ __global__ void __launch_bounds__(kStageThreads, 4)
             __syncthreads();
         }
         // the next tile of this CTA into the other buffer, in flight during this one
-        const long next = tile + gridDim.x;
+        const long next = s_next;
         if (pipelined && next < total) {
             const StageTile tnext = stage_tile<ES, TY>(b, next, per_cu, div_cu, s_ln, s_tn);
             stage_slots_setup<ES>(b, tnext, s_slots[bi ^ 1]);
@@ -1224,7 +1229,7 @@ __global__ void __launch_bounds__(kDecideThreads, 8) k_dep_decide(const __grid_c
     dev::chain_entry();
     // the search has completed: its task counters go back to zero for the
     // next batch (they rest at zero between batches)
-    if (blockIdx.x == 0 && threadIdx.x < 2 * kSizeClasses) b.counts[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < kDepCounters) b.counts[threadIdx.x] = 0;
     using C = dev::Ctu<CTU>;
     const DependentItem &a = b.item[item_of(b)];
     const RungInfo &rinf = b.rung[a.rung];
