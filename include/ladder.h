@@ -226,8 +226,9 @@ LADDER_API void ladder_graph_destroy(ladder_graph_t *graph);
  *                                candidate SADs are the sums of theirs (the
  *                                same candidates over four disjoint quarters
  *                                of its samples), added by the lanes that
- *                                search the sub-CUs; 0: every evaluated CU
- *                                is searched
+ *                                search the sub-CUs or, where these have
+ *                                sum tables, from those tables; 0: every
+ *                                evaluated CU is searched
  * LADDER_E_INVAL for an unknown knob or value. */
 typedef enum {
     LADDER_TUNE_FS_BAND = 0,

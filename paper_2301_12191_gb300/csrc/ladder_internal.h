@@ -311,11 +311,14 @@ struct DependentItem {
 // batch's range (16 or 32) are searched in range x range pieces whose
 // candidate SADs add up in a per-CU table of (2r+1)^2 sums (classes 2 and 3
 // have table room).  Such a CU whose four sub-CUs are evaluated around its
-// own centre is inherited: it has no task, its table (a slot counted down
-// from the top of the class's capacity) takes the sums of its sub-CUs'
-// SADs, added by the lanes that search them; up[c][task] names, for a
-// searched CU, the table slots of its inherited parent and grandparent
-// (0xffffffff: none; the chain stops at the first ancestor not inherited).
+// own centre is inherited: it has no task and its SADs are the sums of its
+// sub-CUs'.  If they are single pieces, its table (a slot counted down from
+// the top of the class's capacity) takes the SADs their lanes add into it,
+// named by up[c][task] of each sub-CU (low word; 0xffffffff: none).  If they
+// have tables of their own (a 64x64 CU of 32x32 sub-CUs at pieces of 16), it
+// has none: the decisions add the four tables entry by entry.  (The high
+// word, a grandparent, is never set: an inherited parent has a table, so the
+// grandparent's table is the decisions' sum.)
 constexpr int kSizeClasses = 4;
 constexpr int kFirstSummedClass = 2;
 constexpr int kFirstUpClass = kFirstSummedClass - 1;  // classes whose CUs may have an inherited ancestor

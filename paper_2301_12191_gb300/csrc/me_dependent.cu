@@ -147,7 +147,12 @@ __global__ void __launch_bounds__(kRulesThreads) k_dep_rules(const __grid_consta
         if (all) f |= kRuleInherited;
     }
     const int c = C::DMAX - d;  // size class: CU size 8 << c
-    if (f & kRuleEvaluated) atomicAdd(&s_cnt[(f & kRuleInherited) ? kSizeClasses + c : c], 1u);
+    // an inherited CU whose sub-CUs are single pieces takes a table that their
+    // lanes add into; one whose sub-CUs have tables of their own has none: the
+    // decisions add the four sub-CUs' tables entry by entry
+    const bool inh_table = (f & kRuleInherited) && (S >> 1) <= b.range;
+    if ((f & kRuleEvaluated) && (!(f & kRuleInherited) || inh_table))
+        atomicAdd(&s_cnt[(f & kRuleInherited) ? kSizeClasses + c : c], 1u);
     const long nk_frame = static_cast<long>(g.ctu_cols) * g.ctu_rows * NK;  // key slots of the frame
     if (mine && in_range(b.status, kbase + tid, nk_frame)) {
         reinterpret_cast<int16_t *>(a.block + rinf.off.dep_cx)[kbase + tid] = cx;
@@ -174,12 +179,15 @@ __global__ void __launch_bounds__(kRulesThreads) k_dep_rules(const __grid_consta
     __syncthreads();
 
     // a searched CU's task: item | key slot << 8, centre in the high word; its
-    // origin.  An inherited CU: a table slot from the top of the class's room.
+    // origin.  An inherited CU with a table: a slot from the top of the class's
+    // room (without one: none, -1).
     int pos = -1;
     if (f & kRuleEvaluated) {
         if (f & kRuleInherited) {
-            const unsigned int k = s_base[kSizeClasses + c] + atomicAdd(&s_cnt[kSizeClasses + c], 1u);
-            if (k < b.cap[c]) pos = static_cast<int>(b.cap[c] - 1 - k);
+            if (inh_table) {
+                const unsigned int k = s_base[kSizeClasses + c] + atomicAdd(&s_cnt[kSizeClasses + c], 1u);
+                if (k < b.cap[c]) pos = static_cast<int>(b.cap[c] - 1 - k);
+            }
         } else {
             const unsigned int p = s_base[c] + atomicAdd(&s_cnt[c], 1u);
             if (p < b.cap[c]) {
@@ -196,8 +204,10 @@ __global__ void __launch_bounds__(kRulesThreads) k_dep_rules(const __grid_consta
         s_inh[tid] = (f & kRuleInherited) ? 1 : 0;
     }
     __syncthreads();
-    // a searched CU's inherited ancestors (parent, then grandparent while the
-    // parent is inherited too): its lanes add their SADs into their tables
+    // a searched CU's inherited ancestors with tables (parent, then grandparent
+    // while the parent is inherited too): its lanes add their SADs into their
+    // tables.  Only single-piece CUs find one: an inherited parent of CUs with
+    // tables has none, and an inherited CU has a table, so its parent has none.
     if ((f & kRuleEvaluated) && !(f & kRuleInherited) && pos >= 0 && c >= kFirstUpClass && c < kSizeClasses - 1 &&
         c < C::DMAX) {
         uint32_t up1 = kNoUp, up2 = kNoUp;
@@ -1252,15 +1262,26 @@ __global__ void __launch_bounds__(kDecideThreads, 8) k_dep_decide(const __grid_c
     __shared__ uint8_t s_fl[C::NKEY];
     __shared__ int s_slot[NBIG > 0 ? NBIG : 1];  // 16x16 CTUs have no CU of 32x32
     __shared__ unsigned long long s_best[NBIG > 0 ? NBIG : 1];
+    // a 64x64 CTU whose SADs are its four sub-CUs' sums: their tables added
+    // up entry by entry, (2r + 1)^2 entries, r <= 32
+    __shared__ unsigned int s_ctu_sum[CTU == 64 ? 65 * 65 : 1];
     for (int i = tid; i < C::NKEY; i += kDecideThreads) {
         s_fl[i] = __ldcg(in_fl + i);
-        if (i < NBIG) s_slot[i] = __ldcg(in_slot + i);
+        if (i < NBIG) {
+            s_slot[i] = __ldcg(in_slot + i);
+            s_best[i] = ~0ull;
+        }
     }
     __syncthreads();
     // CUs searched in pieces: argmin of (SAD, |dx|+|dy|, dy, dx) over the
     // CU's sum table, 16 lanes per CU.  A lane loads kScanBatch entries
-    // before it uses any (one L2 round trip per batch, two for r = 8).
-    auto summed = [&](int i) { return i < NBIG && s_slot[i] >= 0 && (CTU >> depth_of(i, C::DMAX)) > b.range; };
+    // before it uses any (one L2 round trip per batch, two for r = 8).  An
+    // inherited CU whose sub-CUs have tables of their own (only the CTU can
+    // be one: a 64x64 CU with 32x32 sub-CUs) has none: the sub-CUs' lanes add
+    // the entries they load into a shared copy, which the whole CTA then scans.
+    auto own_table = [&](int i) { return i < NBIG && s_slot[i] >= 0 && (CTU >> depth_of(i, C::DMAX)) > b.range; };
+    const bool ctu_kids = CTU == 64 && NBIG > 0 && (s_fl[0] & kRuleInherited) && (CTU >> 1) > b.range;
+    auto summed = [&](int i) { return own_table(i) || (i == 0 && ctu_kids); };
     {
         constexpr int kScanBatch = 10;
         const int hl = tid & 15;
@@ -1269,10 +1290,21 @@ __global__ void __launch_bounds__(kDecideThreads, 8) k_dep_decide(const __grid_c
         // candidate row of entry k: (k + 1/2) / K in fp32 is at least 1/(2K)
         // from an integer for k < 2^16, so the truncation is exact
         const float inv_k = 1.0f / static_cast<float>(K);
+        auto key_of = [&](int k, unsigned int v) {
+            const int dy = static_cast<int>((static_cast<float>(k) + 0.5f) * inv_k);
+            const int dxo = k - dy * K - r, dyo = dy - r;
+            const uint32_t tb = static_cast<uint32_t>((abs(dxo) + abs(dyo)) * KK + k);
+            return (static_cast<unsigned long long>(v) << 32) | tb;
+        };
+        if (ctu_kids) {  // the same for the whole CTA
+            for (int k = tid; k < KK; k += kDecideThreads) s_ctu_sum[k] = 0;
+            __syncthreads();
+        }
         for (int i = tid >> 4; i < NBIG; i += kDecideThreads / 16) {
-            if (!summed(i) || !(s_fl[i] & kRuleEvaluated)) continue;  // the same for the 16 lanes
+            if (!own_table(i) || !(s_fl[i] & kRuleEvaluated)) continue;  // the same for the 16 lanes
             if (!in_range(b.status, s_slot[i], b.cap[C::DMAX - depth_of(i, C::DMAX)])) continue;
             const unsigned int *sum = b.sums[C::DMAX - depth_of(i, C::DMAX)] + static_cast<long>(s_slot[i]) * KK;
+            const bool feed = ctu_kids && i >= 1 && i <= 4;  // a sub-CU of the CTU
             unsigned long long best = ~0ull;
             for (int k0 = hl; k0 < KK; k0 += 16 * kScanBatch) {
                 unsigned int v[kScanBatch];
@@ -1282,10 +1314,9 @@ __global__ void __launch_bounds__(kDecideThreads, 8) k_dep_decide(const __grid_c
                 for (int u = 0; u < kScanBatch; ++u) {
                     const int k = k0 + 16 * u;
                     if (k >= KK) break;
-                    const int dy = static_cast<int>((static_cast<float>(k) + 0.5f) * inv_k);
-                    const int dxo = k - dy * K - r, dyo = dy - r;
-                    const uint32_t tb = static_cast<uint32_t>((abs(dxo) + abs(dyo)) * KK + k);
-                    const unsigned long long key = (static_cast<unsigned long long>(v[u]) << 32) | tb;
+                    if constexpr (CTU == 64)
+                        if (feed) atomicAdd(&s_ctu_sum[k], v[u]);
+                    const unsigned long long key = key_of(k, v[u]);
                     best = key < best ? key : best;
                 }
             }
@@ -1295,6 +1326,22 @@ __global__ void __launch_bounds__(kDecideThreads, 8) k_dep_decide(const __grid_c
                 best = v < best ? v : best;
             }
             if (hl == 0) s_best[i] = best;
+        }
+        if constexpr (CTU == 64) {
+            if (ctu_kids) {
+                __syncthreads();
+                unsigned long long best = ~0ull;
+                for (int k = tid; k < KK; k += kDecideThreads) {
+                    const unsigned long long key = key_of(k, s_ctu_sum[k]);
+                    best = key < best ? key : best;
+                }
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) {
+                    const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+                    best = v < best ? v : best;
+                }
+                if ((tid & 31) == 0) atomicMin(&s_best[0], best);
+            }
         }
     }
     __syncthreads();
