@@ -62,7 +62,7 @@ struct DepSet {
     unsigned long long *tasks[kSizeClasses] = {};
     unsigned int *pos[kSizeClasses] = {};
     unsigned int *sums[kSizeClasses] = {};
-    unsigned long long *up[kSizeClasses] = {};  // classes kFirstUpClass .. kSizeClasses - 2
+    unsigned int *up[kSizeClasses] = {};  // classes kFirstUpClass .. kSizeClasses - 2
     bool counts_dirty = false;  // counters not known to be zero (zeroed with the arena at init)
     cudaEvent_t done = nullptr;
     bool recorded = false;
@@ -675,7 +675,7 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
         l->task_cap[c] = static_cast<unsigned int>(std::min<size_t>(cap, 0xffffffffu));
         task_bytes += kDepSets * (align_up(cap * 8, 256) + align_up(cap * 4, 256));
         if (c >= kFirstSummedClass) task_bytes += kDepSets * align_up(cap * kr2 * 4, 256);
-        if (c >= kFirstUpClass && c < kSizeClasses - 1) task_bytes += kDepSets * align_up(cap * 8, 256);
+        if (c >= kFirstUpClass && c < kSizeClasses - 1) task_bytes += kDepSets * align_up(cap * 4, 256);
     }
     const size_t fixed = 256 + task_bytes;
     l->arena_bytes = fixed + per_slot * geometry->max_frames;
@@ -705,8 +705,8 @@ ladder_status ladder_init(const ladder_geometry *geometry, void *cuda_stream, la
                     tp += align_up(static_cast<size_t>(l->task_cap[c]) * kr2 * 4, 256);
                 }
                 if (c >= kFirstUpClass && c < kSizeClasses - 1) {
-                    ds.up[c] = reinterpret_cast<unsigned long long *>(tp);
-                    tp += align_up(static_cast<size_t>(l->task_cap[c]) * 8, 256);
+                    ds.up[c] = reinterpret_cast<unsigned int *>(tp);
+                    tp += align_up(static_cast<size_t>(l->task_cap[c]) * 4, 256);
                 }
             }
         }

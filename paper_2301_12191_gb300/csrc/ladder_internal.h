@@ -314,11 +314,9 @@ struct DependentItem {
 // own centre is inherited: it has no task and its SADs are the sums of its
 // sub-CUs'.  If they are single pieces, its table (a slot counted down from
 // the top of the class's capacity) takes the SADs their lanes add into it,
-// named by up[c][task] of each sub-CU (low word; 0xffffffff: none).  If they
-// have tables of their own (a 64x64 CU of 32x32 sub-CUs at pieces of 16), it
-// has none: the decisions add the four tables entry by entry.  (The high
-// word, a grandparent, is never set: an inherited parent has a table, so the
-// grandparent's table is the decisions' sum.)
+// named by up[c][task] of each sub-CU (0xffffffff: none).  If they have
+// tables of their own (a 64x64 CU of 32x32 sub-CUs at pieces of 16), it has
+// none: the decisions add the four tables entry by entry.
 constexpr int kSizeClasses = 4;
 constexpr int kFirstSummedClass = 2;
 constexpr int kFirstUpClass = kFirstSummedClass - 1;  // classes whose CUs may have an inherited ancestor
@@ -344,8 +342,8 @@ struct DependentBatch {
     unsigned long long *tasks[kSizeClasses];  // per size class, capacity cap[c]
     unsigned int *pos[kSizeClasses];          // per task: the CU's origin, x | y << 16
     unsigned int *sums[kSizeClasses];         // classes >= kFirstSummedClass: cap[c] x (2r+1)^2
-    unsigned long long *up[kSizeClasses];     // classes kFirstUpClass .. kSizeClasses - 2: per task, the
-                                              // inherited ancestors' table slots (low word parent, high grandparent)
+    unsigned int *up[kSizeClasses];           // classes kFirstUpClass .. kSizeClasses - 2: per task, the table
+                                              // slot of the CU's inherited parent (kNoUp: none)
     unsigned int cap[kSizeClasses];
     unsigned int *counts;   // kDepCounters counters, zero before the rules kernel: tasks per class, inherited
                             // CUs per class (their table slots count down from cap[c] - 1), the next tile

@@ -204,24 +204,16 @@ __global__ void __launch_bounds__(kRulesThreads) k_dep_rules(const __grid_consta
         s_inh[tid] = (f & kRuleInherited) ? 1 : 0;
     }
     __syncthreads();
-    // a searched CU's inherited ancestors with tables (parent, then grandparent
-    // while the parent is inherited too): its lanes add their SADs into their
-    // tables.  Only single-piece CUs find one: an inherited parent of CUs with
-    // tables has none, and an inherited CU has a table, so its parent has none.
+    // a searched CU's inherited parent with a table: its lanes add their SADs
+    // into that table too.  Only single-piece CUs have one (an inherited
+    // parent of CUs with tables has none), and the chain ends there: an
+    // inherited CU has a table, so an inherited grandparent has none.
     if ((f & kRuleEvaluated) && !(f & kRuleInherited) && pos >= 0 && c >= kFirstUpClass && c < kSizeClasses - 1 &&
         c < C::DMAX) {
-        uint32_t up1 = kNoUp, up2 = kNoUp;
-        if (d >= 1) {
-            const int pi = dev::key_index(d - 1, (cyl >> 1) * (n >> 1) + (cxl >> 1));
-            if (s_inh[pi] && s_pos[pi] >= 0) {
-                up1 = static_cast<uint32_t>(s_pos[pi]);
-                if (d >= 2) {
-                    const int gi = dev::key_index(d - 2, (cyl >> 2) * (n >> 2) + (cxl >> 2));
-                    if (s_inh[gi] && s_pos[gi] >= 0) up2 = static_cast<uint32_t>(s_pos[gi]);
-                }
-            }
-        }
-        b.up[c][pos] = static_cast<unsigned long long>(up1) | (static_cast<unsigned long long>(up2) << 32);
+        uint32_t up = kNoUp;
+        const int pi = dev::key_index(d - 1, (cyl >> 1) * (n >> 1) + (cxl >> 1));
+        if (s_inh[pi] && s_pos[pi] >= 0) up = static_cast<uint32_t>(s_pos[pi]);
+        b.up[c][pos] = up;
     }
     if (tid < NBIG) s_big[tid] = S > b.range ? pos : -1;
     __syncthreads();
@@ -496,29 +488,24 @@ __device__ __forceinline__ int sad_bits(int S, int bit_depth)
     return (S == 8 ? 6 : S == 16 ? 8 : S == 32 ? 10 : 12) + bit_depth;
 }
 
-// A searched CU's lane adds its candidates' SADs into the tables of the CU's
-// inherited ancestors (kRuleInherited), every candidate once: no padding
-// lanes (the caller's), no rows a clamped band shares with the band before
-// it, no rows past +r.
+// A searched CU's lane adds its candidates' SADs into the table of the CU's
+// inherited parent, if it has one (kRuleInherited), every candidate once: no
+// padding lanes (the caller's), no rows a clamped band shares with the band
+// before it, no rows past +r.
 template <int TY>
 __device__ __forceinline__ void add_to_ancestors(const DependentBatch &b, int c, unsigned int u, int dxi, int dy0,
                                                  int b0, const uint32_t (&acc)[TY])
 {
     if (c < kFirstUpClass || c >= kSizeClasses - 1 || !b.inherit) return;
     const int r = b.r, K = 2 * r + 1;
-    const unsigned long long up = __ldcg(b.up[c] + u);
+    const uint32_t slot = __ldcg(b.up[c] + u);
+    if (slot == kNoUp || !in_range(b.status, slot, b.cap[c + 1])) return;
+    unsigned int *sum = b.sums[c + 1] + static_cast<long>(slot) * (K * K);
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const uint32_t slot = static_cast<uint32_t>(up >> (32 * k));
-        const int cls = c + 1 + k;
-        if (slot == kNoUp || cls >= kSizeClasses || !in_range(b.status, slot, b.cap[cls])) return;
-        unsigned int *sum = b.sums[cls] + static_cast<long>(slot) * (K * K);
-#pragma unroll
-        for (int i = 0; i < TY; ++i) {
-            const int dyo = dy0 + i;
-            if (dyo >= b0 && dyo <= r && in_range(b.status, (dyo + r) * K + dxi, K * K))
-                atomicAdd(sum + (dyo + r) * K + dxi, acc[i]);
-        }
+    for (int i = 0; i < TY; ++i) {
+        const int dyo = dy0 + i;
+        if (dyo >= b0 && dyo <= r && in_range(b.status, (dyo + r) * K + dxi, K * K))
+            atomicAdd(sum + (dyo + r) * K + dxi, acc[i]);
     }
 }
 
