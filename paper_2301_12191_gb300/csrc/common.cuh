@@ -432,15 +432,17 @@ struct CtuState {
     int npairs;
 };
 
-struct DecideIO {
+template <typename O>
+struct DecideIOT {
     const void *cur, *ref;
     long pitch_bytes;
     const RungGeom *g;
     int qp, satd_mode;
     const int *lambda_q16;  // 52 entries
-    DevDecisions out;
+    O out;                  // DevDecisions or OffDecisions
     int *status;            // debug builds record failed bounds checks here (may be null)
 };
+using DecideIO = DecideIOT<DevDecisions>;
 
 // Index of CU (d, local raster li) in the per-CTU key layout.
 __device__ __forceinline__ int key_index(int d, int li) { return key_offset(d) + li; }
@@ -516,8 +518,8 @@ enum : int {
 //             lengths of the quarter-pel components of vector - predictor
 //   split  -- Sec. 2.1: split iff it may and (it is not a leaf candidate or
 //             the children's best sum is strictly lower), or it must
-template <int CTU>
-__device__ void ctu_split(CtuState<CTU> &st, int lam, const RungGeom &g, const DevDecisions &out, int write, int x0,
+template <int CTU, typename O>
+__device__ void ctu_split(CtuState<CTU> &st, int lam, const RungGeom &g, const O &out, int write, int x0,
                           int y0, bool qpel = false, const int16_t *pmx = nullptr, const int16_t *pmy = nullptr,
                           int *status = nullptr)
 {
@@ -559,17 +561,17 @@ __device__ void ctu_split(CtuState<CTU> &st, int lam, const RungGeom &g, const D
             const long gi = static_cast<long>(y0 / S + li / n) * g.cols[d] + x0 / S + li % n;
             if (!in_range(status, gi, static_cast<long>(g.cols[d]) * g.rows[d])) continue;
             if (write & kSplitWriteVectors) {
-                out.mvx[d][gi] = st.mvx[i];
-                out.mvy[d][gi] = st.mvy[i];
-                out.satd[d][gi] = ev ? st.satd[i] : INT32_MAX;
+                out.at_mvx(d)[gi] = st.mvx[i];
+                out.at_mvy(d)[gi] = st.mvy[i];
+                out.at_satd(d)[gi] = ev ? st.satd[i] : INT32_MAX;
             }
             if ((write & kSplitWriteAll) == kSplitWriteAll) {
-                out.sad[d][gi] = st.sad[i];
-                out.evaluated[d][gi] = ev ? 1 : 0;
+                out.at_sad(d)[gi] = st.sad[i];
+                out.at_evaluated(d)[gi] = ev ? 1 : 0;
             }
-            out.cost[d][gi] = J;
-            out.best[d][gi] = best;
-            out.split[d][gi] = split;
+            out.at_cost(d)[gi] = J;
+            out.at_best(d)[gi] = best;
+            out.at_split(d)[gi] = split;
         }
         __syncthreads();
     }
@@ -586,9 +588,9 @@ __device__ void ctu_split(CtuState<CTU> &st, int lam, const RungGeom &g, const D
         }
         const long li = static_cast<long>(py / 8) * g.cols8 + px / 8;
         if (!in_range(status, li, static_cast<long>(g.cols8) * g.rows8)) continue;
-        out.leaf_depth[li] = static_cast<uint8_t>(d);
-        out.leaf_mvx[li] = st.mvx[i];
-        out.leaf_mvy[li] = st.mvy[i];
+        out.at_leaf_depth()[li] = static_cast<uint8_t>(d);
+        out.at_leaf_mvx()[li] = st.mvx[i];
+        out.at_leaf_mvy()[li] = st.mvy[i];
     }
 }
 
@@ -596,8 +598,8 @@ __device__ void ctu_split(CtuState<CTU> &st, int lam, const RungGeom &g, const D
 // (satd[] must be zero): SATD at the chosen vectors, then ctu_split.  All
 // threads of the CTA take part.
 //   SATD   -- Sec. 5.4.1 SATD equation; Sec. 5.4.2 satd8 / satd_8x4 listings
-template <typename T, int CTU>
-__device__ void ctu_decide(CtuState<CTU> &st, const DecideIO &io, int x0, int y0)
+template <typename T, int CTU, typename O>
+__device__ void ctu_decide(CtuState<CTU> &st, const DecideIOT<O> &io, int x0, int y0)
 {
     using C = Ctu<CTU>;
     const RungGeom &g = *io.g;

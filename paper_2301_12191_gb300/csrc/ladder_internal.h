@@ -119,13 +119,25 @@ struct RungGeom {
     FastDiv div_2w, div_2h;  // division by 2W, 2H
 };
 
-// Device decision arrays of one (rung, frame slot).
+// Device decision arrays of one (rung, frame slot).  The at_* accessors are
+// the interface the decision step writes through (OffDecisions has the same).
 struct DevDecisions {
     int16_t *mvx[kMaxDepths], *mvy[kMaxDepths];
     int32_t *sad[kMaxDepths], *satd[kMaxDepths], *cost[kMaxDepths], *best[kMaxDepths];
     uint8_t *split[kMaxDepths], *evaluated[kMaxDepths];
     uint8_t *leaf_depth;
     int16_t *leaf_mvx, *leaf_mvy;
+    __host__ __device__ int16_t *at_mvx(int d) const { return mvx[d]; }
+    __host__ __device__ int16_t *at_mvy(int d) const { return mvy[d]; }
+    __host__ __device__ int32_t *at_sad(int d) const { return sad[d]; }
+    __host__ __device__ int32_t *at_satd(int d) const { return satd[d]; }
+    __host__ __device__ int32_t *at_cost(int d) const { return cost[d]; }
+    __host__ __device__ int32_t *at_best(int d) const { return best[d]; }
+    __host__ __device__ uint8_t *at_split(int d) const { return split[d]; }
+    __host__ __device__ uint8_t *at_evaluated(int d) const { return evaluated[d]; }
+    __host__ __device__ uint8_t *at_leaf_depth() const { return leaf_depth; }
+    __host__ __device__ int16_t *at_leaf_mvx() const { return leaf_mvx; }
+    __host__ __device__ int16_t *at_leaf_mvy() const { return leaf_mvy; }
 };
 
 // Byte offsets of the decision arrays (and the per-CTU argmin keys) inside
@@ -177,6 +189,27 @@ __host__ __device__ inline DevDecisions decisions_at(char *base, const DecOffset
     d.leaf_mvy = reinterpret_cast<int16_t *>(array_at(base, o.leaf_mvy));
     return d;
 }
+
+// The same arrays as a block and its offsets, for a kernel whose offsets sit
+// in its parameters: each address is formed where it is used, so no table
+// of pointers is held per thread (a kernel at 64 registers kept that table
+// in local memory).  `base` is a rung block (never null here).
+struct OffDecisions {
+    char *base;
+    const DecOffsets *off;
+    template <typename P> __device__ P *at(long o) const { return reinterpret_cast<P *>(base + o); }
+    __device__ int16_t *at_mvx(int d) const { return at<int16_t>(off->mvx[d]); }
+    __device__ int16_t *at_mvy(int d) const { return at<int16_t>(off->mvy[d]); }
+    __device__ int32_t *at_sad(int d) const { return at<int32_t>(off->sad[d]); }
+    __device__ int32_t *at_satd(int d) const { return at<int32_t>(off->satd[d]); }
+    __device__ int32_t *at_cost(int d) const { return at<int32_t>(off->cost[d]); }
+    __device__ int32_t *at_best(int d) const { return at<int32_t>(off->best[d]); }
+    __device__ uint8_t *at_split(int d) const { return at<uint8_t>(off->split[d]); }
+    __device__ uint8_t *at_evaluated(int d) const { return at<uint8_t>(off->evaluated[d]); }
+    __device__ uint8_t *at_leaf_depth() const { return at<uint8_t>(off->leaf_depth); }
+    __device__ int16_t *at_leaf_mvx() const { return at<int16_t>(off->leaf_mvx); }
+    __device__ int16_t *at_leaf_mvy() const { return at<int16_t>(off->leaf_mvy); }
+};
 
 constexpr int kMaxRungs = 16;
 constexpr int kMaxItems = 64;                    // frames per batched launch

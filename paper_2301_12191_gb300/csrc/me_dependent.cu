@@ -1352,8 +1352,8 @@ __global__ void __launch_bounds__(kDecideThreads, 8) k_dep_decide(const __grid_c
     // keys back to ~0 for the next search of this rung
     for (int i = tid; i < C::NKEY; i += kDecideThreads)
         const_cast<unsigned long long *>(keys)[i] = ~0ull;
-    dev::DecideIO io{a.cur, a.ref, a.pitch_bytes, &rinf.g, a.qp, b.satd_mode, c_lambda_q16,
-                     decisions_at(a.block, rinf.off), b.status};
+    dev::DecideIOT<OffDecisions> io{a.cur, a.ref, a.pitch_bytes, &rinf.g, a.qp, b.satd_mode, c_lambda_q16,
+                     OffDecisions{a.block, &rinf.off}, b.status};
     dev::ctu_decide<T, CTU>(st, io, x0, y0);
 }
 
