@@ -1221,7 +1221,7 @@ __global__ void __launch_bounds__(kStageThreads, 4)
 
 // ---- 3. decide --------------------------------------------------------------
 template <typename T, int CTU>
-__global__ void __launch_bounds__(kDecideThreads, 8) k_dep_decide(const __grid_constant__ DependentBatch b)
+__global__ void __launch_bounds__(kDecideThreads, 10) k_dep_decide(const __grid_constant__ DependentBatch b)
 {
     dev::chain_entry();
     // the search has completed: its task counters go back to zero for the
