@@ -488,18 +488,23 @@ __device__ __forceinline__ int sad_bits(int S, int bit_depth)
     return (S == 8 ? 6 : S == 16 ? 8 : S == 32 ? 10 : 12) + bit_depth;
 }
 
-// A searched CU's lane adds its candidates' SADs into the table of the CU's
-// inherited parent, if it has one (kRuleInherited), every candidate once: no
-// padding lanes (the caller's), no rows a clamped band shares with the band
-// before it, no rows past +r.
-template <int TY>
-__device__ __forceinline__ void add_to_ancestors(const DependentBatch &b, int c, unsigned int u, int dxi, int dy0,
-                                                 int b0, const uint32_t (&acc)[TY])
+// The table slot of the inherited parent of task u of class c (kNoUp: none;
+// kRuleInherited).
+__device__ __forceinline__ uint32_t parent_slot(const DependentBatch &b, int c, unsigned int u)
 {
-    if (c < kFirstUpClass || c >= kSizeClasses - 1 || !b.inherit) return;
-    const int r = b.r, K = 2 * r + 1;
-    const uint32_t slot = __ldcg(b.up[c] + u);
+    return (c >= kFirstUpClass && c < kSizeClasses - 1 && b.inherit) ? __ldcg(b.up[c] + u) : kNoUp;
+}
+
+// A searched CU's lane adds its candidates' SADs into the table of the CU's
+// inherited parent (slot from parent_slot), every candidate once: no padding
+// lanes (the caller's), no rows a clamped band shares with the band before
+// it, no rows past +r.
+template <int TY>
+__device__ __forceinline__ void add_to_parent(const DependentBatch &b, int c, uint32_t slot, int dxi, int dy0, int b0,
+                                              const uint32_t (&acc)[TY])
+{
     if (slot == kNoUp || !in_range(b.status, slot, b.cap[c + 1])) return;
+    const int r = b.r, K = 2 * r + 1;
     unsigned int *sum = b.sums[c + 1] + static_cast<long>(slot) * (K * K);
 #pragma unroll
     for (int i = 0; i < TY; ++i) {
@@ -566,7 +571,7 @@ __device__ __forceinline__ void search_tile(const DependentBatch &b, int c, int 
         }
     }
 
-    if (traw < ntask) add_to_ancestors<TY>(b, c, u, dxi, dy0, b0, acc);
+    if (traw < ntask) add_to_parent<TY>(b, c, parent_slot(b, c, u), dxi, dy0, b0, acc);
     if (nr > 1) {
         // add this range's SADs to the CU's table; every candidate exactly
         // once: no padding lanes, no rows a clamped band shares with the
@@ -1054,6 +1059,11 @@ __device__ __forceinline__ void stage_compute(const DependentBatch &b, const Sta
         win = buf;
         curw = buf;
     }
+    // the CU's task word and inherited parent, loaded before the SADs (used
+    // after them)
+    const unsigned int ucu = q >> (2 * t.lg);
+    const unsigned long long task = __ldcg(b.tasks[t.c] + ucu);
+    const uint32_t up = parent_slot(b, t.c, ucu);
     uint32_t acc[TY];
 #pragma unroll
     for (int i = 0; i < TY; ++i) acc[i] = 0;
@@ -1090,9 +1100,7 @@ __device__ __forceinline__ void stage_compute(const DependentBatch &b, const Sta
         }
     }
 
-    const unsigned int ucu = q >> (2 * t.lg);
-    if (traw < t.ntask) add_to_ancestors<TY>(b, t.c, ucu, dxi, dy0, b0, acc);
-    const unsigned long long task = __ldcg(b.tasks[t.c] + ucu);
+    if (traw < t.ntask) add_to_parent<TY>(b, t.c, up, dxi, dy0, b0, acc);
     const uint32_t lo = static_cast<uint32_t>(task);
     const DependentItem &a = b.item[lo & 0xffu];
     const RungInfo &rinf = b.rung[a.rung];
