@@ -97,7 +97,7 @@ DATA = ("synthetic (seeded sinusoid texture + planted global/patch motion + nois
 # of a launch grows with its ladders.
 KERNEL_SOURCES = {"full_search": ["me_full.cu", "common.cuh"], "dependent": ["me_dependent.cu", "common.cuh"]}
 TRAFFIC_NCU = {
-    ("dependent", "uhd8", "e6c20f7a196b"): {"bytes": (259421696 + 40295424) * 8 // 3,
+    ("dependent", "uhd8", "076570b74ddb"): {"bytes": (259427328 + 36680960) * 8 // 3,
                                             "knobs": {"dep_band": 17, "dep_range": 16, "dep_staged": 1,
                                                       "dep_inherit": 1}},
     ("full_search", "uhd8", "fb7e3970fc46"): {"bytes": 2999296 * 8 // 3, "knobs": {"fs_band": 13}},
